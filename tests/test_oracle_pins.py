@@ -1,0 +1,446 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: exact
+properties of the equilibrium, a brute-force entropy minimisation, special
+cases the paper states (gamma = 2 is LBGK), invariants (conservation,
+uniform flow, mirror symmetry), and closed-form flows (Taylor-Green decay,
+Poiseuille profile, conduction state).  CPU only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1608_06915_gb300 import inputs as I
+
+C = np.array([[(i % 3) - 1, (i // 3) % 3 - 1, i // 9 - 1] for i in range(27)], dtype=np.float64)
+W1 = {0: 2.0 / 3.0, -1: 1.0 / 6.0, 1: 1.0 / 6.0}
+W = np.array([W1[int(c[0])] * W1[int(c[1])] * W1[int(c[2])] for c in C])
+OPP = np.array([26 - i for i in range(27)])
+
+
+def rand_state(rng, amp=0.01, u=None):
+    """A near-equilibrium population set: f^eq(rho,u) plus a perturbation."""
+    rho = 1.0 + 0.05 * rng.uniform(-1, 1)
+    u = rng.uniform(-0.08, 0.08, 3) if u is None else np.asarray(u)
+    f = O.feq(rho, u) * (1.0 + amp * rng.uniform(-1, 1, 27))
+    return f
+
+
+def newton_equilibrium(rho, u):
+    """Minimise H = sum f ln(f/W) under mass and momentum constraints by Newton
+    iteration on the Lagrange multipliers: f_i = W_i exp(chi + zeta . c_i)."""
+    lam = np.zeros(4)
+    A = np.hstack([np.ones((27, 1)), C])
+    target = np.concatenate([[rho], rho * np.asarray(u)])
+    for _ in range(60):
+        f = W * np.exp(A @ lam)
+        r = A.T @ f - target
+        J = (A * f[:, None]).T @ A
+        lam -= np.linalg.solve(J, r)
+        if np.max(np.abs(r)) < 1e-16:
+            break
+    return W * np.exp(A @ lam)
+
+
+def moments_of(f):
+    return np.array([np.sum(f * C[:, 0] ** p * C[:, 1] ** q * C[:, 2] ** r)
+                     for r in range(3) for q in range(3) for p in range(3)])
+
+
+# --- pin 1: f^eq carries exactly rho and rho u (Eq. feq_iso with the conservation laws)
+def test_feq_moments():
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        rho = rng.uniform(0.8, 1.2)
+        u = rng.uniform(-0.15, 0.15, 3)
+        f = O.feq(rho, u)
+        assert abs(f.sum() - rho) < 1e-14
+        assert np.max(np.abs(C.T @ f - rho * u)) < 1e-14
+        assert np.all(f > 0)
+
+
+# --- pin 2: f^eq minimises H under the constraints (brute force, Eq. feq_min)
+def test_feq_is_entropy_minimiser():
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        rho = rng.uniform(0.8, 1.2)
+        u = rng.uniform(-0.12, 0.12, 3)
+        assert np.max(np.abs(O.feq(rho, u) - newton_equilibrium(rho, u))) < 1e-10
+
+
+def test_feq_rest_state_is_weights():
+    assert np.max(np.abs(O.feq(1.0, [0, 0, 0]) - W)) < 1e-16
+    assert abs(W.sum() - 1.0) < 1e-15
+
+
+# --- pin 3: equilibrium is a fixed point of the collision
+def test_equilibrium_fixed_point():
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        f = O.feq(rng.uniform(0.9, 1.1), rng.uniform(-0.1, 0.1, 3))
+        out, gam = O.collide(f, 0.9)
+        assert np.max(np.abs(out - f)) < 1e-15
+
+
+# --- pin 4: KBC with gamma = 2 is LBGK with omega = 2 beta (Eq. f_mirr, text after it)
+def test_gamma_two_is_lbgk():
+    rng = np.random.default_rng(3)
+    for beta in (0.55, 0.9, 0.99):
+        for _ in range(10):
+            f = rand_state(rng)
+            m = f.sum(), (C.T @ f) / f.sum()
+            fe = newton_equilibrium(m[0], m[1])
+            lbgk = f + 2.0 * beta * (fe - f)
+            out, _ = O.collide(f, beta, gamma=2.0)
+            assert np.max(np.abs(out - lbgk)) < 1e-14
+            out2, _ = O.collide(f, beta, lbgk=True)
+            assert np.max(np.abs(out2 - lbgk)) < 1e-14
+
+
+# --- the KBC split (Eq. popSplit): k carries the conserved moments, s the
+# deviatoric stress and nothing else, and k + s + h = f
+def test_kbc_split_moments():
+    rng = np.random.default_rng(4)
+    idx = lambda p, q, r: p + 3 * q + 9 * r
+    for _ in range(20):
+        f = rand_state(rng, amp=0.05)
+        k, s, h = O.split(f)
+        assert np.max(np.abs(k + s + h - f)) < 1e-15
+        mf, mk, ms, mh = moments_of(f), moments_of(k), moments_of(s), moments_of(h)
+        cons = [idx(0, 0, 0), idx(1, 0, 0), idx(0, 1, 0), idx(0, 0, 1)]
+        for j in range(27):
+            want_k = mf[j] if j in cons else 0.0
+            assert abs(mk[j] - want_k) < 1e-14
+        P = np.array([[np.sum(f * C[:, a] * C[:, b]) for b in range(3)] for a in range(3)])
+        Pd = P - np.trace(P) / 3.0 * np.eye(3)
+        want = np.zeros(27)
+        want[idx(2, 0, 0)], want[idx(0, 2, 0)], want[idx(0, 0, 2)] = Pd[0, 0], Pd[1, 1], Pd[2, 2]
+        want[idx(1, 1, 0)], want[idx(1, 0, 1)], want[idx(0, 1, 1)] = Pd[0, 1], Pd[0, 2], Pd[1, 2]
+        assert np.max(np.abs(ms - want)) < 1e-14
+        # h holds the trace and everything of order > 2, no conserved moment
+        for j in cons:
+            assert abs(mh[j]) < 1e-14
+        assert abs(mh[idx(2, 0, 0)] + mh[idx(0, 2, 0)] + mh[idx(0, 0, 2)] - np.trace(P)) < 1e-13
+
+
+# --- pin 5 (per node): mass and momentum conservation; EDM adds rho du exactly
+def test_collision_conservation():
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        f = rand_state(rng, amp=0.03)
+        for du in ([0, 0, 0], [1e-4, -2e-4, 3e-5]):
+            out, _ = O.collide(f, 0.8, du=du)
+            assert abs(out.sum() - f.sum()) < 1e-14
+            assert np.max(np.abs(C.T @ out - C.T @ f - f.sum() * np.asarray(du))) < 1e-14
+
+
+# --- pin 6: gamma is the exact minimiser of the quadratic entropy norm
+# <f' - f^eq | f' - f^eq> (the expansion behind Eq. gamma_min_approx) and close
+# to the minimiser of the true H for near-equilibrium states
+def _quad_norm(fp, fe):
+    return np.sum((fp - fe) ** 2 / fe)
+
+
+def _H(fp):
+    return np.sum(fp * np.log(fp / W))
+
+
+def test_gamma_minimises_entropy_norm():
+    rng = np.random.default_rng(6)
+    for beta in (0.6, 0.95):
+        for _ in range(10):
+            f = rand_state(rng, amp=0.02)
+            rho = f.sum()
+            fe = newton_equilibrium(rho, (C.T @ f) / rho)
+            _, gam = O.collide(f, beta)
+            g = np.array([0.0, 1.0, 2.0])
+            N = np.array([_quad_norm(O.collide(f, beta, gamma=gi)[0], fe) for gi in g])
+            a2 = (N[2] - 2 * N[1] + N[0]) / 2.0
+            a1 = N[1] - N[0] - a2
+            g_star = -a1 / (2.0 * a2)
+            assert abs(g_star - gam) < 1e-8 * max(1.0, abs(gam))
+            # true entropy: golden-section search around the estimate
+            lo, hi = gam - 1.0, gam + 1.0
+            phi = (math.sqrt(5) - 1) / 2
+            for _ in range(80):
+                a = hi - phi * (hi - lo)
+                b = lo + phi * (hi - lo)
+                if _H(O.collide(f, beta, gamma=a)[0]) < _H(O.collide(f, beta, gamma=b)[0]):
+                    hi = b
+                else:
+                    lo = a
+            assert abs(0.5 * (lo + hi) - gam) < 2e-2 * max(1.0, abs(gam))
+
+
+def test_gamma_tends_to_two_near_equilibrium_lbgk_limit():
+    # a pure-shear non-equilibrium (h-part zero) leaves gamma on the guard
+    f = O.feq(1.0, [0.02, 0.0, 0.0])
+    k, s, h = O.split(f)
+    _, gam = O.collide(f, 0.9)
+    assert gam == 2.0
+
+
+# --- pin 7: the four-point Lagrange rule (Eq. interp) is the printed
+# (-1, 9, 9, -1)/16, sums to one and is exact for cubics
+def test_lagrange_weights():
+    w = O.lagrange_weights()
+    assert np.max(np.abs(w - np.array([-1, 9, 9, -1]) / 16.0)) < 1e-16
+    x = np.array([-3.0, -1.0, 1.0, 3.0])
+    rng = np.random.default_rng(7)
+    for _ in range(10):
+        p = rng.normal(size=4)
+        vals = p[0] + p[1] * x + p[2] * x ** 2 + p[3] * x ** 3
+        assert abs(np.dot(w, vals) - p[0]) < 1e-14
+    quartic = x ** 4
+    assert abs(np.dot(w, quartic)) > 1.0  # not exact beyond cubic: the rule is genuinely 4-point
+
+
+# ---------------------------------------------------------------------------
+# whole-simulation pins
+
+def make(case, fields):
+    o = O.Oracle(case)
+    for p, info in enumerate(o.patches):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        out = fields(x, y, z, p, info)
+        o.init_equilibrium(p, *out)
+    return o
+
+
+def fluid_totals(o, level_weighted=False):
+    mass, mom = 0.0, np.zeros(3)
+    for p, info in enumerate(o.patches):
+        f = o.get_pop(p)
+        m = o.mask(p) == 1
+        mass += f.sum(axis=0)[m].sum()
+        mom += np.array([np.tensordot(C[:, a], f, axes=(0, 0))[m].sum() for a in range(3)])
+    return mass, mom
+
+
+# --- pin 5 (box): a periodic single-level box conserves mass and momentum
+def test_periodic_box_conservation():
+    rng = np.random.default_rng(8)
+    case = I.tgv_case(n=12, refined=False)
+
+    def fields(x, y, z, p, info):
+        return 1.0 + 0.01 * rng.uniform(-1, 1, x.shape), 0.03 * rng.uniform(-1, 1, (3,) + x.shape)
+
+    o = make(case, fields)
+    m0, j0 = fluid_totals(o)
+    o.step(10)
+    m1, j1 = fluid_totals(o)
+    assert abs(m1 - m0) / m0 < 1e-13
+    assert np.max(np.abs(j1 - j0)) / m0 < 1e-13
+
+
+# --- pin 8: uniform flow crosses every interface unchanged (non-equilibrium
+# zero, interpolation exact on constants, rescaling leaves equilibrium alone)
+@pytest.mark.parametrize("which", ["two_level", "three_level"])
+def test_uniform_flow_stays_uniform(which):
+    if which == "two_level":
+        case = I.tgv_case(n=24, box=(6, 18))
+    else:
+        case = I.tgv_case(n=32, box=(4, 28))
+        case["boxes"] = case["boxes"] + [(2, (10, 10, 10), (22, 22, 22))]
+    u = (0.05, 0.02, -0.01)
+    o = make(case, lambda x, y, z, p, info: I.uniform_fields(x, u))
+    o.step(3)
+    want = O.feq(1.0, u)
+    for p in range(len(o.patches)):
+        f = o.get_pop(p)
+        m = o.mask(p) == 1
+        err = np.max(np.abs(f[:, m] - want[:, None]))
+        assert err < 1e-14, (p, err)
+
+
+# --- pin 9: Taylor-Green decay against exp(-2 nu k^2 t), single- and two-level,
+# and the mirror symmetry of the two-level run about x = n/2
+def tgv_amplitude(o, n):
+    num, den = 0.0, 0.0
+    for p, info in enumerate(o.patches):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        _, shape = I.tgv_fields(x, y, z, n=n, u0=1.0)
+        _, u, _, _ = o.moments(p)
+        m = o.mask(p) == 1
+        w = 8.0 ** (-info["level"])
+        num += w * np.sum((u * shape)[:, m])
+        den += w * np.sum((shape * shape)[:, m])
+    return num / den
+
+
+@pytest.mark.parametrize("refined", [False, True])
+def test_taylor_green_decay(refined):
+    n, nu, u0 = 24, 0.05, 0.02
+    case = I.tgv_case(n=n, box=(6, 18), nu=nu, refined=refined)
+    o = make(case, lambda x, y, z, p, info: I.tgv_fields(x, y, z, n=n, u0=u0, pressure=True))
+    k = 2 * math.pi / n
+    o.step(10)
+    a1 = tgv_amplitude(o, n)
+    o.step(60)
+    a2 = tgv_amplitude(o, n)
+    rate = -math.log(a2 / a1) / 60.0
+    assert abs(rate / (2 * nu * k * k) - 1.0) < 0.01, rate / (2 * nu * k * k)
+
+
+def test_two_level_mirror_symmetry():
+    n = 24
+    case = I.tgv_case(n=n, box=(6, 18), nu=0.02)
+    o = make(case, lambda x, y, z, p, info: I.tgv_fields(x, y, z, n=n, u0=0.05))
+    o.step(4)
+    # mirror x -> n - x maps direction (cx,cy,cz) to (-cx,cy,cz)
+    mir = np.array([(2 - i % 3) + 3 * ((i // 3) % 3) + 9 * (i // 9) for i in range(27)])
+    for p, info in enumerate(o.patches):
+        f = o.get_pop(p)
+        s = 1 << info["level"]
+        ox, dx = info["org"][0], info["dim"][0]
+        # node X maps to s*n - X (periodic on level 0)
+        X = np.arange(ox, ox + dx)
+        Xm = (s * n - X) % (s * n)
+        j = Xm - ox
+        ok = (j >= 0) & (j < dx)
+        fm = f[mir][:, :, :, j[ok]]
+        m = o.mask(p)[:, :, ok] == 1
+        diff = np.abs(f[:, :, :, ok] - fm)[:, m]
+        assert diff.max() < 1e-13, (p, diff.max())
+
+
+# --- pin 10: laminar Poiseuille flow through three levels of wall bands
+def test_poiseuille_three_levels():
+    case = I.channel_case(n=(4, 32, 4), l1=8, l2=4, re_tau=5.0, u_tau=0.004)
+    H = case["height"]
+    a = case["accel0"][0]
+    nu0 = case["nu0"]
+
+    def exact(y):
+        yw = y - case["wall_lo"]
+        return a * yw * (H - yw) / (2.0 * nu0)
+
+    def fields(x, y, z, p, info):
+        return np.ones_like(x), np.stack([exact(y), 0 * y, 0 * y])
+
+    o = make(case, fields)
+    o.step(400)
+    umax = exact(case["wall_lo"] + H / 2)
+    worst = 0.0
+    for p, info in enumerate(o.patches):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        _, u, _, _ = o.moments(p)
+        m = o.mask(p) == 1
+        worst = max(worst, np.max(np.abs(u[0][m] - exact(y[m]))) / umax)
+        assert np.max(np.abs(u[1][m])) < 1e-6 * umax
+    assert worst < 2e-3, worst
+
+
+# --- layout: node counts of the two-level Taylor-Green case (32^3 with the
+# box [8,24]^3: 32^3 - 13^3 coarse nodes and 33^3 fine nodes)
+def test_tgv_layout_counts():
+    o = O.Oracle(I.tgv_case())
+    counts = [int((o.mask(p) == 1).sum()) for p in range(2)]
+    assert counts == [32 ** 3 - 13 ** 3, 33 ** 3]
+    assert o.node_updates_per_step() == 32 ** 3 - 13 ** 3 + 2 * 33 ** 3
+
+
+# --- thermal pins (Sec. II.B)
+def test_grad_equilibrium_moments():
+    rng = np.random.default_rng(9)
+    t0 = 1.0 / 3.0
+    for _ in range(10):
+        rho = rng.uniform(0.9, 1.1)
+        u = rng.uniform(-0.05, 0.05, 3)
+        T = t0 * (1 + 0.03 * rng.uniform(-1, 1))
+        g = O.geq(rho, u, T)
+        E2 = rho * (3 * T + u @ u)
+        assert abs(g.sum() - E2) < 1e-14
+        q = C.T @ g
+        assert np.max(np.abs(q - (E2 * u + 2 * rho * t0 * u))) < 1e-14
+        R = np.array([[np.sum(g * C[:, a] * C[:, b]) for b in range(3)] for a in range(3)])
+        Req = E2 * (t0 * np.eye(3) + np.outer(u, u)) + 2 * rho * t0 * (t0 * np.eye(3) + 2 * np.outer(u, u))
+        assert np.max(np.abs(R - Req)) < 1e-14
+
+
+def test_thermal_collision_conserves_energy_and_mass():
+    rng = np.random.default_rng(10)
+    t0 = 1.0 / 3.0
+    for _ in range(10):
+        rho = rng.uniform(0.95, 1.05)
+        u = rng.uniform(-0.04, 0.04, 3)
+        T = t0 * (1 + 0.02 * rng.uniform(-1, 1))
+        f = O.feq(rho, u) * (1 + 0.01 * rng.uniform(-1, 1, 27))
+        g = O.geq(rho, u, T) * (1 + 0.01 * rng.uniform(-1, 1, 27))
+        fo, go, _ = O.thermal_collide(f, g, 0.9, 0.8)
+        assert abs(go.sum() - g.sum()) < 1e-14
+        assert abs(fo.sum() - f.sum()) < 1e-14
+        assert np.max(np.abs(C.T @ fo - C.T @ f)) < 1e-14
+
+
+def test_thermal_g_relaxes_heat_flux_with_beta1():
+    # for Pr <= 1 the non-equilibrium heat flux q - q^eq - 2 u.(P - P^eq) relaxes with beta1
+    t0 = 1.0 / 3.0
+    rho, u, T = 1.0, np.array([0.0, 0.0, 0.0]), t0
+    f = O.feq(rho, u)
+    g = O.geq(rho, u, T) + 1e-4 * W * C[:, 0] / t0  # pure heat-flux perturbation along x
+    beta, beta1 = 0.9, 0.7
+    _, go, _ = O.thermal_collide(f, g, beta, beta1)
+    q_in = C.T @ g
+    q_out = C.T @ go
+    assert abs(q_out[0] - (1 - 2 * beta1) * q_in[0]) < 1e-15
+
+
+def test_conduction_state_is_steady():
+    # linear temperature between isothermal plates, fluid at rest, no buoyancy
+    case = I.rbc_small_case()
+    case["thermal"] = dict(case["thermal"], glambda=0.0)
+    th = case["thermal"]
+    H = case["height"]
+
+    def fields(x, y, z, p, info):
+        zw = z - case["wall_lo"]
+        T = th["wall_T"][4] + (th["wall_T"][5] - th["wall_T"][4]) * zw / H
+        return np.ones_like(z), np.zeros((3,) + z.shape), T
+
+    o = make(case, fields)
+    o.step(20)
+    worst = 0.0
+    for p, info in enumerate(o.patches):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        _, u, T, _ = o.moments(p)
+        m = o.mask(p) == 1
+        zw = z - case["wall_lo"]
+        Tex = th["wall_T"][4] + (th["wall_T"][5] - th["wall_T"][4]) * zw / H
+        worst = max(worst, np.max(np.abs(T[m] - Tex[m])) / th["dT"])
+        assert np.max(np.abs(u[:, m])) < 1e-6
+    assert worst < 1e-3, worst
+
+
+def test_thermal_heat_flux_combination_relaxes_with_beta1():
+    # Pr <= 1 (Table I rows f*, g*): with a pure-shear non-equilibrium f (k and h at
+    # equilibrium), X = (q - q^eq) - 2 u.(P - P^eq) relaxes as X' = (1 - 2 beta1) X,
+    # whatever u; the sign of the u.(P - P^eq) term in g* decides this.
+    rng = np.random.default_rng(11)
+    t0 = 1.0 / 3.0
+    for _ in range(5):
+        rho = rng.uniform(0.95, 1.05)
+        u = rng.uniform(-0.03, 0.03, 3)
+        T = t0 * (1 + 0.02 * rng.uniform(-1, 1))
+        fe = O.feq(rho, u)
+        _, s, _ = O.split(1e-2 * rng.normal(size=27))
+        f = fe + s
+        g = O.geq(rho, u, T) + 1e-5 * rng.normal(size=27)
+        beta, beta1 = 0.9, 0.6
+
+        def X(fp, gp):
+            E2 = gp.sum()
+            rr = fp.sum()
+            uu = (C.T @ fp) / rr
+            q = C.T @ gp
+            qeq = E2 * uu + 2 * rr * t0 * uu
+            P = np.array([[np.sum(fp * C[:, a] * C[:, b]) for b in range(3)] for a in range(3)])
+            Peq = rr * t0 * np.eye(3) + rr * np.outer(uu, uu)
+            return q - qeq - 2.0 * (P - Peq) @ uu
+
+        fo, go, _ = O.thermal_collide(f, g, beta, beta1)
+        x0, x1 = X(f, g), X(fo, go)
+        # tolerance: the closed-form P^eq differs from sum cc f^eq at O(u^4)
+        assert np.max(np.abs(x1 - (1 - 2 * beta1) * x0)) < 1e-2 * np.max(np.abs(x0)), (x0, x1)
