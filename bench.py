@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Throughput of the grid-refined KBC step on one GB300 (or N replicas).
+
+Workload (default): the three-level turbulent-channel layout -- 256x64x128
+coarse nodes, periodic x/z, half-way bounce-back walls in y, 2x bands
+(y in [0,8], [55,63]) and 4x bands (y in [0,4], [59,63]), body force for
+Re_tau = 180, laminar profile plus seeded +-5% perturbations, FP32.
+A step is one coarse step: every level advances once per 2^-level of the
+coarse time step (78,184,448 node updates).
+
+Metric: fine-node-equivalent MLUPS = node updates per coarse step x steps /
+time / 1e6.  The dominant kernel's HBM roofline fraction is reported next to
+it, from CUDA events around each of its launches inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (fine-node equiv) and % of HBM roofline; adjoint/forward time ratio"
+UNIT = "MLUPS"
+BYTES_PER_UPDATE = {"fp64": 432, "fp32": 216, "fp16s": 108, "bf16s": 108}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16s": "f32", "bf16s": "f32"}
+L2_BYTES = 129e6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--workload", choices=["channel", "channel-half", "tgv", "sphere"], default="channel")
+    ap.add_argument("--storage", choices=sorted(BYTES_PER_UPDATE), default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1608_06915_gb300 import inputs as I
+    if name in ("channel", "channel-half"):
+        n = (256, 64, 128) if name == "channel" else (128, 64, 64)
+        case = I.channel_case(n=n)
+
+        def fields(info):
+            return I.channel_fields(case, info["level"], info["org"], info["dim"])
+        desc = "channel %dx%dx%d coarse, 3 levels (2x y in [0,8],[55,63]; 4x y in [0,4],[59,63]), Re_tau=180" % n
+        return case, fields, desc
+    if name == "sphere":
+        case = I.sphere_case()
+
+        def fields(info):
+            x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+            return I.uniform_fields(x, (0.05, 0.0, 0.0))
+        return case, fields, "sphere wake 384x192x192 coarse, 4 levels, D=64 finest nodes, Re=3700"
+    case = I.tgv_case()
+
+    def fields(info):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        return I.tgv_fields(x, y, z)
+    return case, fields, "Taylor-Green 32^3 with [8,24]^3 refined 2x"
+
+
+def sample_case(name):
+    """Bounded sample of the workload for the oracle: the same layout and
+    parameters with the periodic extents reduced."""
+    from paper_1608_06915_gb300 import inputs as I
+    if name in ("channel", "channel-half"):
+        case = I.channel_case(n=(16, 64, 8))
+
+        def fields(info):
+            return I.channel_fields(case, info["level"], info["org"], info["dim"])
+        return case, fields, "channel 16x64x8 coarse (x/z extents of the 256x64x128 case reduced), same bands"
+    if name == "sphere":
+        case = I.sphere_case(scale=8)
+
+        def fields(info):
+            x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+            return I.uniform_fields(x, (0.05, 0.0, 0.0))
+        return case, fields, "sphere 48x24x24 coarse, same nesting"
+    case, fields, _ = workload(name)
+    return case, fields, "Taylor-Green 32^3 with [8,24]^3 refined"
+
+
+# ---------------------------------------------------------------------------
+def oracle_run(name, seconds=None, steps=None, warmup=0):
+    """Time the FP64 oracle on the bounded sample: either for about `seconds`
+    of work, or exactly `steps` coarse steps after `warmup`."""
+    from oracle import oracle as O
+    O.build()
+    case, fields, desc = sample_case(name)
+    o = O.Oracle(case)
+    for p, info in enumerate(o.patches):
+        out = fields(info)
+        o.init_equilibrium(p, *out)
+    nup = o.node_updates_per_step()
+    for _ in range(warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    done = 0
+    if steps is not None:
+        o.step(steps)
+        done = steps
+    else:
+        while True:
+            o.step(1)
+            done += 1
+            if time.perf_counter() - t0 >= seconds:
+                break
+    dt = time.perf_counter() - t0
+    return dict(value=nup * done / dt / 1e6, unit=UNIT, cores=O.max_threads(), kind="oracle",
+                sample="%s; %d coarse step(s), %.0f node updates each, %.1f s" % (desc, done, nup, dt),
+                seconds=dt, steps=done)
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    r = oracle_run(args.workload, steps=args.steps, warmup=args.warmup)
+    _, _, desc = workload(args.workload)
+    line = dict(impl="reference", metric=METRIC, value=r["value"], unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * r["seconds"] / r["steps"], higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=desc, storage="fp64 (oracle)", sample=r["sample"]),
+                cpu_baseline=dict(value=r["value"], unit=UNIT, cores=r["cores"], kind="oracle", sample=r["sample"]),
+                e2e=dict(value=r["value"], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9 or c[0] != self.gpu:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if c[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("device.cuh", "kernels.cu"):
+        with open(os.path.join(ROOT, "paper_1608_06915_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_name, workload_name, storage):
+    """DRAM bytes per launch recorded in profiles/ for this kernel source, else None."""
+    path = os.path.join(ROOT, "profiles", "%s_%s_%s.md" % (kernel_name, workload_name, storage))
+    if not os.path.exists(path):
+        return None
+    want = source_hash()
+    traffic, srch = None, None
+    for line in open(path):
+        if line.startswith("source_hash:"):
+            srch = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if srch == want else None
+
+
+def end_to_end(args, g, L, host_fields, dfields, nup, world, barrier, dev):
+    """The metric through the public API with host buffers: pinned H2D of the
+    initial fields, init, K coarse steps, moments and D2H of rho and u."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    stream = g.stream
+    h_in = [(torch.from_numpy(np.ascontiguousarray(r, dtype=np.float32)).pin_memory(),
+             torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).pin_memory()) for r, u in host_fields]
+    h_out = [(torch.empty_like(a).pin_memory(), torch.empty_like(b).pin_memory()) for a, b in h_in]
+    d_out = [(torch.empty_like(dr), torch.empty_like(du)) for dr, du in dfields]
+    h2d = sum(a.numel() * 4 + b.numel() * 4 for a, b in h_in)
+    d2h = h2d
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        f0.record(stream)
+        for p, ((hr, hu), (dr, du)) in enumerate(zip(h_in, dfields)):
+            dr.copy_(hr, non_blocking=True)
+            du.copy_(hu, non_blocking=True)
+            g.init_equilibrium(p, dr, du)
+        g.step(args.steps)
+        for p, ((orr, ou), (hr, hu)) in enumerate(zip(d_out, h_out)):
+            L.lib().lbm_moments(g.handle, p, L.Grid._ptr(orr), L.Grid._ptr(ou), None, None, 0)
+            hr.copy_(orr, non_blocking=True)
+            hu.copy_(ou, non_blocking=True)
+        f1.record(stream)
+    barrier()
+    te = f0.elapsed_time(f1) / 1e3
+    te_t = torch.tensor([te], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+    te = float(te_t.item())
+    e2e = dict(value=nup * args.steps * world / te / 1e6, unit=UNIT, h2d_bytes_per_step=h2d / args.steps,
+               d2h_bytes_per_step=d2h / args.steps,
+               note="per job: H2D of initial rho,u (pinned), init, %d coarse steps, D2H of rho,u; grid layout "
+                    "built and bound before timing" % args.steps)
+    return e2e
+
+
+def cuda_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1608_06915_gb300 import lbm as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    case, fields, desc = workload(args.workload)
+    g = L.Grid(case, args.storage, device=dev)
+    host_fields = [fields(info) for info in g.patches]
+    dfields = []
+    for p, (rho, u) in enumerate(host_fields):
+        dr = torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float32)).to(dev)
+        du = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).to(dev)
+        dfields.append((dr, du))
+        g.init_equilibrium(p, dr, du)
+    nup = g.node_updates()
+    stream = g.stream
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up
+    g.step(args.warmup)
+    barrier()
+    # timed region: K coarse steps, events on the grid's stream, per-launch events inside
+    clocks = Clocks(local) if rank == 0 else None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.timing(True)
+    e0.record(stream)
+    g.step(args.steps)
+    e1.record(stream)
+    barrier()
+    report = g.timing_report()
+    g.timing(False)
+    clk = clocks.stop() if clocks else None
+    t = e0.elapsed_time(e1) / 1e3
+    tt = torch.tensor([t], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    t = float(tt.item())
+    diag = g.diagnostics()
+    value = nup * args.steps * world / t / 1e6
+
+    # dominant kernel: the class with the largest device time
+    top = max(report, key=lambda r: r["ms"])
+    bpu = BYTES_PER_UPDATE[args.storage]
+    avg_ms = top["ms"] / top["launches"]
+    nodes_per_launch = top["nodes"] / top["launches"]
+    alg_bytes = nodes_per_launch * bpu
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
+    traffic = ncu_traffic("k_stream_collide", args.workload, args.storage)
+    roofline = dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=traffic,
+                    peak_source="measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                    kernel="k_stream_collide level %d" % top["level"] if top["kind"] == "stream_collide"
+                    else "%s level %d" % (top["kind"], top["level"]),
+                    avg_launch_ms=avg_ms, alg_bytes_per_launch=alg_bytes, bytes_per_node_update=bpu)
+    kernels = [dict(r, avg_us=1e3 * r["ms"] / r["launches"]) for r in report]
+    launches = sum(r["launches"] for r in report)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(args, g, L, host_fields, dfields, nup, world, barrier, dev)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r = oracle_run(args.workload, seconds=15.0)
+        cpu = dict(value=r["value"], unit=UNIT, cores=r["cores"], kind="oracle", sample=r["sample"])
+
+    if rank == 0:
+        ws = g.device_bytes
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=1e3 * t / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                    dtype=DTYPE[args.storage], data="synthetic",
+                    config=dict(workload=desc, storage=args.storage, node_updates_per_coarse_step=nup,
+                                parallelism="replicas" if world > 1 else "single GPU",
+                                l2="no flush: working set %.2f GB > %.0f MB L2" % (ws / 1e9, L2_BYTES / 1e6)),
+                    roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clk,
+                    kernels=kernels,
+                    diagnostics=dict(mass=diag["mass"], min_rho=diag["min_rho"], status=diag["status"]))
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return cuda_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

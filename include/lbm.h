@@ -1,0 +1,206 @@
+/*
+ * lbm.h -- C ABI of liblbm.so: grid-refined entropic lattice Boltzmann
+ * (D3Q27 KBC) on one GPU.
+ *
+ * The method is that of Dorschner, Frapolli, Chikatamarla & Karlin, "Grid
+ * refinement for entropic lattice Boltzmann models" (arXiv:1608.06915):
+ *   - per level, the lattice Boltzmann equation with the KBC mirror state and
+ *     entropic stabiliser gamma (Sec. II.A, Eqs. f_equations, feq_iso,
+ *     popSplit, f_mirr, gamma_min_approx);
+ *   - the two-population thermal model for Pr <= 1 (Sec. II.B);
+ *   - multi-domain refinement with r = 2: twin-node non-equilibrium
+ *     rescaling (Sec. III.A, Eq. f_neq_rescaling_iso and the thermal g
+ *     rule), centred four-point Lagrange reconstruction (Sec. III.B,
+ *     Eq. interp) and the five-step algorithm without time interpolation
+ *     (Sec. III.C), with the fine level taking two steps per parent step;
+ *   - a body force by the exact difference method, du_f = du_c / r (Sec. III.A).
+ *
+ * Conventions
+ *   Velocities: i = (cx+1) + 3(cy+1) + 9(cz+1); rest i = 13; opposite 26 - i.
+ *   Units: everything in the descriptor is in coarse (level-0) lattice units.
+ *   Level l has spacing 2^-l; its integer node coordinates are 2^l times the
+ *   coarse coordinates.
+ *   Layout: a patch is one refinement box of one level; its nodes live in a
+ *   storage box (the bounding box of its nodes, lbm_patch_info).  Arrays that
+ *   cross this ABI are dense over the storage box, x fastest: [z][y][x] for
+ *   scalars, [27][z][y][x] for populations and [3][z][y][x] for vectors.
+ *   Memory: the library allocates no device memory.  lbm_grid_bytes reports
+ *   the size of the one device buffer a grid needs (populations, node tables,
+ *   interface tables and workspace); the caller allocates it and hands it to
+ *   lbm_grid_bind, and frees it after lbm_grid_destroy.  All other pointers
+ *   marked "device" are caller-owned device memory; "host" pointers are
+ *   caller-owned host memory that the call only reads during the call.
+ *   Streams: every call that launches work enqueues it on the stream given
+ *   to lbm_grid_bind and returns without waiting, unless it says otherwise.
+ *   Errors: every call returns an lbm_status; nothing aborts.  A failed call
+ *   leaves a message retrievable with lbm_last_error.
+ */
+#ifndef LBM_H_
+#define LBM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_grid* lbm_grid_t;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,      /* bad argument (null pointer, out-of-range index, size) */
+  LBM_ERR_LAYOUT = -2,   /* refinement layout violates the nesting rules */
+  LBM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+  LBM_ERR_OOM = -4,      /* bound buffer smaller than lbm_grid_bytes */
+  LBM_ERR_UNSTABLE = -5, /* non-finite or non-positive density detected */
+  LBM_ERR_TIMEOUT = -6,  /* a bounded device-side wait expired */
+  LBM_ERR_STATE = -7     /* call not valid in the grid's current state */
+} lbm_status;
+
+typedef enum {
+  LBM_FP64 = 0,       /* populations stored and collided in double */
+  LBM_FP32 = 1,       /* stored and collided in float */
+  LBM_FP16_SHIFT = 2, /* stored as half of f_i - W_i*rho0 (rho0 = 1), collided in float */
+  LBM_BF16_SHIFT = 3  /* stored as bfloat16 of f_i - W_i*rho0, collided in float */
+} lbm_storage;
+
+typedef enum { LBM_ISO_KBC = 0, LBM_THERMAL_KBC = 1 } lbm_model;
+
+/* One refinement box: level >= 1, closed box [lo, hi] in coarse node
+ * coordinates.  A box of level l must lie inside a box of level l-1 (or the
+ * domain for l = 1), at least 4 level-(l-1) nodes inside its interface faces
+ * and at least 8 level-(l-1) spacings wide across each interface axis.  A box
+ * covering all coarse nodes of a periodic axis spans it (no interface there);
+ * a face on a wall is a wall face (no interface there). */
+typedef struct {
+  int32_t level;
+  int32_t lo[3], hi[3];
+} lbm_box;
+
+typedef struct {
+  int32_t n[3];             /* coarse node counts */
+  uint32_t periodic;        /* bit a: axis a periodic */
+  uint32_t walls;           /* bit 2a: half-way bounce-back wall below node 0 of axis a,
+                               bit 2a+1: above the last node (isothermal for g) */
+  int32_t inflow_axis;      /* -1: none; else equilibrium inlet at the min face of this
+                               axis (level 0) and zero-gradient outlet at the max face */
+  double u_in[3];           /* inlet velocity (inlet density 1) */
+  const lbm_box* boxes;     /* host; copied by lbm_grid_create */
+  int32_t n_boxes;
+  const uint8_t* solid;     /* host, nullable: solid mask on level solid_level, [z][y][x]
+                               over solid_dims starting at solid_lo (that level's
+                               coordinates); copied by lbm_grid_create */
+  int32_t solid_level;
+  int32_t solid_lo[3];
+  int32_t solid_dims[3];
+  double nu0;               /* coarse kinematic viscosity (beta_0 from Eq. visc) */
+  double accel0[3];         /* body acceleration, coarse units (isothermal model) */
+  lbm_model model;
+  double pr, t0, glambda, t_ref; /* thermal: Prandtl (<= 1), T0, g*lambda, Boussinesq T_ref */
+  double wall_T[6];         /* thermal wall temperatures per wall face (bit order of walls) */
+  lbm_storage storage;
+  int32_t mirror_lbgk;      /* 1: LBGK mirror state (gamma fixed at 2) */
+} lbm_desc;
+
+/* Builds the level/patch layout, node classes and interface tables
+ * (Sec. III, Fig. 1 layout) and validates the nesting rules.
+ * desc: host, read during the call.  out: receives the handle.
+ * Returns LBM_ERR_LAYOUT (with a message) for invalid layouts. */
+lbm_status lbm_grid_create(const lbm_desc* desc, lbm_grid_t* out);
+
+/* Size in bytes of the device buffer the grid needs. */
+lbm_status lbm_grid_bytes(lbm_grid_t g, size_t* device_bytes);
+
+/* Binds caller-owned device memory (at least lbm_grid_bytes, 256-byte
+ * aligned) and a CUDA stream (cudaStream_t, may be 0) to the grid and uploads
+ * the node and interface tables.  Synchronises that stream before returning. */
+lbm_status lbm_grid_bind(lbm_grid_t g, void* dev_ptr, size_t bytes, void* cuda_stream);
+
+/* Releases the host-side descriptor and tables; does not free bound memory. */
+lbm_status lbm_grid_destroy(lbm_grid_t g);
+
+/* Number of patches (index 0 is level 0) and number of levels. */
+lbm_status lbm_num_patches(lbm_grid_t g, int32_t* n_patches, int32_t* n_levels);
+
+/* Patch metadata: level, parent patch (-1 for level 0), storage-box origin
+ * (level coordinates) and extents, and the relaxation parameters beta, beta1
+ * of its level (Sec. III.A: beta_f = 1/(1 + r(1/beta_c - 1))). */
+lbm_status lbm_patch_info(lbm_grid_t g, int32_t patch, int32_t* level, int32_t* parent, int64_t org[3],
+                          int64_t dim[3], double* beta, double* beta1);
+
+/* Node classes over the storage box, host output [z][y][x]: 0 no node (hole
+ * or outside), 1 fluid, 2 solid. */
+lbm_status lbm_patch_mask(lbm_grid_t g, int32_t patch, uint8_t* host_out);
+
+/* Node updates per coarse step, sum over levels of fluid nodes * 2^level
+ * (the fine-node-equivalent count behind the MLUPS metric). */
+lbm_status lbm_node_updates(lbm_grid_t g, double* per_coarse_step);
+
+/* f = f^eq(rho, u) (Eq. feq_iso) on every fluid node of a patch, and for the
+ * thermal model g = g^eq(rho, u, T) (Table I, Eq. grad_general).  Inlet nodes
+ * take f^eq(1, u_in).  rho: device [z][y][x]; u: device [3][z][y][x];
+ * T: device [z][y][x] or NULL (T0).  dtype: 0 float, 1 double. */
+lbm_status lbm_init_equilibrium(lbm_grid_t g, int32_t patch, const void* rho, const void* u, const void* T,
+                                int32_t dtype);
+
+/* Advances n_coarse_steps coarse steps: one coarse step runs the algorithm of
+ * Sec. III.C recursively, level l taking 2^l steps.  Asynchronous. */
+lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps);
+
+/* Macroscopic fields of a patch's current populations: rho, u = j/rho + du/2
+ * (du of the level's body force, Sec. III.A), T (thermal, else T0) and the
+ * stabiliser gamma that Eq. gamma_min_approx gives for the stored state.
+ * All device outputs, nullable, layouts as above; dtype 0 float, 1 double. */
+lbm_status lbm_moments(lbm_grid_t g, int32_t patch, void* rho, void* u, void* T, void* gamma, int32_t dtype);
+
+/* Copies a patch's current populations (which = 0: f, 1: g) to/from a device
+ * array [27][z][y][x], unshifted, dtype 0 float, 1 double. */
+lbm_status lbm_get_populations(lbm_grid_t g, int32_t patch, int32_t which, void* dst, int32_t dtype);
+lbm_status lbm_set_populations(lbm_grid_t g, int32_t patch, int32_t which, const void* src, int32_t dtype);
+
+/* Sets the body acceleration (coarse units) and, if drag_out is non-NULL,
+ * returns the FP64 momentum-exchange force on the solid nodes of the current
+ * state (coarse units, summed over levels).  Synchronises when drag_out is set. */
+lbm_status lbm_force(lbm_grid_t g, const double* accel0, double* drag_out);
+
+/* FP64 diagnostics over owned fluid nodes (parent nodes that are not twin
+ * nodes of a child, child nodes of depth >= 1), volume-weighted 8^-level:
+ * out = {mass, jx, jy, jz, kinetic energy 1/2 rho |u|^2, fluid node count,
+ * min rho, device status word}.  Synchronises the stream.  Returns
+ * LBM_ERR_UNSTABLE when a density is non-finite or non-positive. */
+lbm_status lbm_diagnostics(lbm_grid_t g, double out[8]);
+
+/* Bytes of one checkpoint (all patches' current f and g populations). */
+lbm_status lbm_checkpoint_bytes(lbm_grid_t g, size_t* bytes);
+
+/* save = 1: copies the current state to dev_dst; save = 0: restores it.
+ * dev: caller-owned device buffer of lbm_checkpoint_bytes. */
+lbm_status lbm_checkpoint(lbm_grid_t g, void* dev, int32_t save);
+
+/* One KBC collision (Eqs. f_equations, f_mirr, gamma_min_approx, plus the
+ * exact-difference-method force du) of n independent nodes: f_in, f_out
+ * device [27][n]; gamma_out device [n] or NULL; dtype 0 float, 1 double.
+ * The same device code the step runs; used to test the collision alone. */
+lbm_status lbm_collide_nodes(const void* f_in, void* f_out, void* gamma_out, int64_t n, double beta,
+                             const double du[3], int32_t lbgk, int32_t dtype, void* cuda_stream);
+
+/* Kernel timing for measurement: enable = 1 makes lbm_step bracket every
+ * kernel it launches with CUDA events on the bound stream (and clears earlier
+ * records); 0 stops recording.  Not part of the method. */
+lbm_status lbm_timing(lbm_grid_t g, int32_t enable);
+
+/* Synchronises the bound stream and reports, per kernel class, the number of
+ * launches recorded, their summed device time (ms) and the fluid nodes they
+ * wrote.  kind: 0 stream_collide, 1 coalesce, 2 samples, 3 explode; level:
+ * the level of the patch written.  Host outputs of length max_rows;
+ * *n_rows receives the number of classes. */
+lbm_status lbm_timing_report(lbm_grid_t g, int32_t max_rows, int32_t* n_rows, int32_t* kind, int32_t* level,
+                             int64_t* launches, double* ms, double* nodes);
+
+const char* lbm_last_error(lbm_grid_t g); /* NULL g: last error of lbm_grid_create */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H_ */

@@ -1,0 +1,560 @@
+// C ABI of liblbm.so (declared in include/lbm.h) and the refined-step scheduler.
+//
+// Time stepping (Sec. III.C, generalised to L levels with r = 2): a coarse step
+// is 2^(L-1) instants; level l is active at every 2^(L-1-l)-th instant, i.e.
+// it takes 2^l steps.  At an instant every active patch is streamed and
+// collided from its previous state into its other buffer; the patch's twin
+// nodes toward each child are coalesced from the child's previous state; and
+// when the patch's parent is active in the same instant (the patch's even
+// steps), its interface layers (depth 0 and 1) are rebuilt from the parent by
+// twin rescaling and reconstruction, then collided -- the explode step.  At
+// the patch's odd steps its depth-1 layer is streamed normally and its depth-0
+// layer is not needed.  This realises steps 1-5 of Sec. III.C without time
+// interpolation: nothing ever reads a parent state between its own steps.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "device.cuh"
+#include "grid.h"
+#include "kernels.h"
+
+using lbm::HostGrid;
+using lbm::HostPatch;
+
+namespace {
+constexpr int kDiagBlocks = 296;  // 2 per SM on 148+ SM parts; fixed for determinism
+std::string g_create_error;
+}  // namespace
+
+struct lbm_grid {
+  HostGrid hg;
+  std::string err;
+  size_t need = 0, bytes = 0;
+  uint8_t* base = nullptr;
+  cudaStream_t stream = nullptr;
+  bool bound = false;
+  size_t off_status = 0, off_partial = 0, off_diag_out = 0;
+  double accel[3] = {0, 0, 0};
+  // measurement: CUDA events around each launch of lbm_step while enabled
+  struct Rec {
+    int kind, level;
+    double nodes;
+    cudaEvent_t e0, e1;
+  };
+  bool timing = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  ~lbm_grid() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+lbm_status fail(lbm_grid* g, lbm_status s, const std::string& m) {
+  if (g) g->err = m;
+  else g_create_error = m;
+  return s;
+}
+
+lbm_status cuda_check(lbm_grid* g, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return LBM_OK;
+  return fail(g, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+lbmk::PatchDev view(const lbm_grid* g, const HostPatch& p) {
+  lbmk::PatchDev v{};
+  for (int a = 0; a < 3; ++a) {
+    v.dim[a] = (int)p.dim[a];
+    v.org[a] = (int)p.org[a];
+    v.maxc[a] = (int)g->hg.maxc(p.level, a);
+    v.span[a] = p.span[a];
+    v.periodic[a] = g->hg.periodic(a);
+  }
+  v.nxp = (int)p.nxp;
+  v.plane = p.plane;
+  v.walls = g->hg.desc.walls;
+  v.inflow = g->hg.desc.inflow_axis;
+  v.type = g->base + p.off_type;
+  return v;
+}
+
+template <typename T>
+T* at(const lbm_grid* g, size_t off) {
+  return reinterpret_cast<T*>(g->base + off);
+}
+
+lbmk::Force level_force(const lbm_grid* g, int level) {
+  lbmk::Force F{};
+  const double s = 1.0 / (double)(1LL << level);  // du_f = du_c / r per level
+  for (int a = 0; a < 3; ++a) F.du[a] = g->accel[a] * s;
+  return F;
+}
+
+int* status_ptr(const lbm_grid* g) { return at<int>(g, g->off_status); }
+
+cudaEvent_t next_event(lbm_grid* g) {
+  if (g->pool_used == g->pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    g->pool.push_back(e);
+  }
+  return g->pool[g->pool_used++];
+}
+
+// Brackets one launch with events when timing is on.
+template <typename F>
+cudaError_t timed(lbm_grid* g, int kind, int level, double nodes, F&& launch) {
+  if (!g->timing) return launch();
+  lbm_grid::Rec r{kind, level, nodes, next_event(g), next_event(g)};
+  if (!r.e0 || !r.e1) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaEventRecord(r.e0, g->stream);
+  if (!e) e = launch();
+  if (!e) e = cudaEventRecord(r.e1, g->stream);
+  g->recs.push_back(r);
+  return e;
+}
+
+double count_types(const HostPatch& p, bool with_d1) { return p.n_bulk + (with_d1 ? p.n_d1 : 0.0); }
+
+lbm_status check_patch(lbm_grid* g, int32_t patch) {
+  if (!g) return LBM_ERR_ARG;
+  if (patch < 0 || patch >= (int32_t)g->hg.P.size()) return fail(g, LBM_ERR_ARG, "patch index out of range");
+  return LBM_OK;
+}
+
+lbm_status check_bound(lbm_grid* g) {
+  if (!g) return LBM_ERR_ARG;
+  if (!g->bound) return fail(g, LBM_ERR_STATE, "grid has no bound device memory");
+  return LBM_OK;
+}
+
+// One instant k (1 .. 2^(L-1)) of the refined step.
+lbm_status run_instant(lbm_grid* g, int k) {
+  HostGrid& hg = g->hg;
+  const int L = hg.nlev;
+  const int storage = hg.desc.storage;
+  const int lbgk = hg.desc.mirror_lbgk;
+  std::vector<int> active;
+  for (int lev = 0; lev < L; ++lev) {
+    const int stride = 1 << (L - 1 - lev);
+    if (k % stride) continue;
+    const int s = k / stride;
+    const bool parent_active = (s % 2) == 0;
+    for (size_t pi = 0; pi < hg.P.size(); ++pi) {
+      HostPatch& p = hg.P[pi];
+      if (p.level != lev) continue;
+      active.push_back((int)pi);
+      const lbmk::PatchDev pv = view(g, p);
+      const lbmk::Force F = level_force(g, lev);
+      void* fin = g->base + p.off_f[p.cur];
+      void* fout = g->base + p.off_f[1 - p.cur];
+      const int odd = (lev > 0 && !parent_active) ? 1 : 0;
+      lbm_status st = cuda_check(
+          g,
+          timed(g, 0, lev, g->timing ? count_types(p, odd) : 0.0,
+                [&] {
+                  cudaError_t e = lbmk::launch_sc_tma(storage, p.tmap[p.cur], p.tmapo[1 - p.cur], p.tmapw[p.cur],
+                                                      pv, at<unsigned long long>(g, p.off_tiles_pure[odd]),
+                                                      (int64_t)p.tiles_pure[odd].size(), p.beta, F, lbgk,
+                                                      status_ptr(g), g->stream);
+                  if (e) return e;
+                  return lbmk::launch_sc_tiles(storage, pv, fin, fout, at<uint32_t>(g, p.off_tiles_mixed[odd]),
+                                               (int64_t)p.tiles_mixed[odd].size(), (int)p.ntx, p.beta, F, odd,
+                                               lbgk, status_ptr(g), g->stream);
+                }),
+          "stream_collide");
+      if (st) return st;
+      for (int ci : p.kids) {
+        HostPatch& c = hg.P[ci];
+        const lbmk::PatchDev cv = view(g, c);
+        st = cuda_check(g,
+                        timed(g, 1, lev, (double)c.cf_parent.size(),
+                              [&] {
+                                return lbmk::launch_coalesce(storage, cv, g->base + c.off_f[c.cur], pv, fout,
+                                                             at<uint32_t>(g, c.off_cf_parent),
+                                                             at<uint32_t>(g, c.off_cf_child),
+                                                             (int64_t)c.cf_parent.size(), 2.0 * c.beta / p.beta,
+                                                             p.beta, F, lbgk, status_ptr(g), g->stream);
+                              }),
+                        "coalesce");
+        if (st) return st;
+      }
+      if (lev > 0 && parent_active) {
+        HostPatch& q = hg.P[p.parent];
+        const lbmk::PatchDev qv = view(g, q);
+        st = cuda_check(g,
+                        timed(g, 2, lev, (double)p.smp_node.size(),
+                              [&] {
+                                return lbmk::launch_samples(storage, qv, g->base + q.off_f[q.cur], pv, fin,
+                                                            at<uint32_t>(g, p.off_smp_node),
+                                                            at<uint8_t>(g, p.off_smp_kind),
+                                                            (int64_t)p.smp_node.size(), g->base + p.off_smp_val,
+                                                            q.beta / (2.0 * p.beta), status_ptr(g), g->stream);
+                              }),
+                        "samples");
+        if (st) return st;
+        st = cuda_check(g,
+                        timed(g, 3, lev, (double)p.ex_node.size(),
+                              [&] {
+                                return lbmk::launch_explode(storage, pv, fout, at<uint32_t>(g, p.off_ex_node),
+                                                            at<uint32_t>(g, p.off_ex_first),
+                                                            at<uint8_t>(g, p.off_ex_mask),
+                                                            at<uint32_t>(g, p.off_ex_sample),
+                                                            (int64_t)p.ex_node.size(), g->base + p.off_smp_val,
+                                                            (int64_t)p.smp_node.size(), p.beta, F, lbgk, g->stream);
+                              }),
+                        "explode");
+        if (st) return st;
+      }
+    }
+  }
+  for (int pi : active) hg.P[pi].cur ^= 1;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_grid_create(const lbm_desc* desc, lbm_grid_t* out) {
+  if (!desc || !out) return fail(nullptr, LBM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (desc->storage < LBM_FP64 || desc->storage > LBM_BF16_SHIFT) return fail(nullptr, LBM_ERR_ARG, "bad storage");
+  if (desc->model != LBM_ISO_KBC) return fail(nullptr, LBM_ERR_ARG, "model not available in this build");
+  if (desc->n_boxes < 0 || (desc->n_boxes > 0 && !desc->boxes)) return fail(nullptr, LBM_ERR_ARG, "bad boxes");
+  lbm_grid* g = new lbm_grid();
+  HostGrid& hg = g->hg;
+  hg.desc = *desc;
+  hg.boxes.assign(desc->boxes, desc->boxes + desc->n_boxes);
+  hg.desc.boxes = nullptr;
+  if (desc->solid) {
+    for (int a = 0; a < 3; ++a)
+      if (desc->solid_dims[a] <= 0) {
+        delete g;
+        return fail(nullptr, LBM_ERR_ARG, "solid mask with empty extent");
+      }
+    size_t ns = (size_t)desc->solid_dims[0] * desc->solid_dims[1] * desc->solid_dims[2];
+    hg.solid.assign(desc->solid, desc->solid + ns);
+  }
+  hg.desc.solid = nullptr;
+  hg.thermal = desc->model == LBM_THERMAL_KBC;
+  hg.pop_bytes = desc->storage == LBM_FP64 ? 8 : desc->storage == LBM_FP32 ? 4 : 2;
+  hg.real_bytes = desc->storage == LBM_FP64 ? 8 : 4;
+  for (int a = 0; a < 3; ++a) g->accel[a] = desc->accel0[a];
+  std::string e = lbm::build_layout(hg);
+  if (!e.empty()) {
+    delete g;
+    return fail(nullptr, LBM_ERR_LAYOUT, e);
+  }
+  for (auto& p : hg.P)
+    if (p.dim[1] > 65535 || p.dim[2] > 65535) {
+      delete g;
+      return fail(nullptr, LBM_ERR_LAYOUT, "patch extent in y or z above 65535 nodes");
+    }
+  for (auto& p : hg.P)
+    for (uint8_t t : p.type) {
+      p.n_bulk += (t == lbm::T_BULK || t == lbm::T_BC);
+      p.n_d1 += (t == lbm::T_D1);
+    }
+  size_t off = lbm::plan_memory(hg);
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += (b + 255) / 256 * 256;
+    return o;
+  };
+  g->off_status = take(64);
+  g->off_partial = take(sizeof(double) * 8 * kDiagBlocks * hg.P.size());
+  g->off_diag_out = take(sizeof(double) * 8);
+  g->need = off;
+  *out = g;
+  return LBM_OK;
+}
+
+lbm_status lbm_grid_bytes(lbm_grid_t g, size_t* device_bytes) {
+  if (!g || !device_bytes) return LBM_ERR_ARG;
+  *device_bytes = g->need;
+  return LBM_OK;
+}
+
+lbm_status lbm_grid_bind(lbm_grid_t g, void* dev_ptr, size_t bytes, void* cuda_stream) {
+  if (!g || !dev_ptr) return fail(g, LBM_ERR_ARG, "null argument");
+  if (bytes < g->need) return fail(g, LBM_ERR_OOM, "bound buffer smaller than lbm_grid_bytes");
+  if (reinterpret_cast<uintptr_t>(dev_ptr) % 256) return fail(g, LBM_ERR_ARG, "device buffer not 256-byte aligned");
+  g->base = static_cast<uint8_t*>(dev_ptr);
+  g->bytes = bytes;
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaStream_t s = g->stream;
+  auto up = [&](size_t off, const void* src, size_t n) -> cudaError_t {
+    if (n == 0) return cudaSuccess;
+    return cudaMemcpyAsync(g->base + off, src, n, cudaMemcpyHostToDevice, s);
+  };
+  cudaError_t e = cudaSuccess;
+  for (auto& p : g->hg.P) {
+    if (!e) e = up(p.off_type, p.type.data(), p.type.size());
+    if (!e) e = up(p.off_ex_node, p.ex_node.data(), 4 * p.ex_node.size());
+    if (!e) e = up(p.off_ex_first, p.ex_first.data(), 4 * p.ex_first.size());
+    if (!e) e = up(p.off_ex_mask, p.ex_mask.data(), p.ex_mask.size());
+    if (!e) e = up(p.off_ex_sample, p.ex_sample.data(), 4 * p.ex_sample.size());
+    if (!e) e = up(p.off_smp_node, p.smp_node.data(), 4 * p.smp_node.size());
+    if (!e) e = up(p.off_smp_kind, p.smp_kind.data(), p.smp_kind.size());
+    if (!e) e = up(p.off_cf_parent, p.cf_parent.data(), 4 * p.cf_parent.size());
+    if (!e) e = up(p.off_cf_child, p.cf_child.data(), 4 * p.cf_child.size());
+    for (int k = 0; k < 2; ++k)
+      if (!e) e = up(p.off_tiles_pure[k], p.tiles_pure[k].data(), 8 * p.tiles_pure[k].size());
+    for (int k = 0; k < 2; ++k)
+      if (!e) e = up(p.off_tiles_mixed[k], p.tiles_mixed[k].data(), 4 * p.tiles_mixed[k].size());
+    p.cur = 0;
+  }
+  for (auto& p : g->hg.P)
+    for (int k = 0; k < 2 && !e; ++k) {
+      e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmap[k], g->base + p.off_f[k], view(g, p), 0);
+      if (!e) e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmapo[k], g->base + p.off_f[k], view(g, p), 1);
+      if (!e) e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmapw[k], g->base + p.off_f[k], view(g, p), 2);
+    }
+  if (!e) e = cudaMemsetAsync(g->base + g->off_status, 0, 64, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return cuda_check(g, e, "lbm_grid_bind");
+  g->bound = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_grid_destroy(lbm_grid_t g) {
+  delete g;
+  return LBM_OK;
+}
+
+lbm_status lbm_num_patches(lbm_grid_t g, int32_t* n_patches, int32_t* n_levels) {
+  if (!g) return LBM_ERR_ARG;
+  if (n_patches) *n_patches = (int32_t)g->hg.P.size();
+  if (n_levels) *n_levels = g->hg.nlev;
+  return LBM_OK;
+}
+
+lbm_status lbm_patch_info(lbm_grid_t g, int32_t patch, int32_t* level, int32_t* parent, int64_t org[3],
+                          int64_t dim[3], double* beta, double* beta1) {
+  if (lbm_status s = check_patch(g, patch)) return s;
+  const HostPatch& p = g->hg.P[patch];
+  if (level) *level = p.level;
+  if (parent) *parent = p.parent;
+  for (int a = 0; a < 3; ++a) {
+    if (org) org[a] = p.org[a];
+    if (dim) dim[a] = p.dim[a];
+  }
+  if (beta) *beta = p.beta;
+  if (beta1) *beta1 = p.beta1;
+  return LBM_OK;
+}
+
+lbm_status lbm_patch_mask(lbm_grid_t g, int32_t patch, uint8_t* host_out) {
+  if (lbm_status s = check_patch(g, patch)) return s;
+  if (!host_out) return fail(g, LBM_ERR_ARG, "null output");
+  const HostPatch& p = g->hg.P[patch];
+  size_t d = 0;
+  for (int64_t z = 0; z < p.dim[2]; ++z)
+    for (int64_t y = 0; y < p.dim[1]; ++y)
+      for (int64_t x = 0; x < p.dim[0]; ++x) {
+        uint8_t t = p.type[(size_t)((z * p.dim[1] + y) * p.nxp + x)];
+        host_out[d++] = t == lbm::T_SKIP ? 0 : (t == lbm::T_SOLID ? 2 : 1);
+      }
+  return LBM_OK;
+}
+
+lbm_status lbm_node_updates(lbm_grid_t g, double* per_coarse_step) {
+  if (!g || !per_coarse_step) return LBM_ERR_ARG;
+  double s = 0;
+  for (auto& p : g->hg.P) s += (double)p.n_fluid * (double)(1LL << p.level);
+  *per_coarse_step = s;
+  return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_grid_t g, int32_t patch, const void* rho, const void* u, const void* T,
+                                int32_t dtype) {
+  if (lbm_status s = check_patch(g, patch)) return s;
+  if (lbm_status s = check_bound(g)) return s;
+  if (!rho || !u || (dtype != 0 && dtype != 1)) return fail(g, LBM_ERR_ARG, "bad rho/u/dtype");
+  (void)T;
+  HostPatch& p = g->hg.P[patch];
+  return cuda_check(g,
+                    lbmk::launch_init(g->hg.desc.storage, view(g, p), g->base + p.off_f[0], g->base + p.off_f[1],
+                                      rho, u, dtype, g->hg.desc.u_in, g->stream),
+                    "lbm_init_equilibrium");
+}
+
+lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps) {
+  if (lbm_status s = check_bound(g)) return s;
+  if (n_coarse_steps < 0) return fail(g, LBM_ERR_ARG, "negative step count");
+  const int K = 1 << (g->hg.nlev - 1);
+  for (int64_t n = 0; n < n_coarse_steps; ++n)
+    for (int k = 1; k <= K; ++k)
+      if (lbm_status s = run_instant(g, k)) return s;
+  return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_grid_t g, int32_t patch, void* rho, void* u, void* T, void* gamma, int32_t dtype) {
+  if (lbm_status s = check_patch(g, patch)) return s;
+  if (lbm_status s = check_bound(g)) return s;
+  if (dtype != 0 && dtype != 1) return fail(g, LBM_ERR_ARG, "bad dtype");
+  (void)T;
+  HostPatch& p = g->hg.P[patch];
+  return cuda_check(g,
+                    lbmk::launch_moments(g->hg.desc.storage, view(g, p), g->base + p.off_f[p.cur], rho, u, gamma,
+                                         dtype, p.beta, level_force(g, p.level), g->hg.desc.mirror_lbgk, g->stream),
+                    "lbm_moments");
+}
+
+static lbm_status copy_pop(lbm_grid_t g, int32_t patch, int32_t which, void* dense, int32_t dtype, int to_dense) {
+  if (lbm_status s = check_patch(g, patch)) return s;
+  if (lbm_status s = check_bound(g)) return s;
+  if (!dense || (dtype != 0 && dtype != 1)) return fail(g, LBM_ERR_ARG, "bad buffer/dtype");
+  if (which != 0 && !(which == 1 && g->hg.thermal)) return fail(g, LBM_ERR_ARG, "bad population set");
+  HostPatch& p = g->hg.P[patch];
+  const size_t* off = which ? p.off_g : p.off_f;
+  const lbmk::PatchDev pv = view(g, p);
+  cudaError_t e = lbmk::launch_copy_pop(g->hg.desc.storage, pv, g->base + off[p.cur], dense, dtype, to_dense,
+                                        g->stream);
+  if (!e && !to_dense)
+    e = lbmk::launch_copy_pop(g->hg.desc.storage, pv, g->base + off[1 - p.cur], dense, dtype, 0, g->stream);
+  return cuda_check(g, e, "population copy");
+}
+
+lbm_status lbm_get_populations(lbm_grid_t g, int32_t patch, int32_t which, void* dst, int32_t dtype) {
+  return copy_pop(g, patch, which, dst, dtype, 1);
+}
+
+lbm_status lbm_set_populations(lbm_grid_t g, int32_t patch, int32_t which, const void* src, int32_t dtype) {
+  return copy_pop(g, patch, which, const_cast<void*>(src), dtype, 0);
+}
+
+lbm_status lbm_diagnostics(lbm_grid_t g, double out[8]) {
+  if (lbm_status s = check_bound(g)) return s;
+  if (!out) return fail(g, LBM_ERR_ARG, "null output");
+  double* partial = at<double>(g, g->off_partial);
+  int nb = 0;
+  cudaError_t e = cudaSuccess;
+  for (auto& p : g->hg.P) {
+    if (!e)
+      e = lbmk::launch_diag(g->hg.desc.storage, view(g, p), g->base + p.off_f[p.cur],
+                            1.0 / (double)(1LL << (3 * p.level)), level_force(g, p.level), partial + 8 * nb,
+                            kDiagBlocks, g->stream);
+    nb += kDiagBlocks;
+  }
+  double* dout = at<double>(g, g->off_diag_out);
+  if (!e) e = lbmk::launch_diag_final(partial, nb, dout, g->stream);
+  double host[8];
+  int status = 0;
+  if (!e) e = cudaMemcpyAsync(host, dout, sizeof host, cudaMemcpyDeviceToHost, g->stream);
+  if (!e) e = cudaMemcpyAsync(&status, status_ptr(g), sizeof status, cudaMemcpyDeviceToHost, g->stream);
+  if (!e) e = cudaStreamSynchronize(g->stream);
+  if (e) return cuda_check(g, e, "lbm_diagnostics");
+  for (int k = 0; k < 6; ++k) out[k] = host[k];
+  out[6] = host[6];
+  out[7] = (double)status;
+  // k_diag slot 7 counts nodes with non-finite or non-positive density
+  if (host[7] > 0 || !(host[6] > 0)) {
+    out[6] = host[7] > 0 ? NAN : host[6];
+    return fail(g, LBM_ERR_UNSTABLE, "non-finite or non-positive density");
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_force(lbm_grid_t g, const double* accel0, double* drag_out) {
+  if (!g) return LBM_ERR_ARG;
+  if (accel0)
+    for (int a = 0; a < 3; ++a) g->accel[a] = accel0[a];
+  if (drag_out) return fail(g, LBM_ERR_STATE, "drag not available in this build");
+  return LBM_OK;
+}
+
+lbm_status lbm_checkpoint_bytes(lbm_grid_t g, size_t* bytes) {
+  if (!g || !bytes) return LBM_ERR_ARG;
+  size_t b = 0;
+  for (auto& p : g->hg.P) b += 27 * (size_t)p.plane * g->hg.pop_bytes * (g->hg.thermal ? 2 : 1);
+  *bytes = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_checkpoint(lbm_grid_t g, void* dev, int32_t save) {
+  if (lbm_status s = check_bound(g)) return s;
+  if (!dev) return fail(g, LBM_ERR_ARG, "null checkpoint buffer");
+  uint8_t* d = static_cast<uint8_t*>(dev);
+  cudaError_t e = cudaSuccess;
+  for (auto& p : g->hg.P) {
+    const size_t n = 27 * (size_t)p.plane * g->hg.pop_bytes;
+    for (int set = 0; set < (g->hg.thermal ? 2 : 1); ++set) {
+      const size_t* off = set ? p.off_g : p.off_f;
+      if (save) {
+        if (!e) e = cudaMemcpyAsync(d, g->base + off[p.cur], n, cudaMemcpyDeviceToDevice, g->stream);
+      } else {
+        if (!e) e = cudaMemcpyAsync(g->base + off[p.cur], d, n, cudaMemcpyDeviceToDevice, g->stream);
+        if (!e) e = cudaMemcpyAsync(g->base + off[1 - p.cur], d, n, cudaMemcpyDeviceToDevice, g->stream);
+      }
+      d += n;
+    }
+  }
+  return cuda_check(g, e, "lbm_checkpoint");
+}
+
+lbm_status lbm_collide_nodes(const void* f_in, void* f_out, void* gamma_out, int64_t n, double beta,
+                             const double du[3], int32_t lbgk, int32_t dtype, void* cuda_stream) {
+  if (!f_in || !f_out || n < 0 || (dtype != 0 && dtype != 1)) return LBM_ERR_ARG;
+  lbmk::Force F{};
+  if (du)
+    for (int a = 0; a < 3; ++a) F.du[a] = du[a];
+  cudaError_t e = lbmk::launch_collide_nodes(f_in, f_out, gamma_out, n, beta, F, lbgk, dtype,
+                                             static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+lbm_status lbm_timing(lbm_grid_t g, int32_t enable) {
+  if (!g) return LBM_ERR_ARG;
+  if (enable) {
+    g->recs.clear();
+    g->pool_used = 0;
+  }
+  g->timing = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_timing_report(lbm_grid_t g, int32_t max_rows, int32_t* n_rows, int32_t* kind, int32_t* level,
+                             int64_t* launches, double* ms, double* nodes) {
+  if (!g || !n_rows) return LBM_ERR_ARG;
+  if (cudaError_t e = cudaStreamSynchronize(g->stream)) return cuda_check(g, e, "lbm_timing_report");
+  struct Row {
+    int kind, level;
+    int64_t n;
+    double ms, nodes;
+  };
+  std::vector<Row> rows;
+  for (auto& r : g->recs) {
+    float t = 0;
+    if (cudaError_t e = cudaEventElapsedTime(&t, r.e0, r.e1)) return cuda_check(g, e, "cudaEventElapsedTime");
+    Row* row = nullptr;
+    for (auto& x : rows)
+      if (x.kind == r.kind && x.level == r.level) row = &x;
+    if (!row) {
+      rows.push_back(Row{r.kind, r.level, 0, 0.0, 0.0});
+      row = &rows.back();
+    }
+    row->n += 1;
+    row->ms += t;
+    row->nodes += r.nodes;
+  }
+  *n_rows = (int32_t)rows.size();
+  for (int32_t k = 0; k < (int32_t)rows.size() && k < max_rows; ++k) {
+    if (kind) kind[k] = rows[k].kind;
+    if (level) level[k] = rows[k].level;
+    if (launches) launches[k] = rows[k].n;
+    if (ms) ms[k] = rows[k].ms;
+    if (nodes) nodes[k] = rows[k].nodes;
+  }
+  return LBM_OK;
+}
+
+const char* lbm_last_error(lbm_grid_t g) { return g ? g->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

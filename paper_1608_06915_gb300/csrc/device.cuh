@@ -1,0 +1,452 @@
+// Device-side lattice, storage conversion, pull-streaming and the KBC collision.
+//
+// Velocity order: i = (cx+1) + 3(cy+1) + 9(cz+1), rest 13, opposite 26 - i.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmk {
+
+enum : uint8_t { T_SKIP = 0, T_BULK = 1, T_BC = 2, T_D1 = 3, T_D0 = 4, T_CF = 5, T_INLET = 6, T_SOLID = 7 };
+
+__host__ __device__ constexpr int CX(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int CY(int i) { return (i / 3) % 3 - 1; }
+__host__ __device__ constexpr int CZ(int i) { return i / 9 - 1; }
+__host__ __device__ constexpr double W1(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+__host__ __device__ constexpr double WI(int i) { return W1(CX(i)) * W1(CY(i)) * W1(CZ(i)); }
+
+// ---------------------------------------------------------------------------
+// Storage: every type holds the deviation f_i - W_i from the rest state at
+// unit density (16-bit types need it for their few mantissa bits; float and
+// double keep 100x more absolute resolution that way).  The compute type R is
+// double for double storage and float otherwise.
+template <typename S>
+struct Stor;
+template <>
+struct Stor<double> {
+  static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+  static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+};
+template <>
+struct Stor<float> {
+  static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+  static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <>
+struct Stor<__half> {
+  static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Stor<__nv_bfloat16> {
+  static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+__device__ __forceinline__ double wi_rt(int i) {
+  // W_i for a runtime direction index
+  const int c[3] = {i % 3, (i / 3) % 3, i / 9};
+  double w = 1.0;
+  for (int a = 0; a < 3; ++a) w *= c[a] == 1 ? 2.0 / 3.0 : 1.0 / 6.0;
+  return w;
+}
+
+// compile-time loop
+template <int N, typename F, int I = 0>
+__device__ __forceinline__ void unroll(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    unroll<N, F, I + 1>(static_cast<F&&>(f));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Patch view passed by value to kernels.
+struct PatchDev {
+  int dim[3];
+  int org[3];
+  int maxc[3];       // last domain coordinate on non-periodic axes (this level)
+  int nxp;
+  long long plane;   // nodes per population plane
+  unsigned char span[3];
+  unsigned char periodic[3];
+  unsigned walls;
+  int inflow;
+  const uint8_t* type;
+};
+
+__device__ __forceinline__ long long node_index(const PatchDev& p, int x, int y, int z) {
+  return ((long long)z * p.dim[1] + y) * p.nxp + x;
+}
+
+// ---------------------------------------------------------------------------
+// Product-form equilibrium, Eq. (feq_iso), per axis and in deviation form:
+//   f_i^eq = rho W_i prod_a ghat_a(c_ia),  ghat(0) = A,  ghat(+1) = A B,
+//   ghat(-1) = A / B,  A = 2 - s,  B = (2u + s)/(1 - u),  s = sqrt(1 + 3u^2).
+// With e = s - 1 = 3u^2/(s + 1), the deviations d = ghat - 1 are
+//   d(0)  = -e,
+//   d(+1) = (u (3 - 3u - 2e) + 2e) / (1 - u),
+//   d(-1) = (u (e - 3) - 2e) / (2u + s),
+// free of cancellation, so f^eq - W_i = W_i (rho~ + rho q_i) with
+// q_i = prod_a (1 + d_a) - 1 and rho~ = rho - 1 keeps full relative accuracy.
+// Division and square root: IEEE in double; in float the hardware reciprocal
+// and reciprocal square root (about 2 ulp), ample for the well-conditioned
+// quotients of the collision (denominators near 1).
+template <typename R>
+__device__ __forceinline__ R rcp_fast(R x) {
+  return R(1) / x;
+}
+template <>
+__device__ __forceinline__ float rcp_fast<float>(float x) {
+  return __fdividef(1.0f, x);
+}
+template <typename R>
+__device__ __forceinline__ R fdiv(R a, R b) {
+  return a / b;
+}
+template <>
+__device__ __forceinline__ float fdiv<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+template <typename R>
+__device__ __forceinline__ R fsqrt1(R x) {  // x >= 1
+  return sqrt(x);
+}
+template <>
+__device__ __forceinline__ float fsqrt1<float>(float x) {
+  return x * rsqrtf(x);
+}
+
+template <typename R>
+struct AxisEq {
+  R d[3];   // ghat - 1 for c = -1, 0, +1
+  R ig[3];  // 1 / (W1(c) ghat(c)), weights of the entropic scalar product
+  R s, B;   // s = sqrt(1 + 3u^2), B as above (for the force increment)
+};
+
+template <typename R>
+__device__ __forceinline__ void axis_eq(R u, AxisEq<R>& a, bool want_inverse) {
+  const R s = fsqrt1(R(1) + R(3) * u * u);
+  const R e = fdiv(R(3) * u * u, s + R(1));
+  const R i1mu = rcp_fast(R(1) - u);
+  a.s = s;
+  a.B = (R(2) * u + s) * i1mu;
+  a.d[1] = -e;
+  a.d[2] = (u * (R(3) - R(3) * u - R(2) * e) + R(2) * e) * i1mu;
+  a.d[0] = fdiv(u * (e - R(3)) - R(2) * e, R(2) * u + s);
+  if (want_inverse) {
+    a.ig[1] = rcp_fast(R(2.0 / 3.0) * (R(1) + a.d[1]));
+    a.ig[2] = rcp_fast(R(1.0 / 6.0) * (R(1) + a.d[2]));
+    a.ig[0] = rcp_fast(R(1.0 / 6.0) * (R(1) + a.d[0]));
+  }
+}
+
+// Increment of the per-axis factors ghat when u -> u + du, evaluated without
+// cancellation: ds = 3 du (2u + du)/(s' + s), dA = -ds,
+// dB = ((2 du + ds)(1 - u) + (2u + s) du) / ((1 - u - du)(1 - u)),
+// d[A B] = dA B' + A dB,  d[A/B] = (dA B - A dB) / (B B').
+template <typename R>
+__device__ __forceinline__ void axis_eq_increment(R u, R du, const AxisEq<R>& a, R (&g1)[3], R (&dg)[3]) {
+  if (du == R(0)) {  // no force along this axis
+    for (int c = 0; c < 3; ++c) {
+      dg[c] = R(0);
+      g1[c] = R(1) + a.d[c];
+    }
+    return;
+  }
+  const R u1 = u + du;
+  const R s1 = fsqrt1(R(1) + R(3) * u1 * u1);
+  const R ds = fdiv(R(3) * du * (R(2) * u + du), s1 + a.s);
+  const R dA = -ds;
+  const R dB = fdiv((R(2) * du + ds) * (R(1) - u) + (R(2) * u + a.s) * du, (R(1) - u1) * (R(1) - u));
+  const R A = R(1) + a.d[1];
+  const R B1 = a.B + dB;
+  dg[1] = dA;
+  dg[2] = dA * B1 + A * dB;
+  dg[0] = fdiv(dA * a.B - A * dB, a.B * B1);
+  for (int c = 0; c < 3; ++c) g1[c] = R(1) + a.d[c] + dg[c];
+}
+
+// Mass deviation rho~ = sum f~, density and velocity from deviation populations.
+// Sums run as three independent partial sums (one per z-layer of the lattice)
+// to keep the dependency chains short.
+template <typename R>
+__device__ __forceinline__ void macro(const R (&f)[27], R& rho_t, R& rho, R& ux, R& uy, R& uz) {
+  R r[3] = {0, 0, 0}, jx[3] = {0, 0, 0}, jy[3] = {0, 0, 0}, jz = 0;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int l = CZ(i) + 1;
+    r[l] += f[i];
+    if constexpr (CX(i) == 1) jx[l] += f[i];
+    if constexpr (CX(i) == -1) jx[l] -= f[i];
+    if constexpr (CY(i) == 1) jy[l] += f[i];
+    if constexpr (CY(i) == -1) jy[l] -= f[i];
+  });
+  jz = r[2] - r[0];
+  rho_t = (r[0] + r[2]) + r[1];
+  rho = R(1) + rho_t;
+  const R ir = rcp_fast(rho);
+  ux = ((jx[0] + jx[2]) + jx[1]) * ir;
+  uy = ((jy[0] + jy[2]) + jy[1]) * ir;
+  uz = jz * ir;
+}
+
+// q_i = prod_a (1 + d_a(c_ia)) - 1 for all i, from the three axes.
+template <int i, typename R>
+__device__ __forceinline__ R qprod(const AxisEq<R>& ex, const AxisEq<R>& ey, const AxisEq<R>& ez) {
+  const R dx = ex.d[CX(i) + 1], dy = ey.d[CY(i) + 1], dz = ez.d[CZ(i) + 1];
+  const R t = dx + dy + dx * dy;
+  return t + dz + t * dz;
+}
+
+// Deviation equilibrium fe~_i = f_i^eq - W_i.
+template <typename R>
+__device__ __forceinline__ void feq_dev(R rho_t, R rho, R ux, R uy, R uz, R (&fe)[27]) {
+  AxisEq<R> ex, ey, ez;
+  axis_eq<R>(ux, ex, false);
+  axis_eq<R>(uy, ey, false);
+  axis_eq<R>(uz, ez, false);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    fe[i] = R(WI(i)) * (rho_t + rho * qprod<i>(ex, ey, ez));
+  });
+}
+
+// Shear part ds_i of a non-equilibrium vector from its second moments
+// (reading: natural-moment basis; face directions carry half the deviatoric
+// normal stress, edge directions a quarter of the off-diagonal stress with
+// sign cx*cy, rest and corners none).
+template <int i, typename R>
+__device__ __forceinline__ R shear_part(R nxx, R nyy, R nzz, R pxy, R pxz, R pyz) {
+  constexpr int ax = CX(i) != 0, ay = CY(i) != 0, az = CZ(i) != 0;
+  if constexpr (ax + ay + az == 1) {
+    if constexpr (ax) return R(0.5) * nxx;
+    else if constexpr (ay) return R(0.5) * nyy;
+    else return R(0.5) * nzz;
+  } else if constexpr (ax + ay + az == 2) {
+    if constexpr (!az) return R(0.25 * CX(i) * CY(i)) * pxy;
+    else if constexpr (!ay) return R(0.25 * CX(i) * CZ(i)) * pxz;
+    else return R(0.25 * CY(i) * CZ(i)) * pyz;
+  } else {
+    return R(0);
+  }
+}
+
+// KBC collision (Eqs. f_equations, f_mirr, gamma_min_approx) in the delta form
+//   f'_i = f_i - beta (2 ds_i + gamma dh_i),  dh = (f - f^eq) - ds,
+// followed by the exact-difference-method force f'_i += f^eq(rho,u+du) - f^eq(rho,u).
+// f holds deviation populations f - W and is replaced by the post-collision
+// deviations; returns gamma.  FM is a compile-time mask of the axes along
+// which du may be nonzero (bit a: axis a; 0: no force).
+//
+// Arithmetic layout: everything per direction is a product of per-axis
+// factors, so the loops read small pair tables -- q_i from (1 + q_xy)(1 + d_z),
+// the entropic weights 1/f_i^eq from (1/g_x g_y)(1/(rho g_z)), the force from
+// g_y g_z -- instead of recomputing the products for each of the 27 directions.
+template <typename R, int FM>
+__device__ __forceinline__ R kbc_collide(R (&f)[27], R beta, R dux, R duy, R duz, bool lbgk) {
+  R rho_t, rho, ux, uy, uz;
+  macro(f, rho_t, rho, ux, uy, uz);
+  AxisEq<R> ex, ey, ez;
+  axis_eq<R>(ux, ex, !lbgk);
+  axis_eq<R>(uy, ey, !lbgk);
+  axis_eq<R>(uz, ez, !lbgk);
+  R fe[27];
+  R sxx[3] = {0, 0, 0}, syy[3] = {0, 0, 0}, sxy[3] = {0, 0, 0}, szz[2] = {0, 0}, sxz[2] = {0, 0},
+    syz[2] = {0, 0};
+  {
+    R qxy[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) qxy[a][b] = ex.d[a] * ey.d[b] + (ex.d[a] + ey.d[b]);
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const R t = qxy[CX(i) + 1][CY(i) + 1], dz = ez.d[CZ(i) + 1];
+      const R q = t * dz + (t + dz);
+      fe[i] = R(WI(i)) * (rho * q + rho_t);
+      const R df = f[i] - fe[i];
+      f[i] = df;
+      constexpr int l = CZ(i) + 1;            // z-layer partial sums
+      constexpr int lz = CZ(i) > 0 ? 1 : 0;  // the two c_z != 0 layers
+      if constexpr (CX(i) != 0) sxx[l] += df;
+      if constexpr (CY(i) != 0) syy[l] += df;
+      if constexpr (CZ(i) != 0) szz[lz] += df;
+      if constexpr (CX(i) * CY(i) == 1) sxy[l] += df;
+      if constexpr (CX(i) * CY(i) == -1) sxy[l] -= df;
+      if constexpr (CX(i) * CZ(i) == 1) sxz[lz] += df;
+      if constexpr (CX(i) * CZ(i) == -1) sxz[lz] -= df;
+      if constexpr (CY(i) * CZ(i) == 1) syz[lz] += df;
+      if constexpr (CY(i) * CZ(i) == -1) syz[lz] -= df;
+    });
+  }
+  const R pxx = (sxx[0] + sxx[2]) + sxx[1], pyy = (syy[0] + syy[2]) + syy[1], pzz = szz[0] + szz[1];
+  const R pxy = (sxy[0] + sxy[2]) + sxy[1], pxz = sxz[0] + sxz[1], pyz = syz[0] + syz[1];
+  const R tr3 = (pxx + pyy + pzz) * R(1.0 / 3.0);
+  const R nxx = pxx - tr3, nyy = pyy - tr3, nzz = pzz - tr3;
+  R gamma = R(2);
+  if (!lbgk) {
+    const R irho = rcp_fast(rho);
+    R wxy[3][3], wz[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      wz[a] = irho * ez.ig[a];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) wxy[a][b] = ex.ig[a] * ey.ig[b];
+    }
+    R shl[3] = {0, 0, 0}, hhl[3] = {0, 0, 0};
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int l = CZ(i) + 1;
+      const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
+      const R dh = f[i] - ds;
+      const R dhw = dh * (wxy[CX(i) + 1][CY(i) + 1] * wz[CZ(i) + 1]);
+      shl[l] += ds * dhw;
+      hhl[l] += dh * dhw;
+    });
+    const R sh = (shl[0] + shl[2]) + shl[1], hh = (hhl[0] + hhl[2]) + hhl[1];
+    if (hh > R(1e-30) * rho * rho) {
+      const R ib = R(1) / beta;
+      gamma = ib - (R(2) - ib) * fdiv(sh, hh);
+    }
+  }
+  // f' = f^eq + (1 - beta gamma) df + beta (gamma - 2) ds  [+ force increment]
+#if defined(LBM_RECOMPUTE_FEQ)
+  {
+    R qxy[3][3];
+#pragma unroll
+    for (int a2 = 0; a2 < 3; ++a2)
+#pragma unroll
+      for (int b2 = 0; b2 < 3; ++b2) qxy[a2][b2] = ex.d[a2] * ey.d[b2] + (ex.d[a2] + ey.d[b2]);
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const R t = qxy[CX(i) + 1][CY(i) + 1], dz = ez.d[CZ(i) + 1];
+      fe[i] = R(WI(i)) * (rho * (t * dz + (t + dz)) + rho_t);
+    });
+  }
+#endif
+  const R a = R(1) - beta * gamma;
+  const R b = beta * (gamma - R(2));
+  if constexpr (FM == 0) {
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      f[i] = a * f[i] + fe[i] + b * shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
+    });
+  } else if constexpr (FM == 1 || FM == 2 || FM == 4) {
+    // force along one axis: f^eq(rho,u+du) - f^eq(rho,u) = rho W_i dg_a(c_ia) prod_{b != a} g_b(c_ib)
+    constexpr int A = FM == 1 ? 0 : (FM == 2 ? 1 : 2);
+    const AxisEq<R>& ea = A == 0 ? ex : (A == 1 ? ey : ez);
+    const AxisEq<R>& e1 = A == 0 ? ey : ex;
+    const AxisEq<R>& e2 = A == 2 ? ey : ez;
+    const R ua = A == 0 ? ux : (A == 1 ? uy : uz);
+    const R dua = A == 0 ? dux : (A == 1 ? duy : duz);
+    R g1[3], dg[3], rdg[3], goth[3][3];
+    axis_eq_increment<R>(ua, dua, ea, g1, dg);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      rdg[c] = rho * dg[c];
+#pragma unroll
+      for (int c2 = 0; c2 < 3; ++c2) goth[c][c2] = (R(1) + e1.d[c]) * (R(1) + e2.d[c2]);
+    }
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int ca = A == 0 ? CX(i) : (A == 1 ? CY(i) : CZ(i));
+      constexpr int c1 = A == 0 ? CY(i) : CX(i);
+      constexpr int c2 = A == 2 ? CY(i) : CZ(i);
+      const R inc = rdg[ca + 1] * (R(WI(i)) * goth[c1 + 1][c2 + 1]);
+      f[i] = a * f[i] + fe[i] + b * shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz) + inc;
+    });
+  } else {
+    // general direction: dgx gy gz + gx' dgy gz + gx' gy' dgz (telescoped)
+    R gx1[3], gy1[3], gz1[3], dgx[3], dgy[3], dgz[3];
+    axis_eq_increment<R>(ux, dux, ex, gx1, dgx);
+    axis_eq_increment<R>(uy, duy, ey, gy1, dgy);
+    axis_eq_increment<R>(uz, duz, ez, gz1, dgz);
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int x = CX(i) + 1, y = CY(i) + 1, z = CZ(i) + 1;
+      const R gy = R(1) + ey.d[y], gz = R(1) + ez.d[z];
+      const R inc = dgx[x] * gy * gz + gx1[x] * (dgy[y] * gz + gy1[y] * dgz[z]);
+      f[i] = a * f[i] + fe[i] + b * shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz) + R(WI(i)) * rho * inc;
+    });
+  }
+  return gamma;
+}
+
+// ---------------------------------------------------------------------------
+// Pull-streaming: f_i(x) = f'_i(x - c_i) from the previous state.
+// Fast path for T_BULK nodes: every source is a stored fluid node, periodic
+// wrap only on spanned axes.
+template <typename S, typename R>
+__device__ __forceinline__ void pull_bulk(const PatchDev& p, const S* __restrict__ fin, int x, int y, int z,
+                                          R (&f)[27]) {
+  const int xm = x == 0 ? p.dim[0] - 1 : x - 1, xp = x == p.dim[0] - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? p.dim[1] - 1 : y - 1, yp = y == p.dim[1] - 1 ? 0 : y + 1;
+  const int zm = z == 0 ? p.dim[2] - 1 : z - 1, zp = z == p.dim[2] - 1 ? 0 : z + 1;
+  const long long row = p.nxp, sl = (long long)p.nxp * p.dim[1];
+  const long long xs[3] = {xp, x, xm};  // source x for cx = -1, 0, +1
+  const long long ys[3] = {yp * row, y * row, ym * row};
+  const long long zs[3] = {zp * sl, z * sl, zm * sl};
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    f[i] = Stor<S>::ld(fin + (long long)i * p.plane + zs[CZ(i) + 1] + ys[CY(i) + 1] + xs[CX(i) + 1]);
+  });
+}
+
+// Generic path: walls (half-way bounce-back), solid nodes (bounce-back),
+// outlet (source clamped to the last node), periodic wrap on spanned axes.
+// A source that resolves to no node sets bit 0 of *status and falls back to
+// bounce-back (never produced by a validated layout).
+template <typename S, typename R>
+__device__ __forceinline__ void pull_generic(const PatchDev& p, const S* __restrict__ fin, int x, int y, int z,
+                                             R (&f)[27], int* status) {
+  const long long own = node_index(p, x, y, z);
+  const int X[3] = {x, y, z};
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int c[3] = {CX(i), CY(i), CZ(i)};
+    int s[3];
+    bool bounce = false, bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      s[a] = X[a] - c[a];
+      if (s[a] < 0 || s[a] >= p.dim[a]) {
+        if (p.span[a]) {
+          s[a] += s[a] < 0 ? p.dim[a] : -p.dim[a];
+        } else if (!p.periodic[a]) {
+          const int G = p.org[a] + s[a];
+          if (G < 0) {
+            if (p.walls & (1u << (2 * a))) bounce = true;
+            else bad = true;
+          } else if (G > p.maxc[a]) {
+            if (p.walls & (1u << (2 * a + 1))) bounce = true;
+            else if (p.inflow == a) s[a] = p.maxc[a] - p.org[a];
+            else bad = true;
+          } else {
+            bad = true;
+          }
+        } else {
+          bad = true;
+        }
+      }
+    }
+    long long src = own;
+    if (!bounce && !bad) {
+      src = node_index(p, s[0], s[1], s[2]);
+      const uint8_t t = p.type[src];
+      if (t == T_SOLID) bounce = true;
+      else if (t == T_SKIP) bad = true;
+    }
+    if (bad) {
+      atomicOr(status, 1);
+      bounce = true;
+    }
+    if (bounce) f[i] = Stor<S>::ld(fin + (long long)(26 - i) * p.plane + own);
+    else f[i] = Stor<S>::ld(fin + (long long)i * p.plane + src);
+  });
+}
+
+}  // namespace lbmk

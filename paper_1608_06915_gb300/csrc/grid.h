@@ -1,0 +1,99 @@
+// Host-side grid description: patches, node classes and interface tables.
+//
+// A patch is one refinement box of one level (level 0 is the whole domain).
+// Its nodes are stored densely over a storage box (the bounding box of the
+// nodes it owns), x padded to a multiple of 32, populations as 27 planes.
+//
+// Node classes (one byte per stored node) decide which kernel writes a node:
+//   T_BULK  fluid, all 27 pull sources are plain stored nodes (fast path)
+//   T_BC    fluid, some source lies beyond a wall / in a solid (bounce-back)
+//           or beyond the outlet (clamped): generic pull
+//   T_D1    child interface node at depth 1 (Sec. III, reconstruction or twin
+//           layer): written by the explode kernel when the parent advances in
+//           the same instant, by the generic stream-collide otherwise
+//   T_D0    child interface node at depth 0: written by explode only
+//   T_CF    parent twin node x_t,cf: written by the coalesce kernel
+//   T_INLET fixed equilibrium inlet node, never written after init
+//   T_SOLID solid node; T_SKIP no node (hole of a child, padding)
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+enum NodeType : uint8_t { T_SKIP = 0, T_BULK = 1, T_BC = 2, T_D1 = 3, T_D0 = 4, T_CF = 5, T_INLET = 6, T_SOLID = 7 };
+
+// Reconstruction sample sources: a parent node (non-equilibrium rescaled to the
+// child scale) or a child node (inside the parent hole, or under a parent twin).
+enum SampleKind : uint8_t { S_PARENT = 0, S_CHILD = 1 };
+
+struct HostPatch {
+  int level = 0, parent = -1;
+  std::vector<int> kids;
+  int64_t blo[3]{}, bhi[3]{};  // box in parent coordinates (level >= 1)
+  bool span[3]{};              // spans a periodic axis completely
+  bool flo[3]{}, fhi[3]{};     // box faces that are interfaces toward the parent
+  int64_t rlo[3]{}, rhi[3]{};  // region in this level's coordinates (inclusive)
+  int64_t org[3]{}, dim[3]{};  // storage box
+  int64_t nxp = 0, plane = 0;  // padded row length, nodes per population plane
+  double beta = 0, beta1 = 0;
+  std::vector<uint8_t> type;  // [z][y][nxp]
+  int64_t n_fluid = 0;
+  double n_bulk = 0, n_d1 = 0;  // BULK+BC nodes and D1 nodes (written by stream_collide)
+
+  // stream-collide work lists: tiles of 128 nodes along x, id = (z*ny + y)*ntx + tx
+  int64_t ntx = 0;
+  // TMA path ([0] even steps: every node a plain bulk node; [1] odd steps: every
+  // node a plain bulk node or a depth-1 node with plain sources): x-tile | y<<16 | z<<32
+  std::vector<uint64_t> tiles_pure[2];
+  std::vector<uint32_t> tiles_mixed[2];  // other tiles with nodes to update: [0] even, [1] odd steps
+  alignas(64) unsigned char tmap[2][128];   // TMA load descriptors of the two population buffers
+  alignas(64) unsigned char tmapo[2][128];  // TMA store descriptors
+  alignas(64) unsigned char tmapw[2][128];  // TMA 16-byte wrap descriptors
+
+  // interface toward the parent (level >= 1)
+  std::vector<uint32_t> ex_node;    // explode targets (nodes of this patch)
+  std::vector<uint32_t> ex_first;   // sample list offsets, size ex_node.size() + 1
+  std::vector<uint8_t> ex_mask;     // bit a: off-lattice along axis a
+  std::vector<uint32_t> ex_sample;  // sample ids
+  std::vector<uint32_t> smp_node;   // per sample: node index in parent or child
+  std::vector<uint8_t> smp_kind;    // per sample: S_PARENT / S_CHILD
+  std::vector<uint32_t> cf_parent;  // coalesce: parent twin node
+  std::vector<uint32_t> cf_child;   // coalesce: coinciding child node
+
+  // device placement (byte offsets into the bound buffer)
+  size_t off_f[2]{}, off_g[2]{}, off_type = 0;
+  size_t off_tiles_pure[2]{}, off_tiles_mixed[2]{};
+  size_t off_ex_node = 0, off_ex_first = 0, off_ex_mask = 0, off_ex_sample = 0;
+  size_t off_smp_node = 0, off_smp_kind = 0, off_smp_val = 0, off_cf_parent = 0, off_cf_child = 0;
+  int cur = 0;  // which population buffer holds the current state
+};
+
+struct HostGrid {
+  lbm_desc desc{};
+  std::vector<lbm_box> boxes;
+  std::vector<uint8_t> solid;
+  std::vector<HostPatch> P;
+  int nlev = 1;
+  bool thermal = false;
+  size_t pop_bytes = 4;   // bytes per stored population value
+  size_t real_bytes = 4;  // bytes of the compute type (samples, outputs)
+
+  bool periodic(int a) const { return (desc.periodic >> a) & 1u; }
+  bool wall(int a, int side) const { return (desc.walls >> (2 * a + side)) & 1u; }
+  int64_t period(int lev, int a) const { return (int64_t)desc.n[a] << lev; }
+  int64_t maxc(int lev, int a) const { return (int64_t)(desc.n[a] - 1) << lev; }
+};
+
+// Builds patches, node classes and interface tables; validates the layout.
+// Returns an empty string on success, else the reason.
+std::string build_layout(HostGrid& g);
+
+// Assigns byte offsets of every device array; returns the total size.
+size_t plan_memory(HostGrid& g);
+
+}  // namespace lbm

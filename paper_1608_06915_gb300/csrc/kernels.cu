@@ -1,0 +1,482 @@
+// CUDA kernels of the refined KBC step (isothermal model).
+//
+// One instant of the refined step runs, per active patch:
+//   k_stream_collide  pull-stream + KBC collide + force of every node whose
+//                     pull sources are valid (Eq. f_equations; Sec. III.C step 1
+//                     and the stream+collide of steps 2 and 5 fused),
+//   k_coalesce        parent twins x_t,cf <- child state rescaled fine->coarse
+//                     (Eq. f_neq_rescaling_iso inverted), then collide,
+//   k_samples         reconstruction samples: pre-collision rho, u and the
+//                     child-scale non-equilibrium part at parent positions,
+//   k_explode         child twins x_t,fc and reconstruction nodes x_r
+//                     (Eq. interp, tensor four-point Lagrange), then collide.
+// Kernels of one instant read only the previous states and write disjoint
+// nodes of the next-state buffers, so they need no ordering among themselves
+// except samples before explode.
+#include <type_traits>
+
+#include "../../include/lbm.h"
+#include "device.cuh"
+#include "kernels.h"
+
+namespace lbmk {
+
+template <typename T>
+struct tag {
+  using type = T;
+};
+
+template <typename F>
+cudaError_t dispatch(int storage, F&& f) {
+  switch (storage) {
+    case LBM_FP64:
+      return f(tag<double>{}, tag<double>{});
+    case LBM_FP32:
+      return f(tag<float>{}, tag<float>{});
+    case LBM_FP16_SHIFT:
+      return f(tag<__half>{}, tag<float>{});
+    case LBM_BF16_SHIFT:
+      return f(tag<__nv_bfloat16>{}, tag<float>{});
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ void store_node(const PatchDev& p, S* __restrict__ fout, long long own, const R (&f)[27]) {
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    Stor<S>::st(fout + (long long)i * p.plane + own, f[i]);
+  });
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ void pull_any(const PatchDev& p, const S* __restrict__ fin, long long node, R (&f)[27],
+                                         int* status) {
+  const int x = (int)(node % p.nxp);
+  const int y = (int)((node / p.nxp) % p.dim[1]);
+  const int z = (int)(node / ((long long)p.nxp * p.dim[1]));
+  if (p.type[node] == T_BULK) pull_bulk<S, R>(p, fin, x, y, z, f);
+  else pull_generic<S, R>(p, fin, x, y, z, f, status);
+}
+
+// ---------------------------------------------------------------------------
+// Fine -> coarse twin coupling: pre-collision child state at the coinciding
+// node, non-equilibrium scaled by r beta_f / beta_c, collided with beta_c.
+template <typename S, typename R, bool FORCE>
+__global__ void __launch_bounds__(128) k_coalesce(PatchDev pc, const S* __restrict__ fin_c, PatchDev pp,
+                                                  S* __restrict__ fout_p, const uint32_t* __restrict__ cf_parent,
+                                                  const uint32_t* __restrict__ cf_child, long long n, R rescale,
+                                                  R beta_p, R dux, R duy, R duz, int lbgk, int* status) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  R f[27];
+  pull_any<S, R>(pc, fin_c, cf_child[k], f, status);
+  R rho_t, rho, ux, uy, uz, fe[27];
+  macro(f, rho_t, rho, ux, uy, uz);
+  feq_dev(rho_t, rho, ux, uy, uz, fe);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    f[i] = fe[i] + rescale * (f[i] - fe[i]);
+  });
+  kbc_collide<R, FORCE ? 7 : 0>(f, beta_p, dux, duy, duz, lbgk != 0);
+  store_node<S, R>(pp, fout_p, cf_parent[k], f);
+}
+
+cudaError_t launch_coalesce(int storage, const PatchDev& child, const void* fin_child, const PatchDev& parent,
+                            void* fout_parent, const uint32_t* cf_parent, const uint32_t* cf_child, int64_t n,
+                            double rescale, double beta_parent, const Force& Fp, int lbgk, int* status,
+                            cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  return dispatch(storage, [&](auto ts, auto tr) {
+    using S = typename decltype(ts)::type;
+    using R = typename decltype(tr)::type;
+    dim3 block(128), grid((unsigned)((n + 127) / 128));
+    if (Fp.on())
+      k_coalesce<S, R, true><<<grid, block, 0, st>>>(child, (const S*)fin_child, parent, (S*)fout_parent, cf_parent,
+                                                      cf_child, n, (R)rescale, (R)beta_parent, (R)Fp.du[0],
+                                                      (R)Fp.du[1], (R)Fp.du[2], lbgk, status);
+    else
+      k_coalesce<S, R, false><<<grid, block, 0, st>>>(child, (const S*)fin_child, parent, (S*)fout_parent,
+                                                       cf_parent, cf_child, n, (R)rescale, (R)beta_parent, R(0),
+                                                       R(0), R(0), lbgk, status);
+    return cudaGetLastError();
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction samples: [31][ns] = rho - 1, ux, uy, uz, neq_0..26 (child scale).
+template <typename S, typename R>
+__global__ void __launch_bounds__(128) k_samples(PatchDev pp, const S* __restrict__ fin_p, PatchDev pc,
+                                                 const S* __restrict__ fin_c, const uint32_t* __restrict__ smp_node,
+                                                 const uint8_t* __restrict__ smp_kind, long long ns,
+                                                 R* __restrict__ out, R rescale_p, int* status) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  R f[27];
+  R factor;
+  if (smp_kind[s] == 0) {
+    pull_any<S, R>(pp, fin_p, smp_node[s], f, status);
+    factor = rescale_p;
+  } else {
+    pull_any<S, R>(pc, fin_c, smp_node[s], f, status);
+    factor = R(1);
+  }
+  R rho_t, rho, ux, uy, uz, fe[27];
+  macro(f, rho_t, rho, ux, uy, uz);
+  feq_dev(rho_t, rho, ux, uy, uz, fe);
+  out[s] = rho_t;
+  out[ns + s] = ux;
+  out[2 * ns + s] = uy;
+  out[3 * ns + s] = uz;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    out[(4 + i) * ns + s] = factor * (f[i] - fe[i]);
+  });
+}
+
+cudaError_t launch_samples(int storage, const PatchDev& parent, const void* fin_parent, const PatchDev& child,
+                           const void* fin_child, const uint32_t* smp_node, const uint8_t* smp_kind, int64_t ns,
+                           void* smp_val, double rescale_parent, int* status, cudaStream_t st) {
+  if (ns == 0) return cudaSuccess;
+  return dispatch(storage, [&](auto ts, auto tr) {
+    using S = typename decltype(ts)::type;
+    using R = typename decltype(tr)::type;
+    dim3 block(128), grid((unsigned)((ns + 127) / 128));
+    k_samples<S, R><<<grid, block, 0, st>>>(parent, (const S*)fin_parent, child, (const S*)fin_child, smp_node,
+                                            smp_kind, ns, (R*)smp_val, (R)rescale_parent, status);
+    return cudaGetLastError();
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Child twins and reconstruction nodes: tensor four-point Lagrange (Eq. interp,
+// weights (-1, 9, 9, -1)/16) of rho, u and the non-equilibrium part over the
+// off-lattice axes; f = f^eq(rho~, u~) + neq~; then collide.
+template <typename S, typename R, bool FORCE>
+__global__ void __launch_bounds__(128) k_explode(PatchDev pc, S* __restrict__ fout_c,
+                                                 const uint32_t* __restrict__ ex_node,
+                                                 const uint32_t* __restrict__ ex_first,
+                                                 const uint8_t* __restrict__ ex_mask,
+                                                 const uint32_t* __restrict__ ex_sample, long long n,
+                                                 const R* __restrict__ smp, long long ns, R beta_c, R dux, R duy,
+                                                 R duz, int lbgk) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const R w4[4] = {R(-1.0 / 16.0), R(9.0 / 16.0), R(9.0 / 16.0), R(-1.0 / 16.0)};
+  const uint8_t mask = ex_mask[k];
+  const int cx = (mask & 1) ? 4 : 1, cy = (mask & 2) ? 4 : 1, cz = (mask & 4) ? 4 : 1;
+  uint32_t j = ex_first[k];
+  R rho_t = 0, ux = 0, uy = 0, uz = 0;
+  R f[27];
+  unroll<27>([&](auto I) { f[decltype(I)::value] = R(0); });
+  for (int kz = 0; kz < cz; ++kz) {
+    const R wz = cz == 4 ? w4[kz] : R(1);
+    for (int ky = 0; ky < cy; ++ky) {
+      const R wyz = wz * (cy == 4 ? w4[ky] : R(1));
+      for (int kx = 0; kx < cx; ++kx) {
+        const R w = wyz * (cx == 4 ? w4[kx] : R(1));
+        const long long s = ex_sample[j++];
+        rho_t += w * __ldg(smp + s);
+        ux += w * __ldg(smp + ns + s);
+        uy += w * __ldg(smp + 2 * ns + s);
+        uz += w * __ldg(smp + 3 * ns + s);
+        unroll<27>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          f[i] += w * __ldg(smp + (4 + i) * ns + s);
+        });
+      }
+    }
+  }
+  R fe[27];
+  feq_dev(rho_t, R(1) + rho_t, ux, uy, uz, fe);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    f[i] += fe[i];
+  });
+  kbc_collide<R, FORCE ? 7 : 0>(f, beta_c, dux, duy, duz, lbgk != 0);
+  store_node<S, R>(pc, fout_c, ex_node[k], f);
+}
+
+cudaError_t launch_explode(int storage, const PatchDev& child, void* fout_child, const uint32_t* ex_node,
+                           const uint32_t* ex_first, const uint8_t* ex_mask, const uint32_t* ex_sample, int64_t n,
+                           const void* smp_val, int64_t ns, double beta_child, const Force& Fc, int lbgk,
+                           cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  return dispatch(storage, [&](auto ts, auto tr) {
+    using S = typename decltype(ts)::type;
+    using R = typename decltype(tr)::type;
+    dim3 block(128), grid((unsigned)((n + 127) / 128));
+    if (Fc.on())
+      k_explode<S, R, true><<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, ex_first, ex_mask, ex_sample,
+                                                     n, (const R*)smp_val, ns, (R)beta_child, (R)Fc.du[0],
+                                                     (R)Fc.du[1], (R)Fc.du[2], lbgk);
+    else
+      k_explode<S, R, false><<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, ex_first, ex_mask, ex_sample,
+                                                      n, (const R*)smp_val, ns, (R)beta_child, R(0), R(0), R(0),
+                                                      lbgk);
+    return cudaGetLastError();
+  });
+}
+
+// ---------------------------------------------------------------------------
+template <typename V>
+__device__ __forceinline__ double ldv(const void* p, long long i) {
+  return (double)((const V*)p)[i];
+}
+
+template <typename S, typename R>
+__global__ void k_init(PatchDev p, S* __restrict__ f0, S* __restrict__ f1, const void* rho_in, const void* u_in,
+                       int dtype, R uix, R uiy, R uiz) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= p.dim[0]) return;
+  const long long own = node_index(p, x, y, z);
+  const long long d = ((long long)z * p.dim[1] + y) * p.dim[0] + x;
+  const long long nd = (long long)p.dim[0] * p.dim[1] * p.dim[2];
+  const uint8_t t = p.type[own];
+  R rho = 1, ux = 0, uy = 0, uz = 0;
+  if (t == T_INLET) {
+    ux = uix;
+    uy = uiy;
+    uz = uiz;
+  } else if (t != T_SKIP && t != T_SOLID) {
+    if (dtype == 1) {
+      rho = (R)ldv<double>(rho_in, d);
+      ux = (R)ldv<double>(u_in, d);
+      uy = (R)ldv<double>(u_in, nd + d);
+      uz = (R)ldv<double>(u_in, 2 * nd + d);
+    } else {
+      rho = (R)ldv<float>(rho_in, d);
+      ux = (R)ldv<float>(u_in, d);
+      uy = (R)ldv<float>(u_in, nd + d);
+      uz = (R)ldv<float>(u_in, 2 * nd + d);
+    }
+  }
+  R fe[27];
+  feq_dev(rho - R(1), rho, ux, uy, uz, fe);
+  store_node<S, R>(p, f0, own, fe);
+  store_node<S, R>(p, f1, own, fe);
+}
+
+cudaError_t launch_init(int storage, const PatchDev& p, void* f0, void* f1, const void* rho, const void* u,
+                        int dtype, const double u_in[3], cudaStream_t st) {
+  return dispatch(storage, [&](auto ts, auto tr) {
+    using S = typename decltype(ts)::type;
+    using R = typename decltype(tr)::type;
+    dim3 block(128), grid((p.dim[0] + 127) / 128, p.dim[1], p.dim[2]);
+    k_init<S, R><<<grid, block, 0, st>>>(p, (S*)f0, (S*)f1, rho, u, dtype, (R)u_in[0], (R)u_in[1], (R)u_in[2]);
+    return cudaGetLastError();
+  });
+}
+
+// ---------------------------------------------------------------------------
+template <typename S, typename R>
+__device__ __forceinline__ void load_node(const PatchDev& p, const S* __restrict__ fin, long long own,
+                                          R (&f)[27]) {
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    f[i] = Stor<S>::ld(fin + (long long)i * p.plane + own);
+  });
+}
+
+template <typename V>
+__device__ __forceinline__ void stv(void* p, long long i, double v) {
+  ((V*)p)[i] = (V)v;
+}
+
+template <typename S, typename R>
+__global__ void k_moments(PatchDev p, const S* __restrict__ fin, void* rho_o, void* u_o, void* gamma_o, int dtype,
+                          R beta, R dux, R duy, R duz, int lbgk) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= p.dim[0]) return;
+  const long long own = node_index(p, x, y, z);
+  const long long d = ((long long)z * p.dim[1] + y) * p.dim[0] + x;
+  const long long nd = (long long)p.dim[0] * p.dim[1] * p.dim[2];
+  const uint8_t t = p.type[own];
+  double vals[5] = {0, 0, 0, 0, 0};
+  if (t != T_SKIP && t != T_SOLID) {
+    R f[27];
+    load_node<S, R>(p, fin, own, f);
+    R rho_t, rho, ux, uy, uz;
+    macro(f, rho_t, rho, ux, uy, uz);
+    vals[0] = (double)rho_t + 1.0;
+    vals[1] = ux + R(0.5) * dux;
+    vals[2] = uy + R(0.5) * duy;
+    vals[3] = uz + R(0.5) * duz;
+    if (gamma_o) vals[4] = kbc_collide<R, 0>(f, beta, R(0), R(0), R(0), lbgk != 0);
+  }
+  if (dtype == 1) {
+    if (rho_o) stv<double>(rho_o, d, vals[0]);
+    if (u_o)
+      for (int a = 0; a < 3; ++a) stv<double>(u_o, a * nd + d, vals[1 + a]);
+    if (gamma_o) stv<double>(gamma_o, d, vals[4]);
+  } else {
+    if (rho_o) stv<float>(rho_o, d, vals[0]);
+    if (u_o)
+      for (int a = 0; a < 3; ++a) stv<float>(u_o, a * nd + d, vals[1 + a]);
+    if (gamma_o) stv<float>(gamma_o, d, vals[4]);
+  }
+}
+
+cudaError_t launch_moments(int storage, const PatchDev& p, const void* fin, void* rho, void* u, void* gamma,
+                           int dtype, double beta, const Force& F, int lbgk, cudaStream_t st) {
+  return dispatch(storage, [&](auto ts, auto tr) {
+    using S = typename decltype(ts)::type;
+    using R = typename decltype(tr)::type;
+    dim3 block(128), grid((p.dim[0] + 127) / 128, p.dim[1], p.dim[2]);
+    k_moments<S, R><<<grid, block, 0, st>>>(p, (const S*)fin, rho, u, gamma, dtype, (R)beta, (R)F.du[0],
+                                            (R)F.du[1], (R)F.du[2], lbgk);
+    return cudaGetLastError();
+  });
+}
+
+// ---------------------------------------------------------------------------
+template <typename S, typename R>
+__global__ void k_copy_pop(PatchDev p, S* fstore, void* dense, int dtype, int to_dense) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= p.dim[0]) return;
+  const long long own = node_index(p, x, y, z);
+  const long long d = ((long long)z * p.dim[1] + y) * p.dim[0] + x;
+  const long long nd = (long long)p.dim[0] * p.dim[1] * p.dim[2];
+  for (int i = 0; i < 27; ++i) {
+    const double w = wi_rt(i);
+    if (to_dense) {
+      const double v = (double)Stor<S>::ld(fstore + (long long)i * p.plane + own) + w;
+      if (dtype == 1) ((double*)dense)[i * nd + d] = v;
+      else ((float*)dense)[i * nd + d] = (float)v;
+    } else {
+      const double v = dtype == 1 ? ((const double*)dense)[i * nd + d] : (double)((const float*)dense)[i * nd + d];
+      Stor<S>::st(fstore + (long long)i * p.plane + own, (R)(v - w));
+    }
+  }
+}
+
+cudaError_t launch_copy_pop(int storage, const PatchDev& p, void* fstore, void* dense, int dtype, int to_dense,
+                            cudaStream_t st) {
+  return dispatch(storage, [&](auto ts, auto tr) {
+    using S = typename decltype(ts)::type;
+    using R = typename decltype(tr)::type;
+    dim3 block(128), grid((p.dim[0] + 127) / 128, p.dim[1], p.dim[2]);
+    k_copy_pop<S, R><<<grid, block, 0, st>>>(p, (S*)fstore, dense, dtype, to_dense);
+    return cudaGetLastError();
+  });
+}
+
+// ---------------------------------------------------------------------------
+// FP64 diagnostics: fixed grid of blocks, fixed-order reductions (deterministic).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) k_diag(PatchDev p, const S* __restrict__ fin, double vw, R dux, R duy,
+                                              R duz, double* __restrict__ partial) {
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  double mn = 1e300;
+  double bad = 0;
+  const long long total = p.plane;
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+       n += (long long)gridDim.x * blockDim.x) {
+    const uint8_t t = p.type[n];
+    if (!(t == T_BULK || t == T_BC || t == T_D1 || t == T_INLET)) continue;
+    R f[27];
+    load_node<S, R>(p, fin, n, f);
+    R rho_t, rho, ux, uy, uz;
+    macro(f, rho_t, rho, ux, uy, uz);
+    const double r = 1.0 + (double)rho_t;
+    const double u[3] = {(double)ux + 0.5 * (double)dux, (double)uy + 0.5 * (double)duy,
+                         (double)uz + 0.5 * (double)duz};
+    if (!(r > 0.0) || !isfinite(r)) bad += 1.0;
+    acc[0] += vw * r;
+    acc[1] += vw * r * u[0];
+    acc[2] += vw * r * u[1];
+    acc[3] += vw * r * u[2];
+    acc[4] += vw * 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    acc[5] += 1.0;
+    mn = fmin(mn, r);
+  }
+  __shared__ double sh[8][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double v[8];
+  for (int k = 0; k < 6; ++k) v[k] = warp_sum(acc[k]);
+  v[6] = warp_min(mn);
+  v[7] = warp_sum(bad);
+  if (lane == 0)
+    for (int k = 0; k < 8; ++k) sh[wid][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int k = threadIdx.x;
+    double s = (k == 6) ? 1e300 : 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = (k == 6) ? fmin(s, sh[w][k]) : s + sh[w][k];
+    partial[blockIdx.x * 8 + k] = s;
+  }
+}
+
+cudaError_t launch_diag(int storage, const PatchDev& p, const void* fin, double vol_weight, const Force& F,
+                        double* partial, int blocks, cudaStream_t st) {
+  return dispatch(storage, [&](auto ts, auto tr) {
+    using S = typename decltype(ts)::type;
+    using R = typename decltype(tr)::type;
+    k_diag<S, R><<<blocks, 256, 0, st>>>(p, (const S*)fin, vol_weight, (R)F.du[0], (R)F.du[1], (R)F.du[2],
+                                          partial);
+    return cudaGetLastError();
+  });
+}
+
+__global__ void k_diag_final(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  if (threadIdx.x >= 8) return;
+  const int k = threadIdx.x;
+  double s = (k == 6) ? 1e300 : 0.0;
+  for (int b = 0; b < nb; ++b) s = (k == 6) ? fmin(s, partial[b * 8 + k]) : s + partial[b * 8 + k];
+  out[k] = s;
+}
+
+cudaError_t launch_diag_final(const double* partial, int total_blocks, double* out8, cudaStream_t st) {
+  k_diag_final<<<1, 32, 0, st>>>(partial, total_blocks, out8);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_collide_nodes(const R* __restrict__ fin, R* __restrict__ fout, R* __restrict__ gam, long long n,
+                                R beta, R dux, R duy, R duz, int lbgk, int force) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  R f[27];
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    f[i] = fin[i * n + k] - R(WI(i));
+  });
+  R g = force ? kbc_collide<R, 7>(f, beta, dux, duy, duz, lbgk != 0)
+              : kbc_collide<R, 0>(f, beta, dux, duy, duz, lbgk != 0);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    fout[i * n + k] = f[i] + R(WI(i));
+  });
+  if (gam) gam[k] = g;
+}
+
+cudaError_t launch_collide_nodes(const void* fin, void* fout, void* gamma, int64_t n, double beta, const Force& F,
+                                 int lbgk, int dtype, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  dim3 block(128), grid((unsigned)((n + 127) / 128));
+  if (dtype == 1)
+    k_collide_nodes<double><<<grid, block, 0, st>>>((const double*)fin, (double*)fout, (double*)gamma, n, beta,
+                                                    F.du[0], F.du[1], F.du[2], lbgk, F.on());
+  else
+    k_collide_nodes<float><<<grid, block, 0, st>>>((const float*)fin, (float*)fout, (float*)gamma, n, (float)beta,
+                                                   (float)F.du[0], (float)F.du[1], (float)F.du[2], lbgk, F.on());
+  return cudaGetLastError();
+}
+
+}  // namespace lbmk

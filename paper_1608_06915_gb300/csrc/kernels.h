@@ -1,0 +1,69 @@
+// Kernel launchers (host side).  Every launcher enqueues on the given stream
+// and returns the launch status; storage selects the instantiation:
+//   LBM_FP64 -> double/double, LBM_FP32 -> float/float,
+//   LBM_FP16_SHIFT -> __half/float, LBM_BF16_SHIFT -> __nv_bfloat16/float.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmk {
+
+struct PatchDev;
+
+struct Force {
+  double du[3];  // velocity increment per step of this level (exact difference method)
+  bool on() const { return du[0] != 0.0 || du[1] != 0.0 || du[2] != 0.0; }
+  // compile-time force mask of the hot kernels: 0 none, 1 x only, 4 z only, 7 any
+  int mask() const {
+    const int m = (du[0] != 0.0) | ((du[1] != 0.0) << 1) | ((du[2] != 0.0) << 2);
+    return (m == 0 || m == 1 || m == 4) ? m : 7;
+  }
+};
+
+// Bulk tiles through TMA (tmap_in / tmap_out / tmap_wrap: CUtensorMaps, 128
+// bytes, of the source buffer with the load box, of the destination buffer with
+// the store box, and of the source buffer with the wrap box; tiles:
+// x-tile | y << 16 | z << 32) and mixed tiles node by node (tile id
+// = (z * ny + y) * ntx + tx); a tile is 128 nodes along x.
+cudaError_t launch_sc_tma(int storage, const void* tmap_in, const void* tmap_out, const void* tmap_wrap,
+                          const PatchDev& p, const unsigned long long* tiles, int64_t ntiles, double beta,
+                          const Force& F, int lbgk, int* status, cudaStream_t st);
+cudaError_t launch_sc_tiles(int storage, const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,
+                            int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk, int* status,
+                            cudaStream_t st);
+// kind 0: load box (tile row + halos), 1: store box (tile row), 2: 16-byte wrap box
+cudaError_t make_tensor_map(int storage, void* out128, const void* base, const PatchDev& p, int kind);
+
+cudaError_t launch_coalesce(int storage, const PatchDev& child, const void* fin_child, const PatchDev& parent,
+                            void* fout_parent, const uint32_t* cf_parent, const uint32_t* cf_child, int64_t n,
+                            double rescale, double beta_parent, const Force& Fp, int lbgk, int* status,
+                            cudaStream_t st);
+
+cudaError_t launch_samples(int storage, const PatchDev& parent, const void* fin_parent, const PatchDev& child,
+                           const void* fin_child, const uint32_t* smp_node, const uint8_t* smp_kind, int64_t ns,
+                           void* smp_val, double rescale_parent, int* status, cudaStream_t st);
+
+cudaError_t launch_explode(int storage, const PatchDev& child, void* fout_child, const uint32_t* ex_node,
+                           const uint32_t* ex_first, const uint8_t* ex_mask, const uint32_t* ex_sample, int64_t n,
+                           const void* smp_val, int64_t ns, double beta_child, const Force& Fc, int lbgk,
+                           cudaStream_t st);
+
+cudaError_t launch_init(int storage, const PatchDev& p, void* f0, void* f1, const void* rho, const void* u,
+                        int dtype, const double u_in[3], cudaStream_t st);
+
+cudaError_t launch_moments(int storage, const PatchDev& p, const void* fin, void* rho, void* u, void* gamma,
+                           int dtype, double beta, const Force& F, int lbgk, cudaStream_t st);
+
+cudaError_t launch_copy_pop(int storage, const PatchDev& p, void* fstore, void* dense, int dtype, int to_dense,
+                            cudaStream_t st);
+
+// FP64 partial sums of one patch into partial[blocks][8]; see lbm_diagnostics.
+cudaError_t launch_diag(int storage, const PatchDev& p, const void* fin, double vol_weight, const Force& F,
+                        double* partial, int blocks, cudaStream_t st);
+cudaError_t launch_diag_final(const double* partial, int total_blocks, double* out8, cudaStream_t st);
+
+cudaError_t launch_collide_nodes(const void* fin, void* fout, void* gamma, int64_t n, double beta, const Force& F,
+                                 int lbgk, int dtype, cudaStream_t st);
+
+}  // namespace lbmk

@@ -1,0 +1,544 @@
+// Layout builder: patches, node classes and interface tables of a refined grid.
+//
+// Geometry (Sec. III, the overlap layout of Fig. 1, which the text describes
+// but does not draw): a level-(l+1) box [a,b] (in level-l coordinates) holds
+// child nodes at every half-integer position of [a,b].  Across each box face
+// that is neither a wall face nor a periodic span, the child interface is two
+// child nodes wide (depth 0 and 1) and the parent keeps one interface layer:
+// parent nodes of [a+1,b-1] outside the hole [a+2,b-2] are the twins x_t,cf.
+// Child interface nodes whose three coordinates fall on the parent lattice are
+// the fine twins x_t,fc; the others are reconstruction nodes x_r, rebuilt by
+// the centred four-point Lagrange rule (Eq. interp) along each off-lattice
+// axis from samples at parent positions +-1/2 and +-3/2 parent spacings away.
+// A sample under a parent twin or inside the parent hole is taken from the
+// child node at that position.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <unordered_map>
+
+#include "grid.h"
+
+namespace lbm {
+namespace {
+
+constexpr int64_t kLo = INT64_MIN / 4;
+constexpr int64_t kHi = INT64_MAX / 4;
+
+inline int cvel(int i, int a) { return (a == 0 ? i % 3 : a == 1 ? (i / 3) % 3 : i / 9) - 1; }
+
+struct Geo {
+  HostGrid& g;
+
+  void wrap(int lev, int64_t X[3]) const {
+    for (int a = 0; a < 3; ++a)
+      if (g.periodic(a)) {
+        int64_t N = g.period(lev, a);
+        X[a] = ((X[a] % N) + N) % N;
+      }
+  }
+  bool in_region(const HostPatch& p, const int64_t X[3]) const {
+    for (int a = 0; a < 3; ++a)
+      if (X[a] < p.rlo[a] || X[a] > p.rhi[a]) return false;
+    return true;
+  }
+  // X in the parent's coordinates
+  bool in_hole(const HostPatch& c, const int64_t X[3]) const {
+    for (int a = 0; a < 3; ++a) {
+      if (c.span[a]) continue;
+      int64_t lo = c.flo[a] ? c.blo[a] + 2 : kLo, hi = c.fhi[a] ? c.bhi[a] - 2 : kHi;
+      if (X[a] < lo || X[a] > hi) return false;
+    }
+    return true;
+  }
+  bool in_cf(const HostPatch& c, const int64_t X[3]) const {
+    for (int a = 0; a < 3; ++a) {
+      if (c.span[a]) continue;
+      int64_t lo = c.flo[a] ? c.blo[a] + 1 : kLo, hi = c.fhi[a] ? c.bhi[a] - 1 : kHi;
+      if (X[a] < lo || X[a] > hi) return false;
+    }
+    return !in_hole(c, X);
+  }
+  int64_t depth(const HostPatch& c, const int64_t Y[3]) const {
+    int64_t d = kHi;
+    for (int a = 0; a < 3; ++a) {
+      if (c.span[a]) continue;
+      if (c.flo[a]) d = std::min(d, Y[a] - 2 * c.blo[a]);
+      if (c.fhi[a]) d = std::min(d, 2 * c.bhi[a] - Y[a]);
+    }
+    return d;
+  }
+  bool exists(const HostPatch& p, const int64_t X[3]) const {
+    if (!in_region(p, X)) return false;
+    for (int k : p.kids)
+      if (in_hole(g.P[k], X)) return false;
+    return true;
+  }
+  bool solid_at(int lev, const int64_t X[3]) const {
+    if (g.solid.empty() || lev != g.desc.solid_level) return false;
+    int64_t o[3];
+    for (int a = 0; a < 3; ++a) {
+      o[a] = X[a] - g.desc.solid_lo[a];
+      if (o[a] < 0 || o[a] >= g.desc.solid_dims[a]) return false;
+    }
+    return g.solid[(size_t)((o[2] * g.desc.solid_dims[1] + o[1]) * g.desc.solid_dims[0] + o[0])] != 0;
+  }
+  // storage index of a global coordinate, -1 outside the storage box
+  int64_t index(const HostPatch& p, const int64_t X[3]) const {
+    int64_t o[3];
+    for (int a = 0; a < 3; ++a) {
+      o[a] = X[a] - p.org[a];
+      if (o[a] < 0 || o[a] >= p.dim[a]) return -1;
+    }
+    return (o[2] * p.dim[1] + o[1]) * p.nxp + o[0];
+  }
+  void coords(const HostPatch& p, int64_t n, int64_t X[3]) const {
+    X[0] = p.org[0] + n % p.nxp;
+    X[1] = p.org[1] + (n / p.nxp) % p.dim[1];
+    X[2] = p.org[2] + n / (p.nxp * p.dim[1]);
+  }
+
+  // Pull source of direction i at node X: 0 plain (src set), 1 bounce-back,
+  // 2 outlet clamp (src set), 3 missing.
+  int resolve(const HostPatch& p, const int64_t X[3], int i, int64_t* src) const {
+    int64_t S[3];
+    bool clamp = false;
+    for (int a = 0; a < 3; ++a) S[a] = X[a] - cvel(i, a);
+    for (int a = 0; a < 3; ++a) {
+      if (g.periodic(a)) continue;
+      if (S[a] < 0) {
+        if (g.wall(a, 0)) return 1;
+        return 3;
+      }
+      if (S[a] > g.maxc(p.level, a)) {
+        if (g.wall(a, 1)) return 1;
+        if (a == g.desc.inflow_axis) {
+          S[a] = g.maxc(p.level, a);
+          clamp = true;
+        } else {
+          return 3;
+        }
+      }
+    }
+    wrap(p.level, S);
+    int64_t j = index(p, S);
+    if (j < 0) return 3;
+    uint8_t t = p.type[j];
+    if (t == T_SKIP) return 3;
+    if (t == T_SOLID) return 1;
+    *src = j;
+    return clamp ? 2 : 0;
+  }
+};
+
+std::string fmt_node(const char* what, int lev, const int64_t X[3]) {
+  return std::string(what) + " at level " + std::to_string(lev) + " node (" + std::to_string(X[0]) + "," +
+         std::to_string(X[1]) + "," + std::to_string(X[2]) + ")";
+}
+
+}  // namespace
+
+std::string build_layout(HostGrid& g) {
+  const lbm_desc& d = g.desc;
+  Geo geo{g};
+  for (int a = 0; a < 3; ++a) {
+    if (d.n[a] < 4) return "domain extent below 4 nodes";
+    if (g.periodic(a) && (g.wall(a, 0) || g.wall(a, 1))) return "periodic axis with walls";
+    if (!g.periodic(a) && a != d.inflow_axis && !(g.wall(a, 0) && g.wall(a, 1)))
+      return "a non-periodic axis needs walls on both faces, or the inflow";
+  }
+  if (d.inflow_axis >= 3) return "inflow axis out of range";
+  if (d.inflow_axis >= 0 &&
+      (g.periodic(d.inflow_axis) || g.wall(d.inflow_axis, 0) || g.wall(d.inflow_axis, 1)))
+    return "inflow axis must be non-periodic and without walls";
+  if (d.nu0 <= 0) return "nu0 must be positive";
+  if (g.thermal && (d.pr <= 0 || d.pr > 1)) return "thermal model implemented for 0 < Pr <= 1";
+
+  g.P.clear();
+  HostPatch root;
+  for (int a = 0; a < 3; ++a) {
+    root.span[a] = g.periodic(a);
+    root.rlo[a] = 0;
+    root.rhi[a] = g.periodic(a) ? g.period(0, a) - 1 : g.maxc(0, a);
+  }
+  g.P.push_back(root);
+  int maxlev = 0;
+  for (auto& b : g.boxes) {
+    if (b.level < 1 || b.level > 12) return "box level out of range";
+    maxlev = std::max(maxlev, (int)b.level);
+  }
+  g.nlev = maxlev + 1;
+  for (int lev = 1; lev <= maxlev; ++lev)
+    for (auto& bx : g.boxes) {
+      if (bx.level != lev) continue;
+      HostPatch c;
+      c.level = lev;
+      for (int a = 0; a < 3; ++a) {
+        if (bx.lo[a] > bx.hi[a] || bx.lo[a] < 0 || bx.hi[a] > d.n[a] - 1) return "box outside the domain";
+        c.span[a] = g.periodic(a) && bx.lo[a] == 0 && bx.hi[a] == d.n[a] - 1;
+        c.blo[a] = (int64_t)bx.lo[a] << (lev - 1);
+        c.bhi[a] = (int64_t)bx.hi[a] << (lev - 1);
+        if (c.span[a]) {
+          c.rlo[a] = 0;
+          c.rhi[a] = g.period(lev, a) - 1;
+        } else {
+          c.rlo[a] = 2 * c.blo[a];
+          c.rhi[a] = 2 * c.bhi[a];
+          c.flo[a] = !(bx.lo[a] == 0 && g.wall(a, 0));
+          c.fhi[a] = !(bx.hi[a] == d.n[a] - 1 && g.wall(a, 1));
+          if ((c.flo[a] || c.fhi[a]) && c.bhi[a] - c.blo[a] < 8)
+            return "refinement box narrower than 8 parent spacings";
+          if (a == d.inflow_axis && (bx.lo[a] < 2 || bx.hi[a] > d.n[a] - 3))
+            return "refinement box too close to the inflow or outflow face";
+        }
+      }
+      int par = -1;
+      for (size_t q = 0; q < g.P.size(); ++q) {
+        const HostPatch& pp = g.P[q];
+        if (pp.level != lev - 1) continue;
+        bool inside = true;
+        for (int a = 0; a < 3; ++a) {
+          if (c.span[a]) {
+            inside = inside && pp.span[a];
+            continue;
+          }
+          inside = inside && c.blo[a] >= pp.rlo[a] && c.bhi[a] <= pp.rhi[a];
+        }
+        if (inside) {
+          if (par >= 0) return "box nests in two parent boxes";
+          par = (int)q;
+        }
+      }
+      if (par < 0) return "refinement box does not nest in a box of the level below";
+      c.parent = par;
+      g.P.push_back(c);
+      g.P[par].kids.push_back((int)g.P.size() - 1);
+    }
+  // sibling boxes must not overlap (holes and interfaces are per child)
+  for (size_t q = 1; q < g.P.size(); ++q)
+    for (size_t r = q + 1; r < g.P.size(); ++r) {
+      if (g.P[q].level != g.P[r].level) continue;
+      bool overlap = true;
+      for (int a = 0; a < 3; ++a)
+        overlap = overlap && !(g.P[q].rhi[a] + 16 < g.P[r].rlo[a] || g.P[r].rhi[a] + 16 < g.P[q].rlo[a]);
+      if (overlap) return "boxes of one level overlap or lie within 8 parent spacings";
+    }
+
+  // relaxation parameters (Eq. visc, Sec. II.B, Sec. III.A)
+  double beta, beta1 = 0;
+  if (g.thermal) {
+    beta = 1.0 / (2.0 * d.nu0 / d.t0 + 1.0);
+    beta1 = 1.0 / (2.0 * (d.nu0 / d.pr) / d.t0 + 1.0);
+  } else {
+    beta = 1.0 / (6.0 * d.nu0 + 1.0);
+  }
+  std::vector<double> bl(g.nlev), bl1(g.nlev);
+  for (int l = 0; l < g.nlev; ++l) {
+    bl[l] = beta;
+    bl1[l] = beta1;
+    beta = 1.0 / (1.0 + 2.0 * (1.0 / beta - 1.0));
+    if (g.thermal) beta1 = 1.0 / (1.0 + 2.0 * (1.0 / beta1 - 1.0));
+  }
+
+  // storage boxes and first-pass classes
+  for (auto& p : g.P) {
+    p.beta = bl[p.level];
+    p.beta1 = bl1[p.level];
+    int64_t lo[3] = {kHi, kHi, kHi}, hi[3] = {kLo, kLo, kLo};
+    // bounding box of the nodes: a node exists unless it lies in a child hole;
+    // the region minus holes is scanned axis by axis on its extreme lines
+    int64_t X[3];
+    for (X[2] = p.rlo[2]; X[2] <= p.rhi[2]; ++X[2])
+      for (X[1] = p.rlo[1]; X[1] <= p.rhi[1]; ++X[1]) {
+        // on one x-row the existing nodes form at most a few runs; test both ends of
+        // every run cheaply by scanning the row only when a hole touches it
+        bool row_has_hole = false;
+        for (int k : p.kids) {
+          const HostPatch& c = g.P[k];
+          bool hit = true;
+          for (int a = 1; a < 3; ++a) {
+            if (c.span[a]) continue;
+            int64_t l2 = c.flo[a] ? c.blo[a] + 2 : kLo, h2 = c.fhi[a] ? c.bhi[a] - 2 : kHi;
+            hit = hit && X[a] >= l2 && X[a] <= h2;
+          }
+          row_has_hole = row_has_hole || hit;
+        }
+        if (!row_has_hole) {
+          lo[0] = std::min(lo[0], p.rlo[0]);
+          hi[0] = std::max(hi[0], p.rhi[0]);
+          for (int a = 1; a < 3; ++a) {
+            lo[a] = std::min(lo[a], X[a]);
+            hi[a] = std::max(hi[a], X[a]);
+          }
+          continue;
+        }
+        for (X[0] = p.rlo[0]; X[0] <= p.rhi[0]; ++X[0]) {
+          if (!geo.exists(p, X)) continue;
+          for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], X[a]);
+            hi[a] = std::max(hi[a], X[a]);
+          }
+        }
+      }
+    if (lo[0] > hi[0]) return "a patch has no nodes";
+    for (int a = 0; a < 3; ++a) {
+      p.org[a] = lo[a];
+      p.dim[a] = hi[a] - lo[a] + 1;
+      if (p.span[a] && p.dim[a] != g.period(p.level, a)) return "periodic span broken by a refinement hole";
+      if (p.dim[a] > (1 << 24)) return "patch extent too large";
+    }
+    p.nxp = (p.dim[0] + 31) / 32 * 32;
+    p.plane = p.nxp * p.dim[1] * p.dim[2];
+    if (p.plane >= (int64_t)UINT32_MAX) return "patch has too many nodes for 32-bit indices";
+    p.type.assign((size_t)p.plane, T_SKIP);
+  }
+  // first pass: classes from geometry (independent per node)
+  for (auto& p : g.P) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t z = 0; z < p.dim[2]; ++z) {
+      int64_t X[3];
+      for (int64_t y = 0; y < p.dim[1]; ++y)
+        for (int64_t x = 0; x < p.dim[0]; ++x) {
+          const int64_t n = (z * p.dim[1] + y) * p.nxp + x;
+          X[0] = p.org[0] + x;
+          X[1] = p.org[1] + y;
+          X[2] = p.org[2] + z;
+          if (!geo.exists(p, X)) continue;
+          uint8_t t = T_BULK;  // provisional fluid class
+          if (geo.solid_at(p.level, X)) t = T_SOLID;
+          else if (p.level == 0 && d.inflow_axis >= 0 && X[d.inflow_axis] == 0) t = T_INLET;
+          else {
+            for (int k : p.kids)
+              if (geo.in_cf(g.P[k], X)) t = T_CF;
+            if (t != T_CF && p.level > 0) {
+              int64_t dp = geo.depth(p, X);
+              if (dp == 0) t = T_D0;
+              else if (dp == 1) t = T_D1;
+            }
+          }
+          p.type[n] = t;
+        }
+    }
+  }
+  // second pass: resolve pull sources of fluid nodes.  Nodes away from the
+  // storage edges (or on spanned axes) only need their 26 neighbours' classes;
+  // edge nodes go through the full resolution (walls, outlet, wrap).
+  for (auto& p : g.P) {
+    std::vector<uint8_t> mark((size_t)p.plane, 0);
+    std::string perr;
+    int64_t fluid = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : fluid)
+    for (int64_t z = 0; z < p.dim[2]; ++z) {
+      int64_t X[3];
+      for (int64_t y = 0; y < p.dim[1]; ++y)
+        for (int64_t x = 0; x < p.dim[0]; ++x) {
+          const int64_t n = (z * p.dim[1] + y) * p.nxp + x;
+          const uint8_t t = p.type[n];
+          if (t == T_SKIP || t == T_SOLID) continue;
+          ++fluid;
+          if (t != T_BULK && t != T_D1) continue;
+          const int64_t L[3] = {x, y, z};
+          bool interior = true;
+          for (int a = 0; a < 3; ++a) interior = interior && (p.span[a] || (L[a] > 0 && L[a] < p.dim[a] - 1));
+          bool special = false, missing = false;
+          if (interior) {
+            for (int i = 0; i < 27 && !missing; ++i) {
+              int64_t S[3];
+              for (int a = 0; a < 3; ++a) {
+                S[a] = L[a] - cvel(i, a);
+                if (S[a] < 0) S[a] += p.dim[a];
+                else if (S[a] >= p.dim[a]) S[a] -= p.dim[a];
+              }
+              const uint8_t tt = p.type[(S[2] * p.dim[1] + S[1]) * p.nxp + S[0]];
+              if (tt == T_SKIP) missing = true;
+              else if (tt == T_SOLID) special = true;
+            }
+          }
+          if (!interior || missing) {
+            special = false;
+            X[0] = p.org[0] + x;
+            X[1] = p.org[1] + y;
+            X[2] = p.org[2] + z;
+            for (int i = 0; i < 27; ++i) {
+              int64_t s;
+              int r = geo.resolve(p, X, i, &s);
+              if (r == 3) {
+#pragma omp critical(lbm_layout_err)
+                if (perr.empty()) perr = fmt_node("unresolved pull source", p.level, X);
+                break;
+              }
+              if (r != 0) special = true;
+            }
+          }
+          if (t == T_BULK && special) mark[n] = 1;
+        }
+    }
+    if (!perr.empty()) return perr;
+    for (int64_t n = 0; n < p.plane; ++n)
+      if (mark[n]) p.type[n] = T_BC;
+    p.n_fluid = fluid;
+    if (p.level > 0 && g.P[p.parent].level != p.level - 1) return "internal: parent level";
+  }
+  // stream-collide tiles
+  for (auto& p : g.P) {
+    p.ntx = (p.dim[0] + 127) / 128;
+    for (int k = 0; k < 2; ++k) {
+      p.tiles_pure[k].clear();
+      p.tiles_mixed[k].clear();
+    }
+    for (int64_t z = 0; z < p.dim[2]; ++z)
+      for (int64_t y = 0; y < p.dim[1]; ++y)
+        for (int64_t tx = 0; tx < p.ntx; ++tx) {
+          int nb = 0, nbc = 0, nd1 = 0, nd1plain = 0, n = 0;
+          for (int64_t x = tx * 128; x < std::min<int64_t>(p.dim[0], tx * 128 + 128); ++x) {
+            const int64_t m = (z * p.dim[1] + y) * p.nxp + x;
+            const uint8_t t = p.type[m];
+            ++n;
+            nb += t == T_BULK;
+            nbc += t == T_BC;
+            if (t == T_D1) {
+              ++nd1;
+              int64_t X[3], src;
+              geo.coords(p, m, X);
+              bool plain = true;
+              for (int i = 0; i < 27 && plain; ++i) plain = geo.resolve(p, X, i, &src) == 0;
+              // plain also along the spanned-axis wrap used by the TMA path
+              nd1plain += plain;
+            }
+          }
+          const uint32_t id = (uint32_t)((z * p.dim[1] + y) * p.ntx + tx);
+          const uint64_t packed = (uint64_t)tx | ((uint64_t)y << 16) | ((uint64_t)z << 32);
+          // the TMA path fetches the periodic wrap of x-spanning rows as 16-byte
+          // boxes at x = dim - H: row-edge tiles need dim a multiple of 8 nodes
+          const bool edge = tx == 0 || (tx + 1) * 128 >= p.dim[0];
+          const bool wrap_ok = !p.span[0] || !edge || p.dim[0] % 8 == 0;
+          // even steps: bulk (and boundary) nodes; depth-1 nodes are rebuilt by explode
+          if (nb == n && wrap_ok) p.tiles_pure[0].push_back(packed);
+          else if (nb + nbc > 0) p.tiles_mixed[0].push_back(id);
+          // odd steps: depth-1 nodes are streamed too
+          if (nb + nd1plain == n && nd1plain == nd1 && wrap_ok) p.tiles_pure[1].push_back(packed);
+          else if (nb + nbc + nd1 > 0) p.tiles_mixed[1].push_back(id);
+        }
+  }
+  // interface tables, stored on the child
+  for (size_t ci = 1; ci < g.P.size(); ++ci) {
+    HostPatch& c = g.P[ci];
+    HostPatch& par = g.P[c.parent];
+    std::unordered_map<uint64_t, uint32_t> ids;
+    auto sample_id = [&](uint8_t kind, int64_t node) -> uint32_t {
+      uint64_t key = ((uint64_t)kind << 40) | (uint64_t)node;
+      auto it = ids.find(key);
+      if (it != ids.end()) return it->second;
+      uint32_t id = (uint32_t)c.smp_node.size();
+      ids.emplace(key, id);
+      c.smp_node.push_back((uint32_t)node);
+      c.smp_kind.push_back(kind);
+      return id;
+    };
+    int64_t Y[3];
+    for (int64_t n = 0; n < c.plane; ++n) {
+      uint8_t t = c.type[n];
+      if (t != T_D0 && t != T_D1) continue;
+      geo.coords(c, n, Y);
+      uint8_t mask = 0;
+      for (int a = 0; a < 3; ++a)
+        if (Y[a] & 1) mask |= (uint8_t)(1u << a);
+      c.ex_node.push_back((uint32_t)n);
+      c.ex_mask.push_back(mask);
+      c.ex_first.push_back((uint32_t)c.ex_sample.size());
+      int cnt[3];
+      int64_t pos[3][4];
+      for (int a = 0; a < 3; ++a) {
+        if (mask & (1u << a)) {
+          cnt[a] = 4;
+          for (int k = 0; k < 4; ++k) pos[a][k] = (Y[a] - 3 + 2 * k) / 2;
+        } else {
+          cnt[a] = 1;
+          pos[a][0] = Y[a] / 2;
+        }
+      }
+      for (int kz = 0; kz < cnt[2]; ++kz)
+        for (int ky = 0; ky < cnt[1]; ++ky)
+          for (int kx = 0; kx < cnt[0]; ++kx) {
+            int64_t X[3] = {pos[0][kx], pos[1][ky], pos[2][kz]};
+            geo.wrap(par.level, X);
+            int64_t pj = geo.index(par, X);
+            bool parent_node = pj >= 0 && par.type[pj] != T_SKIP;
+            if (parent_node && !geo.in_cf(c, X)) {
+              uint8_t pt = par.type[pj];
+              if (pt != T_BULK && pt != T_BC) return fmt_node("reconstruction sample on a non-bulk parent node", par.level, X);
+              c.ex_sample.push_back(sample_id(S_PARENT, pj));
+            } else {
+              if (!parent_node && !geo.in_hole(c, X))
+                return fmt_node("reconstruction sample outside both levels", par.level, X);
+              int64_t Ys[3] = {2 * X[0], 2 * X[1], 2 * X[2]};
+              geo.wrap(c.level, Ys);
+              int64_t cj = geo.index(c, Ys);
+              if (cj < 0 || (c.type[cj] != T_BULK && c.type[cj] != T_BC))
+                return fmt_node("reconstruction sample on a non-bulk child node", c.level, Ys);
+              c.ex_sample.push_back(sample_id(S_CHILD, cj));
+            }
+          }
+    }
+    c.ex_first.push_back((uint32_t)c.ex_sample.size());
+    // coalesce pairs: parent twins x_t,cf and the coinciding child node
+    int64_t X[3];
+    for (int64_t n = 0; n < par.plane; ++n) {
+      if (par.type[n] != T_CF) continue;
+      geo.coords(par, n, X);
+      if (!geo.in_cf(c, X)) continue;
+      int64_t Yc[3] = {2 * X[0], 2 * X[1], 2 * X[2]};
+      geo.wrap(c.level, Yc);
+      int64_t cj = geo.index(c, Yc);
+      if (cj < 0 || (c.type[cj] != T_BULK && c.type[cj] != T_BC))
+        return fmt_node("parent twin without a bulk child twin", par.level, X);
+      c.cf_parent.push_back((uint32_t)n);
+      c.cf_child.push_back((uint32_t)cj);
+    }
+  }
+  // parent twins that are also interface nodes of the parent's own parent
+  for (auto& p : g.P)
+    for (int64_t n = 0; n < p.plane; ++n)
+      if (p.type[n] == T_CF && p.level > 0) {
+        int64_t X[3];
+        geo.coords(p, n, X);
+        if (geo.depth(p, X) <= 1) return fmt_node("child box too close to its parent's interface", p.level, X);
+      }
+  return std::string();
+}
+
+size_t plan_memory(HostGrid& g) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  const size_t ncomp = g.thermal ? 59 : 31;
+  for (auto& p : g.P) {
+    size_t pop = 27 * (size_t)p.plane * g.pop_bytes;
+    p.off_f[0] = take(pop);
+    p.off_f[1] = take(pop);
+    if (g.thermal) {
+      p.off_g[0] = take(pop);
+      p.off_g[1] = take(pop);
+    }
+    p.off_type = take((size_t)p.plane);
+    p.off_tiles_pure[0] = take(8 * p.tiles_pure[0].size());
+    p.off_tiles_pure[1] = take(8 * p.tiles_pure[1].size());
+    p.off_tiles_mixed[0] = take(4 * p.tiles_mixed[0].size());
+    p.off_tiles_mixed[1] = take(4 * p.tiles_mixed[1].size());
+    p.off_ex_node = take(4 * p.ex_node.size());
+    p.off_ex_first = take(4 * p.ex_first.size());
+    p.off_ex_mask = take(p.ex_mask.size());
+    p.off_ex_sample = take(4 * p.ex_sample.size());
+    p.off_smp_node = take(4 * p.smp_node.size());
+    p.off_smp_kind = take(p.smp_kind.size());
+    p.off_smp_val = take(ncomp * p.smp_node.size() * g.real_bytes);
+    p.off_cf_parent = take(4 * p.cf_parent.size());
+    p.off_cf_child = take(4 * p.cf_child.size());
+  }
+  return off;
+}
+
+}  // namespace lbm

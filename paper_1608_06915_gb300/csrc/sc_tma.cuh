@@ -1,0 +1,416 @@
+// Bulk stream-collide through TMA: the hot kernel of the refined step.
+//
+// A tile is a run of 128 nodes along x at one (y, z).  For each of the 27
+// populations the tile pulls one row segment, shifted by -c_i; rows are
+// fetched with cp.async.bulk.tensor (TMA) as boxes [x0 - H, x0 + 128 + H)
+// (H elements = 16 bytes, the start alignment TMA requires), so every shift
+// of -1, 0, +1 along x is a fixed offset into the same shared-memory row.
+// The post-collision tile is written to a shared-memory output stage and
+// stored back by TMA, 27 rows of 128 nodes.
+//
+// Warp roles: one thread of warp 4 is the producer -- it waits until a ring
+// stage is free (mbarrier "empty"), posts the expected byte count and issues the
+// 27 row loads of the next tile; warps 0-3 are consumers -- they wait for the
+// stage (mbarrier "full"), read their 27 values, release the stage, collide,
+// write their 32-node segment of the 27 output rows to shared memory and one
+// lane stores it back with 27 TMA stores, so consumer warps never wait for each
+// other.  TMA instructions are issued by single threads: with per-lane operands
+// the compiler would serialise them lane by lane.  Persistent CTAs walk a list of tiles whose nodes are all
+// plain bulk nodes (every pull source stored, wrap only on spanned axes);
+// tiles holding wall, solid, outlet or interface nodes go to k_sc_tiles,
+// which pulls node by node.
+//
+// Waits are bounded: a stage that does not arrive within about a second sets
+// bit 1 of the status word; the CTA then waits (bounded again) for the copies
+// it has in flight and returns.
+#pragma once
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "../../include/lbm.h"
+#include "device.cuh"
+#include "kernels.h"
+
+namespace lbmk {
+
+template <typename S>
+struct TmaCfg {
+  static constexpr int BX = 128;                                        // nodes per tile
+  static constexpr int H = 16 / (int)sizeof(S);                         // halo, elements
+  static constexpr int W = BX + 2 * H;                                  // load box width, elements
+  static constexpr int SLOT = (W * (int)sizeof(S) + 127) / 128 * 128;   // bytes per loaded row
+  static constexpr int OSEG = 32;                                       // nodes per warp segment
+  static constexpr int OSLOT = OSEG * (int)sizeof(S) < 128 ? 128 : OSEG * (int)sizeof(S);  // bytes per stored row
+  static constexpr int SIDE = 128;                                      // one 16-byte wrap box, padded
+  static constexpr int STAGE = 27 * SLOT + 18 * SIDE;                   // rows + 2 x 9 wrap boxes
+  static constexpr int OSTAGE = 4 * 27 * OSLOT;                         // [warp][population][32 nodes]
+  static constexpr uint32_t TX = 27u * W * (uint32_t)sizeof(S);        // bytes of the 27 row loads
+  static constexpr uint32_t TXW = 9u * 16u;                             // bytes of 9 wrap boxes
+#ifndef LBM_TMA_DI
+  static constexpr int DI = sizeof(S) == 8 ? 2 : 3;                     // load stages
+#else
+  static constexpr int DI = LBM_TMA_DI;
+#endif
+#ifndef LBM_TMA_DO
+  static constexpr int DO = 1;                                          // store stages
+#else
+  static constexpr int DO = LBM_TMA_DO;
+#endif
+#ifndef LBM_TMA_PF
+  static constexpr int PF = 0;                                          // L2 prefetch distance beyond the ring (tiles)
+#else
+  static constexpr int PF = LBM_TMA_PF;
+#endif
+  static constexpr int SMEM = DI * STAGE + DO * OSTAGE + 128;           // + slack for 128-byte alignment
+  static constexpr int THREADS = 160;                                   // 4 consumer warps + 1 producer
+};
+
+template <typename S>
+struct SCvt;
+template <>
+struct SCvt<double> {
+  static __device__ __forceinline__ double to(double v) { return v; }
+};
+template <>
+struct SCvt<float> {
+  static __device__ __forceinline__ float to(float v) { return v; }
+};
+template <>
+struct SCvt<__half> {
+  static __device__ __forceinline__ float to(__half v) { return __half2float(v); }
+};
+template <>
+struct SCvt<__nv_bfloat16> {
+  static __device__ __forceinline__ float to(__nv_bfloat16 v) { return __bfloat162float(v); }
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: about a second at most.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 24); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 32) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_row(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
+                                             int i) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(i), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tma_store_row(const CUtensorMap* map, const void* src, int x, int y, int z, int i) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(z), "r"(i), "r"(smem_u32(src))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_row(const CUtensorMap* map, int x, int y, int z, int i) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z), "r"(i)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ int wrap_axis(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// tile list entries: x-tile | y << 16 | z << 32
+__device__ __forceinline__ void tile_xyz(unsigned long long t, int& tx, int& y, int& z) {
+  tx = (int)(t & 0xffffu);
+  y = (int)((t >> 16) & 0xffffu);
+  z = (int)(t >> 32);
+}
+
+// Periodic x: the first tile of a row needs, for the 9 populations with
+// c_x = +1 (i = 3j + 2), the element at x = dim - 1; the last tile, for the 9
+// with c_x = -1 (i = 3j), the element at x = 0.  Both come as 16-byte boxes
+// (map_wrap) into side slots after the 27 rows of the stage: slot j holds
+// [dim - H, dim) of population 3j + 2, slot 9 + j holds [0, H) of population 3j.
+// Every TMA destination in shared memory starts on a 128-byte boundary.
+template <typename S, typename R, int FM>
+__global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensorMap map_in,
+                                                const __grid_constant__ CUtensorMap map_out,
+                                                const __grid_constant__ CUtensorMap map_wrap, PatchDev p,
+                                                const unsigned long long* __restrict__ tiles, int ntiles, R beta,
+                                                R dux, R duy, R duz, int lbgk, int* status) {
+  using C = TmaCfg<S>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  unsigned char* ostage = smem + C::DI * C::STAGE;
+  __shared__ __align__(8) uint64_t full[C::DI], empty[C::DI];
+  __shared__ int4 tile_at[C::DI];  // tile coordinates of each stage, published with its mbarrier
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nmine = (int)blockIdx.x < ntiles ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  if (tid == 0) {
+    for (int s = 0; s < C::DI; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == 4) {
+    // ---------------- producer (one thread: TMA operands stay warp-uniform) ----------------
+    if (lane != 0) return;
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_in)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_out)) : "memory");
+    for (int k = 0; k < nmine; ++k) {
+      const int s = k % C::DI;
+      if (k >= C::DI && !mbar_wait_bounded(&empty[s], (uint32_t)((k / C::DI) - 1) & 1u)) {
+        atomicOr(status, 2);
+        return;  // consumers time out on the stages never filled
+      }
+      if (C::PF > 0 && k + C::DI + C::PF - 1 < nmine) {
+        // warm L2 with the rows of a tile beyond the ring
+        int px, py, pz;
+        tile_xyz(tiles[blockIdx.x + (size_t)(k + C::DI + C::PF - 1) * gridDim.x], px, py, pz);
+#pragma unroll 1
+        for (int j = 0; j < 9; ++j) {
+          const int sy = wrap_axis(py - (j % 3 - 1), p.dim[1]);
+          const int sz = wrap_axis(pz - (j / 3 - 1), p.dim[2]);
+#pragma unroll
+          for (int cx = 0; cx < 3; ++cx) tma_prefetch_row(&map_in, px * C::BX - C::H, sy, sz, 3 * j + cx);
+        }
+      }
+      int tx, ty, tz;
+      tile_xyz(tiles[blockIdx.x + (size_t)k * gridDim.x], tx, ty, tz);
+      const bool first = p.span[0] && tx == 0;
+      const bool last = p.span[0] && (tx + 1) * C::BX >= p.dim[0];
+      tile_at[s] = make_int4(tx, ty, tz, 0);
+      mbar_expect_tx(&full[s], C::TX + (first ? C::TXW : 0u) + (last ? C::TXW : 0u));
+      unsigned char* stage = smem + s * C::STAGE;
+      unsigned char* side = stage + 27 * C::SLOT;
+      const int x0 = tx * C::BX - C::H;
+#pragma unroll 1
+      for (int cz = 0; cz < 3; ++cz) {
+        const int sz = wrap_axis(tz - (cz - 1), p.dim[2]);
+#pragma unroll 1
+        for (int cy = 0; cy < 3; ++cy) {
+          const int sy = wrap_axis(ty - (cy - 1), p.dim[1]);
+          const int j = 3 * cz + cy;  // populations 3j, 3j + 1, 3j + 2 share this source row
+#pragma unroll
+          for (int cx = 0; cx < 3; ++cx) tma_load_row(stage + (3 * j + cx) * C::SLOT, &map_in, &full[s], x0, sy, sz, 3 * j + cx);
+          if (first) tma_load_row(side + j * C::SIDE, &map_wrap, &full[s], p.dim[0] - C::H, sy, sz, 3 * j + 2);
+          if (last) tma_load_row(side + (9 + j) * C::SIDE, &map_wrap, &full[s], 0, sy, sz, 3 * j);
+        }
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumers (warps 0-3) ----------------
+  for (int k = 0; k < nmine; ++k) {
+    const int s = k % C::DI;
+    const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(k / C::DI) & 1u);
+    if (!ok) {
+      // stage never arrived: flag, wait (bounded) for stages still in flight, drain stores, leave
+      if (tid == 0) atomicOr(status, 2);
+      for (int j = k + 1; j < nmine && j < k + C::DI; ++j) mbar_wait_bounded(&full[j % C::DI], (uint32_t)(j / C::DI) & 1u);
+      if (lane == 0) bulk_wait_all();
+      return;
+    }
+    const int4 tc = tile_at[s];
+    const int tx = tc.x, y = tc.y, z = tc.z;
+    const int x = tx * C::BX + tid;
+    const S* st = reinterpret_cast<const S*>(smem + s * C::STAGE);
+    R f[27];
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      f[i] = SCvt<S>::to(st[i * (C::SLOT / (int)sizeof(S)) + C::H + tid - CX(i)]);
+    });
+    if (p.span[0] && (x == 0 || x == p.dim[0] - 1)) {
+      // periodic wrap along x from the side slots
+      const S* side = reinterpret_cast<const S*>(smem + s * C::STAGE + 27 * C::SLOT);
+      const bool lo = x == 0;
+      unroll<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if (lo && CX(i) == 1) f[i] = SCvt<S>::to(side[(i / 3) * (C::SIDE / (int)sizeof(S)) + C::H - 1]);
+        if (!lo && CX(i) == -1) f[i] = SCvt<S>::to(side[(9 + i / 3) * (C::SIDE / (int)sizeof(S))]);
+      });
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with stage s
+    if (x < p.dim[0]) kbc_collide<R, FM>(f, beta, dux, duy, duz, lbgk != 0);
+    // this warp's output segment in stage o: wait until the stores that last
+    // used it have read it, fill it, store it
+    const int o = k % C::DO;
+    if (lane == 0) bulk_wait_read<C::DO - 1>();
+    __syncwarp();
+    unsigned char* seg = ostage + o * C::OSTAGE + warp * 27 * C::OSLOT;
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      Stor<S>::st(reinterpret_cast<S*>(seg + i * C::OSLOT) + lane, f[i]);
+    });
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) {
+      const int xs = tx * C::BX + warp * C::OSEG;
+#pragma unroll
+      for (int i = 0; i < 27; ++i) tma_store_row(&map_out, seg + i * C::OSLOT, xs, y, z, i);
+      bulk_commit();
+    }
+  }
+  if (lane == 0) bulk_wait_all();
+}
+
+// Mixed tiles: node-by-node pull (walls, solids, outlet, interface layers).
+template <typename S, typename R, int FM>
+__global__ void __launch_bounds__(128) k_sc_tiles(PatchDev p, const S* __restrict__ fin, S* __restrict__ fout,
+                                                  const uint32_t* __restrict__ tiles, int ntx, R beta, R dux, R duy,
+                                                  R duz, int odd, int lbgk, int* status) {
+  const uint32_t t = tiles[blockIdx.x];
+  const int x = (int)(t % (uint32_t)ntx) * 128 + threadIdx.x;
+  const int y = (int)((t / (uint32_t)ntx) % (uint32_t)p.dim[1]);
+  const int z = (int)(t / ((uint32_t)ntx * (uint32_t)p.dim[1]));
+  if (x >= p.dim[0]) return;
+  const long long own = node_index(p, x, y, z);
+  const uint8_t ty = p.type[own];
+  if (!(ty == T_BULK || ty == T_BC || (ty == T_D1 && odd))) return;
+  R f[27];
+  if (ty == T_BULK) pull_bulk<S, R>(p, fin, x, y, z, f);
+  else pull_generic<S, R>(p, fin, x, y, z, f, status);
+  kbc_collide<R, FM>(f, beta, dux, duy, duz, lbgk != 0);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    Stor<S>::st(fout + (long long)i * p.plane + own, f[i]);
+  });
+}
+
+template <typename S, typename R, int FM>
+cudaError_t launch_tma_t(const void* tmap_in, const void* tmap_out, const void* tmap_wrap, const PatchDev& p,
+                         const unsigned long long* tiles, int ntiles, R beta, R dux, R duy, R duz, int lbgk,
+                         int* status, cudaStream_t st) {
+  using C = TmaCfg<S>;
+  static int blocks_per_sm = -1, sms = 0;
+  auto kern = k_sc_tma<S, R, FM>;
+  if (blocks_per_sm < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, C::THREADS, C::SMEM);
+    if (e) return e;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const int grid = std::min(ntiles, blocks_per_sm * sms);
+  CUtensorMap mi, mo, mw;
+  memcpy(&mi, tmap_in, sizeof mi);
+  memcpy(&mo, tmap_out, sizeof mo);
+  memcpy(&mw, tmap_wrap, sizeof mw);
+  kern<<<grid, C::THREADS, C::SMEM, st>>>(mi, mo, mw, p, tiles, ntiles, beta, dux, duy, duz, lbgk, status);
+  return cudaGetLastError();
+}
+
+template <typename S, typename R>
+cudaError_t sc_tma_typed(const void* tmap_in, const void* tmap_out, const void* tmap_wrap, const PatchDev& p,
+                         const unsigned long long* tiles, int64_t ntiles, double beta, const Force& F, int lbgk,
+                         int* status, cudaStream_t st) {
+  if (ntiles == 0) return cudaSuccess;
+  const R b = (R)beta, dx = (R)F.du[0], dy = (R)F.du[1], dz = (R)F.du[2];
+  switch (F.mask()) {
+    case 0:
+      return launch_tma_t<S, R, 0>(tmap_in, tmap_out, tmap_wrap, p, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
+    case 1:
+      return launch_tma_t<S, R, 1>(tmap_in, tmap_out, tmap_wrap, p, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
+    case 4:
+      return launch_tma_t<S, R, 4>(tmap_in, tmap_out, tmap_wrap, p, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
+    default:
+      return launch_tma_t<S, R, 7>(tmap_in, tmap_out, tmap_wrap, p, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
+  }
+}
+
+template <typename S, typename R>
+cudaError_t sc_tiles_typed(const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles, int64_t ntiles,
+                           int ntx, double beta, const Force& F, int odd, int lbgk, int* status, cudaStream_t st) {
+  if (ntiles == 0) return cudaSuccess;
+  const R b = (R)beta, dx = (R)F.du[0], dy = (R)F.du[1], dz = (R)F.du[2];
+  const dim3 grid((unsigned)ntiles), block(128);
+  const S* in = (const S*)fin;
+  S* out = (S*)fout;
+  switch (F.mask()) {
+    case 0:
+      k_sc_tiles<S, R, 0><<<grid, block, 0, st>>>(p, in, out, tiles, ntx, b, dx, dy, dz, odd, lbgk, status);
+      break;
+    case 1:
+      k_sc_tiles<S, R, 1><<<grid, block, 0, st>>>(p, in, out, tiles, ntx, b, dx, dy, dz, odd, lbgk, status);
+      break;
+    case 4:
+      k_sc_tiles<S, R, 4><<<grid, block, 0, st>>>(p, in, out, tiles, ntx, b, dx, dy, dz, odd, lbgk, status);
+      break;
+    default:
+      k_sc_tiles<S, R, 7><<<grid, block, 0, st>>>(p, in, out, tiles, ntx, b, dx, dy, dz, odd, lbgk, status);
+  }
+  return cudaGetLastError();
+}
+
+// per-storage entry points, one translation unit each
+#define LBM_SC_DECL(NAME)                                                                                        \
+  cudaError_t sc_tma_##NAME(const void* tmap_in, const void* tmap_out, const void* tmap_wrap, const PatchDev& p, \
+                            const unsigned long long* tiles, int64_t ntiles, double beta, const Force& F,        \
+                            int lbgk, int* status, cudaStream_t st);                                             \
+  cudaError_t sc_tiles_##NAME(const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,             \
+                              int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk,           \
+                              int* status, cudaStream_t st);
+LBM_SC_DECL(fp64)
+LBM_SC_DECL(fp32)
+LBM_SC_DECL(fp16)
+LBM_SC_DECL(bf16)
+
+#define LBM_SC_DEFINE(NAME, S, R)                                                                                \
+  cudaError_t sc_tma_##NAME(const void* tmap_in, const void* tmap_out, const void* tmap_wrap, const PatchDev& p, \
+                            const unsigned long long* tiles, int64_t ntiles, double beta, const Force& F,        \
+                            int lbgk, int* status, cudaStream_t st) {                                            \
+    return sc_tma_typed<S, R>(tmap_in, tmap_out, tmap_wrap, p, tiles, ntiles, beta, F, lbgk, status, st);        \
+  }                                                                                                              \
+  cudaError_t sc_tiles_##NAME(const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,             \
+                              int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk,           \
+                              int* status, cudaStream_t st) {                                                    \
+    return sc_tiles_typed<S, R>(p, fin, fout, tiles, ntiles, ntx, beta, F, odd, lbgk, status, st);               \
+  }
+
+}  // namespace lbmk

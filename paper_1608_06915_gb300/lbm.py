@@ -1,0 +1,326 @@
+"""Thin ctypes binding of liblbm.so (the C ABI declared in include/lbm.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides the device memory (one uint8 buffer per grid)
+and the CUDA stream.  If the library is missing the import fails loudly;
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbm.so")
+
+LBM_OK = 0
+STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_LAYOUT", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_OOM",
+          -5: "LBM_ERR_UNSTABLE", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_STATE"}
+STORAGE = {"fp64": 0, "fp32": 1, "fp16s": 2, "bf16s": 3}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class lbm_box(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("lo", ctypes.c_int32 * 3), ("hi", ctypes.c_int32 * 3)]
+
+
+class lbm_desc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32 * 3),
+        ("periodic", ctypes.c_uint32),
+        ("walls", ctypes.c_uint32),
+        ("inflow_axis", ctypes.c_int32),
+        ("u_in", ctypes.c_double * 3),
+        ("boxes", ctypes.POINTER(lbm_box)),
+        ("n_boxes", ctypes.c_int32),
+        ("solid", ctypes.POINTER(ctypes.c_uint8)),
+        ("solid_level", ctypes.c_int32),
+        ("solid_lo", ctypes.c_int32 * 3),
+        ("solid_dims", ctypes.c_int32 * 3),
+        ("nu0", ctypes.c_double),
+        ("accel0", ctypes.c_double * 3),
+        ("model", ctypes.c_int32),
+        ("pr", ctypes.c_double),
+        ("t0", ctypes.c_double),
+        ("glambda", ctypes.c_double),
+        ("t_ref", ctypes.c_double),
+        ("wall_T", ctypes.c_double * 6),
+        ("storage", ctypes.c_int32),
+        ("mirror_lbgk", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load liblbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("liblbm.so not built: run __graft_entry__.build() (no fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "lbm_grid_create": [ctypes.POINTER(lbm_desc), ctypes.POINTER(vp)],
+            "lbm_grid_bytes": [vp, ctypes.POINTER(ctypes.c_size_t)],
+            "lbm_grid_bind": [vp, vp, ctypes.c_size_t, vp],
+            "lbm_grid_destroy": [vp],
+            "lbm_num_patches": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+            "lbm_patch_info": [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64),
+                               ctypes.POINTER(i64), dp, dp],
+            "lbm_patch_mask": [vp, i32, ctypes.POINTER(ctypes.c_uint8)],
+            "lbm_node_updates": [vp, dp],
+            "lbm_init_equilibrium": [vp, i32, vp, vp, vp, i32],
+            "lbm_step": [vp, i64],
+            "lbm_moments": [vp, i32, vp, vp, vp, vp, i32],
+            "lbm_get_populations": [vp, i32, i32, vp, i32],
+            "lbm_set_populations": [vp, i32, i32, vp, i32],
+            "lbm_force": [vp, dp, dp],
+            "lbm_diagnostics": [vp, dp],
+            "lbm_checkpoint_bytes": [vp, ctypes.POINTER(ctypes.c_size_t)],
+            "lbm_checkpoint": [vp, vp, i32],
+            "lbm_collide_nodes": [vp, vp, vp, i64, ctypes.c_double, dp, i32, i32, vp],
+            "lbm_timing": [vp, i32],
+            "lbm_timing_report": [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                  ctypes.POINTER(i64), dp, dp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.lbm_last_error.argtypes = [vp]
+        L.lbm_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, handle=None) -> None:
+    if rc != LBM_OK:
+        msg = lib().lbm_last_error(handle)
+        raise LbmError(rc, msg.decode() if msg else "")
+
+
+def make_desc(case: dict, storage: str = "fp32"):
+    """lbm_desc from a case dictionary (see paper_1608_06915_gb300.inputs).
+    Returns (desc, keepalive) -- keepalive holds the host arrays it points to."""
+    d = lbm_desc()
+    d.n[:] = [int(v) for v in case["n"]]
+    d.periodic = sum((1 << a) for a in range(3) if case.get("periodic", (1, 1, 1))[a])
+    d.walls = sum((1 << k) for k, w in enumerate(case.get("walls", (0,) * 6)) if w)
+    d.inflow_axis = int(case.get("inflow_axis", -1))
+    d.u_in[:] = [float(v) for v in case.get("u_in", (0, 0, 0))]
+    boxes = case.get("boxes", [])
+    barr = (lbm_box * max(1, len(boxes)))()
+    for k, (lev, lo, hi) in enumerate(boxes):
+        barr[k].level = int(lev)
+        barr[k].lo[:] = [int(v) for v in lo]
+        barr[k].hi[:] = [int(v) for v in hi]
+    d.boxes = barr
+    d.n_boxes = len(boxes)
+    keep = [barr]
+    solid = case.get("solid")
+    if solid is not None:
+        m = np.ascontiguousarray(solid["mask"], dtype=np.uint8)
+        keep.append(m)
+        d.solid = m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        d.solid_level = int(solid["level"])
+        d.solid_lo[:] = [int(v) for v in solid["lo"]]
+        d.solid_dims[:] = [int(m.shape[2]), int(m.shape[1]), int(m.shape[0])]
+    else:
+        d.solid_level = -1
+    d.nu0 = float(case["nu0"])
+    d.accel0[:] = [float(v) for v in case.get("accel0", (0, 0, 0))]
+    th = case.get("thermal")
+    d.model = 1 if th is not None else 0
+    d.t0 = 1.0 / 3.0
+    if th is not None:
+        d.pr, d.t0, d.glambda, d.t_ref = float(th["pr"]), float(th.get("t0", 1 / 3)), float(th["glambda"]), \
+            float(th["t_ref"])
+        d.wall_T[:] = [float(v) for v in th["wall_T"]]
+    d.storage = STORAGE[storage]
+    d.mirror_lbgk = int(bool(case.get("mirror_lbgk", False)))
+    return d, keep
+
+
+def lbm_grid_create(case: dict, storage: str = "fp32") -> ctypes.c_void_p:
+    d, keep = make_desc(case, storage)
+    h = ctypes.c_void_p()
+    _check(lib().lbm_grid_create(ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+class Grid:
+    """A refined grid bound to torch-owned device memory on the current stream."""
+
+    def __init__(self, case: dict, storage: str = "fp32", device=None, bind: bool = True):
+        self.case = case
+        self.storage = storage
+        self.handle = lbm_grid_create(case, storage)
+        L = lib()
+        n, nl = ctypes.c_int32(), ctypes.c_int32()
+        L.lbm_num_patches(self.handle, ctypes.byref(n), ctypes.byref(nl))
+        self.n_levels = nl.value
+        self.patches = []
+        for p in range(n.value):
+            lev, par = ctypes.c_int32(), ctypes.c_int32()
+            org, dim = (ctypes.c_int64 * 3)(), (ctypes.c_int64 * 3)()
+            b, b1 = ctypes.c_double(), ctypes.c_double()
+            _check(L.lbm_patch_info(self.handle, p, ctypes.byref(lev), ctypes.byref(par), org, dim,
+                                    ctypes.byref(b), ctypes.byref(b1)), self.handle)
+            self.patches.append(dict(level=lev.value, parent=par.value, org=tuple(org), dim=tuple(dim),
+                                     beta=b.value, beta1=b1.value))
+        nb = ctypes.c_size_t()
+        L.lbm_grid_bytes(self.handle, ctypes.byref(nb))
+        self.device_bytes = nb.value
+        self.buffer = None
+        if bind:
+            self.bind(device)
+
+    def bind(self, device=None):
+        import torch
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.buffer = torch.empty(self.device_bytes, dtype=torch.uint8, device=dev)
+        self.stream = torch.cuda.current_stream(dev)
+        _check(lib().lbm_grid_bind(self.handle, ctypes.c_void_p(self.buffer.data_ptr()), self.device_bytes,
+                                   ctypes.c_void_p(self.stream.cuda_stream)), self.handle)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.lbm_grid_destroy(h)
+            self.handle = None
+
+    # ---- host-side queries
+    def shape(self, p: int):
+        dx, dy, dz = self.patches[p]["dim"]
+        return (dz, dy, dx)
+
+    def mask(self, p: int) -> np.ndarray:
+        out = np.empty(self.shape(p), dtype=np.uint8)
+        _check(lib().lbm_patch_mask(self.handle, p, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))),
+               self.handle)
+        return out
+
+    def node_updates(self) -> float:
+        v = ctypes.c_double()
+        _check(lib().lbm_node_updates(self.handle, ctypes.byref(v)), self.handle)
+        return v.value
+
+    # ---- device calls
+    @staticmethod
+    def _ptr(t):
+        return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+    def _need(self, t, shape, what):
+        if t is None:
+            return
+        if tuple(t.shape) != tuple(shape) or not t.is_cuda:
+            raise ValueError("%s: expected a CUDA tensor of shape %s, got %s" % (what, shape, tuple(t.shape)))
+
+    def init_equilibrium(self, p: int, rho, u, T=None):
+        import torch
+        shp = self.shape(p)
+        self._need(rho, shp, "rho")
+        self._need(u, (3,) + shp, "u")
+        self._need(T, shp, "T")
+        dt = torch.float64 if rho.dtype == torch.float64 else torch.float32
+        rho = rho.to(dtype=dt).contiguous()
+        u = u.to(dtype=dt).contiguous()
+        T = None if T is None else T.to(dtype=dt).contiguous()
+        self._keep = (rho, u, T)
+        _check(lib().lbm_init_equilibrium(self.handle, p, self._ptr(rho), self._ptr(u), self._ptr(T),
+                                          1 if dt == torch.float64 else 0), self.handle)
+
+    def step(self, n: int = 1):
+        _check(lib().lbm_step(self.handle, int(n)), self.handle)
+
+    def moments(self, p: int, dtype=None, gamma: bool = False):
+        import torch
+        dtype = dtype or torch.float64
+        shp = self.shape(p)
+        dev = self.buffer.device
+        rho = torch.empty(shp, dtype=dtype, device=dev)
+        u = torch.empty((3,) + shp, dtype=dtype, device=dev)
+        T = torch.empty(shp, dtype=dtype, device=dev)
+        g = torch.empty(shp, dtype=dtype, device=dev) if gamma else None
+        _check(lib().lbm_moments(self.handle, p, self._ptr(rho), self._ptr(u), self._ptr(T), self._ptr(g),
+                                 1 if dtype == torch.float64 else 0), self.handle)
+        return rho, u, T, g
+
+    def get_populations(self, p: int, which: int = 0, dtype=None):
+        import torch
+        dtype = dtype or torch.float64
+        out = torch.empty((27,) + self.shape(p), dtype=dtype, device=self.buffer.device)
+        _check(lib().lbm_get_populations(self.handle, p, which, self._ptr(out), 1 if dtype == torch.float64 else 0),
+               self.handle)
+        return out
+
+    def set_populations(self, p: int, src, which: int = 0):
+        import torch
+        self._need(src, (27,) + self.shape(p), "populations")
+        if src.dtype not in (torch.float32, torch.float64):
+            raise ValueError("populations must be float32 or float64")
+        src = src.contiguous()
+        _check(lib().lbm_set_populations(self.handle, p, which, self._ptr(src),
+                                         1 if src.dtype == torch.float64 else 0), self.handle)
+        self._keep = src
+
+    def diagnostics(self):
+        out = (ctypes.c_double * 8)()
+        rc = lib().lbm_diagnostics(self.handle, out)
+        vals = list(out)
+        if rc != LBM_OK:
+            raise LbmError(rc, lib().lbm_last_error(self.handle).decode())
+        return dict(mass=vals[0], momentum=vals[1:4], kinetic_energy=vals[4], fluid_nodes=vals[5],
+                    min_rho=vals[6], status=int(vals[7]))
+
+    def set_force(self, accel0):
+        a = (ctypes.c_double * 3)(*[float(v) for v in accel0])
+        _check(lib().lbm_force(self.handle, a, None), self.handle)
+
+    def timing(self, enable: bool):
+        _check(lib().lbm_timing(self.handle, 1 if enable else 0), self.handle)
+
+    def timing_report(self):
+        """Per kernel class: dict(kind, level, launches, ms, nodes)."""
+        m = 64
+        n = ctypes.c_int32()
+        kind, lev = (ctypes.c_int32 * m)(), (ctypes.c_int32 * m)()
+        cnt, ms, nodes = (ctypes.c_int64 * m)(), (ctypes.c_double * m)(), (ctypes.c_double * m)()
+        _check(lib().lbm_timing_report(self.handle, m, ctypes.byref(n), kind, lev, cnt, ms, nodes), self.handle)
+        names = {0: "stream_collide", 1: "coalesce", 2: "samples", 3: "explode"}
+        return [dict(kind=names[kind[k]], level=lev[k], launches=cnt[k], ms=ms[k], nodes=nodes[k])
+                for k in range(min(n.value, m))]
+
+    def checkpoint_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().lbm_checkpoint_bytes(self.handle, ctypes.byref(n)), self.handle)
+        return n.value
+
+    def checkpoint(self, buf, save: bool):
+        _check(lib().lbm_checkpoint(self.handle, self._ptr(buf), 1 if save else 0), self.handle)
+
+
+def lbm_collide_nodes(f_in, beta: float, du=(0.0, 0.0, 0.0), lbgk: bool = False):
+    """One KBC collision of n independent nodes, f_in a CUDA tensor [27, n]."""
+    import torch
+    f_in = f_in.contiguous()
+    n = f_in.shape[1]
+    f_out = torch.empty_like(f_in)
+    gam = torch.empty(n, dtype=f_in.dtype, device=f_in.device)
+    d = (ctypes.c_double * 3)(*[float(v) for v in du])
+    rc = lib().lbm_collide_nodes(ctypes.c_void_p(f_in.data_ptr()), ctypes.c_void_p(f_out.data_ptr()),
+                                 ctypes.c_void_p(gam.data_ptr()), n, float(beta), d, int(lbgk),
+                                 1 if f_in.dtype == torch.float64 else 0,
+                                 ctypes.c_void_p(torch.cuda.current_stream(f_in.device).cuda_stream))
+    if rc != LBM_OK:
+        raise LbmError(rc, "lbm_collide_nodes")
+    return f_out, gam
