@@ -190,26 +190,30 @@ class Clocks:
 
 
 def source_hash():
+    """Hash of the sources of the stream-collide kernels (profiles record it)."""
     h = hashlib.sha256()
-    for f in ("device.cuh", "kernels.cu"):
+    for f in ("device.cuh", "sc_tma.cuh", "sc_tma.cu", "sc_tma_fp32.cu", "kernels.cu"):
         with open(os.path.join(ROOT, "paper_1608_06915_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_name, workload_name, storage):
-    """DRAM bytes per launch recorded in profiles/ for this kernel source, else None."""
-    path = os.path.join(ROOT, "profiles", "%s_%s_%s.md" % (kernel_name, workload_name, storage))
+def ncu_traffic(kernel_name, storage, nodes_per_launch):
+    """DRAM bytes (read + write) per launch from the ncu summary in profiles/:
+    the per-node traffic of the captured (smaller) case scaled by the nodes of
+    one launch here; None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel_name, storage))
     if not os.path.exists(path):
         return None
-    want = source_hash()
-    traffic, srch = None, None
+    per_node, srch = None, None
     for line in open(path):
         if line.startswith("source_hash:"):
             srch = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_launch:"):
-            traffic = float(line.split(":", 1)[1].strip())
-    return traffic if srch == want else None
+        if line.startswith("dram_bytes_per_node:"):
+            per_node = float(line.split(":", 1)[1].strip())
+    if per_node is None or srch != source_hash():
+        return None
+    return per_node * nodes_per_launch
 
 
 def end_to_end(args, g, L, host_fields, dfields, nup, world, barrier, dev):
@@ -315,7 +319,8 @@ def cuda_arm(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
-    traffic = ncu_traffic("k_stream_collide", args.workload, args.storage)
+    traffic = ncu_traffic("k_sc_tma_channel", args.storage, nodes_per_launch) if args.workload.startswith(
+        "channel") else None
     roofline = dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=traffic,
                     peak_source="measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                     kernel="k_stream_collide level %d" % top["level"] if top["kind"] == "stream_collide"
