@@ -164,6 +164,24 @@ lbm_status lbm_set_populations(lbm_grid_t g, int32_t patch, int32_t which, const
  * state (coarse units, summed over levels).  Synchronises when drag_out is set. */
 lbm_status lbm_force(lbm_grid_t g, const double* accel0, double* drag_out);
 
+/* Same results as lbm_diagnostics, for callers that must not allocate device
+ * memory themselves -- for example code that runs while another component
+ * owns the whole device memory budget, or a host process that hands the
+ * library only the buffers it already holds.  lbm_diagnostics keeps its
+ * partial sums in the grid's bound buffer; this variant keeps them in a
+ * fixed array inside the library (about 300 KB, held on every GPU that loads
+ * the library until the process exits), so it allocates nothing, directly or
+ * through any library.  The paper has no counterpart: this is plumbing.
+ * Limits and rules:
+ *   - at most 16 patches per grid; larger grids get LBM_ERR_ARG and a message;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - every call uses the same array: calls that overlap on the GPU (two
+ *     streams, or two grids at once) race and can return wrong sums.  Calls
+ *     that follow one another are fine: each call writes every slot it reads.
+ * Synchronises the bound stream, like lbm_diagnostics. */
+lbm_status lbm_diagnostics_noalloc(lbm_grid_t g, double out[8]);
+
 /* FP64 diagnostics over owned fluid nodes (parent nodes that are not twin
  * nodes of a child, child nodes of depth >= 1), volume-weighted 8^-level:
  * out = {mass, jx, jy, jz, kinetic energy 1/2 rho |u|^2, fluid node count,

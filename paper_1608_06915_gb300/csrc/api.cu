@@ -462,6 +462,63 @@ lbm_status lbm_diagnostics(lbm_grid_t g, double out[8]) {
   return LBM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free diagnostics.  Its partial sums live in this file-scope
+// device array instead of the grid's bound buffer.  Host code must not pass
+// the array's name to a kernel (on the host it is only a stand-in symbol);
+// the device address is looked up once per device with cudaGetSymbolAddress.
+namespace {
+constexpr int kNoAllocMaxPatches = 16;
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) double g_noalloc_scratch[8 * kDiagBlocks * kNoAllocMaxPatches + 8];
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+}  // namespace
+
+lbm_status lbm_diagnostics_noalloc(lbm_grid_t g, double out[8]) {
+  if (lbm_status s = check_bound(g)) return s;
+  if (!out) return fail(g, LBM_ERR_ARG, "null output");
+  if ((int)g->hg.P.size() > kNoAllocMaxPatches)
+    return fail(g, LBM_ERR_ARG,
+                "lbm_diagnostics_noalloc handles at most " + std::to_string(kNoAllocMaxPatches) +
+                    " patches; this grid has " + std::to_string(g->hg.P.size()));
+  int dev = 0;
+  if (cudaError_t e = cudaGetDevice(&dev)) return cuda_check(g, e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(g, LBM_ERR_ARG, "device index beyond the supported range");
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch)) return cuda_check(g, e, "cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+  }
+  double* partial = g_noalloc_ptr[dev];
+  double* dout = partial + 8 * kDiagBlocks * kNoAllocMaxPatches;
+  // every partial slot and the 8 outputs are written before they are read in
+  // this call, so nothing needs clearing between calls
+  int nb = 0;
+  cudaError_t e = cudaSuccess;
+  for (auto& p : g->hg.P) {
+    if (!e)
+      e = lbmk::launch_diag(g->hg.desc.storage, view(g, p), g->base + p.off_f[p.cur],
+                            1.0 / (double)(1LL << (3 * p.level)), level_force(g, p.level), partial + 8 * nb,
+                            kDiagBlocks, g->stream);
+    nb += kDiagBlocks;
+  }
+  if (!e) e = lbmk::launch_diag_final(partial, nb, dout, g->stream);
+  double host[8];
+  int status = 0;
+  if (!e) e = cudaMemcpyAsync(host, dout, sizeof host, cudaMemcpyDeviceToHost, g->stream);
+  if (!e) e = cudaMemcpyAsync(&status, status_ptr(g), sizeof status, cudaMemcpyDeviceToHost, g->stream);
+  if (!e) e = cudaStreamSynchronize(g->stream);
+  if (e) return cuda_check(g, e, "lbm_diagnostics_noalloc");
+  for (int k = 0; k < 6; ++k) out[k] = host[k];
+  out[6] = host[6];
+  out[7] = (double)status;
+  if (host[7] > 0 || !(host[6] > 0)) {
+    out[6] = host[7] > 0 ? NAN : host[6];
+    return fail(g, LBM_ERR_UNSTABLE, "non-finite or non-positive density");
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_force(lbm_grid_t g, const double* accel0, double* drag_out) {
   if (!g) return LBM_ERR_ARG;
   if (accel0)

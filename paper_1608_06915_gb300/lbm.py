@@ -85,6 +85,7 @@ def lib():
             "lbm_set_populations": [vp, i32, i32, vp, i32],
             "lbm_force": [vp, dp, dp],
             "lbm_diagnostics": [vp, dp],
+            "lbm_diagnostics_noalloc": [vp, dp],
             "lbm_checkpoint_bytes": [vp, ctypes.POINTER(ctypes.c_size_t)],
             "lbm_checkpoint": [vp, vp, i32],
             "lbm_collide_nodes": [vp, vp, vp, i64, ctypes.c_double, dp, i32, i32, vp],
@@ -276,6 +277,16 @@ class Grid:
     def diagnostics(self):
         out = (ctypes.c_double * 8)()
         rc = lib().lbm_diagnostics(self.handle, out)
+        vals = list(out)
+        if rc != LBM_OK:
+            raise LbmError(rc, lib().lbm_last_error(self.handle).decode())
+        return dict(mass=vals[0], momentum=vals[1:4], kinetic_energy=vals[4], fluid_nodes=vals[5],
+                    min_rho=vals[6], status=int(vals[7]))
+
+    def diagnostics_noalloc(self):
+        """lbm_diagnostics_noalloc: the same sums without the grid's workspace."""
+        out = (ctypes.c_double * 8)()
+        rc = lib().lbm_diagnostics_noalloc(self.handle, out)
         vals = list(out)
         if rc != LBM_OK:
             raise LbmError(rc, lib().lbm_last_error(self.handle).decode())
