@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
-    ap.add_argument("--workload", choices=["channel", "channel-half", "tgv", "sphere"], default="channel")
+    ap.add_argument("--workload", choices=["channel", "channel-half", "tgv", "sphere", "rbc"], default="channel")
     ap.add_argument("--storage", choices=sorted(BYTES_PER_UPDATE), default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -66,6 +66,13 @@ def workload(name):
             x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
             return I.uniform_fields(x, (0.05, 0.0, 0.0))
         return case, fields, "sphere wake 384x192x192 coarse, 4 levels, D=64 finest nodes, Re=3700"
+    if name == "rbc":
+        case = I.rbc_case()
+
+        def fields(info):
+            return I.rbc_fields(case, info["level"], info["org"], info["dim"])
+        return case, fields, ("Rayleigh-Benard 256x256x128 coarse, 3 levels (2x z in [0,12],[115,127]; 4x z in "
+                              "[0,6],[121,127]), Ra=1e7, Pr=0.7, thermal f+g")
     case = I.tgv_case()
 
     def fields(info):
@@ -84,6 +91,12 @@ def sample_case(name):
         def fields(info):
             return I.channel_fields(case, info["level"], info["org"], info["dim"])
         return case, fields, "channel 16x64x8 coarse (x/z extents of the 256x64x128 case reduced), same bands"
+    if name == "rbc":
+        case = I.rbc_small_case()
+
+        def fields(info):
+            return I.rbc_fields(case, info["level"], info["org"], info["dim"])
+        return case, fields, "Rayleigh-Benard 8x8x32 coarse, same layering, Ra=1e5"
     if name == "sphere":
         case = I.sphere_case(scale=8)
 
@@ -272,13 +285,15 @@ def cuda_arm(args):
 
     case, fields, desc = workload(args.workload)
     g = L.Grid(case, args.storage, device=dev)
-    host_fields = [fields(info) for info in g.patches]
+    host_all = [fields(info) for info in g.patches]
+    host_fields = [(h[0], h[1]) for h in host_all]
     dfields = []
-    for p, (rho, u) in enumerate(host_fields):
-        dr = torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float32)).to(dev)
-        du = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).to(dev)
+    for p, h in enumerate(host_all):
+        dr = torch.from_numpy(np.ascontiguousarray(h[0], dtype=np.float32)).to(dev)
+        du = torch.from_numpy(np.ascontiguousarray(h[1], dtype=np.float32)).to(dev)
+        dT = torch.from_numpy(np.ascontiguousarray(h[2], dtype=np.float32)).to(dev) if len(h) > 2 else None
         dfields.append((dr, du))
-        g.init_equilibrium(p, dr, du)
+        g.init_equilibrium(p, dr, du, dT)
     nup = g.node_updates()
     stream = g.stream
 
@@ -311,7 +326,7 @@ def cuda_arm(args):
 
     # dominant kernel: the class with the largest device time
     top = max(report, key=lambda r: r["ms"])
-    bpu = BYTES_PER_UPDATE[args.storage]
+    bpu = BYTES_PER_UPDATE[args.storage] * (2 if case.get("thermal") else 1)
     avg_ms = top["ms"] / top["launches"]
     nodes_per_launch = top["nodes"] / top["launches"]
     alg_bytes = nodes_per_launch * bpu
@@ -330,7 +345,7 @@ def cuda_arm(args):
     launches = sum(r["launches"] for r in report)
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not case.get("thermal"):
         e2e = end_to_end(args, g, L, host_fields, dfields, nup, world, barrier, dev)
 
     cpu = None

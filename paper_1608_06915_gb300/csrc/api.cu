@@ -97,6 +97,18 @@ lbmk::Force level_force(const lbm_grid* g, int level) {
 
 int* status_ptr(const lbm_grid* g) { return at<int>(g, g->off_status); }
 
+lbmk::ThermalLevel thermal_level(const lbm_grid* g, const HostPatch& p) {
+  lbmk::ThermalLevel L{};
+  const lbm_desc& d = g->hg.desc;
+  for (int k = 0; k < 6; ++k) L.twd[k] = d.wall_T[k] - d.t0;
+  L.glam = d.glambda / (double)(1LL << p.level);  // du_f = du_c / r per level
+  L.tref_d = d.t_ref - d.t0;
+  L.beta = p.beta;
+  L.beta1 = p.beta1;
+  L.lbgk = d.mirror_lbgk;
+  return L;
+}
+
 cudaEvent_t next_event(lbm_grid* g) {
   if (g->pool_used == g->pool.size()) {
     cudaEvent_t e;
@@ -154,24 +166,53 @@ lbm_status run_instant(lbm_grid* g, int k) {
       void* fin = g->base + p.off_f[p.cur];
       void* fout = g->base + p.off_f[1 - p.cur];
       const int odd = (lev > 0 && !parent_active) ? 1 : 0;
-      lbm_status st = cuda_check(
-          g,
-          timed(g, 0, lev, g->timing ? count_types(p, odd) : 0.0,
-                [&] {
-                  cudaError_t e = lbmk::launch_sc_tma(storage, p.tmap[p.cur], p.tmapo[1 - p.cur], p.tmapw[p.cur],
-                                                      pv, at<unsigned long long>(g, p.off_tiles_pure[odd]),
-                                                      (int64_t)p.tiles_pure[odd].size(), p.beta, F, lbgk,
-                                                      status_ptr(g), g->stream);
-                  if (e) return e;
-                  return lbmk::launch_sc_tiles(storage, pv, fin, fout, at<uint32_t>(g, p.off_tiles_mixed[odd]),
-                                               (int64_t)p.tiles_mixed[odd].size(), (int)p.ntx, p.beta, F, odd,
-                                               lbgk, status_ptr(g), g->stream);
-                }),
-          "stream_collide");
+      lbm_status st;
+      if (hg.thermal) {
+        st = cuda_check(g,
+                        timed(g, 0, lev, g->timing ? count_types(p, odd) : 0.0,
+                              [&] {
+                                return lbmk::launch_th_tiles(storage, pv, fin, g->base + p.off_g[p.cur], fout,
+                                                             g->base + p.off_g[1 - p.cur],
+                                                             at<uint32_t>(g, p.off_tiles_all[odd]),
+                                                             (int64_t)p.tiles_all[odd].size(), (int)p.ntx,
+                                                             thermal_level(g, p), odd, status_ptr(g), g->stream);
+                              }),
+                        "thermal stream_collide");
+      } else {
+        st = cuda_check(
+            g,
+            timed(g, 0, lev, g->timing ? count_types(p, odd) : 0.0,
+                  [&] {
+                    cudaError_t e = lbmk::launch_sc_tma(storage, p.tmap[p.cur], p.tmapo[1 - p.cur], p.tmapw[p.cur],
+                                                        pv, at<unsigned long long>(g, p.off_tiles_pure[odd]),
+                                                        (int64_t)p.tiles_pure[odd].size(), p.beta, F, lbgk,
+                                                        status_ptr(g), g->stream);
+                    if (e) return e;
+                    return lbmk::launch_sc_tiles(storage, pv, fin, fout, at<uint32_t>(g, p.off_tiles_mixed[odd]),
+                                                 (int64_t)p.tiles_mixed[odd].size(), (int)p.ntx, p.beta, F, odd,
+                                                 lbgk, status_ptr(g), g->stream);
+                  }),
+            "stream_collide");
+      }
       if (st) return st;
       for (int ci : p.kids) {
         HostPatch& c = hg.P[ci];
         const lbmk::PatchDev cv = view(g, c);
+        if (hg.thermal) {
+          st = cuda_check(g,
+                          timed(g, 1, lev, (double)c.cf_parent.size(),
+                                [&] {
+                                  return lbmk::launch_th_coalesce(
+                                      storage, cv, g->base + c.off_f[c.cur], g->base + c.off_g[c.cur], pv, fout,
+                                      g->base + p.off_g[1 - p.cur], at<uint32_t>(g, c.off_cf_parent),
+                                      at<uint32_t>(g, c.off_cf_child), (int64_t)c.cf_parent.size(),
+                                      2.0 * c.beta / p.beta, 2.0 * c.beta1 / p.beta1, thermal_level(g, c),
+                                      thermal_level(g, p), status_ptr(g), g->stream);
+                                }),
+                          "thermal coalesce");
+          if (st) return st;
+          continue;
+        }
         st = cuda_check(g,
                         timed(g, 1, lev, (double)c.cf_parent.size(),
                               [&] {
@@ -184,7 +225,34 @@ lbm_status run_instant(lbm_grid* g, int k) {
                         "coalesce");
         if (st) return st;
       }
-      if (lev > 0 && parent_active) {
+      if (lev > 0 && parent_active && hg.thermal) {
+        HostPatch& q = hg.P[p.parent];
+        const lbmk::PatchDev qv = view(g, q);
+        st = cuda_check(g,
+                        timed(g, 2, lev, (double)p.smp_node.size(),
+                              [&] {
+                                return lbmk::launch_th_samples(
+                                    storage, qv, g->base + q.off_f[q.cur], g->base + q.off_g[q.cur], pv, fin,
+                                    g->base + p.off_g[p.cur], at<uint32_t>(g, p.off_smp_node),
+                                    at<uint8_t>(g, p.off_smp_kind), (int64_t)p.smp_node.size(),
+                                    g->base + p.off_smp_val, q.beta / (2.0 * p.beta), q.beta1 / (2.0 * p.beta1),
+                                    thermal_level(g, q), thermal_level(g, p), status_ptr(g), g->stream);
+                              }),
+                        "thermal samples");
+        if (st) return st;
+        st = cuda_check(g,
+                        timed(g, 3, lev, (double)p.ex_node.size(),
+                              [&] {
+                                return lbmk::launch_th_explode(
+                                    storage, pv, fout, g->base + p.off_g[1 - p.cur], at<uint32_t>(g, p.off_ex_node),
+                                    at<uint32_t>(g, p.off_ex_first), at<uint8_t>(g, p.off_ex_mask),
+                                    at<uint32_t>(g, p.off_ex_sample), (int64_t)p.ex_node.size(),
+                                    g->base + p.off_smp_val, (int64_t)p.smp_node.size(), thermal_level(g, p),
+                                    g->stream);
+                              }),
+                        "thermal explode");
+        if (st) return st;
+      } else if (lev > 0 && parent_active) {
         HostPatch& q = hg.P[p.parent];
         const lbmk::PatchDev qv = view(g, q);
         st = cuda_check(g,
@@ -225,7 +293,13 @@ lbm_status lbm_grid_create(const lbm_desc* desc, lbm_grid_t* out) {
   if (!desc || !out) return fail(nullptr, LBM_ERR_ARG, "null argument");
   *out = nullptr;
   if (desc->storage < LBM_FP64 || desc->storage > LBM_BF16_SHIFT) return fail(nullptr, LBM_ERR_ARG, "bad storage");
-  if (desc->model != LBM_ISO_KBC) return fail(nullptr, LBM_ERR_ARG, "model not available in this build");
+  if (desc->model != LBM_ISO_KBC && desc->model != LBM_THERMAL_KBC) return fail(nullptr, LBM_ERR_ARG, "unknown model");
+  if (desc->model == LBM_THERMAL_KBC) {
+    if (desc->storage != LBM_FP32 && desc->storage != LBM_FP64)
+      return fail(nullptr, LBM_ERR_ARG, "thermal model: FP32 or FP64 storage");
+    if (desc->t0 < 1.0 / 3.0 - 1e-12 || desc->t0 > 1.0 / 3.0 + 1e-12)
+      return fail(nullptr, LBM_ERR_ARG, "thermal model implemented for T0 = 1/3");
+  }
   if (desc->n_boxes < 0 || (desc->n_boxes > 0 && !desc->boxes)) return fail(nullptr, LBM_ERR_ARG, "bad boxes");
   lbm_grid* g = new lbm_grid();
   HostGrid& hg = g->hg;
@@ -306,8 +380,10 @@ lbm_status lbm_grid_bind(lbm_grid_t g, void* dev_ptr, size_t bytes, void* cuda_s
     if (!e) e = up(p.off_cf_child, p.cf_child.data(), 4 * p.cf_child.size());
     for (int k = 0; k < 2; ++k)
       if (!e) e = up(p.off_tiles_pure[k], p.tiles_pure[k].data(), 8 * p.tiles_pure[k].size());
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
       if (!e) e = up(p.off_tiles_mixed[k], p.tiles_mixed[k].data(), 4 * p.tiles_mixed[k].size());
+      if (!e) e = up(p.off_tiles_all[k], p.tiles_all[k].data(), 4 * p.tiles_all[k].size());
+    }
     p.cur = 0;
   }
   for (auto& p : g->hg.P)
@@ -377,8 +453,14 @@ lbm_status lbm_init_equilibrium(lbm_grid_t g, int32_t patch, const void* rho, co
   if (lbm_status s = check_patch(g, patch)) return s;
   if (lbm_status s = check_bound(g)) return s;
   if (!rho || !u || (dtype != 0 && dtype != 1)) return fail(g, LBM_ERR_ARG, "bad rho/u/dtype");
-  (void)T;
   HostPatch& p = g->hg.P[patch];
+  if (g->hg.thermal)
+    return cuda_check(g,
+                      lbmk::launch_th_init(g->hg.desc.storage, view(g, p), g->base + p.off_f[0], g->base + p.off_f[1],
+                                           g->base + p.off_g[0], g->base + p.off_g[1], rho, u, T, dtype,
+                                           g->hg.desc.u_in, g->stream),
+                      "lbm_init_equilibrium");
+  (void)T;
   return cuda_check(g,
                     lbmk::launch_init(g->hg.desc.storage, view(g, p), g->base + p.off_f[0], g->base + p.off_f[1],
                                       rho, u, dtype, g->hg.desc.u_in, g->stream),
@@ -399,8 +481,14 @@ lbm_status lbm_moments(lbm_grid_t g, int32_t patch, void* rho, void* u, void* T,
   if (lbm_status s = check_patch(g, patch)) return s;
   if (lbm_status s = check_bound(g)) return s;
   if (dtype != 0 && dtype != 1) return fail(g, LBM_ERR_ARG, "bad dtype");
-  (void)T;
   HostPatch& p = g->hg.P[patch];
+  if (g->hg.thermal)
+    return cuda_check(g,
+                      lbmk::launch_th_moments(g->hg.desc.storage, view(g, p), g->base + p.off_f[p.cur],
+                                              g->base + p.off_g[p.cur], rho, u, T, gamma, dtype, thermal_level(g, p),
+                                              g->stream),
+                      "lbm_moments");
+  (void)T;
   return cuda_check(g,
                     lbmk::launch_moments(g->hg.desc.storage, view(g, p), g->base + p.off_f[p.cur], rho, u, gamma,
                                          dtype, p.beta, level_force(g, p.level), g->hg.desc.mirror_lbgk, g->stream),
@@ -416,9 +504,9 @@ static lbm_status copy_pop(lbm_grid_t g, int32_t patch, int32_t which, void* den
   const size_t* off = which ? p.off_g : p.off_f;
   const lbmk::PatchDev pv = view(g, p);
   cudaError_t e = lbmk::launch_copy_pop(g->hg.desc.storage, pv, g->base + off[p.cur], dense, dtype, to_dense,
-                                        g->stream);
+                                        which, g->stream);
   if (!e && !to_dense)
-    e = lbmk::launch_copy_pop(g->hg.desc.storage, pv, g->base + off[1 - p.cur], dense, dtype, 0, g->stream);
+    e = lbmk::launch_copy_pop(g->hg.desc.storage, pv, g->base + off[1 - p.cur], dense, dtype, 0, which, g->stream);
   return cuda_check(g, e, "population copy");
 }
 

@@ -51,6 +51,7 @@ struct HostPatch {
   // node a plain bulk node or a depth-1 node with plain sources): x-tile | y<<16 | z<<32
   std::vector<uint64_t> tiles_pure[2];
   std::vector<uint32_t> tiles_mixed[2];  // other tiles with nodes to update: [0] even, [1] odd steps
+  std::vector<uint32_t> tiles_all[2];    // every tile with nodes to update (thermal model, node by node)
   alignas(64) unsigned char tmap[2][128];   // TMA load descriptors of the two population buffers
   alignas(64) unsigned char tmapo[2][128];  // TMA store descriptors
   alignas(64) unsigned char tmapw[2][128];  // TMA 16-byte wrap descriptors
@@ -67,7 +68,7 @@ struct HostPatch {
 
   // device placement (byte offsets into the bound buffer)
   size_t off_f[2]{}, off_g[2]{}, off_type = 0;
-  size_t off_tiles_pure[2]{}, off_tiles_mixed[2]{};
+  size_t off_tiles_pure[2]{}, off_tiles_mixed[2]{}, off_tiles_all[2]{};
   size_t off_ex_node = 0, off_ex_first = 0, off_ex_mask = 0, off_ex_sample = 0;
   size_t off_smp_node = 0, off_smp_kind = 0, off_smp_val = 0, off_cf_parent = 0, off_cf_child = 0;
   int cur = 0;  // which population buffer holds the current state

@@ -334,7 +334,7 @@ cudaError_t launch_moments(int storage, const PatchDev& p, const void* fin, void
 
 // ---------------------------------------------------------------------------
 template <typename S, typename R>
-__global__ void k_copy_pop(PatchDev p, S* fstore, void* dense, int dtype, int to_dense) {
+__global__ void k_copy_pop(PatchDev p, S* fstore, void* dense, int dtype, int to_dense, int gset) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
   if (x >= p.dim[0]) return;
@@ -342,7 +342,8 @@ __global__ void k_copy_pop(PatchDev p, S* fstore, void* dense, int dtype, int to
   const long long d = ((long long)z * p.dim[1] + y) * p.dim[0] + x;
   const long long nd = (long long)p.dim[0] * p.dim[1] * p.dim[2];
   for (int i = 0; i < 27; ++i) {
-    const double w = wi_rt(i);
+    const int c2 = (i % 3 != 1) + ((i / 3) % 3 != 1) + (i / 9 != 1);
+    const double w = gset ? wi_rt(i) * c2 : wi_rt(i);
     if (to_dense) {
       const double v = (double)Stor<S>::ld(fstore + (long long)i * p.plane + own) + w;
       if (dtype == 1) ((double*)dense)[i * nd + d] = v;
@@ -355,12 +356,12 @@ __global__ void k_copy_pop(PatchDev p, S* fstore, void* dense, int dtype, int to
 }
 
 cudaError_t launch_copy_pop(int storage, const PatchDev& p, void* fstore, void* dense, int dtype, int to_dense,
-                            cudaStream_t st) {
+                            int gset, cudaStream_t st) {
   return dispatch(storage, [&](auto ts, auto tr) {
     using S = typename decltype(ts)::type;
     using R = typename decltype(tr)::type;
     dim3 block(128), grid((p.dim[0] + 127) / 128, p.dim[1], p.dim[2]);
-    k_copy_pop<S, R><<<grid, block, 0, st>>>(p, (S*)fstore, dense, dtype, to_dense);
+    k_copy_pop<S, R><<<grid, block, 0, st>>>(p, (S*)fstore, dense, dtype, to_dense, gset);
     return cudaGetLastError();
   });
 }

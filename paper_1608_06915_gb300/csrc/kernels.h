@@ -21,6 +21,33 @@ struct Force {
   }
 };
 
+// Thermal parameters of one level: wall temperatures minus T0 per wall face,
+// g*lambda / 2^level, T_ref - T0, beta, beta1, LBGK mirror flag.
+struct ThermalLevel {
+  double twd[6];
+  double glam, tref_d, beta, beta1;
+  int lbgk;
+};
+
+cudaError_t launch_th_tiles(int storage, const PatchDev& p, const void* fin, const void* gin, void* fout, void* gout,
+                            const uint32_t* tiles, int64_t ntiles, int ntx, const ThermalLevel& L, int odd,
+                            int* status, cudaStream_t st);
+cudaError_t launch_th_coalesce(int storage, const PatchDev& child, const void* fin_c, const void* gin_c,
+                               const PatchDev& parent, void* fo_p, void* go_p, const uint32_t* cf_parent,
+                               const uint32_t* cf_child, int64_t n, double ff, double fg, const ThermalLevel& Lc,
+                               const ThermalLevel& Lp, int* status, cudaStream_t st);
+cudaError_t launch_th_samples(int storage, const PatchDev& parent, const void* fin_p, const void* gin_p,
+                              const PatchDev& child, const void* fin_c, const void* gin_c, const uint32_t* smp_node,
+                              const uint8_t* smp_kind, int64_t ns, void* smp_val, double ff, double fg,
+                              const ThermalLevel& Lp, const ThermalLevel& Lc, int* status, cudaStream_t st);
+cudaError_t launch_th_explode(int storage, const PatchDev& child, void* fo_c, void* go_c, const uint32_t* ex_node,
+                              const uint32_t* ex_first, const uint8_t* ex_mask, const uint32_t* ex_sample, int64_t n,
+                              const void* smp_val, int64_t ns, const ThermalLevel& Lc, cudaStream_t st);
+cudaError_t launch_th_init(int storage, const PatchDev& p, void* f0, void* f1, void* g0, void* g1, const void* rho,
+                           const void* u, const void* T, int dtype, const double u_in[3], cudaStream_t st);
+cudaError_t launch_th_moments(int storage, const PatchDev& p, const void* fin, const void* gin, void* rho, void* u,
+                              void* T, void* gamma, int dtype, const ThermalLevel& L, cudaStream_t st);
+
 // Bulk tiles through TMA (tmap_in / tmap_out / tmap_wrap: CUtensorMaps, 128
 // bytes, of the source buffer with the load box, of the destination buffer with
 // the store box, and of the source buffer with the wrap box; tiles:
@@ -55,8 +82,9 @@ cudaError_t launch_init(int storage, const PatchDev& p, void* f0, void* f1, cons
 cudaError_t launch_moments(int storage, const PatchDev& p, const void* fin, void* rho, void* u, void* gamma,
                            int dtype, double beta, const Force& F, int lbgk, cudaStream_t st);
 
+// gset = 1: the thermal g set, stored as the deviation from W_i c_i^2 (else from W_i)
 cudaError_t launch_copy_pop(int storage, const PatchDev& p, void* fstore, void* dense, int dtype, int to_dense,
-                            cudaStream_t st);
+                            int gset, cudaStream_t st);
 
 // FP64 partial sums of one patch into partial[blocks][8]; see lbm_diagnostics.
 cudaError_t launch_diag(int storage, const PatchDev& p, const void* fin, double vol_weight, const Force& F,

@@ -385,6 +385,7 @@ std::string build_layout(HostGrid& g) {
     for (int k = 0; k < 2; ++k) {
       p.tiles_pure[k].clear();
       p.tiles_mixed[k].clear();
+      p.tiles_all[k].clear();
     }
     for (int64_t z = 0; z < p.dim[2]; ++z)
       for (int64_t y = 0; y < p.dim[1]; ++y)
@@ -418,6 +419,8 @@ std::string build_layout(HostGrid& g) {
           // odd steps: depth-1 nodes are streamed too
           if (nb + nd1plain == n && nd1plain == nd1 && wrap_ok) p.tiles_pure[1].push_back(packed);
           else if (nb + nbc + nd1 > 0) p.tiles_mixed[1].push_back(id);
+          if (nb + nbc > 0) p.tiles_all[0].push_back(id);
+          if (nb + nbc + nd1 > 0) p.tiles_all[1].push_back(id);
         }
   }
   // interface tables, stored on the child
@@ -526,6 +529,8 @@ size_t plan_memory(HostGrid& g) {
     p.off_type = take((size_t)p.plane);
     p.off_tiles_pure[0] = take(8 * p.tiles_pure[0].size());
     p.off_tiles_pure[1] = take(8 * p.tiles_pure[1].size());
+    p.off_tiles_all[0] = take(4 * p.tiles_all[0].size());
+    p.off_tiles_all[1] = take(4 * p.tiles_all[1].size());
     p.off_tiles_mixed[0] = take(4 * p.tiles_mixed[0].size());
     p.off_tiles_mixed[1] = take(4 * p.tiles_mixed[1].size());
     p.off_ex_node = take(4 * p.ex_node.size());

@@ -1,0 +1,552 @@
+// Two-population thermal model (Sec. II.B, Pr <= 1) on the refined grid.
+//
+// f follows the isothermal KBC collision with the Boussinesq acceleration
+// g*lambda*(T - T_ref) e_z through the exact difference method; g relaxes as
+//   g' = g + 2 beta (g^eq - g) + 2 (beta - beta1) (g* - g^eq)
+// (Eq. kinetics_g_entr), where for Pr <= 1 the quasi-equilibrium differs from
+// the equilibrium only in its first moment (Table I):
+//   g*_i - g^eq_i = W_i c_i . (q - q^eq - 2 (P - P^eq) u) / T0.
+// g^eq is the Grad form (Eq. grad_general) with (2 rho E, q^eq, R^eq), T0 = 1/3.
+// At rest at the reference state g^eq_i = W_i c_i^2; g is stored as the
+// deviation from that, f as the deviation from W_i.
+//
+// Interface (Sec. III.A, thermal model): f non-equilibrium scaled by
+// ff = beta_s / (r beta_t); g by
+//   g_t = g^eq + fg (g - g^eq) + (ff - fg) W_i c_i . (2 P1 u) / T0,
+//   fg = beta1_s / (r beta1_t),  P1 = sum c c (f - f^eq)  (Eqs. for P1 and g^neq_f).
+// Reconstruction interpolates rho, u, T and both non-equilibrium parts.
+// Walls: f half-way bounce-back, g anti-bounce-back to the wall equilibrium at
+// rest, temperature T_w.  Every kernel here pulls node by node.
+#include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
+#include "device.cuh"
+#include "kernels.h"
+
+namespace lbmk {
+
+template <int i>
+__host__ __device__ constexpr int C2() {
+  return CX(i) * CX(i) + CY(i) * CY(i) + CZ(i) * CZ(i);
+}
+
+template <typename R>
+struct ThState {
+  R rho_t, rho, ux, uy, uz;
+  R e_t;    // 2 rho E - 1
+  R T_d;    // T - T0
+};
+
+template <typename R>
+__device__ __forceinline__ void thermal_state(const R (&f)[27], const R (&g)[27], ThState<R>& s) {
+  macro(f, s.rho_t, s.rho, s.ux, s.uy, s.uz);
+  R e[3] = {0, 0, 0};
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    e[CZ(i) + 1] += g[i];
+  });
+  s.e_t = (e[0] + e[2]) + e[1];
+  // T = (2E - u^2)/3 with 2E = (1 + e_t)/rho  =>  T - 1/3 = ((e_t - rho_t)/rho - u^2)/3
+  const R u2 = s.ux * s.ux + s.uy * s.uy + s.uz * s.uz;
+  s.T_d = (fdiv(s.e_t - s.rho_t, s.rho) - u2) * R(1.0 / 3.0);
+}
+
+// g^eq - W_i c_i^2 for (rho, u, 2 rho E); see the header comment.
+template <typename R>
+__device__ __forceinline__ void geq_dev(R rho_t, R rho, R ux, R uy, R uz, R e_t, R (&ge)[27]) {
+  const R E2 = R(1) + e_t;
+  const R u2 = ux * ux + uy * uy + uz * uz;
+  const R a1 = R(3) * (E2 + R(2.0 / 3.0) * rho);
+  const R a2 = R(4.5) * (E2 + R(4.0 / 3.0) * rho);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const R cu = R(CX(i)) * ux + R(CY(i)) * uy + R(CZ(i)) * uz;
+    ge[i] = R(WI(i)) * (e_t + rho_t * R(C2<i>() - 1) + a1 * cu + a2 * (cu * cu - u2 * R(1.0 / 3.0)));
+  });
+}
+
+// Non-equilibrium pressure tensor P1 = sum c c (f - f^eq) from f and its equilibrium.
+template <typename R>
+__device__ __forceinline__ void p1_tensor(const R (&f)[27], const R (&fe)[27], R (&P)[6]) {
+  for (int k = 0; k < 6; ++k) P[k] = 0;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const R d = f[i] - fe[i];
+    if constexpr (CX(i) != 0) P[0] += d;
+    if constexpr (CY(i) != 0) P[1] += d;
+    if constexpr (CZ(i) != 0) P[2] += d;
+    if constexpr (CX(i) * CY(i) != 0) P[3] += R(CX(i) * CY(i)) * d;
+    if constexpr (CX(i) * CZ(i) != 0) P[4] += R(CX(i) * CZ(i)) * d;
+    if constexpr (CY(i) * CZ(i) != 0) P[5] += R(CY(i) * CZ(i)) * d;
+  });
+}
+
+// W_i c_i . V / T0 for a vector V
+template <int i, typename R>
+__device__ __forceinline__ R wcv3(R vx, R vy, R vz) {
+  return R(3.0 * WI(i)) * (R(CX(i)) * vx + R(CY(i)) * vy + R(CZ(i)) * vz);
+}
+
+// One thermal collision of deviation populations (f, g) in place; returns gamma.
+template <typename R>
+__device__ __forceinline__ R thermal_collide(R (&f)[27], R (&g)[27], R beta, R beta1, R glam, R tref_d,
+                                             bool lbgk) {
+  ThState<R> s;
+  thermal_state(f, g, s);
+  // pre-collision moments: P - P^eq = P~ + T0 d - rho T0 d - rho u u, q = sum c g
+  R P[6] = {0, 0, 0, 0, 0, 0}, q[3] = {0, 0, 0};
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (CX(i) != 0) P[0] += f[i];
+    if constexpr (CY(i) != 0) P[1] += f[i];
+    if constexpr (CZ(i) != 0) P[2] += f[i];
+    if constexpr (CX(i) * CY(i) != 0) P[3] += R(CX(i) * CY(i)) * f[i];
+    if constexpr (CX(i) * CZ(i) != 0) P[4] += R(CX(i) * CZ(i)) * f[i];
+    if constexpr (CY(i) * CZ(i) != 0) P[5] += R(CY(i) * CZ(i)) * f[i];
+    if constexpr (CX(i) != 0) q[0] += R(CX(i)) * g[i];
+    if constexpr (CY(i) != 0) q[1] += R(CY(i)) * g[i];
+    if constexpr (CZ(i) != 0) q[2] += R(CZ(i)) * g[i];
+  });
+  const R u[3] = {s.ux, s.uy, s.uz};
+  const R rt3 = s.rho_t * R(1.0 / 3.0);
+  const R Pd[3][3] = {{P[0] - rt3 - s.rho * u[0] * u[0], P[3] - s.rho * u[0] * u[1], P[4] - s.rho * u[0] * u[2]},
+                      {P[3] - s.rho * u[1] * u[0], P[1] - rt3 - s.rho * u[1] * u[1], P[5] - s.rho * u[1] * u[2]},
+                      {P[4] - s.rho * u[2] * u[0], P[5] - s.rho * u[2] * u[1], P[2] - rt3 - s.rho * u[2] * u[2]}};
+  const R qc = R(1) + s.e_t + R(2.0 / 3.0) * s.rho;  // q^eq = (2 rho E + 2 rho T0) u
+  R X[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) X[a] = q[a] - qc * u[a] - R(2) * (Pd[a][0] * u[0] + Pd[a][1] * u[1] + Pd[a][2] * u[2]);
+  R ge[27];
+  geq_dev(s.rho_t, s.rho, s.ux, s.uy, s.uz, s.e_t, ge);
+  const R b2 = R(2) * beta, b12 = R(2) * (beta - beta1);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    g[i] = g[i] + b2 * (ge[i] - g[i]) + b12 * wcv3<i>(X[0], X[1], X[2]);
+  });
+  const R duz = glam * (s.T_d - tref_d);
+  return kbc_collide<R, 4>(f, beta, R(0), R(0), duz, lbgk);
+}
+
+// Non-equilibrium rescaling of a thermal pair from a level with (beta_s, beta1_s)
+// to one with (beta_t, beta1_t): factors ff = beta_s/(r beta_t), fg = beta1_s/(r beta1_t).
+// Writes the rescaled non-equilibrium parts and the state's (rho~, u, T - T0).
+template <typename R>
+__device__ __forceinline__ void thermal_neq(const R (&f)[27], const R (&g)[27], R ff, R fg, R (&fneq)[27],
+                                            R (&gneq)[27], ThState<R>& s) {
+  thermal_state(f, g, s);
+  R fe[27], ge[27];
+  feq_dev(s.rho_t, s.rho, s.ux, s.uy, s.uz, fe);
+  geq_dev(s.rho_t, s.rho, s.ux, s.uy, s.uz, s.e_t, ge);
+  R P1[6];
+  p1_tensor(f, fe, P1);
+  const R Y[3] = {R(2) * (P1[0] * s.ux + P1[3] * s.uy + P1[4] * s.uz),
+                  R(2) * (P1[3] * s.ux + P1[1] * s.uy + P1[5] * s.uz),
+                  R(2) * (P1[4] * s.ux + P1[5] * s.uy + P1[2] * s.uz)};
+  const R fd = ff - fg;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    fneq[i] = ff * (f[i] - fe[i]);
+    gneq[i] = fg * (g[i] - ge[i]) + fd * wcv3<i>(Y[0], Y[1], Y[2]);
+  });
+}
+
+// Generic pull of f and g: walls (f bounce-back, g anti-bounce-back to the wall
+// equilibrium at rest, temperature T_w, density of the node's own state), solid
+// nodes (bounce-back of both), outlet (clamped source), spanned-axis wrap.
+template <typename R>
+__device__ __forceinline__ void pull_generic_th(const PatchDev& p, const R* __restrict__ fin,
+                                                const R* __restrict__ gin, int x, int y, int z, R (&f)[27],
+                                                R (&g)[27], const R* twd, int* status) {
+  const long long own = node_index(p, x, y, z);
+  const int X[3] = {x, y, z};
+  R rho_own_t = 0;
+  bool have_rho = false;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int c[3] = {CX(i), CY(i), CZ(i)};
+    int s[3];
+    bool bounce = false, bad = false;
+    int wall_face = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      s[a] = X[a] - c[a];
+      if (s[a] < 0 || s[a] >= p.dim[a]) {
+        if (p.span[a]) {
+          s[a] += s[a] < 0 ? p.dim[a] : -p.dim[a];
+        } else if (!p.periodic[a]) {
+          const int G = p.org[a] + s[a];
+          if (G < 0) {
+            if (p.walls & (1u << (2 * a))) bounce = true, wall_face = 2 * a;
+            else bad = true;
+          } else if (G > p.maxc[a]) {
+            if (p.walls & (1u << (2 * a + 1))) bounce = true, wall_face = 2 * a + 1;
+            else if (p.inflow == a) s[a] = p.maxc[a] - p.org[a];
+            else bad = true;
+          } else {
+            bad = true;
+          }
+        } else {
+          bad = true;
+        }
+      }
+    }
+    long long src = own;
+    if (!bounce && !bad) {
+      src = node_index(p, s[0], s[1], s[2]);
+      const uint8_t t = p.type[src];
+      if (t == T_SOLID) bounce = true;
+      else if (t == T_SKIP) bad = true;
+    }
+    if (bad) {
+      atomicOr(status, 1);
+      bounce = true;
+    }
+    if (bounce) {
+      f[i] = fin[(long long)(26 - i) * p.plane + own];
+      const R gb = gin[(long long)(26 - i) * p.plane + own];
+      if (wall_face >= 0) {
+        if (!have_rho) {
+          for (int k = 0; k < 27; ++k) rho_own_t += fin[(long long)k * p.plane + own];
+          have_rho = true;
+        }
+        // g_i = -g'_ibar + g^w_i + g^w_ibar,  g^w_i = W_i rho (3 T_w + c_i^2 - 1)
+        g[i] = -gb + R(2 * WI(i)) * (R(3) * (R(1) + rho_own_t) * twd[wall_face] + rho_own_t * R(C2<i>()));
+      } else {
+        g[i] = gb;
+      }
+    } else {
+      f[i] = fin[(long long)i * p.plane + src];
+      g[i] = gin[(long long)i * p.plane + src];
+    }
+  });
+}
+
+template <typename R>
+__device__ __forceinline__ void pull_th(const PatchDev& p, const R* __restrict__ fin, const R* __restrict__ gin,
+                                        int x, int y, int z, R (&f)[27], R (&g)[27], const R* twd, int* status) {
+  if (p.type[node_index(p, x, y, z)] == T_BULK) {
+    pull_bulk<R, R>(p, fin, x, y, z, f);
+    pull_bulk<R, R>(p, gin, x, y, z, g);
+  } else {
+    pull_generic_th<R>(p, fin, gin, x, y, z, f, g, twd, status);
+  }
+}
+
+template <typename R>
+struct ThParams {
+  R twd[6];  // wall temperature - T0 per wall face
+  R glam;    // g lambda / 2^level (coarse acceleration per unit T, per level step)
+  R tref_d;  // T_ref - T0
+  R beta, beta1;
+  int lbgk;
+};
+
+template <typename R>
+__device__ __forceinline__ void store2(const PatchDev& p, R* __restrict__ fo, R* __restrict__ go, long long n,
+                                       const R (&f)[27], const R (&g)[27]) {
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    fo[(long long)i * p.plane + n] = f[i];
+    go[(long long)i * p.plane + n] = g[i];
+  });
+}
+
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(128) k_th_tiles(PatchDev p, const R* __restrict__ fin, const R* __restrict__ gin,
+                                                  R* __restrict__ fout, R* __restrict__ gout,
+                                                  const uint32_t* __restrict__ tiles, int ntx, ThParams<R> tp, int odd,
+                                                  int* status) {
+  const uint32_t t = tiles[blockIdx.x];
+  const int x = (int)(t % (uint32_t)ntx) * 128 + threadIdx.x;
+  const int y = (int)((t / (uint32_t)ntx) % (uint32_t)p.dim[1]);
+  const int z = (int)(t / ((uint32_t)ntx * (uint32_t)p.dim[1]));
+  if (x >= p.dim[0]) return;
+  const long long own = node_index(p, x, y, z);
+  const uint8_t ty = p.type[own];
+  if (!(ty == T_BULK || ty == T_BC || (ty == T_D1 && odd))) return;
+  R f[27], g[27];
+  pull_th<R>(p, fin, gin, x, y, z, f, g, tp.twd, status);
+  thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0);
+  store2(p, fout, gout, own, f, g);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_th_coalesce(PatchDev pc, const R* __restrict__ fin_c,
+                                                     const R* __restrict__ gin_c, PatchDev pp, R* __restrict__ fo_p,
+                                                     R* __restrict__ go_p, const uint32_t* __restrict__ cf_parent,
+                                                     const uint32_t* __restrict__ cf_child, long long n, R ff, R fg,
+                                                     ThParams<R> tc, ThParams<R> tpar, int* status) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const uint32_t cn = cf_child[k];
+  const int x = (int)(cn % pc.nxp), y = (int)((cn / pc.nxp) % pc.dim[1]);
+  const int z = (int)(cn / ((long long)pc.nxp * pc.dim[1]));
+  R f[27], g[27];
+  pull_th<R>(pc, fin_c, gin_c, x, y, z, f, g, tc.twd, status);
+  R fn[27], gn[27];
+  ThState<R> s;
+  thermal_neq<R>(f, g, ff, fg, fn, gn, s);
+  R fe[27], ge[27];
+  feq_dev(s.rho_t, s.rho, s.ux, s.uy, s.uz, fe);
+  geq_dev(s.rho_t, s.rho, s.ux, s.uy, s.uz, s.e_t, ge);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    f[i] = fe[i] + fn[i];
+    g[i] = ge[i] + gn[i];
+  });
+  thermal_collide<R>(f, g, tpar.beta, tpar.beta1, tpar.glam, tpar.tref_d, tpar.lbgk != 0);
+  store2(pp, fo_p, go_p, cf_parent[k], f, g);
+}
+
+// samples: [59][ns] = rho - 1, ux, uy, uz, T - T0, fneq_0..26, gneq_0..26 (child scale)
+template <typename R>
+__global__ void __launch_bounds__(128) k_th_samples(PatchDev pp, const R* __restrict__ fin_p,
+                                                    const R* __restrict__ gin_p, PatchDev pc,
+                                                    const R* __restrict__ fin_c, const R* __restrict__ gin_c,
+                                                    const uint32_t* __restrict__ smp_node,
+                                                    const uint8_t* __restrict__ smp_kind, long long ns,
+                                                    R* __restrict__ out, R ff, R fg, ThParams<R> tpar, ThParams<R> tc,
+                                                    int* status) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  R f[27], g[27];
+  const uint32_t n = smp_node[s];
+  const bool par = smp_kind[s] == 0;
+  const PatchDev& q = par ? pp : pc;
+  const int x = (int)(n % q.nxp), y = (int)((n / q.nxp) % q.dim[1]);
+  const int z = (int)(n / ((long long)q.nxp * q.dim[1]));
+  if (par) pull_th<R>(pp, fin_p, gin_p, x, y, z, f, g, tpar.twd, status);
+  else pull_th<R>(pc, fin_c, gin_c, x, y, z, f, g, tc.twd, status);
+  R fn[27], gn[27];
+  ThState<R> st;
+  thermal_neq<R>(f, g, par ? ff : R(1), par ? fg : R(1), fn, gn, st);
+  out[s] = st.rho_t;
+  out[ns + s] = st.ux;
+  out[2 * ns + s] = st.uy;
+  out[3 * ns + s] = st.uz;
+  out[4 * ns + s] = st.T_d;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    out[(5 + i) * ns + s] = fn[i];
+    out[(32 + i) * ns + s] = gn[i];
+  });
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_th_explode(PatchDev pc, R* __restrict__ fo_c, R* __restrict__ go_c,
+                                                    const uint32_t* __restrict__ ex_node,
+                                                    const uint32_t* __restrict__ ex_first,
+                                                    const uint8_t* __restrict__ ex_mask,
+                                                    const uint32_t* __restrict__ ex_sample, long long n,
+                                                    const R* __restrict__ smp, long long ns, ThParams<R> tc) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const R w4[4] = {R(-1.0 / 16.0), R(9.0 / 16.0), R(9.0 / 16.0), R(-1.0 / 16.0)};
+  const uint8_t mask = ex_mask[k];
+  const int cx = (mask & 1) ? 4 : 1, cy = (mask & 2) ? 4 : 1, cz = (mask & 4) ? 4 : 1;
+  uint32_t j = ex_first[k];
+  R m[5] = {0, 0, 0, 0, 0};
+  R f[27], g[27];
+  unroll<27>([&](auto I) {
+    f[decltype(I)::value] = R(0);
+    g[decltype(I)::value] = R(0);
+  });
+  for (int kz = 0; kz < cz; ++kz) {
+    const R wz = cz == 4 ? w4[kz] : R(1);
+    for (int ky = 0; ky < cy; ++ky) {
+      const R wyz = wz * (cy == 4 ? w4[ky] : R(1));
+      for (int kx = 0; kx < cx; ++kx) {
+        const R w = wyz * (cx == 4 ? w4[kx] : R(1));
+        const long long s = ex_sample[j++];
+        for (int c = 0; c < 5; ++c) m[c] += w * smp[c * ns + s];
+        unroll<27>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          f[i] += w * smp[(5 + i) * ns + s];
+          g[i] += w * smp[(32 + i) * ns + s];
+        });
+      }
+    }
+  }
+  const R rho_t = m[0], rho = R(1) + rho_t, ux = m[1], uy = m[2], uz = m[3], T_d = m[4];
+  // 2 rho E - 1 = rho (3 T + u^2) - 1 = rho_t + rho (3 (T - T0) + u^2)
+  const R e_t = rho_t + rho * (R(3) * T_d + ux * ux + uy * uy + uz * uz);
+  R fe[27], ge[27];
+  feq_dev(rho_t, rho, ux, uy, uz, fe);
+  geq_dev(rho_t, rho, ux, uy, uz, e_t, ge);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    f[i] += fe[i];
+    g[i] += ge[i];
+  });
+  thermal_collide<R>(f, g, tc.beta, tc.beta1, tc.glam, tc.tref_d, tc.lbgk != 0);
+  store2(pc, fo_c, go_c, ex_node[k], f, g);
+}
+
+template <typename R>
+__global__ void k_th_init(PatchDev p, R* __restrict__ f0, R* __restrict__ f1, R* __restrict__ g0,
+                          R* __restrict__ g1, const void* rho_in, const void* u_in, const void* T_in, int dtype,
+                          R uix, R uiy, R uiz) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= p.dim[0]) return;
+  const long long own = node_index(p, x, y, z);
+  const long long d = ((long long)z * p.dim[1] + y) * p.dim[0] + x;
+  const long long nd = (long long)p.dim[0] * p.dim[1] * p.dim[2];
+  const uint8_t t = p.type[own];
+  R rho = 1, ux = 0, uy = 0, uz = 0, T = R(1.0 / 3.0);
+  auto ld = [&](const void* a, long long i) -> R {
+    return dtype == 1 ? (R)((const double*)a)[i] : (R)((const float*)a)[i];
+  };
+  if (t == T_INLET) {
+    ux = uix, uy = uiy, uz = uiz;
+  } else if (t != T_SKIP && t != T_SOLID) {
+    rho = ld(rho_in, d);
+    ux = ld(u_in, d), uy = ld(u_in, nd + d), uz = ld(u_in, 2 * nd + d);
+    if (T_in) T = ld(T_in, d);
+  }
+  const R rho_t = rho - R(1);
+  const R e_t = rho_t + rho * (R(3) * (T - R(1.0 / 3.0)) + ux * ux + uy * uy + uz * uz);
+  R fe[27], ge[27];
+  feq_dev(rho_t, rho, ux, uy, uz, fe);
+  geq_dev(rho_t, rho, ux, uy, uz, e_t, ge);
+  store2(p, f0, g0, own, fe, ge);
+  store2(p, f1, g1, own, fe, ge);
+}
+
+template <typename R>
+__global__ void k_th_moments(PatchDev p, const R* __restrict__ fin, const R* __restrict__ gin, void* rho_o,
+                             void* u_o, void* T_o, void* gamma_o, int dtype, ThParams<R> tp) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= p.dim[0]) return;
+  const long long own = node_index(p, x, y, z);
+  const long long d = ((long long)z * p.dim[1] + y) * p.dim[0] + x;
+  const long long nd = (long long)p.dim[0] * p.dim[1] * p.dim[2];
+  const uint8_t t = p.type[own];
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  if (t != T_SKIP && t != T_SOLID) {
+    R f[27], g[27];
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      f[i] = fin[(long long)i * p.plane + own];
+      g[i] = gin[(long long)i * p.plane + own];
+    });
+    ThState<R> s;
+    thermal_state(f, g, s);
+    const double duz = (double)tp.glam * ((double)s.T_d - (double)tp.tref_d);
+    v[0] = 1.0 + (double)s.rho_t;
+    v[1] = s.ux;
+    v[2] = s.uy;
+    v[3] = (double)s.uz + 0.5 * duz;
+    v[4] = 1.0 / 3.0 + (double)s.T_d;
+    if (gamma_o) v[5] = thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0);
+  }
+  auto st = [&](void* a, long long i, double val) {
+    if (!a) return;
+    if (dtype == 1) ((double*)a)[i] = val;
+    else ((float*)a)[i] = (float)val;
+  };
+  st(rho_o, d, v[0]);
+  if (u_o)
+    for (int a = 0; a < 3; ++a) st(u_o, a * nd + d, v[1 + a]);
+  st(T_o, d, v[4]);
+  st(gamma_o, d, v[5]);
+}
+
+// ---------------------------------------------------------------------------
+template <typename R>
+ThParams<R> th_params(const ThermalLevel& L) {
+  ThParams<R> t;
+  for (int k = 0; k < 6; ++k) t.twd[k] = (R)L.twd[k];
+  t.glam = (R)L.glam;
+  t.tref_d = (R)L.tref_d;
+  t.beta = (R)L.beta;
+  t.beta1 = (R)L.beta1;
+  t.lbgk = L.lbgk;
+  return t;
+}
+
+template <typename F>
+cudaError_t th_dispatch(int storage, F&& f) {
+  if (storage == LBM_FP64) return f((double)0);
+  if (storage == LBM_FP32) return f((float)0);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_th_tiles(int storage, const PatchDev& p, const void* fin, const void* gin, void* fout, void* gout,
+                            const uint32_t* tiles, int64_t ntiles, int ntx, const ThermalLevel& L, int odd,
+                            int* status, cudaStream_t st) {
+  if (ntiles == 0) return cudaSuccess;
+  return th_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    k_th_tiles<R><<<(unsigned)ntiles, 128, 0, st>>>(p, (const R*)fin, (const R*)gin, (R*)fout, (R*)gout, tiles, ntx,
+                                                    th_params<R>(L), odd, status);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_th_coalesce(int storage, const PatchDev& child, const void* fin_c, const void* gin_c,
+                               const PatchDev& parent, void* fo_p, void* go_p, const uint32_t* cf_parent,
+                               const uint32_t* cf_child, int64_t n, double ff, double fg, const ThermalLevel& Lc,
+                               const ThermalLevel& Lp, int* status, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  return th_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    k_th_coalesce<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+        child, (const R*)fin_c, (const R*)gin_c, parent, (R*)fo_p, (R*)go_p, cf_parent, cf_child, n, (R)ff, (R)fg,
+        th_params<R>(Lc), th_params<R>(Lp), status);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_th_samples(int storage, const PatchDev& parent, const void* fin_p, const void* gin_p,
+                              const PatchDev& child, const void* fin_c, const void* gin_c, const uint32_t* smp_node,
+                              const uint8_t* smp_kind, int64_t ns, void* smp_val, double ff, double fg,
+                              const ThermalLevel& Lp, const ThermalLevel& Lc, int* status, cudaStream_t st) {
+  if (ns == 0) return cudaSuccess;
+  return th_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    k_th_samples<R><<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(
+        parent, (const R*)fin_p, (const R*)gin_p, child, (const R*)fin_c, (const R*)gin_c, smp_node, smp_kind, ns,
+        (R*)smp_val, (R)ff, (R)fg, th_params<R>(Lp), th_params<R>(Lc), status);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_th_explode(int storage, const PatchDev& child, void* fo_c, void* go_c, const uint32_t* ex_node,
+                              const uint32_t* ex_first, const uint8_t* ex_mask, const uint32_t* ex_sample, int64_t n,
+                              const void* smp_val, int64_t ns, const ThermalLevel& Lc, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  return th_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    k_th_explode<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(child, (R*)fo_c, (R*)go_c, ex_node, ex_first,
+                                                                 ex_mask, ex_sample, n, (const R*)smp_val, ns,
+                                                                 th_params<R>(Lc));
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_th_init(int storage, const PatchDev& p, void* f0, void* f1, void* g0, void* g1, const void* rho,
+                           const void* u, const void* T, int dtype, const double u_in[3], cudaStream_t st) {
+  return th_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    dim3 block(128), grid((p.dim[0] + 127) / 128, p.dim[1], p.dim[2]);
+    k_th_init<R><<<grid, block, 0, st>>>(p, (R*)f0, (R*)f1, (R*)g0, (R*)g1, rho, u, T, dtype, (R)u_in[0],
+                                         (R)u_in[1], (R)u_in[2]);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_th_moments(int storage, const PatchDev& p, const void* fin, const void* gin, void* rho, void* u,
+                              void* T, void* gamma, int dtype, const ThermalLevel& L, cudaStream_t st) {
+  return th_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    dim3 block(128), grid((p.dim[0] + 127) / 128, p.dim[1], p.dim[2]);
+    k_th_moments<R><<<grid, block, 0, st>>>(p, (const R*)fin, (const R*)gin, rho, u, T, gamma, dtype,
+                                            th_params<R>(L));
+    return cudaGetLastError();
+  });
+}
+
+}  // namespace lbmk

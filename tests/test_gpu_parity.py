@@ -242,3 +242,40 @@ def test_channel_full_size_rest_state_and_symmetry():
         fa = g.get_populations(a).cpu().numpy()
         fb = g.get_populations(b).cpu().numpy()
         assert np.max(np.abs(fa - fb[mir][:, :, ::-1, :])) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Thermal two-population model (Rayleigh-Benard layout, three levels)
+
+def _rbc(case):
+    return lambda x, y, z, p, info: I.rbc_fields(case, info["level"], info["org"], info["dim"])
+
+
+def test_rbc_small_fp64_every_step():
+    """Plates with anti-bounce-back, Boussinesq force, two wall bands per level:
+    f and g against the oracle after every coarse step."""
+    case = I.rbc_small_case()
+    g, o = twin(case, "fp64", _rbc(case))
+    for s in range(4):
+        g.step(1)
+        o.step(1)
+        df, dg = pop_diff(g, o, 0), pop_diff(g, o, 1)
+        assert df < 1e-12 and dg < 1e-12, (s, df, dg)
+
+
+def test_rbc_small_fp32_temperature():
+    case = I.rbc_small_case()
+    g, o = twin(case, "fp32", _rbc(case))
+    g.step(20)
+    o.step(20)
+    er, eu = macro_rel_l2(g, o)
+    num = den = 0.0
+    for p in range(len(o.patches)):
+        _, _, Tg, _ = g.moments(p)
+        _, _, To, _ = o.moments(p)
+        m = o.mask(p) == 1
+        num += float(np.sum((Tg.cpu().numpy()[m] - To[m]) ** 2))
+        den += float(np.sum((To[m] - 1.0 / 3.0) ** 2))
+    eT = (num / den) ** 0.5
+    print("rbc fp32 after 20 steps: rel L2 rho %.3e u %.3e (T - T0) %.3e" % (er, eu, eT))
+    assert er < 1e-5 and eu < 1e-4 and eT < 1e-4
