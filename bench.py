@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--storage", choices=sorted(BYTES_PER_UPDATE), default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -205,7 +206,7 @@ class Clocks:
 def source_hash():
     """Hash of the sources of the stream-collide kernels (profiles record it)."""
     h = hashlib.sha256()
-    for f in ("device.cuh", "sc_tma.cuh", "sc_tma.cu", "sc_tma_fp32.cu", "kernels.cu"):
+    for f in ("device.cuh", "sc_tma.cuh", "sc_tma_fp32.cu"):
         with open(os.path.join(ROOT, "paper_1608_06915_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -267,6 +268,42 @@ def end_to_end(args, g, L, host_fields, dfields, nup, world, barrier, dev):
                note="per job: H2D of initial rho,u (pinned), init, %d coarse steps, D2H of rho,u; grid layout "
                     "built and bound before timing" % args.steps)
     return e2e
+
+
+def adjoint_ratio(dev, storage="fp32", K=20):
+    """Time of the discrete adjoint of K coarse steps (lbm_adjoint_step: restore,
+    recompute with snapshots, reverse) over the time of K forward steps, on the
+    64^3 box with the [24,40]^3 box refined 2x (divergence-free random field)."""
+    import torch
+    from paper_1608_06915_gb300 import inputs as I
+    from paper_1608_06915_gb300 import lbm as L
+    case = I.adjoint_case()
+    g = L.Grid(case, storage, device=dev)
+    modes = I.divfree_modes(n=64, kmax=4.0, rms=0.03, seed=4)
+    for p, info in enumerate(g.patches):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        rho, u = I.divfree_fields(x, y, z, modes)
+        g.init_equilibrium(p, torch.from_numpy(rho).to(dev), torch.from_numpy(u).to(dev))
+    ck = torch.empty(g.checkpoint_bytes(), dtype=torch.uint8, device=dev)
+    lam, ws = g.adjoint_buffers(K)
+    g.checkpoint(ck, save=True)
+    g.step(K)
+    g.adjoint_seed(lam, ws)
+    g.adjoint_step(ck, K, lam, ws)  # warm-up
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize(dev)
+    e[0].record(g.stream)
+    g.step(K)
+    e[1].record(g.stream)
+    g.adjoint_seed(lam, ws)
+    e[2].record(g.stream)
+    g.adjoint_step(ck, K, lam, ws)
+    e[3].record(g.stream)
+    torch.cuda.synchronize(dev)
+    fwd, adj = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    return dict(workload="64^3 periodic, [24,40]^3 refined 2x, %s, segments of %d coarse steps" % (storage, K),
+                forward_ms_per_step=fwd / K, adjoint_ms_per_step=adj / K, ratio=adj / fwd,
+                note="adjoint time includes restoring the checkpoint and recomputing the segment")
 
 
 def cuda_arm(args):
@@ -348,6 +385,10 @@ def cuda_arm(args):
     if not args.no_e2e and not case.get("thermal"):
         e2e = end_to_end(args, g, L, host_fields, dfields, nup, world, barrier, dev)
 
+    adj = None
+    if not args.no_adjoint and args.workload == "channel":
+        adj = adjoint_ratio(dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         r = oracle_run(args.workload, seconds=15.0)
@@ -362,6 +403,7 @@ def cuda_arm(args):
                                 parallelism="replicas" if world > 1 else "single GPU",
                                 l2="no flush: working set %.2f GB > %.0f MB L2" % (ws / 1e9, L2_BYTES / 1e6)),
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clk,
+                    adjoint_forward_ratio=adj,
                     kernels=kernels,
                     diagnostics=dict(mass=diag["mass"], min_rho=diag["min_rho"], status=diag["status"]))
         print(json.dumps(line), flush=True)

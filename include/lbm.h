@@ -203,6 +203,38 @@ lbm_status lbm_checkpoint(lbm_grid_t g, void* dev, int32_t save);
 lbm_status lbm_collide_nodes(const void* f_in, void* f_out, void* gamma_out, int64_t n, double beta,
                              const double du[3], int32_t lbgk, int32_t dtype, void* cuda_stream);
 
+/* Discrete adjoint of lbm_step (not in the paper; the reverse of its algorithm)
+ * for isothermal layouts that are periodic -- no walls, solids, inflow or body
+ * force -- with FP32 or FP64 storage.  Adjoint populations lambda use the
+ * packed layout of all patches in order, each [27][z][y][x_padded] over the
+ * storage box with the padded row length the library uses, in the compute
+ * precision (float for FP32, double for FP64); they are device buffers the
+ * caller owns.
+ *
+ * lbm_adjoint_workspace_bytes: sizes of lambda and of the workspace needed by
+ * segments of K coarse steps (one state snapshot per step, a second lambda
+ * buffer, reconstruction-sample adjoints).
+ *
+ * lbm_adjoint_seed: objective J = kinetic energy 1/2 sum rho |u|^2 8^-level of
+ * the current state over owned nodes (a parent owns its nodes outside every
+ * child's [a+1, b-1] box, a child its nodes two or more child spacings inside
+ * its interface faces), returned in *ke_out (FP64, synchronises), and
+ * lambda = dJ/df.
+ *
+ * lbm_adjoint_step: ckpt holds the state at the segment start (the layout of
+ * lbm_checkpoint).  On entry lambda_inout is dJ/d(state after K coarse steps);
+ * the call recomputes the K steps from ckpt (one snapshot each), runs their
+ * adjoints in reverse and leaves dJ/d(state at the segment start) in
+ * lambda_inout and the grid state at the segment start.
+ *
+ * lbm_adjoint_grad_u0: for a state f = f^eq(rho, u0) (Eq. feq_iso) -- the
+ * initial state -- writes dJ/du0 of one patch, device double [3][z][y][x]. */
+lbm_status lbm_adjoint_workspace_bytes(lbm_grid_t g, int32_t K, size_t* lambda_bytes, size_t* workspace_bytes);
+lbm_status lbm_adjoint_seed(lbm_grid_t g, void* lambda, void* workspace, double* ke_out);
+lbm_status lbm_adjoint_step(lbm_grid_t g, const void* ckpt, int32_t K, void* lambda_inout, void* workspace,
+                            size_t ws_bytes);
+lbm_status lbm_adjoint_grad_u0(lbm_grid_t g, const void* lambda, int32_t patch, void* grad_u);
+
 /* Kernel timing for measurement: enable = 1 makes lbm_step bracket every
  * kernel it launches with CUDA events on the bound stream (and clears earlier
  * records); 0 stops recording.  Not part of the method. */

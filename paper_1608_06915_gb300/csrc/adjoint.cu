@@ -1,0 +1,583 @@
+// Discrete adjoint of the refined isothermal KBC step (periodic layouts
+// without walls, solids, inflow or body force).
+//
+// Every forward kernel maps the previous states (pulled) to the nodes it
+// writes; its adjoint takes the adjoint of those nodes (lambda_new), recomputes
+// the forward pre-collision state from the restored previous state, applies
+// the transposed Jacobian of the node map and scatters the result back along
+// the pull (a push: lambda_old[x - c_i][i] += ...).  Scatters that several
+// kernels share (sample nodes, coalesce sources) accumulate with atomic adds.
+//
+// Vector-Jacobian products used here (all per node, in registers):
+//   * KBC collision f' = f^eq + (1 - beta gamma) df + beta (gamma - 2) ds with
+//     df = f - f^eq(f), ds = S df (shear part), dh = df - ds and
+//     gamma = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh>, <x|y> = sum x y / f^eq
+//     (Eqs. f_mirr, gamma_min_approx), differentiated through gamma and the
+//     weights 1/f^eq; gamma held at 2 in the LBGK mirror and in the 0/0 guard;
+//   * f^eq(rho, u) (Eq. feq_iso): d f^eq_i / d rho = f^eq_i / rho and
+//     d f^eq_i / d u_a = f^eq_i L_a(c_ia), L the log-derivative of the axis factor;
+//   * rho = sum f, u = j / rho;
+//   * non-equilibrium rescaling f -> f^eq + r (f - f^eq) and the four-point
+//     tensor interpolation (linear).
+#include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
+#include "device.cuh"
+#include "kernels.h"
+
+namespace lbmk {
+
+// Log-derivatives of the axis factors ghat(c) w.r.t. u (c = -1, 0, +1):
+// L(0) = A'/A, L(+1) = A'/A + B'/B, L(-1) = A'/A - B'/B with
+// A = 2 - s, A' = -3u/s, B = (2u + s)/(1 - u), B' = ((2 + 3u/s)(1 - u) + 2u + s)/(1 - u)^2.
+template <typename R>
+__device__ __forceinline__ void axis_logderiv(R u, const AxisEq<R>& e, R (&L)[3]) {
+  const R s = e.s;
+  const R A = R(1) + e.d[1];
+  const R dA = -R(3) * u / s;
+  const R om = R(1) - u;
+  const R dB = ((R(2) + R(3) * u / s) * om + R(2) * u + s) / (om * om);
+  const R la = dA / A, lb = dB / e.B;
+  L[1] = la;
+  L[2] = la + lb;
+  L[0] = la - lb;
+}
+
+// VJP of f^eq(rho, u) at (rho, u): given xbar (27) with fe_full_i = f^eq_i (full
+// value), returns rhobar = sum xbar_i fe_i / rho and ubar_a = sum xbar_i fe_i L_a.
+template <typename R>
+__device__ __forceinline__ void feq_vjp_rho_u(const R (&xbar)[27], const R (&fefull)[27], R rho, const R (&Lx)[3],
+                                              const R (&Ly)[3], const R (&Lz)[3], R& rhobar, R (&ubar)[3]) {
+  R sx[3] = {0, 0, 0}, sy[3] = {0, 0, 0}, sz[3] = {0, 0, 0}, tot = 0;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const R q = xbar[i] * fefull[i];
+    tot += q;
+    sx[CX(i) + 1] += q;
+    sy[CY(i) + 1] += q;
+    sz[CZ(i) + 1] += q;
+  });
+  rhobar = tot / rho;
+  ubar[0] = sx[0] * Lx[0] + sx[1] * Lx[1] + sx[2] * Lx[2];
+  ubar[1] = sy[0] * Ly[0] + sy[1] * Ly[1] + sy[2] * Ly[2];
+  ubar[2] = sz[0] * Lz[0] + sz[1] * Lz[1] + sz[2] * Lz[2];
+}
+
+// Forward quantities of f^eq at the state of f (deviation populations).
+template <typename R>
+struct EqState {
+  R rho_t, rho, u[3];
+  AxisEq<R> e[3];
+  R L[3][3];
+  R fe[27];      // f^eq - W (deviation)
+  R fefull[27];  // f^eq
+};
+
+template <typename R>
+__device__ __forceinline__ void eq_state_from_moments(R rho_t, R rho, R ux, R uy, R uz, EqState<R>& q,
+                                                      bool want_inverse) {
+  q.rho_t = rho_t;
+  q.rho = rho;
+  q.u[0] = ux, q.u[1] = uy, q.u[2] = uz;
+  for (int a = 0; a < 3; ++a) {
+    axis_eq<R>(q.u[a], q.e[a], want_inverse);
+    axis_logderiv<R>(q.u[a], q.e[a], q.L[a]);
+  }
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    q.fe[i] = R(WI(i)) * (rho_t + rho * qprod<i>(q.e[0], q.e[1], q.e[2]));
+    q.fefull[i] = R(WI(i)) + q.fe[i];
+  });
+}
+
+// fbar += J_feq(f)^T xbar, f^eq as a function of f through rho = sum f and j = sum c f.
+template <typename R>
+__device__ __forceinline__ void add_feq_f_vjp(const EqState<R>& q, const R (&xbar)[27], R (&fbar)[27]) {
+  R rb, ub[3];
+  feq_vjp_rho_u<R>(xbar, q.fefull, q.rho, q.L[0], q.L[1], q.L[2], rb, ub);
+  // u = j / rho: jbar = ubar / rho, rhobar -= ubar . u / rho
+  const R ir = R(1) / q.rho;
+  const R jb[3] = {ub[0] * ir, ub[1] * ir, ub[2] * ir};
+  rb -= (ub[0] * q.u[0] + ub[1] * q.u[1] + ub[2] * q.u[2]) * ir;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    fbar[i] += rb + R(CX(i)) * jb[0] + R(CY(i)) * jb[1] + R(CZ(i)) * jb[2];
+  });
+}
+
+// lam: in = adjoint of the post-collision state, out = adjoint of the
+// pre-collision state f (deviation populations, unchanged).
+template <typename R>
+__device__ void kbc_vjp(const R (&f)[27], R (&lam)[27], R beta, bool lbgk) {
+  R rho_t, rho, ux, uy, uz;
+  macro(f, rho_t, rho, ux, uy, uz);
+  EqState<R> q;
+  eq_state_from_moments<R>(rho_t, rho, ux, uy, uz, q, true);
+  R df[27];
+  R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const R d = f[i] - q.fe[i];
+    df[i] = d;
+    if constexpr (CX(i) != 0) pxx += d;
+    if constexpr (CY(i) != 0) pyy += d;
+    if constexpr (CZ(i) != 0) pzz += d;
+    if constexpr (CX(i) * CY(i) != 0) pxy += R(CX(i) * CY(i)) * d;
+    if constexpr (CX(i) * CZ(i) != 0) pxz += R(CX(i) * CZ(i)) * d;
+    if constexpr (CY(i) * CZ(i) != 0) pyz += R(CY(i) * CZ(i)) * d;
+  });
+  const R tr3 = (pxx + pyy + pzz) * R(1.0 / 3.0);
+  const R nxx = pxx - tr3, nyy = pyy - tr3, nzz = pzz - tr3;
+  R gamma = R(2), sh = 0, hh = 0;
+  bool use_gamma = false;
+  if (!lbgk) {
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
+      const R dh = df[i] - ds;
+      const R w = R(1) / q.fefull[i];
+      sh += ds * dh * w;
+      hh += dh * dh * w;
+    });
+    if (hh > R(1e-30) * rho * rho) {
+      use_gamma = true;
+      gamma = R(1) / beta - (R(2) - R(1) / beta) * sh / hh;
+    }
+  }
+  const R a = R(1) - beta * gamma, b = beta * (gamma - R(2));
+  // reverse of f' = fe + a df + b ds
+  R dfb[27], dsb[27], feb[27];
+  R G = 0;  // dL/dgamma = -beta lam . dh
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
+    dfb[i] = a * lam[i];
+    dsb[i] = b * lam[i];
+    feb[i] = lam[i];
+    G -= beta * lam[i] * (df[i] - ds);
+  });
+  if (use_gamma) {
+    const R c = R(2) - R(1) / beta;
+    const R Lsh = -G * c / hh, Lhh = G * c * sh / (hh * hh);
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
+      const R dh = df[i] - ds;
+      const R w = R(1) / q.fefull[i];
+      const R dhb = (Lsh * ds + R(2) * Lhh * dh) * w;
+      const R wb = Lsh * ds * dh + Lhh * dh * dh;
+      dsb[i] += Lsh * dh * w - dhb;
+      dfb[i] += dhb;
+      feb[i] -= wb * w * w;  // w = 1 / fe
+    });
+  }
+  // ds = S df: adjoint of the second moments, then df-bar += M^T Pbar
+  R Sx = 0, Sy = 0, Sz = 0, Exy = 0, Exz = 0, Eyz = 0;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int ax = CX(i) != 0, ay = CY(i) != 0, az = CZ(i) != 0;
+    if constexpr (ax + ay + az == 1) {
+      if constexpr (ax) Sx += dsb[i];
+      else if constexpr (ay) Sy += dsb[i];
+      else Sz += dsb[i];
+    } else if constexpr (ax + ay + az == 2) {
+      if constexpr (!az) Exy += R(CX(i) * CY(i)) * dsb[i];
+      else if constexpr (!ay) Exz += R(CX(i) * CZ(i)) * dsb[i];
+      else Eyz += R(CY(i) * CZ(i)) * dsb[i];
+    }
+  });
+  // face: ds = (1/3) Pxx - (1/6) Pyy - (1/6) Pzz (for x); edge: ds = c c P / 4
+  const R Pbxx = R(1.0 / 3.0) * Sx - R(1.0 / 6.0) * (Sy + Sz);
+  const R Pbyy = R(1.0 / 3.0) * Sy - R(1.0 / 6.0) * (Sx + Sz);
+  const R Pbzz = R(1.0 / 3.0) * Sz - R(1.0 / 6.0) * (Sx + Sy);
+  const R Pbxy = R(0.25) * Exy, Pbxz = R(0.25) * Exz, Pbyz = R(0.25) * Eyz;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    R v = dfb[i];
+    if constexpr (CX(i) != 0) v += Pbxx;
+    if constexpr (CY(i) != 0) v += Pbyy;
+    if constexpr (CZ(i) != 0) v += Pbzz;
+    if constexpr (CX(i) * CY(i) != 0) v += R(CX(i) * CY(i)) * Pbxy;
+    if constexpr (CX(i) * CZ(i) != 0) v += R(CX(i) * CZ(i)) * Pbxz;
+    if constexpr (CY(i) * CZ(i) != 0) v += R(CY(i) * CZ(i)) * Pbyz;
+    dfb[i] = v;
+    feb[i] -= v;  // df = f - fe
+  });
+  unroll<27>([&](auto I) { lam[decltype(I)::value] = dfb[decltype(I)::value]; });
+  add_feq_f_vjp<R>(q, feb, lam);
+}
+
+// ---------------------------------------------------------------------------
+// Pull sources, replicated from the forward pull for the scatter of the adjoint.
+template <typename R>
+__device__ __forceinline__ void push_adjoint(const PatchDev& p, R* __restrict__ lam_old, int x, int y, int z,
+                                             const R (&fb)[27]) {
+  const long long own = node_index(p, x, y, z);
+  const bool bulk = p.type[own] == T_BULK;
+  const int X[3] = {x, y, z};
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int c[3] = {CX(i), CY(i), CZ(i)};
+    int s[3];
+    bool bounce = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      s[a] = X[a] - c[a];
+      if (s[a] < 0 || s[a] >= p.dim[a]) {
+        if (bulk || p.span[a]) s[a] += s[a] < 0 ? p.dim[a] : -p.dim[a];
+        else bounce = true;  // not produced by the layouts the adjoint accepts
+      }
+    }
+    long long src = own;
+    int comp = 26 - i;
+    if (!bounce) {
+      src = node_index(p, s[0], s[1], s[2]);
+      comp = i;
+    }
+    atomicAdd(lam_old + (long long)comp * p.plane + src, fb[i]);
+  });
+}
+
+template <typename R>
+__device__ __forceinline__ void load_lam(const PatchDev& p, const R* __restrict__ lam, long long n, R (&l)[27]) {
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    l[i] = lam[(long long)i * p.plane + n];
+  });
+}
+
+// bulk stream-collide
+template <typename R>
+__global__ void __launch_bounds__(128) k_adj_sc(PatchDev p, const R* __restrict__ fin, const R* __restrict__ lam_new,
+                                                R* __restrict__ lam_old, R beta, int odd, int lbgk, int* status) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= p.dim[0]) return;
+  const long long own = node_index(p, x, y, z);
+  const uint8_t t = p.type[own];
+  if (!(t == T_BULK || t == T_BC || (t == T_D1 && odd))) return;
+  R f[27], l[27];
+  if (t == T_BULK) pull_bulk<R, R>(p, fin, x, y, z, f);
+  else pull_generic<R, R>(p, fin, x, y, z, f, status);
+  load_lam<R>(p, lam_new, own, l);
+  kbc_vjp<R>(f, l, beta, lbgk != 0);
+  push_adjoint<R>(p, lam_old, x, y, z, l);
+}
+
+__device__ __forceinline__ void node_xyz(const PatchDev& p, long long n, int& x, int& y, int& z) {
+  x = (int)(n % p.nxp);
+  y = (int)((n / p.nxp) % p.dim[1]);
+  z = (int)(n / ((long long)p.nxp * p.dim[1]));
+}
+
+template <typename R>
+__device__ __forceinline__ void pull_node(const PatchDev& p, const R* __restrict__ fin, int x, int y, int z,
+                                          R (&f)[27], int* status) {
+  if (p.type[node_index(p, x, y, z)] == T_BULK) pull_bulk<R, R>(p, fin, x, y, z, f);
+  else pull_generic<R, R>(p, fin, x, y, z, f, status);
+}
+
+// coalesce: parent twin <- collide_parent(f^eq + r (f_child - f^eq))
+template <typename R>
+__global__ void __launch_bounds__(128) k_adj_coalesce(PatchDev pc, const R* __restrict__ fin_c, PatchDev pp,
+                                                      const R* __restrict__ lam_new_p, R* __restrict__ lam_old_c,
+                                                      const uint32_t* __restrict__ cf_parent,
+                                                      const uint32_t* __restrict__ cf_child, long long n, R r,
+                                                      R beta_p, int lbgk, int* status) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int x, y, z;
+  node_xyz(pc, cf_child[k], x, y, z);
+  R f[27];
+  pull_node<R>(pc, fin_c, x, y, z, f, status);
+  R rho_t, rho, ux, uy, uz;
+  macro(f, rho_t, rho, ux, uy, uz);
+  EqState<R> q;
+  eq_state_from_moments<R>(rho_t, rho, ux, uy, uz, q, false);
+  R fc[27];
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    fc[i] = q.fe[i] + r * (f[i] - q.fe[i]);
+  });
+  R l[27];
+  load_lam<R>(pp, lam_new_p, cf_parent[k], l);
+  kbc_vjp<R>(fc, l, beta_p, lbgk != 0);
+  // fc = r f + (1 - r) fe(f)
+  R fb[27], xb[27];
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    fb[i] = r * l[i];
+    xb[i] = (R(1) - r) * l[i];
+  });
+  add_feq_f_vjp<R>(q, xb, fb);
+  push_adjoint<R>(pc, lam_old_c, x, y, z, fb);
+}
+
+// explode: child node <- collide_child(f^eq(rho~, u~) + neq~), (rho~, u~, neq~) the
+// tensor interpolation of the samples; scatters the adjoint of the 31 sample
+// values into sbar [31][ns].
+template <typename R>
+__global__ void __launch_bounds__(128) k_adj_explode(PatchDev pc, const R* __restrict__ lam_new_c,
+                                                     const uint32_t* __restrict__ ex_node,
+                                                     const uint32_t* __restrict__ ex_first,
+                                                     const uint8_t* __restrict__ ex_mask,
+                                                     const uint32_t* __restrict__ ex_sample, long long n,
+                                                     const R* __restrict__ smp, R* __restrict__ sbar, long long ns,
+                                                     R beta_c, int lbgk) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const R w4[4] = {R(-1.0 / 16.0), R(9.0 / 16.0), R(9.0 / 16.0), R(-1.0 / 16.0)};
+  const uint8_t mask = ex_mask[k];
+  const int cx = (mask & 1) ? 4 : 1, cy = (mask & 2) ? 4 : 1, cz = (mask & 4) ? 4 : 1;
+  const uint32_t j0 = ex_first[k];
+  R v[4] = {0, 0, 0, 0}, neq[27];
+  unroll<27>([&](auto I) { neq[decltype(I)::value] = R(0); });
+  uint32_t j = j0;
+  for (int kz = 0; kz < cz; ++kz)
+    for (int ky = 0; ky < cy; ++ky)
+      for (int kx = 0; kx < cx; ++kx) {
+        const R w = (cz == 4 ? w4[kz] : R(1)) * (cy == 4 ? w4[ky] : R(1)) * (cx == 4 ? w4[kx] : R(1));
+        const long long s = ex_sample[j++];
+        for (int c = 0; c < 4; ++c) v[c] += w * smp[c * ns + s];
+        unroll<27>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          neq[i] += w * smp[(4 + i) * ns + s];
+        });
+      }
+  EqState<R> q;
+  eq_state_from_moments<R>(v[0], R(1) + v[0], v[1], v[2], v[3], q, false);
+  R f[27];
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    f[i] = q.fe[i] + neq[i];
+  });
+  R l[27];
+  load_lam<R>(pc, lam_new_c, ex_node[k], l);
+  kbc_vjp<R>(f, l, beta_c, lbgk != 0);
+  // f = fe(rho, u) + neq: neq-bar = l; (rho-bar, u-bar) from fe directly
+  R rb, ub[3];
+  feq_vjp_rho_u<R>(l, q.fefull, q.rho, q.L[0], q.L[1], q.L[2], rb, ub);
+  const R vb[4] = {rb, ub[0], ub[1], ub[2]};  // rho~ enters as rho = 1 + rho~
+  j = j0;
+  for (int kz = 0; kz < cz; ++kz)
+    for (int ky = 0; ky < cy; ++ky)
+      for (int kx = 0; kx < cx; ++kx) {
+        const R w = (cz == 4 ? w4[kz] : R(1)) * (cy == 4 ? w4[ky] : R(1)) * (cx == 4 ? w4[kx] : R(1));
+        const long long s = ex_sample[j++];
+        for (int c = 0; c < 4; ++c) atomicAdd(sbar + c * ns + s, w * vb[c]);
+        unroll<27>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          atomicAdd(sbar + (4 + i) * ns + s, w * l[i]);
+        });
+      }
+}
+
+// samples: (rho~, u, factor (f - f^eq)) of the pulled state of a parent or child node
+template <typename R>
+__global__ void __launch_bounds__(128) k_adj_samples(PatchDev pp, const R* __restrict__ fin_p, R* __restrict__ lam_p,
+                                                     PatchDev pc, const R* __restrict__ fin_c, R* __restrict__ lam_c,
+                                                     const uint32_t* __restrict__ smp_node,
+                                                     const uint8_t* __restrict__ smp_kind, long long ns,
+                                                     const R* __restrict__ sbar, R rescale_p, int* status) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const bool par = smp_kind[s] == 0;
+  const PatchDev& q = par ? pp : pc;
+  int x, y, z;
+  node_xyz(q, smp_node[s], x, y, z);
+  R f[27];
+  pull_node<R>(q, par ? fin_p : fin_c, x, y, z, f, status);
+  const R factor = par ? rescale_p : R(1);
+  R rho_t, rho, ux, uy, uz;
+  macro(f, rho_t, rho, ux, uy, uz);
+  EqState<R> e;
+  eq_state_from_moments<R>(rho_t, rho, ux, uy, uz, e, false);
+  const R rb = sbar[s], ub[3] = {sbar[ns + s], sbar[2 * ns + s], sbar[3 * ns + s]};
+  R nb[27], fb[27], xb[27];
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    nb[i] = sbar[(4 + i) * ns + s];
+    fb[i] = factor * nb[i];
+    xb[i] = -factor * nb[i];
+  });
+  add_feq_f_vjp<R>(e, xb, fb);
+  // rho~ = sum f, u = j / rho
+  const R ir = R(1) / rho;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    fb[i] += rb + ((R(CX(i)) - ux) * ub[0] + (R(CY(i)) - uy) * ub[1] + (R(CZ(i)) - uz) * ub[2]) * ir;
+  });
+  push_adjoint<R>(q, par ? lam_p : lam_c, x, y, z, fb);
+}
+
+// Objective: kinetic energy 1/2 sum rho |u|^2 8^-level over owned nodes (a parent
+// owns its nodes outside every child's [a+1, b-1] box: classes BULK, BC, D0, D1,
+// INLET; a child owns its nodes of depth >= 2: BULK and BC).  Writes dKE/df and
+// FP64 partial sums of KE.
+template <typename R>
+__global__ void __launch_bounds__(256) k_adj_seed(PatchDev p, const R* __restrict__ fin, R* __restrict__ lam,
+                                                  double vw, int child_level, double* __restrict__ partial) {
+  double acc = 0;
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < p.plane;
+       n += (long long)gridDim.x * blockDim.x) {
+    const uint8_t t = p.type[n];
+    bool owned;
+    if (child_level) owned = (t == T_BULK || t == T_BC);
+    else owned = (t == T_BULK || t == T_BC || t == T_D0 || t == T_D1 || t == T_INLET);
+    R l[27];
+    if (owned) {
+      R f[27];
+      unroll<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        f[i] = fin[(long long)i * p.plane + n];
+      });
+      R rho_t, rho, ux, uy, uz;
+      macro(f, rho_t, rho, ux, uy, uz);
+      const double r = 1.0 + (double)rho_t;
+      const double u2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;
+      acc += vw * 0.5 * r * u2;
+      // d/df_i (1/2 |j|^2 / rho) = c_i . u - |u|^2 / 2
+      unroll<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        l[i] = (R)(vw * ((double)(CX(i) * ux + CY(i) * uy + CZ(i) * uz) - 0.5 * u2));
+      });
+    } else {
+      unroll<27>([&](auto I) { l[decltype(I)::value] = R(0); });
+    }
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      lam[(long long)i * p.plane + n] = l[i];
+    });
+  }
+  __shared__ double sh[8];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0;
+    for (int k = 0; k < n; ++k) s += partial[k];
+    *out = s;
+  }
+}
+
+// dJ/du0 at each node of a state f = f^eq(1, u0): sum_i lam_i f^eq_i L_a(c_ia), in FP64.
+template <typename R>
+__global__ void k_adj_grad_u0(PatchDev p, const R* __restrict__ fin, const R* __restrict__ lam, double* __restrict__ g) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= p.dim[0]) return;
+  const long long own = node_index(p, x, y, z);
+  const long long d = ((long long)z * p.dim[1] + y) * p.dim[0] + x;
+  const long long nd = (long long)p.dim[0] * p.dim[1] * p.dim[2];
+  const uint8_t t = p.type[own];
+  double out[3] = {0, 0, 0};
+  if (t != T_SKIP && t != T_SOLID && t != T_INLET) {
+    double f[27], l[27];
+    for (int i = 0; i < 27; ++i) {
+      f[i] = (double)fin[(long long)i * p.plane + own];
+      l[i] = (double)lam[(long long)i * p.plane + own];
+    }
+    double rho_t, rho, ux, uy, uz;
+    macro(f, rho_t, rho, ux, uy, uz);
+    EqState<double> q;
+    eq_state_from_moments<double>(rho_t, rho, ux, uy, uz, q, false);
+    double rb, ub[3];
+    feq_vjp_rho_u<double>(l, q.fefull, q.rho, q.L[0], q.L[1], q.L[2], rb, ub);
+    out[0] = ub[0], out[1] = ub[1], out[2] = ub[2];
+  }
+  for (int a = 0; a < 3; ++a) g[a * nd + d] = out[a];
+}
+
+// ---------------------------------------------------------------------------
+template <typename F>
+cudaError_t adj_dispatch(int storage, F&& f) {
+  if (storage == LBM_FP64) return f((double)0);
+  if (storage == LBM_FP32) return f((float)0);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adj_sc(int storage, const PatchDev& p, const void* fin, const void* lam_new, void* lam_old,
+                          double beta, int odd, int lbgk, int* status, cudaStream_t st) {
+  return adj_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    dim3 block(128), grid((p.dim[0] + 127) / 128, p.dim[1], p.dim[2]);
+    k_adj_sc<R><<<grid, block, 0, st>>>(p, (const R*)fin, (const R*)lam_new, (R*)lam_old, (R)beta, odd, lbgk,
+                                        status);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_adj_coalesce(int storage, const PatchDev& child, const void* fin_c, const PatchDev& parent,
+                                const void* lam_new_p, void* lam_old_c, const uint32_t* cf_parent,
+                                const uint32_t* cf_child, int64_t n, double r, double beta_p, int lbgk, int* status,
+                                cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  return adj_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    k_adj_coalesce<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(child, (const R*)fin_c, parent,
+                                                                   (const R*)lam_new_p, (R*)lam_old_c, cf_parent,
+                                                                   cf_child, n, (R)r, (R)beta_p, lbgk, status);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_adj_explode(int storage, const PatchDev& child, const void* lam_new_c, const uint32_t* ex_node,
+                               const uint32_t* ex_first, const uint8_t* ex_mask, const uint32_t* ex_sample, int64_t n,
+                               const void* smp, void* sbar, int64_t ns, double beta_c, int lbgk, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  return adj_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    k_adj_explode<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(child, (const R*)lam_new_c, ex_node, ex_first,
+                                                                  ex_mask, ex_sample, n, (const R*)smp, (R*)sbar, ns,
+                                                                  (R)beta_c, lbgk);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_adj_samples(int storage, const PatchDev& parent, const void* fin_p, void* lam_p,
+                               const PatchDev& child, const void* fin_c, void* lam_c, const uint32_t* smp_node,
+                               const uint8_t* smp_kind, int64_t ns, const void* sbar, double rescale_p, int* status,
+                               cudaStream_t st) {
+  if (ns == 0) return cudaSuccess;
+  return adj_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    k_adj_samples<R><<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(parent, (const R*)fin_p, (R*)lam_p, child,
+                                                                   (const R*)fin_c, (R*)lam_c, smp_node, smp_kind, ns,
+                                                                   (const R*)sbar, (R)rescale_p, status);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_adj_seed(int storage, const PatchDev& p, const void* fin, void* lam, double vol_weight,
+                            int child_level, double* partial, int blocks, cudaStream_t st) {
+  return adj_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    k_adj_seed<R><<<blocks, 256, 0, st>>>(p, (const R*)fin, (R*)lam, vol_weight, child_level, partial);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_sum_partials(const double* partial, int n, double* out, cudaStream_t st) {
+  k_sum_partials<<<1, 32, 0, st>>>(partial, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_grad_u0(int storage, const PatchDev& p, const void* fin, const void* lam, double* grad,
+                               cudaStream_t st) {
+  return adj_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    dim3 block(128), grid((p.dim[0] + 127) / 128, p.dim[1], p.dim[2]);
+    k_adj_grad_u0<R><<<grid, block, 0, st>>>(p, (const R*)fin, (const R*)lam, grad);
+    return cudaGetLastError();
+  });
+}
+
+}  // namespace lbmk

@@ -551,6 +551,217 @@ lbm_status lbm_diagnostics(lbm_grid_t g, double out[8]) {
 }
 
 // ---------------------------------------------------------------------------
+// Discrete adjoint (isothermal, periodic layouts).
+namespace {
+
+lbm_status adjoint_supported(lbm_grid* g) {
+  const lbm_desc& d = g->hg.desc;
+  if (g->hg.thermal || d.walls || d.inflow_axis >= 0 || !g->hg.solid.empty() || g->accel[0] != 0 ||
+      g->accel[1] != 0 || g->accel[2] != 0)
+    return fail(g, LBM_ERR_STATE,
+                "the adjoint covers isothermal layouts without walls, solids, inflow or body force");
+  if (d.storage != LBM_FP32 && d.storage != LBM_FP64) return fail(g, LBM_ERR_STATE, "adjoint: FP32 or FP64 storage");
+  return LBM_OK;
+}
+
+struct AdjLayout {
+  std::vector<size_t> lam_off;   // per patch, in the packed lambda (and in the second buffer)
+  std::vector<size_t> sbar_off;  // per patch (children), in the workspace
+  size_t lam_bytes = 0, second_off = 0, snap_off = 0, snap_bytes = 0, partial_off = 0, total = 0;
+};
+
+AdjLayout adjoint_layout(const lbm_grid* g, int K) {
+  AdjLayout a;
+  const size_t rb = g->hg.real_bytes;
+  size_t off = 0;
+  for (auto& p : g->hg.P) {
+    a.lam_off.push_back(off);
+    off += 27 * (size_t)p.plane * rb;
+  }
+  a.lam_bytes = off;
+  size_t w = 0;
+  auto take = [&](size_t b) {
+    size_t o = w;
+    w += (b + 255) / 256 * 256;
+    return o;
+  };
+  a.second_off = take(a.lam_bytes);
+  for (auto& p : g->hg.P) a.sbar_off.push_back(take(31 * p.smp_node.size() * rb));
+  a.snap_bytes = 0;
+  for (auto& p : g->hg.P) a.snap_bytes += 27 * (size_t)p.plane * g->hg.pop_bytes;
+  a.snap_off = take(a.snap_bytes * (size_t)K);
+  a.partial_off = take(sizeof(double) * (kDiagBlocks * g->hg.P.size() + 1));
+  a.total = w;
+  return a;
+}
+
+// Copies the state of every patch to/from a packed buffer (both buffers on restore).
+cudaError_t copy_state(lbm_grid* g, uint8_t* dst_or_src, bool save) {
+  cudaError_t e = cudaSuccess;
+  uint8_t* d = dst_or_src;
+  for (auto& p : g->hg.P) {
+    const size_t n = 27 * (size_t)p.plane * g->hg.pop_bytes;
+    if (save) {
+      if (!e) e = cudaMemcpyAsync(d, g->base + p.off_f[p.cur], n, cudaMemcpyDeviceToDevice, g->stream);
+    } else {
+      if (!e) e = cudaMemcpyAsync(g->base + p.off_f[p.cur], d, n, cudaMemcpyDeviceToDevice, g->stream);
+      if (!e) e = cudaMemcpyAsync(g->base + p.off_f[1 - p.cur], d, n, cudaMemcpyDeviceToDevice, g->stream);
+    }
+    d += n;
+  }
+  return e;
+}
+
+// Adjoint of instant k: lambda of the states after k -> lambda of the states before k.
+lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>& lcur, const AdjLayout& a,
+                           uint8_t* ws) {
+  HostGrid& hg = g->hg;
+  const int L = hg.nlev, storage = hg.desc.storage, lbgk = hg.desc.mirror_lbgk;
+  const size_t rb = hg.real_bytes;
+  auto lam_ptr = [&](int pi, int which) { return lam[which] + a.lam_off[pi]; };
+  std::vector<int> active;
+  for (int lev = 0; lev < L; ++lev) {
+    if (k % (1 << (L - 1 - lev))) continue;
+    for (size_t pi = 0; pi < hg.P.size(); ++pi)
+      if (hg.P[pi].level == lev) active.push_back((int)pi);
+  }
+  cudaError_t e = cudaSuccess;
+  for (int pi : active)
+    if (!e) e = cudaMemsetAsync(lam_ptr(pi, 1 - lcur[pi]), 0, 27 * (size_t)hg.P[pi].plane * rb, g->stream);
+  if (e) return cuda_check(g, e, "adjoint zero");
+  for (int pi : active) {
+    HostPatch& p = hg.P[pi];
+    const int lev = p.level;
+    const int s = k / (1 << (L - 1 - lev));
+    const bool parent_active = (s % 2) == 0;
+    const int odd = (lev > 0 && !parent_active) ? 1 : 0;
+    const lbmk::PatchDev pv = view(g, p);
+    if (!e)
+      e = lbmk::launch_adj_sc(storage, pv, g->base + p.off_f[p.cur], lam_ptr(pi, lcur[pi]), lam_ptr(pi, 1 - lcur[pi]),
+                              p.beta, odd, lbgk, status_ptr(g), g->stream);
+    for (int ci : p.kids) {
+      HostPatch& c = hg.P[ci];
+      if (!e)
+        e = lbmk::launch_adj_coalesce(storage, view(g, c), g->base + c.off_f[c.cur], pv, lam_ptr(pi, lcur[pi]),
+                                      lam_ptr(ci, 1 - lcur[ci]), at<uint32_t>(g, c.off_cf_parent),
+                                      at<uint32_t>(g, c.off_cf_child), (int64_t)c.cf_parent.size(),
+                                      2.0 * c.beta / p.beta, p.beta, lbgk, status_ptr(g), g->stream);
+    }
+    if (lev > 0 && parent_active) {
+      HostPatch& q = hg.P[p.parent];
+      const int qi = p.parent;
+      const lbmk::PatchDev qv = view(g, q);
+      uint8_t* sbar = ws + a.sbar_off[pi];
+      const int64_t ns = (int64_t)p.smp_node.size();
+      if (!e)
+        e = lbmk::launch_samples(storage, qv, g->base + q.off_f[q.cur], pv, g->base + p.off_f[p.cur],
+                                 at<uint32_t>(g, p.off_smp_node), at<uint8_t>(g, p.off_smp_kind), ns,
+                                 g->base + p.off_smp_val, q.beta / (2.0 * p.beta), status_ptr(g), g->stream);
+      if (!e && ns) e = cudaMemsetAsync(sbar, 0, 31 * (size_t)ns * rb, g->stream);
+      if (!e)
+        e = lbmk::launch_adj_explode(storage, pv, lam_ptr(pi, lcur[pi]), at<uint32_t>(g, p.off_ex_node),
+                                     at<uint32_t>(g, p.off_ex_first), at<uint8_t>(g, p.off_ex_mask),
+                                     at<uint32_t>(g, p.off_ex_sample), (int64_t)p.ex_node.size(),
+                                     g->base + p.off_smp_val, sbar, ns, p.beta, lbgk, g->stream);
+      if (!e)
+        e = lbmk::launch_adj_samples(storage, qv, g->base + q.off_f[q.cur], lam_ptr(qi, 1 - lcur[qi]), pv,
+                                     g->base + p.off_f[p.cur], lam_ptr(pi, 1 - lcur[pi]),
+                                     at<uint32_t>(g, p.off_smp_node), at<uint8_t>(g, p.off_smp_kind), ns, sbar,
+                                     q.beta / (2.0 * p.beta), status_ptr(g), g->stream);
+    }
+  }
+  if (e) return cuda_check(g, e, "adjoint instant");
+  for (int pi : active) lcur[pi] ^= 1;
+  return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_adjoint_workspace_bytes(lbm_grid_t g, int32_t K, size_t* lambda_bytes, size_t* workspace_bytes) {
+  if (!g || K < 1) return LBM_ERR_ARG;
+  if (lbm_status s = adjoint_supported(g)) return s;
+  AdjLayout a = adjoint_layout(g, K);
+  if (lambda_bytes) *lambda_bytes = a.lam_bytes;
+  if (workspace_bytes) *workspace_bytes = a.total;
+  return LBM_OK;
+}
+
+lbm_status lbm_adjoint_seed(lbm_grid_t g, void* lambda, void* workspace, double* ke_out) {
+  if (lbm_status s = check_bound(g)) return s;
+  if (lbm_status s = adjoint_supported(g)) return s;
+  if (!lambda || !workspace) return fail(g, LBM_ERR_ARG, "null lambda or workspace");
+  AdjLayout a = adjoint_layout(g, 1);
+  double* partial = reinterpret_cast<double*>(static_cast<uint8_t*>(workspace) + a.partial_off);
+  cudaError_t e = cudaSuccess;
+  for (size_t pi = 0; pi < g->hg.P.size() && !e; ++pi) {
+    HostPatch& p = g->hg.P[pi];
+    e = lbmk::launch_adj_seed(g->hg.desc.storage, view(g, p), g->base + p.off_f[p.cur],
+                              static_cast<uint8_t*>(lambda) + a.lam_off[pi], 1.0 / (double)(1LL << (3 * p.level)),
+                              p.level > 0 ? 1 : 0, partial + kDiagBlocks * pi, kDiagBlocks, g->stream);
+  }
+  double* dke = partial + kDiagBlocks * g->hg.P.size();
+  if (!e) e = lbmk::launch_sum_partials(partial, kDiagBlocks * (int)g->hg.P.size(), dke, g->stream);
+  double ke = 0;
+  if (!e) e = cudaMemcpyAsync(&ke, dke, sizeof ke, cudaMemcpyDeviceToHost, g->stream);
+  if (!e) e = cudaStreamSynchronize(g->stream);
+  if (e) return cuda_check(g, e, "lbm_adjoint_seed");
+  if (ke_out) *ke_out = ke;
+  return LBM_OK;
+}
+
+lbm_status lbm_adjoint_step(lbm_grid_t g, const void* ckpt, int32_t K, void* lambda_inout, void* workspace,
+                            size_t ws_bytes) {
+  if (lbm_status s = check_bound(g)) return s;
+  if (lbm_status s = adjoint_supported(g)) return s;
+  if (!ckpt || !lambda_inout || !workspace || K < 1) return fail(g, LBM_ERR_ARG, "bad adjoint arguments");
+  AdjLayout a = adjoint_layout(g, K);
+  if (ws_bytes < a.total) return fail(g, LBM_ERR_OOM, "adjoint workspace smaller than lbm_adjoint_workspace_bytes");
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  uint8_t* lam[2] = {static_cast<uint8_t*>(lambda_inout), ws + a.second_off};
+  std::vector<int> lcur(g->hg.P.size(), 0);
+  cudaError_t e = copy_state(g, const_cast<uint8_t*>(static_cast<const uint8_t*>(ckpt)), false);
+  if (e) return cuda_check(g, e, "adjoint restore");
+  // recompute the segment, one snapshot per coarse step
+  for (int s = 0; s < K; ++s) {
+    e = copy_state(g, ws + a.snap_off + (size_t)s * a.snap_bytes, true);
+    if (e) return cuda_check(g, e, "adjoint snapshot");
+    if (lbm_status st = lbm_step(g, 1)) return st;
+  }
+  const int KI = 1 << (g->hg.nlev - 1);
+  for (int s = K - 1; s >= 0; --s) {
+    uint8_t* snap = ws + a.snap_off + (size_t)s * a.snap_bytes;
+    for (int k = KI; k >= 1; --k) {
+      e = copy_state(g, snap, false);  // the state at the start of this coarse step
+      if (e) return cuda_check(g, e, "adjoint replay");
+      for (int kk = 1; kk < k; ++kk)
+        if (lbm_status st = run_instant(g, kk)) return st;
+      if (lbm_status st = adjoint_instant(g, k, lam, lcur, a, ws)) return st;
+    }
+  }
+  // lambda back into the caller's buffer; grid state back at the segment start
+  for (size_t pi = 0; pi < g->hg.P.size() && !e; ++pi)
+    if (lcur[pi] == 1)
+      e = cudaMemcpyAsync(lam[0] + a.lam_off[pi], lam[1] + a.lam_off[pi], 27 * (size_t)g->hg.P[pi].plane * g->hg.real_bytes,
+                          cudaMemcpyDeviceToDevice, g->stream);
+  if (!e) e = copy_state(g, ws + a.snap_off, false);
+  return cuda_check(g, e, "lbm_adjoint_step");
+}
+
+lbm_status lbm_adjoint_grad_u0(lbm_grid_t g, const void* lambda, int32_t patch, void* grad_u) {
+  if (lbm_status s = check_patch(g, patch)) return s;
+  if (lbm_status s = check_bound(g)) return s;
+  if (lbm_status s = adjoint_supported(g)) return s;
+  if (!lambda || !grad_u) return fail(g, LBM_ERR_ARG, "null lambda or gradient");
+  AdjLayout a = adjoint_layout(g, 1);
+  HostPatch& p = g->hg.P[patch];
+  return cuda_check(g,
+                    lbmk::launch_adj_grad_u0(g->hg.desc.storage, view(g, p), g->base + p.off_f[p.cur],
+                                             static_cast<const uint8_t*>(lambda) + a.lam_off[patch],
+                                             static_cast<double*>(grad_u), g->stream),
+                    "lbm_adjoint_grad_u0");
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free diagnostics.  Its partial sums live in this file-scope
 // device array instead of the grid's bound buffer.  Host code must not pass
 // the array's name to a kernel (on the host it is only a stand-in symbol);

@@ -48,6 +48,26 @@ cudaError_t launch_th_init(int storage, const PatchDev& p, void* f0, void* f1, v
 cudaError_t launch_th_moments(int storage, const PatchDev& p, const void* fin, const void* gin, void* rho, void* u,
                               void* T, void* gamma, int dtype, const ThermalLevel& L, cudaStream_t st);
 
+// Discrete adjoint kernels (adjoint.cu), FP32/FP64 storage, isothermal.
+cudaError_t launch_adj_sc(int storage, const PatchDev& p, const void* fin, const void* lam_new, void* lam_old,
+                          double beta, int odd, int lbgk, int* status, cudaStream_t st);
+cudaError_t launch_adj_coalesce(int storage, const PatchDev& child, const void* fin_c, const PatchDev& parent,
+                                const void* lam_new_p, void* lam_old_c, const uint32_t* cf_parent,
+                                const uint32_t* cf_child, int64_t n, double r, double beta_p, int lbgk, int* status,
+                                cudaStream_t st);
+cudaError_t launch_adj_explode(int storage, const PatchDev& child, const void* lam_new_c, const uint32_t* ex_node,
+                               const uint32_t* ex_first, const uint8_t* ex_mask, const uint32_t* ex_sample, int64_t n,
+                               const void* smp, void* sbar, int64_t ns, double beta_c, int lbgk, cudaStream_t st);
+cudaError_t launch_adj_samples(int storage, const PatchDev& parent, const void* fin_p, void* lam_p,
+                               const PatchDev& child, const void* fin_c, void* lam_c, const uint32_t* smp_node,
+                               const uint8_t* smp_kind, int64_t ns, const void* sbar, double rescale_p, int* status,
+                               cudaStream_t st);
+cudaError_t launch_adj_seed(int storage, const PatchDev& p, const void* fin, void* lam, double vol_weight,
+                            int child_level, double* partial, int blocks, cudaStream_t st);
+cudaError_t launch_sum_partials(const double* partial, int n, double* out, cudaStream_t st);
+cudaError_t launch_adj_grad_u0(int storage, const PatchDev& p, const void* fin, const void* lam, double* grad,
+                               cudaStream_t st);
+
 // Bulk tiles through TMA (tmap_in / tmap_out / tmap_wrap: CUtensorMaps, 128
 // bytes, of the source buffer with the load box, of the destination buffer with
 // the store box, and of the source buffer with the wrap box; tiles:

@@ -90,6 +90,10 @@ def lib():
             "lbm_checkpoint": [vp, vp, i32],
             "lbm_collide_nodes": [vp, vp, vp, i64, ctypes.c_double, dp, i32, i32, vp],
             "lbm_timing": [vp, i32],
+            "lbm_adjoint_workspace_bytes": [vp, i32, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
+            "lbm_adjoint_seed": [vp, vp, vp, dp],
+            "lbm_adjoint_step": [vp, vp, i32, vp, vp, ctypes.c_size_t],
+            "lbm_adjoint_grad_u0": [vp, vp, i32, vp],
             "lbm_timing_report": [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                   ctypes.POINTER(i64), dp, dp],
         }
@@ -311,6 +315,32 @@ class Grid:
         return [dict(kind=names[kind[k]], level=lev[k], launches=cnt[k], ms=ms[k], nodes=nodes[k])
                 for k in range(min(n.value, m))]
 
+    # ---- discrete adjoint
+    def adjoint_buffers(self, K: int):
+        """(lambda, workspace) device buffers for segments of K coarse steps."""
+        import torch
+        lb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib().lbm_adjoint_workspace_bytes(self.handle, int(K), ctypes.byref(lb), ctypes.byref(wb)),
+               self.handle)
+        dev = self.buffer.device
+        return (torch.empty(lb.value, dtype=torch.uint8, device=dev),
+                torch.empty(wb.value, dtype=torch.uint8, device=dev))
+
+    def adjoint_seed(self, lam, ws) -> float:
+        ke = ctypes.c_double()
+        _check(lib().lbm_adjoint_seed(self.handle, self._ptr(lam), self._ptr(ws), ctypes.byref(ke)), self.handle)
+        return ke.value
+
+    def adjoint_step(self, ckpt, K: int, lam, ws):
+        _check(lib().lbm_adjoint_step(self.handle, self._ptr(ckpt), int(K), self._ptr(lam), self._ptr(ws),
+                                      ws.numel()), self.handle)
+
+    def adjoint_grad_u0(self, lam, p: int):
+        import torch
+        out = torch.empty((3,) + self.shape(p), dtype=torch.float64, device=self.buffer.device)
+        _check(lib().lbm_adjoint_grad_u0(self.handle, self._ptr(lam), int(p), self._ptr(out)), self.handle)
+        return out
+
     def checkpoint_bytes(self) -> int:
         n = ctypes.c_size_t()
         _check(lib().lbm_checkpoint_bytes(self.handle, ctypes.byref(n)), self.handle)
@@ -335,3 +365,43 @@ def lbm_collide_nodes(f_in, beta: float, du=(0.0, 0.0, 0.0), lbgk: bool = False)
     if rc != LBM_OK:
         raise LbmError(rc, "lbm_collide_nodes")
     return f_out, gam
+
+
+def kinetic_energy_run(grid: "Grid", u0, n_steps: int, K: int):
+    """J = kinetic energy after n_steps coarse steps from f = f^eq(1, u0), as a
+    differentiable function of the initial velocity fields u0 (one CUDA
+    tensor [3][z][y][x] per patch).  The backward pass runs the library's
+    discrete adjoint with a checkpoint every K coarse steps."""
+    import torch
+
+    class _Run(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, *u0s):
+            dev = grid.buffer.device
+            for p, u in enumerate(u0s):
+                grid.init_equilibrium(p, torch.ones(grid.shape(p), dtype=torch.float64, device=dev),
+                                      u.detach().to(torch.float64))
+            nb = grid.checkpoint_bytes()
+            ckpts = []
+            done = 0
+            while done < n_steps:
+                ck = torch.empty(nb, dtype=torch.uint8, device=dev)
+                grid.checkpoint(ck, save=True)
+                k = min(K, n_steps - done)
+                ckpts.append((ck, k))
+                grid.step(k)
+                done += k
+            lam, ws = grid.adjoint_buffers(K)
+            ke = grid.adjoint_seed(lam, ws)
+            ctx.ckpts, ctx.lam, ctx.ws = ckpts, lam, ws
+            return torch.tensor(ke, dtype=torch.float64, device=dev)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            lam, ws = ctx.lam, ctx.ws
+            for ck, k in reversed(ctx.ckpts):
+                grid.adjoint_step(ck, k, lam, ws)
+            scale = gJ.to(torch.float64)
+            return tuple(grid.adjoint_grad_u0(lam, p) * scale for p in range(len(grid.patches)))
+
+    return _Run.apply(*u0)

@@ -1,0 +1,151 @@
+"""Discrete adjoint: the FP64 reference gradient (PyTorch autograd of a plain
+restatement of the refined step, pinned to the C oracle) and the CUDA adjoint
+(lbm_adjoint_step) against it and against finite differences."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from oracle import torch_oracle as T
+from paper_1608_06915_gb300 import inputs as I
+
+N, A, B, NU = 16, 4, 12, 0.02
+
+
+def small_case():
+    return I.tgv_case(n=N, box=(A, B), nu=NU)
+
+
+def initial_fields(seed=4):
+    modes = I.divfree_modes(n=N, kmax=3.0, rms=0.03, seed=seed)
+    z, y, x = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    _, uc = I.divfree_fields(x * 1.0, y * 1.0, z * 1.0, modes)
+    m = 2 * (B - A) + 1
+    z, y, x = np.meshgrid(*[np.arange(m) + 2 * A] * 3, indexing="ij")
+    _, uf = I.divfree_fields(x * 0.5, y * 0.5, z * 0.5, modes)
+    return uc, uf  # [3][z][y][x]
+
+
+def to_rows(u):
+    return torch.tensor(u.reshape(3, -1).T.copy(), dtype=torch.float64)
+
+
+# --- pins of the reference (CPU)
+def test_torch_oracle_forward_matches_c_oracle():
+    uc, uf = initial_fields()
+    m = T.TwoLevel(N, A, B, NU)
+    fc = T.feq(torch.ones(N ** 3, dtype=torch.float64), to_rows(uc))
+    ff = T.feq(torch.ones(m.m ** 3, dtype=torch.float64), to_rows(uf))
+    o = O.Oracle(small_case())
+    o.init_equilibrium(0, np.ones(uc.shape[1:]), uc)
+    o.init_equilibrium(1, np.ones(uf.shape[1:]), uf)
+    for _ in range(3):
+        fc, ff = m.step(fc, ff)
+        o.step(1)
+    gc = o.get_pop(0).reshape(27, -1).T
+    gf = o.get_pop(1).reshape(27, -1).T
+    mc = o.mask(0).ravel() == 1
+    assert np.max(np.abs(fc.numpy()[mc] - gc[mc])) < 1e-13
+    assert np.max(np.abs(ff.numpy() - gf)) < 1e-13
+
+
+def test_torch_oracle_gradient_matches_central_differences():
+    """autograd gradient vs FP64 central differences of the C oracle's forward."""
+    uc, uf = initial_fields()
+    m = T.TwoLevel(N, A, B, NU)
+    tc, tf = to_rows(uc).requires_grad_(True), to_rows(uf).requires_grad_(True)
+    ke, _, _ = m.run(tc, tf, 3)
+    ke.backward()
+    rng = np.random.default_rng(100)
+
+    def c_oracle_ke(duc, duf):
+        o = O.Oracle(small_case())
+        o.init_equilibrium(0, np.ones(uc.shape[1:]), uc + duc)
+        o.init_equilibrium(1, np.ones(uf.shape[1:]), uf + duf)
+        o.step(3)
+        fc = torch.tensor(o.get_pop(0).reshape(27, -1).T)
+        ff = torch.tensor(o.get_pop(1).reshape(27, -1).T)
+        return float(m.kinetic_energy(fc, ff))
+
+    for _ in range(2):
+        dc, df = rng.normal(size=uc.shape), rng.normal(size=uf.shape)
+        eps = 1e-6  # truncation error ~ eps^2 along white-noise directions (measured 2.5e-8 here)
+        fd = (c_oracle_ke(eps * dc, eps * df) - c_oracle_ke(-eps * dc, -eps * df)) / (2 * eps)
+        ad = float((tc.grad * to_rows(dc)).sum() + (tf.grad * to_rows(df)).sum())
+        assert abs(fd - ad) < 1e-6 * abs(ad), (fd, ad)
+
+
+# --- CUDA adjoint
+def _gpu_grad(storage, steps, K, uc, uf):
+    from paper_1608_06915_gb300 import lbm as L
+    g = L.Grid(small_case(), storage)
+    u0 = [torch.tensor(uc).cuda().requires_grad_(True), torch.tensor(uf).cuda().requires_grad_(True)]
+    J = L.kinetic_energy_run(g, u0, steps, K)
+    J.backward()
+    return float(J), u0[0].grad.cpu().numpy(), u0[1].grad.cpu().numpy()
+
+
+def _ref_grad(steps, uc, uf):
+    m = T.TwoLevel(N, A, B, NU)
+    tc, tf = to_rows(uc).requires_grad_(True), to_rows(uf).requires_grad_(True)
+    ke, _, _ = m.run(tc, tf, steps)
+    ke.backward()
+    return float(ke), tc.grad.numpy().T.reshape(uc.shape), tf.grad.numpy().T.reshape(uf.shape)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-10), ("fp32", 2e-4)])
+def test_cuda_adjoint_matches_reference_gradient(storage, tol):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    uc, uf = initial_fields()
+    jr, gcr, gfr = _ref_grad(6, uc, uf)
+    jg, gcg, gfg = _gpu_grad(storage, 6, 3, uc, uf)
+    scale = max(np.abs(gcr).max(), np.abs(gfr).max())
+    err = max(np.abs(gcg - gcr).max(), np.abs(gfg - gfr).max()) / scale
+    print("adjoint %s: J %.12e vs %.12e, max gradient error / max gradient %.3e" % (storage, jg, jr, err))
+    assert abs(jg - jr) < (1e-12 if storage == "fp64" else 1e-5) * abs(jr)
+    assert err < tol
+
+
+@pytest.mark.gpu
+def test_cuda_adjoint_full_case_finite_differences():
+    """64^3 box with [24,40]^3 refined, FP32, 40 coarse steps, checkpoints every 20:
+    directional derivatives along 4 seeded directions against central differences."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1608_06915_gb300 import lbm as L
+    case = I.adjoint_case()
+    g = L.Grid(case, "fp32")
+    modes = I.divfree_modes(n=64, kmax=4.0, rms=0.03, seed=4)
+    u0 = []
+    for info in g.patches:
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        u0.append(torch.tensor(I.divfree_fields(x, y, z, modes)[1]).cuda())
+    steps, K = 40, 20
+    x0 = [u.clone().requires_grad_(True) for u in u0]
+    J = L.kinetic_energy_run(g, x0, steps, K)
+    J.backward()
+    grads = [u.grad for u in x0]
+    norm = math.sqrt(sum(float((u * u).sum()) for u in u0))
+    worst = 0.0
+    for seed in range(100, 104):
+        # smooth seeded directions (divergence-free Fourier fields, |k| <= 4)
+        dm = I.divfree_modes(n=64, kmax=4.0, rms=0.03, seed=seed)
+        d = []
+        for info in g.patches:
+            x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+            d.append(torch.tensor(I.divfree_fields(x, y, z, dm)[1]).cuda())
+        dn = math.sqrt(sum(float((v * v).sum()) for v in d))
+        d = [v / dn for v in d]
+        eps = 1e-3 * norm
+        jp = float(L.kinetic_energy_run(g, [u + eps * v for u, v in zip(u0, d)], steps, K))
+        jm = float(L.kinetic_energy_run(g, [u - eps * v for u, v in zip(u0, d)], steps, K))
+        fd = (jp - jm) / (2 * eps)
+        ad = sum(float((gr * v).sum()) for gr, v in zip(grads, d))
+        rel = abs(fd - ad) / abs(ad)
+        worst = max(worst, rel)
+        print("direction %d: finite difference %.9e adjoint %.9e rel %.2e" % (seed, fd, ad, rel))
+    assert worst < 1e-3, worst
