@@ -342,18 +342,26 @@ def cuda_arm(args):
     # warm-up
     g.step(args.warmup)
     barrier()
-    # timed region: K coarse steps, events on the grid's stream, per-launch events inside
+    # timed region: K coarse steps replayed as CUDA graphs, events on the grid's stream
     clocks = Clocks(local) if rank == 0 else None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g.timing(True)
     e0.record(stream)
     g.step(args.steps)
     e1.record(stream)
+    barrier()
+    # the same K steps again, every kernel launched directly between its own
+    # pair of events: the per-kernel durations of the roofline
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.timing(True)
+    e2.record(stream)
+    g.step(args.steps)
+    e3.record(stream)
     barrier()
     report = g.timing_report()
     g.timing(False)
     clk = clocks.stop() if clocks else None
     t = e0.elapsed_time(e1) / 1e3
+    t_instr = e2.elapsed_time(e3) / 1e3
     tt = torch.tensor([t], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -401,6 +409,8 @@ def cuda_arm(args):
                     dtype=DTYPE[args.storage], data="synthetic",
                     config=dict(workload=desc, storage=args.storage, node_updates_per_coarse_step=nup,
                                 parallelism="replicas" if world > 1 else "single GPU",
+                                launch="one CUDA graph per coarse step",
+                                direct_launch_ms_per_step=1e3 * t_instr / args.steps,
                                 l2="no flush: working set %.2f GB > %.0f MB L2" % (ws / 1e9, L2_BYTES / 1e6)),
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clk,
                     adjoint_forward_ratio=adj,

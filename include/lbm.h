@@ -148,6 +148,14 @@ lbm_status lbm_init_equilibrium(lbm_grid_t g, int32_t patch, const void* rho, co
  * Sec. III.C recursively, level l taking 2^l steps.  Asynchronous. */
 lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps);
 
+/* lbm_step replays each coarse step as a CUDA graph, one per buffer parity of
+ * level 0, captured on a private stream the first time that parity comes up
+ * (the first step after lbm_grid_bind launches directly).  Replays use the
+ * bound stream.  Binding again or changing the force drops the graphs; steps
+ * taken while lbm_timing is on launch directly.  enable = 0 launches every
+ * kernel directly.  Default: on.  Returns LBM_ERR_ARG for a null grid. */
+lbm_status lbm_graphs(lbm_grid_t g, int32_t enable);
+
 /* Macroscopic fields of a patch's current populations: rho, u = j/rho + du/2
  * (du of the level's body force, Sec. III.A), T (thermal, else T0) and the
  * stabiliser gamma that Eq. gamma_min_approx gives for the stored state.

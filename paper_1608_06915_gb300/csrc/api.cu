@@ -48,7 +48,24 @@ struct lbm_grid {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
+  // CUDA graphs of one coarse step, keyed by the buffer index of every patch;
+  // the first step after binding runs directly, so that capture finds every
+  // kernel loaded and configured
+  bool graphs = true;
+  bool stepped = false;
+  cudaStream_t cap_stream = nullptr;
+  struct StepGraph {
+    std::vector<uint8_t> cur;
+    cudaGraphExec_t exec;
+  };
+  std::vector<StepGraph> gcache;
+  void drop_graphs() {
+    for (auto& x : gcache) cudaGraphExecDestroy(x.exec);
+    gcache.clear();
+  }
   ~lbm_grid() {
+    drop_graphs();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto e : pool) cudaEventDestroy(e);
   }
 };
@@ -359,6 +376,8 @@ lbm_status lbm_grid_bind(lbm_grid_t g, void* dev_ptr, size_t bytes, void* cuda_s
   if (!g || !dev_ptr) return fail(g, LBM_ERR_ARG, "null argument");
   if (bytes < g->need) return fail(g, LBM_ERR_OOM, "bound buffer smaller than lbm_grid_bytes");
   if (reinterpret_cast<uintptr_t>(dev_ptr) % 256) return fail(g, LBM_ERR_ARG, "device buffer not 256-byte aligned");
+  g->drop_graphs();  // the captured launches name the previous buffer and stream
+  g->stepped = false;
   g->base = static_cast<uint8_t*>(dev_ptr);
   g->bytes = bytes;
   g->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -467,13 +486,81 @@ lbm_status lbm_init_equilibrium(lbm_grid_t g, int32_t patch, const void* rho, co
                     "lbm_init_equilibrium");
 }
 
+namespace {
+
+lbm_status coarse_step_eager(lbm_grid* g) {
+  const int K = 1 << (g->hg.nlev - 1);
+  for (int k = 1; k <= K; ++k)
+    if (lbm_status s = run_instant(g, k)) return s;
+  return LBM_OK;
+}
+
+constexpr size_t kMaxStepGraphs = 8;
+
+std::vector<uint8_t> cur_key(const lbm_grid* g) {
+  std::vector<uint8_t> k;
+  for (auto& p : g->hg.P) k.push_back((uint8_t)p.cur);
+  return k;
+}
+
+// Captures one coarse step from the current buffer indices; the host-side
+// indices are put back afterwards (capture launches nothing).
+lbm_status capture_step(lbm_grid* g, const std::vector<uint8_t>& key, cudaGraphExec_t* out) {
+  if (!g->cap_stream) {
+    if (cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking))
+      return cuda_check(g, e, "capture stream");
+  }
+  cudaStream_t keep = g->stream;
+  g->stream = g->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed);
+  lbm_status st = e ? LBM_OK : coarse_step_eager(g);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = e ? cudaSuccess : cudaStreamEndCapture(g->cap_stream, &graph);
+  g->stream = keep;
+  for (size_t i = 0; i < g->hg.P.size(); ++i) g->hg.P[i].cur = key[i];
+  if (e) return cuda_check(g, e, "cudaStreamBeginCapture");
+  if (st || e2) {
+    if (graph) cudaGraphDestroy(graph);
+    return st ? st : cuda_check(g, e2, "cudaStreamEndCapture");
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  return cuda_check(g, e, "cudaGraphInstantiate");
+}
+
+}  // namespace
+
 lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps) {
   if (lbm_status s = check_bound(g)) return s;
   if (n_coarse_steps < 0) return fail(g, LBM_ERR_ARG, "negative step count");
-  const int K = 1 << (g->hg.nlev - 1);
-  for (int64_t n = 0; n < n_coarse_steps; ++n)
-    for (int k = 1; k <= K; ++k)
-      if (lbm_status s = run_instant(g, k)) return s;
+  const int L = g->hg.nlev, K = 1 << (L - 1);
+  for (int64_t n = 0; n < n_coarse_steps; ++n) {
+    if (!g->graphs || g->timing || !g->stepped) {
+      if (lbm_status s = coarse_step_eager(g)) return s;
+      g->stepped = true;
+      continue;
+    }
+    const std::vector<uint8_t> key = cur_key(g);
+    cudaGraphExec_t exec = nullptr;
+    for (auto& x : g->gcache)
+      if (x.cur == key) exec = x.exec;
+    if (!exec) {
+      if (g->gcache.size() >= kMaxStepGraphs) g->drop_graphs();
+      if (lbm_status s = capture_step(g, key, &exec)) return s;
+      g->gcache.push_back({key, exec});
+    }
+    if (cudaError_t e = cudaGraphLaunch(exec, g->stream)) return cuda_check(g, e, "cudaGraphLaunch");
+    // the buffer flips of the replayed step
+    for (auto& p : g->hg.P)
+      if ((K >> (L - 1 - p.level)) & 1) p.cur ^= 1;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_graphs(lbm_grid_t g, int32_t enable) {
+  if (!g) return LBM_ERR_ARG;
+  g->graphs = enable != 0;
+  if (!g->graphs) g->drop_graphs();
   return LBM_OK;
 }
 
@@ -595,8 +682,9 @@ AdjLayout adjoint_layout(const lbm_grid* g, int K) {
   return a;
 }
 
-// Copies the state of every patch to/from a packed buffer (both buffers on restore).
-cudaError_t copy_state(lbm_grid* g, uint8_t* dst_or_src, bool save) {
+// Copies the state of every patch to/from a packed buffer (restore: the current
+// buffer only unless both are asked for).
+cudaError_t copy_state(lbm_grid* g, uint8_t* dst_or_src, bool save, bool both = true) {
   cudaError_t e = cudaSuccess;
   uint8_t* d = dst_or_src;
   for (auto& p : g->hg.P) {
@@ -605,11 +693,18 @@ cudaError_t copy_state(lbm_grid* g, uint8_t* dst_or_src, bool save) {
       if (!e) e = cudaMemcpyAsync(d, g->base + p.off_f[p.cur], n, cudaMemcpyDeviceToDevice, g->stream);
     } else {
       if (!e) e = cudaMemcpyAsync(g->base + p.off_f[p.cur], d, n, cudaMemcpyDeviceToDevice, g->stream);
-      if (!e) e = cudaMemcpyAsync(g->base + p.off_f[1 - p.cur], d, n, cudaMemcpyDeviceToDevice, g->stream);
+      if (!e && both) e = cudaMemcpyAsync(g->base + p.off_f[1 - p.cur], d, n, cudaMemcpyDeviceToDevice, g->stream);
     }
     d += n;
   }
   return e;
+}
+
+// Patches active at instant k of a coarse step.
+void flip_instant(lbm_grid* g, int k) {
+  const int L = g->hg.nlev;
+  for (auto& p : g->hg.P)
+    if (k % (1 << (L - 1 - p.level)) == 0) p.cur ^= 1;
 }
 
 // Adjoint of instant k: lambda of the states after k -> lambda of the states before k.
@@ -730,11 +825,24 @@ lbm_status lbm_adjoint_step(lbm_grid_t g, const void* ckpt, int32_t K, void* lam
   const int KI = 1 << (g->hg.nlev - 1);
   for (int s = K - 1; s >= 0; --s) {
     uint8_t* snap = ws + a.snap_off + (size_t)s * a.snap_bytes;
+    // have: the buffers hold the state after `have` instants of this coarse step;
+    // last: the instant executed most recently (its previous states are still in
+    // the other buffers of the patches it wrote)
+    int have = -1, last = -1;
     for (int k = KI; k >= 1; --k) {
-      e = copy_state(g, snap, false);  // the state at the start of this coarse step
-      if (e) return cuda_check(g, e, "adjoint replay");
-      for (int kk = 1; kk < k; ++kk)
-        if (lbm_status st = run_instant(g, kk)) return st;
+      if (have == k && last == k) {
+        flip_instant(g, k);
+        have = k - 1;
+        last = -1;
+      }
+      if (have != k - 1) {
+        e = copy_state(g, snap, false, false);  // the state at the start of this coarse step
+        if (e) return cuda_check(g, e, "adjoint replay");
+        for (int kk = 1; kk < k; ++kk)
+          if (lbm_status st = run_instant(g, kk)) return st;
+        have = k - 1;
+        last = k - 1;
+      }
       if (lbm_status st = adjoint_instant(g, k, lam, lcur, a, ws)) return st;
     }
   }
@@ -820,8 +928,10 @@ lbm_status lbm_diagnostics_noalloc(lbm_grid_t g, double out[8]) {
 
 lbm_status lbm_force(lbm_grid_t g, const double* accel0, double* drag_out) {
   if (!g) return LBM_ERR_ARG;
-  if (accel0)
+  if (accel0) {
     for (int a = 0; a < 3; ++a) g->accel[a] = accel0[a];
+    g->drop_graphs();  // the force is baked into the captured launches
+  }
   if (drag_out) return fail(g, LBM_ERR_STATE, "drag not available in this build");
   return LBM_OK;
 }

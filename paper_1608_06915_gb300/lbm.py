@@ -90,6 +90,7 @@ def lib():
             "lbm_checkpoint": [vp, vp, i32],
             "lbm_collide_nodes": [vp, vp, vp, i64, ctypes.c_double, dp, i32, i32, vp],
             "lbm_timing": [vp, i32],
+            "lbm_graphs": [vp, i32],
             "lbm_adjoint_workspace_bytes": [vp, i32, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
             "lbm_adjoint_seed": [vp, vp, vp, dp],
             "lbm_adjoint_step": [vp, vp, i32, vp, vp, ctypes.c_size_t],
@@ -300,6 +301,9 @@ class Grid:
     def set_force(self, accel0):
         a = (ctypes.c_double * 3)(*[float(v) for v in accel0])
         _check(lib().lbm_force(self.handle, a, None), self.handle)
+
+    def graphs(self, enable: bool):
+        _check(lib().lbm_graphs(self.handle, 1 if enable else 0), self.handle)
 
     def timing(self, enable: bool):
         _check(lib().lbm_timing(self.handle, 1 if enable else 0), self.handle)

@@ -279,3 +279,28 @@ def test_rbc_small_fp32_temperature():
     eT = (num / den) ** 0.5
     print("rbc fp32 after 20 steps: rel L2 rho %.3e u %.3e (T - T0) %.3e" % (er, eu, eT))
     assert er < 1e-5 and eu < 1e-4 and eT < 1e-4
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16s"])
+def test_graph_replay_matches_direct_launches(storage):
+    """Coarse steps replayed as CUDA graphs (both level-0 parities, a force
+    change that drops them, per-launch timing that bypasses them) give the same
+    bits as launching every kernel directly."""
+    import torch
+    case = I.channel_small_case()
+    case["accel0"] = (1e-5, 0, 0)
+    fields = lambda x, y, z, p, info: I.channel_fields(case, info["level"], info["org"], info["dim"])
+    ga, _ = twin(case, storage, fields, oracle=False)
+    gb, _ = twin(case, storage, fields, oracle=False)
+    gb.graphs(False)
+    for g in (ga, gb):
+        g.step(5)
+        g.set_force((2e-5, 0, 0))
+        g.step(3)
+        g.timing(True)
+        g.step(1)
+        g.timing(False)
+        g.step(4)
+    torch.cuda.synchronize()
+    for p in range(len(ga.patches)):
+        assert torch.equal(ga.get_populations(p), gb.get_populations(p)), p
