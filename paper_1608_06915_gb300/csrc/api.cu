@@ -287,8 +287,7 @@ lbm_status run_instant(lbm_grid* g, int k) {
                         timed(g, 3, lev, (double)p.ex_node.size(),
                               [&] {
                                 return lbmk::launch_explode(storage, pv, fout, at<uint32_t>(g, p.off_ex_node),
-                                                            at<uint32_t>(g, p.off_ex_first),
-                                                            at<uint8_t>(g, p.off_ex_mask),
+                                                            at<uint32_t>(g, p.off_ex_first), p.ex_class,
                                                             at<uint32_t>(g, p.off_ex_sample),
                                                             (int64_t)p.ex_node.size(), g->base + p.off_smp_val,
                                                             (int64_t)p.smp_node.size(), p.beta, F, lbgk, g->stream);

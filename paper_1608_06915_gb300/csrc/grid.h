@@ -61,6 +61,7 @@ struct HostPatch {
   std::vector<uint32_t> ex_first;   // sample list offsets, size ex_node.size() + 1
   std::vector<uint8_t> ex_mask;     // bit a: off-lattice along axis a
   std::vector<uint32_t> ex_sample;  // sample ids
+  uint32_t ex_class[9] = {};        // entries are grouped by mask: class m is [ex_class[m], ex_class[m + 1])
   std::vector<uint32_t> smp_node;   // per sample: node index in parent or child
   std::vector<uint8_t> smp_kind;    // per sample: S_PARENT / S_CHILD
   std::vector<uint32_t> cf_parent;  // coalesce: parent twin node

@@ -153,30 +153,38 @@ cudaError_t launch_samples(int storage, const PatchDev& parent, const void* fin_
 // Child twins and reconstruction nodes: tensor four-point Lagrange (Eq. interp,
 // weights (-1, 9, 9, -1)/16) of rho, u and the non-equilibrium part over the
 // off-lattice axes; f = f^eq(rho~, u~) + neq~; then collide.
-template <typename S, typename R, bool FORCE>
-__global__ void __launch_bounds__(128) k_explode(PatchDev pc, S* __restrict__ fout_c,
-                                                 const uint32_t* __restrict__ ex_node,
-                                                 const uint32_t* __restrict__ ex_first,
-                                                 const uint8_t* __restrict__ ex_mask,
-                                                 const uint32_t* __restrict__ ex_sample, long long n,
-                                                 const R* __restrict__ smp, long long ns, R beta_c, R dux, R duy,
-                                                 R duz, int lbgk) {
-  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const R w4[4] = {R(-1.0 / 16.0), R(9.0 / 16.0), R(9.0 / 16.0), R(-1.0 / 16.0)};
-  const uint8_t mask = ex_mask[k];
-  const int cx = (mask & 1) ? 4 : 1, cy = (mask & 2) ? 4 : 1, cz = (mask & 4) ? 4 : 1;
-  uint32_t j = ex_first[k];
-  R rho_t = 0, ux = 0, uy = 0, uz = 0;
-  R f[27];
+//
+// The entries come grouped by off-lattice mask and every thread block takes
+// entries of one group, so the stencil (1, 4, 16 or 64 samples) is a
+// compile-time shape: no divergence, and the sample indices of a row of the
+// stencil are fetched together.
+struct ExClasses {
+  uint32_t start[9];   // entries of mask m: [start[m], start[m + 1])
+  uint32_t block0[9];  // first thread block of mask m
+};
+
+__host__ __device__ constexpr double lagrange4(int k) { return (k == 1 || k == 2) ? 9.0 / 16.0 : -1.0 / 16.0; }
+
+template <int M, typename R>
+__device__ __forceinline__ void interpolate(const uint32_t* __restrict__ ex_sample, uint32_t j,
+                                            const R* __restrict__ smp, long long ns, R& rho_t, R& ux, R& uy, R& uz,
+                                            R (&f)[27]) {
+  constexpr int cx = (M & 1) ? 4 : 1, cy = (M & 2) ? 4 : 1, cz = (M & 4) ? 4 : 1;
+  rho_t = ux = uy = uz = R(0);
   unroll<27>([&](auto I) { f[decltype(I)::value] = R(0); });
+#pragma unroll 1
   for (int kz = 0; kz < cz; ++kz) {
-    const R wz = cz == 4 ? w4[kz] : R(1);
+    const R wz = cz == 4 ? ((kz == 1 || kz == 2) ? R(9.0 / 16.0) : R(-1.0 / 16.0)) : R(1);
+    uint32_t sid[cy * cx];
+#pragma unroll
+    for (int q = 0; q < cy * cx; ++q) sid[q] = __ldg(ex_sample + j + kz * cy * cx + q);
+#pragma unroll
     for (int ky = 0; ky < cy; ++ky) {
-      const R wyz = wz * (cy == 4 ? w4[ky] : R(1));
+      const R wyz = wz * (cy == 4 ? R(lagrange4(ky)) : R(1));
+#pragma unroll
       for (int kx = 0; kx < cx; ++kx) {
-        const R w = wyz * (cx == 4 ? w4[kx] : R(1));
-        const long long s = ex_sample[j++];
+        const R w = wyz * (cx == 4 ? R(lagrange4(kx)) : R(1));
+        const long long s = sid[ky * cx + kx];
         rho_t += w * __ldg(smp + s);
         ux += w * __ldg(smp + ns + s);
         uy += w * __ldg(smp + 2 * ns + s);
@@ -188,6 +196,17 @@ __global__ void __launch_bounds__(128) k_explode(PatchDev pc, S* __restrict__ fo
       }
     }
   }
+}
+
+template <int M, typename S, typename R, bool FORCE>
+__device__ __forceinline__ void explode_node(const PatchDev& pc, S* __restrict__ fout_c,
+                                             const uint32_t* __restrict__ ex_node,
+                                             const uint32_t* __restrict__ ex_first,
+                                             const uint32_t* __restrict__ ex_sample, uint32_t k,
+                                             const R* __restrict__ smp, long long ns, R beta_c, R dux, R duy,
+                                             R duz, int lbgk) {
+  R rho_t, ux, uy, uz, f[27];
+  interpolate<M, R>(ex_sample, __ldg(ex_first + k), smp, ns, rho_t, ux, uy, uz, f);
   R fe[27];
   feq_dev(rho_t, R(1) + rho_t, ux, uy, uz, fe);
   unroll<27>([&](auto I) {
@@ -195,25 +214,63 @@ __global__ void __launch_bounds__(128) k_explode(PatchDev pc, S* __restrict__ fo
     f[i] += fe[i];
   });
   kbc_collide<R, FORCE ? 7 : 0>(f, beta_c, dux, duy, duz, lbgk != 0);
-  store_node<S, R>(pc, fout_c, ex_node[k], f);
+  store_node<S, R>(pc, fout_c, __ldg(ex_node + k), f);
+}
+
+template <typename S, typename R, bool FORCE>
+__global__ void __launch_bounds__(128) k_explode(PatchDev pc, S* __restrict__ fout_c,
+                                                 const uint32_t* __restrict__ ex_node,
+                                                 const uint32_t* __restrict__ ex_first, const ExClasses cls,
+                                                 const uint32_t* __restrict__ ex_sample, const R* __restrict__ smp,
+                                                 long long ns, R beta_c, R dux, R duy, R duz, int lbgk) {
+  int m = 0;
+#pragma unroll
+  for (int c = 1; c < 8; ++c)
+    if (blockIdx.x >= cls.block0[c]) m = c;
+  const uint32_t k = cls.start[m] + (blockIdx.x - cls.block0[m]) * blockDim.x + threadIdx.x;
+  if (k >= cls.start[m + 1]) return;
+#define LBM_EXPLODE_CASE(MM)                                                                                 \
+  case MM:                                                                                                  \
+    explode_node<MM, S, R, FORCE>(pc, fout_c, ex_node, ex_first, ex_sample, k, smp, ns, beta_c, dux, duy, duz, \
+                                  lbgk);                                                                     \
+    break;
+  switch (m) {
+    LBM_EXPLODE_CASE(0)
+    LBM_EXPLODE_CASE(1)
+    LBM_EXPLODE_CASE(2)
+    LBM_EXPLODE_CASE(3)
+    LBM_EXPLODE_CASE(4)
+    LBM_EXPLODE_CASE(5)
+    LBM_EXPLODE_CASE(6)
+    LBM_EXPLODE_CASE(7)
+  }
+#undef LBM_EXPLODE_CASE
 }
 
 cudaError_t launch_explode(int storage, const PatchDev& child, void* fout_child, const uint32_t* ex_node,
-                           const uint32_t* ex_first, const uint8_t* ex_mask, const uint32_t* ex_sample, int64_t n,
-                           const void* smp_val, int64_t ns, double beta_child, const Force& Fc, int lbgk,
+                           const uint32_t* ex_first, const uint32_t ex_class[9], const uint32_t* ex_sample,
+                           int64_t n, const void* smp_val, int64_t ns, double beta_child, const Force& Fc, int lbgk,
                            cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  ExClasses cls;
+  uint32_t blocks = 0;
+  for (int m = 0; m < 9; ++m) {
+    cls.start[m] = ex_class[m];
+    cls.block0[m] = blocks;
+    if (m < 8) blocks += (ex_class[m + 1] - ex_class[m] + 127) / 128;
+  }
+  if (ex_class[8] != (uint32_t)n) return cudaErrorInvalidValue;
   return dispatch(storage, [&](auto ts, auto tr) {
     using S = typename decltype(ts)::type;
     using R = typename decltype(tr)::type;
-    dim3 block(128), grid((unsigned)((n + 127) / 128));
+    dim3 block(128), grid(blocks);
     if (Fc.on())
-      k_explode<S, R, true><<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, ex_first, ex_mask, ex_sample,
-                                                     n, (const R*)smp_val, ns, (R)beta_child, (R)Fc.du[0],
+      k_explode<S, R, true><<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, ex_first, cls, ex_sample,
+                                                     (const R*)smp_val, ns, (R)beta_child, (R)Fc.du[0],
                                                      (R)Fc.du[1], (R)Fc.du[2], lbgk);
     else
-      k_explode<S, R, false><<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, ex_first, ex_mask, ex_sample,
-                                                      n, (const R*)smp_val, ns, (R)beta_child, R(0), R(0), R(0),
+      k_explode<S, R, false><<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, ex_first, cls, ex_sample,
+                                                      (const R*)smp_val, ns, (R)beta_child, R(0), R(0), R(0),
                                                       lbgk);
     return cudaGetLastError();
   });

@@ -91,9 +91,10 @@ cudaError_t launch_samples(int storage, const PatchDev& parent, const void* fin_
                            const void* fin_child, const uint32_t* smp_node, const uint8_t* smp_kind, int64_t ns,
                            void* smp_val, double rescale_parent, int* status, cudaStream_t st);
 
+// ex_class[m] .. ex_class[m + 1]: the entries with off-lattice mask m (host array)
 cudaError_t launch_explode(int storage, const PatchDev& child, void* fout_child, const uint32_t* ex_node,
-                           const uint32_t* ex_first, const uint8_t* ex_mask, const uint32_t* ex_sample, int64_t n,
-                           const void* smp_val, int64_t ns, double beta_child, const Force& Fc, int lbgk,
+                           const uint32_t* ex_first, const uint32_t ex_class[9], const uint32_t* ex_sample,
+                           int64_t n, const void* smp_val, int64_t ns, double beta_child, const Force& Fc, int lbgk,
                            cudaStream_t st);
 
 cudaError_t launch_init(int storage, const PatchDev& p, void* f0, void* f1, const void* rho, const void* u,

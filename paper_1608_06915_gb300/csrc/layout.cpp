@@ -484,6 +484,54 @@ std::string build_layout(HostGrid& g) {
           }
     }
     c.ex_first.push_back((uint32_t)c.ex_sample.size());
+    {
+      // number the samples in storage order (kind, then node index), so that
+      // neighbouring reconstruction nodes read neighbouring samples
+      const size_t ns = c.smp_node.size();
+      std::vector<uint32_t> order(ns), rank(ns);
+      for (size_t k = 0; k < ns; ++k) order[k] = (uint32_t)k;
+      std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+        if (c.smp_kind[a] != c.smp_kind[b]) return c.smp_kind[a] < c.smp_kind[b];
+        return c.smp_node[a] < c.smp_node[b];
+      });
+      std::vector<uint32_t> node(ns);
+      std::vector<uint8_t> kind(ns);
+      for (size_t k = 0; k < ns; ++k) {
+        rank[order[k]] = (uint32_t)k;
+        node[k] = c.smp_node[order[k]];
+        kind[k] = c.smp_kind[order[k]];
+      }
+      c.smp_node.swap(node);
+      c.smp_kind.swap(kind);
+      for (auto& v : c.ex_sample) v = rank[v];
+    }
+    {
+      // group the entries by mask (node order kept inside a group), so that a
+      // thread block of the explode kernel meets one interpolation stencil only
+      const size_t ne = c.ex_node.size();
+      std::vector<uint32_t> node, first, smp;
+      std::vector<uint8_t> msk;
+      node.reserve(ne);
+      first.reserve(ne + 1);
+      msk.reserve(ne);
+      smp.reserve(c.ex_sample.size());
+      for (int m = 0; m < 8; ++m) {
+        c.ex_class[m] = (uint32_t)node.size();
+        for (size_t k = 0; k < ne; ++k) {
+          if (c.ex_mask[k] != m) continue;
+          node.push_back(c.ex_node[k]);
+          msk.push_back((uint8_t)m);
+          first.push_back((uint32_t)smp.size());
+          smp.insert(smp.end(), c.ex_sample.begin() + c.ex_first[k], c.ex_sample.begin() + c.ex_first[k + 1]);
+        }
+      }
+      c.ex_class[8] = (uint32_t)node.size();
+      first.push_back((uint32_t)smp.size());
+      c.ex_node.swap(node);
+      c.ex_first.swap(first);
+      c.ex_mask.swap(msk);
+      c.ex_sample.swap(smp);
+    }
     // coalesce pairs: parent twins x_t,cf and the coinciding child node
     int64_t X[3];
     for (int64_t n = 0; n < par.plane; ++n) {

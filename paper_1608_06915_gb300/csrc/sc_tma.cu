@@ -37,7 +37,9 @@ cudaError_t launch_sc_tiles(int storage, const PatchDev& p, const void* fin, voi
   }
 }
 
-// Tensor map of one population buffer: 4-D [27][nz][ny][nxp], box (W, 1, 1, 1).
+// Tensor map of one population buffer, 4-D [27][nz][ny][nxp].  Boxes: loads
+// (W, 1, 1, 3) -- one row of three consecutive populations; stores (32, 1, 1, 27)
+// -- one warp's segment of all populations; wrap (16 bytes, 1, 1, 1).
 cudaError_t make_tensor_map(int storage, void* out, const void* base, const PatchDev& p, int kind) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -71,9 +73,10 @@ cudaError_t make_tensor_map(int storage, void* out, const void* base, const Patc
   const cuuint64_t dims[4] = {(cuuint64_t)p.nxp, (cuuint64_t)p.dim[1], (cuuint64_t)p.dim[2], 27};
   const cuuint64_t strides[3] = {(cuuint64_t)p.nxp * es, (cuuint64_t)p.nxp * p.dim[1] * es,
                                  (cuuint64_t)p.plane * es};
-  if (kind == 1) w = TmaCfg<float>::OSEG;  // store box: one warp's 32-node row segment
-  if (kind == 2) w = 16 / es;            // wrap box: 16 bytes
-  const cuuint32_t box[4] = {(cuuint32_t)w, 1, 1, 1};
+  cuuint32_t np = 3;
+  if (kind == 1) w = TmaCfg<float>::OSEG, np = 27;  // store box: one warp's 32-node segment
+  if (kind == 2) w = 16 / es, np = 1;               // wrap box: 16 bytes
+  const cuuint32_t box[4] = {(cuuint32_t)w, 1, 1, np};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = encode(reinterpret_cast<CUtensorMap*>(out), dt, 4, const_cast<void*>(base), dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

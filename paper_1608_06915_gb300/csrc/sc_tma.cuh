@@ -5,21 +5,26 @@
 // fetched with cp.async.bulk.tensor (TMA) as boxes [x0 - H, x0 + 128 + H)
 // (H elements = 16 bytes, the start alignment TMA requires), so every shift
 // of -1, 0, +1 along x is a fixed offset into the same shared-memory row.
-// The post-collision tile is written to a shared-memory output stage and
-// stored back by TMA, 27 rows of 128 nodes.
+// The three populations with the same (c_y, c_z) read the same source row
+// of their planes, so one box of three rows (populations 3j .. 3j + 2)
+// brings them: 9 loads per tile.  The post-collision tile is written to a
+// shared-memory output stage and stored back by TMA, one box of 27 rows x 32
+// nodes per warp.
 //
 // Warp roles: one thread of warp 4 is the producer -- it waits until a ring
 // stage is free (mbarrier "empty"), posts the expected byte count and issues the
-// 27 row loads of the next tile; warps 0-3 are consumers -- they wait for the
+// 9 three-row loads of the next tile; warps 0-3 are consumers -- they wait for the
 // stage (mbarrier "full"), read their 27 values, release the stage, collide,
 // write their 32-node segment of the 27 output rows to shared memory and one
-// lane stores it back with 27 TMA stores, so consumer warps never wait for each
+// lane stores it back with one TMA store, so consumer warps never wait for each
 // other.  TMA instructions are issued by single threads: with per-lane operands
 // the compiler would serialise them lane by lane.  Persistent CTAs walk a list of tiles whose nodes are all
 // plain bulk nodes (every pull source stored, wrap only on spanned axes);
 // tiles holding wall, solid, outlet or interface nodes go to k_sc_tiles,
 // which pulls node by node.
 //
+// Waits suspend in hardware (mbarrier try_wait with a time hint) instead of
+// spinning, so a waiting producer takes no issue slots from the consumers.
 // Waits are bounded: a stage that does not arrive within about a second sets
 // bit 1 of the status word; the CTA then waits (bounded again) for the copies
 // it has in flight and returns.
@@ -40,12 +45,12 @@ struct TmaCfg {
   static constexpr int BX = 128;                                        // nodes per tile
   static constexpr int H = 16 / (int)sizeof(S);                         // halo, elements
   static constexpr int W = BX + 2 * H;                                  // load box width, elements
-  static constexpr int SLOT = (W * (int)sizeof(S) + 127) / 128 * 128;   // bytes per loaded row
+  static constexpr int GROUP = (3 * W * (int)sizeof(S) + 127) / 128 * 128;  // bytes per three-row box
   static constexpr int OSEG = 32;                                       // nodes per warp segment
-  static constexpr int OSLOT = OSEG * (int)sizeof(S) < 128 ? 128 : OSEG * (int)sizeof(S);  // bytes per stored row
+  static constexpr int OSEGB = (27 * OSEG * (int)sizeof(S) + 127) / 128 * 128;  // bytes per [27][32] segment
   static constexpr int SIDE = 128;                                      // one 16-byte wrap box, padded
-  static constexpr int STAGE = 27 * SLOT + 18 * SIDE;                   // rows + 2 x 9 wrap boxes
-  static constexpr int OSTAGE = 4 * 27 * OSLOT;                         // [warp][population][32 nodes]
+  static constexpr int STAGE = 9 * GROUP + 18 * SIDE;                   // rows + 2 x 9 wrap boxes
+  static constexpr int OSTAGE = 4 * OSEGB;                              // [warp][population][32 nodes]
   static constexpr uint32_t TX = 27u * W * (uint32_t)sizeof(S);        // bytes of the 27 row loads
   static constexpr uint32_t TXW = 9u * 16u;                             // bytes of 9 wrap boxes
 #ifndef LBM_TMA_DI
@@ -109,12 +114,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait that may suspend the thread for up to ns nanoseconds (woken early
+// when the phase completes).
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait on an mbarrier phase: about a second at most.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 24); ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (it > 32) __nanosleep(64);
-  }
+  if (mbar_try_wait(bar, parity)) return true;
+  for (int it = 0; it < (1 << 21); ++it)
+    if (mbar_try_wait_sleep(bar, parity, 500u)) return true;
   return false;
 }
 
@@ -162,6 +178,13 @@ __device__ __forceinline__ void tile_xyz(unsigned long long t, int& tx, int& y, 
   tx = (int)(t & 0xffffu);
   y = (int)((t >> 16) & 0xffffu);
   z = (int)(t >> 32);
+}
+
+// Shared-memory row of population i in a load stage (elements): group i / 3,
+// row i % 3 of the three-row box.
+template <typename S>
+__device__ __forceinline__ constexpr int row_base(int i) {
+  return (i / 3) * (TmaCfg<S>::GROUP / (int)sizeof(S)) + (i % 3) * TmaCfg<S>::W;
 }
 
 // Periodic x: the first tile of a row needs, for the 9 populations with
@@ -223,7 +246,7 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
       tile_at[s] = make_int4(tx, ty, tz, 0);
       mbar_expect_tx(&full[s], C::TX + (first ? C::TXW : 0u) + (last ? C::TXW : 0u));
       unsigned char* stage = smem + s * C::STAGE;
-      unsigned char* side = stage + 27 * C::SLOT;
+      unsigned char* side = stage + 9 * C::GROUP;
       const int x0 = tx * C::BX - C::H;
 #pragma unroll 1
       for (int cz = 0; cz < 3; ++cz) {
@@ -232,8 +255,7 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
         for (int cy = 0; cy < 3; ++cy) {
           const int sy = wrap_axis(ty - (cy - 1), p.dim[1]);
           const int j = 3 * cz + cy;  // populations 3j, 3j + 1, 3j + 2 share this source row
-#pragma unroll
-          for (int cx = 0; cx < 3; ++cx) tma_load_row(stage + (3 * j + cx) * C::SLOT, &map_in, &full[s], x0, sy, sz, 3 * j + cx);
+          tma_load_row(stage + j * C::GROUP, &map_in, &full[s], x0, sy, sz, 3 * j);
           if (first) tma_load_row(side + j * C::SIDE, &map_wrap, &full[s], p.dim[0] - C::H, sy, sz, 3 * j + 2);
           if (last) tma_load_row(side + (9 + j) * C::SIDE, &map_wrap, &full[s], 0, sy, sz, 3 * j);
         }
@@ -260,11 +282,11 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
     R f[27];
     unroll<27>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      f[i] = SCvt<S>::to(st[i * (C::SLOT / (int)sizeof(S)) + C::H + tid - CX(i)]);
+      f[i] = SCvt<S>::to(st[row_base<S>(i) + C::H + tid - CX(i)]);
     });
     if (p.span[0] && (x == 0 || x == p.dim[0] - 1)) {
       // periodic wrap along x from the side slots
-      const S* side = reinterpret_cast<const S*>(smem + s * C::STAGE + 27 * C::SLOT);
+      const S* side = reinterpret_cast<const S*>(smem + s * C::STAGE + 9 * C::GROUP);
       const bool lo = x == 0;
       unroll<27>([&](auto I) {
         constexpr int i = decltype(I)::value;
@@ -280,17 +302,15 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
     const int o = k % C::DO;
     if (lane == 0) bulk_wait_read<C::DO - 1>();
     __syncwarp();
-    unsigned char* seg = ostage + o * C::OSTAGE + warp * 27 * C::OSLOT;
+    unsigned char* seg = ostage + o * C::OSTAGE + warp * C::OSEGB;
     unroll<27>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      Stor<S>::st(reinterpret_cast<S*>(seg + i * C::OSLOT) + lane, f[i]);
+      Stor<S>::st(reinterpret_cast<S*>(seg) + i * C::OSEG + lane, f[i]);
     });
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
     if (lane == 0) {
-      const int xs = tx * C::BX + warp * C::OSEG;
-#pragma unroll
-      for (int i = 0; i < 27; ++i) tma_store_row(&map_out, seg + i * C::OSLOT, xs, y, z, i);
+      tma_store_row(&map_out, seg, tx * C::BX + warp * C::OSEG, y, z, 0);
       bulk_commit();
     }
   }
