@@ -380,6 +380,38 @@ std::string build_layout(HostGrid& g) {
     if (p.level > 0 && g.P[p.parent].level != p.level - 1) return "internal: parent level";
   }
   // stream-collide tiles
+  //
+  // A tile (128 nodes along x at one (y, z)) goes to the TMA path when every
+  // node in it is updated in that substep and, for each of the 9 source rows
+  // (c_y, c_z), either all its pulls read the neighbour row (wrapping only on
+  // spanned axes) or all bounce back from a wall across y or z; bit j of the
+  // tile's bounce mask marks row j = (c_y + 1) + 3 (c_z + 1) bounced.
+  // Source of population i at patch-local L: 0 plain neighbour, 1 bounce-back
+  // from a y or z wall, 2 anything else (solid, x wall, outlet).
+  auto outcome = [&](const HostPatch& p, const int64_t L[3], int i) -> int {
+    const int64_t X[3] = {p.org[0] + L[0], p.org[1] + L[1], p.org[2] + L[2]};
+    int64_t src;
+    const int r = geo.resolve(p, X, i, &src);
+    if (r == 0) {
+      int64_t S[3];
+      for (int a = 0; a < 3; ++a) {
+        S[a] = L[a] - cvel(i, a);
+        if (S[a] < 0 || S[a] >= p.dim[a]) {
+          if (!p.span[a]) return 2;
+          S[a] += S[a] < 0 ? p.dim[a] : -p.dim[a];
+        }
+      }
+      return src == (S[2] * p.dim[1] + S[1]) * p.nxp + S[0] ? 0 : 2;
+    }
+    if (r != 1) return 2;
+    bool yz = false;
+    for (int a = 1; a < 3; ++a) {
+      const int64_t sa = X[a] - cvel(i, a);
+      if (!g.periodic(a) && ((sa < 0 && g.wall(a, 0)) || (sa > g.maxc(p.level, a) && g.wall(a, 1)))) yz = true;
+    }
+    const int64_t sx = X[0] - cvel(i, 0);
+    return yz && (g.periodic(0) || (sx >= 0 && sx <= g.maxc(p.level, 0))) ? 1 : 2;
+  };
   for (auto& p : g.P) {
     p.ntx = (p.dim[0] + 127) / 128;
     for (int k = 0; k < 2; ++k) {
@@ -387,41 +419,74 @@ std::string build_layout(HostGrid& g) {
       p.tiles_mixed[k].clear();
       p.tiles_all[k].clear();
     }
-    for (int64_t z = 0; z < p.dim[2]; ++z)
+    struct Rows {
+      std::vector<uint64_t> pure[2];
+      std::vector<uint32_t> mixed[2], all[2];
+    };
+    std::vector<Rows> rows(p.dim[2]);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t z = 0; z < p.dim[2]; ++z) {
+      Rows& R = rows[z];
       for (int64_t y = 0; y < p.dim[1]; ++y)
         for (int64_t tx = 0; tx < p.ntx; ++tx) {
-          int nb = 0, nbc = 0, nd1 = 0, nd1plain = 0, n = 0;
+          // per substep parity k: nodes updated / not updated, row states (-1 unseen, 0 plain, 1 bounce)
+          int active[2] = {0, 0}, idle[2] = {0, 0}, state[2][9];
+          bool ok[2] = {true, true};
+          for (int k = 0; k < 2; ++k)
+            for (int j = 0; j < 9; ++j) state[k][j] = -1;
+          auto merge = [&](int k, int j, int o) {
+            if (state[k][j] < 0) state[k][j] = o;
+            else if (state[k][j] != o) ok[k] = false;
+          };
           for (int64_t x = tx * 128; x < std::min<int64_t>(p.dim[0], tx * 128 + 128); ++x) {
             const int64_t m = (z * p.dim[1] + y) * p.nxp + x;
             const uint8_t t = p.type[m];
-            ++n;
-            nb += t == T_BULK;
-            nbc += t == T_BC;
-            if (t == T_D1) {
-              ++nd1;
-              int64_t X[3], src;
-              geo.coords(p, m, X);
-              bool plain = true;
-              for (int i = 0; i < 27 && plain; ++i) plain = geo.resolve(p, X, i, &src) == 0;
-              // plain also along the spanned-axis wrap used by the TMA path
-              nd1plain += plain;
+            bool act[2];
+            act[0] = t == T_BULK || t == T_BC;
+            act[1] = act[0] || t == T_D1;
+            for (int k = 0; k < 2; ++k) (act[k] ? active[k] : idle[k]) += 1;
+            if (!act[1]) continue;
+            if (t == T_BULK) {
+              for (int k = 0; k < 2; ++k)
+                for (int j = 0; j < 9; ++j) merge(k, j, 0);
+              continue;
+            }
+            const int64_t L[3] = {x, y, z};
+            int o[27];
+            bool good = true;
+            for (int i = 0; i < 27 && good; ++i) good = (o[i] = outcome(p, L, i)) != 2;
+            for (int k = 0; k < 2; ++k) {
+              if (!act[k]) continue;
+              if (!good) ok[k] = false;
+              else
+                for (int i = 0; i < 27; ++i) merge(k, i / 3, o[i]);
             }
           }
           const uint32_t id = (uint32_t)((z * p.dim[1] + y) * p.ntx + tx);
-          const uint64_t packed = (uint64_t)tx | ((uint64_t)y << 16) | ((uint64_t)z << 32);
           // the TMA path fetches the periodic wrap of x-spanning rows as 16-byte
           // boxes at x = dim - H: row-edge tiles need dim a multiple of 8 nodes
           const bool edge = tx == 0 || (tx + 1) * 128 >= p.dim[0];
           const bool wrap_ok = !p.span[0] || !edge || p.dim[0] % 8 == 0;
-          // even steps: bulk (and boundary) nodes; depth-1 nodes are rebuilt by explode
-          if (nb == n && wrap_ok) p.tiles_pure[0].push_back(packed);
-          else if (nb + nbc > 0) p.tiles_mixed[0].push_back(id);
-          // odd steps: depth-1 nodes are streamed too
-          if (nb + nd1plain == n && nd1plain == nd1 && wrap_ok) p.tiles_pure[1].push_back(packed);
-          else if (nb + nbc + nd1 > 0) p.tiles_mixed[1].push_back(id);
-          if (nb + nbc > 0) p.tiles_all[0].push_back(id);
-          if (nb + nbc + nd1 > 0) p.tiles_all[1].push_back(id);
+          for (int k = 0; k < 2; ++k) {
+            if (active[k] == 0) continue;
+            R.all[k].push_back(id);
+            if (ok[k] && idle[k] == 0 && wrap_ok) {
+              uint64_t bm = 0;
+              for (int j = 0; j < 9; ++j)
+                if (state[k][j] == 1) bm |= 1ull << j;
+              R.pure[k].push_back((uint64_t)tx | ((uint64_t)y << 16) | ((uint64_t)z << 32) | (bm << 48));
+            } else {
+              R.mixed[k].push_back(id);
+            }
+          }
         }
+    }
+    for (auto& R : rows)
+      for (int k = 0; k < 2; ++k) {
+        p.tiles_pure[k].insert(p.tiles_pure[k].end(), R.pure[k].begin(), R.pure[k].end());
+        p.tiles_mixed[k].insert(p.tiles_mixed[k].end(), R.mixed[k].begin(), R.mixed[k].end());
+        p.tiles_all[k].insert(p.tiles_all[k].end(), R.all[k].begin(), R.all[k].end());
+      }
   }
   // interface tables, stored on the child
   for (size_t ci = 1; ci < g.P.size(); ++ci) {

@@ -18,10 +18,11 @@
 // write their 32-node segment of the 27 output rows to shared memory and one
 // lane stores it back with one TMA store, so consumer warps never wait for each
 // other.  TMA instructions are issued by single threads: with per-lane operands
-// the compiler would serialise them lane by lane.  Persistent CTAs walk a list of tiles whose nodes are all
-// plain bulk nodes (every pull source stored, wrap only on spanned axes);
-// tiles holding wall, solid, outlet or interface nodes go to k_sc_tiles,
-// which pulls node by node.
+// the compiler would serialise them lane by lane.  Persistent CTAs walk a list of tiles whose nodes all
+// pull from neighbour rows (wrapping only on spanned axes) or bounce back
+// from a wall across y or z, one rule per source row; tiles holding
+// solid, outlet, x-wall or interface nodes go to k_sc_tiles, which pulls node
+// by node.
 //
 // Waits suspend in hardware (mbarrier try_wait with a time hint) instead of
 // spinning, so a waiting producer takes no issue slots from the consumers.
@@ -173,12 +174,13 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 
 __device__ __forceinline__ int wrap_axis(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// tile list entries: x-tile | y << 16 | z << 32
+// tile list entries: x-tile | y << 16 | z << 32 | bounce mask << 48
 __device__ __forceinline__ void tile_xyz(unsigned long long t, int& tx, int& y, int& z) {
   tx = (int)(t & 0xffffu);
   y = (int)((t >> 16) & 0xffffu);
-  z = (int)(t >> 32);
+  z = (int)((t >> 32) & 0xffffu);
 }
+__device__ __forceinline__ int tile_bounce(unsigned long long t) { return (int)((t >> 48) & 0x1ffu); }
 
 // Shared-memory row of population i in a load stage (elements): group i / 3,
 // row i % 3 of the three-row box.
@@ -187,6 +189,12 @@ __device__ __forceinline__ constexpr int row_base(int i) {
   return (i / 3) * (TmaCfg<S>::GROUP / (int)sizeof(S)) + (i % 3) * TmaCfg<S>::W;
 }
 
+// Walls across y or z: when the source row j = (c_y + 1) + 3 (c_z + 1) of a
+// tile lies beyond a wall (bit j of the tile's bounce mask), its three
+// populations i = 3j + k bounce back, f_i(x) = f'_{26-i}(x) at the same node:
+// the stage slot of row j then holds the box of populations 3(8 - j) .. 3(8 - j) + 2
+// from the tile's own row, and population 3j + k reads its row 2 - k unshifted.
+//
 // Periodic x: the first tile of a row needs, for the 9 populations with
 // c_x = +1 (i = 3j + 2), the element at x = dim - 1; the last tile, for the 9
 // with c_x = -1 (i = 3j), the element at x = 0.  Both come as 16-byte boxes
@@ -240,11 +248,14 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
         }
       }
       int tx, ty, tz;
-      tile_xyz(tiles[blockIdx.x + (size_t)k * gridDim.x], tx, ty, tz);
+      const unsigned long long te = tiles[blockIdx.x + (size_t)k * gridDim.x];
+      tile_xyz(te, tx, ty, tz);
+      const int bm = tile_bounce(te);
       const bool first = p.span[0] && tx == 0;
       const bool last = p.span[0] && (tx + 1) * C::BX >= p.dim[0];
-      tile_at[s] = make_int4(tx, ty, tz, 0);
-      mbar_expect_tx(&full[s], C::TX + (first ? C::TXW : 0u) + (last ? C::TXW : 0u));
+      tile_at[s] = make_int4(tx, ty, tz, bm);
+      const uint32_t txw = 16u * (uint32_t)(9 - __popc(bm));  // wrap boxes of the rows not bounced
+      mbar_expect_tx(&full[s], C::TX + (first ? txw : 0u) + (last ? txw : 0u));
       unsigned char* stage = smem + s * C::STAGE;
       unsigned char* side = stage + 9 * C::GROUP;
       const int x0 = tx * C::BX - C::H;
@@ -255,6 +266,10 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
         for (int cy = 0; cy < 3; ++cy) {
           const int sy = wrap_axis(ty - (cy - 1), p.dim[1]);
           const int j = 3 * cz + cy;  // populations 3j, 3j + 1, 3j + 2 share this source row
+          if ((bm >> j) & 1) {
+            tma_load_row(stage + j * C::GROUP, &map_in, &full[s], x0, ty, tz, 3 * (8 - j));
+            continue;
+          }
           tma_load_row(stage + j * C::GROUP, &map_in, &full[s], x0, sy, sz, 3 * j);
           if (first) tma_load_row(side + j * C::SIDE, &map_wrap, &full[s], p.dim[0] - C::H, sy, sz, 3 * j + 2);
           if (last) tma_load_row(side + (9 + j) * C::SIDE, &map_wrap, &full[s], 0, sy, sz, 3 * j);
@@ -276,22 +291,32 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
       return;
     }
     const int4 tc = tile_at[s];
-    const int tx = tc.x, y = tc.y, z = tc.z;
+    const int tx = tc.x, y = tc.y, z = tc.z, bm = tc.w;
     const int x = tx * C::BX + tid;
     const S* st = reinterpret_cast<const S*>(smem + s * C::STAGE);
     R f[27];
-    unroll<27>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      f[i] = SCvt<S>::to(st[row_base<S>(i) + C::H + tid - CX(i)]);
-    });
+    if (bm == 0) {
+      unroll<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        f[i] = SCvt<S>::to(st[row_base<S>(i) + C::H + tid - CX(i)]);
+      });
+    } else {
+      unroll<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const bool b = (bm >> (i / 3)) & 1;
+        f[i] = SCvt<S>::to(st[b ? row_base<S>(3 * (i / 3) + 2 - i % 3) + C::H + tid
+                                : row_base<S>(i) + C::H + tid - CX(i)]);
+      });
+    }
     if (p.span[0] && (x == 0 || x == p.dim[0] - 1)) {
-      // periodic wrap along x from the side slots
+      // periodic wrap along x from the side slots (rows not bounced)
       const S* side = reinterpret_cast<const S*>(smem + s * C::STAGE + 9 * C::GROUP);
       const bool lo = x == 0;
       unroll<27>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        if (lo && CX(i) == 1) f[i] = SCvt<S>::to(side[(i / 3) * (C::SIDE / (int)sizeof(S)) + C::H - 1]);
-        if (!lo && CX(i) == -1) f[i] = SCvt<S>::to(side[(9 + i / 3) * (C::SIDE / (int)sizeof(S))]);
+        const bool b = (bm >> (i / 3)) & 1;
+        if (!b && lo && CX(i) == 1) f[i] = SCvt<S>::to(side[(i / 3) * (C::SIDE / (int)sizeof(S)) + C::H - 1]);
+        if (!b && !lo && CX(i) == -1) f[i] = SCvt<S>::to(side[(9 + i / 3) * (C::SIDE / (int)sizeof(S))]);
       });
     }
     __syncwarp();
