@@ -313,37 +313,31 @@ __global__ void __launch_bounds__(128) k_adj_coalesce(PatchDev pc, const R* __re
   push_adjoint<R>(pc, lam_old_c, x, y, z, fb);
 }
 
-// explode: child node <- collide_child(f^eq(rho~, u~) + neq~), (rho~, u~, neq~) the
-// tensor interpolation of the samples; scatters the adjoint of the 31 sample
-// values into sbar [31][ns].
+// explode: child node <- collide_child(f^eq(rho~, u~) + neq~), (rho~, u~, neq~)
+// one point of the reconstruction point space or the four-point interpolation
+// of four; scatters the adjoint of the 31 values into vbar [31][ld].
 template <typename R>
 __global__ void __launch_bounds__(128) k_adj_explode(PatchDev pc, const R* __restrict__ lam_new_c,
                                                      const uint32_t* __restrict__ ex_node,
-                                                     const uint32_t* __restrict__ ex_first,
-                                                     const uint8_t* __restrict__ ex_mask,
-                                                     const uint32_t* __restrict__ ex_sample, long long n,
-                                                     const R* __restrict__ smp, R* __restrict__ sbar, long long ns,
+                                                     const uint4* __restrict__ ex_src, long long n_one, long long n,
+                                                     const R* __restrict__ val, R* __restrict__ vbar, long long ld,
                                                      R beta_c, int lbgk) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  const R w4[4] = {R(-1.0 / 16.0), R(9.0 / 16.0), R(9.0 / 16.0), R(-1.0 / 16.0)};
-  const uint8_t mask = ex_mask[k];
-  const int cx = (mask & 1) ? 4 : 1, cy = (mask & 2) ? 4 : 1, cz = (mask & 4) ? 4 : 1;
-  const uint32_t j0 = ex_first[k];
-  R v[4] = {0, 0, 0, 0}, neq[27];
-  unroll<27>([&](auto I) { neq[decltype(I)::value] = R(0); });
-  uint32_t j = j0;
-  for (int kz = 0; kz < cz; ++kz)
-    for (int ky = 0; ky < cy; ++ky)
-      for (int kx = 0; kx < cx; ++kx) {
-        const R w = (cz == 4 ? w4[kz] : R(1)) * (cy == 4 ? w4[ky] : R(1)) * (cx == 4 ? w4[kx] : R(1));
-        const long long s = ex_sample[j++];
-        for (int c = 0; c < 4; ++c) v[c] += w * smp[c * ns + s];
-        unroll<27>([&](auto I) {
-          constexpr int i = decltype(I)::value;
-          neq[i] += w * smp[(4 + i) * ns + s];
-        });
-      }
+  const uint4 s = ex_src[k];
+  const bool one = k < n_one;
+  const R w0 = R(-1.0 / 16.0), w1 = R(9.0 / 16.0);
+  auto ip = [&](int c) {
+    const R* v = val + (long long)c * ld;
+    if (one) return v[s.x];
+    return w0 * (v[s.x] + v[s.w]) + w1 * (v[s.y] + v[s.z]);
+  };
+  R v[4], neq[27];
+  for (int c = 0; c < 4; ++c) v[c] = ip(c);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    neq[i] = ip(4 + i);
+  });
   EqState<R> q;
   eq_state_from_moments<R>(v[0], R(1) + v[0], v[1], v[2], v[3], q, false);
   R f[27];
@@ -358,18 +352,40 @@ __global__ void __launch_bounds__(128) k_adj_explode(PatchDev pc, const R* __res
   R rb, ub[3];
   feq_vjp_rho_u<R>(l, q.fefull, q.rho, q.L[0], q.L[1], q.L[2], rb, ub);
   const R vb[4] = {rb, ub[0], ub[1], ub[2]};  // rho~ enters as rho = 1 + rho~
-  j = j0;
-  for (int kz = 0; kz < cz; ++kz)
-    for (int ky = 0; ky < cy; ++ky)
-      for (int kx = 0; kx < cx; ++kx) {
-        const R w = (cz == 4 ? w4[kz] : R(1)) * (cy == 4 ? w4[ky] : R(1)) * (cx == 4 ? w4[kx] : R(1));
-        const long long s = ex_sample[j++];
-        for (int c = 0; c < 4; ++c) atomicAdd(sbar + c * ns + s, w * vb[c]);
-        unroll<27>([&](auto I) {
-          constexpr int i = decltype(I)::value;
-          atomicAdd(sbar + (4 + i) * ns + s, w * l[i]);
-        });
-      }
+  auto push = [&](int c, R x) {
+    R* d = vbar + (long long)c * ld;
+    if (one) {
+      atomicAdd(d + s.x, x);
+    } else {
+      atomicAdd(d + s.x, w0 * x);
+      atomicAdd(d + s.y, w1 * x);
+      atomicAdd(d + s.z, w1 * x);
+      atomicAdd(d + s.w, w0 * x);
+    }
+  };
+  for (int c = 0; c < 4; ++c) push(c, vb[c]);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    push(4 + i, l[i]);
+  });
+}
+
+// transpose of one interpolation pass: vbar[c][src_k] += w_k vbar[c][out0 + q]
+template <typename R>
+__global__ void __launch_bounds__(128) k_adj_points(const uint4* __restrict__ src, long long n, R* __restrict__ vbar,
+                                                    long long ld, long long out0) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const uint4 s = src[q];
+  const R w0 = R(-1.0 / 16.0), w1 = R(9.0 / 16.0);
+  for (int c = 0; c < 31; ++c) {
+    R* d = vbar + (long long)c * ld;
+    const R x = d[out0 + q];
+    atomicAdd(d + s.x, w0 * x);
+    atomicAdd(d + s.y, w1 * x);
+    atomicAdd(d + s.z, w1 * x);
+    atomicAdd(d + s.w, w0 * x);
+  }
 }
 
 // samples: (rho~, u, factor (f - f^eq)) of the pulled state of a parent or child node
@@ -378,7 +394,8 @@ __global__ void __launch_bounds__(128) k_adj_samples(PatchDev pp, const R* __res
                                                      PatchDev pc, const R* __restrict__ fin_c, R* __restrict__ lam_c,
                                                      const uint32_t* __restrict__ smp_node,
                                                      const uint8_t* __restrict__ smp_kind, long long ns,
-                                                     const R* __restrict__ sbar, R rescale_p, int* status) {
+                                                     const R* __restrict__ sbar, long long ld, R rescale_p,
+                                                     int* status) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ns) return;
   const bool par = smp_kind[s] == 0;
@@ -392,11 +409,11 @@ __global__ void __launch_bounds__(128) k_adj_samples(PatchDev pp, const R* __res
   macro(f, rho_t, rho, ux, uy, uz);
   EqState<R> e;
   eq_state_from_moments<R>(rho_t, rho, ux, uy, uz, e, false);
-  const R rb = sbar[s], ub[3] = {sbar[ns + s], sbar[2 * ns + s], sbar[3 * ns + s]};
+  const R rb = sbar[s], ub[3] = {sbar[ld + s], sbar[2 * ld + s], sbar[3 * ld + s]};
   R nb[27], fb[27], xb[27];
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    nb[i] = sbar[(4 + i) * ns + s];
+    nb[i] = sbar[(4 + i) * ld + s];
     fb[i] = factor * nb[i];
     xb[i] = -factor * nb[i];
   });
@@ -530,28 +547,38 @@ cudaError_t launch_adj_coalesce(int storage, const PatchDev& child, const void* 
 }
 
 cudaError_t launch_adj_explode(int storage, const PatchDev& child, const void* lam_new_c, const uint32_t* ex_node,
-                               const uint32_t* ex_first, const uint8_t* ex_mask, const uint32_t* ex_sample, int64_t n,
-                               const void* smp, void* sbar, int64_t ns, double beta_c, int lbgk, cudaStream_t st) {
+                               const uint32_t* ex_src, int64_t n_one, int64_t n, const void* val, void* vbar,
+                               int64_t ld, double beta_c, int lbgk, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   return adj_dispatch(storage, [&](auto z) {
     using R = decltype(z);
-    k_adj_explode<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(child, (const R*)lam_new_c, ex_node, ex_first,
-                                                                  ex_mask, ex_sample, n, (const R*)smp, (R*)sbar, ns,
-                                                                  (R)beta_c, lbgk);
+    k_adj_explode<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(child, (const R*)lam_new_c, ex_node,
+                                                                  (const uint4*)ex_src, n_one, n, (const R*)val,
+                                                                  (R*)vbar, ld, (R)beta_c, lbgk);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_adj_points(int storage, const uint32_t* pt_src, int64_t n, void* vbar, int64_t ld, int64_t out0,
+                              cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  return adj_dispatch(storage, [&](auto z) {
+    using R = decltype(z);
+    k_adj_points<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>((const uint4*)pt_src, n, (R*)vbar, ld, out0);
     return cudaGetLastError();
   });
 }
 
 cudaError_t launch_adj_samples(int storage, const PatchDev& parent, const void* fin_p, void* lam_p,
                                const PatchDev& child, const void* fin_c, void* lam_c, const uint32_t* smp_node,
-                               const uint8_t* smp_kind, int64_t ns, const void* sbar, double rescale_p, int* status,
-                               cudaStream_t st) {
+                               const uint8_t* smp_kind, int64_t ns, const void* sbar, int64_t ld, double rescale_p,
+                               int* status, cudaStream_t st) {
   if (ns == 0) return cudaSuccess;
   return adj_dispatch(storage, [&](auto z) {
     using R = decltype(z);
     k_adj_samples<R><<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(parent, (const R*)fin_p, (R*)lam_p, child,
                                                                    (const R*)fin_c, (R*)lam_c, smp_node, smp_kind, ns,
-                                                                   (const R*)sbar, (R)rescale_p, status);
+                                                                   (const R*)sbar, ld, (R)rescale_p, status);
     return cudaGetLastError();
   });
 }

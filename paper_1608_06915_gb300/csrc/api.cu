@@ -162,6 +162,18 @@ lbm_status check_bound(lbm_grid* g) {
   return LBM_OK;
 }
 
+// Intermediate points of the separable reconstruction, stage 1 then stage 2.
+cudaError_t point_passes(lbm_grid* g, const HostPatch& p, int ncomp) {
+  const int64_t ld = (int64_t)p.n_points(), ns = (int64_t)p.smp_node.size();
+  const uint32_t* src = at<uint32_t>(g, p.off_pt_src);
+  cudaError_t e = lbmk::launch_points(g->hg.desc.storage, ncomp, src, p.n_pt[0], g->base + p.off_smp_val, ld, ns,
+                                      g->stream);
+  if (!e)
+    e = lbmk::launch_points(g->hg.desc.storage, ncomp, src + 4 * (size_t)p.n_pt[0], p.n_pt[1],
+                            g->base + p.off_smp_val, ld, ns + p.n_pt[0], g->stream);
+  return e;
+}
+
 // One instant k (1 .. 2^(L-1)) of the refined step.
 lbm_status run_instant(lbm_grid* g, int k) {
   HostGrid& hg = g->hg;
@@ -246,14 +258,16 @@ lbm_status run_instant(lbm_grid* g, int k) {
         HostPatch& q = hg.P[p.parent];
         const lbmk::PatchDev qv = view(g, q);
         st = cuda_check(g,
-                        timed(g, 2, lev, (double)p.smp_node.size(),
+                        timed(g, 2, lev, (double)p.n_points(),
                               [&] {
-                                return lbmk::launch_th_samples(
+                                cudaError_t e = lbmk::launch_th_samples(
                                     storage, qv, g->base + q.off_f[q.cur], g->base + q.off_g[q.cur], pv, fin,
                                     g->base + p.off_g[p.cur], at<uint32_t>(g, p.off_smp_node),
                                     at<uint8_t>(g, p.off_smp_kind), (int64_t)p.smp_node.size(),
-                                    g->base + p.off_smp_val, q.beta / (2.0 * p.beta), q.beta1 / (2.0 * p.beta1),
-                                    thermal_level(g, q), thermal_level(g, p), status_ptr(g), g->stream);
+                                    g->base + p.off_smp_val, (int64_t)p.n_points(), q.beta / (2.0 * p.beta),
+                                    q.beta1 / (2.0 * p.beta1), thermal_level(g, q), thermal_level(g, p),
+                                    status_ptr(g), g->stream);
+                                return e ? e : point_passes(g, p, 59);
                               }),
                         "thermal samples");
         if (st) return st;
@@ -262,9 +276,8 @@ lbm_status run_instant(lbm_grid* g, int k) {
                               [&] {
                                 return lbmk::launch_th_explode(
                                     storage, pv, fout, g->base + p.off_g[1 - p.cur], at<uint32_t>(g, p.off_ex_node),
-                                    at<uint32_t>(g, p.off_ex_first), at<uint8_t>(g, p.off_ex_mask),
-                                    at<uint32_t>(g, p.off_ex_sample), (int64_t)p.ex_node.size(),
-                                    g->base + p.off_smp_val, (int64_t)p.smp_node.size(), thermal_level(g, p),
+                                    at<uint32_t>(g, p.off_ex_src), (int64_t)p.ex_one, (int64_t)p.ex_node.size(),
+                                    g->base + p.off_smp_val, (int64_t)p.n_points(), thermal_level(g, p),
                                     g->stream);
                               }),
                         "thermal explode");
@@ -273,13 +286,14 @@ lbm_status run_instant(lbm_grid* g, int k) {
         HostPatch& q = hg.P[p.parent];
         const lbmk::PatchDev qv = view(g, q);
         st = cuda_check(g,
-                        timed(g, 2, lev, (double)p.smp_node.size(),
+                        timed(g, 2, lev, (double)p.n_points(),
                               [&] {
-                                return lbmk::launch_samples(storage, qv, g->base + q.off_f[q.cur], pv, fin,
-                                                            at<uint32_t>(g, p.off_smp_node),
-                                                            at<uint8_t>(g, p.off_smp_kind),
-                                                            (int64_t)p.smp_node.size(), g->base + p.off_smp_val,
-                                                            q.beta / (2.0 * p.beta), status_ptr(g), g->stream);
+                                cudaError_t e = lbmk::launch_samples(
+                                    storage, qv, g->base + q.off_f[q.cur], pv, fin, at<uint32_t>(g, p.off_smp_node),
+                                    at<uint8_t>(g, p.off_smp_kind), (int64_t)p.smp_node.size(),
+                                    g->base + p.off_smp_val, (int64_t)p.n_points(), q.beta / (2.0 * p.beta),
+                                    status_ptr(g), g->stream);
+                                return e ? e : point_passes(g, p, 31);
                               }),
                         "samples");
         if (st) return st;
@@ -287,10 +301,9 @@ lbm_status run_instant(lbm_grid* g, int k) {
                         timed(g, 3, lev, (double)p.ex_node.size(),
                               [&] {
                                 return lbmk::launch_explode(storage, pv, fout, at<uint32_t>(g, p.off_ex_node),
-                                                            at<uint32_t>(g, p.off_ex_first), p.ex_class,
-                                                            at<uint32_t>(g, p.off_ex_sample),
+                                                            at<uint32_t>(g, p.off_ex_src), (int64_t)p.ex_one,
                                                             (int64_t)p.ex_node.size(), g->base + p.off_smp_val,
-                                                            (int64_t)p.smp_node.size(), p.beta, F, lbgk, g->stream);
+                                                            (int64_t)p.n_points(), p.beta, F, lbgk, g->stream);
                               }),
                         "explode");
         if (st) return st;
@@ -389,9 +402,8 @@ lbm_status lbm_grid_bind(lbm_grid_t g, void* dev_ptr, size_t bytes, void* cuda_s
   for (auto& p : g->hg.P) {
     if (!e) e = up(p.off_type, p.type.data(), p.type.size());
     if (!e) e = up(p.off_ex_node, p.ex_node.data(), 4 * p.ex_node.size());
-    if (!e) e = up(p.off_ex_first, p.ex_first.data(), 4 * p.ex_first.size());
-    if (!e) e = up(p.off_ex_mask, p.ex_mask.data(), p.ex_mask.size());
-    if (!e) e = up(p.off_ex_sample, p.ex_sample.data(), 4 * p.ex_sample.size());
+    if (!e) e = up(p.off_ex_src, p.ex_src.data(), 4 * p.ex_src.size());
+    if (!e) e = up(p.off_pt_src, p.pt_src.data(), 4 * p.pt_src.size());
     if (!e) e = up(p.off_smp_node, p.smp_node.data(), 4 * p.smp_node.size());
     if (!e) e = up(p.off_smp_kind, p.smp_kind.data(), p.smp_kind.size());
     if (!e) e = up(p.off_cf_parent, p.cf_parent.data(), 4 * p.cf_parent.size());
@@ -672,7 +684,7 @@ AdjLayout adjoint_layout(const lbm_grid* g, int K) {
     return o;
   };
   a.second_off = take(a.lam_bytes);
-  for (auto& p : g->hg.P) a.sbar_off.push_back(take(31 * p.smp_node.size() * rb));
+  for (auto& p : g->hg.P) a.sbar_off.push_back(take(31 * p.n_points() * rb));
   a.snap_bytes = 0;
   for (auto& p : g->hg.P) a.snap_bytes += 27 * (size_t)p.plane * g->hg.pop_bytes;
   a.snap_off = take(a.snap_bytes * (size_t)K);
@@ -746,21 +758,27 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
       const int qi = p.parent;
       const lbmk::PatchDev qv = view(g, q);
       uint8_t* sbar = ws + a.sbar_off[pi];
-      const int64_t ns = (int64_t)p.smp_node.size();
+      const int64_t ns = (int64_t)p.smp_node.size(), ld = (int64_t)p.n_points();
+      const uint32_t* psrc = at<uint32_t>(g, p.off_pt_src);
       if (!e)
         e = lbmk::launch_samples(storage, qv, g->base + q.off_f[q.cur], pv, g->base + p.off_f[p.cur],
                                  at<uint32_t>(g, p.off_smp_node), at<uint8_t>(g, p.off_smp_kind), ns,
-                                 g->base + p.off_smp_val, q.beta / (2.0 * p.beta), status_ptr(g), g->stream);
-      if (!e && ns) e = cudaMemsetAsync(sbar, 0, 31 * (size_t)ns * rb, g->stream);
+                                 g->base + p.off_smp_val, ld, q.beta / (2.0 * p.beta), status_ptr(g), g->stream);
+      if (!e) e = point_passes(g, p, 31);
+      if (!e && ld) e = cudaMemsetAsync(sbar, 0, 31 * (size_t)ld * rb, g->stream);
       if (!e)
         e = lbmk::launch_adj_explode(storage, pv, lam_ptr(pi, lcur[pi]), at<uint32_t>(g, p.off_ex_node),
-                                     at<uint32_t>(g, p.off_ex_first), at<uint8_t>(g, p.off_ex_mask),
-                                     at<uint32_t>(g, p.off_ex_sample), (int64_t)p.ex_node.size(),
-                                     g->base + p.off_smp_val, sbar, ns, p.beta, lbgk, g->stream);
+                                     at<uint32_t>(g, p.off_ex_src), (int64_t)p.ex_one, (int64_t)p.ex_node.size(),
+                                     g->base + p.off_smp_val, sbar, ld, p.beta, lbgk, g->stream);
+      // the interpolation passes transposed, last pass first
+      if (!e)
+        e = lbmk::launch_adj_points(storage, psrc + 4 * (size_t)p.n_pt[0], p.n_pt[1], sbar, ld, ns + p.n_pt[0],
+                                    g->stream);
+      if (!e) e = lbmk::launch_adj_points(storage, psrc, p.n_pt[0], sbar, ld, ns, g->stream);
       if (!e)
         e = lbmk::launch_adj_samples(storage, qv, g->base + q.off_f[q.cur], lam_ptr(qi, 1 - lcur[qi]), pv,
                                      g->base + p.off_f[p.cur], lam_ptr(pi, 1 - lcur[pi]),
-                                     at<uint32_t>(g, p.off_smp_node), at<uint8_t>(g, p.off_smp_kind), ns, sbar,
+                                     at<uint32_t>(g, p.off_smp_node), at<uint8_t>(g, p.off_smp_kind), ns, sbar, ld,
                                      q.beta / (2.0 * p.beta), status_ptr(g), g->stream);
     }
   }

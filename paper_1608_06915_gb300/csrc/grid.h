@@ -56,12 +56,15 @@ struct HostPatch {
   alignas(64) unsigned char tmapo[2][128];  // TMA store descriptors
   alignas(64) unsigned char tmapw[2][128];  // TMA 16-byte wrap descriptors
 
-  // interface toward the parent (level >= 1)
+  // interface toward the parent (level >= 1).  Reconstruction values live in
+  // a point space [0, n_points()): samples, then stage-1 points (off-lattice
+  // along one axis), then stage-2 points (two axes), [value][point] in the
+  // sample buffer.
   std::vector<uint32_t> ex_node;    // explode targets (nodes of this patch)
-  std::vector<uint32_t> ex_first;   // sample list offsets, size ex_node.size() + 1
-  std::vector<uint8_t> ex_mask;     // bit a: off-lattice along axis a
-  std::vector<uint32_t> ex_sample;  // sample ids
-  uint32_t ex_class[9] = {};        // entries are grouped by mask: class m is [ex_class[m], ex_class[m + 1])
+  std::vector<uint32_t> ex_src;     // 4 point ids per target (one-source targets use the first)
+  uint32_t ex_one = 0;              // targets [0, ex_one) read one point, the rest interpolate four
+  std::vector<uint32_t> pt_src;     // 4 point ids per intermediate point (stage 1, then stage 2)
+  uint32_t n_pt[2] = {0, 0};        // intermediate points per stage
   std::vector<uint32_t> smp_node;   // per sample: node index in parent or child
   std::vector<uint8_t> smp_kind;    // per sample: S_PARENT / S_CHILD
   std::vector<uint32_t> cf_parent;  // coalesce: parent twin node
@@ -70,9 +73,10 @@ struct HostPatch {
   // device placement (byte offsets into the bound buffer)
   size_t off_f[2]{}, off_g[2]{}, off_type = 0;
   size_t off_tiles_pure[2]{}, off_tiles_mixed[2]{}, off_tiles_all[2]{};
-  size_t off_ex_node = 0, off_ex_first = 0, off_ex_mask = 0, off_ex_sample = 0;
+  size_t off_ex_node = 0, off_ex_src = 0, off_pt_src = 0;
   size_t off_smp_node = 0, off_smp_kind = 0, off_smp_val = 0, off_cf_parent = 0, off_cf_child = 0;
   int cur = 0;  // which population buffer holds the current state
+  size_t n_points() const { return smp_node.size() + n_pt[0] + n_pt[1]; }
 };
 
 struct HostGrid {

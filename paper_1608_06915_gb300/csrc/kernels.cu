@@ -8,11 +8,12 @@
 //                     (Eq. f_neq_rescaling_iso inverted), then collide,
 //   k_samples         reconstruction samples: pre-collision rho, u and the
 //                     child-scale non-equilibrium part at parent positions,
+//   k_points          intermediate points of the separable tensor interpolation,
 //   k_explode         child twins x_t,fc and reconstruction nodes x_r
 //                     (Eq. interp, tensor four-point Lagrange), then collide.
 // Kernels of one instant read only the previous states and write disjoint
 // nodes of the next-state buffers, so they need no ordering among themselves
-// except samples before explode.
+// except samples, then the point stages, before explode.
 #include <type_traits>
 
 #include "../../include/lbm.h"
@@ -105,12 +106,13 @@ cudaError_t launch_coalesce(int storage, const PatchDev& child, const void* fin_
 }
 
 // ---------------------------------------------------------------------------
-// Reconstruction samples: [31][ns] = rho - 1, ux, uy, uz, neq_0..26 (child scale).
+// Reconstruction samples: [31][ld] = rho - 1, ux, uy, uz, neq_0..26 (child
+// scale), columns [0, ns) of the point space.
 template <typename S, typename R>
 __global__ void __launch_bounds__(128) k_samples(PatchDev pp, const S* __restrict__ fin_p, PatchDev pc,
                                                  const S* __restrict__ fin_c, const uint32_t* __restrict__ smp_node,
                                                  const uint8_t* __restrict__ smp_kind, long long ns,
-                                                 R* __restrict__ out, R rescale_p, int* status) {
+                                                 R* __restrict__ out, long long ld, R rescale_p, int* status) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ns) return;
   R f[27];
@@ -126,89 +128,99 @@ __global__ void __launch_bounds__(128) k_samples(PatchDev pp, const S* __restric
   macro(f, rho_t, rho, ux, uy, uz);
   feq_dev(rho_t, rho, ux, uy, uz, fe);
   out[s] = rho_t;
-  out[ns + s] = ux;
-  out[2 * ns + s] = uy;
-  out[3 * ns + s] = uz;
+  out[ld + s] = ux;
+  out[2 * ld + s] = uy;
+  out[3 * ld + s] = uz;
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    out[(4 + i) * ns + s] = factor * (f[i] - fe[i]);
+    out[(4 + i) * ld + s] = factor * (f[i] - fe[i]);
   });
 }
 
 cudaError_t launch_samples(int storage, const PatchDev& parent, const void* fin_parent, const PatchDev& child,
                            const void* fin_child, const uint32_t* smp_node, const uint8_t* smp_kind, int64_t ns,
-                           void* smp_val, double rescale_parent, int* status, cudaStream_t st) {
+                           void* smp_val, int64_t ld, double rescale_parent, int* status, cudaStream_t st) {
   if (ns == 0) return cudaSuccess;
   return dispatch(storage, [&](auto ts, auto tr) {
     using S = typename decltype(ts)::type;
     using R = typename decltype(tr)::type;
     dim3 block(128), grid((unsigned)((ns + 127) / 128));
     k_samples<S, R><<<grid, block, 0, st>>>(parent, (const S*)fin_parent, child, (const S*)fin_child, smp_node,
-                                            smp_kind, ns, (R*)smp_val, (R)rescale_parent, status);
+                                            smp_kind, ns, (R*)smp_val, ld, (R)rescale_parent, status);
     return cudaGetLastError();
   });
 }
 
 // ---------------------------------------------------------------------------
-// Child twins and reconstruction nodes: tensor four-point Lagrange (Eq. interp,
-// weights (-1, 9, 9, -1)/16) of rho, u and the non-equilibrium part over the
-// off-lattice axes; f = f^eq(rho~, u~) + neq~; then collide.
-//
-// The entries come grouped by off-lattice mask and every thread block takes
-// entries of one group, so the stencil (1, 4, 16 or 64 samples) is a
-// compile-time shape: no divergence, and the sample indices of a row of the
-// stencil are fetched together.
-struct ExClasses {
-  uint32_t start[9];   // entries of mask m: [start[m], start[m + 1])
-  uint32_t block0[9];  // first thread block of mask m
-};
-
-__host__ __device__ constexpr double lagrange4(int k) { return (k == 1 || k == 2) ? 9.0 / 16.0 : -1.0 / 16.0; }
-
-template <int M, typename R>
-__device__ __forceinline__ void interpolate(const uint32_t* __restrict__ ex_sample, uint32_t j,
-                                            const R* __restrict__ smp, long long ns, R& rho_t, R& ux, R& uy, R& uz,
-                                            R (&f)[27]) {
-  constexpr int cx = (M & 1) ? 4 : 1, cy = (M & 2) ? 4 : 1, cz = (M & 4) ? 4 : 1;
-  rho_t = ux = uy = uz = R(0);
-  unroll<27>([&](auto I) { f[decltype(I)::value] = R(0); });
-#pragma unroll 1
-  for (int kz = 0; kz < cz; ++kz) {
-    const R wz = cz == 4 ? ((kz == 1 || kz == 2) ? R(9.0 / 16.0) : R(-1.0 / 16.0)) : R(1);
-    uint32_t sid[cy * cx];
-#pragma unroll
-    for (int q = 0; q < cy * cx; ++q) sid[q] = __ldg(ex_sample + j + kz * cy * cx + q);
-#pragma unroll
-    for (int ky = 0; ky < cy; ++ky) {
-      const R wyz = wz * (cy == 4 ? R(lagrange4(ky)) : R(1));
-#pragma unroll
-      for (int kx = 0; kx < cx; ++kx) {
-        const R w = wyz * (cx == 4 ? R(lagrange4(kx)) : R(1));
-        const long long s = sid[ky * cx + kx];
-        rho_t += w * __ldg(smp + s);
-        ux += w * __ldg(smp + ns + s);
-        uy += w * __ldg(smp + 2 * ns + s);
-        uz += w * __ldg(smp + 3 * ns + s);
-        unroll<27>([&](auto I) {
-          constexpr int i = decltype(I)::value;
-          f[i] += w * __ldg(smp + (4 + i) * ns + s);
-        });
-      }
-    }
+// Intermediate reconstruction points: four-point Lagrange (Eq. interp,
+// weights (-1, 9, 9, -1)/16) along one axis of NC values per point,
+// val[c][out0 + q] = sum_k w_k val[c][src[4q + k]].  The tensor interpolation
+// over two or three off-lattice axes is this one-axis pass applied axis after
+// axis (stage 1 from the samples, stage 2 from stage 1, the targets last).
+template <typename R, int NC>
+__global__ void __launch_bounds__(128) k_points(const uint4* __restrict__ src, long long n, R* __restrict__ val,
+                                                long long ld, long long out0) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const uint4 s = __ldg(src + q);
+  const R w0 = R(-1.0 / 16.0), w1 = R(9.0 / 16.0);
+#pragma unroll 4
+  for (int c = 0; c < NC; ++c) {
+    const R* v = val + (long long)c * ld;
+    const R a = __ldg(v + s.x), b = __ldg(v + s.y), d = __ldg(v + s.z), e = __ldg(v + s.w);
+    val[(long long)c * ld + out0 + q] = w0 * (a + e) + w1 * (b + d);
   }
 }
 
-template <int M, typename S, typename R, bool FORCE>
+cudaError_t launch_points(int storage, int ncomp, const uint32_t* pt_src, int64_t n, void* val, int64_t ld,
+                          int64_t out0, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  return dispatch(storage, [&](auto, auto tr) {
+    using R = typename decltype(tr)::type;
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    if (ncomp == 31)
+      k_points<R, 31><<<blocks, 128, 0, st>>>((const uint4*)pt_src, n, (R*)val, ld, out0);
+    else if (ncomp == 59)
+      k_points<R, 59><<<blocks, 128, 0, st>>>((const uint4*)pt_src, n, (R*)val, ld, out0);
+    else
+      return cudaErrorInvalidValue;
+    return cudaGetLastError();
+  });
+}
+
+// Child twins and reconstruction nodes: the last interpolation pass (or the
+// point itself), f = f^eq(rho~, u~) + neq~, then collide.  Targets
+// [0, n_one) read one point, the others interpolate four; a thread block
+// takes targets of one kind only.
+template <int K, typename S, typename R, bool FORCE>
 __device__ __forceinline__ void explode_node(const PatchDev& pc, S* __restrict__ fout_c,
-                                             const uint32_t* __restrict__ ex_node,
-                                             const uint32_t* __restrict__ ex_first,
-                                             const uint32_t* __restrict__ ex_sample, uint32_t k,
-                                             const R* __restrict__ smp, long long ns, R beta_c, R dux, R duy,
-                                             R duz, int lbgk) {
-  R rho_t, ux, uy, uz, f[27];
-  interpolate<M, R>(ex_sample, __ldg(ex_first + k), smp, ns, rho_t, ux, uy, uz, f);
+                                             const uint32_t* __restrict__ ex_node, const uint4* __restrict__ ex_src,
+                                             long long k, const R* __restrict__ val, long long ld, R beta_c, R dux,
+                                             R duy, R duz, int lbgk) {
+  const uint4 s = __ldg(ex_src + k);
+  R m[4], f[27];
+  if constexpr (K == 1) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) m[c] = __ldg(val + c * ld + s.x);
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      f[i] = __ldg(val + (4 + i) * ld + s.x);
+    });
+  } else {
+    const R w0 = R(-1.0 / 16.0), w1 = R(9.0 / 16.0);
+    auto ip = [&](int c) {
+      const R* v = val + (long long)c * ld;
+      return w0 * (__ldg(v + s.x) + __ldg(v + s.w)) + w1 * (__ldg(v + s.y) + __ldg(v + s.z));
+    };
+#pragma unroll
+    for (int c = 0; c < 4; ++c) m[c] = ip(c);
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      f[i] = ip(4 + i);
+    });
+  }
   R fe[27];
-  feq_dev(rho_t, R(1) + rho_t, ux, uy, uz, fe);
+  feq_dev(m[0], R(1) + m[0], m[1], m[2], m[3], fe);
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
     f[i] += fe[i];
@@ -220,58 +232,34 @@ __device__ __forceinline__ void explode_node(const PatchDev& pc, S* __restrict__
 template <typename S, typename R, bool FORCE>
 __global__ void __launch_bounds__(128) k_explode(PatchDev pc, S* __restrict__ fout_c,
                                                  const uint32_t* __restrict__ ex_node,
-                                                 const uint32_t* __restrict__ ex_first, const ExClasses cls,
-                                                 const uint32_t* __restrict__ ex_sample, const R* __restrict__ smp,
-                                                 long long ns, R beta_c, R dux, R duy, R duz, int lbgk) {
-  int m = 0;
-#pragma unroll
-  for (int c = 1; c < 8; ++c)
-    if (blockIdx.x >= cls.block0[c]) m = c;
-  const uint32_t k = cls.start[m] + (blockIdx.x - cls.block0[m]) * blockDim.x + threadIdx.x;
-  if (k >= cls.start[m + 1]) return;
-#define LBM_EXPLODE_CASE(MM)                                                                                 \
-  case MM:                                                                                                  \
-    explode_node<MM, S, R, FORCE>(pc, fout_c, ex_node, ex_first, ex_sample, k, smp, ns, beta_c, dux, duy, duz, \
-                                  lbgk);                                                                     \
-    break;
-  switch (m) {
-    LBM_EXPLODE_CASE(0)
-    LBM_EXPLODE_CASE(1)
-    LBM_EXPLODE_CASE(2)
-    LBM_EXPLODE_CASE(3)
-    LBM_EXPLODE_CASE(4)
-    LBM_EXPLODE_CASE(5)
-    LBM_EXPLODE_CASE(6)
-    LBM_EXPLODE_CASE(7)
+                                                 const uint4* __restrict__ ex_src, long long n_one, long long n,
+                                                 unsigned blocks_one, const R* __restrict__ val, long long ld,
+                                                 R beta_c, R dux, R duy, R duz, int lbgk) {
+  if (blockIdx.x < blocks_one) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n_one) explode_node<1, S, R, FORCE>(pc, fout_c, ex_node, ex_src, k, val, ld, beta_c, dux, duy, duz, lbgk);
+  } else {
+    const long long k = n_one + (long long)(blockIdx.x - blocks_one) * blockDim.x + threadIdx.x;
+    if (k < n) explode_node<4, S, R, FORCE>(pc, fout_c, ex_node, ex_src, k, val, ld, beta_c, dux, duy, duz, lbgk);
   }
-#undef LBM_EXPLODE_CASE
 }
 
 cudaError_t launch_explode(int storage, const PatchDev& child, void* fout_child, const uint32_t* ex_node,
-                           const uint32_t* ex_first, const uint32_t ex_class[9], const uint32_t* ex_sample,
-                           int64_t n, const void* smp_val, int64_t ns, double beta_child, const Force& Fc, int lbgk,
-                           cudaStream_t st) {
+                           const uint32_t* ex_src, int64_t n_one, int64_t n, const void* val, int64_t ld,
+                           double beta_child, const Force& Fc, int lbgk, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  ExClasses cls;
-  uint32_t blocks = 0;
-  for (int m = 0; m < 9; ++m) {
-    cls.start[m] = ex_class[m];
-    cls.block0[m] = blocks;
-    if (m < 8) blocks += (ex_class[m + 1] - ex_class[m] + 127) / 128;
-  }
-  if (ex_class[8] != (uint32_t)n) return cudaErrorInvalidValue;
+  const unsigned b1 = (unsigned)((n_one + 127) / 128), b4 = (unsigned)((n - n_one + 127) / 128);
   return dispatch(storage, [&](auto ts, auto tr) {
     using S = typename decltype(ts)::type;
     using R = typename decltype(tr)::type;
-    dim3 block(128), grid(blocks);
+    dim3 block(128), grid(b1 + b4);
     if (Fc.on())
-      k_explode<S, R, true><<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, ex_first, cls, ex_sample,
-                                                     (const R*)smp_val, ns, (R)beta_child, (R)Fc.du[0],
-                                                     (R)Fc.du[1], (R)Fc.du[2], lbgk);
+      k_explode<S, R, true><<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, (const uint4*)ex_src, n_one, n,
+                                                     b1, (const R*)val, ld, (R)beta_child, (R)Fc.du[0], (R)Fc.du[1],
+                                                     (R)Fc.du[2], lbgk);
     else
-      k_explode<S, R, false><<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, ex_first, cls, ex_sample,
-                                                      (const R*)smp_val, ns, (R)beta_child, R(0), R(0), R(0),
-                                                      lbgk);
+      k_explode<S, R, false><<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, (const uint4*)ex_src, n_one, n,
+                                                      b1, (const R*)val, ld, (R)beta_child, R(0), R(0), R(0), lbgk);
     return cudaGetLastError();
   });
 }

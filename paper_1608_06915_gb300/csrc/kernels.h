@@ -38,11 +38,11 @@ cudaError_t launch_th_coalesce(int storage, const PatchDev& child, const void* f
                                const ThermalLevel& Lp, int* status, cudaStream_t st);
 cudaError_t launch_th_samples(int storage, const PatchDev& parent, const void* fin_p, const void* gin_p,
                               const PatchDev& child, const void* fin_c, const void* gin_c, const uint32_t* smp_node,
-                              const uint8_t* smp_kind, int64_t ns, void* smp_val, double ff, double fg,
+                              const uint8_t* smp_kind, int64_t ns, void* smp_val, int64_t ld, double ff, double fg,
                               const ThermalLevel& Lp, const ThermalLevel& Lc, int* status, cudaStream_t st);
 cudaError_t launch_th_explode(int storage, const PatchDev& child, void* fo_c, void* go_c, const uint32_t* ex_node,
-                              const uint32_t* ex_first, const uint8_t* ex_mask, const uint32_t* ex_sample, int64_t n,
-                              const void* smp_val, int64_t ns, const ThermalLevel& Lc, cudaStream_t st);
+                              const uint32_t* ex_src, int64_t n_one, int64_t n, const void* val, int64_t ld,
+                              const ThermalLevel& Lc, cudaStream_t st);
 cudaError_t launch_th_init(int storage, const PatchDev& p, void* f0, void* f1, void* g0, void* g1, const void* rho,
                            const void* u, const void* T, int dtype, const double u_in[3], cudaStream_t st);
 cudaError_t launch_th_moments(int storage, const PatchDev& p, const void* fin, const void* gin, void* rho, void* u,
@@ -55,13 +55,17 @@ cudaError_t launch_adj_coalesce(int storage, const PatchDev& child, const void* 
                                 const void* lam_new_p, void* lam_old_c, const uint32_t* cf_parent,
                                 const uint32_t* cf_child, int64_t n, double r, double beta_p, int lbgk, int* status,
                                 cudaStream_t st);
+// vbar [31][ld]: adjoint of the point-space values (accumulated with atomics)
 cudaError_t launch_adj_explode(int storage, const PatchDev& child, const void* lam_new_c, const uint32_t* ex_node,
-                               const uint32_t* ex_first, const uint8_t* ex_mask, const uint32_t* ex_sample, int64_t n,
-                               const void* smp, void* sbar, int64_t ns, double beta_c, int lbgk, cudaStream_t st);
+                               const uint32_t* ex_src, int64_t n_one, int64_t n, const void* val, void* vbar,
+                               int64_t ld, double beta_c, int lbgk, cudaStream_t st);
+// transpose of launch_points: vbar[c][src[4q + k]] += w_k vbar[c][out0 + q]
+cudaError_t launch_adj_points(int storage, const uint32_t* pt_src, int64_t n, void* vbar, int64_t ld, int64_t out0,
+                              cudaStream_t st);
 cudaError_t launch_adj_samples(int storage, const PatchDev& parent, const void* fin_p, void* lam_p,
                                const PatchDev& child, const void* fin_c, void* lam_c, const uint32_t* smp_node,
-                               const uint8_t* smp_kind, int64_t ns, const void* sbar, double rescale_p, int* status,
-                               cudaStream_t st);
+                               const uint8_t* smp_kind, int64_t ns, const void* sbar, int64_t ld, double rescale_p,
+                               int* status, cudaStream_t st);
 cudaError_t launch_adj_seed(int storage, const PatchDev& p, const void* fin, void* lam, double vol_weight,
                             int child_level, double* partial, int blocks, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* partial, int n, double* out, cudaStream_t st);
@@ -89,13 +93,17 @@ cudaError_t launch_coalesce(int storage, const PatchDev& child, const void* fin_
 
 cudaError_t launch_samples(int storage, const PatchDev& parent, const void* fin_parent, const PatchDev& child,
                            const void* fin_child, const uint32_t* smp_node, const uint8_t* smp_kind, int64_t ns,
-                           void* smp_val, double rescale_parent, int* status, cudaStream_t st);
+                           void* smp_val, int64_t ld, double rescale_parent, int* status, cudaStream_t st);
 
-// ex_class[m] .. ex_class[m + 1]: the entries with off-lattice mask m (host array)
+// Point space of the reconstruction: values [ncomp][ld] (compute type),
+// samples in columns [0, ns), intermediate points after them.
+// Intermediate points q < n: column out0 + q from the 4 columns pt_src[4q ..].
+cudaError_t launch_points(int storage, int ncomp, const uint32_t* pt_src, int64_t n, void* val, int64_t ld,
+                          int64_t out0, cudaStream_t st);
+// Targets [0, n_one) read the column ex_src[4k], the others interpolate ex_src[4k .. 4k + 3].
 cudaError_t launch_explode(int storage, const PatchDev& child, void* fout_child, const uint32_t* ex_node,
-                           const uint32_t* ex_first, const uint32_t ex_class[9], const uint32_t* ex_sample,
-                           int64_t n, const void* smp_val, int64_t ns, double beta_child, const Force& Fc, int lbgk,
-                           cudaStream_t st);
+                           const uint32_t* ex_src, int64_t n_one, int64_t n, const void* val, int64_t ld,
+                           double beta_child, const Force& Fc, int lbgk, cudaStream_t st);
 
 cudaError_t launch_init(int storage, const PatchDev& p, void* f0, void* f1, const void* rho, const void* u,
                         int dtype, const double u_in[3], cudaStream_t st);

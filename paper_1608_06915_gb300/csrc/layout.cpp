@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <functional>
 #include <unordered_map>
 
 #include "grid.h"
@@ -503,57 +504,110 @@ std::string build_layout(HostGrid& g) {
       c.smp_kind.push_back(kind);
       return id;
     };
+    // Reconstruction (Eq. interp) as separable four-point passes: a target
+    // off-lattice along the axes of mask m interpolates, along the highest of
+    // them, four points at the coarse positions of that axis -- samples when
+    // no other axis is off-lattice, else intermediate points of mask m minus
+    // that axis, built the same way.  Points are keyed by (mask, fine
+    // position); ids carry their stage in the top two bits until numbered.
+    constexpr uint32_t kStage1 = 1u << 30, kStage2 = 2u << 30, kIdMask = (1u << 30) - 1;
+    std::unordered_map<uint64_t, uint32_t> pts[2];
+    std::vector<uint32_t> psrc[2];   // 4 tagged sources per point
+    std::vector<uint64_t> ppos[2];   // position key of each point (ordering)
+    std::string err;
+    auto pkey = [](int m, const int64_t Q[3]) -> uint64_t {
+      const uint64_t o = 1ull << 19;
+      return ((uint64_t)m << 60) | ((uint64_t)(Q[2] + o) << 40) | ((uint64_t)(Q[1] + o) << 20) | (uint64_t)(Q[0] + o);
+    };
+    std::function<uint32_t(int, const int64_t*)> point = [&](int m, const int64_t* Qin) -> uint32_t {
+      int64_t Q[3] = {Qin[0], Qin[1], Qin[2]};
+      geo.wrap(c.level, Q);
+      if (m == 0) {
+        int64_t X[3] = {Q[0] / 2, Q[1] / 2, Q[2] / 2};
+        geo.wrap(par.level, X);
+        const int64_t pj = geo.index(par, X);
+        const bool parent_node = pj >= 0 && par.type[pj] != T_SKIP;
+        if (parent_node && !geo.in_cf(c, X)) {
+          const uint8_t pt = par.type[pj];
+          if (pt != T_BULK && pt != T_BC) {
+            if (err.empty()) err = fmt_node("reconstruction sample on a non-bulk parent node", par.level, X);
+            return 0;
+          }
+          return sample_id(S_PARENT, pj);
+        }
+        if (!parent_node && !geo.in_hole(c, X)) {
+          if (err.empty()) err = fmt_node("reconstruction sample outside both levels", par.level, X);
+          return 0;
+        }
+        int64_t Ys[3] = {2 * X[0], 2 * X[1], 2 * X[2]};
+        geo.wrap(c.level, Ys);
+        const int64_t cj = geo.index(c, Ys);
+        if (cj < 0 || (c.type[cj] != T_BULK && c.type[cj] != T_BC)) {
+          if (err.empty()) err = fmt_node("reconstruction sample on a non-bulk child node", c.level, Ys);
+          return 0;
+        }
+        return sample_id(S_CHILD, cj);
+      }
+      const int st = __builtin_popcount((unsigned)m) - 1;  // stage 0 or 1 (masks of one or two axes)
+      const uint64_t key = pkey(m, Q);
+      auto it = pts[st].find(key);
+      if (it != pts[st].end()) return it->second;
+      const int top = m & 4 ? 2 : (m & 2 ? 1 : 0);
+      uint32_t src[4];
+      for (int k = 0; k < 4; ++k) {
+        int64_t R[3] = {Q[0], Q[1], Q[2]};
+        R[top] = Q[top] - 3 + 2 * k;
+        src[k] = point(m & ~(1 << top), R);
+      }
+      const uint32_t id = (uint32_t)ppos[st].size() | (st == 0 ? kStage1 : kStage2);
+      pts[st].emplace(key, id);
+      ppos[st].push_back(key);
+      for (int k = 0; k < 4; ++k) psrc[st].push_back(src[k]);
+      return id;
+    };
+    std::vector<uint32_t> tnode, tsrc;  // targets: node, 4 tagged sources (a single source: others ~0)
+    std::vector<uint8_t> tmask;
     int64_t Y[3];
     for (int64_t n = 0; n < c.plane; ++n) {
-      uint8_t t = c.type[n];
+      const uint8_t t = c.type[n];
       if (t != T_D0 && t != T_D1) continue;
       geo.coords(c, n, Y);
-      uint8_t mask = 0;
+      int m = 0;
       for (int a = 0; a < 3; ++a)
-        if (Y[a] & 1) mask |= (uint8_t)(1u << a);
-      c.ex_node.push_back((uint32_t)n);
-      c.ex_mask.push_back(mask);
-      c.ex_first.push_back((uint32_t)c.ex_sample.size());
-      int cnt[3];
-      int64_t pos[3][4];
-      for (int a = 0; a < 3; ++a) {
-        if (mask & (1u << a)) {
-          cnt[a] = 4;
-          for (int k = 0; k < 4; ++k) pos[a][k] = (Y[a] - 3 + 2 * k) / 2;
-        } else {
-          cnt[a] = 1;
-          pos[a][0] = Y[a] / 2;
+        if (Y[a] & 1) m |= 1 << a;
+      tnode.push_back((uint32_t)n);
+      tmask.push_back((uint8_t)m);
+      if (m == 0) {
+        tsrc.push_back(point(0, Y));
+        for (int k = 0; k < 3; ++k) tsrc.push_back(~0u);
+      } else {
+        const int top = m & 4 ? 2 : (m & 2 ? 1 : 0);
+        for (int k = 0; k < 4; ++k) {
+          int64_t R[3] = {Y[0], Y[1], Y[2]};
+          R[top] = Y[top] - 3 + 2 * k;
+          tsrc.push_back(point(m & ~(1 << top), R));
         }
       }
-      for (int kz = 0; kz < cnt[2]; ++kz)
-        for (int ky = 0; ky < cnt[1]; ++ky)
-          for (int kx = 0; kx < cnt[0]; ++kx) {
-            int64_t X[3] = {pos[0][kx], pos[1][ky], pos[2][kz]};
-            geo.wrap(par.level, X);
-            int64_t pj = geo.index(par, X);
-            bool parent_node = pj >= 0 && par.type[pj] != T_SKIP;
-            if (parent_node && !geo.in_cf(c, X)) {
-              uint8_t pt = par.type[pj];
-              if (pt != T_BULK && pt != T_BC) return fmt_node("reconstruction sample on a non-bulk parent node", par.level, X);
-              c.ex_sample.push_back(sample_id(S_PARENT, pj));
-            } else {
-              if (!parent_node && !geo.in_hole(c, X))
-                return fmt_node("reconstruction sample outside both levels", par.level, X);
-              int64_t Ys[3] = {2 * X[0], 2 * X[1], 2 * X[2]};
-              geo.wrap(c.level, Ys);
-              int64_t cj = geo.index(c, Ys);
-              if (cj < 0 || (c.type[cj] != T_BULK && c.type[cj] != T_BC))
-                return fmt_node("reconstruction sample on a non-bulk child node", c.level, Ys);
-              c.ex_sample.push_back(sample_id(S_CHILD, cj));
-            }
-          }
+      if (!err.empty()) return err;
     }
-    c.ex_first.push_back((uint32_t)c.ex_sample.size());
+    // a target that is itself an intermediate point reads that point
+    for (size_t e = 0; e < tnode.size(); ++e) {
+      const int m = tmask[e], pc = __builtin_popcount((unsigned)m);
+      if (pc < 1 || pc > 2) continue;
+      geo.coords(c, tnode[e], Y);
+      int64_t Q[3] = {Y[0], Y[1], Y[2]};
+      geo.wrap(c.level, Q);
+      auto it = pts[pc - 1].find(pkey(m, Q));
+      if (it == pts[pc - 1].end()) continue;
+      tsrc[4 * e] = it->second;
+      for (int k = 1; k < 4; ++k) tsrc[4 * e + k] = ~0u;
+    }
+    // number samples in storage order (kind, node) and points by position, so
+    // that neighbouring nodes read neighbouring values
+    const size_t ns = c.smp_node.size();
+    std::vector<uint32_t> srank(ns), prank[2];
     {
-      // number the samples in storage order (kind, then node index), so that
-      // neighbouring reconstruction nodes read neighbouring samples
-      const size_t ns = c.smp_node.size();
-      std::vector<uint32_t> order(ns), rank(ns);
+      std::vector<uint32_t> order(ns);
       for (size_t k = 0; k < ns; ++k) order[k] = (uint32_t)k;
       std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
         if (c.smp_kind[a] != c.smp_kind[b]) return c.smp_kind[a] < c.smp_kind[b];
@@ -562,40 +616,51 @@ std::string build_layout(HostGrid& g) {
       std::vector<uint32_t> node(ns);
       std::vector<uint8_t> kind(ns);
       for (size_t k = 0; k < ns; ++k) {
-        rank[order[k]] = (uint32_t)k;
+        srank[order[k]] = (uint32_t)k;
         node[k] = c.smp_node[order[k]];
         kind[k] = c.smp_kind[order[k]];
       }
       c.smp_node.swap(node);
       c.smp_kind.swap(kind);
-      for (auto& v : c.ex_sample) v = rank[v];
     }
-    {
-      // group the entries by mask (node order kept inside a group), so that a
-      // thread block of the explode kernel meets one interpolation stencil only
-      const size_t ne = c.ex_node.size();
-      std::vector<uint32_t> node, first, smp;
-      std::vector<uint8_t> msk;
-      node.reserve(ne);
-      first.reserve(ne + 1);
-      msk.reserve(ne);
-      smp.reserve(c.ex_sample.size());
-      for (int m = 0; m < 8; ++m) {
-        c.ex_class[m] = (uint32_t)node.size();
-        for (size_t k = 0; k < ne; ++k) {
-          if (c.ex_mask[k] != m) continue;
-          node.push_back(c.ex_node[k]);
-          msk.push_back((uint8_t)m);
-          first.push_back((uint32_t)smp.size());
-          smp.insert(smp.end(), c.ex_sample.begin() + c.ex_first[k], c.ex_sample.begin() + c.ex_first[k + 1]);
-        }
+    for (int st = 0; st < 2; ++st) {
+      const size_t np = ppos[st].size();
+      std::vector<uint32_t> order(np);
+      for (size_t k = 0; k < np; ++k) order[k] = (uint32_t)k;
+      // position order: z, y, x (the key's low 60 bits), then mask
+      std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+        const uint64_t ka = ppos[st][a], kb = ppos[st][b];
+        const uint64_t m60 = (1ull << 60) - 1;
+        if ((ka & m60) != (kb & m60)) return (ka & m60) < (kb & m60);
+        return ka < kb;
+      });
+      prank[st].assign(np, 0);
+      for (size_t k = 0; k < np; ++k) prank[st][order[k]] = (uint32_t)k;
+      c.n_pt[st] = (uint32_t)np;
+    }
+    auto final_id = [&](uint32_t t) -> uint32_t {
+      const uint32_t tag = t & ~kIdMask, v = t & kIdMask;
+      if (tag == 0) return srank[v];
+      if (tag == kStage1) return (uint32_t)ns + prank[0][v];
+      return (uint32_t)ns + c.n_pt[0] + prank[1][v];
+    };
+    c.pt_src.assign(4 * ((size_t)c.n_pt[0] + c.n_pt[1]), 0);
+    for (int st = 0; st < 2; ++st)
+      for (size_t q = 0; q < ppos[st].size(); ++q) {
+        const size_t row = (st == 0 ? 0 : c.n_pt[0]) + prank[st][q];
+        for (int k = 0; k < 4; ++k) c.pt_src[4 * row + k] = final_id(psrc[st][4 * q + k]);
       }
-      c.ex_class[8] = (uint32_t)node.size();
-      first.push_back((uint32_t)smp.size());
-      c.ex_node.swap(node);
-      c.ex_first.swap(first);
-      c.ex_mask.swap(msk);
-      c.ex_sample.swap(smp);
+    // entries: one-source targets first, then four-source targets, node order inside each
+    c.ex_node.clear();
+    c.ex_src.clear();
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1) c.ex_one = (uint32_t)c.ex_node.size();
+      for (size_t e = 0; e < tnode.size(); ++e) {
+        const bool one = tsrc[4 * e + 1] == ~0u;
+        if (one != (pass == 0)) continue;
+        c.ex_node.push_back(tnode[e]);
+        for (int k = 0; k < 4; ++k) c.ex_src.push_back(one && k > 0 ? 0u : final_id(tsrc[4 * e + k]));
+      }
     }
     // coalesce pairs: parent twins x_t,cf and the coinciding child node
     int64_t X[3];
@@ -647,12 +712,11 @@ size_t plan_memory(HostGrid& g) {
     p.off_tiles_mixed[0] = take(4 * p.tiles_mixed[0].size());
     p.off_tiles_mixed[1] = take(4 * p.tiles_mixed[1].size());
     p.off_ex_node = take(4 * p.ex_node.size());
-    p.off_ex_first = take(4 * p.ex_first.size());
-    p.off_ex_mask = take(p.ex_mask.size());
-    p.off_ex_sample = take(4 * p.ex_sample.size());
+    p.off_ex_src = take(4 * p.ex_src.size());
+    p.off_pt_src = take(4 * p.pt_src.size());
     p.off_smp_node = take(4 * p.smp_node.size());
     p.off_smp_kind = take(p.smp_kind.size());
-    p.off_smp_val = take(ncomp * p.smp_node.size() * g.real_bytes);
+    p.off_smp_val = take(ncomp * p.n_points() * g.real_bytes);
     p.off_cf_parent = take(4 * p.cf_parent.size());
     p.off_cf_child = take(4 * p.cf_child.size());
   }

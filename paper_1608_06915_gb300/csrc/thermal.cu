@@ -299,15 +299,16 @@ __global__ void __launch_bounds__(128) k_th_coalesce(PatchDev pc, const R* __res
   store2(pp, fo_p, go_p, cf_parent[k], f, g);
 }
 
-// samples: [59][ns] = rho - 1, ux, uy, uz, T - T0, fneq_0..26, gneq_0..26 (child scale)
+// samples: [59][ld] = rho - 1, ux, uy, uz, T - T0, fneq_0..26, gneq_0..26 (child
+// scale), columns [0, ns) of the point space
 template <typename R>
 __global__ void __launch_bounds__(128) k_th_samples(PatchDev pp, const R* __restrict__ fin_p,
                                                     const R* __restrict__ gin_p, PatchDev pc,
                                                     const R* __restrict__ fin_c, const R* __restrict__ gin_c,
                                                     const uint32_t* __restrict__ smp_node,
                                                     const uint8_t* __restrict__ smp_kind, long long ns,
-                                                    R* __restrict__ out, R ff, R fg, ThParams<R> tpar, ThParams<R> tc,
-                                                    int* status) {
+                                                    R* __restrict__ out, long long ld, R ff, R fg, ThParams<R> tpar,
+                                                    ThParams<R> tc, int* status) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ns) return;
   R f[27], g[27];
@@ -322,52 +323,42 @@ __global__ void __launch_bounds__(128) k_th_samples(PatchDev pp, const R* __rest
   ThState<R> st;
   thermal_neq<R>(f, g, par ? ff : R(1), par ? fg : R(1), fn, gn, st);
   out[s] = st.rho_t;
-  out[ns + s] = st.ux;
-  out[2 * ns + s] = st.uy;
-  out[3 * ns + s] = st.uz;
-  out[4 * ns + s] = st.T_d;
+  out[ld + s] = st.ux;
+  out[2 * ld + s] = st.uy;
+  out[3 * ld + s] = st.uz;
+  out[4 * ld + s] = st.T_d;
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    out[(5 + i) * ns + s] = fn[i];
-    out[(32 + i) * ns + s] = gn[i];
+    out[(5 + i) * ld + s] = fn[i];
+    out[(32 + i) * ld + s] = gn[i];
   });
 }
 
+// Targets [0, n_one) read one point of the reconstruction point space, the
+// others interpolate four (the last separable Lagrange pass, Eq. interp).
 template <typename R>
 __global__ void __launch_bounds__(128) k_th_explode(PatchDev pc, R* __restrict__ fo_c, R* __restrict__ go_c,
                                                     const uint32_t* __restrict__ ex_node,
-                                                    const uint32_t* __restrict__ ex_first,
-                                                    const uint8_t* __restrict__ ex_mask,
-                                                    const uint32_t* __restrict__ ex_sample, long long n,
-                                                    const R* __restrict__ smp, long long ns, ThParams<R> tc) {
+                                                    const uint4* __restrict__ ex_src, long long n_one, long long n,
+                                                    const R* __restrict__ val, long long ld, ThParams<R> tc) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  const R w4[4] = {R(-1.0 / 16.0), R(9.0 / 16.0), R(9.0 / 16.0), R(-1.0 / 16.0)};
-  const uint8_t mask = ex_mask[k];
-  const int cx = (mask & 1) ? 4 : 1, cy = (mask & 2) ? 4 : 1, cz = (mask & 4) ? 4 : 1;
-  uint32_t j = ex_first[k];
-  R m[5] = {0, 0, 0, 0, 0};
-  R f[27], g[27];
+  const uint4 s = __ldg(ex_src + k);
+  const bool one = k < n_one;
+  const R w0 = R(-1.0 / 16.0), w1 = R(9.0 / 16.0);
+  auto ip = [&](int c) {
+    const R* v = val + (long long)c * ld;
+    if (one) return __ldg(v + s.x);
+    return w0 * (__ldg(v + s.x) + __ldg(v + s.w)) + w1 * (__ldg(v + s.y) + __ldg(v + s.z));
+  };
+  R m[5], f[27], g[27];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) m[c] = ip(c);
   unroll<27>([&](auto I) {
-    f[decltype(I)::value] = R(0);
-    g[decltype(I)::value] = R(0);
+    constexpr int i = decltype(I)::value;
+    f[i] = ip(5 + i);
+    g[i] = ip(32 + i);
   });
-  for (int kz = 0; kz < cz; ++kz) {
-    const R wz = cz == 4 ? w4[kz] : R(1);
-    for (int ky = 0; ky < cy; ++ky) {
-      const R wyz = wz * (cy == 4 ? w4[ky] : R(1));
-      for (int kx = 0; kx < cx; ++kx) {
-        const R w = wyz * (cx == 4 ? w4[kx] : R(1));
-        const long long s = ex_sample[j++];
-        for (int c = 0; c < 5; ++c) m[c] += w * smp[c * ns + s];
-        unroll<27>([&](auto I) {
-          constexpr int i = decltype(I)::value;
-          f[i] += w * smp[(5 + i) * ns + s];
-          g[i] += w * smp[(32 + i) * ns + s];
-        });
-      }
-    }
-  }
   const R rho_t = m[0], rho = R(1) + rho_t, ux = m[1], uy = m[2], uz = m[3], T_d = m[4];
   // 2 rho E - 1 = rho (3 T + u^2) - 1 = rho_t + rho (3 (T - T0) + u^2)
   const R e_t = rho_t + rho * (R(3) * T_d + ux * ux + uy * uy + uz * uz);
@@ -502,26 +493,26 @@ cudaError_t launch_th_coalesce(int storage, const PatchDev& child, const void* f
 
 cudaError_t launch_th_samples(int storage, const PatchDev& parent, const void* fin_p, const void* gin_p,
                               const PatchDev& child, const void* fin_c, const void* gin_c, const uint32_t* smp_node,
-                              const uint8_t* smp_kind, int64_t ns, void* smp_val, double ff, double fg,
+                              const uint8_t* smp_kind, int64_t ns, void* smp_val, int64_t ld, double ff, double fg,
                               const ThermalLevel& Lp, const ThermalLevel& Lc, int* status, cudaStream_t st) {
   if (ns == 0) return cudaSuccess;
   return th_dispatch(storage, [&](auto z) {
     using R = decltype(z);
     k_th_samples<R><<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(
         parent, (const R*)fin_p, (const R*)gin_p, child, (const R*)fin_c, (const R*)gin_c, smp_node, smp_kind, ns,
-        (R*)smp_val, (R)ff, (R)fg, th_params<R>(Lp), th_params<R>(Lc), status);
+        (R*)smp_val, ld, (R)ff, (R)fg, th_params<R>(Lp), th_params<R>(Lc), status);
     return cudaGetLastError();
   });
 }
 
 cudaError_t launch_th_explode(int storage, const PatchDev& child, void* fo_c, void* go_c, const uint32_t* ex_node,
-                              const uint32_t* ex_first, const uint8_t* ex_mask, const uint32_t* ex_sample, int64_t n,
-                              const void* smp_val, int64_t ns, const ThermalLevel& Lc, cudaStream_t st) {
+                              const uint32_t* ex_src, int64_t n_one, int64_t n, const void* val, int64_t ld,
+                              const ThermalLevel& Lc, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   return th_dispatch(storage, [&](auto z) {
     using R = decltype(z);
-    k_th_explode<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(child, (R*)fo_c, (R*)go_c, ex_node, ex_first,
-                                                                 ex_mask, ex_sample, n, (const R*)smp_val, ns,
+    k_th_explode<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(child, (R*)fo_c, (R*)go_c, ex_node,
+                                                                 (const uint4*)ex_src, n_one, n, (const R*)val, ld,
                                                                  th_params<R>(Lc));
     return cudaGetLastError();
   });
