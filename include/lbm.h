@@ -167,9 +167,17 @@ lbm_status lbm_moments(lbm_grid_t g, int32_t patch, void* rho, void* u, void* T,
 lbm_status lbm_get_populations(lbm_grid_t g, int32_t patch, int32_t which, void* dst, int32_t dtype);
 lbm_status lbm_set_populations(lbm_grid_t g, int32_t patch, int32_t which, const void* src, int32_t dtype);
 
-/* Sets the body acceleration (coarse units) and, if drag_out is non-NULL,
- * returns the FP64 momentum-exchange force on the solid nodes of the current
- * state (coarse units, summed over levels).  Synchronises when drag_out is set. */
+/* Sets the body acceleration (coarse units) when accel0 is non-NULL and, when
+ * drag_out is non-NULL, returns the drag F_d of Sec. IV A 2 (flow past a
+ * sphere) as the FP64 momentum-exchange force of half-way bounce-back on the
+ * solid nodes: every link from a fluid node x to a solid neighbour x + c_j
+ * hands the solid 2 c_j f'_j(x), evaluated on the current post-collision
+ * state (what the next substep streams), scaled by 4^-level (a level-l node
+ * holds 8^-l of a coarse volume, a substep lasts 2^-l of a coarse step) and
+ * summed over levels: drag_out[3], coarse units.  Zeros for grids without
+ * solid nodes.  Synchronises the bound stream when drag_out is set; needs a
+ * bound grid (LBM_ERR_STATE otherwise).  Changing the force drops the
+ * captured step graphs. */
 lbm_status lbm_force(lbm_grid_t g, const double* accel0, double* drag_out);
 
 /* Same results as lbm_diagnostics, for callers that must not allocate device

@@ -913,6 +913,37 @@ struct Sim {
         }
   }
 
+  // Drag F_d of Sec. IV A 2 (flow past a sphere), read as the momentum-exchange
+  // force of half-way bounce-back: a post-collision population f'_j at a fluid
+  // node x whose neighbour x + c_j is solid returns as f_{-j}(x), handing the
+  // solid 2 c_j f'_j per substep.  Coarse units: a level-l node carries
+  // 8^-l of a coarse volume and a level-l substep lasts 2^-l of a coarse step,
+  // so each link counts 2 c_j f'_j 4^-l.  Evaluated on the current
+  // post-collision state (what the next substep streams).
+  void drag(double F[3]) const {
+    F[0] = F[1] = F[2] = 0;
+    for (const auto& p : P) {
+      const double scale = 1.0 / (double)(1L << (2 * p.level));
+      for (long m = 0; m < p.size(); ++m) {
+        if (!p.exists[m] || p.solid[m] || !p.vpost[m]) continue;
+        long X[3];
+        coords(p, m, X);
+        for (int j = 0; j < Q; ++j) {
+          long S[3];
+          bool inside = true;
+          for (int a = 0; a < 3; ++a) {
+            S[a] = X[a] + cvel(j, a);
+            if (!periodic(a) && (S[a] < 0 || S[a] > maxc(p.level, a))) inside = false;
+          }
+          if (!inside) continue;
+          wrap(p.level, S);
+          if (!solid_at(p.level, S)) continue;
+          for (int a = 0; a < 3; ++a) F[a] += 2.0 * cvel(j, a) * p.post[m][j] * scale;
+        }
+      }
+    }
+  }
+
   double node_updates_per_step() const {
     double s = 0;
     for (auto& p : P) {
@@ -1140,6 +1171,9 @@ int orc_moments(void* h, int p, double* rho, double* u, double* T, double* gamma
 }
 
 double orc_node_updates_per_step(void* h) { return static_cast<Sim*>(h)->node_updates_per_step(); }
+
+// Momentum-exchange force on the solid nodes of the current state (coarse units).
+void orc_drag(void* h, double* F) { static_cast<Sim*>(h)->drag(F); }
 
 // ---- single-node functions for the pins -----------------------------------
 void orc_feq(double rho, const double* u, double* out) {

@@ -84,6 +84,7 @@ def lib():
             L.orc_moments.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, dp, dp, dp]
             L.orc_node_updates_per_step.restype = ctypes.c_double
             L.orc_node_updates_per_step.argtypes = [ctypes.c_void_p]
+            L.orc_drag.argtypes = [ctypes.c_void_p, dp]
             L.orc_feq.argtypes = [ctypes.c_double, dp, dp]
             L.orc_split.argtypes = [dp, dp, dp, dp]
             L.orc_collide.restype = ctypes.c_double
@@ -290,3 +291,9 @@ class Oracle:
 
     def node_updates_per_step(self) -> float:
         return float(lib().orc_node_updates_per_step(self._h))
+
+    def drag(self) -> np.ndarray:
+        """Momentum-exchange force on the solid nodes of the current state (coarse units)."""
+        F = np.zeros(3)
+        lib().orc_drag(self._h, _dp(F))
+        return F

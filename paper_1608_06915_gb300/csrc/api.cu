@@ -213,9 +213,13 @@ lbm_status run_instant(lbm_grid* g, int k) {
             timed(g, 0, lev, g->timing ? count_types(p, odd) : 0.0,
                   [&] {
                     cudaError_t e = lbmk::launch_sc_tma(storage, p.tmap[p.cur], p.tmapo[1 - p.cur], p.tmapw[p.cur],
-                                                        pv, at<unsigned long long>(g, p.off_tiles_pure[odd]),
+                                                        pv, fin, at<unsigned long long>(g, p.off_tiles_pure[odd]),
                                                         (int64_t)p.tiles_pure[odd].size(), p.beta, F, lbgk,
                                                         status_ptr(g), g->stream);
+                    if (e) return e;
+                    e = lbmk::launch_sc_nodes(storage, pv, fin, fout, at<uint32_t>(g, p.off_fix_nodes[odd]),
+                                              (int64_t)p.fix_nodes[odd].size(), p.beta, F, lbgk, status_ptr(g),
+                                              g->stream);
                     if (e) return e;
                     return lbmk::launch_sc_tiles(storage, pv, fin, fout, at<uint32_t>(g, p.off_tiles_mixed[odd]),
                                                  (int64_t)p.tiles_mixed[odd].size(), (int)p.ntx, p.beta, F, odd,
@@ -408,10 +412,13 @@ lbm_status lbm_grid_bind(lbm_grid_t g, void* dev_ptr, size_t bytes, void* cuda_s
     if (!e) e = up(p.off_smp_kind, p.smp_kind.data(), p.smp_kind.size());
     if (!e) e = up(p.off_cf_parent, p.cf_parent.data(), 4 * p.cf_parent.size());
     if (!e) e = up(p.off_cf_child, p.cf_child.data(), 4 * p.cf_child.size());
+    if (!e) e = up(p.off_drag_node, p.drag_node.data(), 4 * p.drag_node.size());
+    if (!e) e = up(p.off_drag_mask, p.drag_mask.data(), 4 * p.drag_mask.size());
     for (int k = 0; k < 2; ++k)
       if (!e) e = up(p.off_tiles_pure[k], p.tiles_pure[k].data(), 8 * p.tiles_pure[k].size());
     for (int k = 0; k < 2; ++k) {
       if (!e) e = up(p.off_tiles_mixed[k], p.tiles_mixed[k].data(), 4 * p.tiles_mixed[k].size());
+      if (!e) e = up(p.off_fix_nodes[k], p.fix_nodes[k].data(), 4 * p.fix_nodes[k].size());
       if (!e) e = up(p.off_tiles_all[k], p.tiles_all[k].data(), 4 * p.tiles_all[k].size());
     }
     p.cur = 0;
@@ -949,7 +956,28 @@ lbm_status lbm_force(lbm_grid_t g, const double* accel0, double* drag_out) {
     for (int a = 0; a < 3; ++a) g->accel[a] = accel0[a];
     g->drop_graphs();  // the force is baked into the captured launches
   }
-  if (drag_out) return fail(g, LBM_ERR_STATE, "drag not available in this build");
+  if (!drag_out) return LBM_OK;
+  if (lbm_status s = check_bound(g)) return s;
+  double* partial = at<double>(g, g->off_partial);
+  int nb = 0;
+  cudaError_t e = cudaSuccess;
+  for (auto& p : g->hg.P) {
+    if (p.drag_node.empty()) continue;
+    if (!e)
+      e = lbmk::launch_drag(g->hg.desc.storage, g->base + p.off_f[p.cur], p.plane, at<uint32_t>(g, p.off_drag_node),
+                            at<uint32_t>(g, p.off_drag_mask), (int64_t)p.drag_node.size(),
+                            1.0 / (double)(1LL << (2 * p.level)), partial + 3 * nb, kDiagBlocks, g->stream);
+    nb += kDiagBlocks;
+  }
+  double host[3] = {0, 0, 0};
+  if (nb > 0) {
+    double* dout = at<double>(g, g->off_diag_out);
+    if (!e) e = lbmk::launch_drag_final(partial, nb, dout, g->stream);
+    if (!e) e = cudaMemcpyAsync(host, dout, sizeof host, cudaMemcpyDeviceToHost, g->stream);
+    if (!e) e = cudaStreamSynchronize(g->stream);
+    if (e) return cuda_check(g, e, "lbm_force drag");
+  }
+  for (int a = 0; a < 3; ++a) drag_out[a] = host[a];
   return LBM_OK;
 }
 

@@ -47,11 +47,11 @@ struct HostPatch {
 
   // stream-collide work lists: tiles of 128 nodes along x, id = (z*ny + y)*ntx + tx
   int64_t ntx = 0;
-  // TMA path ([0] even steps: every node a plain bulk node; [1] odd steps: every
-  // node a plain bulk node or a depth-1 node with plain sources): x-tile | y<<16 | z<<32
+  // TMA path ([0] even, [1] odd substeps): x-tile | y<<16 | z<<32 | bounce mask<<48 | flags<<57
   std::vector<uint64_t> tiles_pure[2];
   std::vector<uint32_t> tiles_mixed[2];  // other tiles with nodes to update: [0] even, [1] odd steps
   std::vector<uint32_t> tiles_all[2];    // every tile with nodes to update (thermal model, node by node)
+  std::vector<uint32_t> fix_nodes[2];    // nodes of TMA tiles recomputed node by node after the tile pass
   alignas(64) unsigned char tmap[2][128];   // TMA load descriptors of the two population buffers
   alignas(64) unsigned char tmapo[2][128];  // TMA store descriptors
   alignas(64) unsigned char tmapw[2][128];  // TMA 16-byte wrap descriptors
@@ -69,12 +69,15 @@ struct HostPatch {
   std::vector<uint8_t> smp_kind;    // per sample: S_PARENT / S_CHILD
   std::vector<uint32_t> cf_parent;  // coalesce: parent twin node
   std::vector<uint32_t> cf_child;   // coalesce: coinciding child node
+  // momentum exchange: fluid nodes next to a solid node, bit j set when x + c_j is solid
+  std::vector<uint32_t> drag_node, drag_mask;
 
   // device placement (byte offsets into the bound buffer)
   size_t off_f[2]{}, off_g[2]{}, off_type = 0;
-  size_t off_tiles_pure[2]{}, off_tiles_mixed[2]{}, off_tiles_all[2]{};
+  size_t off_tiles_pure[2]{}, off_tiles_mixed[2]{}, off_tiles_all[2]{}, off_fix_nodes[2]{};
   size_t off_ex_node = 0, off_ex_src = 0, off_pt_src = 0;
   size_t off_smp_node = 0, off_smp_kind = 0, off_smp_val = 0, off_cf_parent = 0, off_cf_child = 0;
+  size_t off_drag_node = 0, off_drag_mask = 0;
   int cur = 0;  // which population buffer holds the current state
   size_t n_points() const { return smp_node.size() + n_pt[0] + n_pt[1]; }
 };

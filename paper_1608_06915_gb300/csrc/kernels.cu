@@ -493,6 +493,64 @@ cudaError_t launch_diag_final(const double* partial, int total_blocks, double* o
 }
 
 // ---------------------------------------------------------------------------
+// Momentum exchange of half-way bounce-back (drag of Sec. IV A 2): every link
+// from a fluid node x to a solid neighbour x + c_j hands the solid 2 c_j f'_j(x)
+// per substep; scale = 4^-level converts to coarse units.  FP64 per-block sums.
+template <typename S>
+__global__ void __launch_bounds__(256) k_drag(const S* __restrict__ fin, long long plane,
+                                              const uint32_t* __restrict__ node, const uint32_t* __restrict__ mask,
+                                              long long n, double scale, double* __restrict__ partial) {
+  double acc[3] = {0, 0, 0};
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const uint32_t m = mask[k];
+    const long long nd = node[k];
+    unroll<27>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      if ((m >> j) & 1u) {
+        const double f = WI(j) + (double)Stor<S>::ld(fin + (long long)j * plane + nd);
+        if constexpr (CX(j) != 0) acc[0] += 2.0 * CX(j) * f;
+        if constexpr (CY(j) != 0) acc[1] += 2.0 * CY(j) * f;
+        if constexpr (CZ(j) != 0) acc[2] += 2.0 * CZ(j) * f;
+      }
+    });
+  }
+  __shared__ double sh[8][3];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double v[3];
+  for (int a = 0; a < 3; ++a) v[a] = warp_sum(acc[a]);
+  if (lane == 0)
+    for (int a = 0; a < 3; ++a) sh[wid][a] = v[a];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w][threadIdx.x];
+    partial[blockIdx.x * 3 + threadIdx.x] = scale * t;
+  }
+}
+
+__global__ void k_drag_final(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  if (threadIdx.x >= 3) return;
+  double t = 0;
+  for (int b = 0; b < nb; ++b) t += partial[b * 3 + threadIdx.x];
+  out[threadIdx.x] = t;
+}
+
+cudaError_t launch_drag(int storage, const void* fin, int64_t plane, const uint32_t* node, const uint32_t* mask,
+                        int64_t n, double scale, double* partial, int blocks, cudaStream_t st) {
+  return dispatch(storage, [&](auto ts, auto) {
+    using S = typename decltype(ts)::type;
+    k_drag<S><<<blocks, 256, 0, st>>>((const S*)fin, plane, node, mask, n, scale, partial);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_drag_final(const double* partial, int total_blocks, double* out3, cudaStream_t st) {
+  k_drag_final<<<1, 32, 0, st>>>(partial, total_blocks, out3);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 template <typename R>
 __global__ void k_collide_nodes(const R* __restrict__ fin, R* __restrict__ fout, R* __restrict__ gam, long long n,
                                 R beta, R dux, R duy, R duz, int lbgk, int force) {

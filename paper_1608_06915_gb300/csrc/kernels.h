@@ -77,9 +77,13 @@ cudaError_t launch_adj_grad_u0(int storage, const PatchDev& p, const void* fin, 
 // the store box, and of the source buffer with the wrap box; tiles:
 // x-tile | y << 16 | z << 32) and mixed tiles node by node (tile id
 // = (z * ny + y) * ntx + tx); a tile is 128 nodes along x.
+// fin: the current population buffer (the fixed inlet nodes are copied from it).
 cudaError_t launch_sc_tma(int storage, const void* tmap_in, const void* tmap_out, const void* tmap_wrap,
-                          const PatchDev& p, const unsigned long long* tiles, int64_t ntiles, double beta,
-                          const Force& F, int lbgk, int* status, cudaStream_t st);
+                          const PatchDev& p, const void* fin, const unsigned long long* tiles, int64_t ntiles,
+                          double beta, const Force& F, int lbgk, int* status, cudaStream_t st);
+// node-by-node recomputation of listed nodes (after the TMA tile pass)
+cudaError_t launch_sc_nodes(int storage, const PatchDev& p, const void* fin, void* fout, const uint32_t* nodes,
+                            int64_t n, double beta, const Force& F, int lbgk, int* status, cudaStream_t st);
 cudaError_t launch_sc_tiles(int storage, const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,
                             int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk, int* status,
                             cudaStream_t st);
@@ -119,6 +123,10 @@ cudaError_t launch_copy_pop(int storage, const PatchDev& p, void* fstore, void* 
 cudaError_t launch_diag(int storage, const PatchDev& p, const void* fin, double vol_weight, const Force& F,
                         double* partial, int blocks, cudaStream_t st);
 cudaError_t launch_diag_final(const double* partial, int total_blocks, double* out8, cudaStream_t st);
+// momentum-exchange force: per-block FP64 sums [blocks][3] of 2 c_j f'_j * scale over the links
+cudaError_t launch_drag(int storage, const void* fin, int64_t plane, const uint32_t* node, const uint32_t* mask,
+                        int64_t n, double scale, double* partial, int blocks, cudaStream_t st);
+cudaError_t launch_drag_final(const double* partial, int total_blocks, double* out3, cudaStream_t st);
 
 cudaError_t launch_collide_nodes(const void* fin, void* fout, void* gamma, int64_t n, double beta, const Force& F,
                                  int lbgk, int dtype, cudaStream_t st);

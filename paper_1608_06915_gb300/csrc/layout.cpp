@@ -382,27 +382,41 @@ std::string build_layout(HostGrid& g) {
   }
   // stream-collide tiles
   //
-  // A tile (128 nodes along x at one (y, z)) goes to the TMA path when every
-  // node in it is updated in that substep and, for each of the 9 source rows
-  // (c_y, c_z), either all its pulls read the neighbour row (wrapping only on
-  // spanned axes) or all bounce back from a wall across y or z; bit j of the
-  // tile's bounce mask marks row j = (c_y + 1) + 3 (c_z + 1) bounced.
+  // A tile is 128 nodes along x at one (y, z).  The TMA path updates every
+  // node of a tile from one rule per source row j = (c_y + 1) + 3 (c_z + 1):
+  // pull from the neighbour row (wrapping only on spanned axes), or bounce back
+  // when that row lies beyond a wall across y or z (bit j of the tile's bounce
+  // mask); the first node of a row may be a fixed inlet node (written back
+  // unchanged) and the last the zero-gradient outlet.  Nodes that are not
+  // updated in the substep -- depth-0 and, on even substeps, depth-1 interface
+  // nodes, parent twins, hole and solid nodes -- are overwritten too: explode
+  // and coalesce rewrite the interface nodes later in the same instant, and no
+  // valid node ever reads the others.  Updated nodes whose pulls the row rule
+  // does not give (solid neighbours, x walls) are recomputed node by node
+  // right after the tile pass (fix-up list); a tile with more such nodes than
+  // regular ones goes to the node-by-node path whole.
   // Source of population i at patch-local L: 0 plain neighbour, 1 bounce-back
-  // from a y or z wall, 2 anything else (solid, x wall, outlet).
+  // from a y or z wall, 3 the zero-gradient outlet across x (the node itself
+  // along x), 2 anything else (solid, x wall).
   auto outcome = [&](const HostPatch& p, const int64_t L[3], int i) -> int {
     const int64_t X[3] = {p.org[0] + L[0], p.org[1] + L[1], p.org[2] + L[2]};
     int64_t src;
     const int r = geo.resolve(p, X, i, &src);
-    if (r == 0) {
+    if (r == 0 || r == 2) {
+      const bool clamp = r == 2;
+      if (clamp && !(d.inflow_axis == 0 && cvel(i, 0) == -1 && X[0] == g.maxc(p.level, 0) &&
+                     L[0] == p.dim[0] - 1))
+        return 2;
       int64_t S[3];
       for (int a = 0; a < 3; ++a) {
-        S[a] = L[a] - cvel(i, a);
+        S[a] = L[a] - (clamp && a == 0 ? 0 : cvel(i, a));
         if (S[a] < 0 || S[a] >= p.dim[a]) {
           if (!p.span[a]) return 2;
           S[a] += S[a] < 0 ? p.dim[a] : -p.dim[a];
         }
       }
-      return src == (S[2] * p.dim[1] + S[1]) * p.nxp + S[0] ? 0 : 2;
+      if (src != (S[2] * p.dim[1] + S[1]) * p.nxp + S[0]) return 2;
+      return clamp ? 3 : 0;
     }
     if (r != 1) return 2;
     bool yz = false;
@@ -419,49 +433,51 @@ std::string build_layout(HostGrid& g) {
       p.tiles_pure[k].clear();
       p.tiles_mixed[k].clear();
       p.tiles_all[k].clear();
+      p.fix_nodes[k].clear();
     }
     struct Rows {
       std::vector<uint64_t> pure[2];
-      std::vector<uint32_t> mixed[2], all[2];
+      std::vector<uint32_t> mixed[2], all[2], fix[2];
     };
     std::vector<Rows> rows(p.dim[2]);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t z = 0; z < p.dim[2]; ++z) {
       Rows& R = rows[z];
-      for (int64_t y = 0; y < p.dim[1]; ++y)
+      for (int64_t y = 0; y < p.dim[1]; ++y) {
+        // the row rule: source rows beyond a wall across y or z bounce back
+        uint32_t bm = 0;
+        for (int j = 0; j < 9; ++j) {
+          const int64_t sy = p.org[1] + y - ((j % 3) - 1), sz = p.org[2] + z - ((j / 3) - 1);
+          const bool by = !g.periodic(1) && ((sy < 0 && g.wall(1, 0)) || (sy > g.maxc(p.level, 1) && g.wall(1, 1)));
+          const bool bz = !g.periodic(2) && ((sz < 0 && g.wall(2, 0)) || (sz > g.maxc(p.level, 2) && g.wall(2, 1)));
+          if (by || bz) bm |= 1u << j;
+        }
         for (int64_t tx = 0; tx < p.ntx; ++tx) {
-          // per substep parity k: nodes updated / not updated, row states (-1 unseen, 0 plain, 1 bounce)
-          int active[2] = {0, 0}, idle[2] = {0, 0}, state[2][9];
-          bool ok[2] = {true, true};
-          for (int k = 0; k < 2; ++k)
-            for (int j = 0; j < 9; ++j) state[k][j] = -1;
-          auto merge = [&](int k, int j, int o) {
-            if (state[k][j] < 0) state[k][j] = o;
-            else if (state[k][j] != o) ok[k] = false;
-          };
+          int active[2] = {0, 0};
+          bool inlet = false, outlet = false;
+          std::vector<uint32_t> odd_nodes[2];  // updated nodes the row rule does not give
           for (int64_t x = tx * 128; x < std::min<int64_t>(p.dim[0], tx * 128 + 128); ++x) {
             const int64_t m = (z * p.dim[1] + y) * p.nxp + x;
             const uint8_t t = p.type[m];
+            if (t == T_INLET && d.inflow_axis == 0 && x == 0 && p.org[0] == 0) inlet = true;
             bool act[2];
             act[0] = t == T_BULK || t == T_BC;
             act[1] = act[0] || t == T_D1;
-            for (int k = 0; k < 2; ++k) (act[k] ? active[k] : idle[k]) += 1;
             if (!act[1]) continue;
-            if (t == T_BULK) {
+            for (int k = 0; k < 2; ++k) active[k] += act[k];
+            bool regular = true;
+            if (t != T_BULK) {
+              const int64_t L[3] = {x, y, z};
+              for (int i = 0; i < 27 && regular; ++i) {
+                const int o = outcome(p, L, i);
+                if ((bm >> (i / 3)) & 1u) regular = o == 1;
+                else if (o == 3) outlet = true;  // the outlet node reads itself along x
+                else regular = o == 0;
+              }
+            }
+            if (!regular)
               for (int k = 0; k < 2; ++k)
-                for (int j = 0; j < 9; ++j) merge(k, j, 0);
-              continue;
-            }
-            const int64_t L[3] = {x, y, z};
-            int o[27];
-            bool good = true;
-            for (int i = 0; i < 27 && good; ++i) good = (o[i] = outcome(p, L, i)) != 2;
-            for (int k = 0; k < 2; ++k) {
-              if (!act[k]) continue;
-              if (!good) ok[k] = false;
-              else
-                for (int i = 0; i < 27; ++i) merge(k, i / 3, o[i]);
-            }
+                if (act[k]) odd_nodes[k].push_back((uint32_t)m);
           }
           const uint32_t id = (uint32_t)((z * p.dim[1] + y) * p.ntx + tx);
           // the TMA path fetches the periodic wrap of x-spanning rows as 16-byte
@@ -471,23 +487,57 @@ std::string build_layout(HostGrid& g) {
           for (int k = 0; k < 2; ++k) {
             if (active[k] == 0) continue;
             R.all[k].push_back(id);
-            if (ok[k] && idle[k] == 0 && wrap_ok) {
-              uint64_t bm = 0;
-              for (int j = 0; j < 9; ++j)
-                if (state[k][j] == 1) bm |= 1ull << j;
-              R.pure[k].push_back((uint64_t)tx | ((uint64_t)y << 16) | ((uint64_t)z << 32) | (bm << 48));
+            const int nodd = (int)odd_nodes[k].size();
+            if (wrap_ok && 2 * nodd <= active[k]) {
+              const uint64_t fl = (inlet ? 1ull : 0ull) | (outlet ? 2ull : 0ull);
+              R.pure[k].push_back((uint64_t)tx | ((uint64_t)y << 16) | ((uint64_t)z << 32) | ((uint64_t)bm << 48) |
+                                  (fl << 57));
+              R.fix[k].insert(R.fix[k].end(), odd_nodes[k].begin(), odd_nodes[k].end());
             } else {
               R.mixed[k].push_back(id);
             }
           }
         }
+      }
     }
     for (auto& R : rows)
       for (int k = 0; k < 2; ++k) {
         p.tiles_pure[k].insert(p.tiles_pure[k].end(), R.pure[k].begin(), R.pure[k].end());
         p.tiles_mixed[k].insert(p.tiles_mixed[k].end(), R.mixed[k].begin(), R.mixed[k].end());
         p.tiles_all[k].insert(p.tiles_all[k].end(), R.all[k].begin(), R.all[k].end());
+        p.fix_nodes[k].insert(p.fix_nodes[k].end(), R.fix[k].begin(), R.fix[k].end());
       }
+  }
+  // momentum-exchange links of patches holding solid nodes
+  for (auto& p : g.P) {
+    p.drag_node.clear();
+    p.drag_mask.clear();
+    bool any = false;
+    for (int64_t n = 0; n < p.plane && !any; ++n) any = p.type[n] == T_SOLID;
+    if (!any) continue;
+    int64_t X[3];
+    for (int64_t n = 0; n < p.plane; ++n) {
+      const uint8_t t = p.type[n];
+      if (t == T_SKIP || t == T_SOLID) continue;
+      geo.coords(p, n, X);
+      uint32_t m = 0;
+      for (int j = 0; j < 27; ++j) {
+        int64_t S[3];
+        bool inside = true;
+        for (int a = 0; a < 3; ++a) {
+          S[a] = X[a] + cvel(j, a);
+          if (!g.periodic(a) && (S[a] < 0 || S[a] > g.maxc(p.level, a))) inside = false;
+        }
+        if (!inside) continue;
+        geo.wrap(p.level, S);
+        const int64_t s = geo.index(p, S);
+        if (s >= 0 && p.type[s] == T_SOLID) m |= 1u << j;
+      }
+      if (m) {
+        p.drag_node.push_back((uint32_t)n);
+        p.drag_mask.push_back(m);
+      }
+    }
   }
   // interface tables, stored on the child
   for (size_t ci = 1; ci < g.P.size(); ++ci) {
@@ -711,6 +761,8 @@ size_t plan_memory(HostGrid& g) {
     p.off_tiles_all[1] = take(4 * p.tiles_all[1].size());
     p.off_tiles_mixed[0] = take(4 * p.tiles_mixed[0].size());
     p.off_tiles_mixed[1] = take(4 * p.tiles_mixed[1].size());
+    p.off_fix_nodes[0] = take(4 * p.fix_nodes[0].size());
+    p.off_fix_nodes[1] = take(4 * p.fix_nodes[1].size());
     p.off_ex_node = take(4 * p.ex_node.size());
     p.off_ex_src = take(4 * p.ex_src.size());
     p.off_pt_src = take(4 * p.pt_src.size());
@@ -719,6 +771,8 @@ size_t plan_memory(HostGrid& g) {
     p.off_smp_val = take(ncomp * p.n_points() * g.real_bytes);
     p.off_cf_parent = take(4 * p.cf_parent.size());
     p.off_cf_child = take(4 * p.cf_child.size());
+    p.off_drag_node = take(4 * p.drag_node.size());
+    p.off_drag_mask = take(4 * p.drag_mask.size());
   }
   return off;
 }

@@ -4,17 +4,17 @@
 namespace lbmk {
 
 cudaError_t launch_sc_tma(int storage, const void* tmap_in, const void* tmap_out, const void* tmap_wrap,
-                          const PatchDev& p, const unsigned long long* tiles, int64_t ntiles, double beta,
-                          const Force& F, int lbgk, int* status, cudaStream_t st) {
+                          const PatchDev& p, const void* fin, const unsigned long long* tiles, int64_t ntiles,
+                          double beta, const Force& F, int lbgk, int* status, cudaStream_t st) {
   switch (storage) {
     case LBM_FP64:
-      return sc_tma_fp64(tmap_in, tmap_out, tmap_wrap, p, tiles, ntiles, beta, F, lbgk, status, st);
+      return sc_tma_fp64(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, ntiles, beta, F, lbgk, status, st);
     case LBM_FP32:
-      return sc_tma_fp32(tmap_in, tmap_out, tmap_wrap, p, tiles, ntiles, beta, F, lbgk, status, st);
+      return sc_tma_fp32(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, ntiles, beta, F, lbgk, status, st);
     case LBM_FP16_SHIFT:
-      return sc_tma_fp16(tmap_in, tmap_out, tmap_wrap, p, tiles, ntiles, beta, F, lbgk, status, st);
+      return sc_tma_fp16(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, ntiles, beta, F, lbgk, status, st);
     case LBM_BF16_SHIFT:
-      return sc_tma_bf16(tmap_in, tmap_out, tmap_wrap, p, tiles, ntiles, beta, F, lbgk, status, st);
+      return sc_tma_bf16(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, ntiles, beta, F, lbgk, status, st);
     default:
       return cudaErrorInvalidValue;
   }
@@ -32,6 +32,22 @@ cudaError_t launch_sc_tiles(int storage, const PatchDev& p, const void* fin, voi
       return sc_tiles_fp16(p, fin, fout, tiles, ntiles, ntx, beta, F, odd, lbgk, status, st);
     case LBM_BF16_SHIFT:
       return sc_tiles_bf16(p, fin, fout, tiles, ntiles, ntx, beta, F, odd, lbgk, status, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_sc_nodes(int storage, const PatchDev& p, const void* fin, void* fout, const uint32_t* nodes,
+                            int64_t n, double beta, const Force& F, int lbgk, int* status, cudaStream_t st) {
+  switch (storage) {
+    case LBM_FP64:
+      return sc_nodes_fp64(p, fin, fout, nodes, n, beta, F, lbgk, status, st);
+    case LBM_FP32:
+      return sc_nodes_fp32(p, fin, fout, nodes, n, beta, F, lbgk, status, st);
+    case LBM_FP16_SHIFT:
+      return sc_nodes_fp16(p, fin, fout, nodes, n, beta, F, lbgk, status, st);
+    case LBM_BF16_SHIFT:
+      return sc_nodes_bf16(p, fin, fout, nodes, n, beta, F, lbgk, status, st);
     default:
       return cudaErrorInvalidValue;
   }

@@ -174,13 +174,16 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 
 __device__ __forceinline__ int wrap_axis(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// tile list entries: x-tile | y << 16 | z << 32 | bounce mask << 48
+// tile list entries: x-tile | y << 16 | z << 32 | bounce mask << 48 | flags << 57
+// (flag 1: the row's first node is a fixed inlet node; flag 2: its last node
+// is the zero-gradient outlet)
 __device__ __forceinline__ void tile_xyz(unsigned long long t, int& tx, int& y, int& z) {
   tx = (int)(t & 0xffffu);
   y = (int)((t >> 16) & 0xffffu);
   z = (int)((t >> 32) & 0xffffu);
 }
 __device__ __forceinline__ int tile_bounce(unsigned long long t) { return (int)((t >> 48) & 0x1ffu); }
+__device__ __forceinline__ int tile_flags(unsigned long long t) { return (int)((t >> 57) & 3u); }
 
 // Shared-memory row of population i in a load stage (elements): group i / 3,
 // row i % 3 of the three-row box.
@@ -195,6 +198,11 @@ __device__ __forceinline__ constexpr int row_base(int i) {
 // the stage slot of row j then holds the box of populations 3(8 - j) .. 3(8 - j) + 2
 // from the tile's own row, and population 3j + k reads its row 2 - k unshifted.
 //
+// Inflow along x: a fixed inlet node (x = 0) keeps its populations -- its
+// thread reads them from global memory and writes them back unchanged -- and
+// the outlet node (x = dim - 1) pulls its c_x = -1 populations from itself
+// along x (zero gradient), which the stage holds unshifted.
+//
 // Periodic x: the first tile of a row needs, for the 9 populations with
 // c_x = +1 (i = 3j + 2), the element at x = dim - 1; the last tile, for the 9
 // with c_x = -1 (i = 3j), the element at x = 0.  Both come as 16-byte boxes
@@ -205,6 +213,7 @@ template <typename S, typename R, int FM>
 __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensorMap map_in,
                                                 const __grid_constant__ CUtensorMap map_out,
                                                 const __grid_constant__ CUtensorMap map_wrap, PatchDev p,
+                                                const S* __restrict__ fin,
                                                 const unsigned long long* __restrict__ tiles, int ntiles, R beta,
                                                 R dux, R duy, R duz, int lbgk, int* status) {
   using C = TmaCfg<S>;
@@ -251,9 +260,10 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
       const unsigned long long te = tiles[blockIdx.x + (size_t)k * gridDim.x];
       tile_xyz(te, tx, ty, tz);
       const int bm = tile_bounce(te);
+      const int fl = tile_flags(te);
       const bool first = p.span[0] && tx == 0;
       const bool last = p.span[0] && (tx + 1) * C::BX >= p.dim[0];
-      tile_at[s] = make_int4(tx, ty, tz, bm);
+      tile_at[s] = make_int4(tx, ty, tz, bm | (fl << 9));
       const uint32_t txw = 16u * (uint32_t)(9 - __popc(bm));  // wrap boxes of the rows not bounced
       mbar_expect_tx(&full[s], C::TX + (first ? txw : 0u) + (last ? txw : 0u));
       unsigned char* stage = smem + s * C::STAGE;
@@ -291,7 +301,7 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
       return;
     }
     const int4 tc = tile_at[s];
-    const int tx = tc.x, y = tc.y, z = tc.z, bm = tc.w;
+    const int tx = tc.x, y = tc.y, z = tc.z, bm = tc.w & 0x1ff, fl = tc.w >> 9;
     const int x = tx * C::BX + tid;
     const S* st = reinterpret_cast<const S*>(smem + s * C::STAGE);
     R f[27];
@@ -319,9 +329,27 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
         if (!b && !lo && CX(i) == -1) f[i] = SCvt<S>::to(side[(9 + i / 3) * (C::SIDE / (int)sizeof(S))]);
       });
     }
+    bool fixed = false;
+    if (fl) {
+      if ((fl & 2) && x == p.dim[0] - 1) {
+        // zero-gradient outlet: c_x = -1 populations from the node itself along x
+        unroll<27>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          if (CX(i) == -1 && !((bm >> (i / 3)) & 1)) f[i] = SCvt<S>::to(st[row_base<S>(i) + C::H + tid]);
+        });
+      }
+      if ((fl & 1) && x == 0) {
+        fixed = true;
+        const long long own = node_index(p, 0, y, z);
+        unroll<27>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          f[i] = Stor<S>::ld(fin + (long long)i * p.plane + own);
+        });
+      }
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with stage s
-    if (x < p.dim[0]) kbc_collide<R, FM>(f, beta, dux, duy, duz, lbgk != 0);
+    if (x < p.dim[0] && !fixed) kbc_collide<R, FM>(f, beta, dux, duy, duz, lbgk != 0);
     // this warp's output segment in stage o: wait until the stores that last
     // used it have read it, fill it, store it
     const int o = k % C::DO;
@@ -365,10 +393,30 @@ __global__ void __launch_bounds__(128) k_sc_tiles(PatchDev p, const S* __restric
   });
 }
 
+// Fix-up nodes: updated nodes of TMA tiles whose pulls the row rule does not
+// give (solid neighbours, x walls), recomputed node by node after the tile pass.
+template <typename S, typename R, int FM>
+__global__ void __launch_bounds__(128) k_sc_nodes(PatchDev p, const S* __restrict__ fin, S* __restrict__ fout,
+                                                  const uint32_t* __restrict__ nodes, long long n, R beta, R dux,
+                                                  R duy, R duz, int lbgk, int* status) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const long long own = nodes[k];
+  const int x = (int)(own % p.nxp), y = (int)((own / p.nxp) % p.dim[1]);
+  const int z = (int)(own / ((long long)p.nxp * p.dim[1]));
+  R f[27];
+  pull_generic<S, R>(p, fin, x, y, z, f, status);
+  kbc_collide<R, FM>(f, beta, dux, duy, duz, lbgk != 0);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    Stor<S>::st(fout + (long long)i * p.plane + own, f[i]);
+  });
+}
+
 template <typename S, typename R, int FM>
 cudaError_t launch_tma_t(const void* tmap_in, const void* tmap_out, const void* tmap_wrap, const PatchDev& p,
-                         const unsigned long long* tiles, int ntiles, R beta, R dux, R duy, R duz, int lbgk,
-                         int* status, cudaStream_t st) {
+                         const void* fin, const unsigned long long* tiles, int ntiles, R beta, R dux, R duy, R duz,
+                         int lbgk, int* status, cudaStream_t st) {
   using C = TmaCfg<S>;
   static int blocks_per_sm = -1, sms = 0;
   auto kern = k_sc_tma<S, R, FM>;
@@ -387,26 +435,51 @@ cudaError_t launch_tma_t(const void* tmap_in, const void* tmap_out, const void* 
   memcpy(&mi, tmap_in, sizeof mi);
   memcpy(&mo, tmap_out, sizeof mo);
   memcpy(&mw, tmap_wrap, sizeof mw);
-  kern<<<grid, C::THREADS, C::SMEM, st>>>(mi, mo, mw, p, tiles, ntiles, beta, dux, duy, duz, lbgk, status);
+  kern<<<grid, C::THREADS, C::SMEM, st>>>(mi, mo, mw, p, (const S*)fin, tiles, ntiles, beta, dux, duy, duz, lbgk,
+                                          status);
   return cudaGetLastError();
 }
 
 template <typename S, typename R>
 cudaError_t sc_tma_typed(const void* tmap_in, const void* tmap_out, const void* tmap_wrap, const PatchDev& p,
-                         const unsigned long long* tiles, int64_t ntiles, double beta, const Force& F, int lbgk,
-                         int* status, cudaStream_t st) {
+                         const void* fin, const unsigned long long* tiles, int64_t ntiles, double beta, const Force& F,
+                         int lbgk, int* status, cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;
   const R b = (R)beta, dx = (R)F.du[0], dy = (R)F.du[1], dz = (R)F.du[2];
   switch (F.mask()) {
     case 0:
-      return launch_tma_t<S, R, 0>(tmap_in, tmap_out, tmap_wrap, p, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
+      return launch_tma_t<S, R, 0>(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
     case 1:
-      return launch_tma_t<S, R, 1>(tmap_in, tmap_out, tmap_wrap, p, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
+      return launch_tma_t<S, R, 1>(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
     case 4:
-      return launch_tma_t<S, R, 4>(tmap_in, tmap_out, tmap_wrap, p, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
+      return launch_tma_t<S, R, 4>(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
     default:
-      return launch_tma_t<S, R, 7>(tmap_in, tmap_out, tmap_wrap, p, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
+      return launch_tma_t<S, R, 7>(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
   }
+}
+
+template <typename S, typename R>
+cudaError_t sc_nodes_typed(const PatchDev& p, const void* fin, void* fout, const uint32_t* nodes, int64_t n,
+                           double beta, const Force& F, int lbgk, int* status, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const R b = (R)beta, dx = (R)F.du[0], dy = (R)F.du[1], dz = (R)F.du[2];
+  const unsigned grid = (unsigned)((n + 127) / 128);
+  const S* in = (const S*)fin;
+  S* out = (S*)fout;
+  switch (F.mask()) {
+    case 0:
+      k_sc_nodes<S, R, 0><<<grid, 128, 0, st>>>(p, in, out, nodes, n, b, dx, dy, dz, lbgk, status);
+      break;
+    case 1:
+      k_sc_nodes<S, R, 1><<<grid, 128, 0, st>>>(p, in, out, nodes, n, b, dx, dy, dz, lbgk, status);
+      break;
+    case 4:
+      k_sc_nodes<S, R, 4><<<grid, 128, 0, st>>>(p, in, out, nodes, n, b, dx, dy, dz, lbgk, status);
+      break;
+    default:
+      k_sc_nodes<S, R, 7><<<grid, 128, 0, st>>>(p, in, out, nodes, n, b, dx, dy, dz, lbgk, status);
+  }
+  return cudaGetLastError();
 }
 
 template <typename S, typename R>
@@ -436,11 +509,13 @@ cudaError_t sc_tiles_typed(const PatchDev& p, const void* fin, void* fout, const
 // per-storage entry points, one translation unit each
 #define LBM_SC_DECL(NAME)                                                                                        \
   cudaError_t sc_tma_##NAME(const void* tmap_in, const void* tmap_out, const void* tmap_wrap, const PatchDev& p, \
-                            const unsigned long long* tiles, int64_t ntiles, double beta, const Force& F,        \
-                            int lbgk, int* status, cudaStream_t st);                                             \
+                            const void* fin, const unsigned long long* tiles, int64_t ntiles, double beta,       \
+                            const Force& F, int lbgk, int* status, cudaStream_t st);                             \
   cudaError_t sc_tiles_##NAME(const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,             \
                               int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk,           \
-                              int* status, cudaStream_t st);
+                              int* status, cudaStream_t st);                                                     \
+  cudaError_t sc_nodes_##NAME(const PatchDev& p, const void* fin, void* fout, const uint32_t* nodes, int64_t n,  \
+                              double beta, const Force& F, int lbgk, int* status, cudaStream_t st);
 LBM_SC_DECL(fp64)
 LBM_SC_DECL(fp32)
 LBM_SC_DECL(fp16)
@@ -448,14 +523,18 @@ LBM_SC_DECL(bf16)
 
 #define LBM_SC_DEFINE(NAME, S, R)                                                                                \
   cudaError_t sc_tma_##NAME(const void* tmap_in, const void* tmap_out, const void* tmap_wrap, const PatchDev& p, \
-                            const unsigned long long* tiles, int64_t ntiles, double beta, const Force& F,        \
-                            int lbgk, int* status, cudaStream_t st) {                                            \
-    return sc_tma_typed<S, R>(tmap_in, tmap_out, tmap_wrap, p, tiles, ntiles, beta, F, lbgk, status, st);        \
+                            const void* fin, const unsigned long long* tiles, int64_t ntiles, double beta,       \
+                            const Force& F, int lbgk, int* status, cudaStream_t st) {                            \
+    return sc_tma_typed<S, R>(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, ntiles, beta, F, lbgk, status, st);   \
   }                                                                                                              \
   cudaError_t sc_tiles_##NAME(const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,             \
                               int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk,           \
                               int* status, cudaStream_t st) {                                                    \
     return sc_tiles_typed<S, R>(p, fin, fout, tiles, ntiles, ntx, beta, F, odd, lbgk, status, st);               \
+  }                                                                                                              \
+  cudaError_t sc_nodes_##NAME(const PatchDev& p, const void* fin, void* fout, const uint32_t* nodes, int64_t n,  \
+                              double beta, const Force& F, int lbgk, int* status, cudaStream_t st) {             \
+    return sc_nodes_typed<S, R>(p, fin, fout, nodes, n, beta, F, lbgk, status, st);                              \
   }
 
 }  // namespace lbmk

@@ -302,6 +302,13 @@ class Grid:
         a = (ctypes.c_double * 3)(*[float(v) for v in accel0])
         _check(lib().lbm_force(self.handle, a, None), self.handle)
 
+    def drag(self):
+        """FP64 momentum-exchange force on the solid nodes of the current state
+        (coarse units, summed over levels); synchronises the stream."""
+        out = (ctypes.c_double * 3)()
+        _check(lib().lbm_force(self.handle, None, out), self.handle)
+        return [out[0], out[1], out[2]]
+
     def graphs(self, enable: bool):
         _check(lib().lbm_graphs(self.handle, 1 if enable else 0), self.handle)
 

@@ -129,13 +129,44 @@ def test_channel_small_fp32():
 
 
 def test_sphere_small_fp64():
-    """Four levels, equilibrium inlet, zero-gradient outlet, bounce-back sphere."""
+    """Four levels, equilibrium inlet, zero-gradient outlet, bounce-back sphere;
+    the momentum-exchange drag against the oracle's after every step."""
     case = I.sphere_case(scale=8)
     g, o = twin(case, "fp64", lambda x, y, z, p, info: I.uniform_fields(x, (0.05, 0.0, 0.0)))
     for _ in range(3):
         g.step(1)
         o.step(1)
         assert pop_diff(g, o) < 1e-12
+        Fg, Fo = np.array(g.drag()), o.drag()
+        assert np.max(np.abs(Fg - Fo)) < 1e-12 * np.linalg.norm(Fo), (Fg, Fo)
+
+
+def test_sphere_small_fp32_drag():
+    case = I.sphere_case(scale=8)
+    g, o = twin(case, "fp32", lambda x, y, z, p, info: I.uniform_fields(x, (0.05, 0.0, 0.0)))
+    g.step(10)
+    o.step(10)
+    Fg, Fo = np.array(g.drag()), o.drag()
+    rel = np.max(np.abs(Fg - Fo)) / np.linalg.norm(Fo)
+    print("sphere fp32 drag after 10 steps:", Fg, Fo, "rel %.2e" % rel)
+    assert rel < 1e-4
+
+
+def test_drag_is_the_momentum_the_fluid_loses_on_gpu():
+    """Periodic box with a solid ball, one level, FP64: the drag of the state a
+    step starts from is the fluid momentum that step loses (diagnostics)."""
+    case = dict(name="ball", n=(16, 16, 16), periodic=(1, 1, 1), walls=(0,) * 6, inflow_axis=-1, u_in=(0, 0, 0),
+                boxes=[], solid=I.sphere_mask(0, (8, 8, 8), 6.0), nu0=0.02, accel0=(0, 0, 0), mirror_lbgk=False,
+                thermal=None)
+    g, o = twin(case, "fp64", lambda x, y, z, p, info: I.uniform_fields(x, (0.05, 0.02, -0.01)))
+    for _ in range(3):
+        F = np.array(g.drag())
+        assert np.max(np.abs(F - o.drag())) < 1e-12 * np.linalg.norm(F)
+        J0 = np.array(g.diagnostics()["momentum"])
+        g.step(1)
+        o.step(1)
+        J1 = np.array(g.diagnostics()["momentum"])
+        assert np.max(np.abs((J1 - J0) + F)) < 1e-12 * np.linalg.norm(F), (J1 - J0, F)
 
 
 @pytest.mark.parametrize("storage,bound", [("fp16s", 3e-3), ("bf16s", 3e-2)])

@@ -444,3 +444,65 @@ def test_thermal_heat_flux_combination_relaxes_with_beta1():
         x0, x1 = X(f, g), X(fo, go)
         # tolerance: the closed-form P^eq differs from sum cc f^eq at O(u^4)
         assert np.max(np.abs(x1 - (1 - 2 * beta1) * x0)) < 1e-2 * np.max(np.abs(x0)), (x0, x1)
+
+
+def _ball_case(n=16, boxes=(), level=0, d=6.0, nu0=0.02):
+    return dict(name="ball", n=(n, n, n), periodic=(1, 1, 1), walls=(0,) * 6, inflow_axis=-1, u_in=(0, 0, 0),
+                boxes=list(boxes), solid=I.sphere_mask(level, (n / 2, n / 2, n / 2), d), nu0=nu0,
+                accel0=(0, 0, 0), mirror_lbgk=False, thermal=None)
+
+
+def _fluid_momentum(o):
+    J = np.zeros(3)
+    for p, info in enumerate(o.patches):
+        rho, u, _, _ = o.moments(p)
+        m = o.mask(p) == 1
+        J += np.array([np.sum(rho[m] * u[a][m]) for a in range(3)]) / 8.0 ** info["level"]
+    return J
+
+
+def test_drag_is_the_momentum_the_fluid_loses():
+    """Sec. IV A 2 drag, read as the momentum exchange of half-way bounce-back:
+    in a periodic box without force, collision conserves momentum and streaming
+    hands the solid exactly the exchanged momentum, so over one step the fluid
+    momentum drops by the drag of the state the step starts from."""
+    case = _ball_case()
+    o = O.Oracle(case)
+    rng = np.random.default_rng(3)
+    for p, info in enumerate(o.patches):
+        shp = tuple(info["dim"][::-1])
+        rho = 1.0 + 0.01 * rng.standard_normal(shp)
+        u = np.stack([0.05 + 0.01 * rng.standard_normal(shp), 0.02 + 0.01 * rng.standard_normal(shp),
+                      -0.01 + 0.01 * rng.standard_normal(shp)])
+        o.init_equilibrium(p, rho, u)
+    for _ in range(3):
+        F = o.drag()
+        J0 = _fluid_momentum(o)
+        o.step(1)
+        J1 = _fluid_momentum(o)
+        assert np.linalg.norm(F) > 1e-3
+        assert np.max(np.abs((J1 - J0) + F)) < 1e-12 * np.linalg.norm(F), (J1 - J0, F)
+
+
+def test_drag_units_on_a_refined_level():
+    """Solid on level 1 (each node 1/8 of a coarse volume, each substep half a
+    coarse step): over coarse steps the volume-weighted fluid momentum drops by
+    the drag per coarse step, up to the small non-conservation of the coupling
+    and the change of the drag between substeps."""
+    case = _ball_case(n=16, boxes=[(1, (3, 3, 3), (13, 13, 13))], level=1, d=8.0)
+    o = O.Oracle(case)
+    for p, info in enumerate(o.patches):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        o.init_equilibrium(p, np.ones_like(x), np.stack([0.04 + 0 * x, 0 * x, 0 * x]))
+    o.step(20)
+    J0, Fsum, F = _fluid_momentum(o), np.zeros(3), o.drag()
+    for _ in range(10):
+        o.step(1)
+        F1 = o.drag()
+        Fsum += 0.5 * (F + F1)  # trapezoid over the coarse step
+        F = F1
+    dJ = _fluid_momentum(o) - J0
+    print("momentum change", dJ, "drag sum", Fsum)
+    assert Fsum[0] > 0
+    # a wrong level scaling (2^-l or 8^-l instead of 4^-l) is off by a factor 2
+    assert abs(dJ[0] + Fsum[0]) < 0.1 * Fsum[0]
