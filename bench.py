@@ -339,7 +339,9 @@ def cuda_arm(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # warm-up
+    # setup: the autotuner times each TMA kernel variant over 2 coarse steps
+    # (advancing the state) and keeps the fastest; then the warm-up
+    tune = g.autotune(trials=2)
     g.step(args.warmup)
     barrier()
     # timed region: K coarse steps replayed as CUDA graphs, events on the grid's stream
@@ -383,8 +385,8 @@ def cuda_arm(args):
         "channel") else None
     roofline = dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=traffic,
                     peak_source="measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
-                    kernel="k_stream_collide level %d" % top["level"] if top["kind"] == "stream_collide"
-                    else "%s level %d" % (top["kind"], top["level"]),
+                    kernel=("k_sc_tma, TMA tile pass batched over the patches of each instant"
+                            if top["kind"] == "stream_collide_tma" else "%s level %d" % (top["kind"], top["level"])),
                     avg_launch_ms=avg_ms, alg_bytes_per_launch=alg_bytes, bytes_per_node_update=bpu)
     kernels = [dict(r, avg_us=1e3 * r["ms"] / r["launches"]) for r in report]
     launches = sum(r["launches"] for r in report)
@@ -410,6 +412,7 @@ def cuda_arm(args):
                     config=dict(workload=desc, storage=args.storage, node_updates_per_coarse_step=nup,
                                 parallelism="replicas" if world > 1 else "single GPU",
                                 launch="one CUDA graph per coarse step",
+                                autotune=tune,
                                 direct_launch_ms_per_step=1e3 * t_instr / args.steps,
                                 l2="no flush: working set %.2f GB > %.0f MB L2" % (ws / 1e9, L2_BYTES / 1e6)),
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clk,

@@ -26,6 +26,7 @@ using lbm::HostPatch;
 
 namespace {
 constexpr int kDiagBlocks = 296;  // 2 per SM on 148+ SM parts; fixed for determinism
+constexpr size_t kTmaBatchMax = 8;  // patches per TMA launch
 std::string g_create_error;
 }  // namespace
 
@@ -45,6 +46,7 @@ struct lbm_grid {
     cudaEvent_t e0, e1;
   };
   bool timing = false;
+  int variant = 0;  // TMA kernel variant (lbm_autotune)
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
@@ -181,6 +183,36 @@ lbm_status run_instant(lbm_grid* g, int k) {
   const int storage = hg.desc.storage;
   const int lbgk = hg.desc.mirror_lbgk;
   std::vector<int> active;
+  if (!hg.thermal) {
+    // TMA tile pass of every patch stepped at this instant: one persistent
+    // launch per 8 patches, whatever their levels and sizes
+    std::vector<lbmk::TmaLaunchPatch> batch;
+    double nodes = 0;
+    for (int lev = 0; lev < L; ++lev) {
+      const int stride = 1 << (L - 1 - lev);
+      if (k % stride) continue;
+      const int odd = (lev > 0 && (k / stride) % 2) ? 1 : 0;
+      for (auto& p : hg.P) {
+        if (p.level != lev || p.tiles_pure[odd].empty()) continue;
+        batch.push_back({p.tmap[p.cur], p.tmapo[1 - p.cur], p.tmapw[p.cur], view(g, p), g->base + p.off_f[p.cur],
+                         at<unsigned long long>(g, p.off_tiles_pure[odd]), (int64_t)p.tiles_pure[odd].size(),
+                         p.beta, level_force(g, lev)});
+        nodes += p.n_tma[odd];
+      }
+    }
+    for (size_t b0 = 0; b0 < batch.size(); b0 += kTmaBatchMax) {
+      const int nb = (int)std::min(batch.size() - b0, kTmaBatchMax);
+      if (lbm_status st = cuda_check(g,
+                                     timed(g, 4, -1, b0 == 0 ? nodes : 0.0,
+                                           [&] {
+                                             return lbmk::launch_sc_tma(storage, batch.data() + b0, nb,
+                                                                        g->variant, lbgk, status_ptr(g),
+                                                                        g->stream);
+                                           }),
+                                     "stream_collide (TMA)"))
+        return st;
+    }
+  }
   for (int lev = 0; lev < L; ++lev) {
     const int stride = 1 << (L - 1 - lev);
     if (k % stride) continue;
@@ -208,16 +240,12 @@ lbm_status run_instant(lbm_grid* g, int k) {
                               }),
                         "thermal stream_collide");
       } else {
+        // the nodes the TMA pass does not give: fix-up list, then mixed tiles
         st = cuda_check(
             g,
-            timed(g, 0, lev, g->timing ? count_types(p, odd) : 0.0,
+            timed(g, 0, lev, g->timing ? count_types(p, odd) - p.n_tma[odd] : 0.0,
                   [&] {
-                    cudaError_t e = lbmk::launch_sc_tma(storage, p.tmap[p.cur], p.tmapo[1 - p.cur], p.tmapw[p.cur],
-                                                        pv, fin, at<unsigned long long>(g, p.off_tiles_pure[odd]),
-                                                        (int64_t)p.tiles_pure[odd].size(), p.beta, F, lbgk,
-                                                        status_ptr(g), g->stream);
-                    if (e) return e;
-                    e = lbmk::launch_sc_nodes(storage, pv, fin, fout, at<uint32_t>(g, p.off_fix_nodes[odd]),
+                    cudaError_t e = lbmk::launch_sc_nodes(storage, pv, fin, fout, at<uint32_t>(g, p.off_fix_nodes[odd]),
                                               (int64_t)p.fix_nodes[odd].size(), p.beta, F, lbgk, status_ptr(g),
                                               g->stream);
                     if (e) return e;
@@ -572,6 +600,51 @@ lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps) {
     for (auto& p : g->hg.P)
       if ((K >> (L - 1 - p.level)) & 1) p.cur ^= 1;
   }
+  return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms_per_step, int32_t max_variants,
+                        int32_t* n_variants) {
+  if (lbm_status s = check_bound(g)) return s;
+  if (trials < 1) return fail(g, LBM_ERR_ARG, "autotune needs at least one trial step");
+  const int nv = g->hg.thermal ? 1 : lbmk::sc_tma_variants(g->hg.desc.storage);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (!e) e = cudaEventCreate(&e1);
+  std::vector<float> ms(nv, 0.0f);
+  lbm_status st = LBM_OK;
+  for (int v = 0; v < nv && !e && !st; ++v) {
+    g->variant = v;
+    e = cudaEventRecord(e0, g->stream);
+    for (int t = 0; t < trials && !e && !st; ++t) st = coarse_step_eager(g);
+    if (!e && !st) e = cudaEventRecord(e1, g->stream);
+    if (!e && !st) e = cudaEventSynchronize(e1);
+    if (!e && !st) e = cudaEventElapsedTime(&ms[v], e0, e1);
+    ms[v] /= (float)trials;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) return st;
+  if (e) return cuda_check(g, e, "lbm_autotune");
+  int best = 0;
+  for (int v = 1; v < nv; ++v)
+    if (ms[v] < ms[best]) best = v;
+  g->variant = best;
+  g->stepped = true;
+  g->drop_graphs();
+  if (chosen) *chosen = best;
+  if (n_variants) *n_variants = nv;
+  if (ms_per_step)
+    for (int v = 0; v < nv && v < max_variants; ++v) ms_per_step[v] = ms[v];
+  return LBM_OK;
+}
+
+lbm_status lbm_set_variant(lbm_grid_t g, int32_t variant) {
+  if (!g) return LBM_ERR_ARG;
+  const int nv = g->hg.thermal ? 1 : lbmk::sc_tma_variants(g->hg.desc.storage);
+  if (variant < 0 || variant >= nv) return fail(g, LBM_ERR_ARG, "variant out of range");
+  g->variant = variant;
+  g->drop_graphs();
   return LBM_OK;
 }
 

@@ -52,6 +52,7 @@ struct HostPatch {
   std::vector<uint32_t> tiles_mixed[2];  // other tiles with nodes to update: [0] even, [1] odd steps
   std::vector<uint32_t> tiles_all[2];    // every tile with nodes to update (thermal model, node by node)
   std::vector<uint32_t> fix_nodes[2];    // nodes of TMA tiles recomputed node by node after the tile pass
+  double n_tma[2] = {0, 0};              // updated nodes the TMA pass gives (per parity)
   alignas(64) unsigned char tmap[2][128];   // TMA load descriptors of the two population buffers
   alignas(64) unsigned char tmapo[2][128];  // TMA store descriptors
   alignas(64) unsigned char tmapw[2][128];  // TMA 16-byte wrap descriptors

@@ -77,10 +77,23 @@ cudaError_t launch_adj_grad_u0(int storage, const PatchDev& p, const void* fin, 
 // the store box, and of the source buffer with the wrap box; tiles:
 // x-tile | y << 16 | z << 32) and mixed tiles node by node (tile id
 // = (z * ny + y) * ntx + tx); a tile is 128 nodes along x.
-// fin: the current population buffer (the fixed inlet nodes are copied from it).
-cudaError_t launch_sc_tma(int storage, const void* tmap_in, const void* tmap_out, const void* tmap_wrap,
-                          const PatchDev& p, const void* fin, const unsigned long long* tiles, int64_t ntiles,
-                          double beta, const Force& F, int lbgk, int* status, cudaStream_t st);
+// One patch of a batched TMA tile pass.
+struct TmaLaunchPatch {
+  const void* tmap_in;    // load descriptor of the current buffer
+  const void* tmap_out;   // store descriptor of the next buffer
+  const void* tmap_wrap;  // 16-byte wrap descriptor of the current buffer
+  PatchDev p;
+  const void* fin;        // current buffer (the fixed inlet nodes are copied from it)
+  const unsigned long long* tiles;
+  int64_t ntiles;
+  double beta;
+  Force F;
+};
+// TMA tile pass over up to 8 patches in one persistent launch; variant picks
+// the load-stage / occupancy configuration (0 .. sc_tma_variants() - 1).
+cudaError_t launch_sc_tma(int storage, const TmaLaunchPatch* ps, int n, int variant, int lbgk, int* status,
+                          cudaStream_t st);
+int sc_tma_variants(int storage);
 // node-by-node recomputation of listed nodes (after the TMA tile pass)
 cudaError_t launch_sc_nodes(int storage, const PatchDev& p, const void* fin, void* fout, const uint32_t* nodes,
                             int64_t n, double beta, const Force& F, int lbgk, int* status, cudaStream_t st);

@@ -438,6 +438,7 @@ std::string build_layout(HostGrid& g) {
     struct Rows {
       std::vector<uint64_t> pure[2];
       std::vector<uint32_t> mixed[2], all[2], fix[2];
+      double ntma[2] = {0, 0};
     };
     std::vector<Rows> rows(p.dim[2]);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -493,6 +494,7 @@ std::string build_layout(HostGrid& g) {
               R.pure[k].push_back((uint64_t)tx | ((uint64_t)y << 16) | ((uint64_t)z << 32) | ((uint64_t)bm << 48) |
                                   (fl << 57));
               R.fix[k].insert(R.fix[k].end(), odd_nodes[k].begin(), odd_nodes[k].end());
+              R.ntma[k] += active[k] - nodd;
             } else {
               R.mixed[k].push_back(id);
             }
@@ -500,8 +502,10 @@ std::string build_layout(HostGrid& g) {
         }
       }
     }
+    p.n_tma[0] = p.n_tma[1] = 0;
     for (auto& R : rows)
       for (int k = 0; k < 2; ++k) {
+        p.n_tma[k] += R.ntma[k];
         p.tiles_pure[k].insert(p.tiles_pure[k].end(), R.pure[k].begin(), R.pure[k].end());
         p.tiles_mixed[k].insert(p.tiles_mixed[k].end(), R.mixed[k].begin(), R.mixed[k].end());
         p.tiles_all[k].insert(p.tiles_all[k].end(), R.all[k].begin(), R.all[k].end());

@@ -3,22 +3,23 @@
 
 namespace lbmk {
 
-cudaError_t launch_sc_tma(int storage, const void* tmap_in, const void* tmap_out, const void* tmap_wrap,
-                          const PatchDev& p, const void* fin, const unsigned long long* tiles, int64_t ntiles,
-                          double beta, const Force& F, int lbgk, int* status, cudaStream_t st) {
+cudaError_t launch_sc_tma(int storage, const TmaLaunchPatch* ps, int n, int variant, int lbgk, int* status,
+                          cudaStream_t st) {
   switch (storage) {
     case LBM_FP64:
-      return sc_tma_fp64(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, ntiles, beta, F, lbgk, status, st);
+      return sc_tma_fp64(ps, n, variant, lbgk, status, st);
     case LBM_FP32:
-      return sc_tma_fp32(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, ntiles, beta, F, lbgk, status, st);
+      return sc_tma_fp32(ps, n, variant, lbgk, status, st);
     case LBM_FP16_SHIFT:
-      return sc_tma_fp16(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, ntiles, beta, F, lbgk, status, st);
+      return sc_tma_fp16(ps, n, variant, lbgk, status, st);
     case LBM_BF16_SHIFT:
-      return sc_tma_bf16(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, ntiles, beta, F, lbgk, status, st);
+      return sc_tma_bf16(ps, n, variant, lbgk, status, st);
     default:
       return cudaErrorInvalidValue;
   }
 }
+
+int sc_tma_variants(int) { return 2; }
 
 cudaError_t launch_sc_tiles(int storage, const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,
                             int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk, int* status,

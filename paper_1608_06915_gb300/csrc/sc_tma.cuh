@@ -41,7 +41,16 @@
 
 namespace lbmk {
 
+// Kernel variants the autotuner picks from: load stages DI and the CTAs per SM
+// the register allocation aims for (MINB).  Results do not depend on the variant.
 template <typename S>
+struct TmaVariants {
+  static constexpr int N = 2;
+  static constexpr int DI[N] = {sizeof(S) == 8 ? 2 : 3, sizeof(S) == 8 ? 1 : 2};
+  static constexpr int MINB[N] = {1, sizeof(S) == 8 ? 3 : 4};
+};
+
+template <typename S, int DI_ = TmaVariants<S>::DI[0]>
 struct TmaCfg {
   static constexpr int BX = 128;                                        // nodes per tile
   static constexpr int H = 16 / (int)sizeof(S);                         // halo, elements
@@ -54,21 +63,8 @@ struct TmaCfg {
   static constexpr int OSTAGE = 4 * OSEGB;                              // [warp][population][32 nodes]
   static constexpr uint32_t TX = 27u * W * (uint32_t)sizeof(S);        // bytes of the 27 row loads
   static constexpr uint32_t TXW = 9u * 16u;                             // bytes of 9 wrap boxes
-#ifndef LBM_TMA_DI
-  static constexpr int DI = sizeof(S) == 8 ? 2 : 3;                     // load stages
-#else
-  static constexpr int DI = LBM_TMA_DI;
-#endif
-#ifndef LBM_TMA_DO
+  static constexpr int DI = DI_;                                        // load stages
   static constexpr int DO = 1;                                          // store stages
-#else
-  static constexpr int DO = LBM_TMA_DO;
-#endif
-#ifndef LBM_TMA_PF
-  static constexpr int PF = 0;                                          // L2 prefetch distance beyond the ring (tiles)
-#else
-  static constexpr int PF = LBM_TMA_PF;
-#endif
   static constexpr int SMEM = DI * STAGE + DO * OSTAGE + 128;           // + slack for 128-byte alignment
   static constexpr int THREADS = 160;                                   // 4 consumer warps + 1 producer
 };
@@ -209,14 +205,45 @@ __device__ __forceinline__ constexpr int row_base(int i) {
 // (map_wrap) into side slots after the 27 rows of the stage: slot j holds
 // [dim - H, dim) of population 3j + 2, slot 9 + j holds [0, H) of population 3j.
 // Every TMA destination in shared memory starts on a 128-byte boundary.
-template <typename S, typename R, int FM>
-__global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensorMap map_in,
-                                                const __grid_constant__ CUtensorMap map_out,
-                                                const __grid_constant__ CUtensorMap map_wrap, PatchDev p,
-                                                const S* __restrict__ fin,
-                                                const unsigned long long* __restrict__ tiles, int ntiles, R beta,
-                                                R dux, R duy, R duz, int lbgk, int* status) {
-  using C = TmaCfg<S>;
+//
+// Batching: one launch sweeps the TMA tiles of every patch stepped at an
+// instant (patches of uneven sizes on several levels), as the concatenation of
+// their tile lists; each tile carries its patch's tensor maps, geometry,
+// relaxation and force.
+constexpr int kTmaBatch = 8;  // patches per launch
+
+template <typename S, typename R>
+struct TmaPatch {
+  CUtensorMap map_in, map_out, map_wrap;
+  PatchDev p;
+  const S* fin;                          // current populations (fixed inlet nodes are copied from it)
+  const unsigned long long* tiles;       // this patch's tile list
+  int tile0, ntiles;                     // its range in the concatenated tile index
+  R beta, du[3];
+};
+
+template <typename S, typename R>
+struct TmaBatch {
+  TmaPatch<S, R> e[kTmaBatch];
+  int n, ntiles, lbgk;
+  int* status;
+};
+
+template <typename S, typename R>
+__device__ __forceinline__ int batch_entry(const TmaBatch<S, R>& b, int t) {
+  int e = 0;
+#pragma unroll
+  for (int q = 1; q < kTmaBatch; ++q)
+    if (q < b.n && t >= b.e[q].tile0) e = q;
+  return e;
+}
+
+// MINB: CTAs per SM the register allocation aims for (launch bounds).
+template <typename S, typename R, int FM, int DI, int MINB>
+__global__ void __launch_bounds__(160, MINB) k_sc_tma(const __grid_constant__ TmaBatch<S, R> b) {
+  using C = TmaCfg<S, DI>;
+  const int ntiles = b.ntiles;
+  int* status = b.status;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   unsigned char* ostage = smem + C::DI * C::STAGE;
@@ -236,34 +263,28 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
   if (warp == 4) {
     // ---------------- producer (one thread: TMA operands stay warp-uniform) ----------------
     if (lane != 0) return;
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_in)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_out)) : "memory");
+    for (int q = 0; q < b.n; ++q) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&b.e[q].map_in)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&b.e[q].map_out)) : "memory");
+    }
     for (int k = 0; k < nmine; ++k) {
       const int s = k % C::DI;
       if (k >= C::DI && !mbar_wait_bounded(&empty[s], (uint32_t)((k / C::DI) - 1) & 1u)) {
         atomicOr(status, 2);
         return;  // consumers time out on the stages never filled
       }
-      if (C::PF > 0 && k + C::DI + C::PF - 1 < nmine) {
-        // warm L2 with the rows of a tile beyond the ring
-        int px, py, pz;
-        tile_xyz(tiles[blockIdx.x + (size_t)(k + C::DI + C::PF - 1) * gridDim.x], px, py, pz);
-#pragma unroll 1
-        for (int j = 0; j < 9; ++j) {
-          const int sy = wrap_axis(py - (j % 3 - 1), p.dim[1]);
-          const int sz = wrap_axis(pz - (j / 3 - 1), p.dim[2]);
-#pragma unroll
-          for (int cx = 0; cx < 3; ++cx) tma_prefetch_row(&map_in, px * C::BX - C::H, sy, sz, 3 * j + cx);
-        }
-      }
+      const int t = (int)blockIdx.x + k * (int)gridDim.x;
+      const int ei = batch_entry(b, t);
+      const TmaPatch<S, R>& E = b.e[ei];
+      const PatchDev& p = E.p;
       int tx, ty, tz;
-      const unsigned long long te = tiles[blockIdx.x + (size_t)k * gridDim.x];
+      const unsigned long long te = E.tiles[t - E.tile0];
       tile_xyz(te, tx, ty, tz);
       const int bm = tile_bounce(te);
       const int fl = tile_flags(te);
       const bool first = p.span[0] && tx == 0;
       const bool last = p.span[0] && (tx + 1) * C::BX >= p.dim[0];
-      tile_at[s] = make_int4(tx, ty, tz, bm | (fl << 9));
+      tile_at[s] = make_int4(tx, ty, tz, bm | (fl << 9) | (ei << 11));
       const uint32_t txw = 16u * (uint32_t)(9 - __popc(bm));  // wrap boxes of the rows not bounced
       mbar_expect_tx(&full[s], C::TX + (first ? txw : 0u) + (last ? txw : 0u));
       unsigned char* stage = smem + s * C::STAGE;
@@ -277,12 +298,12 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
           const int sy = wrap_axis(ty - (cy - 1), p.dim[1]);
           const int j = 3 * cz + cy;  // populations 3j, 3j + 1, 3j + 2 share this source row
           if ((bm >> j) & 1) {
-            tma_load_row(stage + j * C::GROUP, &map_in, &full[s], x0, ty, tz, 3 * (8 - j));
+            tma_load_row(stage + j * C::GROUP, &E.map_in, &full[s], x0, ty, tz, 3 * (8 - j));
             continue;
           }
-          tma_load_row(stage + j * C::GROUP, &map_in, &full[s], x0, sy, sz, 3 * j);
-          if (first) tma_load_row(side + j * C::SIDE, &map_wrap, &full[s], p.dim[0] - C::H, sy, sz, 3 * j + 2);
-          if (last) tma_load_row(side + (9 + j) * C::SIDE, &map_wrap, &full[s], 0, sy, sz, 3 * j);
+          tma_load_row(stage + j * C::GROUP, &E.map_in, &full[s], x0, sy, sz, 3 * j);
+          if (first) tma_load_row(side + j * C::SIDE, &E.map_wrap, &full[s], p.dim[0] - C::H, sy, sz, 3 * j + 2);
+          if (last) tma_load_row(side + (9 + j) * C::SIDE, &E.map_wrap, &full[s], 0, sy, sz, 3 * j);
         }
       }
     }
@@ -301,7 +322,9 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
       return;
     }
     const int4 tc = tile_at[s];
-    const int tx = tc.x, y = tc.y, z = tc.z, bm = tc.w & 0x1ff, fl = tc.w >> 9;
+    const int tx = tc.x, y = tc.y, z = tc.z, bm = tc.w & 0x1ff, fl = (tc.w >> 9) & 3;
+    const TmaPatch<S, R>& E = b.e[tc.w >> 11];
+    const PatchDev& p = E.p;
     const int x = tx * C::BX + tid;
     const S* st = reinterpret_cast<const S*>(smem + s * C::STAGE);
     R f[27];
@@ -343,13 +366,13 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
         const long long own = node_index(p, 0, y, z);
         unroll<27>([&](auto I) {
           constexpr int i = decltype(I)::value;
-          f[i] = Stor<S>::ld(fin + (long long)i * p.plane + own);
+          f[i] = Stor<S>::ld(E.fin + (long long)i * p.plane + own);
         });
       }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with stage s
-    if (x < p.dim[0] && !fixed) kbc_collide<R, FM>(f, beta, dux, duy, duz, lbgk != 0);
+    if (x < p.dim[0] && !fixed) kbc_collide<R, FM>(f, E.beta, E.du[0], E.du[1], E.du[2], b.lbgk != 0);
     // this warp's output segment in stage o: wait until the stores that last
     // used it have read it, fill it, store it
     const int o = k % C::DO;
@@ -363,7 +386,7 @@ __global__ void __launch_bounds__(160) k_sc_tma(const __grid_constant__ CUtensor
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
     if (lane == 0) {
-      tma_store_row(&map_out, seg, tx * C::BX + warp * C::OSEG, y, z, 0);
+      tma_store_row(&E.map_out, seg, tx * C::BX + warp * C::OSEG, y, z, 0);
       bulk_commit();
     }
   }
@@ -413,13 +436,12 @@ __global__ void __launch_bounds__(128) k_sc_nodes(PatchDev p, const S* __restric
   });
 }
 
-template <typename S, typename R, int FM>
-cudaError_t launch_tma_t(const void* tmap_in, const void* tmap_out, const void* tmap_wrap, const PatchDev& p,
-                         const void* fin, const unsigned long long* tiles, int ntiles, R beta, R dux, R duy, R duz,
-                         int lbgk, int* status, cudaStream_t st) {
-  using C = TmaCfg<S>;
+template <typename S, typename R, int FM, int V>
+cudaError_t launch_tma_v(const TmaBatch<S, R>& b, cudaStream_t st) {
+  constexpr int DI = TmaVariants<S>::DI[V], MINB = TmaVariants<S>::MINB[V];
+  using C = TmaCfg<S, DI>;
   static int blocks_per_sm = -1, sms = 0;
-  auto kern = k_sc_tma<S, R, FM>;
+  auto kern = k_sc_tma<S, R, FM, DI, MINB>;
   if (blocks_per_sm < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e) return e;
@@ -430,31 +452,52 @@ cudaError_t launch_tma_t(const void* tmap_in, const void* tmap_out, const void* 
     if (e) return e;
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
-  const int grid = std::min(ntiles, blocks_per_sm * sms);
-  CUtensorMap mi, mo, mw;
-  memcpy(&mi, tmap_in, sizeof mi);
-  memcpy(&mo, tmap_out, sizeof mo);
-  memcpy(&mw, tmap_wrap, sizeof mw);
-  kern<<<grid, C::THREADS, C::SMEM, st>>>(mi, mo, mw, p, (const S*)fin, tiles, ntiles, beta, dux, duy, duz, lbgk,
-                                          status);
+  const int grid = std::min(b.ntiles, blocks_per_sm * sms);
+  kern<<<grid, C::THREADS, C::SMEM, st>>>(b);
   return cudaGetLastError();
 }
 
+template <typename S, typename R, int FM>
+cudaError_t launch_tma_fm(const TmaBatch<S, R>& b, int variant, cudaStream_t st) {
+  static_assert(TmaVariants<S>::N == 2, "variant dispatch");
+  return variant == 1 ? launch_tma_v<S, R, FM, 1>(b, st) : launch_tma_v<S, R, FM, 0>(b, st);
+}
+
+// One launch over up to kTmaBatch patches (their force masks must agree).
 template <typename S, typename R>
-cudaError_t sc_tma_typed(const void* tmap_in, const void* tmap_out, const void* tmap_wrap, const PatchDev& p,
-                         const void* fin, const unsigned long long* tiles, int64_t ntiles, double beta, const Force& F,
-                         int lbgk, int* status, cudaStream_t st) {
-  if (ntiles == 0) return cudaSuccess;
-  const R b = (R)beta, dx = (R)F.du[0], dy = (R)F.du[1], dz = (R)F.du[2];
-  switch (F.mask()) {
+cudaError_t sc_tma_typed(const TmaLaunchPatch* ps, int n, int variant, int lbgk, int* status, cudaStream_t st) {
+  TmaBatch<S, R> b;
+  memset(&b, 0, sizeof b);
+  b.lbgk = lbgk;
+  b.status = status;
+  int fm = 0;
+  for (int q = 0; q < n; ++q) {
+    if (ps[q].ntiles <= 0) continue;
+    if (b.n == kTmaBatch) return cudaErrorInvalidValue;
+    TmaPatch<S, R>& E = b.e[b.n++];
+    memcpy(&E.map_in, ps[q].tmap_in, sizeof(CUtensorMap));
+    memcpy(&E.map_out, ps[q].tmap_out, sizeof(CUtensorMap));
+    memcpy(&E.map_wrap, ps[q].tmap_wrap, sizeof(CUtensorMap));
+    E.p = ps[q].p;
+    E.fin = (const S*)ps[q].fin;
+    E.tiles = ps[q].tiles;
+    E.tile0 = b.ntiles;
+    E.ntiles = (int)ps[q].ntiles;
+    E.beta = (R)ps[q].beta;
+    for (int a = 0; a < 3; ++a) E.du[a] = (R)ps[q].F.du[a];
+    b.ntiles += E.ntiles;
+    fm |= ps[q].F.mask();
+  }
+  if (b.ntiles == 0) return cudaSuccess;
+  switch (fm) {
     case 0:
-      return launch_tma_t<S, R, 0>(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
+      return launch_tma_fm<S, R, 0>(b, variant, st);
     case 1:
-      return launch_tma_t<S, R, 1>(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
+      return launch_tma_fm<S, R, 1>(b, variant, st);
     case 4:
-      return launch_tma_t<S, R, 4>(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
+      return launch_tma_fm<S, R, 4>(b, variant, st);
     default:
-      return launch_tma_t<S, R, 7>(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, (int)ntiles, b, dx, dy, dz, lbgk, status, st);
+      return launch_tma_fm<S, R, 7>(b, variant, st);
   }
 }
 
@@ -508,9 +551,8 @@ cudaError_t sc_tiles_typed(const PatchDev& p, const void* fin, void* fout, const
 
 // per-storage entry points, one translation unit each
 #define LBM_SC_DECL(NAME)                                                                                        \
-  cudaError_t sc_tma_##NAME(const void* tmap_in, const void* tmap_out, const void* tmap_wrap, const PatchDev& p, \
-                            const void* fin, const unsigned long long* tiles, int64_t ntiles, double beta,       \
-                            const Force& F, int lbgk, int* status, cudaStream_t st);                             \
+  cudaError_t sc_tma_##NAME(const TmaLaunchPatch* ps, int n, int variant, int lbgk, int* status,                \
+                            cudaStream_t st);                                                                    \
   cudaError_t sc_tiles_##NAME(const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,             \
                               int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk,           \
                               int* status, cudaStream_t st);                                                     \
@@ -522,10 +564,9 @@ LBM_SC_DECL(fp16)
 LBM_SC_DECL(bf16)
 
 #define LBM_SC_DEFINE(NAME, S, R)                                                                                \
-  cudaError_t sc_tma_##NAME(const void* tmap_in, const void* tmap_out, const void* tmap_wrap, const PatchDev& p, \
-                            const void* fin, const unsigned long long* tiles, int64_t ntiles, double beta,       \
-                            const Force& F, int lbgk, int* status, cudaStream_t st) {                            \
-    return sc_tma_typed<S, R>(tmap_in, tmap_out, tmap_wrap, p, fin, tiles, ntiles, beta, F, lbgk, status, st);   \
+  cudaError_t sc_tma_##NAME(const TmaLaunchPatch* ps, int n, int variant, int lbgk, int* status,                \
+                            cudaStream_t st) {                                                                   \
+    return sc_tma_typed<S, R>(ps, n, variant, lbgk, status, st);                                                 \
   }                                                                                                              \
   cudaError_t sc_tiles_##NAME(const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,             \
                               int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk,           \

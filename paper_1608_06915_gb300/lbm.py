@@ -91,6 +91,9 @@ def lib():
             "lbm_collide_nodes": [vp, vp, vp, i64, ctypes.c_double, dp, i32, i32, vp],
             "lbm_timing": [vp, i32],
             "lbm_graphs": [vp, i32],
+            "lbm_autotune": [vp, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float), i32,
+                             ctypes.POINTER(ctypes.c_int32)],
+            "lbm_set_variant": [vp, i32],
             "lbm_adjoint_workspace_bytes": [vp, i32, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
             "lbm_adjoint_seed": [vp, vp, vp, dp],
             "lbm_adjoint_step": [vp, vp, i32, vp, vp, ctypes.c_size_t],
@@ -309,6 +312,18 @@ class Grid:
         _check(lib().lbm_force(self.handle, None, out), self.handle)
         return [out[0], out[1], out[2]]
 
+    def autotune(self, trials: int = 2):
+        """Times each TMA kernel variant over `trials` coarse steps (the state
+        advances) and keeps the fastest: dict(chosen, ms_per_step)."""
+        chosen, n = ctypes.c_int32(), ctypes.c_int32()
+        ms = (ctypes.c_float * 16)()
+        _check(lib().lbm_autotune(self.handle, int(trials), ctypes.byref(chosen), ms, 16, ctypes.byref(n)),
+               self.handle)
+        return dict(chosen=chosen.value, ms_per_step=[ms[i] for i in range(n.value)])
+
+    def set_variant(self, v: int):
+        _check(lib().lbm_set_variant(self.handle, int(v)), self.handle)
+
     def graphs(self, enable: bool):
         _check(lib().lbm_graphs(self.handle, 1 if enable else 0), self.handle)
 
@@ -322,7 +337,7 @@ class Grid:
         kind, lev = (ctypes.c_int32 * m)(), (ctypes.c_int32 * m)()
         cnt, ms, nodes = (ctypes.c_int64 * m)(), (ctypes.c_double * m)(), (ctypes.c_double * m)()
         _check(lib().lbm_timing_report(self.handle, m, ctypes.byref(n), kind, lev, cnt, ms, nodes), self.handle)
-        names = {0: "stream_collide", 1: "coalesce", 2: "samples", 3: "explode"}
+        names = {0: "stream_collide", 1: "coalesce", 2: "samples", 3: "explode", 4: "stream_collide_tma"}
         return [dict(kind=names[kind[k]], level=lev[k], launches=cnt[k], ms=ms[k], nodes=nodes[k])
                 for k in range(min(n.value, m))]
 

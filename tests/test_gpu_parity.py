@@ -335,3 +335,37 @@ def test_graph_replay_matches_direct_launches(storage):
     torch.cuda.synchronize()
     for p in range(len(ga.patches)):
         assert torch.equal(ga.get_populations(p), gb.get_populations(p)), p
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp64", "fp16s"])
+def test_tma_variants_give_identical_results(storage):
+    """The autotuner's kernel variants differ in staging and occupancy only:
+    same bits after several coarse steps on a three-level channel with walls
+    and force, and on the four-level sphere."""
+    import torch
+    for case, fields in [
+        (dict(I.channel_small_case(), accel0=(1e-5, 0, 0)),
+         lambda c: (lambda x, y, z, p, info: I.channel_fields(c, info["level"], info["org"], info["dim"]))),
+        (I.sphere_case(scale=8), lambda c: (lambda x, y, z, p, info: I.uniform_fields(x, (0.05, 0.0, 0.0)))),
+    ]:
+        ga, _ = twin(case, storage, fields(case), oracle=False)
+        gb, _ = twin(case, storage, fields(case), oracle=False)
+        ga.set_variant(0)
+        gb.set_variant(1)
+        ga.step(5)
+        gb.step(5)
+        torch.cuda.synchronize()
+        for p in range(len(ga.patches)):
+            assert torch.equal(ga.get_populations(p), gb.get_populations(p)), (case["name"], p)
+
+
+def test_autotune_reports_and_keeps_the_state_consistent():
+    """autotune advances the state by variants x trials steps, exactly as steps would."""
+    import torch
+    case = dict(I.channel_small_case(), accel0=(1e-5, 0, 0))
+    fields = lambda x, y, z, p, info: I.channel_fields(case, info["level"], info["org"], info["dim"])
+    ga, o = twin(case, "fp64", fields)
+    r = ga.autotune(trials=1)
+    assert r["chosen"] in range(len(r["ms_per_step"])) and all(t > 0 for t in r["ms_per_step"])
+    o.step(len(r["ms_per_step"]))
+    assert pop_diff(ga, o) < 1e-12
