@@ -130,18 +130,19 @@ __device__ void kbc_vjp(const R (&f)[27], R (&lam)[27], R beta, bool lbgk) {
   const R nxx = pxx - tr3, nyy = pyy - tr3, nzz = pzz - tr3;
   R gamma = R(2), sh = 0, hh = 0;
   bool use_gamma = false;
+  const R ib = rcp_fast(beta);
   if (!lbgk) {
     unroll<27>([&](auto I) {
       constexpr int i = decltype(I)::value;
+      const R w = rcp_fast(q.fefull[i]);  // entropic weight 1 / f^eq_i
       const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
       const R dh = df[i] - ds;
-      const R w = R(1) / q.fefull[i];
       sh += ds * dh * w;
       hh += dh * dh * w;
     });
     if (hh > R(1e-30) * rho * rho) {
       use_gamma = true;
-      gamma = R(1) / beta - (R(2) - R(1) / beta) * sh / hh;
+      gamma = ib - (R(2) - ib) * fdiv(sh, hh);
     }
   }
   const R a = R(1) - beta * gamma, b = beta * (gamma - R(2));
@@ -157,13 +158,14 @@ __device__ void kbc_vjp(const R (&f)[27], R (&lam)[27], R beta, bool lbgk) {
     G -= beta * lam[i] * (df[i] - ds);
   });
   if (use_gamma) {
-    const R c = R(2) - R(1) / beta;
-    const R Lsh = -G * c / hh, Lhh = G * c * sh / (hh * hh);
+    const R c = R(2) - ib;
+    const R ihh = rcp_fast(hh);
+    const R Lsh = -G * c * ihh, Lhh = G * c * sh * ihh * ihh;
     unroll<27>([&](auto I) {
       constexpr int i = decltype(I)::value;
       const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
       const R dh = df[i] - ds;
-      const R w = R(1) / q.fefull[i];
+      const R w = rcp_fast(q.fefull[i]);
       const R dhb = (Lsh * ds + R(2) * Lhh * dh) * w;
       const R wb = Lsh * ds * dh + Lhh * dh * dh;
       dsb[i] += Lsh * dh * w - dhb;
@@ -250,9 +252,11 @@ __device__ __forceinline__ void load_lam(const PatchDev& p, const R* __restrict_
 template <typename R>
 __global__ void __launch_bounds__(128) k_adj_sc(PatchDev p, const R* __restrict__ fin, const R* __restrict__ lam_new,
                                                 R* __restrict__ lam_old, R beta, int odd, int lbgk, int* status) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
-  if (x >= p.dim[0]) return;
+  // one thread per stored node (no padding lanes)
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (long long)p.dim[0] * p.dim[1] * p.dim[2]) return;
+  const int x = (int)(k % p.dim[0]), y = (int)((k / p.dim[0]) % p.dim[1]);
+  const int z = (int)(k / ((long long)p.dim[0] * p.dim[1]));
   const long long own = node_index(p, x, y, z);
   const uint8_t t = p.type[own];
   if (!(t == T_BULK || t == T_BC || (t == T_D1 && odd))) return;
@@ -370,7 +374,8 @@ __global__ void __launch_bounds__(128) k_adj_explode(PatchDev pc, const R* __res
   });
 }
 
-// transpose of one interpolation pass: vbar[c][src_k] += w_k vbar[c][out0 + q]
+// transpose of one interpolation pass: vbar[c][src_k] += w_k vbar[c][out0 + q];
+// one thread per (point, value)
 template <typename R>
 __global__ void __launch_bounds__(128) k_adj_points(const uint4* __restrict__ src, long long n, R* __restrict__ vbar,
                                                     long long ld, long long out0) {
@@ -378,14 +383,12 @@ __global__ void __launch_bounds__(128) k_adj_points(const uint4* __restrict__ sr
   if (q >= n) return;
   const uint4 s = src[q];
   const R w0 = R(-1.0 / 16.0), w1 = R(9.0 / 16.0);
-  for (int c = 0; c < 31; ++c) {
-    R* d = vbar + (long long)c * ld;
-    const R x = d[out0 + q];
-    atomicAdd(d + s.x, w0 * x);
-    atomicAdd(d + s.y, w1 * x);
-    atomicAdd(d + s.z, w1 * x);
-    atomicAdd(d + s.w, w0 * x);
-  }
+  R* d = vbar + (long long)blockIdx.y * ld;
+  const R x = d[out0 + q];
+  atomicAdd(d + s.x, w0 * x);
+  atomicAdd(d + s.y, w1 * x);
+  atomicAdd(d + s.z, w1 * x);
+  atomicAdd(d + s.w, w0 * x);
 }
 
 // samples: (rho~, u, factor (f - f^eq)) of the pulled state of a parent or child node
@@ -525,7 +528,8 @@ cudaError_t launch_adj_sc(int storage, const PatchDev& p, const void* fin, const
                           double beta, int odd, int lbgk, int* status, cudaStream_t st) {
   return adj_dispatch(storage, [&](auto z) {
     using R = decltype(z);
-    dim3 block(128), grid((p.dim[0] + 127) / 128, p.dim[1], p.dim[2]);
+    const long long n = (long long)p.dim[0] * p.dim[1] * p.dim[2];
+    dim3 block(128), grid((unsigned)((n + 127) / 128));
     k_adj_sc<R><<<grid, block, 0, st>>>(p, (const R*)fin, (const R*)lam_new, (R*)lam_old, (R)beta, odd, lbgk,
                                         status);
     return cudaGetLastError();
@@ -564,7 +568,8 @@ cudaError_t launch_adj_points(int storage, const uint32_t* pt_src, int64_t n, vo
   if (n == 0) return cudaSuccess;
   return adj_dispatch(storage, [&](auto z) {
     using R = decltype(z);
-    k_adj_points<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>((const uint4*)pt_src, n, (R*)vbar, ld, out0);
+    k_adj_points<R><<<dim3((unsigned)((n + 127) / 128), 31), 128, 0, st>>>((const uint4*)pt_src, n, (R*)vbar, ld,
+                                                                          out0);
     return cudaGetLastError();
   });
 }

@@ -112,43 +112,53 @@ def test_cuda_adjoint_matches_reference_gradient(storage, tol):
 
 @pytest.mark.gpu
 def test_cuda_adjoint_full_case_finite_differences():
-    """64^3 box with [24,40]^3 refined, FP32, 40 coarse steps, checkpoints every 20:
-    directional derivatives along 4 seeded directions against central differences."""
+    """64^3 box with [24,40]^3 refined, objective after 200 coarse steps,
+    checkpoints every 20, 16 seeded smooth directions, central differences of
+    the FP64 forward: the FP64 adjoint within 1e-6 relative per direction; the
+    FP32-storage adjoint (FP64 gradient reduction) within 1e-4 of the
+    gradient's norm (a direction with a small derivative measures the FP32
+    trajectory's rounding, not the adjoint)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1608_06915_gb300 import lbm as L
     case = I.adjoint_case()
-    g = L.Grid(case, "fp32")
+    g32 = L.Grid(case, "fp32")
+    g64 = L.Grid(case, "fp64")
     modes = I.divfree_modes(n=64, kmax=4.0, rms=0.03, seed=4)
     u0 = []
-    for info in g.patches:
+    for info in g32.patches:
         x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
         u0.append(torch.tensor(I.divfree_fields(x, y, z, modes)[1]).cuda())
-    steps, K = 40, 20
-    x0 = [u.clone().requires_grad_(True) for u in u0]
-    J = L.kinetic_energy_run(g, x0, steps, K)
-    J.backward()
-    grads = [u.grad for u in x0]
+    steps, K = 200, 20
+    grads = {}
+    for name, g in (("fp32", g32), ("fp64", g64)):
+        x0 = [u.clone().requires_grad_(True) for u in u0]
+        L.kinetic_energy_run(g, x0, steps, K).backward()
+        grads[name] = [u.grad for u in x0]
+    gnorm = math.sqrt(sum(float((v * v).sum()) for v in grads["fp64"]))
     norm = math.sqrt(sum(float((u * u).sum()) for u in u0))
-    worst = 0.0
-    for seed in range(100, 104):
+    worst64 = worst32 = 0.0
+    for seed in range(100, 116):
         # smooth seeded directions (divergence-free Fourier fields, |k| <= 4)
         dm = I.divfree_modes(n=64, kmax=4.0, rms=0.03, seed=seed)
         d = []
-        for info in g.patches:
+        for info in g32.patches:
             x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
             d.append(torch.tensor(I.divfree_fields(x, y, z, dm)[1]).cuda())
         dn = math.sqrt(sum(float((v * v).sum()) for v in d))
         d = [v / dn for v in d]
-        eps = 1e-3 * norm
-        jp = float(L.kinetic_energy_run(g, [u + eps * v for u, v in zip(u0, d)], steps, K))
-        jm = float(L.kinetic_energy_run(g, [u - eps * v for u, v in zip(u0, d)], steps, K))
+        eps = 1e-4 * norm
+        jp = float(L.kinetic_energy_run(g64, [u + eps * v for u, v in zip(u0, d)], steps, K))
+        jm = float(L.kinetic_energy_run(g64, [u - eps * v for u, v in zip(u0, d)], steps, K))
         fd = (jp - jm) / (2 * eps)
-        ad = sum(float((gr * v).sum()) for gr, v in zip(grads, d))
-        rel = abs(fd - ad) / abs(ad)
-        worst = max(worst, rel)
-        print("direction %d: finite difference %.9e adjoint %.9e rel %.2e" % (seed, fd, ad, rel))
-    assert worst < 1e-3, worst
+        a64 = sum(float((gr * v).sum()) for gr, v in zip(grads["fp64"], d))
+        a32 = sum(float((gr * v).sum()) for gr, v in zip(grads["fp32"], d))
+        r64, r32 = abs(fd - a64) / abs(fd), abs(fd - a32) / gnorm
+        worst64, worst32 = max(worst64, r64), max(worst32, r32)
+        print("direction %d: finite difference %.10e adjoint fp64 %.10e (rel %.1e) fp32 %.10e (/|grad| %.1e)" % (
+            seed, fd, a64, r64, a32, r32))
+    assert worst64 < 1e-6, worst64
+    assert worst32 < 1e-4, worst32
 
 
 @pytest.mark.gpu
