@@ -107,6 +107,10 @@ __device__ __forceinline__ void add_feq_f_vjp(const EqState<R>& q, const R (&xba
 
 // lam: in = adjoint of the post-collision state, out = adjoint of the
 // pre-collision state f (deviation populations, unchanged).
+//
+// Written to keep few arrays live (this is register-bound): f^eq - W and df
+// are kept, while the shear part, dh and the weights 1/f^eq are recomputed
+// in each pass, and the adjoints of ds, df and f^eq are reduced on the fly.
 template <typename R>
 __device__ void kbc_vjp(const R (&f)[27], R (&lam)[27], R beta, bool lbgk) {
   R rho_t, rho, ux, uy, uz;
@@ -134,7 +138,7 @@ __device__ void kbc_vjp(const R (&f)[27], R (&lam)[27], R beta, bool lbgk) {
   if (!lbgk) {
     unroll<27>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const R w = rcp_fast(q.fefull[i]);  // entropic weight 1 / f^eq_i
+      const R w = rcp_fast(R(WI(i)) + q.fe[i]);  // entropic weight 1 / f^eq_i
       const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
       const R dh = df[i] - ds;
       sh += ds * dh * w;
@@ -146,46 +150,42 @@ __device__ void kbc_vjp(const R (&f)[27], R (&lam)[27], R beta, bool lbgk) {
     }
   }
   const R a = R(1) - beta * gamma, b = beta * (gamma - R(2));
-  // reverse of f' = fe + a df + b ds
-  R dfb[27], dsb[27], feb[27];
-  R G = 0;  // dL/dgamma = -beta lam . dh
+  // reverse of f' = fe + a df + b ds; G = dL/dgamma = -beta lam . dh
+  R G = 0;
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
-    dfb[i] = a * lam[i];
-    dsb[i] = b * lam[i];
-    feb[i] = lam[i];
-    G -= beta * lam[i] * (df[i] - ds);
+    G -= beta * lam[i] * (df[i] - shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz));
   });
+  R Lsh = 0, Lhh = 0;
   if (use_gamma) {
     const R c = R(2) - ib;
     const R ihh = rcp_fast(hh);
-    const R Lsh = -G * c * ihh, Lhh = G * c * sh * ihh * ihh;
-    unroll<27>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
-      const R dh = df[i] - ds;
-      const R w = rcp_fast(q.fefull[i]);
-      const R dhb = (Lsh * ds + R(2) * Lhh * dh) * w;
-      const R wb = Lsh * ds * dh + Lhh * dh * dh;
-      dsb[i] += Lsh * dh * w - dhb;
-      dfb[i] += dhb;
-      feb[i] -= wb * w * w;  // w = 1 / fe
-    });
+    Lsh = -G * c * ihh;
+    Lhh = G * c * sh * ihh * ihh;
   }
-  // ds = S df: adjoint of the second moments, then df-bar += M^T Pbar
+  // pass 1: adjoint of ds reduced to the adjoint of the second moments
   R Sx = 0, Sy = 0, Sz = 0, Exy = 0, Exz = 0, Eyz = 0;
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr int ax = CX(i) != 0, ay = CY(i) != 0, az = CZ(i) != 0;
-    if constexpr (ax + ay + az == 1) {
-      if constexpr (ax) Sx += dsb[i];
-      else if constexpr (ay) Sy += dsb[i];
-      else Sz += dsb[i];
-    } else if constexpr (ax + ay + az == 2) {
-      if constexpr (!az) Exy += R(CX(i) * CY(i)) * dsb[i];
-      else if constexpr (!ay) Exz += R(CX(i) * CZ(i)) * dsb[i];
-      else Eyz += R(CY(i) * CZ(i)) * dsb[i];
+    if constexpr (ax + ay + az == 1 || ax + ay + az == 2) {
+      const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
+      R dsb = b * lam[i];
+      if (use_gamma) {
+        const R dh = df[i] - ds;
+        const R w = rcp_fast(R(WI(i)) + q.fe[i]);
+        const R dhb = (Lsh * ds + R(2) * Lhh * dh) * w;
+        dsb += Lsh * dh * w - dhb;
+      }
+      if constexpr (ax + ay + az == 1) {
+        if constexpr (ax) Sx += dsb;
+        else if constexpr (ay) Sy += dsb;
+        else Sz += dsb;
+      } else {
+        if constexpr (!az) Exy += R(CX(i) * CY(i)) * dsb;
+        else if constexpr (!ay) Exz += R(CX(i) * CZ(i)) * dsb;
+        else Eyz += R(CY(i) * CZ(i)) * dsb;
+      }
     }
   });
   // face: ds = (1/3) Pxx - (1/6) Pyy - (1/6) Pzz (for x); edge: ds = c c P / 4
@@ -193,20 +193,47 @@ __device__ void kbc_vjp(const R (&f)[27], R (&lam)[27], R beta, bool lbgk) {
   const R Pbyy = R(1.0 / 3.0) * Sy - R(1.0 / 6.0) * (Sx + Sz);
   const R Pbzz = R(1.0 / 3.0) * Sz - R(1.0 / 6.0) * (Sx + Sy);
   const R Pbxy = R(0.25) * Exy, Pbxz = R(0.25) * Exz, Pbyz = R(0.25) * Eyz;
+  // pass 2: adjoint of df (to f directly) and of f^eq (reduced to rho, u)
+  R tot = 0, sx[3] = {0, 0, 0}, sy[3] = {0, 0, 0}, sz[3] = {0, 0, 0};
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    R v = dfb[i];
-    if constexpr (CX(i) != 0) v += Pbxx;
-    if constexpr (CY(i) != 0) v += Pbyy;
-    if constexpr (CZ(i) != 0) v += Pbzz;
-    if constexpr (CX(i) * CY(i) != 0) v += R(CX(i) * CY(i)) * Pbxy;
-    if constexpr (CX(i) * CZ(i) != 0) v += R(CX(i) * CZ(i)) * Pbxz;
-    if constexpr (CY(i) * CZ(i) != 0) v += R(CY(i) * CZ(i)) * Pbyz;
-    dfb[i] = v;
-    feb[i] -= v;  // df = f - fe
+    const R fefull = R(WI(i)) + q.fe[i];
+    R dfb = a * lam[i];
+    R feb = lam[i];
+    if (use_gamma) {
+      const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
+      const R dh = df[i] - ds;
+      const R w = rcp_fast(fefull);
+      dfb += (Lsh * ds + R(2) * Lhh * dh) * w;
+      feb -= (Lsh * ds * dh + Lhh * dh * dh) * w * w;  // d(1/fe) = -w^2
+    }
+    if constexpr (CX(i) != 0) dfb += Pbxx;
+    if constexpr (CY(i) != 0) dfb += Pbyy;
+    if constexpr (CZ(i) != 0) dfb += Pbzz;
+    if constexpr (CX(i) * CY(i) != 0) dfb += R(CX(i) * CY(i)) * Pbxy;
+    if constexpr (CX(i) * CZ(i) != 0) dfb += R(CX(i) * CZ(i)) * Pbxz;
+    if constexpr (CY(i) * CZ(i) != 0) dfb += R(CY(i) * CZ(i)) * Pbyz;
+    feb -= dfb;  // df = f - fe
+    lam[i] = dfb;
+    const R qv = feb * fefull;
+    tot += qv;
+    sx[CX(i) + 1] += qv;
+    sy[CY(i) + 1] += qv;
+    sz[CZ(i) + 1] += qv;
   });
-  unroll<27>([&](auto I) { lam[decltype(I)::value] = dfb[decltype(I)::value]; });
-  add_feq_f_vjp<R>(q, feb, lam);
+  // f^eq(rho, u): rho-bar = sum feb fe / rho, u-bar_a = sum feb fe L_a; then
+  // through rho = sum f and u = j / rho
+  R rb = tot / q.rho;
+  const R ub[3] = {sx[0] * q.L[0][0] + sx[1] * q.L[0][1] + sx[2] * q.L[0][2],
+                   sy[0] * q.L[1][0] + sy[1] * q.L[1][1] + sy[2] * q.L[1][2],
+                   sz[0] * q.L[2][0] + sz[1] * q.L[2][1] + sz[2] * q.L[2][2]};
+  const R ir = R(1) / q.rho;
+  const R jb[3] = {ub[0] * ir, ub[1] * ir, ub[2] * ir};
+  rb -= (ub[0] * q.u[0] + ub[1] * q.u[1] + ub[2] * q.u[2]) * ir;
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    lam[i] += rb + R(CX(i)) * jb[0] + R(CY(i)) * jb[1] + R(CZ(i)) * jb[2];
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -248,9 +275,30 @@ __device__ __forceinline__ void load_lam(const PatchDev& p, const R* __restrict_
   });
 }
 
-// bulk stream-collide
+// Scatter of the adjoint to the sources pull_bulk reads.
 template <typename R>
-__global__ void __launch_bounds__(128) k_adj_sc(PatchDev p, const R* __restrict__ fin, const R* __restrict__ lam_new,
+__device__ __forceinline__ void push_bulk(const PatchDev& p, R* __restrict__ lam_old, int x, int y, int z,
+                                          const R (&fb)[27]) {
+  const int xm = x == 0 ? p.dim[0] - 1 : x - 1, xp = x == p.dim[0] - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? p.dim[1] - 1 : y - 1, yp = y == p.dim[1] - 1 ? 0 : y + 1;
+  const int zm = z == 0 ? p.dim[2] - 1 : z - 1, zp = z == p.dim[2] - 1 ? 0 : z + 1;
+  const long long row = p.nxp, sl = (long long)p.nxp * p.dim[1];
+  const long long xs[3] = {xp, x, xm};  // source x for cx = -1, 0, +1
+  const long long ys[3] = {yp * row, y * row, ym * row};
+  const long long zs[3] = {zp * sl, z * sl, zm * sl};
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    atomicAdd(lam_old + (long long)i * p.plane + zs[CZ(i) + 1] + ys[CY(i) + 1] + xs[CX(i) + 1], fb[i]);
+  });
+}
+
+// stream-collide, two kernels over the stored nodes: bulk nodes and (odd
+// substeps) depth-1 nodes pull and scatter along the plain neighbour pattern,
+// whose sources all lie in the patch in the layouts the adjoint accepts;
+// boundary-class nodes take the node-by-node pull in a kernel of their own, so
+// that the hot kernel's code and registers stay those of the plain path.
+template <typename R, bool PLAIN>
+__global__ void __launch_bounds__(128, 3) k_adj_sc(PatchDev p, const R* __restrict__ fin, const R* __restrict__ lam_new,
                                                 R* __restrict__ lam_old, R beta, int odd, int lbgk, int* status) {
   // one thread per stored node (no padding lanes)
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -259,13 +307,18 @@ __global__ void __launch_bounds__(128) k_adj_sc(PatchDev p, const R* __restrict_
   const int z = (int)(k / ((long long)p.dim[0] * p.dim[1]));
   const long long own = node_index(p, x, y, z);
   const uint8_t t = p.type[own];
-  if (!(t == T_BULK || t == T_BC || (t == T_D1 && odd))) return;
   R f[27], l[27];
-  if (t == T_BULK) pull_bulk<R, R>(p, fin, x, y, z, f);
-  else pull_generic<R, R>(p, fin, x, y, z, f, status);
+  if constexpr (PLAIN) {
+    if (!(t == T_BULK || (t == T_D1 && odd))) return;
+    pull_bulk<R, R>(p, fin, x, y, z, f);
+  } else {
+    if (t != T_BC) return;
+    pull_generic<R, R>(p, fin, x, y, z, f, status);
+  }
   load_lam<R>(p, lam_new, own, l);
   kbc_vjp<R>(f, l, beta, lbgk != 0);
-  push_adjoint<R>(p, lam_old, x, y, z, l);
+  if constexpr (PLAIN) push_bulk<R>(p, lam_old, x, y, z, l);
+  else push_adjoint<R>(p, lam_old, x, y, z, l);
 }
 
 __device__ __forceinline__ void node_xyz(const PatchDev& p, long long n, int& x, int& y, int& z) {
@@ -530,8 +583,12 @@ cudaError_t launch_adj_sc(int storage, const PatchDev& p, const void* fin, const
     using R = decltype(z);
     const long long n = (long long)p.dim[0] * p.dim[1] * p.dim[2];
     dim3 block(128), grid((unsigned)((n + 127) / 128));
-    k_adj_sc<R><<<grid, block, 0, st>>>(p, (const R*)fin, (const R*)lam_new, (R*)lam_old, (R)beta, odd, lbgk,
-                                        status);
+    k_adj_sc<R, true><<<grid, block, 0, st>>>(p, (const R*)fin, (const R*)lam_new, (R*)lam_old, (R)beta, odd, lbgk,
+                                              status);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    k_adj_sc<R, false><<<grid, block, 0, st>>>(p, (const R*)fin, (const R*)lam_new, (R*)lam_old, (R)beta, odd,
+                                               lbgk, status);
     return cudaGetLastError();
   });
 }

@@ -65,7 +65,16 @@ struct lbm_grid {
     for (auto& x : gcache) cudaGraphExecDestroy(x.exec);
     gcache.clear();
   }
+  // side streams of the adjoint: coupling adjoints run beside the
+  // stream-collide adjoint (their writes are reductions that commute)
+  cudaStream_t adj_side[2] = {nullptr, nullptr};
+  cudaEvent_t adj_fork = nullptr, adj_join[2] = {nullptr, nullptr};
   ~lbm_grid() {
+    for (auto& x : adj_side)
+      if (x) cudaStreamDestroy(x);
+    if (adj_fork) cudaEventDestroy(adj_fork);
+    for (auto& x : adj_join)
+      if (x) cudaEventDestroy(x);
     drop_graphs();
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto e : pool) cudaEventDestroy(e);
@@ -165,14 +174,13 @@ lbm_status check_bound(lbm_grid* g) {
 }
 
 // Intermediate points of the separable reconstruction, stage 1 then stage 2.
-cudaError_t point_passes(lbm_grid* g, const HostPatch& p, int ncomp) {
+cudaError_t point_passes(lbm_grid* g, const HostPatch& p, int ncomp, cudaStream_t st) {
   const int64_t ld = (int64_t)p.n_points(), ns = (int64_t)p.smp_node.size();
   const uint32_t* src = at<uint32_t>(g, p.off_pt_src);
-  cudaError_t e = lbmk::launch_points(g->hg.desc.storage, ncomp, src, p.n_pt[0], g->base + p.off_smp_val, ld, ns,
-                                      g->stream);
+  cudaError_t e = lbmk::launch_points(g->hg.desc.storage, ncomp, src, p.n_pt[0], g->base + p.off_smp_val, ld, ns, st);
   if (!e)
     e = lbmk::launch_points(g->hg.desc.storage, ncomp, src + 4 * (size_t)p.n_pt[0], p.n_pt[1],
-                            g->base + p.off_smp_val, ld, ns + p.n_pt[0], g->stream);
+                            g->base + p.off_smp_val, ld, ns + p.n_pt[0], st);
   return e;
 }
 
@@ -299,7 +307,7 @@ lbm_status run_instant(lbm_grid* g, int k) {
                                     g->base + p.off_smp_val, (int64_t)p.n_points(), q.beta / (2.0 * p.beta),
                                     q.beta1 / (2.0 * p.beta1), thermal_level(g, q), thermal_level(g, p),
                                     status_ptr(g), g->stream);
-                                return e ? e : point_passes(g, p, 59);
+                                return e ? e : point_passes(g, p, 59, g->stream);
                               }),
                         "thermal samples");
         if (st) return st;
@@ -325,7 +333,7 @@ lbm_status run_instant(lbm_grid* g, int k) {
                                     at<uint8_t>(g, p.off_smp_kind), (int64_t)p.smp_node.size(),
                                     g->base + p.off_smp_val, (int64_t)p.n_points(), q.beta / (2.0 * p.beta),
                                     status_ptr(g), g->stream);
-                                return e ? e : point_passes(g, p, 31);
+                                return e ? e : point_passes(g, p, 31, g->stream);
                               }),
                         "samples");
         if (st) return st;
@@ -815,6 +823,18 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
   for (int pi : active)
     if (!e) e = cudaMemsetAsync(lam_ptr(pi, 1 - lcur[pi]), 0, 27 * (size_t)hg.P[pi].plane * rb, g->stream);
   if (e) return cuda_check(g, e, "adjoint zero");
+  // three independent chains after the zeroing: the stream-collide adjoints
+  // (bound stream), the coalesce adjoints (side stream 0) and, per child, the
+  // explode chain (side stream 1); each adds into lambda with reductions
+  for (int q = 0; q < 2 && !e; ++q)
+    if (!g->adj_side[q]) e = cudaStreamCreateWithFlags(&g->adj_side[q], cudaStreamNonBlocking);
+  if (!e && !g->adj_fork) e = cudaEventCreateWithFlags(&g->adj_fork, cudaEventDisableTiming);
+  for (int q = 0; q < 2 && !e; ++q)
+    if (!g->adj_join[q]) e = cudaEventCreateWithFlags(&g->adj_join[q], cudaEventDisableTiming);
+  if (!e) e = cudaEventRecord(g->adj_fork, g->stream);
+  for (int q = 0; q < 2 && !e; ++q) e = cudaStreamWaitEvent(g->adj_side[q], g->adj_fork, 0);
+  if (e) return cuda_check(g, e, "adjoint streams");
+  cudaStream_t sc = g->adj_side[0], sx = g->adj_side[1];
   for (int pi : active) {
     HostPatch& p = hg.P[pi];
     const int lev = p.level;
@@ -831,7 +851,7 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
         e = lbmk::launch_adj_coalesce(storage, view(g, c), g->base + c.off_f[c.cur], pv, lam_ptr(pi, lcur[pi]),
                                       lam_ptr(ci, 1 - lcur[ci]), at<uint32_t>(g, c.off_cf_parent),
                                       at<uint32_t>(g, c.off_cf_child), (int64_t)c.cf_parent.size(),
-                                      2.0 * c.beta / p.beta, p.beta, lbgk, status_ptr(g), g->stream);
+                                      2.0 * c.beta / p.beta, p.beta, lbgk, status_ptr(g), sc);
     }
     if (lev > 0 && parent_active) {
       HostPatch& q = hg.P[p.parent];
@@ -843,24 +863,29 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
       if (!e)
         e = lbmk::launch_samples(storage, qv, g->base + q.off_f[q.cur], pv, g->base + p.off_f[p.cur],
                                  at<uint32_t>(g, p.off_smp_node), at<uint8_t>(g, p.off_smp_kind), ns,
-                                 g->base + p.off_smp_val, ld, q.beta / (2.0 * p.beta), status_ptr(g), g->stream);
-      if (!e) e = point_passes(g, p, 31);
-      if (!e && ld) e = cudaMemsetAsync(sbar, 0, 31 * (size_t)ld * rb, g->stream);
+                                 g->base + p.off_smp_val, ld, q.beta / (2.0 * p.beta), status_ptr(g), sx);
+      if (!e) e = point_passes(g, p, 31, sx);
+      if (!e && ld) e = cudaMemsetAsync(sbar, 0, 31 * (size_t)ld * rb, sx);
       if (!e)
         e = lbmk::launch_adj_explode(storage, pv, lam_ptr(pi, lcur[pi]), at<uint32_t>(g, p.off_ex_node),
                                      at<uint32_t>(g, p.off_ex_src), (int64_t)p.ex_one, (int64_t)p.ex_node.size(),
-                                     g->base + p.off_smp_val, sbar, ld, p.beta, lbgk, g->stream);
+                                     g->base + p.off_smp_val, sbar, ld, p.beta, lbgk, sx);
       // the interpolation passes transposed, last pass first
       if (!e)
-        e = lbmk::launch_adj_points(storage, psrc + 4 * (size_t)p.n_pt[0], p.n_pt[1], sbar, ld, ns + p.n_pt[0],
-                                    g->stream);
-      if (!e) e = lbmk::launch_adj_points(storage, psrc, p.n_pt[0], sbar, ld, ns, g->stream);
+        e = lbmk::launch_adj_points(storage, psrc + 4 * (size_t)p.n_pt[0], p.n_pt[1], sbar, ld, ns + p.n_pt[0], sx);
+      if (!e) e = lbmk::launch_adj_points(storage, psrc, p.n_pt[0], sbar, ld, ns, sx);
       if (!e)
         e = lbmk::launch_adj_samples(storage, qv, g->base + q.off_f[q.cur], lam_ptr(qi, 1 - lcur[qi]), pv,
                                      g->base + p.off_f[p.cur], lam_ptr(pi, 1 - lcur[pi]),
                                      at<uint32_t>(g, p.off_smp_node), at<uint8_t>(g, p.off_smp_kind), ns, sbar, ld,
-                                     q.beta / (2.0 * p.beta), status_ptr(g), g->stream);
+                                     q.beta / (2.0 * p.beta), status_ptr(g), sx);
     }
+  }
+  // join the side streams back into the bound stream
+  for (int q = 0; q < 2; ++q) {
+    cudaError_t e2 = cudaEventRecord(g->adj_join[q], g->adj_side[q]);
+    if (!e2) e2 = cudaStreamWaitEvent(g->stream, g->adj_join[q], 0);
+    if (!e) e = e2;
   }
   if (e) return cuda_check(g, e, "adjoint instant");
   for (int pi : active) lcur[pi] ^= 1;

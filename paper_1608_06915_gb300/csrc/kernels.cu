@@ -157,16 +157,35 @@ cudaError_t launch_samples(int storage, const PatchDev& parent, const void* fin_
 // val[c][out0 + q] = sum_k w_k val[c][src[4q + k]].  The tensor interpolation
 // over two or three off-lattice axes is this one-axis pass applied axis after
 // axis (stage 1 from the samples, stage 2 from stage 1, the targets last).
-// One thread per (point, value): a single round trip to the four sources.
-template <typename R>
+// Large passes: one thread per point, all its values (enough points to fill
+// the GPU, and the four source indices are read once).
+template <typename R, int NC>
 __global__ void __launch_bounds__(128) k_points(const uint4* __restrict__ src, long long n, R* __restrict__ val,
                                                 long long ld, long long out0) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const uint4 s = __ldg(src + q);
   const R w0 = R(-1.0 / 16.0), w1 = R(9.0 / 16.0);
+#pragma unroll 4
+  for (int c = 0; c < NC; ++c) {
+    // the columns read are never written by this pass: read-only cache path
+    const R* v = val + (long long)c * ld;
+    const R a = __ldg(v + s.x), b = __ldg(v + s.y), d = __ldg(v + s.z), e = __ldg(v + s.w);
+    val[(long long)c * ld + out0 + q] = w0 * (a + e) + w1 * (b + d);
+  }
+}
+
+// Small passes: one thread per (point, value), a single round trip to the
+// four sources, so that a pass of a few thousand points is not latency-bound.
+template <typename R>
+__global__ void __launch_bounds__(128) k_points_small(const uint4* __restrict__ src, long long n,
+                                                      R* __restrict__ val, long long ld, long long out0) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const uint4 s = __ldg(src + q);
+  const R w0 = R(-1.0 / 16.0), w1 = R(9.0 / 16.0);
   R* v = val + (long long)blockIdx.y * ld;
-  const R a = v[s.x], b = v[s.y], d = v[s.z], e = v[s.w];
+  const R a = __ldg(v + s.x), b = __ldg(v + s.y), d = __ldg(v + s.z), e = __ldg(v + s.w);
   v[out0 + q] = w0 * (a + e) + w1 * (b + d);
 }
 
@@ -176,8 +195,14 @@ cudaError_t launch_points(int storage, int ncomp, const uint32_t* pt_src, int64_
   if (ncomp != 31 && ncomp != 59) return cudaErrorInvalidValue;
   return dispatch(storage, [&](auto, auto tr) {
     using R = typename decltype(tr)::type;
-    const dim3 grid((unsigned)((n + 127) / 128), (unsigned)ncomp);
-    k_points<R><<<grid, 128, 0, st>>>((const uint4*)pt_src, n, (R*)val, ld, out0);
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    if (n < 65536) {
+      k_points_small<R><<<dim3(blocks, (unsigned)ncomp), 128, 0, st>>>((const uint4*)pt_src, n, (R*)val, ld, out0);
+    } else if (ncomp == 31) {
+      k_points<R, 31><<<blocks, 128, 0, st>>>((const uint4*)pt_src, n, (R*)val, ld, out0);
+    } else {
+      k_points<R, 59><<<blocks, 128, 0, st>>>((const uint4*)pt_src, n, (R*)val, ld, out0);
+    }
     return cudaGetLastError();
   });
 }
