@@ -370,6 +370,10 @@ def cuda_arm(args):
     t = float(tt.item())
     diag = g.diagnostics()
     value = nup * args.steps * world / t / 1e6
+    # the refinement benefit: node updates a uniform finest-level grid would need
+    nlev = 1 + max(info["level"] for info in g.patches)
+    n_uniform = float(np.prod([float(v) * (1 << (nlev - 1)) for v in case["n"]])) * (1 << (nlev - 1))
+    uniform_equiv = n_uniform * args.steps * world / t / 1e6
 
     # dominant kernel: the class with the largest device time
     top = max(report, key=lambda r: r["ms"])
@@ -387,7 +391,8 @@ def cuda_arm(args):
                     peak_source="measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                     kernel=("k_sc_tma, TMA tile pass batched over the patches of each instant"
                             if top["kind"] == "stream_collide_tma" else "%s level %d" % (top["kind"], top["level"])),
-                    avg_launch_ms=avg_ms, alg_bytes_per_launch=alg_bytes, bytes_per_node_update=bpu)
+                    avg_launch_ms=avg_ms, alg_bytes_per_launch=alg_bytes, bytes_per_node_update=bpu,
+                    frac_of_nominal_7900=achieved / 7900.0)
     kernels = [dict(r, avg_us=1e3 * r["ms"] / r["launches"]) for r in report]
     launches = sum(r["launches"] for r in report)
 
@@ -417,6 +422,10 @@ def cuda_arm(args):
                                 l2="no flush: working set %.2f GB > %.0f MB L2" % (ws / 1e9, L2_BYTES / 1e6)),
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clk,
                     adjoint_forward_ratio=adj,
+                    uniform_fine_equivalent=dict(
+                        value=uniform_equiv, unit=UNIT,
+                        note="node updates of a uniform grid at the finest spacing (%d levels) per coarse step, "
+                             "%.4g, over the same time" % (nlev, n_uniform)),
                     kernels=kernels,
                     diagnostics=dict(mass=diag["mass"], min_rho=diag["min_rho"], status=diag["status"]))
         print(json.dumps(line), flush=True)

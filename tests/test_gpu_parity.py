@@ -152,6 +152,19 @@ def test_sphere_small_fp32_drag():
     assert rel < 1e-4
 
 
+@pytest.mark.parametrize("storage,bound", [("fp32", 1e-5), ("fp16s", 3e-3), ("bf16s", 3e-2)])
+def test_sphere_storage_error(storage, bound):
+    """Velocity and density error of each storage against the FP64 oracle on
+    the four-level sphere (48x24x24 coarse), 20 coarse steps from uniform flow."""
+    case = I.sphere_case(scale=8)
+    g, o = twin(case, storage, lambda x, y, z, p, info: I.uniform_fields(x, (0.05, 0.0, 0.0)))
+    g.step(20)
+    o.step(20)
+    er, eu = macro_rel_l2(g, o)
+    print("sphere %s after 20 steps: rel L2 rho %.3e u %.3e" % (storage, er, eu))
+    assert er < bound and eu < bound
+
+
 def test_drag_is_the_momentum_the_fluid_loses_on_gpu():
     """Periodic box with a solid ball, one level, FP64: the drag of the state a
     step starts from is the fluid momentum that step loses (diagnostics)."""
