@@ -559,12 +559,33 @@ std::string build_layout(HostGrid& g) {
       return id;
     };
     // Reconstruction (Eq. interp) as separable four-point passes: a target
-    // off-lattice along the axes of mask m interpolates, along the highest of
-    // them, four points at the coarse positions of that axis -- samples when
+    // off-lattice along the axes of mask m interpolates, along the last of
+    // them in the pass order below, four points at the coarse positions of
+    // that axis -- samples when
     // no other axis is off-lattice, else intermediate points of mask m minus
     // that axis, built the same way.  Points are keyed by (mask, fine
     // position); ids carry their stage in the top two bits until numbered.
     constexpr uint32_t kStage1 = 1u << 30, kStage2 = 2u << 30, kIdMask = (1u << 30) - 1;
+    // Axis order of the passes: axes with interface faces first, the others
+    // after.  Then the last pass runs along a tangential axis, and the points
+    // it combines lie on the interface layers themselves (they are targets),
+    // not in rows reaching into the parent.
+    int order_pos[3];
+    {
+      int pos = 0;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int a = 0; a < 3; ++a) {
+          const bool normal = c.flo[a] || c.fhi[a];
+          if (normal == (pass == 0)) order_pos[a] = pos++;
+        }
+    }
+    auto top_axis = [&](int m) {
+      int t = -1;
+      for (int a = 0; a < 3; ++a)
+        if ((m >> a) & 1)
+          if (t < 0 || order_pos[a] > order_pos[t]) t = a;
+      return t;
+    };
     std::unordered_map<uint64_t, uint32_t> pts[2];
     std::vector<uint32_t> psrc[2];   // 4 tagged sources per point
     std::vector<uint64_t> ppos[2];   // position key of each point (ordering)
@@ -606,7 +627,7 @@ std::string build_layout(HostGrid& g) {
       const uint64_t key = pkey(m, Q);
       auto it = pts[st].find(key);
       if (it != pts[st].end()) return it->second;
-      const int top = m & 4 ? 2 : (m & 2 ? 1 : 0);
+      const int top = top_axis(m);
       uint32_t src[4];
       for (int k = 0; k < 4; ++k) {
         int64_t R[3] = {Q[0], Q[1], Q[2]};
@@ -635,7 +656,7 @@ std::string build_layout(HostGrid& g) {
         tsrc.push_back(point(0, Y));
         for (int k = 0; k < 3; ++k) tsrc.push_back(~0u);
       } else {
-        const int top = m & 4 ? 2 : (m & 2 ? 1 : 0);
+        const int top = top_axis(m);
         for (int k = 0; k < 4; ++k) {
           int64_t R[3] = {Y[0], Y[1], Y[2]};
           R[top] = Y[top] - 3 + 2 * k;
