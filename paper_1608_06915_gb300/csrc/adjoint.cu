@@ -578,7 +578,7 @@ cudaError_t adj_dispatch(int storage, F&& f) {
 }
 
 cudaError_t launch_adj_sc(int storage, const PatchDev& p, const void* fin, const void* lam_new, void* lam_old,
-                          double beta, int odd, int lbgk, int* status, cudaStream_t st) {
+                          double beta, int odd, int lbgk, bool with_bc, int* status, cudaStream_t st) {
   return adj_dispatch(storage, [&](auto z) {
     using R = decltype(z);
     const long long n = (long long)p.dim[0] * p.dim[1] * p.dim[2];
@@ -586,7 +586,7 @@ cudaError_t launch_adj_sc(int storage, const PatchDev& p, const void* fin, const
     k_adj_sc<R, true><<<grid, block, 0, st>>>(p, (const R*)fin, (const R*)lam_new, (R*)lam_old, (R)beta, odd, lbgk,
                                               status);
     cudaError_t e = cudaGetLastError();
-    if (e) return e;
+    if (e || !with_bc) return e;
     k_adj_sc<R, false><<<grid, block, 0, st>>>(p, (const R*)fin, (const R*)lam_new, (R*)lam_old, (R)beta, odd,
                                                lbgk, status);
     return cudaGetLastError();

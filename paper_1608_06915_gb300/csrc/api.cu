@@ -240,11 +240,27 @@ lbm_status run_instant(lbm_grid* g, int k) {
         st = cuda_check(g,
                         timed(g, 0, lev, g->timing ? count_types(p, odd) : 0.0,
                               [&] {
-                                return lbmk::launch_th_tiles(storage, pv, fin, g->base + p.off_g[p.cur], fout,
-                                                             g->base + p.off_g[1 - p.cur],
-                                                             at<uint32_t>(g, p.off_tiles_all[odd]),
-                                                             (int64_t)p.tiles_all[odd].size(), (int)p.ntx,
-                                                             thermal_level(g, p), odd, status_ptr(g), g->stream);
+                                // TMA tile pass, then fix-up nodes and the node-by-node tiles
+                                const void* maps[6] = {p.tmap[p.cur], p.tmapo[1 - p.cur], p.tmapw[p.cur],
+                                                       p.tmapg[p.cur], p.tmapgo[1 - p.cur], p.tmapgw[p.cur]};
+                                const lbmk::ThermalLevel TL = thermal_level(g, p);
+                                void* gin = g->base + p.off_g[p.cur];
+                                void* gout = g->base + p.off_g[1 - p.cur];
+                                cudaError_t e = lbmk::launch_th_tma(storage, maps, pv,
+                                                                   at<unsigned long long>(g, p.off_tiles_pure[odd]),
+                                                                   (int64_t)p.tiles_pure[odd].size(), TL,
+                                                                   status_ptr(g), g->stream);
+                                if (!e)
+                                  e = lbmk::launch_th_nodes(storage, pv, fin, gin, fout, gout,
+                                                            at<uint32_t>(g, p.off_fix_nodes[odd]),
+                                                            (int64_t)p.fix_nodes[odd].size(), TL, status_ptr(g),
+                                                            g->stream);
+                                if (!e)
+                                  e = lbmk::launch_th_tiles(storage, pv, fin, gin, fout, gout,
+                                                            at<uint32_t>(g, p.off_tiles_mixed[odd]),
+                                                            (int64_t)p.tiles_mixed[odd].size(), (int)p.ntx, TL, odd,
+                                                            status_ptr(g), g->stream);
+                                return e;
                               }),
                         "thermal stream_collide");
       } else {
@@ -403,6 +419,7 @@ lbm_status lbm_grid_create(const lbm_desc* desc, lbm_grid_t* out) {
     for (uint8_t t : p.type) {
       p.n_bulk += (t == lbm::T_BULK || t == lbm::T_BC);
       p.n_d1 += (t == lbm::T_D1);
+      p.n_bc += (t == lbm::T_BC);
     }
   size_t off = lbm::plan_memory(hg);
   auto take = [&](size_t b) {
@@ -464,6 +481,11 @@ lbm_status lbm_grid_bind(lbm_grid_t g, void* dev_ptr, size_t bytes, void* cuda_s
       e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmap[k], g->base + p.off_f[k], view(g, p), 0);
       if (!e) e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmapo[k], g->base + p.off_f[k], view(g, p), 1);
       if (!e) e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmapw[k], g->base + p.off_f[k], view(g, p), 2);
+      if (g->hg.thermal) {
+        if (!e) e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmapg[k], g->base + p.off_g[k], view(g, p), 0);
+        if (!e) e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmapgo[k], g->base + p.off_g[k], view(g, p), 1);
+        if (!e) e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmapgw[k], g->base + p.off_g[k], view(g, p), 2);
+      }
     }
   if (!e) e = cudaMemsetAsync(g->base + g->off_status, 0, 64, s);
   if (!e) e = cudaStreamSynchronize(s);
@@ -844,7 +866,7 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
     const lbmk::PatchDev pv = view(g, p);
     if (!e)
       e = lbmk::launch_adj_sc(storage, pv, g->base + p.off_f[p.cur], lam_ptr(pi, lcur[pi]), lam_ptr(pi, 1 - lcur[pi]),
-                              p.beta, odd, lbgk, status_ptr(g), g->stream);
+                              p.beta, odd, lbgk, p.n_bc > 0, status_ptr(g), g->stream);
     for (int ci : p.kids) {
       HostPatch& c = hg.P[ci];
       if (!e)

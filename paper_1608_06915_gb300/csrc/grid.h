@@ -44,6 +44,7 @@ struct HostPatch {
   std::vector<uint8_t> type;  // [z][y][nxp]
   int64_t n_fluid = 0;
   double n_bulk = 0, n_d1 = 0;  // BULK+BC nodes and D1 nodes (written by stream_collide)
+  double n_bc = 0;              // BC nodes
 
   // stream-collide work lists: tiles of 128 nodes along x, id = (z*ny + y)*ntx + tx
   int64_t ntx = 0;
@@ -56,6 +57,9 @@ struct HostPatch {
   alignas(64) unsigned char tmap[2][128];   // TMA load descriptors of the two population buffers
   alignas(64) unsigned char tmapo[2][128];  // TMA store descriptors
   alignas(64) unsigned char tmapw[2][128];  // TMA 16-byte wrap descriptors
+  alignas(64) unsigned char tmapg[2][128];   // the same three for the thermal g buffers
+  alignas(64) unsigned char tmapgo[2][128];
+  alignas(64) unsigned char tmapgw[2][128];
 
   // interface toward the parent (level >= 1).  Reconstruction values live in
   // a point space [0, n_points()): samples, then stage-1 points (off-lattice

@@ -32,6 +32,13 @@ struct ThermalLevel {
 cudaError_t launch_th_tiles(int storage, const PatchDev& p, const void* fin, const void* gin, void* fout, void* gout,
                             const uint32_t* tiles, int64_t ntiles, int ntx, const ThermalLevel& L, int odd,
                             int* status, cudaStream_t st);
+// Thermal TMA tile pass of one patch; maps = {f load, f store, f wrap, g load,
+// g store, g wrap} descriptors (thermal_tma.cu).
+cudaError_t launch_th_tma(int storage, const void* const maps[6], const PatchDev& p,
+                          const unsigned long long* tiles, int64_t ntiles, const ThermalLevel& L, int* status,
+                          cudaStream_t st);
+cudaError_t launch_th_nodes(int storage, const PatchDev& p, const void* fin, const void* gin, void* fout, void* gout,
+                            const uint32_t* nodes, int64_t n, const ThermalLevel& L, int* status, cudaStream_t st);
 cudaError_t launch_th_coalesce(int storage, const PatchDev& child, const void* fin_c, const void* gin_c,
                                const PatchDev& parent, void* fo_p, void* go_p, const uint32_t* cf_parent,
                                const uint32_t* cf_child, int64_t n, double ff, double fg, const ThermalLevel& Lc,
@@ -49,8 +56,9 @@ cudaError_t launch_th_moments(int storage, const PatchDev& p, const void* fin, c
                               void* T, void* gamma, int dtype, const ThermalLevel& L, cudaStream_t st);
 
 // Discrete adjoint kernels (adjoint.cu), FP32/FP64 storage, isothermal.
+// with_bc: the patch has boundary-class nodes (their node-by-node kernel runs too)
 cudaError_t launch_adj_sc(int storage, const PatchDev& p, const void* fin, const void* lam_new, void* lam_old,
-                          double beta, int odd, int lbgk, int* status, cudaStream_t st);
+                          double beta, int odd, int lbgk, bool with_bc, int* status, cudaStream_t st);
 cudaError_t launch_adj_coalesce(int storage, const PatchDev& child, const void* fin_c, const PatchDev& parent,
                                 const void* lam_new_p, void* lam_old_c, const uint32_t* cf_parent,
                                 const uint32_t* cf_child, int64_t n, double r, double beta_p, int lbgk, int* status,
