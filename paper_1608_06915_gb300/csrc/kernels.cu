@@ -64,7 +64,7 @@ __device__ __forceinline__ void pull_any(const PatchDev& p, const S* __restrict_
 // ---------------------------------------------------------------------------
 // Fine -> coarse twin coupling: pre-collision child state at the coinciding
 // node, non-equilibrium scaled by r beta_f / beta_c, collided with beta_c.
-template <typename S, typename R, bool FORCE>
+template <typename S, typename R, int FM>
 __global__ void __launch_bounds__(128) k_coalesce(PatchDev pc, const S* __restrict__ fin_c, PatchDev pp,
                                                   S* __restrict__ fout_p, const uint32_t* __restrict__ cf_parent,
                                                   const uint32_t* __restrict__ cf_child, long long n, R rescale,
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(128) k_coalesce(PatchDev pc, const S* __restri
     constexpr int i = decltype(I)::value;
     f[i] = fe[i] + rescale * (f[i] - fe[i]);
   });
-  kbc_collide<R, FORCE ? 7 : 0>(f, beta_p, dux, duy, duz, lbgk != 0);
+  kbc_collide<R, FM>(f, beta_p, dux, duy, duz, lbgk != 0);
   store_node<S, R>(pp, fout_p, cf_parent[k], f);
 }
 
@@ -93,14 +93,16 @@ cudaError_t launch_coalesce(int storage, const PatchDev& child, const void* fin_
     using S = typename decltype(ts)::type;
     using R = typename decltype(tr)::type;
     dim3 block(128), grid((unsigned)((n + 127) / 128));
-    if (Fp.on())
-      k_coalesce<S, R, true><<<grid, block, 0, st>>>(child, (const S*)fin_child, parent, (S*)fout_parent, cf_parent,
-                                                      cf_child, n, (R)rescale, (R)beta_parent, (R)Fp.du[0],
-                                                      (R)Fp.du[1], (R)Fp.du[2], lbgk, status);
-    else
-      k_coalesce<S, R, false><<<grid, block, 0, st>>>(child, (const S*)fin_child, parent, (S*)fout_parent,
-                                                       cf_parent, cf_child, n, (R)rescale, (R)beta_parent, R(0),
-                                                       R(0), R(0), lbgk, status);
+    auto go = [&](auto kern) {
+      kern<<<grid, block, 0, st>>>(child, (const S*)fin_child, parent, (S*)fout_parent, cf_parent, cf_child, n,
+                                   (R)rescale, (R)beta_parent, (R)Fp.du[0], (R)Fp.du[1], (R)Fp.du[2], lbgk, status);
+    };
+    switch (Fp.mask()) {
+      case 0: go(k_coalesce<S, R, 0>); break;
+      case 1: go(k_coalesce<S, R, 1>); break;
+      case 4: go(k_coalesce<S, R, 4>); break;
+      default: go(k_coalesce<S, R, 7>);
+    }
     return cudaGetLastError();
   });
 }
@@ -211,7 +213,7 @@ cudaError_t launch_points(int storage, int ncomp, const uint32_t* pt_src, int64_
 // point itself), f = f^eq(rho~, u~) + neq~, then collide.  Targets
 // [0, n_one) read one point, the others interpolate four; a thread block
 // takes targets of one kind only.
-template <int K, typename S, typename R, bool FORCE>
+template <int K, typename S, typename R, int FM>
 __device__ __forceinline__ void explode_node(const PatchDev& pc, S* __restrict__ fout_c,
                                              const uint32_t* __restrict__ ex_node, const uint4* __restrict__ ex_src,
                                              long long k, const R* __restrict__ val, long long ld, R beta_c, R dux,
@@ -244,11 +246,11 @@ __device__ __forceinline__ void explode_node(const PatchDev& pc, S* __restrict__
     constexpr int i = decltype(I)::value;
     f[i] += fe[i];
   });
-  kbc_collide<R, FORCE ? 7 : 0>(f, beta_c, dux, duy, duz, lbgk != 0);
+  kbc_collide<R, FM>(f, beta_c, dux, duy, duz, lbgk != 0);
   store_node<S, R>(pc, fout_c, __ldg(ex_node + k), f);
 }
 
-template <typename S, typename R, bool FORCE>
+template <typename S, typename R, int FM>
 __global__ void __launch_bounds__(128) k_explode(PatchDev pc, S* __restrict__ fout_c,
                                                  const uint32_t* __restrict__ ex_node,
                                                  const uint4* __restrict__ ex_src, long long n_one, long long n,
@@ -256,10 +258,10 @@ __global__ void __launch_bounds__(128) k_explode(PatchDev pc, S* __restrict__ fo
                                                  R beta_c, R dux, R duy, R duz, int lbgk) {
   if (blockIdx.x < blocks_one) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n_one) explode_node<1, S, R, FORCE>(pc, fout_c, ex_node, ex_src, k, val, ld, beta_c, dux, duy, duz, lbgk);
+    if (k < n_one) explode_node<1, S, R, FM>(pc, fout_c, ex_node, ex_src, k, val, ld, beta_c, dux, duy, duz, lbgk);
   } else {
     const long long k = n_one + (long long)(blockIdx.x - blocks_one) * blockDim.x + threadIdx.x;
-    if (k < n) explode_node<4, S, R, FORCE>(pc, fout_c, ex_node, ex_src, k, val, ld, beta_c, dux, duy, duz, lbgk);
+    if (k < n) explode_node<4, S, R, FM>(pc, fout_c, ex_node, ex_src, k, val, ld, beta_c, dux, duy, duz, lbgk);
   }
 }
 
@@ -272,13 +274,16 @@ cudaError_t launch_explode(int storage, const PatchDev& child, void* fout_child,
     using S = typename decltype(ts)::type;
     using R = typename decltype(tr)::type;
     dim3 block(128), grid(b1 + b4);
-    if (Fc.on())
-      k_explode<S, R, true><<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, (const uint4*)ex_src, n_one, n,
-                                                     b1, (const R*)val, ld, (R)beta_child, (R)Fc.du[0], (R)Fc.du[1],
-                                                     (R)Fc.du[2], lbgk);
-    else
-      k_explode<S, R, false><<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, (const uint4*)ex_src, n_one, n,
-                                                      b1, (const R*)val, ld, (R)beta_child, R(0), R(0), R(0), lbgk);
+    auto go = [&](auto kern) {
+      kern<<<grid, block, 0, st>>>(child, (S*)fout_child, ex_node, (const uint4*)ex_src, n_one, n, b1, (const R*)val,
+                                   ld, (R)beta_child, (R)Fc.du[0], (R)Fc.du[1], (R)Fc.du[2], lbgk);
+    };
+    switch (Fc.mask()) {
+      case 0: go(k_explode<S, R, 0>); break;
+      case 1: go(k_explode<S, R, 1>); break;
+      case 4: go(k_explode<S, R, 4>); break;
+      default: go(k_explode<S, R, 7>);
+    }
     return cudaGetLastError();
   });
 }
