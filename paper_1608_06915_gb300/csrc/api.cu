@@ -246,7 +246,7 @@ lbm_status run_instant(lbm_grid* g, int k) {
                                 const lbmk::ThermalLevel TL = thermal_level(g, p);
                                 void* gin = g->base + p.off_g[p.cur];
                                 void* gout = g->base + p.off_g[1 - p.cur];
-                                cudaError_t e = lbmk::launch_th_tma(storage, maps, pv,
+                                cudaError_t e = lbmk::launch_th_tma(storage, maps, pv, fin,
                                                                    at<unsigned long long>(g, p.off_tiles_pure[odd]),
                                                                    (int64_t)p.tiles_pure[odd].size(), TL,
                                                                    status_ptr(g), g->stream);

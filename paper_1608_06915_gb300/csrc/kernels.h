@@ -34,7 +34,7 @@ cudaError_t launch_th_tiles(int storage, const PatchDev& p, const void* fin, con
                             int* status, cudaStream_t st);
 // Thermal TMA tile pass of one patch; maps = {f load, f store, f wrap, g load,
 // g store, g wrap} descriptors (thermal_tma.cu).
-cudaError_t launch_th_tma(int storage, const void* const maps[6], const PatchDev& p,
+cudaError_t launch_th_tma(int storage, const void* const maps[6], const PatchDev& p, const void* fin,
                           const unsigned long long* tiles, int64_t ntiles, const ThermalLevel& L, int* status,
                           cudaStream_t st);
 cudaError_t launch_th_nodes(int storage, const PatchDev& p, const void* fin, const void* gin, void* fout, void* gout,

@@ -489,9 +489,8 @@ std::string build_layout(HostGrid& g) {
             if (active[k] == 0) continue;
             R.all[k].push_back(id);
             const int nodd = (int)odd_nodes[k].size();
-            // the thermal tile pass has no wall, inlet or outlet rule (its g walls
-            // need the node's own density): such tiles go node by node
-            const bool rule_ok = !g.thermal || (bm == 0 && !inlet && !outlet);
+            // the thermal tile pass has no inlet or outlet rule: such tiles go node by node
+            const bool rule_ok = !g.thermal || (!inlet && !outlet);
             if (wrap_ok && rule_ok && 2 * nodd <= active[k]) {
               const uint64_t fl = (inlet ? 1ull : 0ull) | (outlet ? 2ull : 0ull);
               R.pure[k].push_back((uint64_t)tx | ((uint64_t)y << 16) | ((uint64_t)z << 32) | ((uint64_t)bm << 48) |

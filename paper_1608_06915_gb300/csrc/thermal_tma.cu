@@ -8,10 +8,14 @@
 // release the stage, run the thermal collision (f: KBC with the Boussinesq
 // force; g: relaxation to the Grad equilibrium with the Pr <= 1
 // quasi-equilibrium), and store their 27 x 32 segments of f and g with one TMA
-// store each.  Tiles next to a wall, inlet or outlet stay on the node-by-node
-// kernel (their g walls need the node's own density); as in the isothermal
-// pass, nodes not updated in the substep are overwritten and rewritten by
-// explode and coalesce later in the instant.  Waits are bounded as there.
+// store each.  Walls across y or z follow the row rule of the isothermal pass
+// (bit j of the tile's bounce mask: source row j lies beyond a wall): f
+// bounces back, g takes the anti-bounce-back to the wall equilibrium at rest,
+// g_i = -g'_-i + 2 W_i (3 rho T_w + rho~ c_i^2) in deviation form, with the
+// density of the node's own state read from global memory.  Tiles with inlet
+// or outlet nodes stay on the node-by-node kernel; as in the isothermal pass,
+// nodes not updated in the substep are overwritten and rewritten by explode
+// and coalesce later in the instant.  Waits are bounded as there.
 #include "sc_tma.cuh"
 #include "thermal.cuh"
 
@@ -36,6 +40,7 @@ struct ThMaps {
 
 template <typename R>
 __global__ void __launch_bounds__(160) k_th_tma(const __grid_constant__ ThMaps<R> m, PatchDev p,
+                                                const R* __restrict__ fin,
                                                 const unsigned long long* __restrict__ tiles, int ntiles,
                                                 ThParams<R> tp, int* status) {
   using T = ThTmaCfg<R>;
@@ -66,11 +71,14 @@ __global__ void __launch_bounds__(160) k_th_tma(const __grid_constant__ ThMaps<R
         return;
       }
       int tx, ty, tz;
-      tile_xyz(tiles[blockIdx.x + (size_t)k * gridDim.x], tx, ty, tz);
+      const unsigned long long te = tiles[blockIdx.x + (size_t)k * gridDim.x];
+      tile_xyz(te, tx, ty, tz);
+      const int bm = tile_bounce(te);
       const bool first = p.span[0] && tx == 0;
       const bool last = p.span[0] && (tx + 1) * C::BX >= p.dim[0];
-      tile_at[s] = make_int4(tx, ty, tz, 0);
-      mbar_expect_tx(&full[s], T::TX + (first ? 2u * C::TXW : 0u) + (last ? 2u * C::TXW : 0u));
+      tile_at[s] = make_int4(tx, ty, tz, bm);
+      const uint32_t txw = 2u * 16u * (uint32_t)(9 - __popc(bm));  // wrap boxes of the rows not bounced
+      mbar_expect_tx(&full[s], T::TX + (first ? txw : 0u) + (last ? txw : 0u));
       unsigned char* stage = smem + s * T::STAGE;
       const int x0 = tx * C::BX - C::H;
 #pragma unroll 1
@@ -81,6 +89,11 @@ __global__ void __launch_bounds__(160) k_th_tma(const __grid_constant__ ThMaps<R
         const CUtensorMap* wr = set ? &m.g_wrap : &m.f_wrap;
 #pragma unroll 1
         for (int j = 0; j < 9; ++j) {
+          if ((bm >> j) & 1) {
+            // beyond a wall: the opposite populations of the tile's own row
+            tma_load_row(half + j * C::GROUP, in, &full[s], x0, ty, tz, 3 * (8 - j));
+            continue;
+          }
           const int sy = wrap_axis(ty - (j % 3 - 1), p.dim[1]);
           const int sz = wrap_axis(tz - (j / 3 - 1), p.dim[2]);
           tma_load_row(half + j * C::GROUP, in, &full[s], x0, sy, sz, 3 * j);
@@ -103,27 +116,57 @@ __global__ void __launch_bounds__(160) k_th_tma(const __grid_constant__ ThMaps<R
       return;
     }
     const int4 tc = tile_at[s];
-    const int tx = tc.x, y = tc.y, z = tc.z;
+    const int tx = tc.x, y = tc.y, z = tc.z, bm = tc.w;
     const int x = tx * C::BX + tid;
     const R* stf = reinterpret_cast<const R*>(smem + s * T::STAGE);
     const R* stg = reinterpret_cast<const R*>(smem + s * T::STAGE + T::HALF);
     R f[27], g[27];
-    unroll<27>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      f[i] = stf[row_base<R>(i) + C::H + tid - CX(i)];
-      g[i] = stg[row_base<R>(i) + C::H + tid - CX(i)];
-    });
+    if (bm == 0) {
+      unroll<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        f[i] = stf[row_base<R>(i) + C::H + tid - CX(i)];
+        g[i] = stg[row_base<R>(i) + C::H + tid - CX(i)];
+      });
+    } else {
+      // wall rows: density of the node's own post-collision state
+      R rho_own_t = 0;
+      if (x < p.dim[0]) {
+        const long long own = node_index(p, x, y, z);
+        unroll<27>([&](auto I) { rho_own_t += fin[(long long)decltype(I)::value * p.plane + own]; });
+      }
+      unroll<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int j = i / 3;
+        if ((bm >> j) & 1) {
+          const int ob = row_base<R>(3 * j + 2 - i % 3) + C::H + tid;
+          f[i] = stf[ob];
+          // wall face: z wins over y where both lie beyond walls
+          const int sy = p.org[1] + y - CY(i), sz = p.org[2] + z - CZ(i);
+          int face = -1;
+          if (sy < 0) face = 2;
+          else if (sy > p.maxc[1]) face = 3;
+          if (sz < 0) face = 4;
+          else if (sz > p.maxc[2]) face = 5;
+          const R tw = face >= 0 ? tp.twd[face] : R(0);
+          g[i] = -stg[ob] + R(2 * WI(i)) * (R(3) * (R(1) + rho_own_t) * tw + rho_own_t * R(C2<i>()));
+        } else {
+          f[i] = stf[row_base<R>(i) + C::H + tid - CX(i)];
+          g[i] = stg[row_base<R>(i) + C::H + tid - CX(i)];
+        }
+      });
+    }
     if (p.span[0] && (x == 0 || x == p.dim[0] - 1)) {
       const R* sf = stf + 9 * C::GROUP / (int)sizeof(R);
       const R* sg = stg + 9 * C::GROUP / (int)sizeof(R);
       const bool lo = x == 0;
       unroll<27>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        if (lo && CX(i) == 1) {
+        const bool b = (bm >> (i / 3)) & 1;
+        if (!b && lo && CX(i) == 1) {
           f[i] = sf[(i / 3) * (C::SIDE / (int)sizeof(R)) + C::H - 1];
           g[i] = sg[(i / 3) * (C::SIDE / (int)sizeof(R)) + C::H - 1];
         }
-        if (!lo && CX(i) == -1) {
+        if (!b && !lo && CX(i) == -1) {
           f[i] = sf[(9 + i / 3) * (C::SIDE / (int)sizeof(R))];
           g[i] = sg[(9 + i / 3) * (C::SIDE / (int)sizeof(R))];
         }
@@ -169,7 +212,7 @@ __global__ void __launch_bounds__(128) k_th_nodes(PatchDev p, const R* __restric
   store2(p, fout, gout, own, f, g);
 }
 
-cudaError_t launch_th_tma(int storage, const void* const maps[6], const PatchDev& p,
+cudaError_t launch_th_tma(int storage, const void* const maps[6], const PatchDev& p, const void* fin,
                           const unsigned long long* tiles, int64_t ntiles, const ThermalLevel& L, int* status,
                           cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;
@@ -196,7 +239,7 @@ cudaError_t launch_th_tma(int storage, const void* const maps[6], const PatchDev
     memcpy(&m.g_out, maps[4], sizeof(CUtensorMap));
     memcpy(&m.g_wrap, maps[5], sizeof(CUtensorMap));
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)blocks_per_sm * sms);
-    kern<<<grid, T::THREADS, T::SMEM, st>>>(m, p, tiles, (int)ntiles, th_params<R>(L), status);
+    kern<<<grid, T::THREADS, T::SMEM, st>>>(m, p, (const R*)fin, tiles, (int)ntiles, th_params<R>(L), status);
     return cudaGetLastError();
   });
 }
