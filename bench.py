@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="only the adjoint/forward timing of the 64^3 adjoint case (diagnostic line)")
     return ap.parse_args()
 
 
@@ -438,6 +440,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.adjoint_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(dict(adjoint_forward_ratio=adjoint_ratio(torch.device("cuda", 0)))), flush=True)
+        return 0
     return cuda_arm(args)
 
 

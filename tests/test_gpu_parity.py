@@ -382,3 +382,23 @@ def test_autotune_reports_and_keeps_the_state_consistent():
     assert r["chosen"] in range(len(r["ms_per_step"])) and all(t > 0 for t in r["ms_per_step"])
     o.step(len(r["ms_per_step"]))
     assert pop_diff(ga, o) < 1e-12
+
+
+def test_more_patches_than_one_tma_batch_fp64():
+    """Ten level-1 boxes side by side: the TMA pass of an instant splits into
+    batches of eight patches; populations against the oracle every step."""
+    boxes = [(1, (4 + 18 * k, 8, 8), (12 + 18 * k, 16, 16)) for k in range(10)]
+    case = dict(I.tgv_case(n=32), name="many", n=(180, 24, 24), boxes=boxes)
+    g, o = twin(case, "fp64", lambda x, y, z, p, info: I.uniform_fields(x, (0.04, 0.01, -0.02)))
+    assert len(g.patches) == 11
+    rng = np.random.default_rng(5)
+    for p, info in enumerate(g.patches):
+        f = o.get_pop(p)
+        f *= 1.0 + 0.01 * rng.standard_normal(f.shape)
+        o.set_pop(p, f)
+        import torch
+        g.set_populations(p, torch.from_numpy(f).cuda())
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
+        assert pop_diff(g, o) < 1e-12
