@@ -403,7 +403,7 @@ def cuda_arm(args):
         e2e = end_to_end(args, g, L, host_fields, dfields, nup, world, barrier, dev)
 
     adj = None
-    if not args.no_adjoint and args.workload == "channel":
+    if rank == 0 and not args.no_adjoint and args.workload == "channel":
         adj = adjoint_ratio(dev)
 
     cpu = None
