@@ -34,10 +34,12 @@ template <typename R>
 __device__ __forceinline__ void axis_logderiv(R u, const AxisEq<R>& e, R (&L)[3]) {
   const R s = e.s;
   const R A = R(1) + e.d[1];
-  const R dA = -R(3) * u / s;
+  const R u_s = R(3) * u * rcp_fast(s);  // 3u / s
+  const R dA = -u_s;
   const R om = R(1) - u;
-  const R dB = ((R(2) + R(3) * u / s) * om + R(2) * u + s) / (om * om);
-  const R la = dA / A, lb = dB / e.B;
+  const R iom = rcp_fast(om);
+  const R dB = ((R(2) + u_s) * om + R(2) * u + s) * (iom * iom);
+  const R la = dA * rcp_fast(A), lb = dB * rcp_fast(e.B);
   L[1] = la;
   L[2] = la + lb;
   L[0] = la - lb;
@@ -57,7 +59,7 @@ __device__ __forceinline__ void feq_vjp_rho_u(const R (&xbar)[27], const R (&fef
     sy[CY(i) + 1] += q;
     sz[CZ(i) + 1] += q;
   });
-  rhobar = tot / rho;
+  rhobar = tot * rcp_fast(rho);
   ubar[0] = sx[0] * Lx[0] + sx[1] * Lx[1] + sx[2] * Lx[2];
   ubar[1] = sy[0] * Ly[0] + sy[1] * Ly[1] + sy[2] * Ly[2];
   ubar[2] = sz[0] * Lz[0] + sz[1] * Lz[1] + sz[2] * Lz[2];
@@ -96,7 +98,7 @@ __device__ __forceinline__ void add_feq_f_vjp(const EqState<R>& q, const R (&xba
   R rb, ub[3];
   feq_vjp_rho_u<R>(xbar, q.fefull, q.rho, q.L[0], q.L[1], q.L[2], rb, ub);
   // u = j / rho: jbar = ubar / rho, rhobar -= ubar . u / rho
-  const R ir = R(1) / q.rho;
+  const R ir = rcp_fast(q.rho);
   const R jb[3] = {ub[0] * ir, ub[1] * ir, ub[2] * ir};
   rb -= (ub[0] * q.u[0] + ub[1] * q.u[1] + ub[2] * q.u[2]) * ir;
   unroll<27>([&](auto I) {
@@ -223,11 +225,11 @@ __device__ void kbc_vjp(const R (&f)[27], R (&lam)[27], R beta, bool lbgk) {
   });
   // f^eq(rho, u): rho-bar = sum feb fe / rho, u-bar_a = sum feb fe L_a; then
   // through rho = sum f and u = j / rho
-  R rb = tot / q.rho;
+  R rb = tot * rcp_fast(q.rho);
   const R ub[3] = {sx[0] * q.L[0][0] + sx[1] * q.L[0][1] + sx[2] * q.L[0][2],
                    sy[0] * q.L[1][0] + sy[1] * q.L[1][1] + sy[2] * q.L[1][2],
                    sz[0] * q.L[2][0] + sz[1] * q.L[2][1] + sz[2] * q.L[2][2]};
-  const R ir = R(1) / q.rho;
+  const R ir = rcp_fast(q.rho);
   const R jb[3] = {ub[0] * ir, ub[1] * ir, ub[2] * ir};
   rb -= (ub[0] * q.u[0] + ub[1] * q.u[1] + ub[2] * q.u[2]) * ir;
   unroll<27>([&](auto I) {
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(128) k_adj_samples(PatchDev pp, const R* __res
   });
   add_feq_f_vjp<R>(e, xb, fb);
   // rho~ = sum f, u = j / rho
-  const R ir = R(1) / rho;
+  const R ir = rcp_fast(rho);
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
     fb[i] += rb + ((R(CX(i)) - ux) * ub[0] + (R(CY(i)) - uy) * ub[1] + (R(CZ(i)) - uz) * ub[2]) * ir;
