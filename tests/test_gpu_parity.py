@@ -402,3 +402,92 @@ def test_more_patches_than_one_tma_batch_fp64():
         g.step(1)
         o.step(1)
         assert pop_diff(g, o) < 1e-12
+
+
+def _gather_pull(f0, xs, ys, zs, xsrc_fn):
+    """Pre-collision populations of the sampled nodes from a device array
+    [27][nz][ny][nx]: f_i = f0_i at (xsrc(x, c_x), y - c_y, z - c_z), periodic in y, z."""
+    import torch
+    nz, ny, nx = f0.shape[1:]
+    out = np.empty((27, len(xs)))
+    for i in range(27):
+        sx = torch.tensor([xsrc_fn(x, C[i, 0]) for x in xs], device=f0.device)
+        sy = torch.tensor([(y - C[i, 1]) % ny for y in ys], device=f0.device)
+        sz = torch.tensor([(z - C[i, 2]) % nz for z in zs], device=f0.device)
+        out[i] = f0[i, sz, sy, sx].double().cpu().numpy()
+    return out
+
+
+def _at(f, xs, ys, zs):
+    import torch
+    dev = f.device
+    return f[:, torch.tensor(zs, device=dev), torch.tensor(ys, device=dev), torch.tensor(xs, device=dev)].double().cpu().numpy()
+
+
+def test_sphere_full_size_sampled_level0_nodes():
+    """One coarse step of the full 384x192x192 sphere case (FP32, noisy
+    inflow field): level-0 bulk nodes recomputed one by one by the oracle's
+    collision from the GPU's pre-step state; outlet nodes pull their c_x = -1
+    populations from themselves; inlet nodes keep their populations."""
+    import torch
+    case = I.sphere_case()
+
+    def fields(x, y, z, p, info):
+        rng = np.random.default_rng(100 + p)
+        rho = 1.0 + 0.01 * rng.standard_normal(np.shape(x))
+        u = np.stack([0.05 + 0.01 * rng.standard_normal(np.shape(x)), 0.01 * rng.standard_normal(np.shape(x)),
+                      0.01 * rng.standard_normal(np.shape(x))])
+        return rho, u
+    g, _ = twin(case, "fp32", fields, oracle=False)
+    f0 = g.get_populations(0, dtype=torch.float32)
+    g.step(1)
+    f1 = g.get_populations(0, dtype=torch.float32)
+    beta = g.patches[0]["beta"]
+    nz, ny, nx = f0.shape[1:]
+    rng = np.random.default_rng(31)
+    n = 150
+    ys, zs = rng.integers(0, ny, n).tolist(), rng.integers(0, nz, n).tolist()
+    # bulk, away from the refined box (coarse x in [80, 160]) and the boundaries
+    xs = rng.integers(2, 70, n).tolist()
+    pre = _gather_pull(f0, xs, ys, zs, lambda x, c: x - c)
+    post = _at(f1, xs, ys, zs)
+    worst = max(float(np.max(np.abs(post[:, k] - O.collide(pre[:, k], beta)[0]))) for k in range(n))
+    assert worst < 2e-6, worst
+    # outlet: zero gradient along x
+    xo = [nx - 1] * n
+    pre = _gather_pull(f0, xo, ys, zs, lambda x, c: x if c == -1 else x - c)
+    post = _at(f1, xo, ys, zs)
+    worst = max(float(np.max(np.abs(post[:, k] - O.collide(pre[:, k], beta)[0]))) for k in range(n))
+    assert worst < 2e-6, worst
+    # inlet: fixed
+    xi = [0] * n
+    assert np.array_equal(_at(f1, xi, ys, zs), _at(f0, xi, ys, zs))
+
+
+def test_rbc_full_size_sampled_level0_nodes():
+    """One coarse step of the full 256x256x128 Rayleigh-Benard case (FP32):
+    level-0 nodes of the bulk recomputed one by one by the oracle's thermal
+    collision (f and g) from the GPU's pre-step state."""
+    import torch
+    case = I.rbc_case()
+    g, _ = twin(case, "fp32", _rbc(case), oracle=False)
+    f0, g0 = g.get_populations(0, 0, dtype=torch.float32), g.get_populations(0, 1, dtype=torch.float32)
+    g.step(1)
+    f1, g1 = g.get_populations(0, 0, dtype=torch.float32), g.get_populations(0, 1, dtype=torch.float32)
+    info = g.patches[0]
+    th = case["thermal"]
+    nz, ny, nx = f0.shape[1:]
+    rng = np.random.default_rng(37)
+    n = 150
+    xs, ys = rng.integers(0, nx, n).tolist(), rng.integers(0, ny, n).tolist()
+    zs = rng.integers(nz // 2 - 30, nz // 2 + 30, n).tolist()  # far from the refined plate layers
+    pf = _gather_pull(f0, xs, ys, zs, lambda x, c: (x - c) % nx)
+    pg = _gather_pull(g0, xs, ys, zs, lambda x, c: (x - c) % nx)
+    qf, qg = _at(f1, xs, ys, zs), _at(g1, xs, ys, zs)
+    wf = wg = 0.0
+    for k in range(n):
+        rf, rg, _ = O.thermal_collide(pf[:, k], pg[:, k], info["beta"], info["beta1"], th["t0"], th["glambda"],
+                                      th["t_ref"])
+        wf, wg = max(wf, float(np.max(np.abs(qf[:, k] - rf)))), max(wg, float(np.max(np.abs(qg[:, k] - rg))))
+    print("rbc full size: max |df| %.2e |dg| %.2e" % (wf, wg))
+    assert wf < 2e-6 and wg < 5e-6, (wf, wg)
