@@ -69,7 +69,13 @@ struct lbm_grid {
   // stream-collide adjoint (their writes are reductions that commute)
   cudaStream_t adj_side[2] = {nullptr, nullptr};
   cudaEvent_t adj_fork = nullptr, adj_join[2] = {nullptr, nullptr};
+  // side stream of the forward step: node-by-node remainders beside the coupling
+  cudaStream_t fwd_side = nullptr;
+  cudaEvent_t fwd_fork = nullptr, fwd_join = nullptr;
   ~lbm_grid() {
+    if (fwd_side) cudaStreamDestroy(fwd_side);
+    if (fwd_fork) cudaEventDestroy(fwd_fork);
+    if (fwd_join) cudaEventDestroy(fwd_join);
     for (auto& x : adj_side)
       if (x) cudaStreamDestroy(x);
     if (adj_fork) cudaEventDestroy(adj_fork);
@@ -221,6 +227,34 @@ lbm_status run_instant(lbm_grid* g, int k) {
         return st;
     }
   }
+  // The node-by-node remainder of the stream-collide (fix-up nodes, mixed
+  // tiles) writes updated nodes only; coalesce and explode write interface
+  // nodes, which are never updated in the same substep, and read the previous
+  // state.  So the remainder runs on a side stream beside the coupling, joined
+  // before the instant ends (not under per-launch timing).
+  cudaStream_t rest = g->stream;
+  bool forked = false;
+  if (!hg.thermal && !g->timing) {
+    bool work = false;
+    for (int lev = 0; lev < L && !work; ++lev) {
+      const int stride = 1 << (L - 1 - lev);
+      if (k % stride) continue;
+      const int odd = (lev > 0 && (k / stride) % 2) ? 1 : 0;
+      for (auto& p : hg.P)
+        if (p.level == lev && (!p.fix_nodes[odd].empty() || !p.tiles_mixed[odd].empty())) work = true;
+    }
+    if (work) {
+      cudaError_t e = cudaSuccess;
+      if (!g->fwd_side) e = cudaStreamCreateWithFlags(&g->fwd_side, cudaStreamNonBlocking);
+      if (!e && !g->fwd_fork) e = cudaEventCreateWithFlags(&g->fwd_fork, cudaEventDisableTiming);
+      if (!e && !g->fwd_join) e = cudaEventCreateWithFlags(&g->fwd_join, cudaEventDisableTiming);
+      if (!e) e = cudaEventRecord(g->fwd_fork, g->stream);
+      if (!e) e = cudaStreamWaitEvent(g->fwd_side, g->fwd_fork, 0);
+      if (e) return cuda_check(g, e, "forward side stream");
+      rest = g->fwd_side;
+      forked = true;
+    }
+  }
   for (int lev = 0; lev < L; ++lev) {
     const int stride = 1 << (L - 1 - lev);
     if (k % stride) continue;
@@ -271,11 +305,11 @@ lbm_status run_instant(lbm_grid* g, int k) {
                   [&] {
                     cudaError_t e = lbmk::launch_sc_nodes(storage, pv, fin, fout, at<uint32_t>(g, p.off_fix_nodes[odd]),
                                               (int64_t)p.fix_nodes[odd].size(), p.beta, F, lbgk, status_ptr(g),
-                                              g->stream);
+                                              rest);
                     if (e) return e;
                     return lbmk::launch_sc_tiles(storage, pv, fin, fout, at<uint32_t>(g, p.off_tiles_mixed[odd]),
                                                  (int64_t)p.tiles_mixed[odd].size(), (int)p.ntx, p.beta, F, odd,
-                                                 lbgk, status_ptr(g), g->stream);
+                                                 lbgk, status_ptr(g), rest);
                   }),
             "stream_collide");
       }
@@ -365,6 +399,11 @@ lbm_status run_instant(lbm_grid* g, int k) {
         if (st) return st;
       }
     }
+  }
+  if (forked) {
+    cudaError_t e = cudaEventRecord(g->fwd_join, g->fwd_side);
+    if (!e) e = cudaStreamWaitEvent(g->stream, g->fwd_join, 0);
+    if (e) return cuda_check(g, e, "forward side stream join");
   }
   for (int pi : active) hg.P[pi].cur ^= 1;
   return LBM_OK;
