@@ -69,13 +69,16 @@ struct lbm_grid {
   // stream-collide adjoint (their writes are reductions that commute)
   cudaStream_t adj_side[2] = {nullptr, nullptr};
   cudaEvent_t adj_fork = nullptr, adj_join[2] = {nullptr, nullptr};
-  // side stream of the forward step: node-by-node remainders beside the coupling
-  cudaStream_t fwd_side = nullptr;
-  cudaEvent_t fwd_fork = nullptr, fwd_join = nullptr;
+  // side streams of the forward step: [0] node-by-node remainders, [1], [2]
+  // coupling chains, all beside each other after the TMA pass of an instant
+  cudaStream_t fwd_side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fwd_fork = nullptr, fwd_join[3] = {nullptr, nullptr, nullptr};
   ~lbm_grid() {
-    if (fwd_side) cudaStreamDestroy(fwd_side);
+    for (auto& x : fwd_side)
+      if (x) cudaStreamDestroy(x);
     if (fwd_fork) cudaEventDestroy(fwd_fork);
-    if (fwd_join) cudaEventDestroy(fwd_join);
+    for (auto& x : fwd_join)
+      if (x) cudaEventDestroy(x);
     for (auto& x : adj_side)
       if (x) cudaStreamDestroy(x);
     if (adj_fork) cudaEventDestroy(adj_fork);
@@ -227,33 +230,30 @@ lbm_status run_instant(lbm_grid* g, int k) {
         return st;
     }
   }
-  // The node-by-node remainder of the stream-collide (fix-up nodes, mixed
-  // tiles) writes updated nodes only; coalesce and explode write interface
-  // nodes, which are never updated in the same substep, and read the previous
-  // state.  So the remainder runs on a side stream beside the coupling, joined
-  // before the instant ends (not under per-launch timing).
-  cudaStream_t rest = g->stream;
-  bool forked = false;
-  if (!hg.thermal && !g->timing) {
-    bool work = false;
-    for (int lev = 0; lev < L && !work; ++lev) {
-      const int stride = 1 << (L - 1 - lev);
-      if (k % stride) continue;
-      const int odd = (lev > 0 && (k / stride) % 2) ? 1 : 0;
-      for (auto& p : hg.P)
-        if (p.level == lev && (!p.fix_nodes[odd].empty() || !p.tiles_mixed[odd].empty())) work = true;
-    }
-    if (work) {
-      cudaError_t e = cudaSuccess;
-      if (!g->fwd_side) e = cudaStreamCreateWithFlags(&g->fwd_side, cudaStreamNonBlocking);
-      if (!e && !g->fwd_fork) e = cudaEventCreateWithFlags(&g->fwd_fork, cudaEventDisableTiming);
-      if (!e && !g->fwd_join) e = cudaEventCreateWithFlags(&g->fwd_join, cudaEventDisableTiming);
-      if (!e) e = cudaEventRecord(g->fwd_fork, g->stream);
-      if (!e) e = cudaStreamWaitEvent(g->fwd_side, g->fwd_fork, 0);
-      if (e) return cuda_check(g, e, "forward side stream");
-      rest = g->fwd_side;
-      forked = true;
-    }
+  // After the TMA pass the rest of the instant splits into independent chains:
+  // the node-by-node remainder of the stream-collide (fix-up nodes, mixed
+  // tiles) writes updated nodes only; each coalesce writes its parent's twin
+  // nodes and each explode chain its child's interface nodes, which are never
+  // updated in the same substep; all of them read the previous state.  So they
+  // run on side streams beside each other, joined before the instant ends
+  // (not under per-launch timing).
+  cudaStream_t rest = g->stream, cpl[2] = {g->stream, g->stream};
+  // (the thermal model steps its patches inside the loop below, so it keeps
+  // everything on the bound stream)
+  const bool forked = !g->timing && !hg.thermal;
+  if (forked) {
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 3 && !e; ++q)
+      if (!g->fwd_side[q]) e = cudaStreamCreateWithFlags(&g->fwd_side[q], cudaStreamNonBlocking);
+    if (!e && !g->fwd_fork) e = cudaEventCreateWithFlags(&g->fwd_fork, cudaEventDisableTiming);
+    for (int q = 0; q < 3 && !e; ++q)
+      if (!g->fwd_join[q]) e = cudaEventCreateWithFlags(&g->fwd_join[q], cudaEventDisableTiming);
+    if (!e) e = cudaEventRecord(g->fwd_fork, g->stream);
+    for (int q = 0; q < 3 && !e; ++q) e = cudaStreamWaitEvent(g->fwd_side[q], g->fwd_fork, 0);
+    if (e) return cuda_check(g, e, "forward side streams");
+    rest = g->fwd_side[0];
+    cpl[0] = g->fwd_side[1];
+    cpl[1] = g->fwd_side[2];
   }
   for (int lev = 0; lev < L; ++lev) {
     const int stride = 1 << (L - 1 - lev);
@@ -326,7 +326,7 @@ lbm_status run_instant(lbm_grid* g, int k) {
                                       g->base + p.off_g[1 - p.cur], at<uint32_t>(g, c.off_cf_parent),
                                       at<uint32_t>(g, c.off_cf_child), (int64_t)c.cf_parent.size(),
                                       2.0 * c.beta / p.beta, 2.0 * c.beta1 / p.beta1, thermal_level(g, c),
-                                      thermal_level(g, p), status_ptr(g), g->stream);
+                                      thermal_level(g, p), status_ptr(g), cpl[(pi + 1) % 2]);
                                 }),
                           "thermal coalesce");
           if (st) return st;
@@ -339,7 +339,7 @@ lbm_status run_instant(lbm_grid* g, int k) {
                                                              at<uint32_t>(g, c.off_cf_parent),
                                                              at<uint32_t>(g, c.off_cf_child),
                                                              (int64_t)c.cf_parent.size(), 2.0 * c.beta / p.beta,
-                                                             p.beta, F, lbgk, status_ptr(g), g->stream);
+                                                             p.beta, F, lbgk, status_ptr(g), cpl[(pi + 1) % 2]);
                               }),
                         "coalesce");
         if (st) return st;
@@ -356,8 +356,8 @@ lbm_status run_instant(lbm_grid* g, int k) {
                                     at<uint8_t>(g, p.off_smp_kind), (int64_t)p.smp_node.size(),
                                     g->base + p.off_smp_val, (int64_t)p.n_points(), q.beta / (2.0 * p.beta),
                                     q.beta1 / (2.0 * p.beta1), thermal_level(g, q), thermal_level(g, p),
-                                    status_ptr(g), g->stream);
-                                return e ? e : point_passes(g, p, 59, g->stream);
+                                    status_ptr(g), cpl[pi % 2]);
+                                return e ? e : point_passes(g, p, 59, cpl[pi % 2]);
                               }),
                         "thermal samples");
         if (st) return st;
@@ -368,7 +368,7 @@ lbm_status run_instant(lbm_grid* g, int k) {
                                     storage, pv, fout, g->base + p.off_g[1 - p.cur], at<uint32_t>(g, p.off_ex_node),
                                     at<uint32_t>(g, p.off_ex_src), (int64_t)p.ex_one, (int64_t)p.ex_node.size(),
                                     g->base + p.off_smp_val, (int64_t)p.n_points(), thermal_level(g, p),
-                                    g->stream);
+                                    cpl[pi % 2]);
                               }),
                         "thermal explode");
         if (st) return st;
@@ -382,8 +382,8 @@ lbm_status run_instant(lbm_grid* g, int k) {
                                     storage, qv, g->base + q.off_f[q.cur], pv, fin, at<uint32_t>(g, p.off_smp_node),
                                     at<uint8_t>(g, p.off_smp_kind), (int64_t)p.smp_node.size(),
                                     g->base + p.off_smp_val, (int64_t)p.n_points(), q.beta / (2.0 * p.beta),
-                                    status_ptr(g), g->stream);
-                                return e ? e : point_passes(g, p, 31, g->stream);
+                                    status_ptr(g), cpl[pi % 2]);
+                                return e ? e : point_passes(g, p, 31, cpl[pi % 2]);
                               }),
                         "samples");
         if (st) return st;
@@ -393,7 +393,7 @@ lbm_status run_instant(lbm_grid* g, int k) {
                                 return lbmk::launch_explode(storage, pv, fout, at<uint32_t>(g, p.off_ex_node),
                                                             at<uint32_t>(g, p.off_ex_src), (int64_t)p.ex_one,
                                                             (int64_t)p.ex_node.size(), g->base + p.off_smp_val,
-                                                            (int64_t)p.n_points(), p.beta, F, lbgk, g->stream);
+                                                            (int64_t)p.n_points(), p.beta, F, lbgk, cpl[pi % 2]);
                               }),
                         "explode");
         if (st) return st;
@@ -401,8 +401,11 @@ lbm_status run_instant(lbm_grid* g, int k) {
     }
   }
   if (forked) {
-    cudaError_t e = cudaEventRecord(g->fwd_join, g->fwd_side);
-    if (!e) e = cudaStreamWaitEvent(g->stream, g->fwd_join, 0);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 3 && !e; ++q) {
+      e = cudaEventRecord(g->fwd_join[q], g->fwd_side[q]);
+      if (!e) e = cudaStreamWaitEvent(g->stream, g->fwd_join[q], 0);
+    }
     if (e) return cuda_check(g, e, "forward side stream join");
   }
   for (int pi : active) hg.P[pi].cur ^= 1;
