@@ -145,7 +145,11 @@ lbm_status lbm_init_equilibrium(lbm_grid_t g, int32_t patch, const void* rho, co
                                 int32_t dtype);
 
 /* Advances n_coarse_steps coarse steps: one coarse step runs the algorithm of
- * Sec. III.C recursively, level l taking 2^l steps.  Asynchronous. */
+ * Sec. III.C recursively, level l taking 2^l steps.  Asynchronous with respect
+ * to the host and ordered on the bound stream: work forked onto the library's
+ * internal streams inside an instant is joined back into the bound stream
+ * before the instant ends.  LBM_ERR_ARG for a negative count, LBM_ERR_STATE for
+ * an unbound grid, LBM_ERR_CUDA for a launch failure. */
 lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps);
 
 /* Autotuner of the stream-collide tile pass.  The TMA kernel comes in

@@ -11,6 +11,12 @@
 // the patch's odd steps its depth-1 layer is streamed normally and its depth-0
 // layer is not needed.  This realises steps 1-5 of Sec. III.C without time
 // interpolation: nothing ever reads a parent state between its own steps.
+//
+// Execution of an instant: one batched TMA tile pass over every active patch
+// (isothermal model), then the node-by-node remainder, the coalesces and the
+// explode chains on side streams, joined before the next instant; a coarse
+// step is captured once per set of buffer indices and replayed as a CUDA
+// graph.
 #include <cstdio>
 #include <cstring>
 #include <string>
