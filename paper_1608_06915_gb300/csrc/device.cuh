@@ -258,10 +258,21 @@ __host__ __device__ constexpr int wclass() {
   return (CX(i) != 0) + (CY(i) != 0) + (CZ(i) != 0);
 }
 
+// The same with the moments of f given (callers that already hold them).
+template <typename R, int FM>
+__device__ __forceinline__ R kbc_collide_m(R (&f)[27], R rho_t, R rho, R ux, R uy, R uz, R beta, R dux, R duy,
+                                           R duz, bool lbgk);
+
 template <typename R, int FM>
 __device__ __forceinline__ R kbc_collide(R (&f)[27], R beta, R dux, R duy, R duz, bool lbgk) {
   R rho_t, rho, ux, uy, uz;
   macro(f, rho_t, rho, ux, uy, uz);
+  return kbc_collide_m<R, FM>(f, rho_t, rho, ux, uy, uz, beta, dux, duy, duz, lbgk);
+}
+
+template <typename R, int FM>
+__device__ __forceinline__ R kbc_collide_m(R (&f)[27], R rho_t, R rho, R ux, R uy, R uz, R beta, R dux, R duy,
+                                           R duz, bool lbgk) {
   AxisEq<R> ex, ey, ez;
   axis_eq<R>(ux, ex, !lbgk);
   axis_eq<R>(uy, ey, !lbgk);

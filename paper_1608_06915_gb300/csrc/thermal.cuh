@@ -109,7 +109,8 @@ __device__ __forceinline__ R thermal_collide(R (&f)[27], R (&g)[27], R beta, R b
     g[i] = g[i] + b2 * (ge[i] - g[i]) + b12 * wcv3<i>(X[0], X[1], X[2]);
   });
   const R duz = glam * (s.T_d - tref_d);
-  return kbc_collide<R, 4>(f, beta, R(0), R(0), duz, lbgk);
+  // f is still the pre-collision state: its moments are those of thermal_state
+  return kbc_collide_m<R, 4>(f, s.rho_t, s.rho, s.ux, s.uy, s.uz, beta, R(0), R(0), duz, lbgk);
 }
 
 // Non-equilibrium rescaling of a thermal pair from a level with (beta_s, beta1_s)
