@@ -79,11 +79,14 @@ struct lbm_grid {
   // coupling chains, all beside each other after the TMA pass of an instant
   cudaStream_t fwd_side[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t fwd_fork = nullptr, fwd_join[3] = {nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> patch_done;  // thermal model: a patch's stream-collide has been issued
   ~lbm_grid() {
     for (auto& x : fwd_side)
       if (x) cudaStreamDestroy(x);
     if (fwd_fork) cudaEventDestroy(fwd_fork);
     for (auto& x : fwd_join)
+      if (x) cudaEventDestroy(x);
+    for (auto& x : patch_done)
       if (x) cudaEventDestroy(x);
     for (auto& x : adj_side)
       if (x) cudaStreamDestroy(x);
@@ -243,21 +246,30 @@ lbm_status run_instant(lbm_grid* g, int k) {
   // updated in the same substep; all of them read the previous state.  So they
   // run on side streams beside each other, joined before the instant ends
   // (not under per-launch timing).
+  // The thermal model issues each patch's stream-collide inside the loop
+  // below; its coupling chains then start on the side streams once that
+  // patch's stream-collide has been issued (one event per patch).
   cudaStream_t rest = g->stream, cpl[2] = {g->stream, g->stream};
-  // (the thermal model steps its patches inside the loop below, so it keeps
-  // everything on the bound stream)
-  const bool forked = !g->timing && !hg.thermal;
-  if (forked) {
+  const bool side = !g->timing;
+  const bool forked = side && !hg.thermal;
+  if (side) {
     cudaError_t e = cudaSuccess;
     for (int q = 0; q < 3 && !e; ++q)
       if (!g->fwd_side[q]) e = cudaStreamCreateWithFlags(&g->fwd_side[q], cudaStreamNonBlocking);
     if (!e && !g->fwd_fork) e = cudaEventCreateWithFlags(&g->fwd_fork, cudaEventDisableTiming);
     for (int q = 0; q < 3 && !e; ++q)
       if (!g->fwd_join[q]) e = cudaEventCreateWithFlags(&g->fwd_join[q], cudaEventDisableTiming);
-    if (!e) e = cudaEventRecord(g->fwd_fork, g->stream);
-    for (int q = 0; q < 3 && !e; ++q) e = cudaStreamWaitEvent(g->fwd_side[q], g->fwd_fork, 0);
+    if (hg.thermal && g->patch_done.size() != hg.P.size()) {
+      g->patch_done.assign(hg.P.size(), nullptr);
+      for (auto& x : g->patch_done)
+        if (!e) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    }
+    if (forked) {
+      if (!e) e = cudaEventRecord(g->fwd_fork, g->stream);
+      for (int q = 0; q < 3 && !e; ++q) e = cudaStreamWaitEvent(g->fwd_side[q], g->fwd_fork, 0);
+      rest = g->fwd_side[0];
+    }
     if (e) return cuda_check(g, e, "forward side streams");
-    rest = g->fwd_side[0];
     cpl[0] = g->fwd_side[1];
     cpl[1] = g->fwd_side[2];
   }
@@ -320,6 +332,12 @@ lbm_status run_instant(lbm_grid* g, int k) {
             "stream_collide");
       }
       if (st) return st;
+      if (side && hg.thermal) {
+        // this patch's coupling chains wait for its stream-collide only
+        cudaError_t e = cudaEventRecord(g->patch_done[pi], g->stream);
+        for (int q = 0; q < 2 && !e; ++q) e = cudaStreamWaitEvent(cpl[q], g->patch_done[pi], 0);
+        if (e) return cuda_check(g, e, "thermal side streams");
+      }
       for (int ci : p.kids) {
         HostPatch& c = hg.P[ci];
         const lbmk::PatchDev cv = view(g, c);
@@ -406,9 +424,11 @@ lbm_status run_instant(lbm_grid* g, int k) {
       }
     }
   }
-  if (forked) {
+  if (side) {
+    // join the side streams used in this instant (the remainder stream only
+    // when it was forked)
     cudaError_t e = cudaSuccess;
-    for (int q = 0; q < 3 && !e; ++q) {
+    for (int q = forked ? 0 : 1; q < 3 && !e; ++q) {
       e = cudaEventRecord(g->fwd_join[q], g->fwd_side[q]);
       if (!e) e = cudaStreamWaitEvent(g->stream, g->fwd_join[q], 0);
     }
