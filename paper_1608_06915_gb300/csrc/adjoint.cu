@@ -336,97 +336,324 @@ __device__ __forceinline__ void pull_node(const PatchDev& p, const R* __restrict
   else pull_generic<R, R>(p, fin, x, y, z, f, status);
 }
 
-// coalesce: parent twin <- collide_parent(f^eq + r (f_child - f^eq))
+// ---------------------------------------------------------------------------
+// Warp-cooperative node maps for the coupling adjoints.  The coupling sets are
+// small (a few thousand nodes) and each node's VJP is a long serial chain, so
+// one warp takes one node: lane i < 27 holds population i, lanes 27..31 hold
+// zeros (or, in the explode, the four moment values), and every sum over the
+// populations is a butterfly reduction across the warp.
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// Sums over the warp of N values at once (the N butterflies interleaved).
+template <int N, typename R>
+__device__ __forceinline__ void wsum(R (&v)[N]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] += __shfl_xor_sync(kFullMask, v[j], o);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R sel3(int c, const R (&a)[3]) {
+  return c < 0 ? a[0] : (c == 0 ? a[1] : a[2]);
+}
+
+// The lane's direction: idle lanes take the rest direction (finite
+// equilibrium values) and are masked out of every sum and store.
+struct Lane {
+  int i, c[3], na;  // direction, velocity, number of non-zero components
+  bool on;
+};
+
+__device__ __forceinline__ Lane lane_dir() {
+  Lane d;
+  const int l = threadIdx.x & 31;
+  d.on = l < 27;
+  d.i = d.on ? l : 13;
+  d.c[0] = d.i % 3 - 1, d.c[1] = (d.i / 3) % 3 - 1, d.c[2] = d.i / 9 - 1;
+  d.na = (d.c[0] != 0) + (d.c[1] != 0) + (d.c[2] != 0);
+  return d;
+}
+
+// Equilibrium quantities of one node, the lane's share: f^eq - W and f^eq of
+// its direction and the log-derivatives L_a(c_ia) of its axis factors.
+template <typename R>
+struct WEq {
+  R rho_t, rho, ir, u[3];
+  R fe, fefull, Ld[3];
+};
+
+template <typename R>
+__device__ __forceinline__ void weq_from_moments(R rho_t, R rho, R ux, R uy, R uz, const Lane& d, WEq<R>& q) {
+  q.rho_t = rho_t;
+  q.rho = rho;
+  q.ir = rcp_fast(rho);
+  q.u[0] = ux, q.u[1] = uy, q.u[2] = uz;
+  R dv[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    AxisEq<R> e;
+    axis_eq<R>(q.u[a], e, false);
+    R L[3];
+    axis_logderiv<R>(q.u[a], e, L);
+    dv[a] = sel3(d.c[a], e.d);
+    q.Ld[a] = sel3(d.c[a], L);
+  }
+  const R t = dv[0] + dv[1] + dv[0] * dv[1];
+  const R qp = t + dv[2] + t * dv[2];
+  const R W = R(wi_rt(d.i));
+  q.fe = W * (rho_t + rho * qp);
+  q.fefull = W + q.fe;
+}
+
+// rho~ = sum f, u = j / rho, reduced over the warp, then the equilibrium.
+template <typename R>
+__device__ __forceinline__ void weq_of(R f, const Lane& d, WEq<R>& q) {
+  R m[4] = {f, R(d.c[0]) * f, R(d.c[1]) * f, R(d.c[2]) * f};
+  wsum<4>(m);
+  const R rho = R(1) + m[0];
+  const R ir = rcp_fast(rho);
+  weq_from_moments<R>(m[0], rho, m[1] * ir, m[2] * ir, m[3] * ir, d, q);
+}
+
+// VJP of f^eq(rho, u) at q: given the lane's xbar, returns rhobar and ubar
+// (sum_i xbar_i f^eq_i / rho, sum_i xbar_i f^eq_i L_a(c_ia)).
+template <typename R>
+__device__ __forceinline__ void wfeq_vjp_rho_u(R xbar, const Lane& d, const WEq<R>& q, R& rb, R (&ub)[3]) {
+  const R x = d.on ? xbar * q.fefull : R(0);
+  R v[4] = {x, x * q.Ld[0], x * q.Ld[1], x * q.Ld[2]};
+  wsum<4>(v);
+  rb = v[0] * q.ir;
+  ub[0] = v[1], ub[1] = v[2], ub[2] = v[3];
+}
+
+// fbar += (J_feq(f)^T xbar)_i, f^eq through rho = sum f and u = j / rho.
+template <typename R>
+__device__ __forceinline__ R wadd_feq_f_vjp(R xbar, const Lane& d, const WEq<R>& q) {
+  R rb, ub[3];
+  wfeq_vjp_rho_u<R>(xbar, d, q, rb, ub);
+  const R jb[3] = {ub[0] * q.ir, ub[1] * q.ir, ub[2] * q.ir};
+  rb -= (ub[0] * q.u[0] + ub[1] * q.u[1] + ub[2] * q.u[2]) * q.ir;
+  return rb + R(d.c[0]) * jb[0] + R(d.c[1]) * jb[1] + R(d.c[2]) * jb[2];
+}
+
+// The KBC collision VJP of kbc_vjp, one node per warp: f and lam are the
+// lane's pre-collision population and post-collision adjoint; returns the
+// lane's pre-collision adjoint (garbage on idle lanes).
+template <typename R>
+__device__ R wkbc_vjp(R f, R lam, const Lane& d, R beta, bool lbgk) {
+  WEq<R> q;
+  weq_of<R>(f, d, q);
+  const R df = d.on ? f - q.fe : R(0);
+  const int cx = d.c[0], cy = d.c[1], cz = d.c[2];
+  R m[6] = {cx ? df : R(0), cy ? df : R(0), cz ? df : R(0), R(cx * cy) * df, R(cx * cz) * df, R(cy * cz) * df};
+  wsum<6>(m);
+  const R tr3 = (m[0] + m[1] + m[2]) * R(1.0 / 3.0);
+  const R nxx = m[0] - tr3, nyy = m[1] - tr3, nzz = m[2] - tr3;
+  const R pxy = m[3], pxz = m[4], pyz = m[5];
+  // shear part of the lane's direction (zero at rest and corners)
+  R ds = R(0);
+  if (d.na == 1) ds = R(0.5) * (cx ? nxx : (cy ? nyy : nzz));
+  else if (d.na == 2) ds = R(0.25) * (cz == 0 ? R(cx * cy) * pxy : (cy == 0 ? R(cx * cz) * pxz : R(cy * cz) * pyz));
+  const R dh = df - ds;
+  const R w = rcp_fast(q.fefull);  // entropic weight 1 / f^eq_i
+  R t3[3] = {ds * dh * w, dh * dh * w, d.on ? lam * dh : R(0)};
+  wsum<3>(t3);
+  const R sh = t3[0], hh = t3[1];
+  const R G = -beta * t3[2];  // dL/dgamma
+  const R ib = rcp_fast(beta);
+  R gamma = R(2);
+  bool use_gamma = false;
+  if (!lbgk && hh > R(1e-30) * q.rho * q.rho) {
+    use_gamma = true;
+    gamma = ib - (R(2) - ib) * fdiv(sh, hh);
+  }
+  const R a = R(1) - beta * gamma, b = beta * (gamma - R(2));
+  R Lsh = 0, Lhh = 0;
+  if (use_gamma) {
+    const R c = R(2) - ib;
+    const R ihh = rcp_fast(hh);
+    Lsh = -G * c * ihh;
+    Lhh = G * c * sh * ihh * ihh;
+  }
+  // adjoint of ds, reduced to the adjoint of the second moments
+  R dsb = b * lam, gw = R(0);
+  if (use_gamma) {
+    gw = (Lsh * ds + R(2) * Lhh * dh) * w;
+    dsb += Lsh * dh * w - gw;
+  }
+  const bool face = d.on && d.na == 1, edge = d.on && d.na == 2;
+  R S[6] = {face && cx ? dsb : R(0),
+            face && cy ? dsb : R(0),
+            face && cz ? dsb : R(0),
+            edge && cz == 0 ? R(cx * cy) * dsb : R(0),
+            edge && cy == 0 ? R(cx * cz) * dsb : R(0),
+            edge && cx == 0 ? R(cy * cz) * dsb : R(0)};
+  wsum<6>(S);
+  const R Pbxx = R(1.0 / 3.0) * S[0] - R(1.0 / 6.0) * (S[1] + S[2]);
+  const R Pbyy = R(1.0 / 3.0) * S[1] - R(1.0 / 6.0) * (S[0] + S[2]);
+  const R Pbzz = R(1.0 / 3.0) * S[2] - R(1.0 / 6.0) * (S[0] + S[1]);
+  const R Pbxy = R(0.25) * S[3], Pbxz = R(0.25) * S[4], Pbyz = R(0.25) * S[5];
+  // adjoint of df (to f directly) and of f^eq (reduced to rho, u)
+  R dfb = a * lam + gw;
+  if (cx) dfb += Pbxx;
+  if (cy) dfb += Pbyy;
+  if (cz) dfb += Pbzz;
+  dfb += R(cx * cy) * Pbxy + R(cx * cz) * Pbxz + R(cy * cz) * Pbyz;
+  R feb = lam;
+  if (use_gamma) feb -= (Lsh * ds * dh + Lhh * dh * dh) * w * w;  // d(1/fe) = -w^2
+  feb -= dfb;                                                     // df = f - fe
+  return dfb + wadd_feq_f_vjp<R>(feb, d, q);
+}
+
+// The lane's population of the pull of node (x, y, z): pull_generic for one
+// runtime direction (bulk nodes wrap, as pull_bulk does).
+template <typename R>
+__device__ __forceinline__ R pull_one(const PatchDev& p, const R* __restrict__ fin, int x, int y, int z, const Lane& d,
+                                      int* status) {
+  const long long own = node_index(p, x, y, z);
+  const bool bulk = p.type[own] == T_BULK;
+  const int X[3] = {x, y, z};
+  int s[3];
+  bool bounce = false, bad = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    s[a] = X[a] - d.c[a];
+    if (s[a] < 0 || s[a] >= p.dim[a]) {
+      if (bulk || p.span[a]) {
+        s[a] += s[a] < 0 ? p.dim[a] : -p.dim[a];
+      } else if (!p.periodic[a]) {
+        const int Gc = p.org[a] + s[a];
+        if (Gc < 0) {
+          if (p.walls & (1u << (2 * a))) bounce = true;
+          else bad = true;
+        } else if (Gc > p.maxc[a]) {
+          if (p.walls & (1u << (2 * a + 1))) bounce = true;
+          else if (p.inflow == a) s[a] = p.maxc[a] - p.org[a];
+          else bad = true;
+        } else {
+          bad = true;
+        }
+      } else {
+        bad = true;
+      }
+    }
+  }
+  long long src = own;
+  if (!bounce && !bad) {
+    src = node_index(p, s[0], s[1], s[2]);
+    if (!bulk) {
+      const uint8_t t = p.type[src];
+      if (t == T_SOLID) bounce = true;
+      else if (t == T_SKIP) bad = true;
+    }
+  }
+  if (bad) {
+    atomicOr(status, 1);
+    bounce = true;
+  }
+  if (bounce) return __ldg(fin + (long long)(26 - d.i) * p.plane + own);
+  return __ldg(fin + (long long)d.i * p.plane + src);
+}
+
+// Scatter of the lane's adjoint along the reversed pull (push_adjoint for one
+// runtime direction).
+template <typename R>
+__device__ __forceinline__ void push_one(const PatchDev& p, R* __restrict__ lam_old, int x, int y, int z, const Lane& d,
+                                         R v) {
+  const long long own = node_index(p, x, y, z);
+  const bool bulk = p.type[own] == T_BULK;
+  const int X[3] = {x, y, z};
+  int s[3];
+  bool bounce = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    s[a] = X[a] - d.c[a];
+    if (s[a] < 0 || s[a] >= p.dim[a]) {
+      if (bulk || p.span[a]) s[a] += s[a] < 0 ? p.dim[a] : -p.dim[a];
+      else bounce = true;  // not produced by the layouts the adjoint accepts
+    }
+  }
+  if (bounce) atomicAdd(lam_old + (long long)(26 - d.i) * p.plane + own, v);
+  else atomicAdd(lam_old + (long long)d.i * p.plane + node_index(p, s[0], s[1], s[2]), v);
+}
+
+__device__ __forceinline__ long long warp_id() {
+  return ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+}
+
+// coalesce: parent twin <- collide_parent(f^eq + r (f_child - f^eq)); one warp per twin
 template <typename R>
 __global__ void __launch_bounds__(128) k_adj_coalesce(PatchDev pc, const R* __restrict__ fin_c, PatchDev pp,
                                                       const R* __restrict__ lam_new_p, R* __restrict__ lam_old_c,
                                                       const uint32_t* __restrict__ cf_parent,
                                                       const uint32_t* __restrict__ cf_child, long long n, R r,
                                                       R beta_p, int lbgk, int* status) {
-  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+  const long long k = warp_id();
+  if (k >= n) return;  // whole warp
+  const Lane d = lane_dir();
   int x, y, z;
   node_xyz(pc, cf_child[k], x, y, z);
-  R f[27];
-  pull_node<R>(pc, fin_c, x, y, z, f, status);
-  R rho_t, rho, ux, uy, uz;
-  macro(f, rho_t, rho, ux, uy, uz);
-  EqState<R> q;
-  eq_state_from_moments<R>(rho_t, rho, ux, uy, uz, q, false);
-  R fc[27];
-  unroll<27>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    fc[i] = q.fe[i] + r * (f[i] - q.fe[i]);
-  });
-  R l[27];
-  load_lam<R>(pp, lam_new_p, cf_parent[k], l);
-  kbc_vjp<R>(fc, l, beta_p, lbgk != 0);
+  const R f = d.on ? pull_one<R>(pc, fin_c, x, y, z, d, status) : R(0);
+  WEq<R> q;
+  weq_of<R>(f, d, q);
+  const R fc = d.on ? q.fe + r * (f - q.fe) : R(0);
+  R l = d.on ? lam_new_p[(long long)d.i * pp.plane + cf_parent[k]] : R(0);
+  l = wkbc_vjp<R>(fc, l, d, beta_p, lbgk != 0);
   // fc = r f + (1 - r) fe(f)
-  R fb[27], xb[27];
-  unroll<27>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    fb[i] = r * l[i];
-    xb[i] = (R(1) - r) * l[i];
-  });
-  add_feq_f_vjp<R>(q, xb, fb);
-  push_adjoint<R>(pc, lam_old_c, x, y, z, fb);
+  const R fb = r * l + wadd_feq_f_vjp<R>((R(1) - r) * l, d, q);
+  if (d.on) push_one<R>(pc, lam_old_c, x, y, z, d, fb);
 }
 
 // explode: child node <- collide_child(f^eq(rho~, u~) + neq~), (rho~, u~, neq~)
 // one point of the reconstruction point space or the four-point interpolation
-// of four; scatters the adjoint of the 31 values into vbar [31][ld].
+// of four; scatters the adjoint of the 31 values into vbar [31][ld].  One warp
+// per node: lane i < 27 takes neq~_i (value 4 + i), lanes 27..30 the values
+// 0..3 (rho~, u~).
 template <typename R>
 __global__ void __launch_bounds__(128) k_adj_explode(PatchDev pc, const R* __restrict__ lam_new_c,
                                                      const uint32_t* __restrict__ ex_node,
                                                      const uint4* __restrict__ ex_src, long long n_one, long long n,
                                                      const R* __restrict__ val, R* __restrict__ vbar, long long ld,
                                                      R beta_c, int lbgk) {
-  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+  const long long k = warp_id();
+  if (k >= n) return;  // whole warp
+  const Lane d = lane_dir();
+  const int lane = threadIdx.x & 31;
+  const int vi = lane < 27 ? 4 + lane : lane - 27;  // this lane's value (lane 31: none)
   const uint4 s = ex_src[k];
   const bool one = k < n_one;
   const R w0 = R(-1.0 / 16.0), w1 = R(9.0 / 16.0);
-  auto ip = [&](int c) {
-    const R* v = val + (long long)c * ld;
-    if (one) return v[s.x];
-    return w0 * (v[s.x] + v[s.w]) + w1 * (v[s.y] + v[s.z]);
-  };
-  R v[4], neq[27];
-  for (int c = 0; c < 4; ++c) v[c] = ip(c);
-  unroll<27>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    neq[i] = ip(4 + i);
-  });
-  EqState<R> q;
-  eq_state_from_moments<R>(v[0], R(1) + v[0], v[1], v[2], v[3], q, false);
-  R f[27];
-  unroll<27>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    f[i] = q.fe[i] + neq[i];
-  });
-  R l[27];
-  load_lam<R>(pc, lam_new_c, ex_node[k], l);
-  kbc_vjp<R>(f, l, beta_c, lbgk != 0);
+  R mine = R(0);
+  if (lane < 31) {
+    const R* v = val + (long long)vi * ld;
+    mine = one ? v[s.x] : w0 * (v[s.x] + v[s.w]) + w1 * (v[s.y] + v[s.z]);
+  }
+  R v4[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) v4[c] = __shfl_sync(kFullMask, mine, 27 + c);
+  WEq<R> q;
+  weq_from_moments<R>(v4[0], R(1) + v4[0], v4[1], v4[2], v4[3], d, q);
+  const R f = d.on ? q.fe + mine : R(0);
+  R l = d.on ? lam_new_c[(long long)d.i * pc.plane + ex_node[k]] : R(0);
+  l = wkbc_vjp<R>(f, l, d, beta_c, lbgk != 0);
   // f = fe(rho, u) + neq: neq-bar = l; (rho-bar, u-bar) from fe directly
   R rb, ub[3];
-  feq_vjp_rho_u<R>(l, q.fefull, q.rho, q.L[0], q.L[1], q.L[2], rb, ub);
-  const R vb[4] = {rb, ub[0], ub[1], ub[2]};  // rho~ enters as rho = 1 + rho~
-  auto push = [&](int c, R x) {
-    R* d = vbar + (long long)c * ld;
+  wfeq_vjp_rho_u<R>(l, d, q, rb, ub);  // rho~ enters as rho = 1 + rho~
+  const R x = lane < 27 ? l : (lane == 27 ? rb : (lane == 28 ? ub[0] : (lane == 29 ? ub[1] : ub[2])));
+  if (lane < 31) {
+    R* dst = vbar + (long long)vi * ld;
     if (one) {
-      atomicAdd(d + s.x, x);
+      atomicAdd(dst + s.x, x);
     } else {
-      atomicAdd(d + s.x, w0 * x);
-      atomicAdd(d + s.y, w1 * x);
-      atomicAdd(d + s.z, w1 * x);
-      atomicAdd(d + s.w, w0 * x);
+      atomicAdd(dst + s.x, w0 * x);
+      atomicAdd(dst + s.y, w1 * x);
+      atomicAdd(dst + s.z, w1 * x);
+      atomicAdd(dst + s.w, w0 * x);
     }
-  };
-  for (int c = 0; c < 4; ++c) push(c, vb[c]);
-  unroll<27>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    push(4 + i, l[i]);
-  });
+  }
 }
 
 // transpose of one interpolation pass: vbar[c][src_k] += w_k vbar[c][out0 + q];
@@ -446,7 +673,8 @@ __global__ void __launch_bounds__(128) k_adj_points(const uint4* __restrict__ sr
   atomicAdd(d + s.w, w0 * x);
 }
 
-// samples: (rho~, u, factor (f - f^eq)) of the pulled state of a parent or child node
+// samples: (rho~, u, factor (f - f^eq)) of the pulled state of a parent or
+// child node; one warp per sample
 template <typename R>
 __global__ void __launch_bounds__(128) k_adj_samples(PatchDev pp, const R* __restrict__ fin_p, R* __restrict__ lam_p,
                                                      PatchDev pc, const R* __restrict__ fin_c, R* __restrict__ lam_c,
@@ -454,35 +682,24 @@ __global__ void __launch_bounds__(128) k_adj_samples(PatchDev pp, const R* __res
                                                      const uint8_t* __restrict__ smp_kind, long long ns,
                                                      const R* __restrict__ sbar, long long ld, R rescale_p,
                                                      int* status) {
-  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= ns) return;
+  const long long s = warp_id();
+  if (s >= ns) return;  // whole warp
+  const Lane d = lane_dir();
   const bool par = smp_kind[s] == 0;
   const PatchDev& q = par ? pp : pc;
   int x, y, z;
   node_xyz(q, smp_node[s], x, y, z);
-  R f[27];
-  pull_node<R>(q, par ? fin_p : fin_c, x, y, z, f, status);
+  const R f = d.on ? pull_one<R>(q, par ? fin_p : fin_c, x, y, z, d, status) : R(0);
   const R factor = par ? rescale_p : R(1);
-  R rho_t, rho, ux, uy, uz;
-  macro(f, rho_t, rho, ux, uy, uz);
-  EqState<R> e;
-  eq_state_from_moments<R>(rho_t, rho, ux, uy, uz, e, false);
+  WEq<R> e;
+  weq_of<R>(f, d, e);
   const R rb = sbar[s], ub[3] = {sbar[ld + s], sbar[2 * ld + s], sbar[3 * ld + s]};
-  R nb[27], fb[27], xb[27];
-  unroll<27>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    nb[i] = sbar[(4 + i) * ld + s];
-    fb[i] = factor * nb[i];
-    xb[i] = -factor * nb[i];
-  });
-  add_feq_f_vjp<R>(e, xb, fb);
+  const R nb = d.on ? sbar[(4 + d.i) * ld + s] : R(0);
+  // neq = factor (f - fe(f))
+  R fb = factor * nb + wadd_feq_f_vjp<R>(-factor * nb, d, e);
   // rho~ = sum f, u = j / rho
-  const R ir = rcp_fast(rho);
-  unroll<27>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    fb[i] += rb + ((R(CX(i)) - ux) * ub[0] + (R(CY(i)) - uy) * ub[1] + (R(CZ(i)) - uz) * ub[2]) * ir;
-  });
-  push_adjoint<R>(q, par ? lam_p : lam_c, x, y, z, fb);
+  fb += rb + ((R(d.c[0]) - e.u[0]) * ub[0] + (R(d.c[1]) - e.u[1]) * ub[1] + (R(d.c[2]) - e.u[2]) * ub[2]) * e.ir;
+  if (d.on) push_one<R>(q, par ? lam_p : lam_c, x, y, z, d, fb);
 }
 
 // Objective: kinetic energy 1/2 sum rho |u|^2 8^-level over owned nodes (a parent
@@ -602,7 +819,7 @@ cudaError_t launch_adj_coalesce(int storage, const PatchDev& child, const void* 
   if (n == 0) return cudaSuccess;
   return adj_dispatch(storage, [&](auto z) {
     using R = decltype(z);
-    k_adj_coalesce<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(child, (const R*)fin_c, parent,
+    k_adj_coalesce<R><<<(unsigned)((n + 3) / 4), 128, 0, st>>>(child, (const R*)fin_c, parent,
                                                                    (const R*)lam_new_p, (R*)lam_old_c, cf_parent,
                                                                    cf_child, n, (R)r, (R)beta_p, lbgk, status);
     return cudaGetLastError();
@@ -615,7 +832,7 @@ cudaError_t launch_adj_explode(int storage, const PatchDev& child, const void* l
   if (n == 0) return cudaSuccess;
   return adj_dispatch(storage, [&](auto z) {
     using R = decltype(z);
-    k_adj_explode<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(child, (const R*)lam_new_c, ex_node,
+    k_adj_explode<R><<<(unsigned)((n + 3) / 4), 128, 0, st>>>(child, (const R*)lam_new_c, ex_node,
                                                                   (const uint4*)ex_src, n_one, n, (const R*)val,
                                                                   (R*)vbar, ld, (R)beta_c, lbgk);
     return cudaGetLastError();
@@ -640,7 +857,7 @@ cudaError_t launch_adj_samples(int storage, const PatchDev& parent, const void* 
   if (ns == 0) return cudaSuccess;
   return adj_dispatch(storage, [&](auto z) {
     using R = decltype(z);
-    k_adj_samples<R><<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(parent, (const R*)fin_p, (R*)lam_p, child,
+    k_adj_samples<R><<<(unsigned)((ns + 3) / 4), 128, 0, st>>>(parent, (const R*)fin_p, (R*)lam_p, child,
                                                                    (const R*)fin_c, (R*)lam_c, smp_node, smp_kind, ns,
                                                                    (const R*)sbar, ld, (R)rescale_p, status);
     return cudaGetLastError();

@@ -607,4 +607,38 @@ cudaError_t launch_collide_nodes(const void* fin, void* fout, void* gamma, int64
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Segmented device copy: blockIdx.y picks the segment; the widest access the
+// segment's addresses and size allow (16, 8, 4 or 1 bytes), grid-stride.
+template <typename V>
+__device__ __forceinline__ void copy_words(V* __restrict__ d, const V* __restrict__ s, size_t n) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    d[k] = __ldg(s + k);
+}
+
+__global__ void __launch_bounds__(256) k_copy(CopySegs segs) {
+  const int j = blockIdx.y;
+  const uintptr_t a = (uintptr_t)segs.dst[j] | (uintptr_t)segs.src[j] | (uintptr_t)segs.bytes[j];
+  const size_t n = segs.bytes[j];
+  if ((a & 15) == 0) copy_words((uint4*)segs.dst[j], (const uint4*)segs.src[j], n / 16);
+  else if ((a & 7) == 0) copy_words((uint2*)segs.dst[j], (const uint2*)segs.src[j], n / 8);
+  else if ((a & 3) == 0) copy_words((unsigned*)segs.dst[j], (const unsigned*)segs.src[j], n / 4);
+  else copy_words((unsigned char*)segs.dst[j], (const unsigned char*)segs.src[j], n);
+}
+
+cudaError_t launch_copy(const CopySegs& segs, cudaStream_t st) {
+  if (segs.n <= 0) return cudaSuccess;
+  if (segs.n > kCopySegs) return cudaErrorInvalidValue;
+  size_t most = 0;
+  for (int j = 0; j < segs.n; ++j) most = segs.bytes[j] > most ? segs.bytes[j] : most;
+  if (most == 0) return cudaSuccess;
+  // about four 16-byte words per thread for the largest segment, at most
+  // 8 blocks per SM (152 SMs)
+  size_t blocks = (most / 16 + 1023) / 1024;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_copy<<<dim3((unsigned)blocks, (unsigned)segs.n), 256, 0, st>>>(segs);
+  return cudaGetLastError();
+}
+
 }  // namespace lbmk

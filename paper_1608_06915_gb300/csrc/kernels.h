@@ -141,6 +141,17 @@ cudaError_t launch_copy_pop(int storage, const PatchDev& p, void* fstore, void* 
                             int gset, cudaStream_t st);
 
 // FP64 partial sums of one patch into partial[blocks][8]; see lbm_diagnostics.
+// Device-to-device copies of up to kCopySegs segments in one launch (the
+// copy engines are slower than the SMs for state-sized copies).
+constexpr int kCopySegs = 16;
+struct CopySegs {
+  void* dst[kCopySegs];
+  const void* src[kCopySegs];
+  size_t bytes[kCopySegs];
+  int n;
+};
+cudaError_t launch_copy(const CopySegs& segs, cudaStream_t st);
+
 cudaError_t launch_diag(int storage, const PatchDev& p, const void* fin, double vol_weight, const Force& F,
                         double* partial, int blocks, cudaStream_t st);
 cudaError_t launch_diag_final(const double* partial, int total_blocks, double* out8, cudaStream_t st);

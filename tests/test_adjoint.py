@@ -203,3 +203,42 @@ def test_cuda_adjoint_three_levels_finite_differences():
         worst = max(worst, rel)
         print("three levels, direction %d: finite difference %.12e adjoint %.12e rel %.2e" % (seed, fd, ad, rel))
     assert worst < 1e-6, worst
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("levels", [2, 3])
+def test_cuda_adjoint_graph_sweeps_match_direct_sweeps(levels):
+    """The reverse sweeps of lbm_adjoint_step run directly (graphs off), then
+    captured as CUDA graphs, then replayed from the graph cache: the three
+    lambdas agree to rounding (the scatters are atomic additions, so their
+    order, not their terms, may differ)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1608_06915_gb300 import lbm as L
+    if levels == 2:
+        case = small_case()
+    else:
+        case = dict(I.tgv_case(n=32, box=(4, 28)),
+                    boxes=[(1, (4, 4, 4), (28, 28, 28)), (2, (10, 10, 10), (22, 22, 22))])
+    g = L.Grid(case, "fp64")
+    n = case["n"][0] if isinstance(case["n"], (tuple, list)) else case["n"]
+    m = I.divfree_modes(n=n, kmax=3.0, rms=0.03, seed=11)
+    for p, info in enumerate(g.patches):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        rho, u = I.divfree_fields(x, y, z, m)
+        g.init_equilibrium(p, torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    K = 3
+    ck = torch.empty(g.checkpoint_bytes(), dtype=torch.uint8, device="cuda")
+    g.checkpoint(ck, save=True)
+    lam, ws = g.adjoint_buffers(K)
+    out = []
+    for graphs in (False, True, True):
+        g.graphs(graphs)
+        g.step(K)
+        g.adjoint_seed(lam, ws)
+        g.adjoint_step(ck, K, lam, ws)
+        out.append(lam.view(torch.float64).cpu().numpy().copy())
+    scale = np.abs(out[0]).max()
+    assert scale > 0
+    for o in out[1:]:
+        assert np.abs(o - out[0]).max() <= 1e-12 * scale
