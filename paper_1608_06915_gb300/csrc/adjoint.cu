@@ -337,11 +337,11 @@ __device__ __forceinline__ void pull_node(const PatchDev& p, const R* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Warp-cooperative node maps for the coupling adjoints.  The coupling sets are
-// small (a few thousand nodes) and each node's VJP is a long serial chain, so
-// one warp takes one node: lane i < 27 holds population i, lanes 27..31 hold
-// zeros (or, in the explode, the four moment values), and every sum over the
-// populations is a butterfly reduction across the warp.
+// Warp-cooperative node maps for the coalesce and sample adjoints.  Their
+// node sets are small (a few thousand nodes) and each node's VJP is a long
+// serial chain, so one warp takes one node: lane i < 27 holds population i,
+// lanes 27..31 hold zeros, and every sum over the populations is a butterfly
+// reduction across the warp.
 
 constexpr unsigned kFullMask = 0xffffffffu;
 
@@ -609,51 +609,61 @@ __global__ void __launch_bounds__(128) k_adj_coalesce(PatchDev pc, const R* __re
 
 // explode: child node <- collide_child(f^eq(rho~, u~) + neq~), (rho~, u~, neq~)
 // one point of the reconstruction point space or the four-point interpolation
-// of four; scatters the adjoint of the 31 values into vbar [31][ld].  One warp
-// per node: lane i < 27 takes neq~_i (value 4 + i), lanes 27..30 the values
-// 0..3 (rho~, u~).
+// of four; scatters the adjoint of the 31 values into vbar [31][ld].  One
+// thread per node: the explode set is large enough (about ten thousand nodes)
+// that a warp per node would be bound by instruction issue.
 template <typename R>
 __global__ void __launch_bounds__(128) k_adj_explode(PatchDev pc, const R* __restrict__ lam_new_c,
                                                      const uint32_t* __restrict__ ex_node,
                                                      const uint4* __restrict__ ex_src, long long n_one, long long n,
                                                      const R* __restrict__ val, R* __restrict__ vbar, long long ld,
                                                      R beta_c, int lbgk) {
-  const long long k = warp_id();
-  if (k >= n) return;  // whole warp
-  const Lane d = lane_dir();
-  const int lane = threadIdx.x & 31;
-  const int vi = lane < 27 ? 4 + lane : lane - 27;  // this lane's value (lane 31: none)
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
   const uint4 s = ex_src[k];
   const bool one = k < n_one;
   const R w0 = R(-1.0 / 16.0), w1 = R(9.0 / 16.0);
-  R mine = R(0);
-  if (lane < 31) {
-    const R* v = val + (long long)vi * ld;
-    mine = one ? v[s.x] : w0 * (v[s.x] + v[s.w]) + w1 * (v[s.y] + v[s.z]);
-  }
-  R v4[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) v4[c] = __shfl_sync(kFullMask, mine, 27 + c);
-  WEq<R> q;
-  weq_from_moments<R>(v4[0], R(1) + v4[0], v4[1], v4[2], v4[3], d, q);
-  const R f = d.on ? q.fe + mine : R(0);
-  R l = d.on ? lam_new_c[(long long)d.i * pc.plane + ex_node[k]] : R(0);
-  l = wkbc_vjp<R>(f, l, d, beta_c, lbgk != 0);
+  auto ip = [&](int c) {
+    const R* v = val + (long long)c * ld;
+    if (one) return v[s.x];
+    return w0 * (v[s.x] + v[s.w]) + w1 * (v[s.y] + v[s.z]);
+  };
+  R v[4], neq[27];
+  for (int c = 0; c < 4; ++c) v[c] = ip(c);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    neq[i] = ip(4 + i);
+  });
+  EqState<R> q;
+  eq_state_from_moments<R>(v[0], R(1) + v[0], v[1], v[2], v[3], q, false);
+  R f[27];
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    f[i] = q.fe[i] + neq[i];
+  });
+  R l[27];
+  load_lam<R>(pc, lam_new_c, ex_node[k], l);
+  kbc_vjp<R>(f, l, beta_c, lbgk != 0);
   // f = fe(rho, u) + neq: neq-bar = l; (rho-bar, u-bar) from fe directly
   R rb, ub[3];
-  wfeq_vjp_rho_u<R>(l, d, q, rb, ub);  // rho~ enters as rho = 1 + rho~
-  const R x = lane < 27 ? l : (lane == 27 ? rb : (lane == 28 ? ub[0] : (lane == 29 ? ub[1] : ub[2])));
-  if (lane < 31) {
-    R* dst = vbar + (long long)vi * ld;
+  feq_vjp_rho_u<R>(l, q.fefull, q.rho, q.L[0], q.L[1], q.L[2], rb, ub);
+  const R vb[4] = {rb, ub[0], ub[1], ub[2]};  // rho~ enters as rho = 1 + rho~
+  auto push = [&](int c, R x) {
+    R* d = vbar + (long long)c * ld;
     if (one) {
-      atomicAdd(dst + s.x, x);
+      atomicAdd(d + s.x, x);
     } else {
-      atomicAdd(dst + s.x, w0 * x);
-      atomicAdd(dst + s.y, w1 * x);
-      atomicAdd(dst + s.z, w1 * x);
-      atomicAdd(dst + s.w, w0 * x);
+      atomicAdd(d + s.x, w0 * x);
+      atomicAdd(d + s.y, w1 * x);
+      atomicAdd(d + s.z, w1 * x);
+      atomicAdd(d + s.w, w0 * x);
     }
-  }
+  };
+  for (int c = 0; c < 4; ++c) push(c, vb[c]);
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    push(4 + i, l[i]);
+  });
 }
 
 // transpose of one interpolation pass: vbar[c][src_k] += w_k vbar[c][out0 + q];
@@ -832,7 +842,7 @@ cudaError_t launch_adj_explode(int storage, const PatchDev& child, const void* l
   if (n == 0) return cudaSuccess;
   return adj_dispatch(storage, [&](auto z) {
     using R = decltype(z);
-    k_adj_explode<R><<<(unsigned)((n + 3) / 4), 128, 0, st>>>(child, (const R*)lam_new_c, ex_node,
+    k_adj_explode<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(child, (const R*)lam_new_c, ex_node,
                                                                   (const uint4*)ex_src, n_one, n, (const R*)val,
                                                                   (R*)vbar, ld, (R)beta_c, lbgk);
     return cudaGetLastError();

@@ -113,6 +113,15 @@ struct lbm_grid {
 
 namespace {
 
+// Side streams take the highest priority: their kernels (coupling chains,
+// short and latency-bound) are scheduled ahead of the remaining blocks of a
+// large kernel on the bound stream.  Graphs keep the priority per node.
+cudaError_t side_stream(cudaStream_t* s) {
+  int least = 0, greatest = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  return e ? e : cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, greatest);
+}
+
 lbm_status fail(lbm_grid* g, lbm_status s, const std::string& m) {
   if (g) g->err = m;
   else g_create_error = m;
@@ -267,7 +276,7 @@ lbm_status run_instant(lbm_grid* g, int k) {
   if (side) {
     cudaError_t e = cudaSuccess;
     for (int q = 0; q < 3 && !e; ++q)
-      if (!g->fwd_side[q]) e = cudaStreamCreateWithFlags(&g->fwd_side[q], cudaStreamNonBlocking);
+      if (!g->fwd_side[q]) e = side_stream(&g->fwd_side[q]);
     if (!e && !g->fwd_fork) e = cudaEventCreateWithFlags(&g->fwd_fork, cudaEventDisableTiming);
     for (int q = 0; q < 3 && !e; ++q)
       if (!g->fwd_join[q]) e = cudaEventCreateWithFlags(&g->fwd_join[q], cudaEventDisableTiming);
@@ -679,7 +688,7 @@ lbm_status capture_step(lbm_grid* g, const std::vector<uint8_t>& key, cudaGraphE
     if (graph) cudaGraphDestroy(graph);
     return st ? st : cuda_check(g, e2, "cudaStreamEndCapture");
   }
-  e = cudaGraphInstantiate(out, graph, 0);
+  e = cudaGraphInstantiate(out, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   return cuda_check(g, e, "cudaGraphInstantiate");
 }
@@ -855,6 +864,7 @@ lbm_status adjoint_supported(lbm_grid* g) {
 struct AdjLayout {
   std::vector<size_t> lam_off;   // per patch, in the packed lambda (and in the second buffer)
   std::vector<size_t> sbar_off;  // per patch (children), in the workspace
+  std::vector<size_t> snap_patch_off;  // per patch, within one snapshot
   size_t lam_bytes = 0, second_off = 0, snap_off = 0, snap_bytes = 0, partial_off = 0, total = 0;
 };
 
@@ -876,7 +886,10 @@ AdjLayout adjoint_layout(const lbm_grid* g, int K) {
   a.second_off = take(a.lam_bytes);
   for (auto& p : g->hg.P) a.sbar_off.push_back(take(31 * p.n_points() * rb));
   a.snap_bytes = 0;
-  for (auto& p : g->hg.P) a.snap_bytes += 27 * (size_t)p.plane * g->hg.pop_bytes;
+  for (auto& p : g->hg.P) {
+    a.snap_patch_off.push_back(a.snap_bytes);
+    a.snap_bytes += 27 * (size_t)p.plane * g->hg.pop_bytes;
+  }
   a.snap_off = take(a.snap_bytes * (size_t)K);
   a.partial_off = take(sizeof(double) * (kDiagBlocks * g->hg.P.size() + 1));
   a.total = w;
@@ -885,7 +898,7 @@ AdjLayout adjoint_layout(const lbm_grid* g, int K) {
 
 // Copies the state of every patch to/from a packed buffer (restore: the current
 // buffer only unless both are asked for).
-cudaError_t copy_state(lbm_grid* g, uint8_t* dst_or_src, bool save, bool both = true) {
+cudaError_t copy_state(lbm_grid* g, uint8_t* dst_or_src, bool save, bool both = true, int min_level = 0) {
   cudaError_t e = cudaSuccess;
   uint8_t* d = dst_or_src;
   lbmk::CopySegs segs{};
@@ -899,6 +912,10 @@ cudaError_t copy_state(lbm_grid* g, uint8_t* dst_or_src, bool save, bool both = 
   };
   for (auto& p : g->hg.P) {
     const size_t n = 27 * (size_t)p.plane * g->hg.pop_bytes;
+    if (p.level < min_level) {
+      d += n;
+      continue;
+    }
     if (save) {
       add(d, g->base + p.off_f[p.cur], n);
     } else {
@@ -920,8 +937,14 @@ void flip_instant(lbm_grid* g, int k) {
 
 // Adjoint of instant k: lambda of the states after k -> lambda of the states before k.
 lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>& lcur, const AdjLayout& a,
-                           uint8_t* ws) {
+                           uint8_t* ws, uint8_t* snap) {
   HostGrid& hg = g->hg;
+  // pre-states: level 0 steps once per coarse step, at the top instant, so its
+  // state before every instant is the snapshot itself
+  auto state = [&](int pi) -> uint8_t* {
+    const HostPatch& p = hg.P[pi];
+    return p.level == 0 ? snap + a.snap_patch_off[pi] : g->base + p.off_f[p.cur];
+  };
   const int L = hg.nlev, storage = hg.desc.storage, lbgk = hg.desc.mirror_lbgk;
   const size_t rb = hg.real_bytes;
   auto lam_ptr = [&](int pi, int which) { return lam[which] + a.lam_off[pi]; };
@@ -939,7 +962,7 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
   // (bound stream), the coalesce adjoints (side stream 0) and, per child, the
   // explode chain (side stream 1); each adds into lambda with reductions
   for (int q = 0; q < 2 && !e; ++q)
-    if (!g->adj_side[q]) e = cudaStreamCreateWithFlags(&g->adj_side[q], cudaStreamNonBlocking);
+    if (!g->adj_side[q]) e = side_stream(&g->adj_side[q]);
   if (!e && !g->adj_fork) e = cudaEventCreateWithFlags(&g->adj_fork, cudaEventDisableTiming);
   for (int q = 0; q < 2 && !e; ++q)
     if (!g->adj_join[q]) e = cudaEventCreateWithFlags(&g->adj_join[q], cudaEventDisableTiming);
@@ -955,12 +978,12 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
     const int odd = (lev > 0 && !parent_active) ? 1 : 0;
     const lbmk::PatchDev pv = view(g, p);
     if (!e)
-      e = lbmk::launch_adj_sc(storage, pv, g->base + p.off_f[p.cur], lam_ptr(pi, lcur[pi]), lam_ptr(pi, 1 - lcur[pi]),
+      e = lbmk::launch_adj_sc(storage, pv, state(pi), lam_ptr(pi, lcur[pi]), lam_ptr(pi, 1 - lcur[pi]),
                               p.beta, odd, lbgk, p.n_bc > 0, status_ptr(g), g->stream);
     for (int ci : p.kids) {
       HostPatch& c = hg.P[ci];
       if (!e)
-        e = lbmk::launch_adj_coalesce(storage, view(g, c), g->base + c.off_f[c.cur], pv, lam_ptr(pi, lcur[pi]),
+        e = lbmk::launch_adj_coalesce(storage, view(g, c), state(ci), pv, lam_ptr(pi, lcur[pi]),
                                       lam_ptr(ci, 1 - lcur[ci]), at<uint32_t>(g, c.off_cf_parent),
                                       at<uint32_t>(g, c.off_cf_child), (int64_t)c.cf_parent.size(),
                                       2.0 * c.beta / p.beta, p.beta, lbgk, status_ptr(g), sc);
@@ -973,7 +996,7 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
       const int64_t ns = (int64_t)p.smp_node.size(), ld = (int64_t)p.n_points();
       const uint32_t* psrc = at<uint32_t>(g, p.off_pt_src);
       if (!e)
-        e = lbmk::launch_samples(storage, qv, g->base + q.off_f[q.cur], pv, g->base + p.off_f[p.cur],
+        e = lbmk::launch_samples(storage, qv, state(qi), pv, state(pi),
                                  at<uint32_t>(g, p.off_smp_node), at<uint8_t>(g, p.off_smp_kind), ns,
                                  g->base + p.off_smp_val, ld, q.beta / (2.0 * p.beta), status_ptr(g), sx);
       if (!e) e = point_passes(g, p, 31, sx);
@@ -987,8 +1010,8 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
         e = lbmk::launch_adj_points(storage, psrc + 4 * (size_t)p.n_pt[0], p.n_pt[1], sbar, ld, ns + p.n_pt[0], sx);
       if (!e) e = lbmk::launch_adj_points(storage, psrc, p.n_pt[0], sbar, ld, ns, sx);
       if (!e)
-        e = lbmk::launch_adj_samples(storage, qv, g->base + q.off_f[q.cur], lam_ptr(qi, 1 - lcur[qi]), pv,
-                                     g->base + p.off_f[p.cur], lam_ptr(pi, 1 - lcur[pi]),
+        e = lbmk::launch_adj_samples(storage, qv, state(qi), lam_ptr(qi, 1 - lcur[qi]), pv, state(pi),
+                                     lam_ptr(pi, 1 - lcur[pi]),
                                      at<uint32_t>(g, p.off_smp_node), at<uint8_t>(g, p.off_smp_kind), ns, sbar, ld,
                                      q.beta / (2.0 * p.beta), status_ptr(g), sx);
     }
@@ -1021,14 +1044,16 @@ lbm_status adjoint_sweep(lbm_grid* g, uint8_t* snap, uint8_t* lam[2], std::vecto
       last = -1;
     }
     if (have != k - 1) {
-      cudaError_t e = copy_state(g, snap, false, false);  // the state at the start of this coarse step
+      // the state at the start of this coarse step, for the levels the
+      // replayed instants step (level 0 is read from the snapshot itself)
+      cudaError_t e = copy_state(g, snap, false, false, 1);
       if (e) return cuda_check(g, e, "adjoint replay");
       for (int kk = 1; kk < k; ++kk)
         if (lbm_status st = run_instant(g, kk)) return st;
       have = k - 1;
       last = k - 1;
     }
-    if (lbm_status st = adjoint_instant(g, k, lam, lcur, a, ws)) return st;
+    if (lbm_status st = adjoint_instant(g, k, lam, lcur, a, ws, snap)) return st;
   }
   return LBM_OK;
 }
@@ -1055,7 +1080,7 @@ lbm_status capture_sweep(lbm_grid* g, uint8_t* snap, uint8_t* lam[2], std::vecto
     if (graph) cudaGraphDestroy(graph);
     return st ? st : cuda_check(g, e2, "cudaStreamEndCapture");
   }
-  e = cudaGraphInstantiate(out, graph, 0);
+  e = cudaGraphInstantiate(out, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   return cuda_check(g, e, "cudaGraphInstantiate");
 }
