@@ -152,21 +152,23 @@ lbm_status lbm_init_equilibrium(lbm_grid_t g, int32_t patch, const void* rho, co
  * an unbound grid, LBM_ERR_CUDA for a launch failure. */
 lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps);
 
-/* Autotuner of the stream-collide tile pass.  The TMA kernel comes in
- * variants (load stages in shared memory x CTAs per SM the register
- * allocation aims for) that give identical results; this runs `trials` coarse
- * steps with each variant, CUDA events around them, and keeps the fastest.
+/* Autotuner of the instant schedule.  A variant is a TMA kernel variant (load
+ * stages in shared memory x CTAs per SM the register allocation aims for) and
+ * a schedule of the reconstruction samples (after the TMA pass, or beside it
+ * on the coupling streams): variant v = kernel + n_kernels * schedule.  All
+ * give identical results; this runs `trials` coarse steps with each variant,
+ * CUDA events around them, and keeps the fastest.
  * The state advances by n_variants * trials coarse steps.  chosen (nullable)
  * gets the variant kept, ms_per_step[0 .. min(n, max_variants)) (nullable)
  * the measured time per coarse step of each, n_variants (nullable) their
- * number (1 for the thermal model, which does not use the TMA pass).
+ * number (1 for the thermal model, whose TMA pass has a single variant).
  * Synchronises the bound stream; drops captured step graphs.  Without a call
  * the grid uses variant 0.  The paper has no counterpart. */
 lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms_per_step, int32_t max_variants,
                         int32_t* n_variants);
 
-/* Selects a TMA kernel variant directly (0 .. n_variants - 1); LBM_ERR_ARG
- * out of range. */
+/* Selects a variant of lbm_autotune directly (0 .. n_variants - 1);
+ * LBM_ERR_ARG out of range. */
 lbm_status lbm_set_variant(lbm_grid_t g, int32_t variant);
 
 /* lbm_step replays each coarse step as a CUDA graph, one per buffer parity of

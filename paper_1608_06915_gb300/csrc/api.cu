@@ -52,7 +52,8 @@ struct lbm_grid {
     cudaEvent_t e0, e1;
   };
   bool timing = false;
-  int variant = 0;  // TMA kernel variant (lbm_autotune)
+  int variant = 0;         // TMA kernel variant (lbm_autotune)
+  bool presample = false;  // reconstruction samples beside the TMA pass (lbm_autotune)
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
@@ -91,11 +92,13 @@ struct lbm_grid {
   // coupling chains, all beside each other after the TMA pass of an instant
   cudaStream_t fwd_side[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t fwd_fork = nullptr, fwd_join[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fwd_pre = nullptr;  // the instant's pre-states are ready (before its TMA pass)
   std::vector<cudaEvent_t> patch_done;  // thermal model: a patch's stream-collide has been issued
   ~lbm_grid() {
     for (auto& x : fwd_side)
       if (x) cudaStreamDestroy(x);
     if (fwd_fork) cudaEventDestroy(fwd_fork);
+    if (fwd_pre) cudaEventDestroy(fwd_pre);
     for (auto& x : fwd_join)
       if (x) cudaEventDestroy(x);
     for (auto& x : patch_done)
@@ -230,6 +233,43 @@ lbm_status run_instant(lbm_grid* g, int k) {
   const int storage = hg.desc.storage;
   const int lbgk = hg.desc.mirror_lbgk;
   std::vector<int> active;
+  const bool side = !g->timing;
+  if (side) {
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 3 && !e; ++q)
+      if (!g->fwd_side[q]) e = side_stream(&g->fwd_side[q]);
+    if (!e && !g->fwd_fork) e = cudaEventCreateWithFlags(&g->fwd_fork, cudaEventDisableTiming);
+    if (!e && !g->fwd_pre) e = cudaEventCreateWithFlags(&g->fwd_pre, cudaEventDisableTiming);
+    for (int q = 0; q < 3 && !e; ++q)
+      if (!g->fwd_join[q]) e = cudaEventCreateWithFlags(&g->fwd_join[q], cudaEventDisableTiming);
+    if (e) return cuda_check(g, e, "forward side streams");
+  }
+  // The reconstruction samples and their point passes read only pre-states:
+  // in the isothermal model they may start on the coupling streams before the
+  // TMA pass and run beside it, the explode after the pass finding them done.
+  // That pays where the pass leaves the GPU idle (small grids) and costs where
+  // the pass fills it, so it is a schedule variant that lbm_autotune times.
+  const bool presample = side && !hg.thermal && g->presample;
+  if (presample) {
+    cudaError_t e = cudaEventRecord(g->fwd_pre, g->stream);
+    for (int q = 1; q < 3 && !e; ++q) e = cudaStreamWaitEvent(g->fwd_side[q], g->fwd_pre, 0);
+    for (int lev = 1; lev < L && !e; ++lev) {
+      const int stride = 1 << (L - 1 - lev);
+      if (k % stride || (k / stride) % 2) continue;  // stepped, with the parent active
+      for (size_t pi = 0; pi < hg.P.size() && !e; ++pi) {
+        HostPatch& p = hg.P[pi];
+        if (p.level != lev) continue;
+        HostPatch& q = hg.P[p.parent];
+        cudaStream_t cs = g->fwd_side[1 + pi % 2];
+        e = lbmk::launch_samples(storage, view(g, q), g->base + q.off_f[q.cur], view(g, p), g->base + p.off_f[p.cur],
+                                 at<uint32_t>(g, p.off_smp_node), at<uint8_t>(g, p.off_smp_kind),
+                                 (int64_t)p.smp_node.size(), g->base + p.off_smp_val, (int64_t)p.n_points(),
+                                 q.beta / (2.0 * p.beta), status_ptr(g), cs);
+        if (!e) e = point_passes(g, p, 31, cs);
+      }
+    }
+    if (e) return cuda_check(g, e, "samples");
+  }
   if (!hg.thermal) {
     // TMA tile pass of every patch stepped at this instant: one persistent
     // launch per 8 patches, whatever their levels and sizes
@@ -271,15 +311,9 @@ lbm_status run_instant(lbm_grid* g, int k) {
   // below; its coupling chains then start on the side streams once that
   // patch's stream-collide has been issued (one event per patch).
   cudaStream_t rest = g->stream, cpl[2] = {g->stream, g->stream};
-  const bool side = !g->timing;
   const bool forked = side && !hg.thermal;
   if (side) {
     cudaError_t e = cudaSuccess;
-    for (int q = 0; q < 3 && !e; ++q)
-      if (!g->fwd_side[q]) e = side_stream(&g->fwd_side[q]);
-    if (!e && !g->fwd_fork) e = cudaEventCreateWithFlags(&g->fwd_fork, cudaEventDisableTiming);
-    for (int q = 0; q < 3 && !e; ++q)
-      if (!g->fwd_join[q]) e = cudaEventCreateWithFlags(&g->fwd_join[q], cudaEventDisableTiming);
     if (hg.thermal && g->patch_done.size() != hg.P.size()) {
       g->patch_done.assign(hg.P.size(), nullptr);
       for (auto& x : g->patch_done)
@@ -420,18 +454,20 @@ lbm_status run_instant(lbm_grid* g, int k) {
       } else if (lev > 0 && parent_active) {
         HostPatch& q = hg.P[p.parent];
         const lbmk::PatchDev qv = view(g, q);
-        st = cuda_check(g,
-                        timed(g, 2, lev, (double)p.n_points(),
-                              [&] {
-                                cudaError_t e = lbmk::launch_samples(
-                                    storage, qv, g->base + q.off_f[q.cur], pv, fin, at<uint32_t>(g, p.off_smp_node),
-                                    at<uint8_t>(g, p.off_smp_kind), (int64_t)p.smp_node.size(),
-                                    g->base + p.off_smp_val, (int64_t)p.n_points(), q.beta / (2.0 * p.beta),
-                                    status_ptr(g), cpl[pi % 2]);
-                                return e ? e : point_passes(g, p, 31, cpl[pi % 2]);
-                              }),
-                        "samples");
-        if (st) return st;
+        if (!presample) {  // (otherwise issued before the TMA pass)
+          st = cuda_check(g,
+                          timed(g, 2, lev, (double)p.n_points(),
+                                [&] {
+                                  cudaError_t e = lbmk::launch_samples(
+                                      storage, qv, g->base + q.off_f[q.cur], pv, fin, at<uint32_t>(g, p.off_smp_node),
+                                      at<uint8_t>(g, p.off_smp_kind), (int64_t)p.smp_node.size(),
+                                      g->base + p.off_smp_val, (int64_t)p.n_points(), q.beta / (2.0 * p.beta),
+                                      status_ptr(g), cpl[pi % 2]);
+                                  return e ? e : point_passes(g, p, 31, cpl[pi % 2]);
+                                }),
+                          "samples");
+          if (st) return st;
+        }
         st = cuda_check(g,
                         timed(g, 3, lev, (double)p.ex_node.size(),
                               [&] {
@@ -726,14 +762,16 @@ lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms
                         int32_t* n_variants) {
   if (lbm_status s = check_bound(g)) return s;
   if (trials < 1) return fail(g, LBM_ERR_ARG, "autotune needs at least one trial step");
-  const int nv = g->hg.thermal ? 1 : lbmk::sc_tma_variants(g->hg.desc.storage);
+  const int nt = g->hg.thermal ? 1 : lbmk::sc_tma_variants(g->hg.desc.storage);
+  const int nv = g->hg.thermal ? 1 : 2 * nt;  // TMA kernel variant x sample schedule
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (!e) e = cudaEventCreate(&e1);
   std::vector<float> ms(nv, 0.0f);
   lbm_status st = LBM_OK;
   for (int v = 0; v < nv && !e && !st; ++v) {
-    g->variant = v;
+    g->variant = v % nt;
+    g->presample = v >= nt;
     e = cudaEventRecord(e0, g->stream);
     for (int t = 0; t < trials && !e && !st; ++t) st = coarse_step_eager(g);
     if (!e && !st) e = cudaEventRecord(e1, g->stream);
@@ -748,7 +786,8 @@ lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms
   int best = 0;
   for (int v = 1; v < nv; ++v)
     if (ms[v] < ms[best]) best = v;
-  g->variant = best;
+  g->variant = best % nt;
+  g->presample = best >= nt;
   g->stepped = true;
   g->drop_graphs();
   if (chosen) *chosen = best;
@@ -760,9 +799,11 @@ lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms
 
 lbm_status lbm_set_variant(lbm_grid_t g, int32_t variant) {
   if (!g) return LBM_ERR_ARG;
-  const int nv = g->hg.thermal ? 1 : lbmk::sc_tma_variants(g->hg.desc.storage);
+  const int nt = g->hg.thermal ? 1 : lbmk::sc_tma_variants(g->hg.desc.storage);
+  const int nv = g->hg.thermal ? 1 : 2 * nt;
   if (variant < 0 || variant >= nv) return fail(g, LBM_ERR_ARG, "variant out of range");
-  g->variant = variant;
+  g->variant = variant % nt;
+  g->presample = variant >= nt;
   g->drop_graphs();
   return LBM_OK;
 }

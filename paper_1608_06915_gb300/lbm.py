@@ -313,8 +313,9 @@ class Grid:
         return [out[0], out[1], out[2]]
 
     def autotune(self, trials: int = 2):
-        """Times each TMA kernel variant over `trials` coarse steps (the state
-        advances) and keeps the fastest: dict(chosen, ms_per_step)."""
+        """Times each variant (TMA kernel x schedule of the reconstruction
+        samples) over `trials` coarse steps (the state advances) and keeps the
+        fastest: dict(chosen, ms_per_step)."""
         chosen, n = ctypes.c_int32(), ctypes.c_int32()
         ms = (ctypes.c_float * 16)()
         _check(lib().lbm_autotune(self.handle, int(trials), ctypes.byref(chosen), ms, 16, ctypes.byref(n)),

@@ -352,9 +352,10 @@ def test_graph_replay_matches_direct_launches(storage):
 
 @pytest.mark.parametrize("storage", ["fp32", "fp64", "fp16s"])
 def test_tma_variants_give_identical_results(storage):
-    """The autotuner's kernel variants differ in staging and occupancy only:
-    same bits after several coarse steps on a three-level channel with walls
-    and force, and on the four-level sphere."""
+    """The autotuner's variants differ in staging, occupancy and the schedule
+    of the reconstruction samples only: same bits after several coarse steps
+    on a three-level channel with walls and force, and on the four-level
+    sphere, for each of the four variants."""
     import torch
     for case, fields in [
         (dict(I.channel_small_case(), accel0=(1e-5, 0, 0)),
@@ -362,14 +363,18 @@ def test_tma_variants_give_identical_results(storage):
         (I.sphere_case(scale=8), lambda c: (lambda x, y, z, p, info: I.uniform_fields(x, (0.05, 0.0, 0.0)))),
     ]:
         ga, _ = twin(case, storage, fields(case), oracle=False)
-        gb, _ = twin(case, storage, fields(case), oracle=False)
         ga.set_variant(0)
-        gb.set_variant(1)
         ga.step(5)
-        gb.step(5)
         torch.cuda.synchronize()
-        for p in range(len(ga.patches)):
-            assert torch.equal(ga.get_populations(p), gb.get_populations(p)), (case["name"], p)
+        for v in (1, 2, 3):
+            gb, _ = twin(case, storage, fields(case), oracle=False)
+            gb.set_variant(v)
+            gb.step(5)
+            torch.cuda.synchronize()
+            for p in range(len(ga.patches)):
+                assert torch.equal(ga.get_populations(p), gb.get_populations(p)), (case["name"], v, p)
+        with pytest.raises(Exception):
+            gb.set_variant(4)
 
 
 def test_autotune_reports_and_keeps_the_state_consistent():
