@@ -158,7 +158,8 @@ lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps);
  * on the coupling streams): variant v = kernel + n_kernels * schedule.  All
  * give identical results; this runs `trials` coarse steps with each variant,
  * CUDA events around them, and keeps the fastest.
- * The state advances by n_variants * trials coarse steps.  chosen (nullable)
+ * The state advances by 1 + n_variants * trials coarse steps (an untimed
+ * warm-up step, then the trials).  chosen (nullable)
  * gets the variant kept, ms_per_step[0 .. min(n, max_variants)) (nullable)
  * the measured time per coarse step of each, n_variants (nullable) their
  * number (1 for the thermal model, whose TMA pass has a single variant).

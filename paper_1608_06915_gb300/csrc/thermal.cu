@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(128) k_th_coalesce(PatchDev pc, const R* __res
 // samples: [59][ld] = rho - 1, ux, uy, uz, T - T0, fneq_0..26, gneq_0..26 (child
 // scale), columns [0, ns) of the point space
 template <typename R>
-__global__ void __launch_bounds__(128) k_th_samples(PatchDev pp, const R* __restrict__ fin_p,
+__global__ void __launch_bounds__(128, 4) k_th_samples(PatchDev pp, const R* __restrict__ fin_p,
                                                     const R* __restrict__ gin_p, PatchDev pc,
                                                     const R* __restrict__ fin_c, const R* __restrict__ gin_c,
                                                     const uint32_t* __restrict__ smp_node,
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(128) k_th_samples(PatchDev pp, const R* __rest
 // Targets [0, n_one) read one point of the reconstruction point space, the
 // others interpolate four (the last separable Lagrange pass, Eq. interp).
 template <typename R>
-__global__ void __launch_bounds__(128) k_th_explode(PatchDev pc, R* __restrict__ fo_c, R* __restrict__ go_c,
+__global__ void __launch_bounds__(128, 4) k_th_explode(PatchDev pc, R* __restrict__ fo_c, R* __restrict__ go_c,
                                                     const uint32_t* __restrict__ ex_node,
                                                     const uint4* __restrict__ ex_src, long long n_one, long long n,
                                                     const R* __restrict__ val, long long ld, ThParams<R> tc) {
