@@ -342,9 +342,9 @@ def cuda_arm(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # setup: the autotuner times each variant (TMA kernel x sample schedule) over 2 coarse steps
+    # setup: the autotuner times each variant (TMA kernel x sample schedule) over 4 coarse steps
     # (advancing the state) and keeps the fastest; then the warm-up
-    tune = g.autotune(trials=2)
+    tune = g.autotune(trials=4)
     g.step(args.warmup)
     barrier()
     # timed region: K coarse steps replayed as CUDA graphs, events on the grid's stream

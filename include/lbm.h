@@ -156,10 +156,12 @@ lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps);
  * stages in shared memory x CTAs per SM the register allocation aims for) and
  * a schedule of the reconstruction samples (after the TMA pass, or beside it
  * on the coupling streams): variant v = kernel + n_kernels * schedule.  All
- * give identical results; this runs `trials` coarse steps with each variant,
- * CUDA events around them, and keeps the fastest.
- * The state advances by 1 + n_variants * trials coarse steps (an untimed
- * warm-up step, then the trials).  chosen (nullable)
+ * give identical results; this times `trials` coarse steps of each variant
+ * the way lbm_step runs them (graph replays unless lbm_graphs is off), CUDA
+ * events around them, and keeps the fastest.  The state advances by
+ * 1 + n_variants * (2 + trials) coarse steps: one untimed step first, and
+ * per variant two untimed steps that capture its step graphs before the
+ * trials.  chosen (nullable)
  * gets the variant kept, ms_per_step[0 .. min(n, max_variants)) (nullable)
  * the measured time per coarse step of each, n_variants (nullable) their
  * number (1 for the thermal model, whose TMA pass has a single variant).
