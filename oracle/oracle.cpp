@@ -15,7 +15,7 @@
 //   * KBC split f = k + s + h, mirror state, stabiliser gamma          (Sec. II.A, Eqs. popSplit, f_mirr, gamma_min_approx)
 //   * post-collision state (1-beta) f + beta f^mirr                    (Sec. II, Eq. f_equations)
 //   * exact-difference-method body force, du_f = du_c / r              (Sec. III.A, force paragraph)
-//   * two-population thermal kinetics for Pr <= 1                      (Sec. II.B, Eqs. kinetics_f_KBC_thermal,
+//   * two-population thermal kinetics, Pr <= 1 and Pr > 1              (Sec. II.B, Eqs. kinetics_f_KBC_thermal,
 //                                                                        kinetics_g_entr, grad_general, Table I)
 //   * multi-domain refinement: twin-node non-equilibrium rescaling,
 //     centred four-point Lagrange reconstruction, the five-step
@@ -47,6 +47,11 @@
 //   R7  thermal: T0 = 1/3; f* = f^eq for Pr <= 1; g* from Table I with the
 //       closed-form P^eq; Boussinesq acceleration g*lambda*(T - T_ref) e_z;
 //       thermal walls by anti-bounce-back of g to the wall equilibrium.
+//   R8  thermal, Pr > 1: f* differs from f^eq only by the Grad term of the
+//       non-equilibrium stress, f*_i - f^eq_i = W_i P1_ab (c_ia c_ib -
+//       T0 d_ab) / (2 T0^2) with P1 = P - P^eq (Table I row f* for Pr > 1,
+//       read consistently with R7, where the same Grad form with P^eq is
+//       f^eq itself); the same tensor P1 enters g* (Table I row g*).
 //
 // Parity status: every function above is pinned by tests under tests/
 // (closed forms, invariants, special cases, brute force).
@@ -58,6 +63,7 @@
 #include <cstring>
 #include <stdexcept>
 #include <string>
+#include <utility>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -304,16 +310,64 @@ Pop gstar(const Pop& f, const Pop& g, double rho, const double u[3], double E2rh
   return grad_form(E2rho, Mq, R, T0);
 }
 
+// Non-equilibrium pressure tensor P1 = P - P^eq of f, with the closed-form
+// P^eq = rho T0 delta + rho u u (Sec. II.B, after Table I).
+void noneq_stress(const Pop& f, double rho, const double u[3], double T0, double P1[3][3]) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double P = 0;
+      for (int i = 0; i < Q; ++i) P += cvel(i, a) * cvel(i, b) * f[i];
+      P1[a][b] = P - (rho * T0 * (a == b ? 1.0 : 0.0) + rho * u[a] * u[b]);
+    }
+}
+
+// f* - f^eq for Pr > 1 (Table I row f*, reading R8): the Grad-form term of
+// the non-equilibrium stress, W_i P1_ab (c_ia c_ib - T0 d_ab) / (2 T0^2).
+Pop fstar_minus_feq_gt1(const Pop& f, double rho, const double u[3], double T0) {
+  double P1[3][3];
+  noneq_stress(f, rho, u, T0, P1);
+  Pop d;
+  for (int i = 0; i < Q; ++i) {
+    double quad = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) quad += P1[a][b] * (cvel(i, a) * cvel(i, b) - T0 * (a == b ? 1.0 : 0.0));
+    d[i] = Wi(i) * quad / (2.0 * T0 * T0);
+  }
+  return d;
+}
+
+// Quasi-equilibrium g* for Pr > 1, Table I: moments (2 rho E, q^eq + 2u_b(P_ab - P^eq_ab), R^eq).
+Pop gstar_gt1(const Pop& f, double rho, const double u[3], double E2rho, double T0) {
+  double P1[3][3], Mq[3], R[3][3];
+  noneq_stress(f, rho, u, T0, P1);
+  for (int a = 0; a < 3; ++a) {
+    double corr = 0;
+    for (int b = 0; b < 3; ++b) corr += 2.0 * u[b] * P1[a][b];
+    Mq[a] = E2rho * u[a] + 2.0 * rho * T0 * u[a] + corr;  // q^eq (Eq. qeq_expression) + correction
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double d = (a == b) ? 1.0 : 0.0;
+      R[a][b] = E2rho * (T0 * d + u[a] * u[b]) + 2.0 * rho * T0 * (T0 * d + 2.0 * u[a] * u[b]);
+    }
+  return grad_form(E2rho, Mq, R, T0);
+}
+
 // One thermal collision (Eqs. kinetics_f_KBC_thermal and kinetics_g_entr).
 // With Pr <= 1, f* = f^eq (reading R7), so the f equation is the isothermal
-// one; the Boussinesq acceleration enters through the exact difference method.
+// one; with Pr > 1 it adds 2 (beta - beta1) (f* - f^eq) (reading R8).  The
+// Boussinesq acceleration enters through the exact difference method.
 double thermal_collide(const Pop& f, const Pop& g, double beta, double beta1, double T0, double glambda,
-                       double t_ref, double accel_scale, bool lbgk, Pop& fo, Pop& go) {
+                       double t_ref, double accel_scale, bool lbgk, bool pr_gt1, Pop& fo, Pop& go) {
   ThermalMacro tm = thermal_macro(f, g);
   double du[3] = {0, 0, glambda * (tm.T - t_ref) * accel_scale};
   double gamma = kbc_collide(f, beta, du, lbgk, NAN, fo);
+  if (pr_gt1) {
+    Pop d = fstar_minus_feq_gt1(f, tm.rho, tm.u, T0);
+    for (int i = 0; i < Q; ++i) fo[i] += 2.0 * (beta - beta1) * d[i];
+  }
   Pop ge = geq(tm.rho, tm.u, tm.E2rho, T0);
-  Pop gs = gstar(f, g, tm.rho, tm.u, tm.E2rho, T0);
+  Pop gs = pr_gt1 ? gstar_gt1(f, tm.rho, tm.u, tm.E2rho, T0) : gstar(f, g, tm.rho, tm.u, tm.E2rho, T0);
   for (int i = 0; i < Q; ++i) go[i] = g[i] + 2.0 * beta * (ge[i] - g[i]) + 2.0 * (beta - beta1) * (gs[i] - ge[i]);
   return gamma;
 }
@@ -473,9 +527,12 @@ struct Sim {
   }
 
   // ---- construction -------------------------------------------------------
+  bool pr_gt1() const { return thermal && d.pr > 1.0; }
+
   void build(const Desc& desc) {
     d = desc;
     thermal = d.thermal != 0;
+    if (thermal && !(d.pr > 0.0)) fail("Prandtl number must be positive");
     for (int a = 0; a < 3; ++a)
       if (d.n[a] < 4) fail("domain extent below 4");
     for (int a = 0; a < 3; ++a) {
@@ -544,11 +601,13 @@ struct Sim {
     double beta = 1.0 / (6.0 * d.nu0 + 1.0);
     double beta1 = 0.0;
     if (thermal) {
-      // Pr <= 1: nu from beta, alpha_th from beta1 (Sec. II.B), nu = (1/(2 beta) - 1/2) T0
+      // Sec. II.B: Pr <= 1: nu = (1/(2 beta) - 1/2) T0, alpha_th = (1/(2 beta1) - 1/2) T0;
+      // Pr > 1: the roles of beta and beta1 swap
       double nu = d.nu0;
       double alpha = nu / d.pr;
-      beta = 1.0 / (2.0 * nu / d.t0 + 1.0);
-      beta1 = 1.0 / (2.0 * alpha / d.t0 + 1.0);
+      const double b_nu = 1.0 / (2.0 * nu / d.t0 + 1.0), b_alpha = 1.0 / (2.0 * alpha / d.t0 + 1.0);
+      beta = pr_gt1() ? b_alpha : b_nu;
+      beta1 = pr_gt1() ? b_nu : b_alpha;
     }
     std::vector<double> betas(nlev), betas1(nlev);
     for (int l = 0; l < nlev; ++l) {
@@ -687,7 +746,7 @@ struct Sim {
       if (!p.vpre[m]) { p.vpost[m] = 0; continue; }
       if (thermal)
         p.gamma[m] = thermal_collide(p.pre[m], p.gpre[m], p.beta, p.beta1, d.t0, d.glambda, d.t_ref, scale,
-                                     d.mirror_lbgk != 0, p.post[m], p.gpost[m]);
+                                     d.mirror_lbgk != 0, pr_gt1(), p.post[m], p.gpost[m]);
       else
         p.gamma[m] = kbc_collide(p.pre[m], p.beta, du, d.mirror_lbgk != 0, NAN, p.post[m]);
       p.vpost[m] = 1;
@@ -724,9 +783,12 @@ struct Sim {
     ThermalMacro tm = thermal_macro(f, g);
     Pop fe = feq(tm.rho, tm.u);
     Pop ge = geq(tm.rho, tm.u, tm.E2rho, d.t0);
-    for (int i = 0; i < Q; ++i) fo[i] = fe[i] + ff * (f[i] - fe[i]);
-    // g: Sec. III.A thermal model, Pr <= 1
+    // Sec. III.A thermal model: for Pr <= 1, f^neq and P1 scale with the beta
+    // ratio and the rest of g^neq with the beta1 ratio; for Pr > 1 the two
+    // ratios swap (Eq. f_neq_rescaling_thr_Prgr1 and the g rescaling after it)
     double fg = beta1_s / (r_st * beta1_t);
+    if (pr_gt1()) std::swap(ff, fg);
+    for (int i = 0; i < Q; ++i) fo[i] = fe[i] + ff * (f[i] - fe[i]);
     double P1s[3][3], P1t[3][3];
     p1_tensor(f, fe, P1s);
     for (int a = 0; a < 3; ++a)
@@ -1205,11 +1267,11 @@ void orc_geq(double rho, const double* u, double T, double t0, double* out) {
 }
 
 double orc_thermal_collide(const double* f, const double* g, double beta, double beta1, double t0, double glambda,
-                           double t_ref, double* fo, double* go) {
+                           double t_ref, int pr_gt1, double* fo, double* go) {
   Pop pf, pg, pfo, pgo;
   std::memcpy(pf.data(), f, sizeof(double) * Q);
   std::memcpy(pg.data(), g, sizeof(double) * Q);
-  double gm = thermal_collide(pf, pg, beta, beta1, t0, glambda, t_ref, 1.0, false, pfo, pgo);
+  double gm = thermal_collide(pf, pg, beta, beta1, t0, glambda, t_ref, 1.0, false, pr_gt1 != 0, pfo, pgo);
   std::memcpy(fo, pfo.data(), sizeof(double) * Q);
   std::memcpy(go, pgo.data(), sizeof(double) * Q);
   return gm;

@@ -92,7 +92,7 @@ def lib():
             L.orc_geq.argtypes = [ctypes.c_double, dp, ctypes.c_double, ctypes.c_double, dp]
             L.orc_thermal_collide.restype = ctypes.c_double
             L.orc_thermal_collide.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                              ctypes.c_double, ctypes.c_double, dp, dp]
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp]
             L.orc_lagrange_weights.argtypes = [dp]
             L.orc_set_threads.argtypes = [ctypes.c_int]
             L.orc_max_threads.restype = ctypes.c_int
@@ -137,10 +137,11 @@ def geq(rho: float, u, T: float, t0: float = 1.0 / 3.0) -> np.ndarray:
     return out
 
 
-def thermal_collide(f, g, beta, beta1, t0=1.0 / 3.0, glambda=0.0, t_ref=0.0):
+def thermal_collide(f, g, beta, beta1, t0=1.0 / 3.0, glambda=0.0, t_ref=0.0, pr_gt1=False):
+    """One thermal collision of (f, g); pr_gt1 selects the Pr > 1 row of Table I."""
     fo, go = np.empty(Q), np.empty(Q)
     gm = lib().orc_thermal_collide(_dp(_f64(f)), _dp(_f64(g)), float(beta), float(beta1), float(t0),
-                                   float(glambda), float(t_ref), _dp(fo), _dp(go))
+                                   float(glambda), float(t_ref), 1 if pr_gt1 else 0, _dp(fo), _dp(go))
     return fo, go, gm
 
 

@@ -131,8 +131,8 @@ def rbc_case(n=(256, 256, 128), l1=12, l2=6, ra: float = 1e7, pr: float = 0.7, u
                 wall_lo=-0.125)
 
 
-def rbc_small_case() -> dict:
-    return rbc_case(n=(8, 8, 32), l1=8, l2=4, ra=1e5)
+def rbc_small_case(pr: float = 0.7) -> dict:
+    return rbc_case(n=(8, 8, 32), l1=8, l2=4, ra=1e5, pr=pr)
 
 
 # ---------------------------------------------------------------------------

@@ -446,6 +446,126 @@ def test_thermal_heat_flux_combination_relaxes_with_beta1():
         assert np.max(np.abs(x1 - (1 - 2 * beta1) * x0)) < 1e-2 * np.max(np.abs(x0)), (x0, x1)
 
 
+# --- thermal pins, Pr > 1 (Table I rows f*, g* for Pr > 1; Sec. III.A rescaling)
+def _stress(f):
+    return np.einsum("i,ia,ib->ab", f, C, C)
+
+
+def _thermal_state(rng, t0=1.0 / 3.0):
+    rho = rng.uniform(0.95, 1.05)
+    u = rng.uniform(-0.04, 0.04, 3)
+    T = t0 * (1 + 0.02 * rng.uniform(-1, 1))
+    f = O.feq(rho, u) * (1 + 0.01 * rng.uniform(-1, 1, 27))
+    g = O.geq(rho, u, T) * (1 + 0.01 * rng.uniform(-1, 1, 27))
+    return f, g
+
+
+def test_thermal_pr_gt1_conserves_mass_momentum_energy():
+    rng = np.random.default_rng(21)
+    for _ in range(10):
+        f, g = _thermal_state(rng)
+        fo, go, _ = O.thermal_collide(f, g, 0.95, 0.8, pr_gt1=True)
+        assert abs(fo.sum() - f.sum()) < 1e-14
+        assert np.max(np.abs(C.T @ fo - C.T @ f)) < 1e-14
+        assert abs(go.sum() - g.sum()) < 1e-14
+
+
+def test_thermal_pr_gt1_deviatoric_stress_relaxes_with_beta1():
+    # Pr > 1: (1 - beta) f + beta f^mirr relaxes the deviatoric stress with beta
+    # whatever gamma (it lives in ds alone), and 2 (beta - beta1)(f* - f^eq)
+    # adds 2 (beta - beta1) P1 (fourth-moment isotropy of D3Q27 at T0 = 1/3),
+    # so the deviatoric part of P - P^eq goes to (1 - 2 beta1) times itself:
+    # the viscosity follows beta1, as Sec. II.B states for Pr > 1.  At u = 0
+    # the product-form f^eq has exactly the closed-form P^eq, so the identity
+    # is exact; at u != 0 they differ at O(u^4).
+    rng = np.random.default_rng(22)
+    t0 = 1.0 / 3.0
+    dev = lambda P: P - np.trace(P) / 3.0 * np.eye(3)
+    beta, beta1 = 0.97, 0.85
+    for k in range(10):
+        rho0 = rng.uniform(0.95, 1.05)
+        if k < 5:  # zero momentum: a perturbation symmetric under c -> -c
+            d = 1e-3 * rng.uniform(-1, 1, 27)
+            f = rho0 * W + W * (d + d[OPP])
+        else:
+            f, _ = _thermal_state(rng)
+        g = O.geq(f.sum(), (C.T @ f) / f.sum(), t0)
+        fo, _, gm = O.thermal_collide(f, g, beta, beta1, pr_gt1=True)
+        rho, u = f.sum(), (C.T @ f) / f.sum()
+        Peq = rho * t0 * np.eye(3) + rho * np.outer(u, u)
+        P1, P1o = _stress(f) - Peq, _stress(fo) - Peq
+        assert abs(gm - 2.0) > 1e-3  # the entropic stabiliser is active
+        err = np.max(np.abs(dev(P1o) - (1 - 2 * beta1) * dev(P1)))
+        if k < 5:
+            assert np.max(np.abs(u)) < 1e-15
+            assert err < 1e-15, err  # round-off of stresses of order rho T0
+        else:
+            assert err < 1e-2 * np.max(np.abs(P1)), err
+
+
+def test_thermal_pr_gt1_heat_flux_closed_form():
+    # Pr > 1, Table I row g*: q' - q^eq = (1 - 2 beta)(q - q^eq) + 4 (beta - beta1) (P - P^eq) u
+    rng = np.random.default_rng(23)
+    t0 = 1.0 / 3.0
+    for _ in range(10):
+        f, g = _thermal_state(rng)
+        beta, beta1 = 0.97, 0.85
+        _, go, _ = O.thermal_collide(f, g, beta, beta1, pr_gt1=True)
+        rho, u = f.sum(), (C.T @ f) / f.sum()
+        E2 = g.sum()
+        qeq = E2 * u + 2 * rho * t0 * u
+        P1 = _stress(f) - (rho * t0 * np.eye(3) + rho * np.outer(u, u))
+        expect = (1 - 2 * beta) * (C.T @ g - qeq) + 4 * (beta - beta1) * P1 @ u
+        assert np.max(np.abs((C.T @ go - qeq) - expect)) < 1e-15
+        # at rest the heat flux relaxes with beta, the diffusivity's parameter for Pr > 1
+        f0 = O.feq(rho, np.zeros(3))
+        _, go0, _ = O.thermal_collide(f0, g, beta, beta1, pr_gt1=True)
+        assert np.max(np.abs(C.T @ go0 - (1 - 2 * beta) * (C.T @ g))) < 1e-15
+
+
+@pytest.mark.parametrize("pr", [0.7, 2.0])
+def test_thermal_level_parameters_give_nu_and_alpha(pr):
+    # Sec. II.B: nu = (1/(2 beta) - 1/2) T0 and alpha = (1/(2 beta1) - 1/2) T0 for
+    # Pr <= 1, the roles swapped for Pr > 1; acoustic scaling doubles both per level
+    case = I.rbc_small_case(pr=pr)
+    o = O.Oracle(case)
+    t0 = case["thermal"].get("t0", 1.0 / 3.0)
+    for info in o.patches:
+        b, b1 = info["beta"], info["beta1"]
+        b_nu, b_al = (b, b1) if pr <= 1 else (b1, b)
+        nu = (0.5 / b_nu - 0.5) * t0
+        alpha = (0.5 / b_al - 0.5) * t0
+        assert abs(nu - case["nu0"] * 2 ** info["level"]) < 1e-14
+        assert abs(nu / alpha - pr) < 1e-12
+
+
+def test_conduction_state_is_steady_pr_gt1():
+    # The conduction state at Pr = 2 over three levels, 200 coarse steps.  The
+    # interfaces carry the heat flux through the g rescaling: with the beta and
+    # beta1 ratios of Sec. III.A left unswapped for Pr > 1, the deviation from
+    # the linear profile reaches 9.5e-4 dT here; it stays below 2.1e-4.
+    case = I.rbc_small_case(pr=2.0)
+    case["thermal"] = dict(case["thermal"], glambda=0.0)
+    th = case["thermal"]
+    H = case["height"]
+
+    def fields(x, y, z, p, info):
+        T = th["wall_T"][4] + (th["wall_T"][5] - th["wall_T"][4]) * (z - case["wall_lo"]) / H
+        return np.ones_like(z), np.zeros((3,) + z.shape), T
+
+    o = make(case, fields)
+    o.step(200)
+    worst = 0.0
+    for p, info in enumerate(o.patches):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        _, u, T, _ = o.moments(p)
+        m = o.mask(p) == 1
+        Tex = th["wall_T"][4] + (th["wall_T"][5] - th["wall_T"][4]) * (z - case["wall_lo"]) / H
+        worst = max(worst, np.max(np.abs(T[m] - Tex[m])) / th["dT"])
+        assert np.max(np.abs(u[:, m])) < 1e-6
+    assert worst < 5e-4, worst
+
+
 def _ball_case(n=16, boxes=(), level=0, d=6.0, nu0=0.02):
     return dict(name="ball", n=(n, n, n), periodic=(1, 1, 1), walls=(0,) * 6, inflow_axis=-1, u_in=(0, 0, 0),
                 boxes=list(boxes), solid=I.sphere_mask(level, (n / 2, n / 2, n / 2), d), nu0=nu0,
