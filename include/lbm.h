@@ -7,7 +7,7 @@
  *   - per level, the lattice Boltzmann equation with the KBC mirror state and
  *     entropic stabiliser gamma (Sec. II.A, Eqs. f_equations, feq_iso,
  *     popSplit, f_mirr, gamma_min_approx);
- *   - the two-population thermal model for Pr <= 1 (Sec. II.B);
+ *   - the two-population thermal model, Pr <= 1 and Pr > 1 (Sec. II.B);
  *   - multi-domain refinement with r = 2: twin-node non-equilibrium
  *     rescaling (Sec. III.A, Eq. f_neq_rescaling_iso and the thermal g
  *     rule), centred four-point Lagrange reconstruction (Sec. III.B,
@@ -97,7 +97,8 @@ typedef struct {
   double nu0;               /* coarse kinematic viscosity (beta_0 from Eq. visc) */
   double accel0[3];         /* body acceleration, coarse units (isothermal model) */
   lbm_model model;
-  double pr, t0, glambda, t_ref; /* thermal: Prandtl (<= 1), T0, g*lambda, Boussinesq T_ref */
+  double pr, t0, glambda, t_ref; /* thermal: Prandtl (> 0; Table I's Pr > 1 rows above 1),
+                                   T0 (1/3), g*lambda, Boussinesq T_ref */
   double wall_T[6];         /* thermal wall temperatures per wall face (bit order of walls) */
   lbm_storage storage;
   int32_t mirror_lbgk;      /* 1: LBGK mirror state (gamma fixed at 2) */

@@ -176,6 +176,7 @@ lbmk::ThermalLevel thermal_level(const lbm_grid* g, const HostPatch& p) {
   L.beta = p.beta;
   L.beta1 = p.beta1;
   L.lbgk = d.mirror_lbgk;
+  L.pr_gt1 = g->hg.pr_gt1 ? 1 : 0;
   return L;
 }
 
@@ -400,12 +401,13 @@ lbm_status run_instant(lbm_grid* g, int k) {
           st = cuda_check(g,
                           timed(g, 1, lev, (double)c.cf_parent.size(),
                                 [&] {
+                                  double ff = 2.0 * c.beta / p.beta, fg = 2.0 * c.beta1 / p.beta1;
+                                  if (hg.pr_gt1) std::swap(ff, fg);  // Sec. III.A, Pr > 1
                                   return lbmk::launch_th_coalesce(
                                       storage, cv, g->base + c.off_f[c.cur], g->base + c.off_g[c.cur], pv, fout,
                                       g->base + p.off_g[1 - p.cur], at<uint32_t>(g, c.off_cf_parent),
-                                      at<uint32_t>(g, c.off_cf_child), (int64_t)c.cf_parent.size(),
-                                      2.0 * c.beta / p.beta, 2.0 * c.beta1 / p.beta1, thermal_level(g, c),
-                                      thermal_level(g, p), status_ptr(g), cpl[(pi + 1) % 2]);
+                                      at<uint32_t>(g, c.off_cf_child), (int64_t)c.cf_parent.size(), ff, fg,
+                                      thermal_level(g, c), thermal_level(g, p), status_ptr(g), cpl[(pi + 1) % 2]);
                                 }),
                           "thermal coalesce");
           if (st) return st;
@@ -429,13 +431,14 @@ lbm_status run_instant(lbm_grid* g, int k) {
         st = cuda_check(g,
                         timed(g, 2, lev, (double)p.n_points(),
                               [&] {
+                                double ff = q.beta / (2.0 * p.beta), fg = q.beta1 / (2.0 * p.beta1);
+                                if (hg.pr_gt1) std::swap(ff, fg);  // Sec. III.A, Pr > 1
                                 cudaError_t e = lbmk::launch_th_samples(
                                     storage, qv, g->base + q.off_f[q.cur], g->base + q.off_g[q.cur], pv, fin,
                                     g->base + p.off_g[p.cur], at<uint32_t>(g, p.off_smp_node),
                                     at<uint8_t>(g, p.off_smp_kind), (int64_t)p.smp_node.size(),
-                                    g->base + p.off_smp_val, (int64_t)p.n_points(), q.beta / (2.0 * p.beta),
-                                    q.beta1 / (2.0 * p.beta1), thermal_level(g, q), thermal_level(g, p),
-                                    status_ptr(g), cpl[pi % 2]);
+                                    g->base + p.off_smp_val, (int64_t)p.n_points(), ff, fg, thermal_level(g, q),
+                                    thermal_level(g, p), status_ptr(g), cpl[pi % 2]);
                                 return e ? e : point_passes(g, p, 59, cpl[pi % 2]);
                               }),
                         "thermal samples");

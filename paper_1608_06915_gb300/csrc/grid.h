@@ -94,6 +94,7 @@ struct HostGrid {
   std::vector<HostPatch> P;
   int nlev = 1;
   bool thermal = false;
+  bool pr_gt1 = false;  // thermal model in the Pr > 1 regime (Table I)
   size_t pop_bytes = 4;   // bytes per stored population value
   size_t real_bytes = 4;  // bytes of the compute type (samples, outputs)
 

@@ -27,6 +27,7 @@ struct ThermalLevel {
   double twd[6];
   double glam, tref_d, beta, beta1;
   int lbgk;
+  int pr_gt1;  // Pr > 1 rows of Table I
 };
 
 cudaError_t launch_th_tiles(int storage, const PatchDev& p, const void* fin, const void* gin, void* fout, void* gout,

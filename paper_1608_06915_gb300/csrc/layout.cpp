@@ -14,6 +14,7 @@
 // child node at that position.
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <functional>
 #include <unordered_map>
@@ -153,7 +154,9 @@ std::string build_layout(HostGrid& g) {
       (g.periodic(d.inflow_axis) || g.wall(d.inflow_axis, 0) || g.wall(d.inflow_axis, 1)))
     return "inflow axis must be non-periodic and without walls";
   if (d.nu0 <= 0) return "nu0 must be positive";
-  if (g.thermal && (d.pr <= 0 || d.pr > 1)) return "thermal model implemented for 0 < Pr <= 1";
+  if (g.thermal && !(d.pr > 0)) return "Prandtl number must be positive";
+  if (g.thermal && std::fabs(d.t0 - 1.0 / 3.0) > 1e-12) return "thermal model needs T0 = 1/3 (D3Q27)";
+  g.pr_gt1 = g.thermal && d.pr > 1.0;
 
   g.P.clear();
   HostPatch root;
@@ -228,8 +231,11 @@ std::string build_layout(HostGrid& g) {
   // relaxation parameters (Eq. visc, Sec. II.B, Sec. III.A)
   double beta, beta1 = 0;
   if (g.thermal) {
-    beta = 1.0 / (2.0 * d.nu0 / d.t0 + 1.0);
-    beta1 = 1.0 / (2.0 * (d.nu0 / d.pr) / d.t0 + 1.0);
+    // Sec. II.B: for Pr <= 1 beta sets nu and beta1 alpha_th; for Pr > 1 they swap
+    const double b_nu = 1.0 / (2.0 * d.nu0 / d.t0 + 1.0);
+    const double b_alpha = 1.0 / (2.0 * (d.nu0 / d.pr) / d.t0 + 1.0);
+    beta = g.pr_gt1 ? b_alpha : b_nu;
+    beta1 = g.pr_gt1 ? b_nu : b_alpha;
   } else {
     beta = 1.0 / (6.0 * d.nu0 + 1.0);
   }

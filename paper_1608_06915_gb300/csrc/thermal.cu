@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(128) k_th_tiles(PatchDev p, const R* __restric
   if (!(ty == T_BULK || ty == T_BC || (ty == T_D1 && odd))) return;
   R f[27], g[27];
   pull_th<R>(p, fin, gin, x, y, z, f, g, tp.twd, status);
-  thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0);
+  thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0, tp.pr_gt1 != 0);
   store2(p, fout, gout, own, f, g);
 }
 
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(128) k_th_coalesce(PatchDev pc, const R* __res
     f[i] = fe[i] + fn[i];
     g[i] = ge[i] + gn[i];
   });
-  thermal_collide<R>(f, g, tpar.beta, tpar.beta1, tpar.glam, tpar.tref_d, tpar.lbgk != 0);
+  thermal_collide<R>(f, g, tpar.beta, tpar.beta1, tpar.glam, tpar.tref_d, tpar.lbgk != 0, tpar.pr_gt1 != 0);
   store2(pp, fo_p, go_p, cf_parent[k], f, g);
 }
 
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(128, 4) k_th_explode(PatchDev pc, R* __restric
     f[i] += fe[i];
     g[i] += ge[i];
   });
-  thermal_collide<R>(f, g, tc.beta, tc.beta1, tc.glam, tc.tref_d, tc.lbgk != 0);
+  thermal_collide<R>(f, g, tc.beta, tc.beta1, tc.glam, tc.tref_d, tc.lbgk != 0, tc.pr_gt1 != 0);
   store2(pc, fo_c, go_c, ex_node[k], f, g);
 }
 
@@ -206,7 +206,7 @@ __global__ void k_th_moments(PatchDev p, const R* __restrict__ fin, const R* __r
     v[2] = s.uy;
     v[3] = (double)s.uz + 0.5 * duz;
     v[4] = 1.0 / 3.0 + (double)s.T_d;
-    if (gamma_o) v[5] = thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0);
+    if (gamma_o) v[5] = thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0, tp.pr_gt1 != 0);
   }
   auto st = [&](void* a, long long i, double val) {
     if (!a) return;

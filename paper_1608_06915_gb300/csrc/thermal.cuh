@@ -73,9 +73,12 @@ __device__ __forceinline__ R wcv3(R vx, R vy, R vz) {
 }
 
 // One thermal collision of deviation populations (f, g) in place; returns gamma.
+// Pr <= 1: f* = f^eq and g* carries q - 2 u.(P - P^eq) (Table I); Pr > 1:
+// f* - f^eq is the Grad term W_i (P - P^eq)_ab (c_ia c_ib - T0 d_ab)/(2 T0^2)
+// and g* carries q^eq + 2 u.(P - P^eq), with the closed-form P^eq.
 template <typename R>
 __device__ __forceinline__ R thermal_collide(R (&f)[27], R (&g)[27], R beta, R beta1, R glam, R tref_d,
-                                             bool lbgk) {
+                                             bool lbgk, bool pr_gt1) {
   ThState<R> s;
   thermal_state(f, g, s);
   // pre-collision moments: P - P^eq = P~ + T0 d - rho T0 d - rho u u, q = sum c g
@@ -98,9 +101,12 @@ __device__ __forceinline__ R thermal_collide(R (&f)[27], R (&g)[27], R beta, R b
                       {P[3] - s.rho * u[1] * u[0], P[1] - rt3 - s.rho * u[1] * u[1], P[5] - s.rho * u[1] * u[2]},
                       {P[4] - s.rho * u[2] * u[0], P[5] - s.rho * u[2] * u[1], P[2] - rt3 - s.rho * u[2] * u[2]}};
   const R qc = R(1) + s.e_t + R(2.0 / 3.0) * s.rho;  // q^eq = (2 rho E + 2 rho T0) u
-  R X[3];
+  R X[3];  // (g* - g^eq) first moment
 #pragma unroll
-  for (int a = 0; a < 3; ++a) X[a] = q[a] - qc * u[a] - R(2) * (Pd[a][0] * u[0] + Pd[a][1] * u[1] + Pd[a][2] * u[2]);
+  for (int a = 0; a < 3; ++a) {
+    const R Pu2 = R(2) * (Pd[a][0] * u[0] + Pd[a][1] * u[1] + Pd[a][2] * u[2]);
+    X[a] = pr_gt1 ? Pu2 : q[a] - qc * u[a] - Pu2;
+  }
   R ge[27];
   geq_dev(s.rho_t, s.rho, s.ux, s.uy, s.uz, s.e_t, ge);
   const R b2 = R(2) * beta, b12 = R(2) * (beta - beta1);
@@ -110,7 +116,24 @@ __device__ __forceinline__ R thermal_collide(R (&f)[27], R (&g)[27], R beta, R b
   });
   const R duz = glam * (s.T_d - tref_d);
   // f is still the pre-collision state: its moments are those of thermal_state
-  return kbc_collide_m<R, 4>(f, s.rho_t, s.rho, s.ux, s.uy, s.uz, beta, R(0), R(0), duz, lbgk);
+  const R gamma = kbc_collide_m<R, 4>(f, s.rho_t, s.rho, s.ux, s.uy, s.uz, beta, R(0), R(0), duz, lbgk);
+  if (pr_gt1) {
+    // 2 (beta - beta1)(f* - f^eq) at T0 = 1/3: 9 (beta - beta1) W_i Pd_ab (c_ia c_ib - d_ab / 3)
+    const R k9 = R(9) * (beta - beta1);
+    const R tr3 = (Pd[0][0] + Pd[1][1] + Pd[2][2]) * R(1.0 / 3.0);
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      R v = -tr3;
+      if constexpr (CX(i) != 0) v += Pd[0][0];
+      if constexpr (CY(i) != 0) v += Pd[1][1];
+      if constexpr (CZ(i) != 0) v += Pd[2][2];
+      if constexpr (CX(i) * CY(i) != 0) v += R(2 * CX(i) * CY(i)) * Pd[0][1];
+      if constexpr (CX(i) * CZ(i) != 0) v += R(2 * CX(i) * CZ(i)) * Pd[0][2];
+      if constexpr (CY(i) * CZ(i) != 0) v += R(2 * CY(i) * CZ(i)) * Pd[1][2];
+      f[i] += k9 * R(WI(i)) * v;
+    });
+  }
+  return gamma;
 }
 
 // Non-equilibrium rescaling of a thermal pair from a level with (beta_s, beta1_s)
@@ -225,6 +248,7 @@ struct ThParams {
   R tref_d;  // T_ref - T0
   R beta, beta1;
   int lbgk;
+  int pr_gt1;  // Pr > 1 rows of Table I
 };
 
 template <typename R>
@@ -246,6 +270,7 @@ ThParams<R> th_params(const ThermalLevel& L) {
   t.beta = (R)L.beta;
   t.beta1 = (R)L.beta1;
   t.lbgk = L.lbgk;
+  t.pr_gt1 = L.pr_gt1;
   return t;
 }
 

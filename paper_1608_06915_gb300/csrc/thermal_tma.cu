@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(160) k_th_tma(const __grid_constant__ ThMaps<R
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
-    if (x < p.dim[0]) thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0);
+    if (x < p.dim[0]) thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0, tp.pr_gt1 != 0);
     if (lane == 0) bulk_wait_read<0>();
     __syncwarp();
     unsigned char* segf = ostage + warp * C::OSEGB;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(128) k_th_nodes(PatchDev p, const R* __restric
   const int z = (int)(own / ((long long)p.nxp * p.dim[1]));
   R f[27], g[27];
   pull_th<R>(p, fin, gin, x, y, z, f, g, tp.twd, status);
-  thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0);
+  thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0, tp.pr_gt1 != 0);
   store2(p, fout, gout, own, f, g);
 }
 

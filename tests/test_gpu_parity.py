@@ -295,10 +295,12 @@ def _rbc(case):
     return lambda x, y, z, p, info: I.rbc_fields(case, info["level"], info["org"], info["dim"])
 
 
-def test_rbc_small_fp64_every_step():
+@pytest.mark.parametrize("pr", [0.7, 2.0])
+def test_rbc_small_fp64_every_step(pr):
     """Plates with anti-bounce-back, Boussinesq force, two wall bands per level:
-    f and g against the oracle after every coarse step."""
-    case = I.rbc_small_case()
+    f and g against the oracle after every coarse step, in both Prandtl regimes
+    of Table I (Pr <= 1 and Pr > 1)."""
+    case = I.rbc_small_case(pr=pr)
     g, o = twin(case, "fp64", _rbc(case))
     for s in range(4):
         g.step(1)
@@ -307,8 +309,9 @@ def test_rbc_small_fp64_every_step():
         assert df < 1e-12 and dg < 1e-12, (s, df, dg)
 
 
-def test_rbc_small_fp32_temperature():
-    case = I.rbc_small_case()
+@pytest.mark.parametrize("pr", [0.7, 2.0])
+def test_rbc_small_fp32_temperature(pr):
+    case = I.rbc_small_case(pr=pr)
     g, o = twin(case, "fp32", _rbc(case))
     g.step(20)
     o.step(20)
