@@ -398,6 +398,8 @@ struct Desc {
   int32_t thermal;
   double pr, t0, glambda, t_ref;
   double wall_T[6];
+  double solid_T;            // thermal: temperature of solid surfaces
+  int32_t solid_isothermal;  // thermal: 1 = solid surfaces held at solid_T, 0 = adiabatic
 };
 
 struct Patch {
@@ -700,18 +702,19 @@ struct Sim {
           }
         }
         if (!ok) break;
-        bool bounce = wall_axis >= 0;
+        bool bounce = wall_axis >= 0, solid_wall = false;
         if (!bounce) {
           wrap(lev, S);
-          bounce = solid_at(lev, S);
+          bounce = solid_wall = solid_at(lev, S);
         }
         if (bounce) {
           if (!p.vpost[m]) { ok = false; break; }
           p.pre[m][i] = p.post[m][opposite(i)];
           if (thermal) {
-            if (wall_axis >= 0) {
-              // anti-bounce-back to the wall equilibrium at rest, temperature wall_T
-              double Tw = d.wall_T[2 * wall_axis + wall_side];
+            if (wall_axis >= 0 || (solid_wall && d.solid_isothermal)) {
+              // anti-bounce-back to the wall equilibrium at rest, temperature
+              // wall_T of the face, or solid_T of an isothermal solid surface
+              double Tw = wall_axis >= 0 ? d.wall_T[2 * wall_axis + wall_side] : d.solid_T;
               double rho = 0;
               for (int k = 0; k < Q; ++k) rho += p.post[m][k];
               double zero[3] = {0, 0, 0};
@@ -1049,6 +1052,8 @@ typedef struct {
   int32_t thermal;
   double pr, t0, glambda, t_ref;
   double wall_T[6];
+  double solid_T;
+  int32_t solid_isothermal;
 } orc_desc;
 
 static std::string g_last_error;
@@ -1095,6 +1100,8 @@ void* orc_create(const orc_desc* cd) {
     d.glambda = cd->glambda;
     d.t_ref = cd->t_ref;
     std::memcpy(d.wall_T, cd->wall_T, sizeof d.wall_T);
+    d.solid_T = cd->solid_T;
+    d.solid_isothermal = cd->solid_isothermal;
     try {
       s->build(d);
     } catch (...) {

@@ -59,6 +59,8 @@ class OrcDesc(ctypes.Structure):
         ("glambda", ctypes.c_double),
         ("t_ref", ctypes.c_double),
         ("wall_T", ctypes.c_double * 6),
+        ("solid_T", ctypes.c_double),
+        ("solid_isothermal", ctypes.c_int32),
     ]
 
 
@@ -177,7 +179,8 @@ class Oracle:
     ``(level, lo, hi)`` in coarse units), ``solid`` (None or dict with
     ``level``, ``lo`` and a uint8 ``mask`` indexed [z][y][x]), ``nu0``,
     ``accel0``, ``mirror_lbgk`` and ``thermal`` (None or dict with ``pr``,
-    ``t0``, ``glambda``, ``t_ref``, ``wall_T``).
+    ``t0``, ``glambda``, ``t_ref``, ``wall_T`` and, for isothermal solid
+    surfaces, ``solid_T``).
     """
 
     def __init__(self, case: dict):
@@ -217,6 +220,9 @@ class Oracle:
             d.glambda = float(th["glambda"])
             d.t_ref = float(th["t_ref"])
             d.wall_T[:] = [float(v) for v in th["wall_T"]]
+            if th.get("solid_T") is not None:  # isothermal solid surfaces
+                d.solid_T = float(th["solid_T"])
+                d.solid_isothermal = 1
         else:
             d.t0 = 1.0 / 3.0
         self.thermal = th is not None

@@ -135,6 +135,38 @@ def rbc_small_case(pr: float = 0.7) -> dict:
     return rbc_case(n=(8, 8, 32), l1=8, l2=4, ra=1e5, pr=pr)
 
 
+def heated_slab_case(n=(4, 4, 16), slab: int = 3, refined: bool = False, pr: float = 0.7, nu0: float = 0.02,
+                     dT: float = 0.01) -> dict:
+    """Conduction between an isothermal solid slab and a cold plate: walls at
+    z, a solid slab filling the first ``slab`` coarse layers at T0 + dT/2 (the
+    wall below it is never seen by the fluid and held at T0 - dT), the top
+    plate at T0 - dT/2, no buoyancy.  With ``refined`` a level-1 band covers
+    the slab and the layers above it, and the slab is given on level 1."""
+    nx, ny, nz = n
+    boxes = []
+    if refined:
+        boxes = [(1, (0, 0, 0), (nx - 1, ny - 1, slab + 6))]
+        lev, s = 1, 2
+    else:
+        lev, s = 0, 1
+    mask = np.ones((slab * s, ny * s, nx * s), dtype=np.uint8)
+    th = dict(pr=pr, t0=T0, glambda=0.0, t_ref=T0, dT=dT,
+              wall_T=(0, 0, 0, 0, T0 - dT, T0 - dT / 2), solid_T=T0 + dT / 2)
+    # fluid between the slab surface (half a level-lev spacing above its top
+    # layer) and the top plate (half a coarse spacing above the last node)
+    z_lo = (slab * s - 0.5) / s
+    z_hi = nz - 0.5
+    return dict(name="slab", n=n, periodic=(1, 1, 0), walls=(0, 0, 0, 0, 1, 1), inflow_axis=-1, u_in=(0, 0, 0),
+                boxes=boxes, solid=dict(level=lev, lo=(0, 0, 0), mask=mask), nu0=nu0, accel0=(0, 0, 0),
+                mirror_lbgk=False, thermal=th, z_lo=z_lo, z_hi=z_hi)
+
+
+def heated_slab_profile(case: dict, z):
+    """Linear conduction profile of heated_slab_case at coarse height z."""
+    th = case["thermal"]
+    return th["solid_T"] + (th["wall_T"][5] - th["solid_T"]) * (z - case["z_lo"]) / (case["z_hi"] - case["z_lo"])
+
+
 # ---------------------------------------------------------------------------
 # initial fields, evaluated at node positions given in coarse units
 

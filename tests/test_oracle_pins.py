@@ -566,6 +566,30 @@ def test_conduction_state_is_steady_pr_gt1():
     assert worst < 5e-4, worst
 
 
+@pytest.mark.parametrize("refined", [False, True])
+def test_isothermal_solid_conduction(refined):
+    # Sec. IV heated-sphere wall, on a flat solid surface: a slab held at T_s
+    # below a cold plate.  The linear profile between the slab surface (half a
+    # spacing above its top layer) and the plate is the steady state; on one
+    # level the lattice keeps it to round-off.  An adiabatic solid (plain
+    # bounce-back of g) drifts 0.12 dT from it in the same 100 steps.
+    case = I.heated_slab_case(refined=refined)
+
+    def fields(x, y, z, p, info):
+        return np.ones_like(z), np.zeros((3,) + z.shape), I.heated_slab_profile(case, z)
+
+    o = make(case, fields)
+    o.step(100)
+    worst = 0.0
+    for p, info in enumerate(o.patches):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        _, u, T, _ = o.moments(p)
+        m = o.mask(p) == 1
+        worst = max(worst, np.max(np.abs(T[m] - I.heated_slab_profile(case, z)[m])) / case["thermal"]["dT"])
+        assert np.max(np.abs(u[:, m])) < 1e-6
+    assert worst < (1e-3 if refined else 1e-10), worst
+
+
 def _ball_case(n=16, boxes=(), level=0, d=6.0, nu0=0.02):
     return dict(name="ball", n=(n, n, n), periodic=(1, 1, 1), walls=(0,) * 6, inflow_axis=-1, u_in=(0, 0, 0),
                 boxes=list(boxes), solid=I.sphere_mask(level, (n / 2, n / 2, n / 2), d), nu0=nu0,
