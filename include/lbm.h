@@ -102,6 +102,10 @@ typedef struct {
   double wall_T[6];         /* thermal wall temperatures per wall face (bit order of walls) */
   lbm_storage storage;
   int32_t mirror_lbgk;      /* 1: LBGK mirror state (gamma fixed at 2) */
+  double solid_T;           /* thermal: temperature of solid surfaces when solid_isothermal */
+  int32_t solid_isothermal; /* thermal: 1 = solid surfaces held at solid_T (anti-bounce-back
+                               of g, as at the plates; the heated sphere of Sec. IV),
+                               0 = adiabatic solids (bounce-back of g) */
 } lbm_desc;
 
 /* Builds the level/patch layout, node classes and interface tables

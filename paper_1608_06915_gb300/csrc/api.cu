@@ -171,6 +171,8 @@ lbmk::ThermalLevel thermal_level(const lbm_grid* g, const HostPatch& p) {
   lbmk::ThermalLevel L{};
   const lbm_desc& d = g->hg.desc;
   for (int k = 0; k < 6; ++k) L.twd[k] = d.wall_T[k] - d.t0;
+  L.twd[6] = d.solid_T - d.t0;
+  L.solid_iso = d.solid_isothermal ? 1 : 0;
   L.glam = d.glambda / (double)(1LL << p.level);  // du_f = du_c / r per level
   L.tref_d = d.t_ref - d.t0;
   L.beta = p.beta;

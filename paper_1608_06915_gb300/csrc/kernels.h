@@ -24,10 +24,11 @@ struct Force {
 // Thermal parameters of one level: wall temperatures minus T0 per wall face,
 // g*lambda / 2^level, T_ref - T0, beta, beta1, LBGK mirror flag.
 struct ThermalLevel {
-  double twd[6];
+  double twd[7];  // wall temperature - T0 per wall face; [6]: isothermal solid surfaces
   double glam, tref_d, beta, beta1;
   int lbgk;
-  int pr_gt1;  // Pr > 1 rows of Table I
+  int pr_gt1;     // Pr > 1 rows of Table I
+  int solid_iso;  // solid surfaces held at twd[6] (else adiabatic)
 };
 
 cudaError_t launch_th_tiles(int storage, const PatchDev& p, const void* fin, const void* gin, void* fout, void* gout,

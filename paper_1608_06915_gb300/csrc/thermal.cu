@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(128) k_th_tiles(PatchDev p, const R* __restric
   const uint8_t ty = p.type[own];
   if (!(ty == T_BULK || ty == T_BC || (ty == T_D1 && odd))) return;
   R f[27], g[27];
-  pull_th<R>(p, fin, gin, x, y, z, f, g, tp.twd, status);
+  pull_th<R>(p, fin, gin, x, y, z, f, g, tp.twd, tp.solid_iso != 0, status);
   thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0, tp.pr_gt1 != 0);
   store2(p, fout, gout, own, f, g);
 }
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(128) k_th_coalesce(PatchDev pc, const R* __res
   const int x = (int)(cn % pc.nxp), y = (int)((cn / pc.nxp) % pc.dim[1]);
   const int z = (int)(cn / ((long long)pc.nxp * pc.dim[1]));
   R f[27], g[27];
-  pull_th<R>(pc, fin_c, gin_c, x, y, z, f, g, tc.twd, status);
+  pull_th<R>(pc, fin_c, gin_c, x, y, z, f, g, tc.twd, tc.solid_iso != 0, status);
   R fn[27], gn[27];
   ThState<R> s;
   thermal_neq<R>(f, g, ff, fg, fn, gn, s);
@@ -92,8 +92,8 @@ __global__ void __launch_bounds__(128, 4) k_th_samples(PatchDev pp, const R* __r
   const PatchDev& q = par ? pp : pc;
   const int x = (int)(n % q.nxp), y = (int)((n / q.nxp) % q.dim[1]);
   const int z = (int)(n / ((long long)q.nxp * q.dim[1]));
-  if (par) pull_th<R>(pp, fin_p, gin_p, x, y, z, f, g, tpar.twd, status);
-  else pull_th<R>(pc, fin_c, gin_c, x, y, z, f, g, tc.twd, status);
+  if (par) pull_th<R>(pp, fin_p, gin_p, x, y, z, f, g, tpar.twd, tpar.solid_iso != 0, status);
+  else pull_th<R>(pc, fin_c, gin_c, x, y, z, f, g, tc.twd, tc.solid_iso != 0, status);
   R fn[27], gn[27];
   ThState<R> st;
   thermal_neq<R>(f, g, par ? ff : R(1), par ? fg : R(1), fn, gn, st);

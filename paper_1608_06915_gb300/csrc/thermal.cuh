@@ -161,11 +161,13 @@ __device__ __forceinline__ void thermal_neq(const R (&f)[27], const R (&g)[27], 
 
 // Generic pull of f and g: walls (f bounce-back, g anti-bounce-back to the wall
 // equilibrium at rest, temperature T_w, density of the node's own state), solid
-// nodes (bounce-back of both), outlet (clamped source), spanned-axis wrap.
+// nodes (f bounce-back; g bounce-back when adiabatic, else anti-bounce-back to
+// the solid temperature twd[6] as at the walls), outlet (clamped source),
+// spanned-axis wrap.
 template <typename R>
 __device__ __forceinline__ void pull_generic_th(const PatchDev& p, const R* __restrict__ fin,
                                                 const R* __restrict__ gin, int x, int y, int z, R (&f)[27],
-                                                R (&g)[27], const R* twd, int* status) {
+                                                R (&g)[27], const R* twd, bool solid_iso, int* status) {
   const long long own = node_index(p, x, y, z);
   const int X[3] = {x, y, z};
   R rho_own_t = 0;
@@ -203,7 +205,10 @@ __device__ __forceinline__ void pull_generic_th(const PatchDev& p, const R* __re
     if (!bounce && !bad) {
       src = node_index(p, s[0], s[1], s[2]);
       const uint8_t t = p.type[src];
-      if (t == T_SOLID) bounce = true;
+      if (t == T_SOLID) {
+        bounce = true;
+        if (solid_iso) wall_face = 6;  // isothermal solid surface at twd[6]
+      }
       else if (t == T_SKIP) bad = true;
     }
     if (bad) {
@@ -232,23 +237,25 @@ __device__ __forceinline__ void pull_generic_th(const PatchDev& p, const R* __re
 
 template <typename R>
 __device__ __forceinline__ void pull_th(const PatchDev& p, const R* __restrict__ fin, const R* __restrict__ gin,
-                                        int x, int y, int z, R (&f)[27], R (&g)[27], const R* twd, int* status) {
+                                        int x, int y, int z, R (&f)[27], R (&g)[27], const R* twd, bool solid_iso,
+                                        int* status) {
   if (p.type[node_index(p, x, y, z)] == T_BULK) {
     pull_bulk<R, R>(p, fin, x, y, z, f);
     pull_bulk<R, R>(p, gin, x, y, z, g);
   } else {
-    pull_generic_th<R>(p, fin, gin, x, y, z, f, g, twd, status);
+    pull_generic_th<R>(p, fin, gin, x, y, z, f, g, twd, solid_iso, status);
   }
 }
 
 template <typename R>
 struct ThParams {
-  R twd[6];  // wall temperature - T0 per wall face
+  R twd[7];  // wall temperature - T0 per wall face; [6]: isothermal solid surfaces
   R glam;    // g lambda / 2^level (coarse acceleration per unit T, per level step)
   R tref_d;  // T_ref - T0
   R beta, beta1;
   int lbgk;
-  int pr_gt1;  // Pr > 1 rows of Table I
+  int pr_gt1;     // Pr > 1 rows of Table I
+  int solid_iso;  // solid surfaces held at twd[6] (else adiabatic)
 };
 
 template <typename R>
@@ -264,7 +271,8 @@ __device__ __forceinline__ void store2(const PatchDev& p, R* __restrict__ fo, R*
 template <typename R>
 ThParams<R> th_params(const ThermalLevel& L) {
   ThParams<R> t;
-  for (int k = 0; k < 6; ++k) t.twd[k] = (R)L.twd[k];
+  for (int k = 0; k < 7; ++k) t.twd[k] = (R)L.twd[k];
+  t.solid_iso = L.solid_iso;
   t.glam = (R)L.glam;
   t.tref_d = (R)L.tref_d;
   t.beta = (R)L.beta;

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(128) k_th_nodes(PatchDev p, const R* __restric
   const int x = (int)(own % p.nxp), y = (int)((own / p.nxp) % p.dim[1]);
   const int z = (int)(own / ((long long)p.nxp * p.dim[1]));
   R f[27], g[27];
-  pull_th<R>(p, fin, gin, x, y, z, f, g, tp.twd, status);
+  pull_th<R>(p, fin, gin, x, y, z, f, g, tp.twd, tp.solid_iso != 0, status);
   thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0, tp.pr_gt1 != 0);
   store2(p, fout, gout, own, f, g);
 }

@@ -54,6 +54,8 @@ class lbm_desc(ctypes.Structure):
         ("wall_T", ctypes.c_double * 6),
         ("storage", ctypes.c_int32),
         ("mirror_lbgk", ctypes.c_int32),
+        ("solid_T", ctypes.c_double),
+        ("solid_isothermal", ctypes.c_int32),
     ]
 
 
@@ -154,6 +156,9 @@ def make_desc(case: dict, storage: str = "fp32"):
         d.pr, d.t0, d.glambda, d.t_ref = float(th["pr"]), float(th.get("t0", 1 / 3)), float(th["glambda"]), \
             float(th["t_ref"])
         d.wall_T[:] = [float(v) for v in th["wall_T"]]
+        if th.get("solid_T") is not None:  # isothermal solid surfaces
+            d.solid_T = float(th["solid_T"])
+            d.solid_isothermal = 1
     d.storage = STORAGE[storage]
     d.mirror_lbgk = int(bool(case.get("mirror_lbgk", False)))
     return d, keep

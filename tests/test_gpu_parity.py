@@ -309,6 +309,28 @@ def test_rbc_small_fp64_every_step(pr):
         assert df < 1e-12 and dg < 1e-12, (s, df, dg)
 
 
+@pytest.mark.parametrize("refined", [False, True])
+def test_heated_slab_fp64_every_step(refined):
+    """Isothermal solid surfaces (anti-bounce-back of g to the solid
+    temperature): a heated slab under a cold plate, one level or with the slab
+    on a refined band, perturbed off its conduction profile; f and g against
+    the oracle after every coarse step."""
+    case = I.heated_slab_case(refined=refined)
+
+    def fields(x, y, z, p, info):
+        T = I.heated_slab_profile(case, z) + 1e-3 * np.sin(2 * np.pi * x / case["n"][0]) * np.cos(z)
+        u = 0.01 * np.stack([np.sin(2 * np.pi * y / case["n"][1]), np.cos(2 * np.pi * x / case["n"][0]),
+                             np.zeros_like(z)])
+        return np.ones_like(z) + 1e-3 * np.cos(z), u, T
+
+    g, o = twin(case, "fp64", fields)
+    for s in range(5):
+        g.step(1)
+        o.step(1)
+        df, dg = pop_diff(g, o, 0), pop_diff(g, o, 1)
+        assert df < 1e-12 and dg < 1e-12, (s, df, dg)
+
+
 @pytest.mark.parametrize("pr", [0.7, 2.0])
 def test_rbc_small_fp32_temperature(pr):
     case = I.rbc_small_case(pr=pr)
@@ -452,8 +474,8 @@ def test_sphere_full_size_sampled_level0_nodes():
     f1 = g.get_populations(0, dtype=torch.float32)
     beta = g.patches[0]["beta"]
     nz, ny, nx = f0.shape[1:]
-    rng = np.random.default_rng(31)
     n = 150
+    rng = np.random.default_rng(31)
     ys, zs = rng.integers(0, ny, n).tolist(), rng.integers(0, nz, n).tolist()
     # bulk, away from the refined box (coarse x in [80, 160]) and the boundaries
     xs = rng.integers(2, 70, n).tolist()
