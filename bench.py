@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--workload", choices=["channel", "channel-half", "tgv", "sphere", "rbc"], default="channel")
     ap.add_argument("--storage", choices=sorted(BYTES_PER_UPDATE), default="fp32")
+    ap.add_argument("--pr", type=float, default=0.7, help="Prandtl number of the rbc workload (Table I regime)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -52,7 +53,7 @@ def parse():
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, pr=0.7):
     from paper_1608_06915_gb300 import inputs as I
     if name in ("channel", "channel-half"):
         n = (256, 64, 128) if name == "channel" else (128, 64, 64)
@@ -70,12 +71,12 @@ def workload(name):
             return I.uniform_fields(x, (0.05, 0.0, 0.0))
         return case, fields, "sphere wake 384x192x192 coarse, 4 levels, D=64 finest nodes, Re=3700"
     if name == "rbc":
-        case = I.rbc_case()
+        case = I.rbc_case(pr=pr)
 
         def fields(info):
             return I.rbc_fields(case, info["level"], info["org"], info["dim"])
         return case, fields, ("Rayleigh-Benard 256x256x128 coarse, 3 levels (2x z in [0,12],[115,127]; 4x z in "
-                              "[0,6],[121,127]), Ra=1e7, Pr=0.7, thermal f+g")
+                              "[0,6],[121,127]), Ra=1e7, Pr=%g, thermal f+g" % pr)
     case = I.tgv_case()
 
     def fields(info):
@@ -147,7 +148,7 @@ def reference_arm(args):
     if rank != 0:
         return 0
     r = oracle_run(args.workload, steps=args.steps, warmup=args.warmup)
-    _, _, desc = workload(args.workload)
+    _, _, desc = workload(args.workload, args.pr)
     line = dict(impl="reference", metric=METRIC, value=r["value"], unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * r["seconds"] / r["steps"], higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
@@ -323,7 +324,7 @@ def cuda_arm(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    case, fields, desc = workload(args.workload)
+    case, fields, desc = workload(args.workload, args.pr)
     g = L.Grid(case, args.storage, device=dev)
     host_all = [fields(info) for info in g.patches]
     host_fields = [(h[0], h[1]) for h in host_all]
