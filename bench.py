@@ -273,6 +273,27 @@ def end_to_end(args, g, L, host_fields, dfields, nup, world, barrier, dev):
     return e2e
 
 
+def gamma_indicator(g, bpu, peak, block=8, reps=10):
+    """Time of the refinement indicator (lbm_gamma_blocks) over the level-0
+    patch: it reads the stored f of every fluid node once (half the bytes of
+    an isothermal node update, bpu), CUDA events on the grid's stream after
+    one warm call."""
+    import torch
+    fluid = float((g.mask(0) == 1).sum())
+    g.gamma_blocks(0, block)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(g.stream)
+    for _ in range(reps):
+        g.gamma_blocks(0, block)
+    e1.record(g.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    gbs = fluid * bpu / 2 / (ms / 1e3) / 1e9
+    return dict(kernel="k_gamma_blocks, level 0, blocks of %d^3" % block, ms_per_call=ms, fluid_nodes=fluid,
+                bytes_per_node=bpu / 2, achieved_gbs=gbs, frac=gbs / peak)
+
+
 def adjoint_ratio(dev, storage="fp32", K=20):
     """Time of the discrete adjoint of K coarse steps (lbm_adjoint_step: restore,
     recompute with snapshots, reverse) over the time of K forward steps, on the
@@ -400,6 +421,8 @@ def cuda_arm(args):
     kernels = [dict(r, avg_us=1e3 * r["ms"] / r["launches"]) for r in report]
     launches = sum(r["launches"] for r in report)
 
+    indicator = gamma_indicator(g, BYTES_PER_UPDATE[args.storage], peak) if rank == 0 else None
+
     e2e = None
     if not args.no_e2e and not case.get("thermal"):
         e2e = end_to_end(args, g, L, host_fields, dfields, nup, world, barrier, dev)
@@ -425,7 +448,7 @@ def cuda_arm(args):
                                 direct_launch_ms_per_step=1e3 * t_instr / args.steps,
                                 l2="no flush: working set %.2f GB > %.0f MB L2" % (ws / 1e9, L2_BYTES / 1e6)),
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clk,
-                    adjoint_forward_ratio=adj,
+                    adjoint_forward_ratio=adj, gamma_indicator=indicator,
                     uniform_fine_equivalent=dict(
                         value=uniform_equiv, unit=UNIT,
                         note="node updates of a uniform grid at the finest spacing (%d levels) per coarse step, "

@@ -134,6 +134,18 @@ lbm_status lbm_num_patches(lbm_grid_t g, int32_t* n_patches, int32_t* n_levels);
 lbm_status lbm_patch_info(lbm_grid_t g, int32_t patch, int32_t* level, int32_t* parent, int64_t org[3],
                           int64_t dim[3], double* beta, double* beta1);
 
+/* Refinement indicator (Sec. IV, channel: the stabiliser gamma of Eq.
+ * gamma_min_approx tends to its LBGK value 2 where the flow is resolved, so
+ * its deviation measures under-resolution; the conclusion proposes it as the
+ * criterion of adaptive refinement).  For each block of block^3 nodes of the
+ * patch's storage box, out receives the largest |gamma - 2| over the block's
+ * fluid nodes (0 without fluid nodes), gamma as lbm_moments gives it for the
+ * stored f.  out: caller-owned device float [nbz][nby][nbx], nb_a =
+ * ceil(dim_a / block) with dim from lbm_patch_info; zeroed, then filled,
+ * asynchronously on the bound stream.  LBM_ERR_ARG for a bad patch, block < 1
+ * or null out; LBM_ERR_STATE if unbound. */
+lbm_status lbm_gamma_blocks(lbm_grid_t g, int32_t patch, int32_t block, float* out);
+
 /* Node classes over the storage box, host output [z][y][x]: 0 no node (hole
  * or outside), 1 fluid, 2 solid. */
 lbm_status lbm_patch_mask(lbm_grid_t g, int32_t patch, uint8_t* host_out);

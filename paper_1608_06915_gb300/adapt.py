@@ -1,0 +1,134 @@
+"""Refinement boxes from the stabiliser gamma.
+
+The paper observes (Sec. IV, channel) that the KBC stabiliser gamma of Eq.
+gamma_min_approx tends to its LBGK value 2 where the flow is resolved, so
+that |gamma - 2| measures under-resolution, and its conclusion proposes this
+as the criterion of adaptive refinement.  ``lbm_gamma_blocks`` computes the
+largest |gamma - 2| per block of nodes on the GPU; this module turns the
+flagged blocks of a patch into candidate boxes of the next level in the
+layout's coarse units, widened to the layout's minimum width and merged
+until they satisfy the layout rules that ``lbm_grid_create`` checks.  Moving a state onto the new layout is not done
+here.
+
+Host logic only (numpy): clustering, conversion to coarse units, merging.
+"""
+import numpy as np
+
+
+def clusters(flags: np.ndarray) -> list:
+    """Face-connected clusters of True entries of a 3-D array [z][y][x]:
+    a list of (lo, hi) index bounding boxes, each a tuple (x, y, z), closed."""
+    flags = np.asarray(flags, dtype=bool)
+    seen = np.zeros_like(flags)
+    out = []
+    nz, ny, nx = flags.shape
+    for start in zip(*np.nonzero(flags)):
+        if seen[start]:
+            continue
+        seen[start] = True
+        stack, lo, hi = [start], list(start), list(start)
+        while stack:
+            z, y, x = stack.pop()
+            for a in range(3):
+                lo[a] = min(lo[a], (z, y, x)[a])
+                hi[a] = max(hi[a], (z, y, x)[a])
+            for dz, dy, dx in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                q = (z + dz, y + dy, x + dx)
+                if 0 <= q[0] < nz and 0 <= q[1] < ny and 0 <= q[2] < nx and flags[q] and not seen[q]:
+                    seen[q] = True
+                    stack.append(q)
+        out.append(((lo[2], lo[1], lo[0]), (hi[2], hi[1], hi[0])))
+    return out
+
+
+def block_box_to_coarse(info: dict, block: int, lo_b, hi_b, margin: int, n) -> tuple:
+    """Coarse-unit closed box [lo, hi] covering blocks lo_b..hi_b of a patch
+    (storage-box block indices, x y z), grown by ``margin`` coarse units and
+    clipped to the domain [0, n - 1]."""
+    s = 1 << info["level"]
+    lo, hi = [], []
+    for a in range(3):
+        i0 = lo_b[a] * block
+        i1 = min((hi_b[a] + 1) * block, info["dim"][a]) - 1
+        c0 = (info["org"][a] + i0) // s - margin
+        c1 = -((-(info["org"][a] + i1)) // s) + margin  # ceil
+        lo.append(max(0, c0))
+        hi.append(min(int(n[a]) - 1, c1))
+    return tuple(lo), tuple(hi)
+
+
+def widen(box, min_width: float, n) -> tuple:
+    """A closed box (lo, hi) grown about its centre to at least ``min_width``
+    per axis (hi - lo), shifted back inside the domain [0, n - 1]."""
+    lo, hi = list(box[0]), list(box[1])
+    for a in range(3):
+        w = hi[a] - lo[a]
+        if w < min_width:
+            extra = int(np.ceil(min_width - w))
+            lo[a] -= extra // 2
+            hi[a] += extra - extra // 2
+        if lo[a] < 0:
+            hi[a] = min(int(n[a]) - 1, hi[a] - lo[a])
+            lo[a] = 0
+        if hi[a] > int(n[a]) - 1:
+            lo[a] = max(0, lo[a] - (hi[a] - (int(n[a]) - 1)))
+            hi[a] = int(n[a]) - 1
+    return tuple(lo), tuple(hi)
+
+
+def merge_boxes(boxes: list, gap: float) -> list:
+    """Merge closed boxes (lo, hi) until no two of them overlap or lie within
+    ``gap`` of each other on every axis; a merged pair becomes its bounding box."""
+    boxes = [(tuple(lo), tuple(hi)) for lo, hi in boxes]
+    changed = True
+    while changed:
+        changed = False
+        for i in range(len(boxes)):
+            for j in range(i + 1, len(boxes)):
+                (alo, ahi), (blo, bhi) = boxes[i], boxes[j]
+                near = all(not (ahi[a] + gap < blo[a] or bhi[a] + gap < alo[a]) for a in range(3))
+                if near:
+                    boxes[i] = (tuple(min(alo[a], blo[a]) for a in range(3)),
+                                tuple(max(ahi[a], bhi[a]) for a in range(3)))
+                    del boxes[j]
+                    changed = True
+                    break
+            if changed:
+                break
+    return boxes
+
+
+def refinement_boxes(grid, case: dict, patch: int, block: int = 4, threshold: float = 0.1,
+                     margin: int = 1) -> list:
+    """Candidate level-(l+1) boxes (level, lo, hi) in coarse units for the
+    blocks of ``patch`` (level l) whose largest |gamma - 2| exceeds
+    ``threshold`` (non-finite values count as flagged).  Boxes closer than the
+    layout's 8 parent spacings are merged; if the layout with the new boxes
+    added is still rejected, one bounding box of all flagged blocks is tried,
+    then none.  The grid's current state is read, not changed."""
+    from . import lbm as L
+    info = grid.patches[patch]
+    dev = grid.gamma_blocks(patch, block).cpu().numpy()
+    flags = ~(dev <= threshold)
+    cl = clusters(flags)
+    if not cl:
+        return []
+    spacing = 8.0 / (1 << info["level"])  # 8 parent spacings in coarse units
+    boxes = [widen(block_box_to_coarse(info, block, lo, hi, margin, case["n"]), spacing, case["n"])
+             for lo, hi in cl]
+    lev = info["level"] + 1
+    boxes = merge_boxes(boxes, spacing)
+    candidates = [boxes]
+    if len(boxes) > 1:
+        lo = tuple(min(b[0][a] for b in boxes) for a in range(3))
+        hi = tuple(max(b[1][a] for b in boxes) for a in range(3))
+        candidates.append([(lo, hi)])
+    for cand in candidates:
+        new = [(lev, lo, hi) for lo, hi in cand]
+        trial = dict(case, boxes=list(case.get("boxes", [])) + new)
+        try:
+            L.Grid(trial, grid.storage, bind=False)
+        except Exception:
+            continue
+        return new
+    return []

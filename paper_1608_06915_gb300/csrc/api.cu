@@ -848,6 +848,17 @@ lbm_status lbm_moments(lbm_grid_t g, int32_t patch, void* rho, void* u, void* T,
                     "lbm_moments");
 }
 
+lbm_status lbm_gamma_blocks(lbm_grid_t g, int32_t patch, int32_t block, float* out) {
+  if (lbm_status s = check_patch(g, patch)) return s;
+  if (lbm_status s = check_bound(g)) return s;
+  if (block < 1 || !out) return fail(g, LBM_ERR_ARG, "block must be >= 1 and out non-null");
+  HostPatch& p = g->hg.P[patch];
+  return cuda_check(g,
+                    lbmk::launch_gamma_blocks(g->hg.desc.storage, view(g, p), g->base + p.off_f[p.cur], p.beta,
+                                              g->hg.desc.mirror_lbgk, block, out, g->stream),
+                    "lbm_gamma_blocks");
+}
+
 static lbm_status copy_pop(lbm_grid_t g, int32_t patch, int32_t which, void* dense, int32_t dtype, int to_dense) {
   if (lbm_status s = check_patch(g, patch)) return s;
   if (lbm_status s = check_bound(g)) return s;

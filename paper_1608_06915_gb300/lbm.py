@@ -83,6 +83,7 @@ def lib():
             "lbm_init_equilibrium": [vp, i32, vp, vp, vp, i32],
             "lbm_step": [vp, i64],
             "lbm_moments": [vp, i32, vp, vp, vp, vp, i32],
+            "lbm_gamma_blocks": [vp, i32, i32, vp],
             "lbm_get_populations": [vp, i32, i32, vp, i32],
             "lbm_set_populations": [vp, i32, i32, vp, i32],
             "lbm_force": [vp, dp, dp],
@@ -216,6 +217,17 @@ class Grid:
     def shape(self, p: int):
         dx, dy, dz = self.patches[p]["dim"]
         return (dz, dy, dx)
+
+    def gamma_blocks(self, p: int, block: int):
+        """Refinement indicator of patch p: the largest |gamma - 2| over the
+        fluid nodes of each block^3 block of its storage box, a device float
+        tensor [nbz][nby][nbx] (lbm_gamma_blocks)."""
+        import torch
+        dx, dy, dz = self.patches[p]["dim"]
+        nb = [(d + block - 1) // block for d in (dz, dy, dx)]
+        out = torch.empty(nb, dtype=torch.float32, device=self.buffer.device)
+        _check(lib().lbm_gamma_blocks(self.handle, int(p), int(block), self._ptr(out)), self.handle)
+        return out
 
     def mask(self, p: int) -> np.ndarray:
         out = np.empty(self.shape(p), dtype=np.uint8)

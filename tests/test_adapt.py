@@ -1,0 +1,120 @@
+"""Refinement boxes from the stabiliser gamma (Sec. IV channel discussion and
+the conclusion's adaptive-refinement criterion): the host logic that turns
+flagged blocks into layout boxes (CPU), and the GPU indicator against the
+oracle's gamma (gpu)."""
+import numpy as np
+import pytest
+
+from paper_1608_06915_gb300 import adapt as A
+from paper_1608_06915_gb300 import inputs as I
+
+
+def test_clusters_are_face_connected_components():
+    f = np.zeros((6, 5, 7), dtype=bool)
+    f[1, 1, 1:4] = True          # a run along x
+    f[2, 1, 3] = True            # joined to it through a face
+    f[4, 3, 5] = True            # a separate single block
+    f[4, 4, 6] = True            # diagonal neighbour of the last: separate
+    got = sorted(A.clusters(f))
+    assert got == sorted([((1, 1, 1), (3, 1, 2)), ((5, 3, 4), (5, 3, 4)), ((6, 4, 4), (6, 4, 4))])
+    assert A.clusters(np.zeros((2, 2, 2), dtype=bool)) == []
+
+
+def test_block_box_to_coarse_units():
+    # a level-1 patch whose storage box starts at level coordinate 8 (coarse 4)
+    info = dict(level=1, org=(8, 8, 8), dim=(17, 17, 17))
+    lo, hi = A.block_box_to_coarse(info, 4, (0, 1, 4), (1, 1, 4), 0, (32, 32, 32))
+    # x: nodes 0..7 -> level 8..15 -> coarse 4..7.5 -> [4, 8]; y: nodes 4..7 -> [6, 8];
+    # z: block 4 is node 16 only (the box has 17 nodes) -> level 24 -> coarse [12, 12]
+    assert (lo, hi) == ((4, 6, 12), (8, 8, 12))
+    lo, hi = A.block_box_to_coarse(info, 4, (0, 0, 0), (4, 4, 4), 2, (12, 12, 12))
+    assert lo == (2, 2, 2) and hi == (11, 11, 11)  # grown by 2, clipped to the domain
+
+
+def test_merge_boxes_until_separated():
+    b = [((0, 0, 0), (3, 3, 3)), ((10, 0, 0), (12, 3, 3)), ((30, 0, 0), (31, 3, 3))]
+    assert A.merge_boxes(b, 8) == [((0, 0, 0), (12, 3, 3)), ((30, 0, 0), (31, 3, 3))]
+    assert len(A.merge_boxes(b, 20)) == 1
+    # separated along one axis only is enough
+    assert len(A.merge_boxes([((0, 0, 0), (3, 3, 3)), ((0, 20, 0), (3, 23, 3))], 8)) == 2
+
+
+def test_widen_keeps_boxes_inside_the_domain():
+    assert A.widen(((10, 10, 10), (12, 10, 11)), 8, (32, 32, 32)) == ((7, 6, 7), (15, 14, 15))
+    assert A.widen(((0, 0, 29), (1, 2, 31)), 8, (32, 32, 32)) == ((0, 0, 23), (8, 8, 31))
+
+
+def test_widened_merged_boxes_pass_the_layout_validation():
+    from paper_1608_06915_gb300 import lbm as L
+    case = I.tgv_case(n=32, refined=False)
+    raw = [((6, 6, 6), (10, 10, 10)), ((14, 6, 6), (16, 10, 10))]
+    boxes = A.merge_boxes([A.widen(b, 8.0, case["n"]) for b in raw], 8.0)
+    assert len(boxes) == 1
+    L.Grid(dict(case, boxes=[(1, lo, hi) for lo, hi in boxes]), "fp32", bind=False)
+    with pytest.raises(Exception):  # as they came, the boxes are too narrow and too close
+        L.Grid(dict(case, boxes=[(1, lo, hi) for lo, hi in raw]), "fp32", bind=False)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_gamma_blocks_match_the_oracle(storage):
+    """The GPU indicator against the oracle's own gamma: per node, the
+    stabiliser of Eq. gamma_min_approx for the oracle's stored populations
+    (oracle collide), then the block maximum of |gamma - 2| over fluid nodes."""
+    import torch
+    from oracle import oracle as O
+    from paper_1608_06915_gb300 import lbm as L
+    case = I.tgv_case(n=16, box=(4, 12), nu=0.002)
+    o = O.Oracle(case)
+    g = L.Grid(case, storage)
+    rng = np.random.default_rng(41)
+    for p, info in enumerate(g.patches):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        rho = 1.0 + 0.02 * rng.standard_normal(x.shape)
+        u = 0.08 * rng.standard_normal((3,) + x.shape)  # rough: gamma far from 2 in places
+        o.init_equilibrium(p, rho, u)
+        g.init_equilibrium(p, torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    o.step(3)
+    for p in range(len(o.patches)):
+        g.set_populations(p, torch.from_numpy(o.get_pop(p)).cuda())
+    block = 3
+    for p, info in enumerate(o.patches):
+        f, m = o.get_pop(p), o.mask(p) == 1
+        gam = np.full(m.shape, 2.0)
+        for idx in zip(*np.nonzero(m)):
+            gam[idx] = O.collide(f[(slice(None),) + idx], info["beta"])[1]
+        dev = np.abs(gam - 2.0) * m
+        nb = [(s + block - 1) // block for s in m.shape]
+        ref = np.zeros(nb)
+        for idx in np.ndindex(*m.shape):
+            b = tuple(i // block for i in idx)
+            ref[b] = max(ref[b], dev[idx])
+        got = g.gamma_blocks(p, block).cpu().numpy()
+        assert got.shape == ref.shape
+        tol = 1e-6 if storage == "fp64" else 1e-3
+        assert ref.max() > 0.05, ref.max()
+        assert np.max(np.abs(got - ref)) < tol * max(1.0, ref.max()), (p, np.max(np.abs(got - ref)))
+
+
+@pytest.mark.gpu
+def test_refinement_boxes_cover_the_rough_region():
+    """A smooth field with one rough region: the suggested level-1 box covers
+    it and the layout accepts it."""
+    import torch
+    from paper_1608_06915_gb300 import lbm as L
+    case = I.tgv_case(n=32, refined=False, nu=0.002)
+    g = L.Grid(case, "fp64")
+    info = g.patches[0]
+    x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+    rng = np.random.default_rng(42)
+    rough = (np.abs(x - 20) < 3) & (np.abs(y - 12) < 3) & (np.abs(z - 16) < 3)
+    u = 0.01 * np.stack([np.sin(2 * np.pi * y / 32), np.zeros_like(x), np.zeros_like(x)])
+    u = u + 0.1 * rough * rng.standard_normal((3,) + x.shape)
+    g.init_equilibrium(0, torch.ones(x.shape, dtype=torch.float64).cuda(), torch.from_numpy(u).cuda())
+    g.step(2)
+    boxes = A.refinement_boxes(g, case, 0, block=4, threshold=0.2)
+    assert len(boxes) == 1
+    lev, lo, hi = boxes[0]
+    assert lev == 1
+    assert lo[0] <= 17 and hi[0] >= 23 and lo[1] <= 9 and hi[1] >= 15 and lo[2] <= 13 and hi[2] >= 19, boxes
+    assert all(hi[a] - lo[a] < 24 for a in range(3)), boxes  # not the whole domain
