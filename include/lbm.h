@@ -139,8 +139,9 @@ lbm_status lbm_patch_info(lbm_grid_t g, int32_t patch, int32_t* level, int32_t* 
  * its deviation measures under-resolution; the conclusion proposes it as the
  * criterion of adaptive refinement).  For each block of block^3 nodes of the
  * patch's storage box, out receives the largest |gamma - 2| over the block's
- * fluid nodes (0 without fluid nodes), gamma as lbm_moments gives it for the
- * stored f.  out: caller-owned device float [nbz][nby][nbx], nb_a =
+ * bulk and boundary-class nodes (0 without such nodes), gamma of the state
+ * the next lbm_step collides there: the pull of the stored f.  Interface
+ * nodes, whose next state comes from the coupling, are left out.  out: caller-owned device float [nbz][nby][nbx], nb_a =
  * ceil(dim_a / block) with dim from lbm_patch_info; zeroed, then filled,
  * asynchronously on the bound stream.  LBM_ERR_ARG for a bad patch, block < 1
  * or null out; LBM_ERR_STATE if unbound. */
@@ -201,7 +202,9 @@ lbm_status lbm_graphs(lbm_grid_t g, int32_t enable);
 
 /* Macroscopic fields of a patch's current populations: rho, u = j/rho + du/2
  * (du of the level's body force, Sec. III.A), T (thermal, else T0) and the
- * stabiliser gamma that Eq. gamma_min_approx gives for the stored state.
+ * stabiliser gamma that Eq. gamma_min_approx gives for the stored state (for
+ * a post-collision state, which lbm_step stores, that is 2 up to rounding;
+ * lbm_gamma_blocks gives the stabiliser of the next collision instead).
  * All device outputs, nullable, layouts as above; dtype 0 float, 1 double. */
 lbm_status lbm_moments(lbm_grid_t g, int32_t patch, void* rho, void* u, void* T, void* gamma, int32_t dtype);
 

@@ -855,7 +855,7 @@ lbm_status lbm_gamma_blocks(lbm_grid_t g, int32_t patch, int32_t block, float* o
   HostPatch& p = g->hg.P[patch];
   return cuda_check(g,
                     lbmk::launch_gamma_blocks(g->hg.desc.storage, view(g, p), g->base + p.off_f[p.cur], p.beta,
-                                              g->hg.desc.mirror_lbgk, block, out, g->stream),
+                                              g->hg.desc.mirror_lbgk, block, out, status_ptr(g), g->stream),
                     "lbm_gamma_blocks");
 }
 

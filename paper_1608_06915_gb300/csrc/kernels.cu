@@ -403,24 +403,28 @@ cudaError_t launch_moments(int storage, const PatchDev& p, const void* fin, void
 
 // ---------------------------------------------------------------------------
 // Refinement indicator: per block of B^3 nodes of the storage box, the largest
-// |gamma - 2| over its fluid nodes, gamma from Eq. gamma_min_approx for the
-// stored state (as k_moments gives it).  The stabiliser tends to its LBGK
-// value 2 where the flow is resolved, so its deviation measures
-// under-resolution (Sec. IV, channel; the conclusion proposes it as the
-// criterion of adaptive refinement).  out [nbz][nby][nbx] is zeroed first;
-// maxima of non-negative floats combine as integer maxima of their bits.
+// |gamma - 2| over its bulk and boundary-class nodes, gamma from Eq.
+// gamma_min_approx for the state the next stream-collide collides there (the
+// pull of the stored post-collision state; a post-collision state itself has
+// gamma = 2 exactly).  The stabiliser tends to its LBGK value 2 where the flow
+// is resolved, so its deviation measures under-resolution (Sec. IV, channel;
+// the conclusion proposes it as the criterion of adaptive refinement).
+// Interface nodes, whose next state comes from the coupling, are left out.
+// out [nbz][nby][nbx] is zeroed first; maxima of non-negative floats combine
+// as integer maxima of their bits.
 template <typename S, typename R>
 __global__ void __launch_bounds__(128) k_gamma_blocks(PatchDev p, const S* __restrict__ fin, R beta, int lbgk, int B,
-                                                      int nbx, int nby, float* __restrict__ out) {
+                                                      int nbx, int nby, float* __restrict__ out, int* status) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
   float dev = 0.0f;
   if (x < p.dim[0]) {
     const long long own = node_index(p, x, y, z);
     const uint8_t t = p.type[own];
-    if (t != T_SKIP && t != T_SOLID) {
+    if (t == T_BULK || t == T_BC) {
       R f[27];
-      load_node<S, R>(p, fin, own, f);
+      if (t == T_BULK) pull_bulk<S, R>(p, fin, x, y, z, f);
+      else pull_generic<S, R>(p, fin, x, y, z, f, status);
       const R gamma = kbc_collide<R, 0>(f, beta, R(0), R(0), R(0), lbgk != 0);
       dev = (float)fabs((double)gamma - 2.0);
     }
@@ -441,7 +445,7 @@ __global__ void __launch_bounds__(128) k_gamma_blocks(PatchDev p, const S* __res
 }
 
 cudaError_t launch_gamma_blocks(int storage, const PatchDev& p, const void* fin, double beta, int lbgk, int B,
-                                float* out, cudaStream_t st) {
+                                float* out, int* status, cudaStream_t st) {
   const int nbx = (p.dim[0] + B - 1) / B, nby = (p.dim[1] + B - 1) / B, nbz = (p.dim[2] + B - 1) / B;
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * (size_t)nbx * nby * nbz, st);
   if (e) return e;
@@ -449,7 +453,7 @@ cudaError_t launch_gamma_blocks(int storage, const PatchDev& p, const void* fin,
     using S = typename decltype(ts)::type;
     using R = typename decltype(tr)::type;
     dim3 block(128), grid((p.dim[0] + 127) / 128, p.dim[1], p.dim[2]);
-    k_gamma_blocks<S, R><<<grid, block, 0, st>>>(p, (const S*)fin, (R)beta, lbgk, B, nbx, nby, out);
+    k_gamma_blocks<S, R><<<grid, block, 0, st>>>(p, (const S*)fin, (R)beta, lbgk, B, nbx, nby, out, status);
     return cudaGetLastError();
   });
 }

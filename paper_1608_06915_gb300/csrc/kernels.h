@@ -155,7 +155,7 @@ struct CopySegs {
 cudaError_t launch_copy(const CopySegs& segs, cudaStream_t st);
 
 cudaError_t launch_gamma_blocks(int storage, const PatchDev& p, const void* fin, double beta, int lbgk, int B,
-                                float* out, cudaStream_t st);
+                                float* out, int* status, cudaStream_t st);
 cudaError_t launch_diag(int storage, const PatchDev& p, const void* fin, double vol_weight, const Force& F,
                         double* partial, int blocks, cudaStream_t st);
 cudaError_t launch_diag_final(const double* partial, int total_blocks, double* out8, cudaStream_t st);
