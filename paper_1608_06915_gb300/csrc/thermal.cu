@@ -1,11 +1,14 @@
-// Two-population thermal model (Sec. II.B, Pr <= 1) on the refined grid.
+// Two-population thermal model (Sec. II.B, both Prandtl regimes of Table I)
+// on the refined grid.
 //
 // f follows the isothermal KBC collision with the Boussinesq acceleration
-// g*lambda*(T - T_ref) e_z through the exact difference method; g relaxes as
+// g*lambda*(T - T_ref) e_z through the exact difference method, plus, for
+// Pr > 1, 2 (beta - beta1)(f* - f^eq) with the Grad term of P - P^eq; g relaxes as
 //   g' = g + 2 beta (g^eq - g) + 2 (beta - beta1) (g* - g^eq)
-// (Eq. kinetics_g_entr), where for Pr <= 1 the quasi-equilibrium differs from
-// the equilibrium only in its first moment (Table I):
-//   g*_i - g^eq_i = W_i c_i . (q - q^eq - 2 (P - P^eq) u) / T0.
+// (Eq. kinetics_g_entr), where the quasi-equilibrium differs from the
+// equilibrium only in its first moment (Table I):
+//   Pr <= 1: g*_i - g^eq_i = W_i c_i . (q - q^eq - 2 (P - P^eq) u) / T0,
+//   Pr > 1:  g*_i - g^eq_i = W_i c_i . (2 (P - P^eq) u) / T0.
 // g^eq is the Grad form (Eq. grad_general) with (2 rho E, q^eq, R^eq), T0 = 1/3.
 // At rest at the reference state g^eq_i = W_i c_i^2; g is stored as the
 // deviation from that, f as the deviation from W_i.
@@ -13,10 +16,12 @@
 // Interface (Sec. III.A, thermal model): f non-equilibrium scaled by
 // ff = beta_s / (r beta_t); g by
 //   g_t = g^eq + fg (g - g^eq) + (ff - fg) W_i c_i . (2 P1 u) / T0,
-//   fg = beta1_s / (r beta1_t),  P1 = sum c c (f - f^eq)  (Eqs. for P1 and g^neq_f).
+//   fg = beta1_s / (r beta1_t),  P1 = sum c c (f - f^eq)  (Eqs. for P1 and g^neq_f);
+// for Pr > 1 the two ratios swap (the host passes them).
 // Reconstruction interpolates rho, u, T and both non-equilibrium parts.
 // Walls: f half-way bounce-back, g anti-bounce-back to the wall equilibrium at
-// rest, temperature T_w.  Every kernel here pulls node by node.
+// rest, temperature T_w; solids likewise at their temperature when isothermal,
+// else bounce-back of g.  Every kernel here pulls node by node.
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"

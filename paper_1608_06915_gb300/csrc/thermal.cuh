@@ -1,4 +1,4 @@
-// Device functions of the two-population thermal model (Sec. II.B, Pr <= 1),
+// Device functions of the two-population thermal model (Sec. II.B, both regimes of Table I),
 // shared by the node-by-node kernels (thermal.cu) and the TMA tile pass
 // (thermal_tma.cu).  The model and storage conventions are stated in thermal.cu.
 #pragma once

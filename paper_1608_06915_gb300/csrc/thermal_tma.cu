@@ -6,8 +6,8 @@
 // populations 3j .. 3j + 2), plus the 16-byte wrap boxes of both sets on the
 // edge tiles of x-periodic rows.  Four consumer warps pull their 54 values,
 // release the stage, run the thermal collision (f: KBC with the Boussinesq
-// force; g: relaxation to the Grad equilibrium with the Pr <= 1
-// quasi-equilibrium), and store their 27 x 32 segments of f and g with one TMA
+// force; g: relaxation to the Grad equilibrium with the quasi-equilibrium
+// of the grid's Prandtl regime), and store their 27 x 32 segments of f and g with one TMA
 // store each.  Walls across y or z follow the row rule of the isothermal pass
 // (bit j of the tile's bounce mask: source row j lies beyond a wall): f
 // bounces back, g takes the anti-bounce-back to the wall equilibrium at rest,
