@@ -103,3 +103,20 @@ def test_bad_arguments(L):
     case["periodic"] = (0, 1, 1)
     with pytest.raises(L.LbmError):
         L.Grid(case, bind=False)
+
+
+def test_thermal_parameters_validated(L):
+    """Both Prandtl regimes are accepted (Table I), with the relaxation
+    parameters swapped for Pr > 1; Pr <= 0 and T0 != 1/3 are rejected."""
+    g07 = L.Grid(I.rbc_small_case(pr=0.7), bind=False)
+    g2 = L.Grid(I.rbc_small_case(pr=2.0), bind=False)
+    t0 = 1.0 / 3.0
+    for g, pr in ((g07, 0.7), (g2, 2.0)):
+        b, b1 = g.patches[0]["beta"], g.patches[0]["beta1"]
+        b_nu, b_al = (b, b1) if pr <= 1 else (b1, b)
+        assert abs(((0.5 / b_nu - 0.5) * t0) / ((0.5 / b_al - 0.5) * t0) - pr) < 1e-12
+    for bad in (dict(pr=0.0), dict(pr=-1.0), dict(t0=0.3)):
+        case = I.rbc_small_case()
+        case["thermal"] = dict(case["thermal"], **bad)
+        with pytest.raises(L.LbmError):
+            L.Grid(case, bind=False)
