@@ -47,6 +47,10 @@
 //   R7  thermal: T0 = 1/3; f* = f^eq for Pr <= 1; g* from Table I with the
 //       closed-form P^eq; Boussinesq acceleration g*lambda*(T - T_ref) e_z;
 //       thermal walls by anti-bounce-back of g to the wall equilibrium.
+//   R9  state transfer onto another layout (not in the paper; see
+//       Sim::transfer_from): the source level nearest the node's own that
+//       holds it (own, then finer, then coarser), coinciding node or trilinear
+//       cell corners, f - f^eq rescaled by beta_s/(r beta_t).
 //   R8  thermal, Pr > 1: f* differs from f^eq only by the Grad term of the
 //       non-equilibrium stress, f*_i - f^eq_i = W_i P1_ab (c_ia c_ib -
 //       T0 d_ab) / (2 T0^2) with P1 = P - P^eq (Table I row f* for Pr > 1,
@@ -56,6 +60,7 @@
 // Parity status: every function above is pinned by tests under tests/
 // (closed forms, invariants, special cases, brute force).
 
+#include <algorithm>
 #include <array>
 #include <climits>
 #include <cmath>
@@ -526,6 +531,115 @@ struct Sim {
       perr.clear();
       fail(m);
     }
+  }
+
+  // ---- state transfer onto another layout (regridding) ---------------------
+  // Not in the paper, which leaves adaptive refinement to future work (its
+  // conclusion); reading R9.  Every fluid node of this layout takes the state
+  // of the source level nearest its own that holds it, trying its own level,
+  // then finer levels (nearest first), then coarser ones (nearest first): from
+  // the coinciding node when that level is as fine or finer, else trilinearly
+  // from the corners of the source cell around it (rho, u and f - f^eq
+  // interpolated; only corners of non-zero weight are needed).
+  // The stored states are post-collision, whose f - f^eq is (1 - 2 beta) times
+  // the pre-collision one in the shear part (the whole of it with the LBGK
+  // mirror); the pre-collision part scales between levels with the ratio of
+  // Eq. f_neq_rescaling_iso, beta_s / (r beta_t), r = dx_s / dx_t.  So the
+  // stored f - f^eq is scaled by (1 - 2 beta_t)/(1 - 2 beta_s) beta_s/(r beta_t),
+  // and dropped where 1 - 2 beta_s vanishes (a fully relaxed state keeps none).
+  // Solid nodes take the rest state and inlet nodes the inflow equilibrium, as
+  // at initialisation.  Returns the number of fluid nodes no source level
+  // holds (they take the rest state).
+  long transfer_from(const Sim& src) {
+    long missing = 0;
+    const double rest[3] = {0, 0, 0};
+    for (Patch& p : P) {
+      std::vector<int> order(src.P.size());
+      for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+      auto rank = [&](int k) {
+        const int dl = src.P[k].level - p.level;
+        return dl >= 0 ? dl : 1000 - dl;
+      };
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rank(a) < rank(b); });
+      for (long m = 0; m < p.size(); ++m) {
+        if (!p.exists[m]) continue;
+        if (p.solid[m]) {
+          p.post[m] = feq(1.0, rest);
+          p.vpost[m] = 0;
+          continue;
+        }
+        if (p.inlet[m]) {
+          p.post[m] = feq(1.0, d.u_in);
+          p.vpost[m] = 1;
+          continue;
+        }
+        long X[3];
+        coords(p, m, X);
+        bool done = false;
+        for (int qi : order) {
+          const Patch& q = src.P[qi];
+          const int dl = q.level - p.level;
+          double rho = 0, u[3] = {0, 0, 0};
+          Pop neq{};
+          if (dl >= 0) {
+            long Y[3] = {X[0] << dl, X[1] << dl, X[2] << dl};
+            src.wrap(q.level, Y);
+            long n = src.index_of(q, Y);
+            if (n < 0 || q.solid[n] || !q.vpost[n]) continue;
+            Macro mc = macro(q.post[n]);
+            Pop fe = feq(mc.rho, mc.u);
+            rho = mc.rho;
+            for (int a = 0; a < 3; ++a) u[a] = mc.u[a];
+            for (int i = 0; i < Q; ++i) neq[i] = q.post[n][i] - fe[i];
+          } else {
+            const long sdiv = 1L << (-dl);
+            long base[3];
+            double fr[3];
+            for (int a = 0; a < 3; ++a) {
+              base[a] = X[a] >= 0 ? X[a] / sdiv : -((-X[a] + sdiv - 1) / sdiv);
+              fr[a] = (double)(X[a] - base[a] * sdiv) / (double)sdiv;
+            }
+            bool ok = true;
+            for (int c = 0; c < 8 && ok; ++c) {
+              double w = 1.0;
+              long Y[3];
+              for (int a = 0; a < 3; ++a) {
+                const int bit = (c >> a) & 1;
+                w *= bit ? fr[a] : 1.0 - fr[a];
+                Y[a] = base[a] + bit;
+              }
+              if (w == 0.0) continue;
+              src.wrap(q.level, Y);
+              long n = src.index_of(q, Y);
+              if (n < 0 || q.solid[n] || !q.vpost[n]) {
+                ok = false;
+                break;
+              }
+              Macro mc = macro(q.post[n]);
+              Pop fe = feq(mc.rho, mc.u);
+              rho += w * mc.rho;
+              for (int a = 0; a < 3; ++a) u[a] += w * mc.u[a];
+              for (int i = 0; i < Q; ++i) neq[i] += w * (q.post[n][i] - fe[i]);
+            }
+            if (!ok) continue;
+          }
+          const double r = std::ldexp(1.0, -dl);  // dx_s / dx_t = 2^(level_t - level_s)
+          const double post_s = 1.0 - 2.0 * q.beta, post_t = 1.0 - 2.0 * p.beta;
+          const double factor = std::fabs(post_s) < 1e-12 ? 0.0 : (post_t / post_s) * q.beta / (r * p.beta);
+          Pop fe = feq(rho, u);
+          for (int i = 0; i < Q; ++i) p.post[m][i] = fe[i] + factor * neq[i];
+          p.vpost[m] = 1;
+          done = true;
+          break;
+        }
+        if (!done) {
+          p.post[m] = feq(1.0, rest);
+          p.vpost[m] = 1;
+          ++missing;
+        }
+      }
+    }
+    return missing;
   }
 
   // ---- construction -------------------------------------------------------
@@ -1200,6 +1314,17 @@ int orc_set_pop(void* h, int p, int which, const double* in) {
     if (q.exists[m] && !q.solid[m]) q.vpost[m] = 1;
   }
   return 0;
+}
+
+// State transfer from another oracle with the same domain (reading R9);
+// returns the number of fluid nodes no source level holds, or -1.
+long orc_transfer(void* dst, void* src) {
+  Sim* a = static_cast<Sim*>(dst);
+  Sim* b = static_cast<Sim*>(src);
+  if (!a || !b || a->thermal || b->thermal) return -1;
+  for (int k = 0; k < 3; ++k)
+    if (a->d.n[k] != b->d.n[k] || a->periodic(k) != b->periodic(k)) return -1;
+  return a->transfer_from(*b);
 }
 
 int orc_step(void* h, int64_t n) {

@@ -96,6 +96,8 @@ def lib():
             L.orc_thermal_collide.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp]
             L.orc_lagrange_weights.argtypes = [dp]
+            L.orc_transfer.restype = ctypes.c_long
+            L.orc_transfer.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
             L.orc_set_threads.argtypes = [ctypes.c_int]
             L.orc_max_threads.restype = ctypes.c_int
             _lib = L
@@ -284,6 +286,15 @@ class Oracle:
         a = _f64(arr)
         if lib().orc_set_pop(self._h, p, which, _dp(a)):
             raise RuntimeError("orc_set_pop failed")
+
+    def transfer_from(self, src: "Oracle") -> int:
+        """Take the state of another oracle of the same domain onto this
+        layout (reading R9); returns the number of fluid nodes no source
+        level holds."""
+        n = lib().orc_transfer(self._h, src._h)
+        if n < 0:
+            raise ValueError("oracle transfer between incompatible grids")
+        return int(n)
 
     def step(self, n: int = 1) -> None:
         if lib().orc_step(self._h, int(n)):

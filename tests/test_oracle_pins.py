@@ -650,3 +650,91 @@ def test_drag_units_on_a_refined_level():
     assert Fsum[0] > 0
     # a wrong level scaling (2^-l or 8^-l instead of 4^-l) is off by a factor 2
     assert abs(dJ[0] + Fsum[0]) < 0.1 * Fsum[0]
+
+
+# --- state transfer onto another layout (reading R9; not in the paper)
+def _linear_fields(x, y, z, p, info):
+    rho = 1.0 + 1e-3 * y
+    u = np.stack([0.01 + 1e-3 * y, 2e-3 * z, -1e-3 * x])
+    return rho, u
+
+
+def test_transfer_onto_the_same_layout_is_the_identity():
+    case = I.tgv_case(n=16, box=(4, 12))
+    a = make(case, lambda x, y, z, p, info: I.tgv_fields(x, y, z, n=16))
+    a.step(3)
+    b = O.Oracle(case)
+    assert b.transfer_from(a) == 0
+    for p in range(len(a.patches)):
+        m = a.mask(p) == 1
+        assert np.max(np.abs(b.get_pop(p)[:, m] - a.get_pop(p)[:, m])) < 1e-15
+
+
+def test_transfer_of_a_linear_equilibrium_onto_a_finer_layout_is_exact():
+    # trilinear interpolation reproduces a linear field; at equilibrium f - f^eq = 0
+    src = make(I.tgv_case(n=32, refined=False), _linear_fields)
+    case = I.tgv_case(n=32, box=(8, 24))
+    dst = O.Oracle(case)
+    assert dst.transfer_from(src) == 0
+    for p, info in enumerate(dst.patches):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        rho, u = _linear_fields(x, y, z, p, info)
+        m = dst.mask(p) == 1
+        f = dst.get_pop(p)
+        worst = max(np.max(np.abs(f[:, k, j, i] - O.feq(rho[k, j, i], u[:, k, j, i])))
+                    for k, j, i in zip(*np.nonzero(m)))
+        assert worst < 1e-14, (p, worst)
+
+
+def test_transfer_refine_then_coarsen_round_trip():
+    # a state with a non-equilibrium part, onto a two-level layout and back: the
+    # rescaling factors of the two directions cancel and coinciding nodes are copied
+    base = I.tgv_case(n=16, refined=False, nu=0.005)
+    a = make(base, lambda x, y, z, p, info: I.tgv_fields(x, y, z, n=16))
+    a.step(4)
+    mid = O.Oracle(I.tgv_case(n=16, box=(4, 12), nu=0.005))
+    assert mid.transfer_from(a) == 0
+    back = O.Oracle(base)
+    assert back.transfer_from(mid) == 0
+    fa, fb = a.get_pop(0), back.get_pop(0)
+    neq = np.max(np.abs(fa - np.stack([O.feq(*_mr(fa[:, k, j, i])) for k, j, i in np.ndindex(16, 16, 16)],
+                                      axis=1).reshape(fa.shape)))
+    assert neq > 1e-7  # the state carries a non-equilibrium part
+    assert np.max(np.abs(fb - fa)) < 1e-15
+
+
+def _mr(f):
+    rho = f.sum()
+    return rho, (C.T @ f) / rho
+
+
+def test_transfer_carries_the_chapman_enskog_state_of_a_shear_flow():
+    # Uniform shear u_x = S y, LBGK mirror: the first-order non-equilibrium part
+    # before collision is -(1/(2 beta)) (rho W_i / c_s^2) (c_ix c_iy) 2 S per
+    # level lattice unit, and the stored state after collision carries (1 - 2 beta)
+    # times it.  Built this way on one level and moved onto a level-1 box, the
+    # fine nodes must hold the same construction with the fine beta and the fine
+    # gradient S/2 (the rescaling of Eq. f_neq_rescaling_iso, post-collision).
+    n, S = 32, 1e-3
+    base = dict(I.tgv_case(n=n, refined=False, nu=0.01, lbgk=True))
+    cs2 = 1.0 / 3.0
+
+    def ce_state(x, y, z, beta, grad):
+        f = np.empty((27,) + x.shape)
+        pre = -(1.0 / (2.0 * beta)) * (W / cs2) * (C[:, 0] * C[:, 1]) * 2.0 * grad
+        for idx in np.ndindex(*x.shape):
+            u = np.array([S * (y[idx] - n / 2), 0.0, 0.0])
+            f[(slice(None),) + idx] = O.feq(1.0, u) + (1.0 - 2.0 * beta) * pre
+        return f
+
+    src = O.Oracle(base)
+    info = src.patches[0]
+    x, y, z = I.node_positions(0, info["org"], info["dim"])
+    src.set_pop(0, ce_state(x, y, z, info["beta"], S))
+    dst = O.Oracle(dict(base, boxes=[(1, (8, 8, 8), (24, 24, 24))]))
+    assert dst.transfer_from(src) == 0
+    fi = dst.patches[1]
+    xf, yf, zf = I.node_positions(1, fi["org"], fi["dim"])
+    want = ce_state(xf, yf, zf, fi["beta"], S / 2.0)
+    m = dst.mask(1) == 1
+    assert np.max(np.abs(dst.get_pop(1)[:, m] - want[:, m])) < 1e-14
