@@ -147,6 +147,21 @@ lbm_status lbm_patch_info(lbm_grid_t g, int32_t patch, int32_t* level, int32_t* 
  * or null out; LBM_ERR_STATE if unbound. */
 lbm_status lbm_gamma_blocks(lbm_grid_t g, int32_t patch, int32_t block, float* out);
 
+/* State transfer onto another layout (regridding), for adaptive refinement,
+ * which the paper leaves to future work.  Every node of dst takes the state of
+ * the src level nearest its own that holds it (own level, then finer ones,
+ * then coarser ones): the coinciding node, or a trilinear interpolation of rho,
+ * u and f - f^eq over the source cell around it.  The stored f - f^eq is
+ * rescaled between levels by (1 - 2 beta_t)/(1 - 2 beta_s) beta_s/(r beta_t),
+ * r = dx_s / dx_t: the ratio of Eq. f_neq_rescaling_iso for the pre-collision
+ * part, with each level's post-collision factor.  Solid nodes take the rest
+ * state and inlet nodes the inflow equilibrium.  Both grids bound, isothermal,
+ * same storage, extents and periodicity; at most 16 source patches (else
+ * LBM_ERR_ARG).  Waits for src's stream, runs on dst's and synchronises it.
+ * missing (nullable) receives the number of fluid nodes no source level holds;
+ * they take the rest state. */
+lbm_status lbm_transfer(lbm_grid_t dst, lbm_grid_t src, int64_t* missing);
+
 /* Node classes over the storage box, host output [z][y][x]: 0 no node (hole
  * or outside), 1 fluid, 2 solid. */
 lbm_status lbm_patch_mask(lbm_grid_t g, int32_t patch, uint8_t* host_out);

@@ -7,8 +7,8 @@ as the criterion of adaptive refinement.  ``lbm_gamma_blocks`` computes the
 largest |gamma - 2| per block of nodes on the GPU; this module turns the
 flagged blocks of a patch into candidate boxes of the next level in the
 layout's coarse units, widened to the layout's minimum width and merged
-until they satisfy the layout rules that ``lbm_grid_create`` checks.  Moving a state onto the new layout is not done
-here.
+until they satisfy the layout rules that ``lbm_grid_create`` checks; ``regrid`` then moves the state onto the new
+layout (``lbm_transfer``).
 
 Host logic only (numpy): clustering, conversion to coarse units, merging.
 """
@@ -132,3 +132,13 @@ def refinement_boxes(grid, case: dict, patch: int, block: int = 4, threshold: fl
             continue
         return new
     return []
+
+
+def regrid(grid, case: dict, boxes: list):
+    """A new grid of ``case`` with ``boxes`` (the full list, all levels) in
+    the storage of ``grid``, holding ``grid``'s state (lbm_transfer).
+    Returns (new grid, number of fluid nodes no source level held)."""
+    from . import lbm as L
+    new = L.Grid(dict(case, boxes=list(boxes)), grid.storage, device=grid.buffer.device)
+    missing = new.transfer_from(grid)
+    return new, missing

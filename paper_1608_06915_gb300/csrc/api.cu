@@ -17,6 +17,7 @@
 // explode chains on side streams, joined before the next instant; a coarse
 // step is captured once per set of buffer indices and replayed as a CUDA
 // graph.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -846,6 +847,53 @@ lbm_status lbm_moments(lbm_grid_t g, int32_t patch, void* rho, void* u, void* T,
                     lbmk::launch_moments(g->hg.desc.storage, view(g, p), g->base + p.off_f[p.cur], rho, u, gamma,
                                          dtype, p.beta, level_force(g, p.level), g->hg.desc.mirror_lbgk, g->stream),
                     "lbm_moments");
+}
+
+lbm_status lbm_transfer(lbm_grid_t dst, lbm_grid_t src, int64_t* missing) {
+  if (!dst || !src || dst == src) return dst ? fail(dst, LBM_ERR_ARG, "transfer needs two grids") : LBM_ERR_ARG;
+  if (lbm_status s = check_bound(dst)) return s;
+  if (lbm_status s = check_bound(src)) return fail(dst, s, "source grid not bound");
+  const lbm_desc &a = dst->hg.desc, &b = src->hg.desc;
+  if (dst->hg.thermal || src->hg.thermal) return fail(dst, LBM_ERR_ARG, "transfer is for the isothermal model");
+  if (a.storage != b.storage) return fail(dst, LBM_ERR_ARG, "transfer between different storages");
+  for (int k = 0; k < 3; ++k)
+    if (a.n[k] != b.n[k] || dst->hg.periodic(k) != src->hg.periodic(k))
+      return fail(dst, LBM_ERR_ARG, "transfer between different domains");
+  if ((int)src->hg.P.size() > lbmk::kTransferMax) return fail(dst, LBM_ERR_ARG, "too many source patches");
+  // the source state must be complete before the destination reads it
+  if (cudaError_t e = cudaStreamSynchronize(src->stream)) return cuda_check(dst, e, "lbm_transfer");
+  lbmk::TransferSrc T{};
+  T.n_src = (int)src->hg.P.size();
+  for (int k = 0; k < 3; ++k) T.n[k] = a.n[k], T.periodic[k] = dst->hg.periodic(k) ? 1 : 0;
+  for (int q = 0; q < T.n_src; ++q) {
+    const HostPatch& sp = src->hg.P[q];
+    T.p[q] = view(src, sp);
+    T.f[q] = src->base + sp.off_f[sp.cur];
+    T.level[q] = sp.level;
+    T.beta[q] = sp.beta;
+  }
+  auto* count = at<unsigned long long>(dst, dst->off_partial);
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), dst->stream);
+  for (auto& p : dst->hg.P) {
+    // own level first, then finer levels nearest first, then coarser nearest first
+    std::vector<int> order(T.n_src);
+    for (int q = 0; q < T.n_src; ++q) order[q] = q;
+    auto rank = [&](int q) {
+      const int dl = T.level[q] - p.level;
+      return dl >= 0 ? dl : 1000 - dl;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return rank(x) < rank(y); });
+    for (int q = 0; q < T.n_src; ++q) T.order[q] = order[q];
+    if (!e)
+      e = lbmk::launch_transfer(a.storage, view(dst, p), dst->base + p.off_f[0], dst->base + p.off_f[1], p.level,
+                                p.beta, a.u_in, T, count, dst->stream);
+  }
+  unsigned long long host = 0;
+  if (!e) e = cudaMemcpyAsync(&host, count, sizeof host, cudaMemcpyDeviceToHost, dst->stream);
+  if (!e) e = cudaStreamSynchronize(dst->stream);
+  if (e) return cuda_check(dst, e, "lbm_transfer");
+  if (missing) *missing = (int64_t)host;
+  return LBM_OK;
 }
 
 lbm_status lbm_gamma_blocks(lbm_grid_t g, int32_t patch, int32_t block, float* out) {

@@ -349,6 +349,140 @@ __device__ __forceinline__ void load_node(const PatchDev& p, const S* __restrict
   });
 }
 
+// ---------------------------------------------------------------------------
+// State transfer onto another layout (regridding; the paper leaves adaptive
+// refinement to future work).  Each node of the destination patch takes the
+// state of the source level nearest its own that holds it (the host orders
+// the source patches: own level, finer nearest first, coarser nearest first):
+// the coinciding node when that level is as fine or finer, else a trilinear
+// interpolation of rho, u and f - f^eq over the corners of non-zero weight of
+// the source cell around it.  The stored (post-collision) f - f^eq is scaled
+// by (1 - 2 beta_t)/(1 - 2 beta_s) beta_s/(r beta_t), r = dx_s / dx_t (Eq.
+// f_neq_rescaling_iso for the pre-collision part, times the post-collision
+// factor of each level), and dropped where 1 - 2 beta_s vanishes.  Solid and
+// hole nodes take the rest state, inlet nodes the inflow equilibrium; both
+// destination buffers are written.  Nodes no source level holds take the rest
+// state and are counted in *missing.
+template <typename S, typename R>
+__device__ __forceinline__ bool src_node(const TransferSrc& T, int k, long long Y0, long long Y1, long long Y2,
+                                         long long& idx) {
+  const PatchDev& q = T.p[k];
+  long long Y[3] = {Y0, Y1, Y2};
+  for (int a = 0; a < 3; ++a) {
+    if (T.periodic[a]) {
+      const long long P = (long long)T.n[a] << T.level[k];
+      Y[a] = ((Y[a] % P) + P) % P;
+    }
+    Y[a] -= q.org[a];
+    if (Y[a] < 0 || Y[a] >= q.dim[a]) return false;
+  }
+  idx = node_index(q, (int)Y[0], (int)Y[1], (int)Y[2]);
+  const uint8_t t = q.type[idx];
+  return t != T_SKIP && t != T_SOLID;
+}
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(128) k_transfer(PatchDev p, S* __restrict__ f0, S* __restrict__ f1, int level,
+                                                  R beta_t, R uix, R uiy, R uiz, TransferSrc T,
+                                                  unsigned long long* missing) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= p.dim[0]) return;
+  const long long own = node_index(p, x, y, z);
+  const uint8_t t = p.type[own];
+  R fo[27];
+  if (t == T_SKIP || t == T_SOLID || t == T_INLET) {
+    const bool in = t == T_INLET;
+    feq_dev(R(0), R(1), in ? uix : R(0), in ? uiy : R(0), in ? uiz : R(0), fo);
+    store_node<S, R>(p, f0, own, fo);
+    store_node<S, R>(p, f1, own, fo);
+    return;
+  }
+  const long long X[3] = {(long long)p.org[0] + x, (long long)p.org[1] + y, (long long)p.org[2] + z};
+  bool done = false;
+  for (int o = 0; o < T.n_src && !done; ++o) {
+    const int k = T.order[o];
+    const int dl = T.level[k] - level;
+    R rt = 0, ux = 0, uy = 0, uz = 0, neq[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) neq[i] = 0;
+    bool ok = true;
+    if (dl >= 0) {
+      long long n;
+      ok = src_node<S, R>(T, k, X[0] << dl, X[1] << dl, X[2] << dl, n);
+      if (ok) {
+        R f[27], fe[27];
+        load_node<S, R>(T.p[k], static_cast<const S*>(T.f[k]), n, f);
+        R rho;
+        macro(f, rt, rho, ux, uy, uz);
+        feq_dev(rt, rho, ux, uy, uz, fe);
+#pragma unroll
+        for (int i = 0; i < 27; ++i) neq[i] = f[i] - fe[i];
+      }
+    } else {
+      const long long sdiv = 1LL << (-dl);
+      long long base[3];
+      R fr[3];
+      for (int a = 0; a < 3; ++a) {
+        base[a] = X[a] >= 0 ? X[a] / sdiv : -((-X[a] + sdiv - 1) / sdiv);
+        fr[a] = (R)(double)(X[a] - base[a] * sdiv) / (R)(double)sdiv;
+      }
+      for (int c = 0; c < 8 && ok; ++c) {
+        R w = 1;
+        long long Y[3];
+        for (int a = 0; a < 3; ++a) {
+          const int bit = (c >> a) & 1;
+          w *= bit ? fr[a] : R(1) - fr[a];
+          Y[a] = base[a] + bit;
+        }
+        if (w == R(0)) continue;
+        long long n;
+        if (!src_node<S, R>(T, k, Y[0], Y[1], Y[2], n)) {
+          ok = false;
+          break;
+        }
+        R f[27], fe[27], r1, rho1, u1x, u1y, u1z;
+        load_node<S, R>(T.p[k], static_cast<const S*>(T.f[k]), n, f);
+        macro(f, r1, rho1, u1x, u1y, u1z);
+        feq_dev(r1, rho1, u1x, u1y, u1z, fe);
+        rt += w * r1;
+        ux += w * u1x;
+        uy += w * u1y;
+        uz += w * u1z;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) neq[i] += w * (f[i] - fe[i]);
+      }
+    }
+    if (!ok) continue;
+    const double r = ldexp(1.0, -dl);  // dx_s / dx_t
+    const double bs = T.beta[k], post_s = 1.0 - 2.0 * bs, post_t = 1.0 - 2.0 * (double)beta_t;
+    const R factor = fabs(post_s) < 1e-12 ? R(0) : (R)((post_t / post_s) * bs / (r * (double)beta_t));
+    feq_dev(rt, R(1) + rt, ux, uy, uz, fo);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) fo[i] += factor * neq[i];
+    done = true;
+  }
+  if (!done) {
+    feq_dev(R(0), R(1), R(0), R(0), R(0), fo);
+    atomicAdd(missing, 1ull);
+  }
+  store_node<S, R>(p, f0, own, fo);
+  store_node<S, R>(p, f1, own, fo);
+}
+
+cudaError_t launch_transfer(int storage, const PatchDev& p, void* f0, void* f1, int level, double beta,
+                            const double u_in[3], const TransferSrc& T, unsigned long long* missing,
+                            cudaStream_t st) {
+  return dispatch(storage, [&](auto ts, auto tr) {
+    using S = typename decltype(ts)::type;
+    using R = typename decltype(tr)::type;
+    dim3 block(128), grid((p.dim[0] + 127) / 128, p.dim[1], p.dim[2]);
+    k_transfer<S, R><<<grid, block, 0, st>>>(p, (S*)f0, (S*)f1, level, (R)beta, (R)u_in[0], (R)u_in[1],
+                                             (R)u_in[2], T, missing);
+    return cudaGetLastError();
+  });
+}
+
 template <typename V>
 __device__ __forceinline__ void stv(void* p, long long i, double v) {
   ((V*)p)[i] = (V)v;

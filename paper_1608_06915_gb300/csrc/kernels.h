@@ -154,6 +154,22 @@ struct CopySegs {
 };
 cudaError_t launch_copy(const CopySegs& segs, cudaStream_t st);
 
+// Source patches of a state transfer (regridding): views, current f buffers,
+// levels and betas, and the order in which a destination level tries them.
+constexpr int kTransferMax = 16;
+struct TransferSrc {
+  PatchDev p[kTransferMax];
+  const void* f[kTransferMax];
+  int level[kTransferMax];
+  double beta[kTransferMax];
+  int order[kTransferMax];
+  int n_src;
+  int n[3];
+  int periodic[3];
+};
+cudaError_t launch_transfer(int storage, const PatchDev& p, void* f0, void* f1, int level, double beta,
+                            const double u_in[3], const TransferSrc& T, unsigned long long* missing,
+                            cudaStream_t st);
 cudaError_t launch_gamma_blocks(int storage, const PatchDev& p, const void* fin, double beta, int lbgk, int B,
                                 float* out, int* status, cudaStream_t st);
 cudaError_t launch_diag(int storage, const PatchDev& p, const void* fin, double vol_weight, const Force& F,

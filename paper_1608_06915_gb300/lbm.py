@@ -84,6 +84,7 @@ def lib():
             "lbm_step": [vp, i64],
             "lbm_moments": [vp, i32, vp, vp, vp, vp, i32],
             "lbm_gamma_blocks": [vp, i32, i32, vp],
+            "lbm_transfer": [vp, vp, ctypes.POINTER(i64)],
             "lbm_get_populations": [vp, i32, i32, vp, i32],
             "lbm_set_populations": [vp, i32, i32, vp, i32],
             "lbm_force": [vp, dp, dp],
@@ -228,6 +229,13 @@ class Grid:
         out = torch.empty(nb, dtype=torch.float32, device=self.buffer.device)
         _check(lib().lbm_gamma_blocks(self.handle, int(p), int(block), self._ptr(out)), self.handle)
         return out
+
+    def transfer_from(self, src: "Grid") -> int:
+        """Take the state of another grid of the same domain onto this layout
+        (lbm_transfer); returns the number of fluid nodes no source level holds."""
+        n = ctypes.c_int64()
+        _check(lib().lbm_transfer(self.handle, src.handle, ctypes.byref(n)), self.handle)
+        return n.value
 
     def mask(self, p: int) -> np.ndarray:
         out = np.empty(self.shape(p), dtype=np.uint8)

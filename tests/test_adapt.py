@@ -130,3 +130,67 @@ def test_refinement_boxes_cover_the_rough_region():
     assert lev == 1
     assert lo[0] <= 18 and hi[0] >= 22 and lo[1] <= 10 and hi[1] >= 14 and lo[2] <= 14 and hi[2] >= 18, boxes
     assert all(hi[a] - lo[a] < 24 for a in range(3)), boxes  # not the whole domain
+
+
+def _load_from_oracle(g, o):
+    import torch
+    for p in range(len(o.patches)):
+        g.set_populations(p, torch.from_numpy(o.get_pop(p)).cuda())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_transfer_matches_the_oracle_and_steps_on(storage, tol):
+    """A two-level state (after four oracle steps) moved onto a layout with
+    the level-1 box shifted and a level-2 box added: every node against the
+    oracle's own transfer (reading R9), then two more coarse steps on both."""
+    from oracle import oracle as O
+    from paper_1608_06915_gb300 import lbm as L
+    src_case = I.tgv_case(n=16, box=(4, 12), nu=0.005)
+    o_src = O.Oracle(src_case)
+    for p, info in enumerate(o_src.patches):
+        x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+        o_src.init_equilibrium(p, *I.tgv_fields(x, y, z, n=16))
+    o_src.step(4)
+    g_src = L.Grid(src_case, storage)
+    _load_from_oracle(g_src, o_src)
+    dst_case = dict(src_case, boxes=[(1, (6, 5, 6), (15, 13, 14)), (2, (8, 7, 8), (12, 11, 12))])
+    o_dst = O.Oracle(dst_case)
+    g_dst = L.Grid(dst_case, storage)
+    assert o_dst.transfer_from(o_src) == 0
+    assert g_dst.transfer_from(g_src) == 0
+    for step in range(3):
+        for p in range(len(o_dst.patches)):
+            m = o_dst.mask(p) == 1
+            d = np.max(np.abs(g_dst.get_populations(p).cpu().numpy()[:, m] - o_dst.get_pop(p)[:, m]))
+            assert d < tol, (step, p, d)
+        o_dst.step(1)
+        g_dst.step(1)
+
+
+@pytest.mark.gpu
+def test_regrid_from_the_indicator():
+    """Indicator, boxes and transfer together: a rough region gets a level-1
+    box, the state moves onto the new layout with no node left without a
+    source, and the new grid steps on, its mass kept."""
+    import torch
+    from paper_1608_06915_gb300 import lbm as L
+    case = I.tgv_case(n=32, refined=False, nu=0.002)
+    g = L.Grid(case, "fp64")
+    info = g.patches[0]
+    x, y, z = I.node_positions(info["level"], info["org"], info["dim"])
+    rng = np.random.default_rng(43)
+    rough = (np.abs(x - 16) < 3) & (np.abs(y - 16) < 3) & (np.abs(z - 16) < 3)
+    u = 0.04 * rough * rng.standard_normal((3,) + x.shape)
+    g.init_equilibrium(0, torch.ones(x.shape, dtype=torch.float64).cuda(), torch.from_numpy(u).cuda())
+    g.step(2)
+    dev = g.gamma_blocks(0, 4).cpu().numpy()
+    boxes = A.refinement_boxes(g, case, 0, block=4, threshold=0.5 * float(dev.max()))
+    assert len(boxes) == 1
+    new, missing = A.regrid(g, case, boxes)
+    assert missing == 0 and len(new.patches) == 2
+    m0 = new.diagnostics()["mass"]  # on the new layout (the level weighting differs from the old one)
+    new.step(5)
+    d = new.diagnostics()
+    assert d["status"] == 0
+    assert abs(d["mass"] - m0) < 1e-4 * m0, (d["mass"], m0)
