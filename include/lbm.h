@@ -13,7 +13,10 @@
  *     rule), centred four-point Lagrange reconstruction (Sec. III.B,
  *     Eq. interp) and the five-step algorithm without time interpolation
  *     (Sec. III.C), with the fine level taking two steps per parent step;
- *   - a body force by the exact difference method, du_f = du_c / r (Sec. III.A).
+ *   - a body force by the exact difference method, du_f = du_c / r (Sec. III.A);
+ *   - around the method: the momentum-exchange drag, a discrete adjoint of the
+ *     refined step, the refinement indicator |gamma - 2| the paper proposes
+ *     (Sec. IV and its conclusion) and a state transfer onto a new layout.
  *
  * Conventions
  *   Velocities: i = (cx+1) + 3(cy+1) + 9(cz+1); rest i = 13; opposite 26 - i.
