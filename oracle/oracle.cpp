@@ -582,7 +582,8 @@ struct Sim {
           double rho = 0, u[3] = {0, 0, 0};
           Pop neq{};
           if (dl >= 0) {
-            long Y[3] = {X[0] << dl, X[1] << dl, X[2] << dl};
+            const long sc = 1L << dl;
+            long Y[3] = {X[0] * sc, X[1] * sc, X[2] * sc};
             src.wrap(q.level, Y);
             long n = src.index_of(q, Y);
             if (n < 0 || q.solid[n] || !q.vpost[n]) continue;

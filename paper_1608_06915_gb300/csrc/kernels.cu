@@ -409,7 +409,8 @@ __global__ void __launch_bounds__(128) k_transfer(PatchDev p, S* __restrict__ f0
     bool ok = true;
     if (dl >= 0) {
       long long n;
-      ok = src_node<S, R>(T, k, X[0] << dl, X[1] << dl, X[2] << dl, n);
+      const long long sc = 1LL << dl;
+      ok = src_node<S, R>(T, k, X[0] * sc, X[1] * sc, X[2] * sc, n);
       if (ok) {
         R f[27], fe[27];
         load_node<S, R>(T.p[k], static_cast<const S*>(T.f[k]), n, f);
