@@ -120,3 +120,20 @@ def test_thermal_parameters_validated(L):
         case["thermal"] = dict(case["thermal"], **bad)
         with pytest.raises(L.LbmError):
             L.Grid(case, bind=False)
+
+
+def test_indicator_and_transfer_refuse_unbound_grids(L):
+    """lbm_gamma_blocks and lbm_transfer check their arguments before any
+    device work: an unbound grid is LBM_ERR_STATE, a bad block or patch
+    LBM_ERR_ARG (no GPU needed)."""
+    import ctypes
+    lib = L.lib()
+    a = L.Grid(I.tgv_case(n=16, box=(4, 12)), bind=False)
+    b = L.Grid(I.tgv_case(n=16, refined=False), bind=False)
+    assert lib.lbm_gamma_blocks(a.handle, 0, 4, ctypes.c_void_p(16)) == -7  # LBM_ERR_STATE: unbound
+    assert lib.lbm_gamma_blocks(a.handle, 5, 4, ctypes.c_void_p(16)) == -1  # no patch 5
+    n = ctypes.c_int64(-1)
+    assert lib.lbm_transfer(a.handle, b.handle, ctypes.byref(n)) == -7
+    assert lib.lbm_transfer(a.handle, a.handle, ctypes.byref(n)) == -1
+    assert lib.lbm_transfer(None, b.handle, ctypes.byref(n)) == -1
+    assert n.value == -1
