@@ -128,7 +128,7 @@ def refinement_boxes(grid, case: dict, patch: int, block: int = 4, threshold: fl
         trial = dict(case, boxes=list(case.get("boxes", [])) + new)
         try:
             L.Grid(trial, grid.storage, bind=False)
-        except Exception:
+        except L.LbmError:  # the layout validation rejected these boxes
             continue
         return new
     return []

@@ -51,7 +51,7 @@ def test_widened_merged_boxes_pass_the_layout_validation():
     boxes = A.merge_boxes([A.widen(b, 8.0, case["n"]) for b in raw], 8.0)
     assert len(boxes) == 1
     L.Grid(dict(case, boxes=[(1, lo, hi) for lo, hi in boxes]), "fp32", bind=False)
-    with pytest.raises(Exception):  # as they came, the boxes are too narrow and too close
+    with pytest.raises(L.LbmError):  # as they came, the boxes are too narrow and too close
         L.Grid(dict(case, boxes=[(1, lo, hi) for lo, hi in raw]), "fp32", bind=False)
 
 
