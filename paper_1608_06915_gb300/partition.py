@@ -10,7 +10,10 @@ rest of the step stays on the rank that owns the node.
 This module holds the host-side logic: slab bounds, which populations cross a
 face, packing and unpacking them, the exchange over torch.distributed
 (point-to-point send/recv, so any backend), and the local pull over a slab
-with its ghost layers.  Populations are arrays [27][nz][ny][nx] (x fastest),
+with its ghost layers.  For refined layouts it also gives the slabs of every
+level, aligned with the coarse slabs so that coarse/fine twins stay on one
+rank, the parent halo the interface coupling needs beyond a slab edge, and
+a deterministic FP64 all-reduce for the diagnostics.  Populations are arrays [27][nz][ny][nx] (x fastest),
 velocity order i = (cx+1) + 3(cy+1) + 9(cz+1); y and z are periodic within
 every slab.
 """
@@ -87,3 +90,61 @@ def exchange(f: np.ndarray, rank: int, ranks: int, dist) -> tuple:
     for r in reqs:
         r.wait()
     return from_left.numpy(), from_right.numpy()
+
+
+# ---------------------------------------------------------------------------
+# Refined layouts
+
+def level_slab(nx: int, ranks: int, rank: int, level: int) -> tuple:
+    """[x0, x1) of rank's slab on ``level`` in that level's node coordinates:
+    the coarse slab of slab_bounds scaled by 2^level, so every level-l node
+    that coincides with a coarse node lies on the rank owning that coarse node
+    (twins of the coupling, Sec. III.A, stay on one rank)."""
+    a, b = slab_bounds(nx, ranks, rank)
+    s = 1 << level
+    return a * s, b * s
+
+
+def owner(x_level: int, nx: int, ranks: int, level: int) -> int:
+    """Rank owning the level node with x coordinate ``x_level`` (periodic in x)."""
+    period = nx << level
+    x = x_level % period
+    for r in range(ranks):
+        a, b = level_slab(nx, ranks, r, level)
+        if a <= x < b:
+            return r
+    raise ValueError("no owner")
+
+
+# Reconstruction samples sit at +-1/2 and +-3/2 parent spacings from a
+# reconstructed child node along each off-lattice axis (the centred four-point
+# Lagrange rule, Eq. interp), and each sample is a parent (or coinciding child)
+# node; the pull of every sample node reaches one parent spacing further.
+SAMPLE_OFFSETS = (-1.5, -0.5, 0.5, 1.5)
+
+
+def parent_halo() -> tuple:
+    """Parent layers (below, above) a slab that the coupling of the slab's
+    child nodes reads, with level slabs as level_slab gives them: a child
+    slab [2a, 2b) starts on parent node a and ends half a parent spacing past
+    parent node b - 1.  The first off-lattice child node (a + 1/2) samples
+    down to parent node a - 1, the last (b - 1/2) up to b + 1, and each
+    sample is the pulled state of its node, one layer further."""
+    first, last = 0.5, -0.5  # parent coordinates relative to a and to b
+    below = -(first + min(SAMPLE_OFFSETS)) + 1  # a - 1, then its pull
+    above = (last + max(SAMPLE_OFFSETS)) + 1 + 1  # b + 1 is layer 2 past b - 1, then its pull
+    return int(below), int(above)
+
+
+def allreduce_sums(values, dist) -> np.ndarray:
+    """FP64 sums of per-rank partial values, identical on every rank and equal
+    to the serial sum in rank order: all-gather, then add rank by rank (an
+    all-reduce's own order of additions may differ between ranks and runs)."""
+    import torch
+    v = torch.as_tensor(np.asarray(values, dtype=np.float64))
+    parts = [torch.empty_like(v) for _ in range(dist.get_world_size())]
+    dist.all_gather(parts, v)
+    total = np.zeros(v.shape, dtype=np.float64)
+    for p in parts:
+        total = total + p.numpy()
+    return total

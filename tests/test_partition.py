@@ -110,3 +110,67 @@ def test_two_gloo_ranks_match_the_unsplit_oracle(tmp_path):
     o.step(3)
     split = np.concatenate([np.load(tmp_path / ("slab%d.npy" % r)) for r in range(world)], axis=-1)
     assert np.array_equal(split, o.get_pop(0))
+
+
+# ---------------------------------------------------------------------------
+# Refined layouts: aligned level slabs, the coupling's parent halo, FP64 sums
+
+def test_level_slabs_keep_twins_on_one_rank():
+    nx = 13
+    for P in (1, 2, 3, 4):
+        for level in (1, 2):
+            spans = [PT.level_slab(nx, P, r, level) for r in range(P)]
+            assert spans[0][0] == 0 and spans[-1][1] == nx << level
+            assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
+            for x in range(nx << level):
+                r = PT.owner(x, nx, P, level)
+                if x % (1 << level) == 0:  # coincides with a coarse node: same rank
+                    assert r == PT.owner(x >> level, nx, P, 0)
+
+
+def test_parent_halo_covers_every_reconstruction_sample():
+    """Brute force over the child nodes of each slab: every parent sample of
+    the four-point rule, and every pull source of it, lies within the
+    parent_halo() layers below and above the slab, and both bounds are reached."""
+    hl, hh = PT.parent_halo()
+    assert (hl, hh) == (2, 3)
+    nx, P = 12, 3
+    for r in range(P):
+        a, b = PT.slab_bounds(nx, P, r)  # parent (coarse) slab [a, b)
+        lo, hi = a, b - 1
+        for xc in range(2 * a, 2 * b):  # the slab's child nodes, child units
+            if xc % 2 == 0:
+                continue  # on the parent lattice along x: no interpolation along x
+            for off in PT.SAMPLE_OFFSETS:
+                xs = xc / 2.0 + off  # parent node of the sample
+                assert xs == int(xs)
+                for pull in (-1, 0, 1):  # the sample is the pulled state of that node
+                    lo, hi = min(lo, xs + pull), max(hi, xs + pull)
+        assert (lo, hi) == (a - hl, b - 1 + hh), (r, lo, hi)
+
+
+def _sum_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(100 + rank)
+        mine = rng.standard_normal(8) * 10.0 ** rng.integers(-8, 8, 8)
+        tot = PT.allreduce_sums(mine, dist)
+        np.save(os.path.join(out_dir, "sum%d.npy" % rank), tot)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_allreduce_sums_equal_the_serial_sum_on_every_rank(tmp_path):
+    import torch.multiprocessing as mp
+    world = 2
+    mp.spawn(_sum_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    parts = [np.random.default_rng(100 + r) for r in range(world)]
+    serial = np.zeros(8)
+    for g in parts:
+        serial = serial + g.standard_normal(8) * 10.0 ** g.integers(-8, 8, 8)
+    for r in range(world):
+        assert np.array_equal(np.load(tmp_path / ("sum%d.npy" % r)), serial)
