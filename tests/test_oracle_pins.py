@@ -709,10 +709,10 @@ def _mr(f):
 
 
 def test_transfer_carries_the_chapman_enskog_state_of_a_shear_flow():
-    # Uniform shear u_x = S y, LBGK mirror: the first-order non-equilibrium part
-    # before collision is -(1/(2 beta)) (rho W_i / c_s^2) (c_ix c_iy) 2 S per
-    # level lattice unit, and the stored state after collision carries (1 - 2 beta)
-    # times it.  Built this way on one level and moved onto a level-1 box, the
+    # Uniform shear u_x = S y, LBGK mirror: the Chapman-Enskog first-order
+    # non-equilibrium part before collision is -tau (rho W_i / c_s^2) c_ix c_iy S
+    # with tau = 1/(2 beta) and S per level lattice unit, and the stored state
+    # after collision carries (1 - 2 beta) times it.  Built this way on one level and moved onto a level-1 box, the
     # fine nodes must hold the same construction with the fine beta and the fine
     # gradient S/2 (the rescaling of Eq. f_neq_rescaling_iso, post-collision).
     n, S = 32, 1e-3
@@ -721,7 +721,7 @@ def test_transfer_carries_the_chapman_enskog_state_of_a_shear_flow():
 
     def ce_state(x, y, z, beta, grad):
         f = np.empty((27,) + x.shape)
-        pre = -(1.0 / (2.0 * beta)) * (W / cs2) * (C[:, 0] * C[:, 1]) * 2.0 * grad
+        pre = -(1.0 / (2.0 * beta)) * (W / cs2) * (C[:, 0] * C[:, 1]) * grad
         for idx in np.ndindex(*x.shape):
             u = np.array([S * (y[idx] - n / 2), 0.0, 0.0])
             f[(slice(None),) + idx] = O.feq(1.0, u) + (1.0 - 2.0 * beta) * pre
