@@ -98,40 +98,48 @@ def merge_boxes(boxes: list, gap: float) -> list:
     return boxes
 
 
-def refinement_boxes(grid, case: dict, patch: int, block: int = 4, threshold: float = 0.1,
-                     margin: int = 1) -> list:
-    """Candidate level-(l+1) boxes (level, lo, hi) in coarse units for the
-    blocks of ``patch`` (level l) whose largest |gamma - 2| exceeds
-    ``threshold`` (non-finite values count as flagged).  Boxes closer than the
-    layout's 8 parent spacings are merged; if the layout with the new boxes
-    added is still rejected, one bounding box of all flagged blocks is tried,
-    then none.  The grid's current state is read, not changed."""
+def boxes_from_flags(flags: np.ndarray, info: dict, block: int, case: dict, margin: int = 1,
+                     storage: str = "fp32"):
+    """The full box list (all levels) of a layout that covers the flagged
+    blocks ([z][y][x] bools over a level-l patch's storage box, ``info`` as
+    in Grid.patches) with level-(l+1) boxes, or None when nothing is flagged
+    or no valid layout is found.  The new boxes are widened to the layout's
+    minimum width and merged with each other and with the existing
+    level-(l+1) boxes while closer than 8 parent spacings; if that layout is
+    rejected, one bounding box of all of them is tried."""
     from . import lbm as L
-    info = grid.patches[patch]
-    dev = grid.gamma_blocks(patch, block).cpu().numpy()
-    flags = ~(dev <= threshold)
     cl = clusters(flags)
     if not cl:
-        return []
+        return None
     spacing = 8.0 / (1 << info["level"])  # 8 parent spacings in coarse units
-    boxes = [widen(block_box_to_coarse(info, block, lo, hi, margin, case["n"]), spacing, case["n"])
-             for lo, hi in cl]
     lev = info["level"] + 1
-    boxes = merge_boxes(boxes, spacing)
-    candidates = [boxes]
-    if len(boxes) > 1:
-        lo = tuple(min(b[0][a] for b in boxes) for a in range(3))
-        hi = tuple(max(b[1][a] for b in boxes) for a in range(3))
+    new = [widen(block_box_to_coarse(info, block, lo, hi, margin, case["n"]), spacing, case["n"])
+           for lo, hi in cl]
+    old = [(tuple(b[1]), tuple(b[2])) for b in case.get("boxes", []) if b[0] == lev]
+    keep = [b for b in case.get("boxes", []) if b[0] != lev]
+    merged = merge_boxes(old + new, spacing)
+    candidates = [merged]
+    if len(merged) > 1:
+        lo = tuple(min(b[0][a] for b in merged) for a in range(3))
+        hi = tuple(max(b[1][a] for b in merged) for a in range(3))
         candidates.append([(lo, hi)])
     for cand in candidates:
-        new = [(lev, lo, hi) for lo, hi in cand]
-        trial = dict(case, boxes=list(case.get("boxes", [])) + new)
+        boxes = keep + [(lev, lo, hi) for lo, hi in cand]
         try:
-            L.Grid(trial, grid.storage, bind=False)
+            L.Grid(dict(case, boxes=boxes), storage, bind=False)
         except L.LbmError:  # the layout validation rejected these boxes
             continue
-        return new
-    return []
+        return boxes
+    return None
+
+
+def refinement_boxes(grid, case: dict, patch: int, block: int = 4, threshold: float = 0.1, margin: int = 1):
+    """The full box list of a layout refining the blocks of ``patch`` whose
+    largest |gamma - 2| (lbm_gamma_blocks) exceeds ``threshold``; non-finite
+    values count as flagged.  None when nothing is flagged or no valid layout
+    is found (boxes_from_flags).  The grid's state is read, not changed."""
+    dev = grid.gamma_blocks(patch, block).cpu().numpy()
+    return boxes_from_flags(~(dev <= threshold), grid.patches[patch], block, case, margin, grid.storage)
 
 
 def regrid(grid, case: dict, boxes: list):

@@ -39,6 +39,26 @@ def test_merge_boxes_until_separated():
     assert len(A.merge_boxes([((0, 0, 0), (3, 3, 3)), ((0, 20, 0), (3, 23, 3))], 8)) == 2
 
 
+def test_boxes_from_flags_merges_with_existing_boxes():
+    """Flagged blocks next to an existing level-1 box join it; far ones get a
+    box of their own; the resulting layouts pass the validation."""
+    from paper_1608_06915_gb300 import lbm as L
+    case = I.tgv_case(n=48, box=(8, 18))  # one level-1 box [8, 18]^3
+    info = dict(level=0, org=(0, 0, 0), dim=(48, 48, 48))
+    f = np.zeros((12, 12, 12), dtype=bool)  # blocks of 4 nodes
+    f[4, 4, 5] = True  # x 20..23, y 16..19, z 16..19: within 8 of the existing box
+    boxes = A.boxes_from_flags(f, info, 4, case)
+    assert boxes is not None and len(boxes) == 1
+    lev, lo, hi = boxes[0]
+    assert lev == 1 and lo[0] <= 8 and hi[0] >= 23 and lo[1] <= 8 and hi[1] >= 19
+    f = np.zeros((12, 12, 12), dtype=bool)
+    f[9, 9, 9] = True  # x, y, z 36..39: far from it
+    boxes = A.boxes_from_flags(f, info, 4, case)
+    assert boxes is not None and len(boxes) == 2 and (1, (8, 8, 8), (18, 18, 18)) in boxes
+    L.Grid(dict(case, boxes=boxes), "fp32", bind=False)
+    assert A.boxes_from_flags(np.zeros((12, 12, 12), dtype=bool), info, 4, case) is None
+
+
 def test_widen_keeps_boxes_inside_the_domain():
     assert A.widen(((10, 10, 10), (12, 10, 11)), 8, (32, 32, 32)) == ((7, 6, 7), (15, 14, 15))
     assert A.widen(((0, 0, 29), (1, 2, 31)), 8, (32, 32, 32)) == ((0, 0, 23), (8, 8, 31))
