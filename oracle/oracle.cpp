@@ -58,7 +58,9 @@
 //       f^eq itself); the same tensor P1 enters g* (Table I row g*).
 //
 // Parity status: every function above is pinned by tests under tests/
-// (closed forms, invariants, special cases, brute force).
+// (closed forms, invariants, special cases, brute force, a two-level run
+// against a uniform run at the fine spacing, and the Chapman-Enskog state of
+// a shear flow through the interface rescaling).
 
 #include <algorithm>
 #include <array>
@@ -375,6 +377,71 @@ double thermal_collide(const Pop& f, const Pop& g, double beta, double beta1, do
   Pop gs = pr_gt1 ? gstar_gt1(f, tm.rho, tm.u, tm.E2rho, T0) : gstar(f, g, tm.rho, tm.u, tm.E2rho, T0);
   for (int i = 0; i < Q; ++i) go[i] = g[i] + 2.0 * beta * (ge[i] - g[i]) + 2.0 * (beta - beta1) * (gs[i] - ge[i]);
   return gamma;
+}
+
+// Non-equilibrium moments for the thermal g rescaling: P1 = sum cc (f - f^eq) (Sec. III.A, thermal).
+void p1_tensor(const Pop& f, const Pop& fe, double P1[3][3]) {
+for (int a = 0; a < 3; ++a)
+  for (int b = 0; b < 3; ++b) {
+    double acc = 0;
+    for (int i = 0; i < Q; ++i) acc += cvel(i, a) * cvel(i, b) * (f[i] - fe[i]);
+    P1[a][b] = acc;
+  }
+}
+
+// Interface rescaling of Sec. III.A: the non-equilibrium part of (f, g) moves
+// from a level with (beta_s, beta1_s) to one with (beta_t, beta1_t);
+// factor = beta_s / (r_st beta_t), r_st = dx_s / dx_t (2 for coarse-to-fine,
+// 1/2 for fine-to-coarse).  Isothermal model: Eq. f_neq_rescaling_iso on the
+// whole f - f^eq.  Thermal model: f as Eq. f_neq_rescaling_iso (Pr <= 1) or
+// Eq. f_neq_rescaling_thr_Prgr1 (Pr > 1); g by the thermal rule of Sec. III.A,
+// the part W_i 2 u_b P1_ab c_ia / T0 taken out, the rest rescaled with the
+// other ratio, and the part added back with the rescaled P1.
+void interface_rescale(bool thermal, bool pr_gt1, double t0, const Pop& f, const Pop& g, double beta_s,
+                     double beta_t, double beta1_s, double beta1_t, double r_st, Pop& fo, Pop& go,
+                     Pop* fneq_out, Pop* gneq_out, Macro* mac_out, ThermalMacro* tmac_out) {
+  double ff = beta_s / (r_st * beta_t);
+  if (!thermal) {
+    Macro mc = macro(f);
+    Pop fe = feq(mc.rho, mc.u);
+    for (int i = 0; i < Q; ++i) fo[i] = fe[i] + ff * (f[i] - fe[i]);
+    if (fneq_out)
+      for (int i = 0; i < Q; ++i) (*fneq_out)[i] = ff * (f[i] - fe[i]);
+    if (mac_out) *mac_out = mc;
+    return;
+  }
+  ThermalMacro tm = thermal_macro(f, g);
+  Pop fe = feq(tm.rho, tm.u);
+  Pop ge = geq(tm.rho, tm.u, tm.E2rho, t0);
+  // Sec. III.A thermal model: for Pr <= 1, f^neq and P1 scale with the beta
+  // ratio and the rest of g^neq with the beta1 ratio; for Pr > 1 the two
+  // ratios swap (Eq. f_neq_rescaling_thr_Prgr1 and the g rescaling after it)
+  double fg = beta1_s / (r_st * beta1_t);
+  if (pr_gt1) std::swap(ff, fg);
+  for (int i = 0; i < Q; ++i) fo[i] = fe[i] + ff * (f[i] - fe[i]);
+  double P1s[3][3], P1t[3][3];
+  p1_tensor(f, fe, P1s);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) P1t[a][b] = ff * P1s[a][b];
+  Pop gneq;
+  for (int i = 0; i < Q; ++i) {
+    double ts = 0, tt = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        ts += 2.0 * tm.u[b] * P1s[a][b] * cvel(i, a);
+        tt += 2.0 * tm.u[b] * P1t[a][b] * cvel(i, a);
+      }
+    gneq[i] = fg * ((g[i] - ge[i]) - Wi(i) * ts / t0) + Wi(i) * tt / t0;
+    go[i] = ge[i] + gneq[i];
+  }
+  if (fneq_out)
+    for (int i = 0; i < Q; ++i) (*fneq_out)[i] = ff * (f[i] - fe[i]);
+  if (gneq_out) *gneq_out = gneq;
+  if (mac_out) {
+    mac_out->rho = tm.rho;
+    for (int a = 0; a < 3; ++a) mac_out->u[a] = tm.u[a];
+  }
+  if (tmac_out) *tmac_out = tm;
 }
 
 // ---------------------------------------------------------------------------
@@ -872,64 +939,13 @@ struct Sim {
   }
 
   // ---- coupling (Sec. III.A, III.B; algorithm steps 3 and 4) ---------------
-  // Non-equilibrium moments for the thermal g rescaling: P1 = sum cc (f - f^eq) (Sec. III.A, thermal).
-  static void p1_tensor(const Pop& f, const Pop& fe, double P1[3][3]) {
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        double acc = 0;
-        for (int i = 0; i < Q; ++i) acc += cvel(i, a) * cvel(i, b) * (f[i] - fe[i]);
-        P1[a][b] = acc;
-      }
-  }
-
   // Rescale the non-equilibrium part of (f, g) from a level with (beta_s, beta1_s)
-  // to one with (beta_t, beta1_t); factor = beta_s / (r_st beta_t) where
-  // r_st = dx_s / dx_t (2 for coarse-to-fine, 1/2 for fine-to-coarse).
+  // to one with (beta_t, beta1_t): interface_rescale with this simulation's model.
   void rescale(const Pop& f, const Pop& g, double beta_s, double beta_t, double beta1_s, double beta1_t,
                double r_st, Pop& fo, Pop& go, Pop* fneq_out, Pop* gneq_out, Macro* mac_out,
                ThermalMacro* tmac_out) const {
-    double ff = beta_s / (r_st * beta_t);
-    if (!thermal) {
-      Macro mc = macro(f);
-      Pop fe = feq(mc.rho, mc.u);
-      for (int i = 0; i < Q; ++i) fo[i] = fe[i] + ff * (f[i] - fe[i]);
-      if (fneq_out)
-        for (int i = 0; i < Q; ++i) (*fneq_out)[i] = ff * (f[i] - fe[i]);
-      if (mac_out) *mac_out = mc;
-      return;
-    }
-    ThermalMacro tm = thermal_macro(f, g);
-    Pop fe = feq(tm.rho, tm.u);
-    Pop ge = geq(tm.rho, tm.u, tm.E2rho, d.t0);
-    // Sec. III.A thermal model: for Pr <= 1, f^neq and P1 scale with the beta
-    // ratio and the rest of g^neq with the beta1 ratio; for Pr > 1 the two
-    // ratios swap (Eq. f_neq_rescaling_thr_Prgr1 and the g rescaling after it)
-    double fg = beta1_s / (r_st * beta1_t);
-    if (pr_gt1()) std::swap(ff, fg);
-    for (int i = 0; i < Q; ++i) fo[i] = fe[i] + ff * (f[i] - fe[i]);
-    double P1s[3][3], P1t[3][3];
-    p1_tensor(f, fe, P1s);
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) P1t[a][b] = ff * P1s[a][b];
-    Pop gneq;
-    for (int i = 0; i < Q; ++i) {
-      double ts = 0, tt = 0;
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-          ts += 2.0 * tm.u[b] * P1s[a][b] * cvel(i, a);
-          tt += 2.0 * tm.u[b] * P1t[a][b] * cvel(i, a);
-        }
-      gneq[i] = fg * ((g[i] - ge[i]) - Wi(i) * ts / d.t0) + Wi(i) * tt / d.t0;
-      go[i] = ge[i] + gneq[i];
-    }
-    if (fneq_out)
-      for (int i = 0; i < Q; ++i) (*fneq_out)[i] = ff * (f[i] - fe[i]);
-    if (gneq_out) *gneq_out = gneq;
-    if (mac_out) {
-      mac_out->rho = tm.rho;
-      for (int a = 0; a < 3; ++a) mac_out->u[a] = tm.u[a];
-    }
-    if (tmac_out) *tmac_out = tm;
+    interface_rescale(thermal, pr_gt1(), d.t0, f, g, beta_s, beta_t, beta1_s, beta1_t, r_st, fo, go, fneq_out,
+                      gneq_out, mac_out, tmac_out);
   }
 
   // Centred four-point Lagrange weights at the midpoint of nodes x = -3,-1,1,3
@@ -1174,6 +1190,23 @@ typedef struct {
 static std::string g_last_error;
 
 const char* orc_last_error(void) { return g_last_error.c_str(); }
+
+// Interface rescaling of one node (Sec. III.A): thermal 0/1, pr_gt1 0/1;
+// g and go may be NULL for the isothermal model.
+void orc_rescale(const double* f, const double* g, double beta_s, double beta_t, double beta1_s, double beta1_t,
+                 double r_st, int thermal, int pr_gt1, double t0, double* fo, double* go) {
+  Pop F{}, G{}, FO{}, GO{};
+  for (int i = 0; i < Q; ++i) {
+    F[i] = f[i];
+    G[i] = g ? g[i] : 0.0;
+  }
+  interface_rescale(thermal != 0, pr_gt1 != 0, t0, F, G, beta_s, beta_t, beta1_s, beta1_t, r_st, FO, GO, nullptr,
+                    nullptr, nullptr, nullptr);
+  for (int i = 0; i < Q; ++i) {
+    fo[i] = FO[i];
+    if (go) go[i] = GO[i];
+  }
+}
 
 void orc_set_threads(int n) {
 #ifdef _OPENMP

@@ -96,6 +96,8 @@ def lib():
             L.orc_thermal_collide.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp]
             L.orc_lagrange_weights.argtypes = [dp]
+            L.orc_rescale.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
             L.orc_transfer.restype = ctypes.c_long
             L.orc_transfer.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
             L.orc_set_threads.argtypes = [ctypes.c_int]
@@ -147,6 +149,18 @@ def thermal_collide(f, g, beta, beta1, t0=1.0 / 3.0, glambda=0.0, t_ref=0.0, pr_
     gm = lib().orc_thermal_collide(_dp(_f64(f)), _dp(_f64(g)), float(beta), float(beta1), float(t0),
                                    float(glambda), float(t_ref), 1 if pr_gt1 else 0, _dp(fo), _dp(go))
     return fo, go, gm
+
+
+def rescale(f, g, beta_s, beta_t, beta1_s=1.0, beta1_t=1.0, r=2.0, thermal=False, pr_gt1=False,
+            t0=1.0 / 3.0):
+    """Interface rescaling of one node's populations from a level with
+    (beta_s, beta1_s) to one with (beta_t, beta1_t), r = dx_s / dx_t
+    (Sec. III.A).  Returns (f, g); g is None for the isothermal model."""
+    fo, go = np.empty(Q), np.empty(Q)
+    gin = _f64(g) if g is not None else np.zeros(Q)
+    lib().orc_rescale(_dp(_f64(f)), _dp(gin), float(beta_s), float(beta_t), float(beta1_s), float(beta1_t),
+                      float(r), int(bool(thermal)), int(bool(pr_gt1)), float(t0), _dp(fo), _dp(go))
+    return fo, (go if thermal else None)
 
 
 def lagrange_weights() -> np.ndarray:
