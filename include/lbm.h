@@ -210,6 +210,18 @@ lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms
  * LBM_ERR_ARG out of range. */
 lbm_status lbm_set_variant(lbm_grid_t g, int32_t variant);
 
+/* Bound of the waits of the TMA stream-collide passes (isothermal and
+ * thermal) for a loaded stage, in suspensions of at most 0.5 us each: default
+ * 2^21 (about a second); 0 tests once without waiting.  A wait that runs out
+ * sets bit 1 of the device status word, and its warps skip the rest of their
+ * tiles after waiting (with the full bound) for the copies they may have in
+ * flight, so the nodes of those tiles keep stale values; lbm_diagnostics then
+ * returns LBM_ERR_TIMEOUT.  Only the consumers' waits take this bound; the
+ * waits that drain copies keep the full one.  Not part of the method: this is
+ * failure detection, and a small bound exists to test it.  Drops the captured
+ * step graphs.  LBM_ERR_ARG for a null grid or a negative bound. */
+lbm_status lbm_wait_limit(lbm_grid_t g, int32_t sleeps);
+
 /* lbm_step replays each coarse step as a CUDA graph, one per buffer parity of
  * level 0, captured on a private stream the first time that parity comes up
  * (the first step after lbm_grid_bind launches directly).  Replays use the
@@ -254,8 +266,14 @@ lbm_status lbm_force(lbm_grid_t g, const double* accel0, double* drag_out);
  * through any library.  The paper has no counterpart: this is plumbing.
  * Limits and rules:
  *   - at most 16 patches per grid; larger grids get LBM_ERR_ARG and a message;
+ *   - it runs on the device of the grid's bound buffer, made current for the
+ *     call (the caller's current device is restored afterwards);
  *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     With CUDA's lazy module loading (the default), that first lookup may be
+ *     where the driver loads the library's module, and with it the array,
+ *     onto the device: device memory can change on the first call only, and
+ *     later calls leave it unchanged;
  *   - every call uses the same array: calls that overlap on the GPU (two
  *     streams, or two grids at once) race and can return wrong sums.  Calls
  *     that follow one another are fine: each call writes every slot it reads.
@@ -265,8 +283,12 @@ lbm_status lbm_diagnostics_noalloc(lbm_grid_t g, double out[8]);
 /* FP64 diagnostics over owned fluid nodes (parent nodes that are not twin
  * nodes of a child, child nodes of depth >= 1), volume-weighted 8^-level:
  * out = {mass, jx, jy, jz, kinetic energy 1/2 rho |u|^2, fluid node count,
- * min rho, device status word}.  Synchronises the stream.  Returns
- * LBM_ERR_UNSTABLE when a density is non-finite or non-positive. */
+ * min rho, device status word}.  Synchronises the stream.  The status word's
+ * bit 0 flags a pull source that resolved to no node (never on a validated
+ * layout), bit 1 an expired bounded wait (lbm_wait_limit).  Returns
+ * LBM_ERR_TIMEOUT when bit 1 is set, and clears that bit, so the next call
+ * reports only new expiries; otherwise LBM_ERR_UNSTABLE when a density is
+ * non-finite or non-positive; out is filled in every case. */
 lbm_status lbm_diagnostics(lbm_grid_t g, double out[8]);
 
 /* Bytes of one checkpoint (all patches' current f and g populations). */

@@ -98,26 +98,69 @@ def merge_boxes(boxes: list, gap: float) -> list:
     return boxes
 
 
+def parent_region(info: dict, n) -> tuple:
+    """The coarse-unit closed box a next-level box must lie in to nest in the
+    level-l patch ``info``: the patch's box, less 4 level-l spacings on each
+    face that does not reach the domain's edge (an interface face), rounded
+    inwards to whole coarse units.  Level 0: the whole domain."""
+    if info["level"] == 0:
+        return tuple(0 for _ in range(3)), tuple(int(v) - 1 for v in n)
+    s = 1 << info["level"]
+    inset = -(-4 // s)  # ceil(4 / s) coarse units
+    lo, hi = [], []
+    for a in range(3):
+        plo = -(-info["org"][a] // s)
+        phi = (info["org"][a] + info["dim"][a] - 1) // s
+        lo.append(plo + inset if plo > 0 else plo)
+        hi.append(phi - inset if phi < int(n[a]) - 1 else phi)
+    return tuple(lo), tuple(hi)
+
+
+def _inside(box, region) -> bool:
+    return all(region[0][a] <= box[0][a] and box[1][a] <= region[1][a] for a in range(3))
+
+
+def _fit(box, region) -> tuple:
+    """A closed box moved inside ``region`` along each axis where it fits,
+    and clipped to it where it is wider."""
+    lo, hi = list(box[0]), list(box[1])
+    for a in range(3):
+        if hi[a] > region[1][a]:
+            lo[a] -= hi[a] - region[1][a]
+            hi[a] = region[1][a]
+        if lo[a] < region[0][a]:
+            hi[a] = min(region[1][a], hi[a] + region[0][a] - lo[a])
+            lo[a] = region[0][a]
+    return tuple(lo), tuple(hi)
+
+
 def boxes_from_flags(flags: np.ndarray, info: dict, block: int, case: dict, margin: int = 1,
                      storage: str = "fp32"):
     """The full box list (all levels) of a layout that covers the flagged
     blocks ([z][y][x] bools over a level-l patch's storage box, ``info`` as
     in Grid.patches) with level-(l+1) boxes, or None when nothing is flagged
     or no valid layout is found.  The new boxes are widened to the layout's
-    minimum width and merged with each other and with the existing
-    level-(l+1) boxes while closer than 8 parent spacings; if that layout is
-    rejected, one bounding box of all of them is tried."""
+    minimum width, moved into the region where they nest in this patch
+    (parent_region), and merged with each other and with the existing
+    level-(l+1) boxes inside that region while closer than 8 parent spacings;
+    level-(l+1) boxes under other patches are kept as they are.  If that
+    layout is rejected, one bounding box of the merged ones is tried."""
     from . import lbm as L
     cl = clusters(flags)
     if not cl:
         return None
     spacing = 8.0 / (1 << info["level"])  # 8 parent spacings in coarse units
     lev = info["level"] + 1
-    new = [widen(block_box_to_coarse(info, block, lo, hi, margin, case["n"]), spacing, case["n"])
+    region = parent_region(info, case["n"])
+    new = [_fit(widen(block_box_to_coarse(info, block, lo, hi, margin, case["n"]), spacing, case["n"]), region)
            for lo, hi in cl]
-    old = [(tuple(b[1]), tuple(b[2])) for b in case.get("boxes", []) if b[0] == lev]
-    keep = [b for b in case.get("boxes", []) if b[0] != lev]
-    merged = merge_boxes(old + new, spacing)
+    new = [b for b in new if all(b[0][a] <= b[1][a] for a in range(3))]
+    if not new:
+        return None
+    mine = [(tuple(b[1]), tuple(b[2])) for b in case.get("boxes", []) if b[0] == lev
+            and _inside((tuple(b[1]), tuple(b[2])), region)]
+    keep = [b for b in case.get("boxes", []) if not (b[0] == lev and _inside((tuple(b[1]), tuple(b[2])), region))]
+    merged = merge_boxes(mine + new, spacing)
     candidates = [merged]
     if len(merged) > 1:
         lo = tuple(min(b[0][a] for b in merged) for a in range(3))

@@ -18,8 +18,10 @@
 // step is captured once per set of buffer indices and replayed as a CUDA
 // graph.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -54,6 +56,8 @@ struct lbm_grid {
   };
   bool timing = false;
   int variant = 0;         // TMA kernel variant (lbm_autotune)
+  int wait_sleeps = 1 << 21;  // bound of the TMA passes' stage waits (lbm_wait_limit)
+  int device = -1;         // device of the bound buffer
   bool presample = false;  // reconstruction samples beside the TMA pass (lbm_autotune)
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
@@ -180,6 +184,7 @@ lbmk::ThermalLevel thermal_level(const lbm_grid* g, const HostPatch& p) {
   L.beta1 = p.beta1;
   L.lbgk = d.mirror_lbgk;
   L.pr_gt1 = g->hg.pr_gt1 ? 1 : 0;
+  L.wait_sleeps = g->wait_sleeps;
   return L;
 }
 
@@ -297,8 +302,8 @@ lbm_status run_instant(lbm_grid* g, int k) {
                                      timed(g, 4, -1, b0 == 0 ? nodes : 0.0,
                                            [&] {
                                              return lbmk::launch_sc_tma(storage, batch.data() + b0, nb,
-                                                                        g->variant, lbgk, status_ptr(g),
-                                                                        g->stream);
+                                                                        g->variant, lbgk, g->wait_sleeps,
+                                                                        status_ptr(g), g->stream);
                                            }),
                                      "stream_collide (TMA)"))
         return st;
@@ -576,6 +581,11 @@ lbm_status lbm_grid_bind(lbm_grid_t g, void* dev_ptr, size_t bytes, void* cuda_s
   if (!g || !dev_ptr) return fail(g, LBM_ERR_ARG, "null argument");
   if (bytes < g->need) return fail(g, LBM_ERR_OOM, "bound buffer smaller than lbm_grid_bytes");
   if (reinterpret_cast<uintptr_t>(dev_ptr) % 256) return fail(g, LBM_ERR_ARG, "device buffer not 256-byte aligned");
+  cudaPointerAttributes pa{};
+  if (cudaError_t e = cudaPointerGetAttributes(&pa, dev_ptr)) return cuda_check(g, e, "cudaPointerGetAttributes");
+  if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)
+    return fail(g, LBM_ERR_ARG, "bound buffer is not device memory");
+  g->device = pa.device;
   g->drop_graphs();  // the captured launches name the previous buffer and stream
   g->stepped = false;
   g->base = static_cast<uint8_t*>(dev_ptr);
@@ -824,6 +834,14 @@ lbm_status lbm_set_variant(lbm_grid_t g, int32_t variant) {
   return LBM_OK;
 }
 
+lbm_status lbm_wait_limit(lbm_grid_t g, int32_t sleeps) {
+  if (!g) return LBM_ERR_ARG;
+  if (sleeps < 0) return fail(g, LBM_ERR_ARG, "negative wait limit");
+  g->wait_sleeps = sleeps;
+  g->drop_graphs();  // the bound is baked into the captured launches
+  return LBM_OK;
+}
+
 lbm_status lbm_graphs(lbm_grid_t g, int32_t enable) {
   if (!g) return LBM_ERR_ARG;
   g->graphs = enable != 0;
@@ -930,6 +948,29 @@ lbm_status lbm_set_populations(lbm_grid_t g, int32_t patch, int32_t which, const
   return copy_pop(g, patch, which, const_cast<void*>(src), dtype, 0);
 }
 
+namespace {
+// Common ending of both diagnostics calls: out from the FP64 sums, the
+// status word in out[7].  Bit 1 of the status word (a bounded wait of a TMA
+// pass expired, so nodes of that pass kept stale values) gives
+// LBM_ERR_TIMEOUT and is cleared once reported; k_diag's slot 7 (nodes with
+// non-finite or non-positive density) gives LBM_ERR_UNSTABLE.
+lbm_status diag_result(lbm_grid* g, const double host[8], int status, double out[8]) {
+  for (int k = 0; k < 6; ++k) out[k] = host[k];
+  out[6] = host[6];
+  out[7] = (double)status;
+  if (status & 2) {
+    if (cudaError_t e = lbmk::launch_status_clear(status_ptr(g), 2, g->stream))
+      return cuda_check(g, e, "status clear");
+    return fail(g, LBM_ERR_TIMEOUT, "a bounded wait of the TMA pass expired; the state is not valid");
+  }
+  if (host[7] > 0 || !(host[6] > 0)) {
+    out[6] = host[7] > 0 ? NAN : host[6];
+    return fail(g, LBM_ERR_UNSTABLE, "non-finite or non-positive density");
+  }
+  return LBM_OK;
+}
+}  // namespace
+
 lbm_status lbm_diagnostics(lbm_grid_t g, double out[8]) {
   if (lbm_status s = check_bound(g)) return s;
   if (!out) return fail(g, LBM_ERR_ARG, "null output");
@@ -951,15 +992,7 @@ lbm_status lbm_diagnostics(lbm_grid_t g, double out[8]) {
   if (!e) e = cudaMemcpyAsync(&status, status_ptr(g), sizeof status, cudaMemcpyDeviceToHost, g->stream);
   if (!e) e = cudaStreamSynchronize(g->stream);
   if (e) return cuda_check(g, e, "lbm_diagnostics");
-  for (int k = 0; k < 6; ++k) out[k] = host[k];
-  out[6] = host[6];
-  out[7] = (double)status;
-  // k_diag slot 7 counts nodes with non-finite or non-positive density
-  if (host[7] > 0 || !(host[6] > 0)) {
-    out[6] = host[7] > 0 ? NAN : host[6];
-    return fail(g, LBM_ERR_UNSTABLE, "non-finite or non-positive density");
-  }
-  return LBM_OK;
+  return diag_result(g, host, status, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -1315,7 +1348,41 @@ namespace {
 constexpr int kNoAllocMaxPatches = 16;
 constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_noalloc_scratch[8 * kDiagBlocks * kNoAllocMaxPatches + 8];
-double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::atomic<double*> g_noalloc_ptr[kMaxDevices];
+std::mutex g_noalloc_lookup;
+
+// Makes a device current for the lifetime of the guard and restores the
+// caller's current device afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (!err && prev != dev) err = cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Device address of the scratch array on device dev (current), looked up once
+// per device under a lock and published atomically.
+cudaError_t noalloc_scratch(int dev, double** out) {
+  double* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    std::lock_guard<std::mutex> lock(g_noalloc_lookup);
+    p = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+    if (!p) {
+      void* ptr = nullptr;
+      if (cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch)) return e;
+      p = static_cast<double*>(ptr);
+      g_noalloc_ptr[dev].store(p, std::memory_order_release);
+    }
+  }
+  *out = p;
+  return cudaSuccess;
+}
 }  // namespace
 
 lbm_status lbm_diagnostics_noalloc(lbm_grid_t g, double out[8]) {
@@ -1325,15 +1392,13 @@ lbm_status lbm_diagnostics_noalloc(lbm_grid_t g, double out[8]) {
     return fail(g, LBM_ERR_ARG,
                 "lbm_diagnostics_noalloc handles at most " + std::to_string(kNoAllocMaxPatches) +
                     " patches; this grid has " + std::to_string(g->hg.P.size()));
-  int dev = 0;
-  if (cudaError_t e = cudaGetDevice(&dev)) return cuda_check(g, e, "cudaGetDevice");
+  // the grid's device (that of its bound buffer), current for this call
+  const int dev = g->device;
   if (dev < 0 || dev >= kMaxDevices) return fail(g, LBM_ERR_ARG, "device index beyond the supported range");
-  if (!g_noalloc_ptr[dev]) {
-    void* ptr = nullptr;
-    if (cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch)) return cuda_check(g, e, "cudaGetSymbolAddress");
-    g_noalloc_ptr[dev] = static_cast<double*>(ptr);
-  }
-  double* partial = g_noalloc_ptr[dev];
+  DeviceGuard guard(dev);
+  if (guard.err) return cuda_check(g, guard.err, "cudaSetDevice");
+  double* partial = nullptr;
+  if (cudaError_t e = noalloc_scratch(dev, &partial)) return cuda_check(g, e, "cudaGetSymbolAddress");
   double* dout = partial + 8 * kDiagBlocks * kNoAllocMaxPatches;
   // every partial slot and the 8 outputs are written before they are read in
   // this call, so nothing needs clearing between calls
@@ -1353,14 +1418,7 @@ lbm_status lbm_diagnostics_noalloc(lbm_grid_t g, double out[8]) {
   if (!e) e = cudaMemcpyAsync(&status, status_ptr(g), sizeof status, cudaMemcpyDeviceToHost, g->stream);
   if (!e) e = cudaStreamSynchronize(g->stream);
   if (e) return cuda_check(g, e, "lbm_diagnostics_noalloc");
-  for (int k = 0; k < 6; ++k) out[k] = host[k];
-  out[6] = host[6];
-  out[7] = (double)status;
-  if (host[7] > 0 || !(host[6] > 0)) {
-    out[6] = host[7] > 0 ? NAN : host[6];
-    return fail(g, LBM_ERR_UNSTABLE, "non-finite or non-positive density");
-  }
-  return LBM_OK;
+  return diag_result(g, host, status, out);
 }
 
 lbm_status lbm_force(lbm_grid_t g, const double* accel0, double* drag_out) {

@@ -703,6 +703,13 @@ __global__ void k_diag_final(const double* __restrict__ partial, int nb, double*
   out[k] = s;
 }
 
+__global__ void k_status_clear(int* status, int bits) { atomicAnd(status, ~bits); }
+
+cudaError_t launch_status_clear(int* status, int bits, cudaStream_t st) {
+  k_status_clear<<<1, 1, 0, st>>>(status, bits);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_diag_final(const double* partial, int total_blocks, double* out8, cudaStream_t st) {
   k_diag_final<<<1, 32, 0, st>>>(partial, total_blocks, out8);
   return cudaGetLastError();

@@ -29,6 +29,7 @@ struct ThermalLevel {
   int lbgk;
   int pr_gt1;     // Pr > 1 rows of Table I
   int solid_iso;  // solid surfaces held at twd[6] (else adiabatic)
+  int wait_sleeps;  // bound of the TMA pass's waits for a loaded stage (lbm_wait_limit)
 };
 
 cudaError_t launch_th_tiles(int storage, const PatchDev& p, const void* fin, const void* gin, void* fout, void* gout,
@@ -101,8 +102,10 @@ struct TmaLaunchPatch {
 };
 // TMA tile pass over up to 8 patches in one persistent launch; variant picks
 // the load-stage / occupancy configuration (0 .. sc_tma_variants() - 1).
-cudaError_t launch_sc_tma(int storage, const TmaLaunchPatch* ps, int n, int variant, int lbgk, int* status,
-                          cudaStream_t st);
+// wait_sleeps: bound of the consumers' waits for a loaded stage (0.5 us
+// suspensions; about a second by default, set from lbm_wait_limit).
+cudaError_t launch_sc_tma(int storage, const TmaLaunchPatch* ps, int n, int variant, int lbgk, int wait_sleeps,
+                          int* status, cudaStream_t st);
 int sc_tma_variants(int storage);
 // node-by-node recomputation of listed nodes (after the TMA tile pass)
 cudaError_t launch_sc_nodes(int storage, const PatchDev& p, const void* fin, void* fout, const uint32_t* nodes,
@@ -175,6 +178,8 @@ cudaError_t launch_gamma_blocks(int storage, const PatchDev& p, const void* fin,
 cudaError_t launch_diag(int storage, const PatchDev& p, const void* fin, double vol_weight, const Force& F,
                         double* partial, int blocks, cudaStream_t st);
 cudaError_t launch_diag_final(const double* partial, int total_blocks, double* out8, cudaStream_t st);
+// clears the given bits of the device status word (one atomic)
+cudaError_t launch_status_clear(int* status, int bits, cudaStream_t st);
 // momentum-exchange force: per-block FP64 sums [blocks][3] of 2 c_j f'_j * scale over the links
 cudaError_t launch_drag(int storage, const void* fin, int64_t plane, const uint32_t* node, const uint32_t* mask,
                         int64_t n, double scale, double* partial, int blocks, cudaStream_t st);

@@ -3,17 +3,17 @@
 
 namespace lbmk {
 
-cudaError_t launch_sc_tma(int storage, const TmaLaunchPatch* ps, int n, int variant, int lbgk, int* status,
-                          cudaStream_t st) {
+cudaError_t launch_sc_tma(int storage, const TmaLaunchPatch* ps, int n, int variant, int lbgk, int wait_sleeps,
+                          int* status, cudaStream_t st) {
   switch (storage) {
     case LBM_FP64:
-      return sc_tma_fp64(ps, n, variant, lbgk, status, st);
+      return sc_tma_fp64(ps, n, variant, lbgk, wait_sleeps, status, st);
     case LBM_FP32:
-      return sc_tma_fp32(ps, n, variant, lbgk, status, st);
+      return sc_tma_fp32(ps, n, variant, lbgk, wait_sleeps, status, st);
     case LBM_FP16_SHIFT:
-      return sc_tma_fp16(ps, n, variant, lbgk, status, st);
+      return sc_tma_fp16(ps, n, variant, lbgk, wait_sleeps, status, st);
     case LBM_BF16_SHIFT:
-      return sc_tma_bf16(ps, n, variant, lbgk, status, st);
+      return sc_tma_bf16(ps, n, variant, lbgk, wait_sleeps, status, st);
     default:
       return cudaErrorInvalidValue;
   }

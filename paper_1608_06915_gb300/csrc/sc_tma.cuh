@@ -18,17 +18,24 @@
 // write their 32-node segment of the 27 output rows to shared memory and one
 // lane stores it back with one TMA store, so consumer warps never wait for each
 // other.  TMA instructions are issued by single threads: with per-lane operands
-// the compiler would serialise them lane by lane.  Persistent CTAs walk a list of tiles whose nodes all
-// pull from neighbour rows (wrapping only on spanned axes) or bounce back
-// from a wall across y or z, one rule per source row; tiles holding
-// solid, outlet, x-wall or interface nodes go to k_sc_tiles, which pulls node
-// by node.
+// the compiler would serialise them lane by lane.  Persistent CTAs walk a list
+// of tiles whose rows pull by one rule per source row: from the neighbour row
+// (wrapping only on spanned axes), or, beyond a wall across y or z, by
+// bounce-back from the tile's own row.  Inlet and outlet rows and interface
+// tiles take this path too: the inlet node keeps its populations, the outlet
+// node pulls its c_x = -1 populations from itself, and nodes not updated in
+// the substep are overwritten and rewritten later in the instant by the
+// coupling.  Updated nodes whose pull the row rule cannot express (solid
+// neighbours, walls across x) are recomputed afterwards from a fix-up list
+// (k_sc_nodes); only tiles the row rule cannot serve at all go to k_sc_tiles,
+// which pulls node by node.
 //
 // Waits suspend in hardware (mbarrier try_wait with a time hint) instead of
 // spinning, so a waiting producer takes no issue slots from the consumers.
-// Waits are bounded: a stage that does not arrive within about a second sets
-// bit 1 of the status word; the CTA then waits (bounded again) for the copies
-// it has in flight and returns.
+// Waits are bounded: a stage that does not arrive within the batch's bound
+// (about a second unless the host sets it lower) sets bit 1 of the status
+// word; the CTA then waits (with the full bound) for the copies it may have in
+// flight and returns.
 #pragma once
 #include <cuda.h>
 
@@ -123,10 +130,25 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
   return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase: about a second at most.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Non-blocking test of an mbarrier phase.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: up to `sleeps` suspensions of at most
+// 0.5 us each (kWaitSleeps: about a second); sleeps = 0 tests once without
+// waiting.
+constexpr int kWaitSleeps = 1 << 21;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int sleeps = kWaitSleeps) {
+  if (sleeps <= 0) return mbar_test_wait(bar, parity);
   if (mbar_try_wait(bar, parity)) return true;
-  for (int it = 0; it < (1 << 21); ++it)
+  for (int it = 0; it < sleeps; ++it)
     if (mbar_try_wait_sleep(bar, parity, 500u)) return true;
   return false;
 }
@@ -226,6 +248,7 @@ template <typename S, typename R>
 struct TmaBatch {
   TmaPatch<S, R> e[kTmaBatch];
   int n, ntiles, lbgk;
+  int wait_sleeps;  // bound of the consumers' waits for a loaded stage (mbar_wait_bounded)
   int* status;
 };
 
@@ -313,11 +336,12 @@ __global__ void __launch_bounds__(160, MINB) k_sc_tma(const __grid_constant__ Tm
   // ---------------- consumers (warps 0-3) ----------------
   for (int k = 0; k < nmine; ++k) {
     const int s = k % C::DI;
-    const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(k / C::DI) & 1u);
+    const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(k / C::DI) & 1u, b.wait_sleeps);
     if (!ok) {
-      // stage never arrived: flag, wait (bounded) for stages still in flight, drain stores, leave
-      if (tid == 0) atomicOr(status, 2);
-      for (int j = k + 1; j < nmine && j < k + C::DI; ++j) mbar_wait_bounded(&full[j % C::DI], (uint32_t)(j / C::DI) & 1u);
+      // stage not arrived in time: flag, wait (full bound) for the loads that
+      // may still be in flight, this stage's included, drain stores, leave
+      if (lane == 0) atomicOr(status, 2);
+      for (int j = k; j < nmine && j < k + C::DI; ++j) mbar_wait_bounded(&full[j % C::DI], (uint32_t)(j / C::DI) & 1u);
       if (lane == 0) bulk_wait_all();
       return;
     }
@@ -465,10 +489,12 @@ cudaError_t launch_tma_fm(const TmaBatch<S, R>& b, int variant, cudaStream_t st)
 
 // One launch over up to kTmaBatch patches (their force masks must agree).
 template <typename S, typename R>
-cudaError_t sc_tma_typed(const TmaLaunchPatch* ps, int n, int variant, int lbgk, int* status, cudaStream_t st) {
+cudaError_t sc_tma_typed(const TmaLaunchPatch* ps, int n, int variant, int lbgk, int wait_sleeps, int* status,
+                         cudaStream_t st) {
   TmaBatch<S, R> b;
   memset(&b, 0, sizeof b);
   b.lbgk = lbgk;
+  b.wait_sleeps = wait_sleeps;
   b.status = status;
   int fm = 0;
   for (int q = 0; q < n; ++q) {
@@ -551,8 +577,8 @@ cudaError_t sc_tiles_typed(const PatchDev& p, const void* fin, void* fout, const
 
 // per-storage entry points, one translation unit each
 #define LBM_SC_DECL(NAME)                                                                                        \
-  cudaError_t sc_tma_##NAME(const TmaLaunchPatch* ps, int n, int variant, int lbgk, int* status,                \
-                            cudaStream_t st);                                                                    \
+  cudaError_t sc_tma_##NAME(const TmaLaunchPatch* ps, int n, int variant, int lbgk, int wait_sleeps,           \
+                            int* status, cudaStream_t st);                                                       \
   cudaError_t sc_tiles_##NAME(const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,             \
                               int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk,           \
                               int* status, cudaStream_t st);                                                     \
@@ -564,9 +590,9 @@ LBM_SC_DECL(fp16)
 LBM_SC_DECL(bf16)
 
 #define LBM_SC_DEFINE(NAME, S, R)                                                                                \
-  cudaError_t sc_tma_##NAME(const TmaLaunchPatch* ps, int n, int variant, int lbgk, int* status,                \
-                            cudaStream_t st) {                                                                   \
-    return sc_tma_typed<S, R>(ps, n, variant, lbgk, status, st);                                                 \
+  cudaError_t sc_tma_##NAME(const TmaLaunchPatch* ps, int n, int variant, int lbgk, int wait_sleeps,           \
+                            int* status, cudaStream_t st) {                                                      \
+    return sc_tma_typed<S, R>(ps, n, variant, lbgk, wait_sleeps, status, st);                                    \
   }                                                                                                              \
   cudaError_t sc_tiles_##NAME(const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,             \
                               int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk,           \

@@ -256,6 +256,7 @@ struct ThParams {
   int lbgk;
   int pr_gt1;     // Pr > 1 rows of Table I
   int solid_iso;  // solid surfaces held at twd[6] (else adiabatic)
+  int wait_sleeps;  // bound of the TMA pass's waits for a loaded stage
 };
 
 template <typename R>
@@ -279,6 +280,7 @@ ThParams<R> th_params(const ThermalLevel& L) {
   t.beta1 = (R)L.beta1;
   t.lbgk = L.lbgk;
   t.pr_gt1 = L.pr_gt1;
+  t.wait_sleeps = L.wait_sleeps;
   return t;
 }
 

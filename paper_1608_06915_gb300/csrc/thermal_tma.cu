@@ -108,9 +108,11 @@ __global__ void __launch_bounds__(160) k_th_tma(const __grid_constant__ ThMaps<R
   // ---------------- consumers (warps 0-3) ----------------
   for (int k = 0; k < nmine; ++k) {
     const int s = k % T::DI;
-    if (!mbar_wait_bounded(&full[s], (uint32_t)(k / T::DI) & 1u)) {
-      if (tid == 0) atomicOr(status, 2);
-      for (int j = k + 1; j < nmine && j < k + T::DI; ++j)
+    if (!mbar_wait_bounded(&full[s], (uint32_t)(k / T::DI) & 1u, tp.wait_sleeps)) {
+      // not arrived in time: flag, wait (full bound) for the loads that may
+      // still be in flight, this stage's included, drain stores, leave
+      if (lane == 0) atomicOr(status, 2);
+      for (int j = k; j < nmine && j < k + T::DI; ++j)
         mbar_wait_bounded(&full[j % T::DI], (uint32_t)(j / T::DI) & 1u);
       if (lane == 0) bulk_wait_all();
       return;

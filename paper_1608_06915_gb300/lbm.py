@@ -95,6 +95,7 @@ def lib():
             "lbm_collide_nodes": [vp, vp, vp, i64, ctypes.c_double, dp, i32, i32, vp],
             "lbm_timing": [vp, i32],
             "lbm_graphs": [vp, i32],
+            "lbm_wait_limit": [vp, i32],
             "lbm_autotune": [vp, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float), i32,
                              ctypes.POINTER(ctypes.c_int32)],
             "lbm_set_variant": [vp, i32],
@@ -353,6 +354,10 @@ class Grid:
 
     def graphs(self, enable: bool):
         _check(lib().lbm_graphs(self.handle, 1 if enable else 0), self.handle)
+
+    def wait_limit(self, sleeps: int):
+        """lbm_wait_limit: bound of the TMA passes' stage waits (0.5 us units)."""
+        _check(lib().lbm_wait_limit(self.handle, int(sleeps)), self.handle)
 
     def timing(self, enable: bool):
         _check(lib().lbm_timing(self.handle, 1 if enable else 0), self.handle)

@@ -59,6 +59,32 @@ def test_boxes_from_flags_merges_with_existing_boxes():
     assert A.boxes_from_flags(np.zeros((12, 12, 12), dtype=bool), info, 4, case) is None
 
 
+def test_boxes_from_flags_keeps_to_the_parent_patch():
+    """Blocks flagged at the face of a level-1 patch: widened to the minimum
+    width, their level-2 box would stick out of the patch, which the layout
+    rules reject.  It is moved back inside the region where it nests; the
+    level-2 box under the other level-1 patch is kept as it was."""
+    from paper_1608_06915_gb300 import lbm as L
+    case = I.tgv_case(n=64, refined=False)
+    case["boxes"] = [(1, (4, 4, 4), (24, 24, 24)), (1, (34, 4, 4), (56, 26, 26)),
+                     (2, (36, 10, 10), (42, 20, 20))]
+    g = L.Grid(case, "fp32", bind=False)
+    info = g.patches[1]
+    assert info["level"] == 1 and tuple(info["org"]) == (8, 8, 8)
+    assert A.parent_region(info, case["n"]) == ((6, 6, 6), (22, 22, 22))
+    nb = [-(-d // 4) for d in info["dim"]]  # blocks of 4 level-1 nodes
+    f = np.zeros((nb[2], nb[1], nb[0]), dtype=bool)
+    f[5, 5, nb[0] - 1] = True  # the last block along x: coarse x 24
+    boxes = A.boxes_from_flags(f, info, 4, case)
+    assert boxes is not None
+    assert (2, (36, 10, 10), (42, 20, 20)) in boxes and (1, (34, 4, 4), (56, 26, 26)) in boxes
+    lev2 = [b for b in boxes if b[0] == 2 and b != (2, (36, 10, 10), (42, 20, 20))]
+    assert len(lev2) == 1
+    _, lo, hi = lev2[0]
+    assert all(6 <= lo[a] and hi[a] <= 22 and hi[a] - lo[a] >= 4 for a in range(3)) and hi[0] == 22
+    L.Grid(dict(case, boxes=boxes), "fp32", bind=False)
+
+
 def test_widen_keeps_boxes_inside_the_domain():
     assert A.widen(((10, 10, 10), (12, 10, 11)), 8, (32, 32, 32)) == ((7, 6, 7), (15, 14, 15))
     assert A.widen(((0, 0, 29), (1, 2, 31)), 8, (32, 32, 32)) == ((0, 0, 23), (8, 8, 31))

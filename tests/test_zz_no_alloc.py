@@ -55,6 +55,35 @@ def test_noalloc_matches_diagnostics_two_calls(storage):
         g.step(1)
 
 
+def test_noalloc_allocates_nothing_after_the_first_call():
+    # The first call on a device may be where CUDA's lazy module loading
+    # places the library's module, and the array with it, on the device; from
+    # then on a call must leave the device's memory as it found it: nothing
+    # through torch's allocator and nothing through the driver.
+    # Python's cycle collector is held off while measuring, so that tensors
+    # of earlier tests freed meanwhile do not move the counts.
+    import gc
+
+    import torch
+    case = I.channel_small_case()
+    g = _grid(case, "fp32", lambda x, y, z, info: I.channel_fields(case, info["level"], info["org"], info["dim"]))
+    g.step(1)
+    g.diagnostics_noalloc()
+    torch.cuda.synchronize()
+    gc.collect()
+    gc.disable()
+    try:
+        alloc0 = torch.cuda.memory_allocated()
+        free0, _ = torch.cuda.mem_get_info()
+        for _ in range(3):
+            g.diagnostics_noalloc()
+            torch.cuda.synchronize()
+            assert torch.cuda.memory_allocated() == alloc0
+            assert torch.cuda.mem_get_info()[0] == free0
+    finally:
+        gc.enable()
+
+
 def test_noalloc_rejects_too_many_patches():
     from paper_1608_06915_gb300 import lbm as L
     case = I.tgv_case(n=64)
