@@ -240,183 +240,7 @@ __device__ __forceinline__ R shear_part(R nxx, R nyy, R nzz, R pxy, R pxz, R pyz
   }
 }
 
-// KBC collision (Eqs. f_equations, f_mirr, gamma_min_approx) in the delta form
-//   f'_i = f_i - beta (2 ds_i + gamma dh_i),  dh = (f - f^eq) - ds,
-// followed by the exact-difference-method force f'_i += f^eq(rho,u+du) - f^eq(rho,u).
-// f holds deviation populations f - W and is replaced by the post-collision
-// deviations; returns gamma.  FM is a compile-time mask of the axes along
-// which du may be nonzero (bit a: axis a; 0: no force).
-//
-// Arithmetic layout: every per-direction quantity is a product of per-axis
-// factors, so the loops read small tables instead of forming 27 products --
-// q_i from (1 + q_xy)(1 + d_z), rho W_i from the four weight classes, the
-// second moments from the three z-columns of each (c_x, c_y) pair, the
-// entropic weights 1/f_i^eq as (1/g_x g_y) per column with (1/(rho g_z)) per
-// layer, the force from per-axis tables.
-template <int i>
-__host__ __device__ constexpr int wclass() {
-  return (CX(i) != 0) + (CY(i) != 0) + (CZ(i) != 0);
-}
-
-// The same with the moments of f given (callers that already hold them).
-template <typename R, int FM>
-__device__ __forceinline__ R kbc_collide_m(R (&f)[27], R rho_t, R rho, R ux, R uy, R uz, R beta, R dux, R duy,
-                                           R duz, bool lbgk);
-
-template <typename R, int FM>
-__device__ __forceinline__ R kbc_collide(R (&f)[27], R beta, R dux, R duy, R duz, bool lbgk) {
-  R rho_t, rho, ux, uy, uz;
-  macro(f, rho_t, rho, ux, uy, uz);
-  return kbc_collide_m<R, FM>(f, rho_t, rho, ux, uy, uz, beta, dux, duy, duz, lbgk);
-}
-
-template <typename R, int FM>
-__device__ __forceinline__ R kbc_collide_m(R (&f)[27], R rho_t, R rho, R ux, R uy, R uz, R beta, R dux, R duy,
-                                           R duz, bool lbgk) {
-  AxisEq<R> ex, ey, ez;
-  axis_eq<R>(ux, ex, !lbgk);
-  axis_eq<R>(uy, ey, !lbgk);
-  axis_eq<R>(uz, ez, !lbgk);
-  R fe[27];
-  {
-    // W_i by the number of nonzero velocity components: 8/27, 2/27, 1/54, 1/216
-    constexpr double WK[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
-    R wr[4], wrt[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      wr[k] = R(WK[k]) * rho;
-      wrt[k] = R(WK[k]) * rho_t;
-    }
-    R qxy[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) qxy[a][b] = ex.d[a] * ey.d[b] + (ex.d[a] + ey.d[b]);
-    unroll<27>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      const R t = qxy[CX(i) + 1][CY(i) + 1], dz = ez.d[CZ(i) + 1];
-      const R q = t * dz + (t + dz);
-      fe[i] = wr[wclass<i>()] * q + wrt[wclass<i>()];
-      f[i] = f[i] - fe[i];
-    });
-  }
-  // second moments of df: per (c_x, c_y) column, z0 = sum over c_z, z1 = sum c_z df, z2 = sum c_z^2 df
-  R pxx, pyy, pzz, pxy, pxz, pyz;
-  {
-    R z0[3][3], z1[3][3], z2[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const R lo = f[a + 3 * b], mid = f[a + 3 * b + 9], hi = f[a + 3 * b + 18];
-        z2[a][b] = lo + hi;
-        z1[a][b] = hi - lo;
-        z0[a][b] = z2[a][b] + mid;
-      }
-    pxx = ((z0[0][0] + z0[2][0]) + (z0[0][1] + z0[2][1])) + (z0[0][2] + z0[2][2]);
-    pyy = ((z0[0][0] + z0[0][2]) + (z0[1][0] + z0[1][2])) + (z0[2][0] + z0[2][2]);
-    pzz = ((z2[0][0] + z2[1][0]) + (z2[2][0] + z2[0][1])) + ((z2[1][1] + z2[2][1]) + (z2[0][2] + z2[1][2])) +
-          z2[2][2];
-    pxy = (z0[0][0] + z0[2][2]) - (z0[2][0] + z0[0][2]);
-    pxz = ((z1[2][0] - z1[0][0]) + (z1[2][1] - z1[0][1])) + (z1[2][2] - z1[0][2]);
-    pyz = ((z1[0][2] - z1[0][0]) + (z1[1][2] - z1[1][0])) + (z1[2][2] - z1[2][0]);
-  }
-  const R tr3 = (pxx + pyy + pzz) * R(1.0 / 3.0);
-  const R nxx = pxx - tr3, nyy = pyy - tr3, nzz = pzz - tr3;
-  R gamma = R(2);
-  if (!lbgk) {
-    R wxy[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) wxy[a][b] = ex.ig[a] * ey.ig[b];
-    R shl[3] = {0, 0, 0}, hhl[3] = {0, 0, 0};
-    unroll<27>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      constexpr int l = CZ(i) + 1;
-      const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
-      const R dh = f[i] - ds;
-      const R dhw = dh * wxy[CX(i) + 1][CY(i) + 1];
-      shl[l] += ds * dhw;
-      hhl[l] += dh * dhw;
-    });
-    // layer weights 1/(rho g_z) applied once per layer
-    const R irho = rcp_fast(rho);
-    const R w0 = irho * ez.ig[0], w1 = irho * ez.ig[1], w2 = irho * ez.ig[2];
-    const R sh = (w0 * shl[0] + w2 * shl[2]) + w1 * shl[1];
-    const R hh = (w0 * hhl[0] + w2 * hhl[2]) + w1 * hhl[1];
-    if (hh > R(1e-30) * rho * rho) {
-      const R ib = rcp_fast(beta);
-      gamma = ib - (R(2) - ib) * fdiv(sh, hh);
-    }
-  }
-  // f' = f^eq + (1 - beta gamma) df + beta (gamma - 2) ds  [+ force increment]
-  const R a = R(1) - beta * gamma;
-  const R b = beta * (gamma - R(2));
-  if constexpr (FM == 0) {
-    unroll<27>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      f[i] = a * f[i] + fe[i] + b * shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
-    });
-  } else if constexpr (FM == 1 || FM == 2 || FM == 4) {
-    // force along one axis A: f^eq(rho,u+du) - f^eq(rho,u) = rho W_i dg_A(c_iA) prod_{b != A} g_b(c_ib)
-    //   = [rho W1(c_iA) dg_A(c_iA)] [W1(c_i1) g_1(c_i1)] [W1(c_i2) g_2(c_i2)]
-    constexpr int A = FM == 1 ? 0 : (FM == 2 ? 1 : 2);
-    const AxisEq<R>& ea = A == 0 ? ex : (A == 1 ? ey : ez);
-    const AxisEq<R>& e1 = A == 0 ? ey : ex;
-    const AxisEq<R>& e2 = A == 2 ? ey : ez;
-    const R ua = A == 0 ? ux : (A == 1 ? uy : uz);
-    const R dua = A == 0 ? dux : (A == 1 ? duy : duz);
-    R g1[3], dg[3], rdg[3], gw1[3], gw2[3], G[3][3];
-    axis_eq_increment<R>(ua, dua, ea, g1, dg);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      rdg[c] = (R(W1(c - 1)) * rho) * dg[c];
-      gw1[c] = R(W1(c - 1)) * (R(1) + e1.d[c]);
-      gw2[c] = R(W1(c - 1)) * (R(1) + e2.d[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int c2 = 0; c2 < 3; ++c2) G[c][c2] = gw1[c] * gw2[c2];
-    unroll<27>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      constexpr int ca = A == 0 ? CX(i) : (A == 1 ? CY(i) : CZ(i));
-      constexpr int c1 = A == 0 ? CY(i) : CX(i);
-      constexpr int c2 = A == 2 ? CY(i) : CZ(i);
-      f[i] = rdg[ca + 1] * G[c1 + 1][c2 + 1] + (a * f[i] + fe[i] + b * shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz));
-    });
-  } else {
-    // general direction, telescoped: dgx gy gz + gx' (dgy gz + gy' dgz), with
-    // rho W1(c_x) on the x factors and W1(c_y) W1(c_z) on the (y, z) tables
-    R gx1[3], gy1[3], gz1[3], dgx[3], dgy[3], dgz[3];
-    axis_eq_increment<R>(ux, dux, ex, gx1, dgx);
-    axis_eq_increment<R>(uy, duy, ey, gy1, dgy);
-    axis_eq_increment<R>(uz, duz, ez, gz1, dgz);
-    R X0[3], X1[3], P[3][3], Q[3][3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const R rw = R(W1(c - 1)) * rho;
-      X0[c] = rw * dgx[c];
-      X1[c] = rw * gx1[c];
-    }
-#pragma unroll
-    for (int y = 0; y < 3; ++y)
-#pragma unroll
-      for (int z = 0; z < 3; ++z) {
-        const R wyz = R(W1(y - 1) * W1(z - 1));
-        const R gz = R(1) + ez.d[z];
-        P[y][z] = wyz * ((R(1) + ey.d[y]) * gz);
-        Q[y][z] = wyz * (dgy[y] * gz + gy1[y] * dgz[z]);
-      }
-    unroll<27>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      constexpr int x = CX(i) + 1, y = CY(i) + 1, z = CZ(i) + 1;
-      f[i] = X0[x] * P[y][z] + (X1[x] * Q[y][z] + (a * f[i] + fe[i] + b * shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz)));
-    });
-  }
-  return gamma;
-}
+// The KBC collision itself is in collide.cuh.
 
 // ---------------------------------------------------------------------------
 // Pull-streaming: f_i(x) = f'_i(x - c_i) from the previous state.

@@ -17,6 +17,7 @@
 #include <type_traits>
 
 #include "../../include/lbm.h"
+#include "collide.cuh"
 #include "device.cuh"
 #include "kernels.h"
 

@@ -19,7 +19,9 @@ cudaError_t launch_sc_tma(int storage, const TmaLaunchPatch* ps, int n, int vari
   }
 }
 
-int sc_tma_variants(int) { return 2; }
+// scalar kernels 0, 1 for every storage; packed-pair kernels 2, 3 for FP32
+// arithmetic (FP32 and 16-bit storage)
+int sc_tma_variants(int storage) { return storage == LBM_FP64 ? 2 : 4; }
 
 cudaError_t launch_sc_tiles(int storage, const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,
                             int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk, int* status,

@@ -41,8 +41,10 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "../../include/lbm.h"
+#include "collide.cuh"
 #include "device.cuh"
 #include "kernels.h"
 
@@ -417,6 +419,224 @@ __global__ void __launch_bounds__(160, MINB) k_sc_tma(const __grid_constant__ Tm
   if (lane == 0) bulk_wait_all();
 }
 
+// ---------------------------------------------------------------------------
+// The tile pass on node pairs (FP32 arithmetic, any FP32 or 16-bit storage).
+// Same tiles, stage layout and row rule as k_sc_tma; a consumer thread takes
+// two neighbouring nodes x, x + 1 of its warp's 64-node half of a tile and
+// collides them together with the packed FP32x2 instructions (F2), so one
+// instruction stream serves two nodes.  Results equal k_sc_tma's bit for bit
+// (collide.cuh).  A pair's populations with c_x = 0 and the bounced ones sit
+// at an even offset of the stage row and load as one 8-byte (4-byte for
+// 16-bit) word; the others load as two elements.  Each warp stores its half
+// tile as two [27][32] boxes.
+template <typename S>
+struct Pair;
+template <>
+struct Pair<float> {
+  static __device__ __forceinline__ F2 ld2(const float* p) {  // p 8-byte aligned
+    return F2(*reinterpret_cast<const float2*>(p));
+  }
+  static __device__ __forceinline__ void st2(float* p, F2 v) { *reinterpret_cast<float2*>(p) = v.v; }
+};
+template <>
+struct Pair<__half> {
+  static __device__ __forceinline__ F2 ld2(const __half* p) {
+    return F2(__half22float2(*reinterpret_cast<const __half2*>(p)));
+  }
+  static __device__ __forceinline__ void st2(__half* p, F2 v) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v.v.x, v.v.y);
+  }
+};
+template <>
+struct Pair<__nv_bfloat16> {
+  static __device__ __forceinline__ F2 ld2(const __nv_bfloat16* p) {
+    return F2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)));
+  }
+  static __device__ __forceinline__ void st2(__nv_bfloat16* p, F2 v) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.v.x, v.v.y);
+  }
+};
+
+// Loads of one tile into a stage (the producer's part of k_sc_tma, shared by
+// k_sc_tma2, where consumer threads issue them): 9 three-row boxes, the
+// bounce rule, the x-periodic wrap boxes; records the tile in tile_at.
+template <typename S, int DI>
+__device__ __forceinline__ void issue_tile(const TmaBatch<S, float>& b, int t, unsigned char* stage,
+                                           uint64_t* full, int4* tile_at) {
+  using C = TmaCfg<S, DI>;
+  const int ei = batch_entry(b, t);
+  const TmaPatch<S, float>& E = b.e[ei];
+  const PatchDev& p = E.p;
+  int tx, ty, tz;
+  const unsigned long long te = E.tiles[t - E.tile0];
+  tile_xyz(te, tx, ty, tz);
+  const int bm = tile_bounce(te);
+  const int fl = tile_flags(te);
+  const bool first = p.span[0] && tx == 0;
+  const bool last = p.span[0] && (tx + 1) * C::BX >= p.dim[0];
+  *tile_at = make_int4(tx, ty, tz, bm | (fl << 9) | (ei << 11));
+  const uint32_t txw = 16u * (uint32_t)(9 - __popc(bm));  // wrap boxes of the rows not bounced
+  mbar_expect_tx(full, C::TX + (first ? txw : 0u) + (last ? txw : 0u));
+  unsigned char* side = stage + 9 * C::GROUP;
+  const int x0 = tx * C::BX - C::H;
+#pragma unroll 1
+  for (int j = 0; j < 9; ++j) {
+    if ((bm >> j) & 1) {
+      tma_load_row(stage + j * C::GROUP, &E.map_in, full, x0, ty, tz, 3 * (8 - j));
+      continue;
+    }
+    const int sy = wrap_axis(ty - (j % 3 - 1), p.dim[1]);
+    const int sz = wrap_axis(tz - (j / 3 - 1), p.dim[2]);
+    tma_load_row(stage + j * C::GROUP, &E.map_in, full, x0, sy, sz, 3 * j);
+    if (first) tma_load_row(side + j * C::SIDE, &E.map_wrap, full, p.dim[0] - C::H, sy, sz, 3 * j + 2);
+    if (last) tma_load_row(side + (9 + j) * C::SIDE, &E.map_wrap, full, 0, sy, sz, 3 * j);
+  }
+}
+
+// No producer warp: NP pairs of consumer warps take alternate tiles of the
+// CTA's sequence from a ring of DI stages (DI a multiple of NP, so each pair
+// cycles through DI / NP stages of its own).  Thread 0 loads the first DI
+// tiles; after a pair has read tile k (named barrier of its 64 threads), its
+// first thread loads tile k + DI into the same stage.  Without the producer
+// a CTA has NP * 2 warps, so two CTAs of two pairs fit the register file at
+// up to 255 registers a thread: two consumer warps per SM sub-partition.
+template <typename S, int FM, int DI, int NP, int MINB>
+__global__ void __launch_bounds__(NP * 64, MINB) k_sc_tma2(const __grid_constant__ TmaBatch<S, float> b) {
+  static_assert(DI % NP == 0, "each pair owns DI / NP stages");
+  using C = TmaCfg<S, DI>;
+  const int ntiles = b.ntiles;
+  int* status = b.status;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  unsigned char* ostage = smem + DI * C::STAGE;
+  __shared__ __align__(8) uint64_t full[DI];
+  __shared__ int4 tile_at[DI];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nmine = (int)blockIdx.x < ntiles ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  if (tid == 0) {
+    for (int s = 0; s < DI; ++s) mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int q = 0; q < b.n; ++q) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&b.e[q].map_in)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&b.e[q].map_out)) : "memory");
+    }
+    for (int k = 0; k < nmine && k < DI; ++k)
+      issue_tile<S, DI>(b, (int)blockIdx.x + k * (int)gridDim.x, smem + k * C::STAGE, &full[k], &tile_at[k]);
+  }
+  __syncthreads();
+
+  const int cp = warp >> 1, h = warp & 1;
+  const bool leader = h == 0 && lane == 0;
+  const int e0 = 64 * h + 2 * lane;  // offset of the thread's first node in the tile
+  unsigned char* myseg = ostage + warp * 2 * C::OSEGB;
+  for (int k = cp; k < nmine; k += NP) {
+    const int s = k % DI;
+    if (!mbar_wait_bounded(&full[s], (uint32_t)(k / DI) & 1u, b.wait_sleeps)) {
+      // not arrived in time: flag, wait (full bound) for the loads that may
+      // still be in flight, this stage's included, drain stores, leave
+      if (lane == 0) atomicOr(status, 2);
+      for (int j = k; j < nmine && j < k + DI; j += NP) mbar_wait_bounded(&full[j % DI], (uint32_t)(j / DI) & 1u);
+      if (lane == 0) bulk_wait_all();
+      return;
+    }
+    const int4 tc = tile_at[s];
+    const int tx = tc.x, y = tc.y, z = tc.z, bm = tc.w & 0x1ff, fl = (tc.w >> 9) & 3;
+    const TmaPatch<S, float>& E = b.e[tc.w >> 11];
+    const PatchDev& p = E.p;
+    const int xa = tx * C::BX + e0;  // the pair's nodes: xa, xa + 1
+    const S* st = reinterpret_cast<const S*>(smem + s * C::STAGE);
+    F2 f[27];
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int cx = CX(i);
+      if ((bm >> (i / 3)) & 1) {
+        f[i] = Pair<S>::ld2(st + row_base<S>(3 * (i / 3) + 2 - i % 3) + C::H + e0);
+      } else if constexpr (cx == 0) {
+        f[i] = Pair<S>::ld2(st + row_base<S>(i) + C::H + e0);
+      } else {
+        const S* r = st + row_base<S>(i) + C::H + e0 - cx;
+        f[i] = F2(SCvt<S>::to(r[0]), SCvt<S>::to(r[1]));
+      }
+    });
+    // rare nodes, lane by lane: x-periodic wrap, outlet, tail beyond the row
+    const bool lo_edge = xa == 0, hi_a = xa == p.dim[0] - 1, hi_b = xa + 1 == p.dim[0] - 1;
+    if (p.span[0] && (lo_edge || hi_a || hi_b)) {
+      const S* side = reinterpret_cast<const S*>(smem + s * C::STAGE + 9 * C::GROUP);
+      unroll<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if ((bm >> (i / 3)) & 1) return;
+        if constexpr (CX(i) == 1) {
+          if (lo_edge) f[i].v.x = SCvt<S>::to(side[(i / 3) * (C::SIDE / (int)sizeof(S)) + C::H - 1]);
+        }
+        if constexpr (CX(i) == -1) {
+          const float w = SCvt<S>::to(side[(9 + i / 3) * (C::SIDE / (int)sizeof(S))]);
+          if (hi_a) f[i].v.x = w;
+          if (hi_b) f[i].v.y = w;
+        }
+      });
+    }
+    if ((fl & 2) && (hi_a || hi_b)) {
+      // zero-gradient outlet: c_x = -1 populations from the node itself along x
+      unroll<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if constexpr (CX(i) == -1) {
+          if (!((bm >> (i / 3)) & 1)) {
+            const S* r = st + row_base<S>(i) + C::H + e0;
+            if (hi_a) f[i].v.x = SCvt<S>::to(r[0]);
+            if (hi_b) f[i].v.y = SCvt<S>::to(r[1]);
+          }
+        }
+      });
+    }
+    if (xa + 1 >= p.dim[0]) {
+      // beyond the row (storage padding): the rest state, so that the
+      // arithmetic stays finite; TMA stores it into the padding
+      const bool out_a = xa >= p.dim[0];
+      unroll<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if (out_a) f[i].v.x = 0.0f;
+        f[i].v.y = 0.0f;
+      });
+    }
+    // both warps of the pair have read stage s: its leader loads the pair's
+    // tile k + DI into it
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + cp) : "memory");
+    if (leader && k + DI < nmine)
+      issue_tile<S, DI>(b, (int)blockIdx.x + (k + DI) * (int)gridDim.x, smem + s * C::STAGE, &full[s], &tile_at[s]);
+    {
+      F2 rho_t, rho, ux, uy, uz;
+      macro_v<F2>(f, rho_t, rho, ux, uy, uz);
+      kbc_collide_v<F2, FM>(f, rho_t, rho, ux, uy, uz, F2(E.beta), F2(E.du[0]), F2(E.du[1]), F2(E.du[2]),
+                            E.du[0] != 0.0f, E.du[1] != 0.0f, E.du[2] != 0.0f, b.lbgk != 0);
+    }
+    if ((fl & 1) && lo_edge) {
+      // fixed inlet node: keeps its populations
+      const long long own = node_index(p, 0, y, z);
+      unroll<27>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        f[i].v.x = Stor<S>::ld(E.fin + (long long)i * p.plane + own);
+      });
+    }
+    // this warp's two [27][32] output segments: wait until the stores that
+    // last used them have read them, fill, store
+    if (lane == 0) bulk_wait_read<0>();
+    __syncwarp();
+    S* seg = reinterpret_cast<S*>(myseg + (lane >> 4) * C::OSEGB) + ((2 * lane) & 31);
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      Pair<S>::st2(seg + i * C::OSEG, f[i]);
+    });
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) {
+      tma_store_row(&E.map_out, myseg, tx * C::BX + 64 * h, y, z, 0);
+      tma_store_row(&E.map_out, myseg + C::OSEGB, tx * C::BX + 64 * h + 32, y, z, 0);
+      bulk_commit();
+    }
+  }
+  if (lane == 0) bulk_wait_all();
+}
+
 // Mixed tiles: node-by-node pull (walls, solids, outlet, interface layers).
 template <typename S, typename R, int FM>
 __global__ void __launch_bounds__(128) k_sc_tiles(PatchDev p, const S* __restrict__ fin, S* __restrict__ fout,
@@ -481,9 +701,42 @@ cudaError_t launch_tma_v(const TmaBatch<S, R>& b, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Packed-pair variants (k_sc_tma2): load stages, consumer pairs, CTAs per SM.
+struct Tma2Variant {
+  int di, np, minb;
+};
+constexpr Tma2Variant kTma2[2] = {{4, 2, 3}, {2, 2, 3}};
+
+template <typename S, int FM, int V>
+cudaError_t launch_tma2_v(const TmaBatch<S, float>& b, cudaStream_t st) {
+  constexpr int DI = kTma2[V].di, NP = kTma2[V].np, MINB = kTma2[V].minb;
+  using C = TmaCfg<S, DI>;
+  constexpr int THREADS = NP * 64;
+  constexpr int SMEM = DI * C::STAGE + 2 * NP * 2 * C::OSEGB + 128;
+  static int blocks_per_sm = -1, sms = 0;
+  auto kern = k_sc_tma2<S, FM, DI, NP, MINB>;
+  if (blocks_per_sm < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, THREADS, SMEM);
+    if (e) return e;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const int grid = std::min(b.ntiles, blocks_per_sm * sms);
+  kern<<<grid, THREADS, SMEM, st>>>(b);
+  return cudaGetLastError();
+}
+
 template <typename S, typename R, int FM>
 cudaError_t launch_tma_fm(const TmaBatch<S, R>& b, int variant, cudaStream_t st) {
   static_assert(TmaVariants<S>::N == 2, "variant dispatch");
+  if constexpr (std::is_same<R, float>::value) {
+    if (variant == 2) return launch_tma2_v<S, FM, 0>(b, st);
+    if (variant == 3) return launch_tma2_v<S, FM, 1>(b, st);
+  }
   return variant == 1 ? launch_tma_v<S, R, FM, 1>(b, st) : launch_tma_v<S, R, FM, 0>(b, st);
 }
 

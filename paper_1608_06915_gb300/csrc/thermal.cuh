@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
+#include "collide.cuh"
 #include "device.cuh"
 #include "kernels.h"
 

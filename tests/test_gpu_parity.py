@@ -377,10 +377,13 @@ def test_graph_replay_matches_direct_launches(storage):
 
 @pytest.mark.parametrize("storage", ["fp32", "fp64", "fp16s"])
 def test_tma_variants_give_identical_results(storage):
-    """The autotuner's variants differ in staging, occupancy and the schedule
-    of the reconstruction samples only: same bits after several coarse steps
-    on a three-level channel with walls and force, and on the four-level
-    sphere, for each of the four variants."""
+    """The autotuner's variants differ in staging, occupancy, nodes per
+    thread (single nodes, or node pairs on the packed FP32x2 instructions)
+    and the schedule of the reconstruction samples only: same bits after
+    several coarse steps on a three-level channel with walls and force, and
+    on the four-level sphere, for every variant (four TMA kernels for FP32
+    arithmetic, two for FP64, times two schedules)."""
+    nv = 4 if storage == "fp64" else 8
     import torch
     for case, fields in [
         (dict(I.channel_small_case(), accel0=(1e-5, 0, 0)),
@@ -391,7 +394,7 @@ def test_tma_variants_give_identical_results(storage):
         ga.set_variant(0)
         ga.step(5)
         torch.cuda.synchronize()
-        for v in (1, 2, 3):
+        for v in range(1, nv):
             gb, _ = twin(case, storage, fields(case), oracle=False)
             gb.set_variant(v)
             gb.step(5)
@@ -399,7 +402,7 @@ def test_tma_variants_give_identical_results(storage):
             for p in range(len(ga.patches)):
                 assert torch.equal(ga.get_populations(p), gb.get_populations(p)), (case["name"], v, p)
         with pytest.raises(Exception):
-            gb.set_variant(4)
+            gb.set_variant(nv)
 
 
 def test_autotune_reports_and_keeps_the_state_consistent():
