@@ -313,8 +313,11 @@ def adjoint_ratio(dev, storage="fp32", K=20):
     lam, ws = g.adjoint_buffers(K)
     g.checkpoint(ck, save=True)
     g.step(K)
-    g.adjoint_seed(lam, ws)
-    g.adjoint_step(ck, K, lam, ws)  # warm-up
+    # warm-up: the first call runs the reverse walk directly, the second
+    # captures it as a CUDA graph, which later calls replay
+    for _ in range(2):
+        g.adjoint_seed(lam, ws)
+        g.adjoint_step(ck, K, lam, ws)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     torch.cuda.synchronize(dev)
     e[0].record(g.stream)

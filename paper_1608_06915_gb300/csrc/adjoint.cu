@@ -137,10 +137,25 @@ __device__ void kbc_vjp(const R (&f)[27], R (&lam)[27], R beta, bool lbgk) {
   R gamma = R(2), sh = 0, hh = 0;
   bool use_gamma = false;
   const R ib = rcp_fast(beta);
+  // entropic weights 1 / f^eq_i in product form: (1/rho) ig_x(c_x) ig_y(c_y) ig_z(c_z)
+  R wxy[3][3], wz[3];
+  {
+    const R irho = rcp_fast(q.rho);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      wz[a] = irho * q.e[2].ig[a];
+#pragma unroll
+      for (int b2 = 0; b2 < 3; ++b2) wxy[a][b2] = q.e[0].ig[a] * q.e[1].ig[b2];
+    }
+  }
+  auto wgt = [&](auto I) -> R {
+    constexpr int i = decltype(I)::value;
+    return wxy[CX(i) + 1][CY(i) + 1] * wz[CZ(i) + 1];
+  };
   if (!lbgk) {
     unroll<27>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const R w = rcp_fast(R(WI(i)) + q.fe[i]);  // entropic weight 1 / f^eq_i
+      const R w = wgt(I);  // entropic weight 1 / f^eq_i
       const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
       const R dh = df[i] - ds;
       sh += ds * dh * w;
@@ -175,7 +190,7 @@ __device__ void kbc_vjp(const R (&f)[27], R (&lam)[27], R beta, bool lbgk) {
       R dsb = b * lam[i];
       if (use_gamma) {
         const R dh = df[i] - ds;
-        const R w = rcp_fast(R(WI(i)) + q.fe[i]);
+        const R w = wgt(I);
         const R dhb = (Lsh * ds + R(2) * Lhh * dh) * w;
         dsb += Lsh * dh * w - dhb;
       }
@@ -205,7 +220,7 @@ __device__ void kbc_vjp(const R (&f)[27], R (&lam)[27], R beta, bool lbgk) {
     if (use_gamma) {
       const R ds = shear_part<i>(nxx, nyy, nzz, pxy, pxz, pyz);
       const R dh = df[i] - ds;
-      const R w = rcp_fast(fefull);
+      const R w = wgt(I);
       dfb += (Lsh * ds + R(2) * Lhh * dh) * w;
       feb -= (Lsh * ds * dh + Lhh * dh * dh) * w * w;  // d(1/fe) = -w^2
     }
@@ -321,6 +336,57 @@ __global__ void __launch_bounds__(128, 3) k_adj_sc(PatchDev p, const R* __restri
   kbc_vjp<R>(f, l, beta, lbgk != 0);
   if constexpr (PLAIN) push_bulk<R>(p, lam_old, x, y, z, l);
   else push_adjoint<R>(p, lam_old, x, y, z, l);
+}
+
+// Stream-collide adjoint with plain stores, for patches without boundary-class
+// nodes: every entry (y, i) of lambda_old has exactly one pusher, the node
+// x = y + c_i (wrapped on spanned axes).  A node updated in the substep pushes
+// the adjoint of its pre-collision state; any other stored node pushes zeros;
+// an entry whose pusher lies beyond a non-spanned face of the storage box is
+// zeroed by its own node.  So the kernel writes every entry once, needs no
+// clearing beforehand, and its result does not depend on the order threads
+// run in.  The coupling adjoints add to lambda_old after it.
+template <typename R>
+__global__ void __launch_bounds__(128, 4) k_adj_sc_st(PatchDev p, const R* __restrict__ fin,
+                                                   const R* __restrict__ lam_new, R* __restrict__ lam_old, R beta,
+                                                   int odd, int lbgk) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (long long)p.dim[0] * p.dim[1] * p.dim[2]) return;
+  const int x = (int)(k % p.dim[0]), y = (int)((k / p.dim[0]) % p.dim[1]);
+  const int z = (int)(k / ((long long)p.dim[0] * p.dim[1]));
+  const long long own = node_index(p, x, y, z);
+  const uint8_t t = p.type[own];
+  R l[27];
+  if (t == T_BULK || (t == T_D1 && odd)) {
+    R f[27];
+    pull_bulk<R, R>(p, fin, x, y, z, f);
+    load_lam<R>(p, lam_new, own, l);
+    kbc_vjp<R>(f, l, beta, lbgk != 0);
+  } else {
+    unroll<27>([&](auto I) { l[decltype(I)::value] = R(0); });
+  }
+  // source coordinate along an axis for shift -c (the pull source), -1 if
+  // beyond a non-spanned face
+  const int X[3] = {x, y, z};
+  int src[3][3], dst_in[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = -1; c <= 1; ++c) {
+      int v = X[a] - c;
+      if (v < 0 || v >= p.dim[a]) v = p.span[a] ? (v < 0 ? v + p.dim[a] : v - p.dim[a]) : -1;
+      src[a][c + 1] = v;
+      const int w = X[a] + c;  // the pusher of this node's entry along the axis
+      dst_in[a][c + 1] = (w >= 0 && w < p.dim[a]) || p.span[a];
+    }
+  const long long row = p.nxp, sl = (long long)p.nxp * p.dim[1];
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int sx = src[0][CX(i) + 1], sy = src[1][CY(i) + 1], sz = src[2][CZ(i) + 1];
+    if (sx >= 0 && sy >= 0 && sz >= 0) lam_old[(long long)i * p.plane + sz * sl + sy * row + sx] = l[i];
+    if (!(dst_in[0][CX(i) + 1] && dst_in[1][CY(i) + 1] && dst_in[2][CZ(i) + 1]))
+      lam_old[(long long)i * p.plane + own] = R(0);
+  });
 }
 
 __device__ __forceinline__ void node_xyz(const PatchDev& p, long long n, int& x, int& y, int& z) {
@@ -812,6 +878,10 @@ cudaError_t launch_adj_sc(int storage, const PatchDev& p, const void* fin, const
     using R = decltype(z);
     const long long n = (long long)p.dim[0] * p.dim[1] * p.dim[2];
     dim3 block(128), grid((unsigned)((n + 127) / 128));
+    if (!with_bc) {  // plain stores, lambda_old needs no clearing
+      k_adj_sc_st<R><<<grid, block, 0, st>>>(p, (const R*)fin, (const R*)lam_new, (R*)lam_old, (R)beta, odd, lbgk);
+      return cudaGetLastError();
+    }
     k_adj_sc<R, true><<<grid, block, 0, st>>>(p, (const R*)fin, (const R*)lam_new, (R*)lam_old, (R)beta, odd, lbgk,
                                               status);
     cudaError_t e = cudaGetLastError();

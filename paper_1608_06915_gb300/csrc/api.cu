@@ -73,26 +73,42 @@ struct lbm_grid {
     cudaGraphExec_t exec;
   };
   std::vector<StepGraph> gcache;
-  // CUDA graphs of the reverse sweep of one coarse step of the adjoint, keyed
-  // by the buffer indices of the state and of lambda, the snapshot and the
-  // caller's buffers; they hold the indices the sweep leaves behind
+  // CUDA graphs of the adjoint's reverse walk over a segment, keyed by the
+  // buffer indices of lambda, the segment length and the caller's buffers;
+  // they hold the indices the walk leaves behind
   struct AdjGraph {
-    std::vector<uint8_t> cur, lcur, cur_after, lcur_after;
-    const void *snap, *lam, *ws;
+    std::vector<uint8_t> lcur, lcur_after;
+    int K;
+    const void *lam, *ws;
     cudaGraphExec_t exec;
   };
   std::vector<AdjGraph> acache;
   bool adj_swept = false;
+  // CUDA graphs of the recording step of the adjoint's recompute, keyed by the
+  // buffer indices, the record's device word and the record's size
+  struct RecGraph {
+    std::vector<uint8_t> cur;
+    const unsigned long long* slot;
+    size_t step_bytes;
+    cudaGraphExec_t exec;
+  };
+  std::vector<RecGraph> rcache;
+  bool rec_warm = false;
   void drop_graphs() {
     for (auto& x : gcache) cudaGraphExecDestroy(x.exec);
     gcache.clear();
     for (auto& x : acache) cudaGraphExecDestroy(x.exec);
     acache.clear();
+    for (auto& x : rcache) cudaGraphExecDestroy(x.exec);
+    rcache.clear();
   }
   // side streams of the adjoint: coupling adjoints run beside the
   // stream-collide adjoint (their writes are reductions that commute)
   cudaStream_t adj_side[2] = {nullptr, nullptr};
   cudaEvent_t adj_fork = nullptr, adj_join[2] = {nullptr, nullptr};
+  cudaEvent_t adj_sc = nullptr, adj_cf = nullptr;  // stream-collide and coalesce adjoints of an instant done
+  cudaEvent_t adj_s0 = nullptr;                     // side stream 0's work so far
+
   // side streams of the forward step: [0] node-by-node remainders, [1], [2]
   // coupling chains, all beside each other after the TMA pass of an instant
   cudaStream_t fwd_side[3] = {nullptr, nullptr, nullptr};
@@ -111,6 +127,10 @@ struct lbm_grid {
     for (auto& x : adj_side)
       if (x) cudaStreamDestroy(x);
     if (adj_fork) cudaEventDestroy(adj_fork);
+    if (adj_sc) cudaEventDestroy(adj_sc);
+    if (adj_s0) cudaEventDestroy(adj_s0);
+    if (adj_cf) cudaEventDestroy(adj_cf);
+
     for (auto& x : adj_join)
       if (x) cudaEventDestroy(x);
     drop_graphs();
@@ -1009,11 +1029,23 @@ lbm_status adjoint_supported(lbm_grid* g) {
   return LBM_OK;
 }
 
+// Workspace of lbm_adjoint_step: the second lambda buffer, the sample
+// adjoints, and per coarse step of the segment one record of the recompute:
+// the state of every patch at the step's start (outer snapshot), then, after
+// each inner instant k = 1 .. 2^(L-1) - 1, the state of the levels >= 1 (inner
+// snapshot k), so that the adjoint of every instant finds its pre-states
+// without replaying the forward.
 struct AdjLayout {
   std::vector<size_t> lam_off;   // per patch, in the packed lambda (and in the second buffer)
   std::vector<size_t> sbar_off;  // per patch (children), in the workspace
-  std::vector<size_t> snap_patch_off;  // per patch, within one snapshot
-  size_t lam_bytes = 0, second_off = 0, snap_off = 0, snap_bytes = 0, partial_off = 0, total = 0;
+  std::vector<size_t> snap_patch_off;   // per patch, within an outer snapshot
+  std::vector<size_t> inner_patch_off;  // per patch of level >= 1, within an inner snapshot
+  // per patch and instant k: offset of the reconstruction values recorded when
+  // the patch exploded at k (its parent stepped too), (size_t)-1 otherwise
+  std::vector<std::vector<size_t>> smp_rec_off;
+  size_t lam_bytes = 0, second_off = 0, snap_off = 0, snap_bytes = 0, inner_bytes = 0, step_bytes = 0;
+  size_t slot_off = 0, partial_off = 0, total = 0;
+  int inner = 0;  // inner instants per coarse step
 };
 
 AdjLayout adjoint_layout(const lbm_grid* g, int K) {
@@ -1036,12 +1068,91 @@ AdjLayout adjoint_layout(const lbm_grid* g, int K) {
   a.snap_bytes = 0;
   for (auto& p : g->hg.P) {
     a.snap_patch_off.push_back(a.snap_bytes);
-    a.snap_bytes += 27 * (size_t)p.plane * g->hg.pop_bytes;
+    a.inner_patch_off.push_back(a.inner_bytes);
+    const size_t n = 27 * (size_t)p.plane * g->hg.pop_bytes;
+    a.snap_bytes += n;
+    if (p.level > 0) a.inner_bytes += n;
   }
-  a.snap_off = take(a.snap_bytes * (size_t)K);
+  a.inner = (1 << (g->hg.nlev - 1)) - 1;
+  size_t rec = a.snap_bytes + (size_t)a.inner * a.inner_bytes;
+  const int L = g->hg.nlev, KI = 1 << (L - 1);
+  for (auto& p : g->hg.P) {
+    std::vector<size_t> offs(KI + 1, (size_t)-1);
+    if (p.level > 0)
+      for (int k = 1; k <= KI; ++k) {
+        const int stride = 1 << (L - 1 - p.level);
+        if (k % stride || (k / stride) % 2) continue;  // stepped, with the parent active
+        rec = (rec + 255) / 256 * 256;
+        offs[k] = rec;
+        rec += 31 * p.n_points() * g->hg.real_bytes;
+      }
+    a.smp_rec_off.push_back(offs);
+  }
+  a.step_bytes = (rec + 255) / 256 * 256;
+  a.snap_off = take(a.step_bytes * (size_t)K);
+  a.slot_off = take(sizeof(unsigned long long));
   a.partial_off = take(sizeof(double) * (kDiagBlocks * g->hg.P.size() + 1));
   a.total = w;
   return a;
+}
+
+// Pre-state of patch pi before instant k (1 .. 2^(L-1)) of the coarse step
+// recorded at `step`: level 0 and every level at k = 1 from the outer
+// snapshot, the others from inner snapshot k - 1 (the state after instant
+// k - 1, which is the patch's state before its step at k).
+uint8_t* pre_state(const lbm_grid* g, const AdjLayout& a, uint8_t* step, int pi, int k) {
+  const HostPatch& p = g->hg.P[pi];
+  if (p.level == 0 || k == 1) return step + a.snap_patch_off[pi];
+  return step + a.snap_bytes + (size_t)(k - 2) * a.inner_bytes + a.inner_patch_off[pi];
+}
+
+// One coarse step of the recompute, recording its snapshots through the
+// device word at `slot` (the current step's record; advanced at the end), so
+// that one captured graph serves every step of the segment.
+lbm_status recording_step(lbm_grid* g, const AdjLayout& a, unsigned long long* slot) {
+  const int L = g->hg.nlev, KI = 1 << (L - 1);
+  lbmk::CopySegs segs{};
+  segs.rel = slot;
+  cudaError_t e = cudaSuccess;
+  auto add = [&](size_t off, const void* src, size_t n) {
+    if (segs.n == lbmk::kCopySegs) {
+      if (!e) e = lbmk::launch_copy(segs, g->stream);
+      segs.n = 0;
+    }
+    segs.dst[segs.n] = reinterpret_cast<void*>(off);
+    segs.src[segs.n] = src;
+    segs.bytes[segs.n] = n;
+    ++segs.n;
+  };
+  auto flush = [&] {
+    if (!e) e = lbmk::launch_copy(segs, g->stream);
+    segs.n = 0;
+  };
+  // outer snapshot: every patch at the step's start
+  for (size_t pi = 0; pi < g->hg.P.size(); ++pi) {
+    const HostPatch& p = g->hg.P[pi];
+    add(a.snap_patch_off[pi], g->base + p.off_f[p.cur], 27 * (size_t)p.plane * g->hg.pop_bytes);
+  }
+  flush();
+  if (e) return cuda_check(g, e, "adjoint snapshot");
+  for (int k = 1; k <= KI; ++k) {
+    if (lbm_status st = run_instant(g, k)) return st;
+    // the reconstruction values of the children that exploded at k
+    for (size_t pi = 0; pi < g->hg.P.size(); ++pi)
+      if (a.smp_rec_off[pi][k] != (size_t)-1)
+        add(a.smp_rec_off[pi][k], g->base + g->hg.P[pi].off_smp_val, 31 * g->hg.P[pi].n_points() * g->hg.real_bytes);
+    // inner snapshot k: the levels >= 1 after instant k
+    if (k < KI)
+      for (size_t pi = 0; pi < g->hg.P.size(); ++pi) {
+        const HostPatch& p = g->hg.P[pi];
+        if (p.level == 0) continue;
+        add(a.snap_bytes + (size_t)(k - 1) * a.inner_bytes + a.inner_patch_off[pi], g->base + p.off_f[p.cur],
+            27 * (size_t)p.plane * g->hg.pop_bytes);
+      }
+    flush();
+    if (e) return cuda_check(g, e, "adjoint snapshot");
+  }
+  return cuda_check(g, lbmk::launch_word(slot, a.step_bytes, 1, g->stream), "adjoint snapshot slot");
 }
 
 // Copies the state of every patch to/from a packed buffer (restore: the current
@@ -1085,14 +1196,10 @@ void flip_instant(lbm_grid* g, int k) {
 
 // Adjoint of instant k: lambda of the states after k -> lambda of the states before k.
 lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>& lcur, const AdjLayout& a,
-                           uint8_t* ws, uint8_t* snap) {
+                           uint8_t* ws, uint8_t* step) {
   HostGrid& hg = g->hg;
-  // pre-states: level 0 steps once per coarse step, at the top instant, so its
-  // state before every instant is the snapshot itself
-  auto state = [&](int pi) -> uint8_t* {
-    const HostPatch& p = hg.P[pi];
-    return p.level == 0 ? snap + a.snap_patch_off[pi] : g->base + p.off_f[p.cur];
-  };
+  // pre-states of the instant, from the record of its coarse step
+  auto state = [&](int pi) -> uint8_t* { return pre_state(g, a, step, pi, k); };
   const int L = hg.nlev, storage = hg.desc.storage, lbgk = hg.desc.mirror_lbgk;
   const size_t rb = hg.real_bytes;
   auto lam_ptr = [&](int pi, int which) { return lam[which] + a.lam_off[pi]; };
@@ -1103,31 +1210,49 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
       if (hg.P[pi].level == lev) active.push_back((int)pi);
   }
   cudaError_t e = cudaSuccess;
+  // lambda_old of patches with boundary-class nodes is accumulated and needs
+  // clearing; the others are written entry by entry by their stream-collide
+  // adjoint (k_adj_sc_st)
   for (int pi : active)
-    if (!e) e = cudaMemsetAsync(lam_ptr(pi, 1 - lcur[pi]), 0, 27 * (size_t)hg.P[pi].plane * rb, g->stream);
+    if (!e && hg.P[pi].n_bc > 0)
+      e = cudaMemsetAsync(lam_ptr(pi, 1 - lcur[pi]), 0, 27 * (size_t)hg.P[pi].plane * rb, g->stream);
   if (e) return cuda_check(g, e, "adjoint zero");
-  // three independent chains after the zeroing: the stream-collide adjoints
-  // (bound stream), the coalesce adjoints (side stream 0) and, per child, the
-  // explode chain (side stream 1); each adds into lambda with reductions
   for (int q = 0; q < 2 && !e; ++q)
     if (!g->adj_side[q]) e = side_stream(&g->adj_side[q]);
   if (!e && !g->adj_fork) e = cudaEventCreateWithFlags(&g->adj_fork, cudaEventDisableTiming);
+  if (!e && !g->adj_sc) e = cudaEventCreateWithFlags(&g->adj_sc, cudaEventDisableTiming);
+  if (!e && !g->adj_cf) e = cudaEventCreateWithFlags(&g->adj_cf, cudaEventDisableTiming);
   for (int q = 0; q < 2 && !e; ++q)
     if (!g->adj_join[q]) e = cudaEventCreateWithFlags(&g->adj_join[q], cudaEventDisableTiming);
+  // side stream 0 carries the levels >= 1 from instant to instant and is not
+  // joined into the bound stream at the end of an instant (the walk joins it
+  // at its end), so that level 0's adjoint of the next coarse step runs beside
+  // the level-1 work of an instant that steps level 1 alone; side stream 1
+  // (the explode chain reads the children's lambda) waits for it
+  if (!e && !g->adj_s0) e = cudaEventCreateWithFlags(&g->adj_s0, cudaEventDisableTiming);
   if (!e) e = cudaEventRecord(g->adj_fork, g->stream);
   for (int q = 0; q < 2 && !e; ++q) e = cudaStreamWaitEvent(g->adj_side[q], g->adj_fork, 0);
+  if (!e) e = cudaEventRecord(g->adj_s0, g->adj_side[0]);
+  if (!e) e = cudaStreamWaitEvent(g->adj_side[1], g->adj_s0, 0);
   if (e) return cuda_check(g, e, "adjoint streams");
   cudaStream_t sc = g->adj_side[0], sx = g->adj_side[1];
+  // (1) the stream-collide adjoints, which write (or start) every lambda_old:
+  // level 0 on the bound stream; the levels >= 1 on side stream 0, followed
+  // there by (2) the coalesce adjoints, which add into the children's
+  // lambda_old, so that level 0's runs beside both
   for (int pi : active) {
     HostPatch& p = hg.P[pi];
     const int lev = p.level;
     const int s = k / (1 << (L - 1 - lev));
-    const bool parent_active = (s % 2) == 0;
-    const int odd = (lev > 0 && !parent_active) ? 1 : 0;
-    const lbmk::PatchDev pv = view(g, p);
+    const int odd = (lev > 0 && (s % 2)) ? 1 : 0;
     if (!e)
-      e = lbmk::launch_adj_sc(storage, pv, state(pi), lam_ptr(pi, lcur[pi]), lam_ptr(pi, 1 - lcur[pi]),
-                              p.beta, odd, lbgk, p.n_bc > 0, status_ptr(g), g->stream);
+      e = lbmk::launch_adj_sc(storage, view(g, p), state(pi), lam_ptr(pi, lcur[pi]), lam_ptr(pi, 1 - lcur[pi]),
+                              p.beta, odd, lbgk, p.n_bc > 0, status_ptr(g), lev == 0 ? g->stream : sc);
+  }
+  if (!e) e = cudaEventRecord(g->adj_sc, g->stream);
+  for (int pi : active) {
+    HostPatch& p = hg.P[pi];
+    const lbmk::PatchDev pv = view(g, p);
     for (int ci : p.kids) {
       HostPatch& c = hg.P[ci];
       if (!e)
@@ -1136,38 +1261,51 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
                                       at<uint32_t>(g, c.off_cf_child), (int64_t)c.cf_parent.size(),
                                       2.0 * c.beta / p.beta, p.beta, lbgk, status_ptr(g), sc);
     }
-    if (lev > 0 && parent_active) {
-      HostPatch& q = hg.P[p.parent];
-      const int qi = p.parent;
-      const lbmk::PatchDev qv = view(g, q);
-      uint8_t* sbar = ws + a.sbar_off[pi];
-      const int64_t ns = (int64_t)p.smp_node.size(), ld = (int64_t)p.n_points();
-      const uint32_t* psrc = at<uint32_t>(g, p.off_pt_src);
-      if (!e)
-        e = lbmk::launch_samples(storage, qv, state(qi), pv, state(pi),
-                                 at<uint32_t>(g, p.off_smp_node), at<uint8_t>(g, p.off_smp_kind), ns,
-                                 g->base + p.off_smp_val, ld, q.beta / (2.0 * p.beta), status_ptr(g), sx);
-      if (!e) e = point_passes(g, p, 31, sx);
-      if (!e && ld) e = cudaMemsetAsync(sbar, 0, 31 * (size_t)ld * rb, sx);
-      if (!e)
-        e = lbmk::launch_adj_explode(storage, pv, lam_ptr(pi, lcur[pi]), at<uint32_t>(g, p.off_ex_node),
-                                     at<uint32_t>(g, p.off_ex_src), (int64_t)p.ex_one, (int64_t)p.ex_node.size(),
-                                     g->base + p.off_smp_val, sbar, ld, p.beta, lbgk, sx);
-      // the interpolation passes transposed, last pass first
-      if (!e)
-        e = lbmk::launch_adj_points(storage, psrc + 4 * (size_t)p.n_pt[0], p.n_pt[1], sbar, ld, ns + p.n_pt[0], sx);
-      if (!e) e = lbmk::launch_adj_points(storage, psrc, p.n_pt[0], sbar, ld, ns, sx);
-      if (!e)
-        e = lbmk::launch_adj_samples(storage, qv, state(qi), lam_ptr(qi, 1 - lcur[qi]), pv, state(pi),
-                                     lam_ptr(pi, 1 - lcur[pi]),
-                                     at<uint32_t>(g, p.off_smp_node), at<uint8_t>(g, p.off_smp_kind), ns, sbar, ld,
-                                     q.beta / (2.0 * p.beta), status_ptr(g), sx);
-    }
   }
-  // join the side streams back into the bound stream
-  for (int q = 0; q < 2; ++q) {
-    cudaError_t e2 = cudaEventRecord(g->adj_join[q], g->adj_side[q]);
-    if (!e2) e2 = cudaStreamWaitEvent(g->stream, g->adj_join[q], 0);
+  if (!e) e = cudaEventRecord(g->adj_cf, sc);
+  // (3) per child stepped with its parent: the explode chain -- the explode
+  // adjoint on the reconstruction values the recompute recorded, the point
+  // passes transposed (last first) -- beside (1) and (2), then the sample
+  // adjoint, which adds into both levels' lambda_old after (1) and (2): each
+  // entry takes its additions in a fixed order
+  bool waited = false;
+  for (int pi : active) {
+    HostPatch& p = hg.P[pi];
+    const int lev = p.level;
+    const int s = k / (1 << (L - 1 - lev));
+    if (!(lev > 0 && (s % 2) == 0)) continue;
+    const lbmk::PatchDev pv = view(g, p);
+    HostPatch& q = hg.P[p.parent];
+    const int qi = p.parent;
+    const lbmk::PatchDev qv = view(g, q);
+    uint8_t* sbar = ws + a.sbar_off[pi];
+    const int64_t ns = (int64_t)p.smp_node.size(), ld = (int64_t)p.n_points();
+    const uint32_t* psrc = at<uint32_t>(g, p.off_pt_src);
+    // the reconstruction values of this explode, recorded by the recompute
+    const uint8_t* val = step + a.smp_rec_off[pi][k];
+    if (!e && ld) e = cudaMemsetAsync(sbar, 0, 31 * (size_t)ld * rb, sx);
+    if (!e)
+      e = lbmk::launch_adj_explode(storage, pv, lam_ptr(pi, lcur[pi]), at<uint32_t>(g, p.off_ex_node),
+                                   at<uint32_t>(g, p.off_ex_src), (int64_t)p.ex_one, (int64_t)p.ex_node.size(),
+                                   val, sbar, ld, p.beta, lbgk, sx);
+    if (!e)
+      e = lbmk::launch_adj_points(storage, psrc + 4 * (size_t)p.n_pt[0], p.n_pt[1], sbar, ld, ns + p.n_pt[0], sx);
+    if (!e) e = lbmk::launch_adj_points(storage, psrc, p.n_pt[0], sbar, ld, ns, sx);
+    if (!e && !waited) {
+      e = cudaStreamWaitEvent(sx, g->adj_sc, 0);
+      if (!e) e = cudaStreamWaitEvent(sx, g->adj_cf, 0);
+      waited = true;
+    }
+    if (!e)
+      e = lbmk::launch_adj_samples(storage, qv, state(qi), lam_ptr(qi, 1 - lcur[qi]), pv, state(pi),
+                                   lam_ptr(pi, 1 - lcur[pi]), at<uint32_t>(g, p.off_smp_node),
+                                   at<uint8_t>(g, p.off_smp_kind), ns, sbar, ld, q.beta / (2.0 * p.beta),
+                                   status_ptr(g), sx);
+  }
+  // join side stream 1 back into the bound stream (side stream 0 at the end of the walk)
+  {
+    cudaError_t e2 = cudaEventRecord(g->adj_join[1], g->adj_side[1]);
+    if (!e2) e2 = cudaStreamWaitEvent(g->stream, g->adj_join[1], 0);
     if (!e) e = e2;
   }
   if (e) return cuda_check(g, e, "adjoint instant");
@@ -1175,43 +1313,28 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
   return LBM_OK;
 }
 
-// Reverse sweep of one coarse step from its snapshot: every instant's adjoint,
-// top instant first, with the forward instants replayed where the states they
-// need are no longer in the buffers.
-lbm_status adjoint_sweep(lbm_grid* g, uint8_t* snap, uint8_t* lam[2], std::vector<int>& lcur, const AdjLayout& a,
-                         uint8_t* ws) {
+// Reverse walk of a segment of K coarse steps from their records: every
+// instant's adjoint, last coarse step and top instant first; the pre-states
+// come from the records, so nothing is replayed and the grid's state buffers
+// are not touched.  Side stream 0 is joined into the bound stream at the end.
+lbm_status adjoint_walk(lbm_grid* g, int K, uint8_t* lam[2], std::vector<int>& lcur, const AdjLayout& a, uint8_t* ws) {
   const int KI = 1 << (g->hg.nlev - 1);
-  // have: the buffers hold the state after `have` instants of this coarse step;
-  // last: the instant executed most recently (its previous states are still in
-  // the other buffers of the patches it wrote)
-  int have = -1, last = -1;
-  for (int k = KI; k >= 1; --k) {
-    if (have == k && last == k) {
-      flip_instant(g, k);
-      have = k - 1;
-      last = -1;
-    }
-    if (have != k - 1) {
-      // the state at the start of this coarse step, for the levels the
-      // replayed instants step (level 0 is read from the snapshot itself)
-      cudaError_t e = copy_state(g, snap, false, false, 1);
-      if (e) return cuda_check(g, e, "adjoint replay");
-      for (int kk = 1; kk < k; ++kk)
-        if (lbm_status st = run_instant(g, kk)) return st;
-      have = k - 1;
-      last = k - 1;
-    }
-    if (lbm_status st = adjoint_instant(g, k, lam, lcur, a, ws, snap)) return st;
+  for (int s = K - 1; s >= 0; --s) {
+    uint8_t* step = ws + a.snap_off + (size_t)s * a.step_bytes;
+    for (int k = KI; k >= 1; --k)
+      if (lbm_status st = adjoint_instant(g, k, lam, lcur, a, ws, step)) return st;
   }
-  return LBM_OK;
+  cudaError_t e = cudaEventRecord(g->adj_join[0], g->adj_side[0]);
+  if (!e) e = cudaStreamWaitEvent(g->stream, g->adj_join[0], 0);
+  return cuda_check(g, e, "adjoint walk join");
 }
 
 constexpr size_t kMaxAdjGraphs = 64;
 
-// Captures one reverse sweep; the host-side buffer indices advance as in the
-// direct sweep (the caller launches the graph).
-lbm_status capture_sweep(lbm_grid* g, uint8_t* snap, uint8_t* lam[2], std::vector<int>& lcur, const AdjLayout& a,
-                         uint8_t* ws, cudaGraphExec_t* out) {
+// Captures one recording step of the recompute; the host-side buffer indices
+// are put back afterwards (capture launches nothing).
+lbm_status capture_recording(lbm_grid* g, const AdjLayout& a, unsigned long long* slot, const std::vector<uint8_t>& key,
+                             cudaGraphExec_t* out) {
   if (!g->cap_stream) {
     if (cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking))
       return cuda_check(g, e, "capture stream");
@@ -1219,7 +1342,33 @@ lbm_status capture_sweep(lbm_grid* g, uint8_t* snap, uint8_t* lam[2], std::vecto
   cudaStream_t keep = g->stream;
   g->stream = g->cap_stream;
   cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed);
-  lbm_status st = e ? LBM_OK : adjoint_sweep(g, snap, lam, lcur, a, ws);
+  lbm_status st = e ? LBM_OK : recording_step(g, a, slot);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = e ? cudaSuccess : cudaStreamEndCapture(g->cap_stream, &graph);
+  g->stream = keep;
+  for (size_t i = 0; i < g->hg.P.size(); ++i) g->hg.P[i].cur = key[i];
+  if (e) return cuda_check(g, e, "cudaStreamBeginCapture");
+  if (st || e2) {
+    if (graph) cudaGraphDestroy(graph);
+    return st ? st : cuda_check(g, e2, "cudaStreamEndCapture");
+  }
+  e = cudaGraphInstantiate(out, graph, cudaGraphInstantiateFlagUseNodePriority);
+  cudaGraphDestroy(graph);
+  return cuda_check(g, e, "cudaGraphInstantiate");
+}
+
+// Captures the reverse walk; the host-side lambda indices advance as in the
+// direct walk (the caller launches the graph).
+lbm_status capture_walk(lbm_grid* g, int K, uint8_t* lam[2], std::vector<int>& lcur, const AdjLayout& a, uint8_t* ws,
+                        cudaGraphExec_t* out) {
+  if (!g->cap_stream) {
+    if (cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking))
+      return cuda_check(g, e, "capture stream");
+  }
+  cudaStream_t keep = g->stream;
+  g->stream = g->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed);
+  lbm_status st = e ? LBM_OK : adjoint_walk(g, K, lam, lcur, a, ws);
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = e ? cudaSuccess : cudaStreamEndCapture(g->cap_stream, &graph);
   g->stream = keep;
@@ -1279,42 +1428,58 @@ lbm_status lbm_adjoint_step(lbm_grid_t g, const void* ckpt, int32_t K, void* lam
   std::vector<int> lcur(g->hg.P.size(), 0);
   cudaError_t e = copy_state(g, const_cast<uint8_t*>(static_cast<const uint8_t*>(ckpt)), false);
   if (e) return cuda_check(g, e, "adjoint restore");
-  // recompute the segment, one snapshot per coarse step
+  // recompute the segment, recording each coarse step (outer and inner
+  // snapshots); the record's address is a device word the steps advance, so
+  // the recording step replays as one CUDA graph per buffer parity
+  auto* slot = reinterpret_cast<unsigned long long*>(ws + a.slot_off);
+  e = lbmk::launch_word(slot, (unsigned long long)(uintptr_t)(ws + a.snap_off), 0, g->stream);
+  if (e) return cuda_check(g, e, "adjoint record");
   for (int s = 0; s < K; ++s) {
-    e = copy_state(g, ws + a.snap_off + (size_t)s * a.snap_bytes, true);
-    if (e) return cuda_check(g, e, "adjoint snapshot");
-    if (lbm_status st = lbm_step(g, 1)) return st;
-  }
-  for (int s = K - 1; s >= 0; --s) {
-    uint8_t* snap = ws + a.snap_off + (size_t)s * a.snap_bytes;
-    if (!g->graphs || g->timing || !g->adj_swept) {
-      // the first sweep runs directly, so that capture finds every kernel loaded
-      if (lbm_status st = adjoint_sweep(g, snap, lam, lcur, a, ws)) return st;
-      g->adj_swept = true;
+    if (!g->graphs || g->timing || !g->rec_warm) {
+      // the first recording step runs directly, so that capture finds every kernel loaded
+      if (lbm_status st = recording_step(g, a, slot)) return st;
+      g->rec_warm = true;
       continue;
     }
-    std::vector<uint8_t> lkey(lcur.begin(), lcur.end());
     const std::vector<uint8_t> key = cur_key(g);
+    cudaGraphExec_t exec = nullptr;
+    for (auto& x : g->rcache)
+      if (x.cur == key && x.slot == slot && x.step_bytes == a.step_bytes) exec = x.exec;
+    if (!exec) {
+      if (g->rcache.size() >= kMaxStepGraphs) {
+        for (auto& x : g->rcache) cudaGraphExecDestroy(x.exec);
+        g->rcache.clear();
+      }
+      if (lbm_status st = capture_recording(g, a, slot, key, &exec)) return st;
+      g->rcache.push_back({key, slot, a.step_bytes, exec});
+    }
+    if (cudaError_t e2 = cudaGraphLaunch(exec, g->stream)) return cuda_check(g, e2, "cudaGraphLaunch");
+    const int L = g->hg.nlev, KI = 1 << (L - 1);
+    for (auto& p : g->hg.P)
+      if ((KI >> (L - 1 - p.level)) & 1) p.cur ^= 1;
+  }
+  if (!g->graphs || g->timing || !g->adj_swept) {
+    // the first walk runs directly, so that capture finds every kernel loaded
+    if (lbm_status st = adjoint_walk(g, K, lam, lcur, a, ws)) return st;
+    g->adj_swept = true;
+  } else {
+    std::vector<uint8_t> lkey(lcur.begin(), lcur.end());
     const lbm_grid::AdjGraph* hit = nullptr;
     for (auto& x : g->acache)
-      if (x.cur == key && x.lcur == lkey && x.snap == snap && x.lam == lam[0] && x.ws == ws) hit = &x;
+      if (x.lcur == lkey && x.K == K && x.lam == lam[0] && x.ws == ws) hit = &x;
     if (!hit) {
       if (g->acache.size() >= kMaxAdjGraphs) {
         for (auto& x : g->acache) cudaGraphExecDestroy(x.exec);
         g->acache.clear();
       }
-      lbm_grid::AdjGraph ag{key, lkey, {}, {}, snap, lam[0], ws, nullptr};
-      if (lbm_status st = capture_sweep(g, snap, lam, lcur, a, ws, &ag.exec)) return st;
-      ag.cur_after = cur_key(g);
+      lbm_grid::AdjGraph ag{lkey, {}, K, lam[0], ws, nullptr};
+      if (lbm_status st = capture_walk(g, K, lam, lcur, a, ws, &ag.exec)) return st;
       ag.lcur_after.assign(lcur.begin(), lcur.end());
       g->acache.push_back(ag);
       hit = &g->acache.back();
     }
     if (cudaError_t e2 = cudaGraphLaunch(hit->exec, g->stream)) return cuda_check(g, e2, "cudaGraphLaunch");
-    for (size_t i = 0; i < g->hg.P.size(); ++i) {
-      g->hg.P[i].cur = hit->cur_after[i];
-      lcur[i] = hit->lcur_after[i];
-    }
+    for (size_t i = 0; i < g->hg.P.size(); ++i) lcur[i] = hit->lcur_after[i];
   }
   // lambda back into the caller's buffer; grid state back at the segment start
   for (size_t pi = 0; pi < g->hg.P.size() && !e; ++pi)

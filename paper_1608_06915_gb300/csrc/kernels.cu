@@ -818,12 +818,22 @@ __device__ __forceinline__ void copy_words(V* __restrict__ d, const V* __restric
 
 __global__ void __launch_bounds__(256) k_copy(CopySegs segs) {
   const int j = blockIdx.y;
-  const uintptr_t a = (uintptr_t)segs.dst[j] | (uintptr_t)segs.src[j] | (uintptr_t)segs.bytes[j];
+  void* dst = segs.rel ? (void*)(uintptr_t)(*segs.rel + (uintptr_t)segs.dst[j]) : segs.dst[j];
+  const uintptr_t a = (uintptr_t)dst | (uintptr_t)segs.src[j] | (uintptr_t)segs.bytes[j];
   const size_t n = segs.bytes[j];
-  if ((a & 15) == 0) copy_words((uint4*)segs.dst[j], (const uint4*)segs.src[j], n / 16);
-  else if ((a & 7) == 0) copy_words((uint2*)segs.dst[j], (const uint2*)segs.src[j], n / 8);
-  else if ((a & 3) == 0) copy_words((unsigned*)segs.dst[j], (const unsigned*)segs.src[j], n / 4);
-  else copy_words((unsigned char*)segs.dst[j], (const unsigned char*)segs.src[j], n);
+  if ((a & 15) == 0) copy_words((uint4*)dst, (const uint4*)segs.src[j], n / 16);
+  else if ((a & 7) == 0) copy_words((uint2*)dst, (const uint2*)segs.src[j], n / 8);
+  else if ((a & 3) == 0) copy_words((unsigned*)dst, (const unsigned*)segs.src[j], n / 4);
+  else copy_words((unsigned char*)dst, (const unsigned char*)segs.src[j], n);
+}
+
+__global__ void k_word(unsigned long long* word, unsigned long long value, int advance) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *word = advance ? *word + value : value;
+}
+
+cudaError_t launch_word(unsigned long long* word, unsigned long long value, int advance, cudaStream_t st) {
+  k_word<<<1, 32, 0, st>>>(word, value, advance);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_copy(const CopySegs& segs, cudaStream_t st) {

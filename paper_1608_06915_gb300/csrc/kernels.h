@@ -59,7 +59,9 @@ cudaError_t launch_th_moments(int storage, const PatchDev& p, const void* fin, c
                               void* T, void* gamma, int dtype, const ThermalLevel& L, cudaStream_t st);
 
 // Discrete adjoint kernels (adjoint.cu), FP32/FP64 storage, isothermal.
-// with_bc: the patch has boundary-class nodes (their node-by-node kernel runs too)
+// with_bc: the patch has boundary-class nodes (their node-by-node kernel runs
+// too, and both add into lambda_old, which must be cleared first); without
+// them one kernel writes every entry of lambda_old with plain stores
 cudaError_t launch_adj_sc(int storage, const PatchDev& p, const void* fin, const void* lam_new, void* lam_old,
                           double beta, int odd, int lbgk, bool with_bc, int* status, cudaStream_t st);
 cudaError_t launch_adj_coalesce(int storage, const PatchDev& child, const void* fin_c, const PatchDev& parent,
@@ -148,14 +150,19 @@ cudaError_t launch_copy_pop(int storage, const PatchDev& p, void* fstore, void* 
 // FP64 partial sums of one patch into partial[blocks][8]; see lbm_diagnostics.
 // Device-to-device copies of up to kCopySegs segments in one launch (the
 // copy engines are slower than the SMs for state-sized copies).
+// With rel set, dst[j] holds offsets from the address stored at *rel (a
+// device word), so that a captured graph can copy to a moving destination.
 constexpr int kCopySegs = 16;
 struct CopySegs {
   void* dst[kCopySegs];
   const void* src[kCopySegs];
   size_t bytes[kCopySegs];
   int n;
+  const unsigned long long* rel;
 };
 cudaError_t launch_copy(const CopySegs& segs, cudaStream_t st);
+// *word = value (set) or *word += value (advance), one thread
+cudaError_t launch_word(unsigned long long* word, unsigned long long value, int advance, cudaStream_t st);
 
 // Source patches of a state transfer (regridding): views, current f buffers,
 // levels and betas, and the order in which a destination level tries them.
