@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the full sphere and Rayleigh-Benard lines and the storage sweep")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the adjoint/forward timing of the 64^3 adjoint case (diagnostic line)")
     return ap.parse_args()
@@ -209,7 +211,7 @@ class Clocks:
 def source_hash():
     """Hash of the sources of the stream-collide kernels (profiles record it)."""
     h = hashlib.sha256()
-    for f in ("device.cuh", "sc_tma.cuh", "sc_tma_fp32.cu"):
+    for f in ("device.cuh", "collide.cuh", "sc_tma.cuh", "sc_tma_fp32.cu"):
         with open(os.path.join(ROOT, "paper_1608_06915_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -334,6 +336,83 @@ def adjoint_ratio(dev, storage="fp32", K=20):
                 note="adjoint time includes restoring the checkpoint and recomputing the segment")
 
 
+def measure_workload(name, storage, steps, warmup, dev, pr=0.7, peak=None, instrument=True):
+    """One workload on one GPU: layout, equilibrium init, autotune, warm-up,
+    `steps` coarse steps replayed as graphs (CUDA events on the grid's
+    stream), then the same steps launched kernel by kernel between events for
+    the per-class kernel table and the dominant kernel's roofline.  Returns
+    a dict; frees the grid."""
+    import numpy as np
+    import torch
+    from paper_1608_06915_gb300 import lbm as L
+    case, fields, desc = workload(name, pr)
+    g = L.Grid(case, storage, device=dev)
+    for p, info in enumerate(g.patches):
+        h = fields(info)
+        t = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev) for a in h]
+        g.init_equilibrium(p, t[0], t[1], t[2] if len(t) > 2 else None)
+    nup = g.node_updates()
+    tune = g.autotune(trials=2)
+    g.step(warmup)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(g.stream)
+    g.step(steps)
+    e1.record(g.stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    out = dict(workload=desc, storage=storage, value=nup / (ms / 1e3) / 1e6, unit=UNIT, ms_per_step=ms,
+               steps=steps, node_updates_per_coarse_step=nup, autotune=tune)
+    if instrument:
+        g.timing(True)
+        g.step(steps)
+        torch.cuda.synchronize(dev)
+        report = g.timing_report()
+        g.timing(False)
+        top = max(report, key=lambda r: r["ms"])
+        bpu = BYTES_PER_UPDATE[storage] * (2 if case.get("thermal") else 1)
+        avg_ms = top["ms"] / top["launches"]
+        alg = top["nodes"] / top["launches"] * bpu
+        achieved = alg / (avg_ms / 1e3) / 1e9
+        out["roofline"] = dict(bound="hbm", kernel="%s level %d" % (top["kind"], top["level"]), achieved=achieved,
+                               peak=peak, unit="GB/s", frac=achieved / peak if peak else None,
+                               bytes_per_node_update=bpu, avg_launch_ms=avg_ms)
+        out["kernels"] = [dict(r, avg_us=1e3 * r["ms"] / r["launches"]) for r in report]
+    d = g.diagnostics()
+    out["diagnostics"] = dict(mass=d["mass"], min_rho=d["min_rho"], status=d["status"])
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
+def storage_error(name, storage, dev, steps):
+    """Relative L2 error of the velocity of a storage against FP64 storage on
+    the reduced case of the workload after `steps` coarse steps, both on the
+    GPU (the FP64 path equals the FP64 oracle to 1e-12, which the parity tests
+    check)."""
+    import numpy as np
+    import torch
+    from paper_1608_06915_gb300 import lbm as L
+    case, fields, desc = sample_case(name)
+    res = {}
+    for st in ("fp64", storage):
+        g = L.Grid(case, st, device=dev)
+        for p, info in enumerate(g.patches):
+            h = fields(info)
+            g.init_equilibrium(p, torch.from_numpy(np.ascontiguousarray(h[0])).to(dev),
+                               torch.from_numpy(np.ascontiguousarray(h[1])).to(dev))
+        g.step(steps)
+        us = []
+        for p in range(len(g.patches)):
+            _, u, _, _ = g.moments(p)
+            m = g.mask(p) == 1
+            us.append(u.cpu().numpy()[:, m])
+        res[st] = np.concatenate(us, axis=1)
+        del g
+    ref = res["fp64"]
+    return float(np.sqrt(np.sum((res[storage] - ref) ** 2) / np.sum(ref ** 2)))
+
+
 def cuda_arm(args):
     import numpy as np
     import torch
@@ -434,13 +513,41 @@ def cuda_arm(args):
     if rank == 0 and not args.no_adjoint and args.workload == "channel":
         adj = adjoint_ratio(dev)
 
+    # the other workloads at full size, and the storage sweep (rank 0, after
+    # the timed region; each grid is freed before the next)
+    extras = {}
+    ws = g.device_bytes
+    if rank == 0 and args.workload == "channel" and not args.no_extras:
+        del g
+        torch.cuda.empty_cache()
+        extras["sphere"] = measure_workload("sphere", "fp32", 10, 3, dev, peak=peak)
+        extras["rbc"] = measure_workload("rbc", "fp32", 4, 2, dev, pr=args.pr, peak=peak)
+        sweep = []
+        for name in ("channel", "sphere"):
+            for st in ("fp32", "fp16s", "bf16s"):
+                if name == "channel" and st == args.storage:
+                    r = dict(workload=desc, storage=st, value=value, ms_per_step=1e3 * t / args.steps,
+                             roofline=dict(frac=roofline["frac"], bytes_per_node_update=bpu))
+                elif name == "sphere" and st == "fp32":
+                    r = extras["sphere"]
+                else:
+                    r = measure_workload(name, st, 10, 3, dev, peak=peak)
+                err = storage_error(name, st, dev, 50 if name == "channel" else 20) if st != "fp64" else 0.0
+                sweep.append(dict(workload=name, storage=st, mlups=r["value"], ms_per_step=r["ms_per_step"],
+                                  roofline_frac=r["roofline"]["frac"],
+                                  bytes_per_node_update=r["roofline"]["bytes_per_node_update"],
+                                  u_rel_l2_vs_fp64=err))
+        extras["storage_sweep"] = dict(
+            rows=sweep, note="MLUPS and the dominant kernel's HBM fraction at the storage's bytes per node update; "
+                             "u_rel_l2_vs_fp64: velocity error against FP64 storage on the reduced case (channel "
+                             "16x64x8, 50 coarse steps; sphere 48x24x24, 20 coarse steps), both on the GPU")
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         r = oracle_run(args.workload, seconds=15.0)
         cpu = dict(value=r["value"], unit=UNIT, cores=r["cores"], kind="oracle", sample=r["sample"])
 
     if rank == 0:
-        ws = g.device_bytes
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=1e3 * t / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                     dtype=DTYPE[args.storage], data="synthetic",
@@ -451,7 +558,7 @@ def cuda_arm(args):
                                 direct_launch_ms_per_step=1e3 * t_instr / args.steps,
                                 l2="no flush: working set %.2f GB > %.0f MB L2" % (ws / 1e9, L2_BYTES / 1e6)),
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clk,
-                    adjoint_forward_ratio=adj, gamma_indicator=indicator,
+                    adjoint_forward_ratio=adj, gamma_indicator=indicator, **extras,
                     uniform_fine_equivalent=dict(
                         value=uniform_equiv, unit=UNIT,
                         note="node updates of a uniform grid at the finest spacing (%d levels) per coarse step, "
