@@ -57,6 +57,13 @@
 //       read consistently with R7, where the same Grad form with P^eq is
 //       f^eq itself); the same tensor P1 enters g* (Table I row g*).
 //
+//   R10 curved solid surfaces (the heated sphere of Sec. IV): an analytic
+//       sphere, cylinder or plane gives the fraction q of each solid link at
+//       which the wall lies; the population returning from it is interpolated
+//       linearly along the link (Bouzidi, Firdaouss & Lallemand 2001) -- for g
+//       of an isothermal surface the same construction on the anti-bounce-back
+//       rule -- and the drag takes the returning value; q = 1/2 without a
+//       surface (half-way bounce-back, the staircase of the solid mask).
 // Parity status: every function above is pinned by tests under tests/
 // (closed forms, invariants, special cases, brute force, a two-level run
 // against a uniform run at the fine spacing, and the Chapman-Enskog state of
@@ -472,6 +479,15 @@ struct Desc {
   double wall_T[6];
   double solid_T;            // thermal: temperature of solid surfaces
   int32_t solid_isothermal;  // thermal: 1 = solid surfaces held at solid_T, 0 = adiabatic
+  // curved solid surface (reading R10): 0 none (half-way, staircase), 1 sphere,
+  // 2 cylinder along shape_axis, 3 plane normal to shape_axis; centre (a point
+  // of the plane) and radius in coarse units; shape_solid_inside: the solid
+  // is inside the sphere or cylinder (below the plane), else outside (above)
+  int32_t shape_kind;
+  double shape_c[3];
+  double shape_r;
+  int32_t shape_axis;
+  int32_t shape_solid_inside;
 };
 
 struct Patch {
@@ -848,6 +864,82 @@ struct Sim {
     }
   }
 
+  // ---- curved solid surfaces (reading R10) ----------------------------------
+  // Fraction q in (0, 1] of the link from node X (level lev) along c_k at which
+  // it enters the solid side of the analytic surface: the root of
+  // |P + t D - C|^2 = R^2 (sphere; cylinder without the axis component) or of
+  // P_a + t D_a = C_a (plane), P = X h, D = c_k h, h = 2^-lev.  Without a
+  // surface, or without a root in (0, 1], q = 1/2: half-way bounce-back.
+  double wall_q(int lev, const long X[3], int k) const {
+    if (d.shape_kind == 0) return 0.5;
+    const double h = 1.0 / (double)(1L << lev);
+    double P[3], D[3];
+    for (int a = 0; a < 3; ++a) {
+      P[a] = (double)X[a] * h;
+      D[a] = (double)cvel(k, a) * h;
+    }
+    double t = -1.0;
+    if (d.shape_kind == 3) {
+      const int a = d.shape_axis;
+      if (D[a] != 0.0) t = (d.shape_c[a] - P[a]) / D[a];
+    } else {
+      double A = 0, B = 0, C = -d.shape_r * d.shape_r;
+      for (int a = 0; a < 3; ++a) {
+        if (d.shape_kind == 2 && a == d.shape_axis) continue;
+        const double pc = P[a] - d.shape_c[a];
+        A += D[a] * D[a];
+        B += 2.0 * D[a] * pc;
+        C += pc * pc;
+      }
+      const double disc = B * B - 4.0 * A * C;
+      if (A > 0.0 && disc >= 0.0) {
+        // entering the body from outside: the first root; leaving a cavity: the second
+        const double sq = std::sqrt(disc);
+        t = d.shape_solid_inside ? (-B - sq) / (2.0 * A) : (-B + sq) / (2.0 * A);
+      }
+    }
+    return (t > 0.0 && t <= 1.0) ? t : 0.5;
+  }
+
+  // Population i arriving at fluid node m (coordinates X) from a solid
+  // neighbour X - c_i, from the post-collision state (reading R10): with the
+  // wall at fraction q of the link from X along c_ib (ib the opposite of i),
+  // follow the particle that leaves along c_ib and returns along c_i within
+  // one step, and interpolate linearly along the link (Bouzidi, Firdaouss &
+  // Lallemand 2001):
+  //   q < 1/2: it left from X - (1 - 2q) c_ib, between X and the fluid node
+  //            X + c_i behind:  a = 2q a'(X) + (1 - 2q) a'(X + c_i), along ib;
+  //   q >= 1/2: it lands at X + (2q - 1) c_ib; with the population along i
+  //            that X sends to X + c_i:
+  //            f_i(X) = (1/(2q)) a + ((2q - 1)/(2q)) f'_i(X),  a = f'_ib(X);
+  // where a is the reflected value: f'_ib for bounce-back, -g'_ib + w for the
+  // anti-bounce-back of a surface at a fixed temperature (w the wall term).
+  // q = 1/2 is half-way bounce-back; without a usable node behind, q < 1/2
+  // falls back to it.
+  double incoming(const Patch& p, long m, const long X[3], int i, double q, const std::vector<Pop>& post,
+                  bool anti, double w) const {
+    const int ib = opposite(i);
+    if (q < 0.5) {
+      long Bk[3];
+      for (int a = 0; a < 3; ++a) Bk[a] = X[a] + cvel(i, a);
+      bool in = true;
+      for (int a = 0; a < 3; ++a)
+        if (!periodic(a) && (Bk[a] < 0 || Bk[a] > maxc(p.level, a))) in = false;
+      long b = -1;
+      if (in) {
+        wrap(p.level, Bk);
+        b = index_of(p, Bk);
+      }
+      if (b >= 0 && !p.solid[b] && p.vpost[b]) {
+        const double mix = 2.0 * q * post[m][ib] + (1.0 - 2.0 * q) * post[b][ib];
+        return anti ? -mix + w : mix;
+      }
+      return anti ? -post[m][ib] + w : post[m][ib];
+    }
+    const double a = anti ? -post[m][ib] + w : post[m][ib];
+    return a / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * post[m][i];
+  }
+
   // ---- streaming (left-hand side of Eq. f_equations) ----------------------
   // pre(X)_i = post(X - c_i)_i, with the boundary rules of reading R6.
   void stream(Patch& p) {
@@ -891,7 +983,10 @@ struct Sim {
         }
         if (bounce) {
           if (!p.vpost[m]) { ok = false; break; }
-          p.pre[m][i] = p.post[m][opposite(i)];
+          // domain walls: half-way; solid surfaces: at the fraction q of the
+          // analytic surface (half-way without one)
+          const double q = solid_wall ? wall_q(lev, X, opposite(i)) : 0.5;
+          p.pre[m][i] = incoming(p, m, X, i, q, p.post, false, 0.0);
           if (thermal) {
             if (wall_axis >= 0 || (solid_wall && d.solid_isothermal)) {
               // anti-bounce-back to the wall equilibrium at rest, temperature
@@ -902,9 +997,9 @@ struct Sim {
               double zero[3] = {0, 0, 0};
               double E2 = rho * 3.0 * Tw;  // 2 rho E with u = 0
               Pop gw = geq(rho, zero, E2, d.t0);
-              p.gpre[m][i] = -p.gpost[m][opposite(i)] + gw[i] + gw[opposite(i)];
+              p.gpre[m][i] = incoming(p, m, X, i, q, p.gpost, true, gw[i] + gw[opposite(i)]);
             } else {
-              p.gpre[m][i] = p.gpost[m][opposite(i)];
+              p.gpre[m][i] = incoming(p, m, X, i, q, p.gpost, false, 0.0);
             }
           }
           continue;
@@ -1110,11 +1205,13 @@ struct Sim {
   }
 
   // Drag F_d of Sec. IV A 2 (flow past a sphere), read as the momentum-exchange
-  // force of half-way bounce-back: a post-collision population f'_j at a fluid
-  // node x whose neighbour x + c_j is solid returns as f_{-j}(x), handing the
-  // solid 2 c_j f'_j per substep.  Coarse units: a level-l node carries
-  // 8^-l of a coarse volume and a level-l substep lasts 2^-l of a coarse step,
-  // so each link counts 2 c_j f'_j 4^-l.  Evaluated on the current
+  // force of the solid links: a post-collision population f'_j at a fluid
+  // node x whose neighbour x + c_j is solid leaves along c_j and f_{-j}(x) of
+  // the next pull arrives back (half-way bounce-back: f'_j itself, so 2 c_j
+  // f'_j; curved surfaces: the interpolated value of reading R10), handing
+  // the solid c_j (f'_j + f_{-j}) per substep.  Coarse units: a level-l node
+  // carries 8^-l of a coarse volume and a level-l substep lasts 2^-l of a
+  // coarse step, so each link counts 4^-l.  Evaluated on the current
   // post-collision state (what the next substep streams).
   void drag(double F[3]) const {
     F[0] = F[1] = F[2] = 0;
@@ -1134,7 +1231,9 @@ struct Sim {
           if (!inside) continue;
           wrap(p.level, S);
           if (!solid_at(p.level, S)) continue;
-          for (int a = 0; a < 3; ++a) F[a] += 2.0 * cvel(j, a) * p.post[m][j] * scale;
+          const int i = opposite(j);
+          const double back = incoming(p, m, X, i, wall_q(p.level, X, j), p.post, false, 0.0);
+          for (int a = 0; a < 3; ++a) F[a] += (double)cvel(j, a) * (p.post[m][j] + back) * scale;
         }
       }
     }
@@ -1185,6 +1284,11 @@ typedef struct {
   double wall_T[6];
   double solid_T;
   int32_t solid_isothermal;
+  int32_t shape_kind;
+  double shape_c[3];
+  double shape_r;
+  int32_t shape_axis;
+  int32_t shape_solid_inside;
 } orc_desc;
 
 static std::string g_last_error;
@@ -1250,6 +1354,11 @@ void* orc_create(const orc_desc* cd) {
     std::memcpy(d.wall_T, cd->wall_T, sizeof d.wall_T);
     d.solid_T = cd->solid_T;
     d.solid_isothermal = cd->solid_isothermal;
+    d.shape_kind = cd->shape_kind;
+    std::memcpy(d.shape_c, cd->shape_c, sizeof d.shape_c);
+    d.shape_r = cd->shape_r;
+    d.shape_axis = cd->shape_axis;
+    d.shape_solid_inside = cd->shape_solid_inside;
     try {
       s->build(d);
     } catch (...) {

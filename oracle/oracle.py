@@ -61,6 +61,11 @@ class OrcDesc(ctypes.Structure):
         ("wall_T", ctypes.c_double * 6),
         ("solid_T", ctypes.c_double),
         ("solid_isothermal", ctypes.c_int32),
+        ("shape_kind", ctypes.c_int32),
+        ("shape_c", ctypes.c_double * 3),
+        ("shape_r", ctypes.c_double),
+        ("shape_axis", ctypes.c_int32),
+        ("shape_solid_inside", ctypes.c_int32),
     ]
 
 
@@ -194,9 +199,11 @@ class Oracle:
     -x,+x,-y,+y,-z,+z), ``inflow_axis``, ``u_in``, ``boxes`` (list of
     ``(level, lo, hi)`` in coarse units), ``solid`` (None or dict with
     ``level``, ``lo`` and a uint8 ``mask`` indexed [z][y][x]), ``nu0``,
-    ``accel0``, ``mirror_lbgk`` and ``thermal`` (None or dict with ``pr``,
+    ``accel0``, ``mirror_lbgk``, ``thermal`` (None or dict with ``pr``,
     ``t0``, ``glambda``, ``t_ref``, ``wall_T`` and, for isothermal solid
-    surfaces, ``solid_T``).
+    surfaces, ``solid_T``) and ``wall_shape`` (None or dict with ``kind``
+    sphere / cylinder / plane, ``c``, ``r``, ``axis``, ``solid_inside``: the
+    analytic solid surface of curved walls, coarse units).
     """
 
     def __init__(self, case: dict):
@@ -225,6 +232,13 @@ class Oracle:
             d.solid_dims[:] = [int(self._solid.shape[2]), int(self._solid.shape[1]), int(self._solid.shape[0])]
         else:
             d.solid_level = -1
+        shape = case.get("wall_shape")
+        if shape is not None:  # curved solid surface (reading R10)
+            d.shape_kind = {"sphere": 1, "cylinder": 2, "plane": 3}[shape["kind"]]
+            d.shape_c[:] = [float(v) for v in shape["c"]]
+            d.shape_r = float(shape.get("r", 0.0))
+            d.shape_axis = int(shape.get("axis", 0))
+            d.shape_solid_inside = int(bool(shape.get("solid_inside", True)))
         d.nu0 = float(case["nu0"])
         d.accel0[:] = [float(v) for v in case.get("accel0", (0, 0, 0))]
         d.mirror_lbgk = int(bool(case.get("mirror_lbgk", False)))

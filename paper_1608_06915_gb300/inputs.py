@@ -167,6 +167,44 @@ def heated_slab_profile(case: dict, z):
     return th["solid_T"] + (th["wall_T"][5] - th["solid_T"]) * (z - case["z_lo"]) / (case["z_hi"] - case["z_lo"])
 
 
+def pipe_case(R: float = 10.0, nu: float = 0.1, u_max: float = 0.01, curved: bool = True, nz: int = 4) -> dict:
+    """Flow through a circular pipe along z driven by a body force: periodic
+    box of 2R + 4 nodes across, solid outside the radius R about the box
+    centre (the mask holds the nodes at r >= R; with ``curved`` the cylinder
+    itself is the analytic surface of the wall).  The force gives a centreline
+    velocity u_max: a = 4 nu u_max / R^2."""
+    n = int(2 * R + 4)
+    c = (n - 1) / 2.0
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(n), np.arange(n), indexing="ij")
+    mask = (((x - c) ** 2 + (y - c) ** 2) >= R * R).astype(np.uint8)
+    case = dict(name="pipe", n=(n, n, nz), periodic=(1, 1, 1), walls=(0,) * 6, inflow_axis=-1, u_in=(0, 0, 0),
+                boxes=[], solid=dict(level=0, lo=(0, 0, 0), mask=mask), nu0=nu,
+                accel0=(0, 0, 4.0 * nu * u_max / (R * R)), mirror_lbgk=False, thermal=None, radius=R, centre=c)
+    if curved:
+        case["wall_shape"] = dict(kind="cylinder", c=(c, c, 0.0), r=R, axis=2, solid_inside=False)
+    return case
+
+
+def offset_slab_case(z_s: float, n=(4, 4, 16), curved: bool = True, pr: float = 0.7, nu0: float = 0.05,
+                     dT: float = 0.01) -> dict:
+    """Conduction between an isothermal solid (the nodes below z_s, held at
+    T0 + dT/2) and the cold top plate (T0 - dT/2, half a spacing above the last
+    node), no buoyancy.  The solid surface is the plane z = z_s, anywhere
+    between two node layers; with ``curved`` it is the analytic surface of the
+    wall, else the mask's staircase (half a spacing above its top layer)."""
+    nx, ny, nz = n
+    top = int(math.floor(z_s))
+    mask = np.ones((top + 1, ny, nx), dtype=np.uint8)
+    th = dict(pr=pr, t0=T0, glambda=0.0, t_ref=T0, dT=dT,
+              wall_T=(0, 0, 0, 0, T0 - dT, T0 - dT / 2), solid_T=T0 + dT / 2)
+    case = dict(name="offset_slab", n=n, periodic=(1, 1, 0), walls=(0, 0, 0, 0, 1, 1), inflow_axis=-1,
+                u_in=(0, 0, 0), boxes=[], solid=dict(level=0, lo=(0, 0, 0), mask=mask), nu0=nu0, accel0=(0, 0, 0),
+                mirror_lbgk=False, thermal=th, z_lo=z_s, z_hi=nz - 0.5)
+    if curved:
+        case["wall_shape"] = dict(kind="plane", c=(0.0, 0.0, z_s), axis=2, solid_inside=True)
+    return case
+
+
 # ---------------------------------------------------------------------------
 # initial fields, evaluated at node positions given in coarse units
 

@@ -479,6 +479,57 @@ def test_thermal_rescaling_carries_the_chapman_enskog_state_of_a_shear_flow(pr):
     assert np.max(np.abs(gneq)) * abs(ratio_f - ratio_g) > 1e3 * 1e-16
 
 
+# --- curved solid surfaces (reading R10: the linear interpolation of Bouzidi,
+# Firdaouss & Lallemand along each solid link).  Flow through a circular pipe
+# (Hagen-Poiseuille, u_z = a (R^2 - r^2) / (4 nu)) converges at second order in
+# the radius with the interpolated wall; the staircase of half-way bounce-back
+# on the same mask is several times worse and about first order.
+def _pipe_error(R, curved):
+    case = I.pipe_case(R=R, curved=curved)
+    nu, a, c = case["nu0"], case["accel0"][2], case["centre"]
+    o = O.Oracle(case)
+    x, y, z = I.node_positions(0, o.patches[0]["org"], o.patches[0]["dim"])
+    r2 = (x - c) ** 2 + (y - c) ** 2
+    exact = np.where(r2 < R * R, a * (R * R - r2) / (4.0 * nu), 0.0)
+    o.init_equilibrium(0, np.ones_like(x), np.stack([0 * x, 0 * x, exact]))
+    o.step(int(4 * R * R / nu))  # four viscous times of the pipe
+    _, u, _, _ = o.moments(0)
+    m = o.mask(0) == 1
+    return math.sqrt(np.mean((u[2][m] - exact[m]) ** 2) / np.mean(exact[m] ** 2))
+
+
+def test_curved_wall_pipe_flow_converges_at_second_order():
+    # measured: R = 5 -> 1.9e-2, R = 10 -> 4.4e-3 (ratio 4.2); staircase 5.7e-2, 3.4e-2
+    coarse, fine = _pipe_error(5, True), _pipe_error(10, True)
+    stair = _pipe_error(10, False)
+    assert fine < 6e-3, fine
+    assert coarse / fine > 3.0, (coarse, fine)
+    assert fine < stair / 5.0, (fine, stair)
+
+
+# --- an isothermal surface between two node layers (reading R10 on the
+# anti-bounce-back of g): steady conduction to the cold plate is the linear
+# profile from the true surface position, which the interpolation reproduces
+# exactly (1e-8 after 3000 steps, both q < 1/2 and q > 1/2); the staircase
+# puts the surface half a spacing above the mask's top layer (2% off)
+@pytest.mark.parametrize("z_s", [2.2, 2.8])
+def test_curved_isothermal_surface_gives_the_exact_conduction_profile(z_s):
+    def run(curved):
+        case = I.offset_slab_case(z_s, curved=curved)
+        th = case["thermal"]
+        o = O.Oracle(case)
+        x, y, z = I.node_positions(0, o.patches[0]["org"], o.patches[0]["dim"])
+        o.init_equilibrium(0, np.ones_like(x), np.zeros((3,) + x.shape), np.full(x.shape, th["t0"]))
+        o.step(3000)
+        _, _, T, _ = o.moments(0)
+        m = o.mask(0) == 1
+        exact = th["solid_T"] + (th["wall_T"][5] - th["solid_T"]) * (z - case["z_lo"]) / (case["z_hi"] - case["z_lo"])
+        return np.abs(T[m] - exact[m]).max() / th["dT"]
+
+    assert run(True) < 1e-6
+    assert run(False) > 1e-2  # the staircase wall sits elsewhere
+
+
 # --- layout: node counts of the two-level Taylor-Green case (32^3 with the
 # box [8,24]^3: 32^3 - 13^3 coarse nodes and 33^3 fine nodes)
 def test_tgv_layout_counts():
