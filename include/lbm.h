@@ -109,6 +109,24 @@ typedef struct {
   int32_t solid_isothermal; /* thermal: 1 = solid surfaces held at solid_T (anti-bounce-back
                                of g, as at the plates; the heated sphere of Sec. IV),
                                0 = adiabatic solids (bounce-back of g) */
+  /* Curved solid surface (the sphere of Sec. IV; the paper's own wall
+   * condition is Grad's, whose definition it cites elsewhere): with
+   * shape_kind 0 the solid mask's links reflect half-way (a staircase);
+   * otherwise the analytic surface -- 1 sphere (centre shape_c, radius
+   * shape_r), 2 cylinder along axis shape_axis, 3 plane normal to shape_axis
+   * through shape_c; coarse units -- gives, on every link from a fluid node to
+   * a solid node of solid_level, the fraction q of the link at which the wall
+   * lies, and the returning populations are interpolated linearly along the
+   * link (Bouzidi, Firdaouss & Lallemand 2001: f; the same construction on
+   * the anti-bounce-back of g at an isothermal surface).  shape_solid_inside:
+   * the solid is inside the sphere or cylinder (on the lower side of the
+   * plane), else outside.  A link the surface does not cross in (0, 1]
+   * reflects half-way. */
+  int32_t shape_kind;
+  double shape_c[3];
+  double shape_r;
+  int32_t shape_axis;
+  int32_t shape_solid_inside;
 } lbm_desc;
 
 /* Builds the level/patch layout, node classes and interface tables

@@ -175,6 +175,8 @@ lbmk::PatchDev view(const lbm_grid* g, const HostPatch& p) {
   v.walls = g->hg.desc.walls;
   v.inflow = g->hg.desc.inflow_axis;
   v.type = g->base + p.off_type;
+  v.wq_idx = p.wq_idx.empty() ? nullptr : reinterpret_cast<const int32_t*>(g->base + p.off_wq_idx);
+  v.wq = p.wq.empty() ? nullptr : reinterpret_cast<const double*>(g->base + p.off_wq);
   return v;
 }
 
@@ -628,6 +630,8 @@ lbm_status lbm_grid_bind(lbm_grid_t g, void* dev_ptr, size_t bytes, void* cuda_s
     if (!e) e = up(p.off_cf_child, p.cf_child.data(), 4 * p.cf_child.size());
     if (!e) e = up(p.off_drag_node, p.drag_node.data(), 4 * p.drag_node.size());
     if (!e) e = up(p.off_drag_mask, p.drag_mask.data(), 4 * p.drag_mask.size());
+    if (!e) e = up(p.off_wq, p.wq.data(), 8 * p.wq.size());
+    if (!e) e = up(p.off_wq_idx, p.wq_idx.data(), 4 * p.wq_idx.size());
     for (int k = 0; k < 2; ++k)
       if (!e) e = up(p.off_tiles_pure[k], p.tiles_pure[k].data(), 8 * p.tiles_pure[k].size());
     for (int k = 0; k < 2; ++k) {
@@ -1600,7 +1604,7 @@ lbm_status lbm_force(lbm_grid_t g, const double* accel0, double* drag_out) {
   for (auto& p : g->hg.P) {
     if (p.drag_node.empty()) continue;
     if (!e)
-      e = lbmk::launch_drag(g->hg.desc.storage, g->base + p.off_f[p.cur], p.plane, at<uint32_t>(g, p.off_drag_node),
+      e = lbmk::launch_drag(g->hg.desc.storage, view(g, p), g->base + p.off_f[p.cur], at<uint32_t>(g, p.off_drag_node),
                             at<uint32_t>(g, p.off_drag_mask), (int64_t)p.drag_node.size(),
                             1.0 / (double)(1LL << (2 * p.level)), partial + 3 * nb, kDiagBlocks, g->stream);
     nb += kDiagBlocks;

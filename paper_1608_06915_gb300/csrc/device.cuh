@@ -76,6 +76,10 @@ struct PatchDev {
   unsigned walls;
   int inflow;
   const uint8_t* type;
+  // curved solid surface (null without one): wq_idx over the storage box, and
+  // wq[27 k + j] the wall fraction of the link along c_j of node k
+  const int32_t* wq_idx;
+  const double* wq;
 };
 
 __device__ __forceinline__ long long node_index(const PatchDev& p, int x, int y, int z) {
@@ -262,7 +266,54 @@ __device__ __forceinline__ void pull_bulk(const PatchDev& p, const S* __restrict
   });
 }
 
-// Generic path: walls (half-way bounce-back), solid nodes (bounce-back),
+// Population i returning to node own (coordinates X) from a solid neighbour
+// X - c_i, with the wall at fraction q of the link from X along c_ib
+// (ib = 26 - i): the particle that leaves along c_ib and comes back along c_i
+// within one step, interpolated linearly along the link (Bouzidi, Firdaouss
+// & Lallemand 2001).  For q < 1/2 it left from between X and the fluid node
+// X + c_i behind it: 2q a'(X) + (1 - 2q) a'(X + c_i) along ib; for q >= 1/2 it
+// lands between X and the wall and X takes (1/(2q)) a + ((2q - 1)/(2q)) a'_i(X)
+// with a the reflected value.  a is a'_ib (bounce-back) or, with anti,
+// -a'_ib + w (anti-bounce-back of an isothermal surface, w its wall term).  A
+// missing node behind gives half-way bounce-back.  arr holds deviations from
+// a weight that is the same for i and ib, and the weights of each formula
+// sum to one, so deviations map to deviations.
+template <int i, typename S, typename R>
+__device__ __forceinline__ R returning(const PatchDev& p, const S* __restrict__ arr, long long own, const int X[3],
+                                       R q, bool anti, R w) {
+  constexpr int ib = 26 - i;
+  constexpr int c[3] = {CX(i), CY(i), CZ(i)};
+  const R own_ib = Stor<S>::ld(arr + (long long)ib * p.plane + own);
+  if (q < R(0.5)) {
+    int b[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      b[a] = X[a] + c[a];
+      if (b[a] < 0 || b[a] >= p.dim[a]) {
+        if (p.span[a]) b[a] += b[a] < 0 ? p.dim[a] : -p.dim[a];
+        else ok = false;
+      }
+    }
+    long long bi = 0;
+    if (ok) {
+      bi = node_index(p, b[0], b[1], b[2]);
+      const uint8_t t = p.type[bi];
+      ok = t != T_SOLID && t != T_SKIP;
+    }
+    if (ok) {
+      const R mix = R(2) * q * own_ib + (R(1) - R(2) * q) * Stor<S>::ld(arr + (long long)ib * p.plane + bi);
+      return anti ? w - mix : mix;
+    }
+    return anti ? w - own_ib : own_ib;
+  }
+  const R a = anti ? w - own_ib : own_ib;
+  const R i2q = R(1) / (R(2) * q);
+  return a * i2q + (R(2) * q - R(1)) * i2q * Stor<S>::ld(arr + (long long)i * p.plane + own);
+}
+
+// Generic path: walls (half-way bounce-back), solid nodes (bounce-back,
+// interpolated along the link at a curved surface),
 // outlet (source clamped to the last node), periodic wrap on spanned axes.
 // A source that resolves to no node sets bit 0 of *status and falls back to
 // bounce-back (never produced by a validated layout).
@@ -271,6 +322,7 @@ __device__ __forceinline__ void pull_generic(const PatchDev& p, const S* __restr
                                              R (&f)[27], int* status) {
   const long long own = node_index(p, x, y, z);
   const int X[3] = {x, y, z};
+  const int wk = p.wq_idx ? p.wq_idx[own] : -1;  // this node's row of wall fractions
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr int c[3] = {CX(i), CY(i), CZ(i)};
@@ -300,17 +352,19 @@ __device__ __forceinline__ void pull_generic(const PatchDev& p, const S* __restr
       }
     }
     long long src = own;
+    bool solid = false;
     if (!bounce && !bad) {
       src = node_index(p, s[0], s[1], s[2]);
       const uint8_t t = p.type[src];
-      if (t == T_SOLID) bounce = true;
+      if (t == T_SOLID) bounce = solid = true;
       else if (t == T_SKIP) bad = true;
     }
     if (bad) {
       atomicOr(status, 1);
       bounce = true;
     }
-    if (bounce) f[i] = Stor<S>::ld(fin + (long long)(26 - i) * p.plane + own);
+    if (solid && wk >= 0) f[i] = returning<i, S, R>(p, fin, own, X, R(p.wq[27 * wk + 26 - i]), false, R(0));
+    else if (bounce) f[i] = Stor<S>::ld(fin + (long long)(26 - i) * p.plane + own);
     else f[i] = Stor<S>::ld(fin + (long long)i * p.plane + src);
   });
 }

@@ -76,13 +76,19 @@ struct HostPatch {
   std::vector<uint32_t> cf_child;   // coalesce: coinciding child node
   // momentum exchange: fluid nodes next to a solid node, bit j set when x + c_j is solid
   std::vector<uint32_t> drag_node, drag_mask;
+  // curved solid surface: per drag node k, wq[27 k + j] the fraction of the
+  // link along c_j at which the wall lies (1/2 on other links); wq_idx over
+  // the storage box gives k, -1 for nodes without solid links.  Empty without
+  // an analytic surface.
+  std::vector<double> wq;
+  std::vector<int32_t> wq_idx;
 
   // device placement (byte offsets into the bound buffer)
   size_t off_f[2]{}, off_g[2]{}, off_type = 0;
   size_t off_tiles_pure[2]{}, off_tiles_mixed[2]{}, off_tiles_all[2]{}, off_fix_nodes[2]{};
   size_t off_ex_node = 0, off_ex_src = 0, off_pt_src = 0;
   size_t off_smp_node = 0, off_smp_kind = 0, off_smp_val = 0, off_cf_parent = 0, off_cf_child = 0;
-  size_t off_drag_node = 0, off_drag_mask = 0;
+  size_t off_drag_node = 0, off_drag_mask = 0, off_wq = 0, off_wq_idx = 0;
   int cur = 0;  // which population buffer holds the current state
   size_t n_points() const { return smp_node.size() + n_pt[0] + n_pt[1]; }
 };

@@ -721,21 +721,28 @@ cudaError_t launch_diag_final(const double* partial, int total_blocks, double* o
 // from a fluid node x to a solid neighbour x + c_j hands the solid 2 c_j f'_j(x)
 // per substep; scale = 4^-level converts to coarse units.  FP64 per-block sums.
 template <typename S>
-__global__ void __launch_bounds__(256) k_drag(const S* __restrict__ fin, long long plane,
+__global__ void __launch_bounds__(256) k_drag(PatchDev p, const S* __restrict__ fin,
                                               const uint32_t* __restrict__ node, const uint32_t* __restrict__ mask,
                                               long long n, double scale, double* __restrict__ partial) {
+  const long long plane = p.plane;
   double acc[3] = {0, 0, 0};
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     const uint32_t m = mask[k];
     const long long nd = node[k];
+    const int X[3] = {(int)(nd % p.nxp), (int)((nd / p.nxp) % p.dim[1]), (int)(nd / ((long long)p.nxp * p.dim[1]))};
     unroll<27>([&](auto J) {
       constexpr int j = decltype(J)::value;
       if ((m >> j) & 1u) {
-        const double f = WI(j) + (double)Stor<S>::ld(fin + (long long)j * plane + nd);
-        if constexpr (CX(j) != 0) acc[0] += 2.0 * CX(j) * f;
-        if constexpr (CY(j) != 0) acc[1] += 2.0 * CY(j) * f;
-        if constexpr (CZ(j) != 0) acc[2] += 2.0 * CZ(j) * f;
+        // f'_j leaves along c_j, f_{-j} of the next pull comes back: c_j (f'_j + f_{-j})
+        const double out = WI(j) + (double)Stor<S>::ld(fin + (long long)j * plane + nd);
+        const double back = p.wq ? WI(j) + (double)returning<26 - j, S, double>(p, fin, nd, X, p.wq[27 * k + j],
+                                                                                 false, 0.0)
+                                 : out;
+        const double f = out + back;
+        if constexpr (CX(j) != 0) acc[0] += CX(j) * f;
+        if constexpr (CY(j) != 0) acc[1] += CY(j) * f;
+        if constexpr (CZ(j) != 0) acc[2] += CZ(j) * f;
       }
     });
   }
@@ -760,11 +767,11 @@ __global__ void k_drag_final(const double* __restrict__ partial, int nb, double*
   out[threadIdx.x] = t;
 }
 
-cudaError_t launch_drag(int storage, const void* fin, int64_t plane, const uint32_t* node, const uint32_t* mask,
+cudaError_t launch_drag(int storage, const PatchDev& p, const void* fin, const uint32_t* node, const uint32_t* mask,
                         int64_t n, double scale, double* partial, int blocks, cudaStream_t st) {
   return dispatch(storage, [&](auto ts, auto) {
     using S = typename decltype(ts)::type;
-    k_drag<S><<<blocks, 256, 0, st>>>((const S*)fin, plane, node, mask, n, scale, partial);
+    k_drag<S><<<blocks, 256, 0, st>>>(p, (const S*)fin, node, mask, n, scale, partial);
     return cudaGetLastError();
   });
 }

@@ -187,8 +187,9 @@ cudaError_t launch_diag(int storage, const PatchDev& p, const void* fin, double 
 cudaError_t launch_diag_final(const double* partial, int total_blocks, double* out8, cudaStream_t st);
 // clears the given bits of the device status word (one atomic)
 cudaError_t launch_status_clear(int* status, int bits, cudaStream_t st);
-// momentum-exchange force: per-block FP64 sums [blocks][3] of 2 c_j f'_j * scale over the links
-cudaError_t launch_drag(int storage, const void* fin, int64_t plane, const uint32_t* node, const uint32_t* mask,
+// momentum-exchange force: per-block FP64 sums [blocks][3] of c_j (f'_j + f_{-j}) * scale over the links, the
+// returning f_{-j} = f'_j at a half-way wall and interpolated along the link where p carries wall fractions
+cudaError_t launch_drag(int storage, const PatchDev& p, const void* fin, const uint32_t* node, const uint32_t* mask,
                         int64_t n, double scale, double* partial, int blocks, cudaStream_t st);
 cudaError_t launch_drag_final(const double* partial, int total_blocks, double* out3, cudaStream_t st);
 

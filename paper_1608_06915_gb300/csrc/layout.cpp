@@ -29,6 +29,40 @@ constexpr int64_t kHi = INT64_MAX / 4;
 
 inline int cvel(int i, int a) { return (a == 0 ? i % 3 : a == 1 ? (i / 3) % 3 : i / 9) - 1; }
 
+// Fraction q in (0, 1] of the link from node X (level lev) along c_j at which
+// it crosses into the solid side of the descriptor's analytic surface (the
+// first crossing into a body, the way out of a cavity); 1/2 when the surface
+// does not cross the link there.  Positions in coarse units: X 2^-lev.
+double wall_fraction(const lbm_desc& d, int lev, const int64_t X[3], int j) {
+  const double h = std::ldexp(1.0, -lev);
+  double from[3], step[3];
+  for (int a = 0; a < 3; ++a) {
+    from[a] = (double)X[a] * h;
+    step[a] = (double)cvel(j, a) * h;
+  }
+  double t = -1.0;
+  if (d.shape_kind == 3) {
+    const int a = d.shape_axis;
+    if (step[a] != 0.0) t = (d.shape_c[a] - from[a]) / step[a];
+  } else if (d.shape_kind == 1 || d.shape_kind == 2) {
+    // |from + t step - c|^2 = r^2 over the axes of the shape
+    double qa = 0.0, qb = 0.0, qc = -d.shape_r * d.shape_r;
+    for (int a = 0; a < 3; ++a) {
+      if (d.shape_kind == 2 && a == d.shape_axis) continue;
+      const double rel = from[a] - d.shape_c[a];
+      qa += step[a] * step[a];
+      qb += 2.0 * step[a] * rel;
+      qc += rel * rel;
+    }
+    const double disc = qb * qb - 4.0 * qa * qc;
+    if (qa > 0.0 && disc >= 0.0) {
+      const double root = std::sqrt(disc);
+      t = (d.shape_solid_inside ? -qb - root : -qb + root) / (2.0 * qa);
+    }
+  }
+  return (t > 0.0 && t <= 1.0) ? t : 0.5;
+}
+
 struct Geo {
   HostGrid& g;
 
@@ -550,6 +584,19 @@ std::string build_layout(HostGrid& g) {
         p.drag_mask.push_back(m);
       }
     }
+    // curved surface: the wall fraction of every solid link of the drag nodes
+    p.wq.clear();
+    p.wq_idx.clear();
+    if (g.desc.shape_kind != 0 && !p.drag_node.empty()) {
+      p.wq_idx.assign((size_t)p.plane, -1);
+      p.wq.assign(27 * p.drag_node.size(), 0.5);
+      for (size_t k = 0; k < p.drag_node.size(); ++k) {
+        p.wq_idx[p.drag_node[k]] = (int32_t)k;
+        geo.coords(p, p.drag_node[k], X);
+        for (int j = 0; j < 27; ++j)
+          if ((p.drag_mask[k] >> j) & 1u) p.wq[27 * k + j] = wall_fraction(g.desc, p.level, X, j);
+      }
+    }
   }
   // interface tables, stored on the child
   for (size_t ci = 1; ci < g.P.size(); ++ci) {
@@ -806,6 +853,8 @@ size_t plan_memory(HostGrid& g) {
     p.off_cf_child = take(4 * p.cf_child.size());
     p.off_drag_node = take(4 * p.drag_node.size());
     p.off_drag_mask = take(4 * p.drag_mask.size());
+    p.off_wq = take(8 * p.wq.size());
+    p.off_wq_idx = take(4 * p.wq_idx.size());
   }
   return off;
 }

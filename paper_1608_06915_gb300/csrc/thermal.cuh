@@ -171,6 +171,7 @@ __device__ __forceinline__ void pull_generic_th(const PatchDev& p, const R* __re
                                                 R (&g)[27], const R* twd, bool solid_iso, int* status) {
   const long long own = node_index(p, x, y, z);
   const int X[3] = {x, y, z};
+  const int wk = p.wq_idx ? p.wq_idx[own] : -1;  // this node's row of wall fractions
   R rho_own_t = 0;
   bool have_rho = false;
   unroll<27>([&](auto I) {
@@ -203,11 +204,12 @@ __device__ __forceinline__ void pull_generic_th(const PatchDev& p, const R* __re
       }
     }
     long long src = own;
+    bool solid = false;
     if (!bounce && !bad) {
       src = node_index(p, s[0], s[1], s[2]);
       const uint8_t t = p.type[src];
       if (t == T_SOLID) {
-        bounce = true;
+        bounce = solid = true;
         if (solid_iso) wall_face = 6;  // isothermal solid surface at twd[6]
       }
       else if (t == T_SKIP) bad = true;
@@ -217,17 +219,26 @@ __device__ __forceinline__ void pull_generic_th(const PatchDev& p, const R* __re
       bounce = true;
     }
     if (bounce) {
-      f[i] = fin[(long long)(26 - i) * p.plane + own];
-      const R gb = gin[(long long)(26 - i) * p.plane + own];
+      // the wall term of an isothermal face or surface, in deviation form:
+      // g^w_i + g^w_ibar - 2 W_i c_i^2 = 2 W_i (3 rho T_w' + rho~ c_i^2),
+      // T_w' = T_w - T0, g^w_i = W_i rho (3 T_w + c_i^2 - 1)
+      R w = 0;
       if (wall_face >= 0) {
         if (!have_rho) {
           for (int k = 0; k < 27; ++k) rho_own_t += fin[(long long)k * p.plane + own];
           have_rho = true;
         }
-        // g_i = -g'_ibar + g^w_i + g^w_ibar,  g^w_i = W_i rho (3 T_w + c_i^2 - 1)
-        g[i] = -gb + R(2 * WI(i)) * (R(3) * (R(1) + rho_own_t) * twd[wall_face] + rho_own_t * R(C2<i>()));
+        w = R(2 * WI(i)) * (R(3) * (R(1) + rho_own_t) * twd[wall_face] + rho_own_t * R(C2<i>()));
+      }
+      if (solid && wk >= 0) {
+        // curved surface: interpolated along the link
+        const R q = R(p.wq[27 * wk + 26 - i]);
+        f[i] = returning<i, R, R>(p, fin, own, X, q, false, R(0));
+        g[i] = returning<i, R, R>(p, gin, own, X, q, wall_face >= 0, w);
       } else {
-        g[i] = gb;
+        f[i] = fin[(long long)(26 - i) * p.plane + own];
+        const R gb = gin[(long long)(26 - i) * p.plane + own];
+        g[i] = wall_face >= 0 ? w - gb : gb;
       }
     } else {
       f[i] = fin[(long long)i * p.plane + src];

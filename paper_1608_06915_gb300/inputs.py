@@ -85,9 +85,11 @@ def sphere_mask(level: int, centre, diameter_fine: float):
     return dict(level=level, lo=tuple(lo), mask=mask)
 
 
-def sphere_case(scale: int = 1, re: float = 3700.0, u: float = 0.05) -> dict:
+def sphere_case(scale: int = 1, re: float = 3700.0, u: float = 0.05, curved: bool = False) -> dict:
     """Flow past a sphere, 4 levels.  scale=1 is the full 384x192x192 case;
-    scale=8 gives a 48x24x24 coarse grid with the same nesting."""
+    scale=8 gives a 48x24x24 coarse grid with the same nesting.  With
+    ``curved`` the sphere itself is the analytic surface of the wall
+    (interpolated bounce-back), else the staircase of its solid nodes."""
     if scale == 1:
         n = (384, 192, 192)
         boxes = [(1, (80, 80, 80), (160, 112, 112)), (2, (86, 86, 86), (132, 106, 106)),
@@ -99,9 +101,13 @@ def sphere_case(scale: int = 1, re: float = 3700.0, u: float = 0.05) -> dict:
         centre, d_fine = (18, 12, 12), 24.0
     nu_fine = u * d_fine / re
     nu0 = nu_fine / 8.0
-    return dict(name="sphere", n=n, periodic=(0, 1, 1), walls=(0,) * 6, inflow_axis=0, u_in=(u, 0, 0),
+    case = dict(name="sphere", n=n, periodic=(0, 1, 1), walls=(0,) * 6, inflow_axis=0, u_in=(u, 0, 0),
                 boxes=boxes, solid=sphere_mask(3, centre, d_fine), nu0=nu0, accel0=(0, 0, 0), mirror_lbgk=False,
                 thermal=None)
+    if curved:
+        case["wall_shape"] = dict(kind="sphere", c=tuple(float(c) for c in centre), r=d_fine / 16.0,
+                                  solid_inside=True)
+    return case
 
 
 def adjoint_case(n: int = 64, box=(24, 40), nu: float = 0.01) -> dict:

@@ -56,6 +56,11 @@ class lbm_desc(ctypes.Structure):
         ("mirror_lbgk", ctypes.c_int32),
         ("solid_T", ctypes.c_double),
         ("solid_isothermal", ctypes.c_int32),
+        ("shape_kind", ctypes.c_int32),
+        ("shape_c", ctypes.c_double * 3),
+        ("shape_r", ctypes.c_double),
+        ("shape_axis", ctypes.c_int32),
+        ("shape_solid_inside", ctypes.c_int32),
     ]
 
 
@@ -162,6 +167,13 @@ def make_desc(case: dict, storage: str = "fp32"):
         if th.get("solid_T") is not None:  # isothermal solid surfaces
             d.solid_T = float(th["solid_T"])
             d.solid_isothermal = 1
+    shape = case.get("wall_shape")
+    if shape is not None:  # analytic surface of curved solid walls
+        d.shape_kind = {"sphere": 1, "cylinder": 2, "plane": 3}[shape["kind"]]
+        d.shape_c[:] = [float(v) for v in shape["c"]]
+        d.shape_r = float(shape.get("r", 0.0))
+        d.shape_axis = int(shape.get("axis", 0))
+        d.shape_solid_inside = int(bool(shape.get("solid_inside", True)))
     d.storage = STORAGE[storage]
     d.mirror_lbgk = int(bool(case.get("mirror_lbgk", False)))
     return d, keep

@@ -182,6 +182,79 @@ def test_drag_is_the_momentum_the_fluid_loses_on_gpu():
         assert np.max(np.abs((J1 - J0) + F)) < 1e-12 * np.linalg.norm(F), (J1 - J0, F)
 
 
+def test_curved_pipe_fp64_every_step():
+    """Interpolated bounce-back on a cylinder (the wall fraction of every solid
+    link from the analytic surface, both branches q < 1/2 and q >= 1/2):
+    populations and drag against the oracle after every step."""
+    rng = np.random.default_rng(31)
+    case = I.pipe_case(R=10.0, u_max=0.02)
+    c, R = case["centre"], case["radius"]
+
+    def fields(x, y, z, p, info):
+        r2 = ((x - c) ** 2 + (y - c) ** 2) / (R * R)
+        u = np.stack([0.01 * rng.uniform(-1, 1, x.shape), 0.01 * rng.uniform(-1, 1, x.shape),
+                      0.02 * np.clip(1.0 - r2, 0.0, None)])
+        return 1.0 + 0.01 * rng.uniform(-1, 1, x.shape), u
+
+    g, o = twin(case, "fp64", fields)
+    for s in range(6):
+        g.step(1)
+        o.step(1)
+        d = pop_diff(g, o)
+        assert d < 1e-12, (s, d)
+        Fg, Fo = np.array(g.drag()), o.drag()
+        assert np.max(np.abs(Fg - Fo)) < 1e-12 * np.linalg.norm(Fo), (Fg, Fo)
+
+
+def test_curved_sphere_fp64_every_step():
+    """The four-level sphere with its analytic surface on the finest level:
+    populations of every level and the drag against the oracle."""
+    case = I.sphere_case(scale=8, curved=True)
+    g, o = twin(case, "fp64", lambda x, y, z, p, info: I.uniform_fields(x, (0.05, 0.0, 0.0)))
+    for s in range(3):
+        g.step(1)
+        o.step(1)
+        d = pop_diff(g, o)
+        assert d < 1e-12, (s, d)
+        Fg, Fo = np.array(g.drag()), o.drag()
+        assert np.max(np.abs(Fg - Fo)) < 1e-12 * np.linalg.norm(Fo), (Fg, Fo)
+
+
+@pytest.mark.parametrize("storage,bound", [("fp32", 1e-4), ("fp16s", 3e-3)])
+def test_curved_sphere_drag_storage(storage, bound):
+    case = I.sphere_case(scale=8, curved=True)
+    g, o = twin(case, storage, lambda x, y, z, p, info: I.uniform_fields(x, (0.05, 0.0, 0.0)))
+    g.step(10)
+    o.step(10)
+    Fg, Fo = np.array(g.drag()), o.drag()
+    rel = np.max(np.abs(Fg - Fo)) / np.linalg.norm(Fo)
+    print("curved sphere %s drag after 10 steps:" % storage, Fg, Fo, "rel %.2e" % rel)
+    assert rel < bound
+
+
+@pytest.mark.parametrize("z_s", [2.2, 2.8])
+def test_curved_isothermal_surface_fp64_every_step(z_s):
+    """Anti-bounce-back of g interpolated along the link to an isothermal plane
+    between node layers (q < 1/2 and q > 1/2), perturbed off the conduction
+    profile: f and g against the oracle after every step."""
+    case = I.offset_slab_case(z_s)
+
+    def fields(x, y, z, p, info):
+        zl, zh = case["z_lo"], case["z_hi"]
+        dT = case["thermal"]["dT"]
+        T = I.T0 + dT / 2 - dT * (z - zl) / (zh - zl) + 1e-3 * np.sin(2 * np.pi * x / case["n"][0])
+        u = 0.01 * np.stack([np.sin(2 * np.pi * y / case["n"][1]), np.cos(2 * np.pi * x / case["n"][0]),
+                             0.1 * np.sin(z)])
+        return np.ones_like(z) + 1e-3 * np.cos(z), u, T
+
+    g, o = twin(case, "fp64", fields)
+    for s in range(5):
+        g.step(1)
+        o.step(1)
+        df, dg = pop_diff(g, o, 0), pop_diff(g, o, 1)
+        assert df < 1e-12 and dg < 1e-12, (s, df, dg)
+
+
 @pytest.mark.parametrize("storage,bound", [("fp16s", 3e-3), ("bf16s", 3e-2)])
 def test_shifted_16bit_storage_error(storage, bound):
     case = I.tgv_case()
