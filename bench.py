@@ -211,7 +211,7 @@ class Clocks:
 def source_hash():
     """Hash of the sources of the stream-collide kernels (profiles record it)."""
     h = hashlib.sha256()
-    for f in ("device.cuh", "collide.cuh", "sc_tma.cuh", "sc_tma_fp32.cu"):
+    for f in ("device.cuh", "collide.cuh", "sc_tma.cuh", "sc_tma.cu", "sc_tma_fp32.cu"):
         with open(os.path.join(ROOT, "paper_1608_06915_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

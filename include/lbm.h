@@ -206,11 +206,15 @@ lbm_status lbm_init_equilibrium(lbm_grid_t g, int32_t patch, const void* rho, co
  * an unbound grid, LBM_ERR_CUDA for a launch failure. */
 lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps);
 
-/* Autotuner of the instant schedule.  A variant is a TMA kernel variant (load
- * stages in shared memory x CTAs per SM the register allocation aims for) and
- * a schedule of the reconstruction samples (after the TMA pass, or beside it
- * on the coupling streams): variant v = kernel + n_kernels * schedule.  All
- * give identical results; this times `trials` coarse steps of each variant
+/* Autotuner of the instant schedule.  Isothermal model: a variant is a TMA
+ * kernel (load stages in shared memory x CTAs per SM the register allocation
+ * aims for; for FP32 arithmetic also the node-pair kernels on packed FP32x2
+ * instructions) and a schedule of the reconstruction samples (after the TMA
+ * pass, or beside it on the coupling streams): variant v = kernel + n_kernels *
+ * schedule, 8 variants (4 for FP64 storage), all with identical results.
+ * Thermal model: 2 variants of its TMA pass (f and g stored from registers
+ * straight to memory, or through a shared-memory stage by TMA), identical
+ * results.  This times `trials` coarse steps of each variant
  * the way lbm_step runs them (graph replays unless lbm_graphs is off), CUDA
  * events around them, and keeps the fastest.  The state advances by
  * 1 + n_variants * (2 + trials) coarse steps: one untimed step first, and
@@ -218,7 +222,7 @@ lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps);
  * trials.  chosen (nullable)
  * gets the variant kept, ms_per_step[0 .. min(n, max_variants)) (nullable)
  * the measured time per coarse step of each, n_variants (nullable) their
- * number (1 for the thermal model, whose TMA pass has a single variant).
+ * number.
  * Synchronises the bound stream; drops captured step graphs.  Without a call
  * the grid uses variant 0.  The paper has no counterpart. */
 lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms_per_step, int32_t max_variants,

@@ -384,7 +384,7 @@ lbm_status run_instant(lbm_grid* g, int k) {
                                 const lbmk::ThermalLevel TL = thermal_level(g, p);
                                 void* gin = g->base + p.off_g[p.cur];
                                 void* gout = g->base + p.off_g[1 - p.cur];
-                                cudaError_t e = lbmk::launch_th_tma(storage, maps, pv, fin,
+                                cudaError_t e = lbmk::launch_th_tma(storage, g->variant, maps, pv, fin, fout, gout,
                                                                    at<unsigned long long>(g, p.off_tiles_pure[odd]),
                                                                    (int64_t)p.tiles_pure[odd].size(), TL,
                                                                    status_ptr(g), g->stream);
@@ -804,8 +804,9 @@ lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms
                         int32_t* n_variants) {
   if (lbm_status s = check_bound(g)) return s;
   if (trials < 1) return fail(g, LBM_ERR_ARG, "autotune needs at least one trial step");
-  const int nt = g->hg.thermal ? 1 : lbmk::sc_tma_variants(g->hg.desc.storage);
-  const int nv = g->hg.thermal ? 1 : 2 * nt;  // TMA kernel variant x sample schedule
+  // isothermal: TMA kernel variant x sample schedule; thermal: TMA kernel variant
+  const int nt = g->hg.thermal ? lbmk::th_tma_variants() : lbmk::sc_tma_variants(g->hg.desc.storage);
+  const int nv = g->hg.thermal ? nt : 2 * nt;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (!e) e = cudaEventCreate(&e1);
@@ -849,8 +850,8 @@ lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms
 
 lbm_status lbm_set_variant(lbm_grid_t g, int32_t variant) {
   if (!g) return LBM_ERR_ARG;
-  const int nt = g->hg.thermal ? 1 : lbmk::sc_tma_variants(g->hg.desc.storage);
-  const int nv = g->hg.thermal ? 1 : 2 * nt;
+  const int nt = g->hg.thermal ? lbmk::th_tma_variants() : lbmk::sc_tma_variants(g->hg.desc.storage);
+  const int nv = g->hg.thermal ? nt : 2 * nt;
   if (variant < 0 || variant >= nv) return fail(g, LBM_ERR_ARG, "variant out of range");
   g->variant = variant % nt;
   g->presample = variant >= nt;

@@ -36,10 +36,13 @@ cudaError_t launch_th_tiles(int storage, const PatchDev& p, const void* fin, con
                             const uint32_t* tiles, int64_t ntiles, int ntx, const ThermalLevel& L, int odd,
                             int* status, cudaStream_t st);
 // Thermal TMA tile pass of one patch; maps = {f load, f store, f wrap, g load,
-// g store, g wrap} descriptors (thermal_tma.cu).
-cudaError_t launch_th_tma(int storage, const void* const maps[6], const PatchDev& p, const void* fin,
-                          const unsigned long long* tiles, int64_t ntiles, const ThermalLevel& L, int* status,
-                          cudaStream_t st);
+// g store, g wrap} descriptors (thermal_tma.cu).  Variant 0 stores f and g
+// from registers directly to fout and gout (3 CTAs per SM); variant 1 stores
+// them through a shared-memory stage with TMA (2 CTAs per SM).
+int th_tma_variants();
+cudaError_t launch_th_tma(int storage, int variant, const void* const maps[6], const PatchDev& p, const void* fin,
+                          void* fout, void* gout, const unsigned long long* tiles, int64_t ntiles,
+                          const ThermalLevel& L, int* status, cudaStream_t st);
 cudaError_t launch_th_nodes(int storage, const PatchDev& p, const void* fin, const void* gin, void* fout, void* gout,
                             const uint32_t* nodes, int64_t n, const ThermalLevel& L, int* status, cudaStream_t st);
 cudaError_t launch_th_coalesce(int storage, const PatchDev& child, const void* fin_c, const void* gin_c,

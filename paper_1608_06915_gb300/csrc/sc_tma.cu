@@ -56,9 +56,12 @@ cudaError_t launch_sc_nodes(int storage, const PatchDev& p, const void* fin, voi
   }
 }
 
-// Tensor map of one population buffer, 4-D [27][nz][ny][nxp].  Boxes: loads
-// (W, 1, 1, 3) -- one row of three consecutive populations; stores (32, 1, 1, 27)
-// -- one warp's segment of all populations; wrap (16 bytes, 1, 1, 1).
+// Tensor map of one population buffer, 4-D [27][nz][ny][nx] with the row
+// pitch nxp.  Boxes: loads (W, 1, 1, 3) -- one row of three consecutive
+// populations; stores (32, 1, 1, 27) -- one warp's segment of all populations;
+// wrap (16 bytes, 1, 1, 1).  The x extent is the patch's node count, not the
+// padded pitch: the padding columns of a ragged row then lie outside the
+// tensor, so loads fill them without reading memory and stores skip them.
 cudaError_t make_tensor_map(int storage, void* out, const void* base, const PatchDev& p, int kind) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -89,7 +92,7 @@ cudaError_t make_tensor_map(int storage, void* out, const void* base, const Patc
     default:
       return cudaErrorInvalidValue;
   }
-  const cuuint64_t dims[4] = {(cuuint64_t)p.nxp, (cuuint64_t)p.dim[1], (cuuint64_t)p.dim[2], 27};
+  const cuuint64_t dims[4] = {(cuuint64_t)p.dim[0], (cuuint64_t)p.dim[1], (cuuint64_t)p.dim[2], 27};
   const cuuint64_t strides[3] = {(cuuint64_t)p.nxp * es, (cuuint64_t)p.nxp * p.dim[1] * es,
                                  (cuuint64_t)p.plane * es};
   cuuint32_t np = 3;

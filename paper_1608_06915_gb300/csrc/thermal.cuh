@@ -73,15 +73,29 @@ __device__ __forceinline__ R wcv3(R vx, R vy, R vz) {
   return R(3.0 * WI(i)) * (R(CX(i)) * vx + R(CY(i)) * vy + R(CZ(i)) * vz);
 }
 
-// One thermal collision of deviation populations (f, g) in place; returns gamma.
+// One thermal collision of deviation populations: f in place, g read through
+// gget(I) (the pre-collision g_i, any number of times) and written through
+// gput(I, g'_i) once per population after every read; returns gamma.
 // Pr <= 1: f* = f^eq and g* carries q - 2 u.(P - P^eq) (Table I); Pr > 1:
 // f* - f^eq is the Grad term W_i (P - P^eq)_ab (c_ia c_ib - T0 d_ab)/(2 T0^2)
-// and g* carries q^eq + 2 u.(P - P^eq), with the closed-form P^eq.
-template <typename R>
-__device__ __forceinline__ R thermal_collide(R (&f)[27], R (&g)[27], R beta, R beta1, R glam, R tref_d,
-                                             bool lbgk, bool pr_gt1) {
+// and g* carries q^eq + 2 u.(P - P^eq), with the closed-form P^eq.  The g
+// update of each population needs only the node's moments.
+template <typename R, typename GGet, typename GPut>
+__device__ __forceinline__ R thermal_collide_acc(R (&f)[27], GGet&& gget, GPut&& gput, R beta, R beta1, R glam,
+                                                 R tref_d, bool lbgk, bool pr_gt1) {
   ThState<R> s;
-  thermal_state(f, g, s);
+  macro(f, s.rho_t, s.rho, s.ux, s.uy, s.uz);
+  {
+    R e[3] = {0, 0, 0};
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      e[CZ(i) + 1] += gget(I);
+    });
+    s.e_t = (e[0] + e[2]) + e[1];
+    // T = (2E - u^2)/3 with 2E = (1 + e_t)/rho  =>  T - 1/3 = ((e_t - rho_t)/rho - u^2)/3
+    const R u2 = s.ux * s.ux + s.uy * s.uy + s.uz * s.uz;
+    s.T_d = (fdiv(s.e_t - s.rho_t, s.rho) - u2) * R(1.0 / 3.0);
+  }
   // pre-collision moments: P - P^eq = P~ + T0 d - rho T0 d - rho u u, q = sum c g
   R P[6] = {0, 0, 0, 0, 0, 0}, q[3] = {0, 0, 0};
   unroll<27>([&](auto I) {
@@ -92,9 +106,15 @@ __device__ __forceinline__ R thermal_collide(R (&f)[27], R (&g)[27], R beta, R b
     if constexpr (CX(i) * CY(i) != 0) P[3] += R(CX(i) * CY(i)) * f[i];
     if constexpr (CX(i) * CZ(i) != 0) P[4] += R(CX(i) * CZ(i)) * f[i];
     if constexpr (CY(i) * CZ(i) != 0) P[5] += R(CY(i) * CZ(i)) * f[i];
-    if constexpr (CX(i) != 0) q[0] += R(CX(i)) * g[i];
-    if constexpr (CY(i) != 0) q[1] += R(CY(i)) * g[i];
-    if constexpr (CZ(i) != 0) q[2] += R(CZ(i)) * g[i];
+  });
+  unroll<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (CX(i) != 0 || CY(i) != 0 || CZ(i) != 0) {
+      const R gi = gget(I);
+      if constexpr (CX(i) != 0) q[0] += R(CX(i)) * gi;
+      if constexpr (CY(i) != 0) q[1] += R(CY(i)) * gi;
+      if constexpr (CZ(i) != 0) q[2] += R(CZ(i)) * gi;
+    }
   });
   const R u[3] = {s.ux, s.uy, s.uz};
   const R rt3 = s.rho_t * R(1.0 / 3.0);
@@ -108,15 +128,23 @@ __device__ __forceinline__ R thermal_collide(R (&f)[27], R (&g)[27], R beta, R b
     const R Pu2 = R(2) * (Pd[a][0] * u[0] + Pd[a][1] * u[1] + Pd[a][2] * u[2]);
     X[a] = pr_gt1 ? Pu2 : q[a] - qc * u[a] - Pu2;
   }
-  R ge[27];
-  geq_dev(s.rho_t, s.rho, s.ux, s.uy, s.uz, s.e_t, ge);
-  const R b2 = R(2) * beta, b12 = R(2) * (beta - beta1);
-  unroll<27>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    g[i] = g[i] + b2 * (ge[i] - g[i]) + b12 * wcv3<i>(X[0], X[1], X[2]);
-  });
+  // g^eq - W_i c_i^2 for (rho, u, 2 rho E) (geq_dev), population by population
+  {
+    const R E2 = R(1) + s.e_t;
+    const R u2 = s.ux * s.ux + s.uy * s.uy + s.uz * s.uz;
+    const R a1 = R(3) * (E2 + R(2.0 / 3.0) * s.rho);
+    const R a2 = R(4.5) * (E2 + R(4.0 / 3.0) * s.rho);
+    const R b2 = R(2) * beta, b12 = R(2) * (beta - beta1);
+    unroll<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const R cu = R(CX(i)) * s.ux + R(CY(i)) * s.uy + R(CZ(i)) * s.uz;
+      const R ge = R(WI(i)) * (s.e_t + s.rho_t * R(C2<i>() - 1) + a1 * cu + a2 * (cu * cu - u2 * R(1.0 / 3.0)));
+      const R gi = gget(I);
+      gput(I, gi + b2 * (ge - gi) + b12 * wcv3<i>(X[0], X[1], X[2]));
+    });
+  }
   const R duz = glam * (s.T_d - tref_d);
-  // f is still the pre-collision state: its moments are those of thermal_state
+  // f is still the pre-collision state: its moments are those computed above
   const R gamma = kbc_collide_m<R, 4>(f, s.rho_t, s.rho, s.ux, s.uy, s.uz, beta, R(0), R(0), duz, lbgk);
   if (pr_gt1) {
     // 2 (beta - beta1)(f* - f^eq) at T0 = 1/3: 9 (beta - beta1) W_i Pd_ab (c_ia c_ib - d_ab / 3)
@@ -135,6 +163,15 @@ __device__ __forceinline__ R thermal_collide(R (&f)[27], R (&g)[27], R beta, R b
     });
   }
   return gamma;
+}
+
+// The same collision with g held in registers (in place).
+template <typename R>
+__device__ __forceinline__ R thermal_collide(R (&f)[27], R (&g)[27], R beta, R beta1, R glam, R tref_d, bool lbgk,
+                                             bool pr_gt1) {
+  return thermal_collide_acc<R>(
+      f, [&](auto I) -> R { return g[decltype(I)::value]; }, [&](auto I, R v) { g[decltype(I)::value] = v; }, beta,
+      beta1, glam, tref_d, lbgk, pr_gt1);
 }
 
 // Non-equilibrium rescaling of a thermal pair from a level with (beta_s, beta1_s)

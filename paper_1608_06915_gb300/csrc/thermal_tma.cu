@@ -7,8 +7,11 @@
 // edge tiles of x-periodic rows.  Four consumer warps pull their 54 values,
 // release the stage, run the thermal collision (f: KBC with the Boussinesq
 // force; g: relaxation to the Grad equilibrium with the quasi-equilibrium
-// of the grid's Prandtl regime), and store their 27 x 32 segments of f and g with one TMA
-// store each.  Walls across y or z follow the row rule of the isothermal pass
+// of the grid's Prandtl regime), and store their 27 x 32 segments of f and g:
+// straight from registers, one 128-byte line per warp and population
+// (k_th_tma_d: without an output stage 3 CTAs fit an SM), or through a
+// shared-memory stage with one TMA store per set (k_th_tma: 2 CTAs per SM).
+// Walls across y or z follow the row rule of the isothermal pass
 // (bit j of the tile's bounce mask: source row j lies beyond a wall): f
 // bounces back, g takes the anti-bounce-back to the wall equilibrium at rest,
 // g_i = -g'_-i + 2 W_i (3 rho T_w + rho~ c_i^2) in deviation form, with the
@@ -21,16 +24,21 @@
 
 namespace lbmk {
 
-template <typename S>
+// OUT 0: the output goes through a shared-memory stage and TMA stores (2 CTAs
+// per SM fit); OUT 1: each warp stores its rows from registers straight to
+// global memory (one 128-byte line per population), and without the output
+// stage 3 CTAs per SM fit.
+template <typename S, int OUT = 0>
 struct ThTmaCfg {
   using C = TmaCfg<S, 2>;
   static constexpr int DI = sizeof(S) == 8 ? 1 : 2;                   // load stages
   static constexpr int HALF = 9 * C::GROUP + 18 * C::SIDE;             // f rows + wrap slots; g follows
   static constexpr int STAGE = 2 * HALF;
-  static constexpr int OSTAGE = 2 * 4 * C::OSEGB;                      // [set][warp][population][32]
+  static constexpr int OSTAGE = OUT ? 0 : 2 * 4 * C::OSEGB;           // [set][warp][population][32]
   static constexpr uint32_t TX = 2u * C::TX;
   static constexpr int SMEM = DI * STAGE + OSTAGE + 128;
   static constexpr int THREADS = 160;
+  static constexpr int MINB = (OUT && sizeof(S) == 4) ? 3 : 1;        // CTAs per SM the registers aim for
 };
 
 template <typename S>
@@ -38,12 +46,12 @@ struct ThMaps {
   CUtensorMap f_in, f_out, f_wrap, g_in, g_out, g_wrap;
 };
 
-template <typename R>
-__global__ void __launch_bounds__(160) k_th_tma(const __grid_constant__ ThMaps<R> m, PatchDev p,
-                                                const R* __restrict__ fin,
-                                                const unsigned long long* __restrict__ tiles, int ntiles,
-                                                ThParams<R> tp, int* status) {
-  using T = ThTmaCfg<R>;
+template <typename R, int OUT>
+__device__ __forceinline__ void th_tma_body(const ThMaps<R>& m, const PatchDev& p, const R* __restrict__ fin,
+                                            R* __restrict__ fout, R* __restrict__ gout,
+                                            const unsigned long long* __restrict__ tiles, int ntiles,
+                                            const ThParams<R>& tp, int* status) {
+  using T = ThTmaCfg<R, OUT>;
   using C = typename T::C;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -177,6 +185,17 @@ __global__ void __launch_bounds__(160) k_th_tma(const __grid_constant__ ThMaps<R
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
     if (x < p.dim[0]) thermal_collide<R>(f, g, tp.beta, tp.beta1, tp.glam, tp.tref_d, tp.lbgk != 0, tp.pr_gt1 != 0);
+    if constexpr (OUT == 1) {
+      if (x < p.dim[0]) {
+        const long long own = node_index(p, x, y, z);
+        unroll<27>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          __stcs(fout + (long long)i * p.plane + own, f[i]);
+          __stcs(gout + (long long)i * p.plane + own, g[i]);
+        });
+      }
+      continue;
+    }
     if (lane == 0) bulk_wait_read<0>();
     __syncwarp();
     unsigned char* segf = ostage + warp * C::OSEGB;
@@ -197,6 +216,25 @@ __global__ void __launch_bounds__(160) k_th_tma(const __grid_constant__ ThMaps<R
   if (lane == 0) bulk_wait_all();
 }
 
+// The kernels: through the output stage (registers left to the compiler; 2
+// CTAs per SM fit in shared memory) and with direct stores (3 CTAs per SM).
+template <typename R>
+__global__ void __launch_bounds__(160) k_th_tma(const __grid_constant__ ThMaps<R> m, PatchDev p,
+                                                const R* __restrict__ fin, R* __restrict__ fout,
+                                                R* __restrict__ gout, const unsigned long long* __restrict__ tiles,
+                                                int ntiles, ThParams<R> tp, int* status) {
+  th_tma_body<R, 0>(m, p, fin, fout, gout, tiles, ntiles, tp, status);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(160, ThTmaCfg<R, 1>::MINB) k_th_tma_d(const __grid_constant__ ThMaps<R> m,
+                                                                       PatchDev p, const R* __restrict__ fin,
+                                                                       R* __restrict__ fout, R* __restrict__ gout,
+                                                                       const unsigned long long* __restrict__ tiles,
+                                                                       int ntiles, ThParams<R> tp, int* status) {
+  th_tma_body<R, 1>(m, p, fin, fout, gout, tiles, ntiles, tp, status);
+}
+
 // Nodes of TMA tiles the row rule does not give, recomputed node by node.
 template <typename R>
 __global__ void __launch_bounds__(128) k_th_nodes(PatchDev p, const R* __restrict__ fin, const R* __restrict__ gin,
@@ -214,25 +252,32 @@ __global__ void __launch_bounds__(128) k_th_nodes(PatchDev p, const R* __restric
   store2(p, fout, gout, own, f, g);
 }
 
-cudaError_t launch_th_tma(int storage, const void* const maps[6], const PatchDev& p, const void* fin,
-                          const unsigned long long* tiles, int64_t ntiles, const ThermalLevel& L, int* status,
-                          cudaStream_t st) {
+template <typename R, typename T, typename K>
+cudaError_t th_tma_go(K kern, int& blocks_per_sm, int& sms) {
+  if (blocks_per_sm < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
+    if (e) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, T::THREADS, T::SMEM);
+    if (e) return e;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  return cudaSuccess;
+}
+
+// 0: k_th_tma_d, direct stores (3 CTAs per SM); 1: k_th_tma, TMA stores through
+// the output stage (2 CTAs per SM)
+int th_tma_variants() { return 2; }
+
+cudaError_t launch_th_tma(int storage, int variant, const void* const maps[6], const PatchDev& p, const void* fin,
+                          void* fout, void* gout, const unsigned long long* tiles, int64_t ntiles,
+                          const ThermalLevel& L, int* status, cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;
+  if (variant < 0 || variant > 1) return cudaErrorInvalidValue;
   return th_dispatch(storage, [&](auto z) -> cudaError_t {
     using R = decltype(z);
-    using T = ThTmaCfg<R>;
-    static int blocks_per_sm = -1, sms = 0;
-    auto kern = k_th_tma<R>;
-    if (blocks_per_sm < 0) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
-      if (e) return e;
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, T::THREADS, T::SMEM);
-      if (e) return e;
-      if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
     ThMaps<R> m;
     memcpy(&m.f_in, maps[0], sizeof(CUtensorMap));
     memcpy(&m.f_out, maps[1], sizeof(CUtensorMap));
@@ -240,9 +285,17 @@ cudaError_t launch_th_tma(int storage, const void* const maps[6], const PatchDev
     memcpy(&m.g_in, maps[3], sizeof(CUtensorMap));
     memcpy(&m.g_out, maps[4], sizeof(CUtensorMap));
     memcpy(&m.g_wrap, maps[5], sizeof(CUtensorMap));
-    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)blocks_per_sm * sms);
-    kern<<<grid, T::THREADS, T::SMEM, st>>>(m, p, (const R*)fin, tiles, (int)ntiles, th_params<R>(L), status);
-    return cudaGetLastError();
+    auto go = [&](auto kern, auto cfg, int& blocks_per_sm, int& sms) -> cudaError_t {
+      using T = decltype(cfg);
+      if (cudaError_t e = th_tma_go<R, T>(kern, blocks_per_sm, sms)) return e;
+      const int grid = (int)std::min<int64_t>(ntiles, (int64_t)blocks_per_sm * sms);
+      kern<<<grid, T::THREADS, T::SMEM, st>>>(m, p, (const R*)fin, (R*)fout, (R*)gout, tiles, (int)ntiles,
+                                              th_params<R>(L), status);
+      return cudaGetLastError();
+    };
+    static int bps[2] = {-1, -1}, sms[2] = {0, 0};
+    if (variant == 0) return go(k_th_tma_d<R>, ThTmaCfg<R, 1>{}, bps[0], sms[0]);
+    return go(k_th_tma<R>, ThTmaCfg<R, 0>{}, bps[1], sms[1]);
   });
 }
 

@@ -368,13 +368,16 @@ def _rbc(case):
     return lambda x, y, z, p, info: I.rbc_fields(case, info["level"], info["org"], info["dim"])
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("pr", [0.7, 2.0])
-def test_rbc_small_fp64_every_step(pr):
+def test_rbc_small_fp64_every_step(pr, variant):
     """Plates with anti-bounce-back, Boussinesq force, two wall bands per level:
     f and g against the oracle after every coarse step, in both Prandtl regimes
-    of Table I (Pr <= 1 and Pr > 1)."""
+    of Table I (Pr <= 1 and Pr > 1), with either thermal TMA pass (g in
+    registers, or updated from the load stage)."""
     case = I.rbc_small_case(pr=pr)
     g, o = twin(case, "fp64", _rbc(case))
+    g.set_variant(variant)
     for s in range(4):
         g.step(1)
         o.step(1)
@@ -382,8 +385,9 @@ def test_rbc_small_fp64_every_step(pr):
         assert df < 1e-12 and dg < 1e-12, (s, df, dg)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("refined", [False, True])
-def test_heated_slab_fp64_every_step(refined):
+def test_heated_slab_fp64_every_step(refined, variant):
     """Isothermal solid surfaces (anti-bounce-back of g to the solid
     temperature): a heated slab under a cold plate, one level or with the slab
     on a refined band, perturbed off its conduction profile; f and g against
@@ -397,6 +401,7 @@ def test_heated_slab_fp64_every_step(refined):
         return np.ones_like(z) + 1e-3 * np.cos(z), u, T
 
     g, o = twin(case, "fp64", fields)
+    g.set_variant(variant)
     for s in range(5):
         g.step(1)
         o.step(1)
@@ -446,6 +451,34 @@ def test_graph_replay_matches_direct_launches(storage):
     torch.cuda.synchronize()
     for p in range(len(ga.patches)):
         assert torch.equal(ga.get_populations(p), gb.get_populations(p)), p
+
+
+@pytest.mark.parametrize("pr", [0.7, 2.0])
+def test_thermal_tma_variants_agree(pr):
+    """The two thermal TMA passes (stores straight from registers at 3 CTAs
+    per SM; TMA stores through a shared-memory stage at 2) run the same
+    arithmetic: FP32 f and g after 10 coarse steps of the three-level
+    Rayleigh-Benard layout are the same bits."""
+    import torch
+    case = I.rbc_small_case(pr=pr)
+    ga, _ = twin(case, "fp32", _rbc(case), oracle=False)
+    ga.set_variant(0)
+    ga.step(10)
+    for v in (1,):
+        gb, _ = twin(case, "fp32", _rbc(case), oracle=False)
+        gb.set_variant(v)
+        gb.step(10)
+        torch.cuda.synchronize()
+        worst, same = 0.0, True
+        for p in range(len(ga.patches)):
+            for which in (0, 1):
+                a, b = ga.get_populations(p, which), gb.get_populations(p, which)
+                same = same and torch.equal(a, b)
+                worst = max(worst, float((a.double() - b.double()).abs().max()))
+        print("thermal variant %d against 0, pr %.1f: max |diff| %.3e, bit-identical %s" % (v, pr, worst, same))
+        assert same, worst
+    with pytest.raises(Exception):
+        ga.set_variant(2)
 
 
 @pytest.mark.parametrize("storage", ["fp32", "fp64", "fp16s"])
