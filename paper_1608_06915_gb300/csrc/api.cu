@@ -1095,7 +1095,7 @@ AdjLayout adjoint_layout(const lbm_grid* g, int K) {
   }
   a.step_bytes = (rec + 255) / 256 * 256;
   a.snap_off = take(a.step_bytes * (size_t)K);
-  a.slot_off = take(sizeof(unsigned long long));
+  a.slot_off = take(2 * sizeof(unsigned long long));  // the record's base word, then the copy-completion count
   a.partial_off = take(sizeof(double) * (kDiagBlocks * g->hg.P.size() + 1));
   a.total = w;
   return a;
@@ -1118,6 +1118,7 @@ lbm_status recording_step(lbm_grid* g, const AdjLayout& a, unsigned long long* s
   const int L = g->hg.nlev, KI = 1 << (L - 1);
   lbmk::CopySegs segs{};
   segs.rel = slot;
+  unsigned* done = reinterpret_cast<unsigned*>(slot + 1);  // completion count beside the word
   cudaError_t e = cudaSuccess;
   auto add = [&](size_t off, const void* src, size_t n) {
     if (segs.n == lbmk::kCopySegs) {
@@ -1129,16 +1130,20 @@ lbm_status recording_step(lbm_grid* g, const AdjLayout& a, unsigned long long* s
     segs.bytes[segs.n] = n;
     ++segs.n;
   };
-  auto flush = [&] {
+  auto flush = [&](bool last) {
+    // the step's last copy advances the record's base word when it is done
+    segs.done = last ? done : nullptr;
+    segs.advance = last ? a.step_bytes : 0;
     if (!e) e = lbmk::launch_copy(segs, g->stream);
     segs.n = 0;
+    segs.done = nullptr;
   };
   // outer snapshot: every patch at the step's start
   for (size_t pi = 0; pi < g->hg.P.size(); ++pi) {
     const HostPatch& p = g->hg.P[pi];
     add(a.snap_patch_off[pi], g->base + p.off_f[p.cur], 27 * (size_t)p.plane * g->hg.pop_bytes);
   }
-  flush();
+  flush(false);
   if (e) return cuda_check(g, e, "adjoint snapshot");
   for (int k = 1; k <= KI; ++k) {
     if (lbm_status st = run_instant(g, k)) return st;
@@ -1154,10 +1159,12 @@ lbm_status recording_step(lbm_grid* g, const AdjLayout& a, unsigned long long* s
         add(a.snap_bytes + (size_t)(k - 1) * a.inner_bytes + a.inner_patch_off[pi], g->base + p.off_f[p.cur],
             27 * (size_t)p.plane * g->hg.pop_bytes);
       }
-    flush();
+    if (k < KI) flush(false);
     if (e) return cuda_check(g, e, "adjoint snapshot");
   }
-  return cuda_check(g, lbmk::launch_word(slot, a.step_bytes, 1, g->stream), "adjoint snapshot slot");
+  if (segs.n == 0) return cuda_check(g, lbmk::launch_word(slot, a.step_bytes, 1, g->stream), "adjoint snapshot slot");
+  flush(true);
+  return cuda_check(g, e, "adjoint snapshot");
 }
 
 // Copies the state of every patch to/from a packed buffer (restore: the current

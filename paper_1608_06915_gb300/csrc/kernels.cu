@@ -832,10 +832,24 @@ __global__ void __launch_bounds__(256) k_copy(CopySegs segs) {
   else if ((a & 7) == 0) copy_words((uint2*)dst, (const uint2*)segs.src[j], n / 8);
   else if ((a & 3) == 0) copy_words((unsigned*)dst, (const unsigned*)segs.src[j], n / 4);
   else copy_words((unsigned char*)dst, (const unsigned char*)segs.src[j], n);
+  if (segs.done) {
+    // the last block advances the base word: all blocks read it before this
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned total = gridDim.x * gridDim.y;
+      if (atomicAdd(segs.done, 1u) == total - 1) {
+        *segs.rel += segs.advance;
+        *segs.done = 0;
+      }
+    }
+  }
 }
 
 __global__ void k_word(unsigned long long* word, unsigned long long value, int advance) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *word = advance ? *word + value : value;
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *word = advance ? *word + value : value;
+    if (!advance) *reinterpret_cast<unsigned*>(word + 1) = 0;  // the copy-completion count beside it
+  }
 }
 
 cudaError_t launch_word(unsigned long long* word, unsigned long long value, int advance, cudaStream_t st) {

@@ -161,10 +161,16 @@ struct CopySegs {
   const void* src[kCopySegs];
   size_t bytes[kCopySegs];
   int n;
-  const unsigned long long* rel;
+  // destinations relative to *rel when set; with done set, the last block to
+  // finish adds `advance` to *rel (every block has read it by then) and
+  // clears *done, which must be 0 at launch
+  unsigned long long* rel;
+  unsigned long long advance;
+  unsigned* done;
 };
 cudaError_t launch_copy(const CopySegs& segs, cudaStream_t st);
-// *word = value (set) or *word += value (advance), one thread
+// *word = value (set, which also clears the 32-bit count that follows the
+// word) or *word += value (advance), one thread
 cudaError_t launch_word(unsigned long long* word, unsigned long long value, int advance, cudaStream_t st);
 
 // Source patches of a state transfer (regridding): views, current f buffers,
