@@ -266,14 +266,14 @@ __device__ __forceinline__ void push_adjoint(const PatchDev& p, R* __restrict__ 
     constexpr int c[3] = {CX(i), CY(i), CZ(i)};
     int s[3];
     bool bounce = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    unroll<3>([&](auto A) {
+      constexpr int a = decltype(A)::value;
       s[a] = X[a] - c[a];
       if (s[a] < 0 || s[a] >= p.dim[a]) {
         if (bulk || p.span[a]) s[a] += s[a] < 0 ? p.dim[a] : -p.dim[a];
         else bounce = true;  // not produced by the layouts the adjoint accepts
       }
-    }
+    });
     long long src = own;
     int comp = 26 - i;
     if (!bounce) {
@@ -369,16 +369,17 @@ __global__ void __launch_bounds__(128, 4) k_adj_sc_st(PatchDev p, const R* __res
   // beyond a non-spanned face
   const int X[3] = {x, y, z};
   int src[3][3], dst_in[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int c = -1; c <= 1; ++c) {
+  unroll<3>([&](auto A) {
+    constexpr int a = decltype(A)::value;
+    unroll<3>([&](auto C) {
+      constexpr int c = (int)decltype(C)::value - 1;
       int v = X[a] - c;
       if (v < 0 || v >= p.dim[a]) v = p.span[a] ? (v < 0 ? v + p.dim[a] : v - p.dim[a]) : -1;
       src[a][c + 1] = v;
       const int w = X[a] + c;  // the pusher of this node's entry along the axis
       dst_in[a][c + 1] = (w >= 0 && w < p.dim[a]) || p.span[a];
-    }
+    });
+  });
   const long long row = p.nxp, sl = (long long)p.nxp * p.dim[1];
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -584,8 +585,8 @@ __device__ __forceinline__ R pull_one(const PatchDev& p, const R* __restrict__ f
   const int X[3] = {x, y, z};
   int s[3];
   bool bounce = false, bad = false;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
+  unroll<3>([&](auto A) {
+    constexpr int a = decltype(A)::value;
     s[a] = X[a] - d.c[a];
     if (s[a] < 0 || s[a] >= p.dim[a]) {
       if (bulk || p.span[a]) {
@@ -606,7 +607,7 @@ __device__ __forceinline__ R pull_one(const PatchDev& p, const R* __restrict__ f
         bad = true;
       }
     }
-  }
+  });
   long long src = own;
   if (!bounce && !bad) {
     src = node_index(p, s[0], s[1], s[2]);
@@ -634,14 +635,14 @@ __device__ __forceinline__ void push_one(const PatchDev& p, R* __restrict__ lam_
   const int X[3] = {x, y, z};
   int s[3];
   bool bounce = false;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
+  unroll<3>([&](auto A) {
+    constexpr int a = decltype(A)::value;
     s[a] = X[a] - d.c[a];
     if (s[a] < 0 || s[a] >= p.dim[a]) {
       if (bulk || p.span[a]) s[a] += s[a] < 0 ? p.dim[a] : -p.dim[a];
       else bounce = true;  // not produced by the layouts the adjoint accepts
     }
-  }
+  });
   if (bounce) atomicAdd(lam_old + (long long)(26 - d.i) * p.plane + own, v);
   else atomicAdd(lam_old + (long long)d.i * p.plane + node_index(p, s[0], s[1], s[2]), v);
 }
@@ -682,7 +683,7 @@ template <typename R>
 __global__ void __launch_bounds__(128) k_adj_explode(PatchDev pc, const R* __restrict__ lam_new_c,
                                                      const uint32_t* __restrict__ ex_node,
                                                      const uint4* __restrict__ ex_src, long long n_one, long long n,
-                                                     const R* __restrict__ val, R* __restrict__ vbar, long long ld,
+                                                     const R* __restrict__ val, R* __restrict__ tbar, long long ld,
                                                      R beta_c, int lbgk) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
@@ -714,39 +715,36 @@ __global__ void __launch_bounds__(128) k_adj_explode(PatchDev pc, const R* __res
   R rb, ub[3];
   feq_vjp_rho_u<R>(l, q.fefull, q.rho, q.L[0], q.L[1], q.L[2], rb, ub);
   const R vb[4] = {rb, ub[0], ub[1], ub[2]};  // rho~ enters as rho = 1 + rho~
-  auto push = [&](int c, R x) {
-    R* d = vbar + (long long)c * ld;
-    if (one) {
-      atomicAdd(d + s.x, x);
-    } else {
-      atomicAdd(d + s.x, w0 * x);
-      atomicAdd(d + s.y, w1 * x);
-      atomicAdd(d + s.z, w1 * x);
-      atomicAdd(d + s.w, w0 * x);
-    }
-  };
-  for (int c = 0; c < 4; ++c) push(c, vb[c]);
+  // the adjoint of the target's interpolated values, tbar[c][k]; the point
+  // columns gather them (k_adj_gather)
+  for (int c = 0; c < 4; ++c) tbar[(long long)c * n + k] = vb[c];
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    push(4 + i, l[i]);
+    tbar[(long long)(4 + i) * n + k] = l[i];
   });
 }
 
-// transpose of one interpolation pass: vbar[c][src_k] += w_k vbar[c][out0 + q];
-// one thread per (point, value)
+// The transpose of the interpolation passes in gather form: each point column
+// j in [j0, j1) sums w * (adjoint of its consumer) over its consumer list --
+// targets (tbar) and points of later stages (vbar) -- in a fixed order, so
+// the result does not depend on scheduling.  One thread per (column, value).
 template <typename R>
-__global__ void __launch_bounds__(128) k_adj_points(const uint4* __restrict__ src, long long n, R* __restrict__ vbar,
-                                                    long long ld, long long out0) {
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  const uint4 s = src[q];
-  const R w0 = R(-1.0 / 16.0), w1 = R(9.0 / 16.0);
-  R* d = vbar + (long long)blockIdx.y * ld;
-  const R x = d[out0 + q];
-  atomicAdd(d + s.x, w0 * x);
-  atomicAdd(d + s.y, w1 * x);
-  atomicAdd(d + s.z, w1 * x);
-  atomicAdd(d + s.w, w0 * x);
+__global__ void __launch_bounds__(128) k_adj_gather(const uint32_t* __restrict__ use_ptr,
+                                                    const uint32_t* __restrict__ use_ent, long long j0, long long j1,
+                                                    R* __restrict__ vbar, long long ld, const R* __restrict__ tbar,
+                                                    long long nt) {
+  const long long j = j0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= j1) return;
+  const int c = blockIdx.y;
+  const R w[4] = {R(-1.0 / 16.0), R(9.0 / 16.0), R(9.0 / 16.0), R(-1.0 / 16.0)};
+  R acc = R(0);
+  for (uint32_t e = use_ptr[j]; e < use_ptr[j + 1]; ++e) {
+    const uint32_t u = use_ent[e];
+    const uint32_t id = u & ((1u << 28) - 1);
+    const R x = (u >> 31) ? vbar[(long long)c * ld + id] : tbar[(long long)c * nt + id];
+    acc += ((u >> 30) & 1u) ? x : w[(u >> 28) & 3u] * x;
+  }
+  vbar[(long long)c * ld + j] = acc;
 }
 
 // samples: (rho~, u, factor (f - f^eq)) of the pulled state of a parent or
@@ -907,25 +905,25 @@ cudaError_t launch_adj_coalesce(int storage, const PatchDev& child, const void* 
 }
 
 cudaError_t launch_adj_explode(int storage, const PatchDev& child, const void* lam_new_c, const uint32_t* ex_node,
-                               const uint32_t* ex_src, int64_t n_one, int64_t n, const void* val, void* vbar,
+                               const uint32_t* ex_src, int64_t n_one, int64_t n, const void* val, void* tbar,
                                int64_t ld, double beta_c, int lbgk, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   return adj_dispatch(storage, [&](auto z) {
     using R = decltype(z);
     k_adj_explode<R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(child, (const R*)lam_new_c, ex_node,
                                                                   (const uint4*)ex_src, n_one, n, (const R*)val,
-                                                                  (R*)vbar, ld, (R)beta_c, lbgk);
+                                                                  (R*)tbar, ld, (R)beta_c, lbgk);
     return cudaGetLastError();
   });
 }
 
-cudaError_t launch_adj_points(int storage, const uint32_t* pt_src, int64_t n, void* vbar, int64_t ld, int64_t out0,
-                              cudaStream_t st) {
-  if (n == 0) return cudaSuccess;
+cudaError_t launch_adj_gather(int storage, const uint32_t* use_ptr, const uint32_t* use_ent, int64_t j0, int64_t j1,
+                              void* vbar, int64_t ld, const void* tbar, int64_t nt, cudaStream_t st) {
+  if (j1 <= j0) return cudaSuccess;
   return adj_dispatch(storage, [&](auto z) {
     using R = decltype(z);
-    k_adj_points<R><<<dim3((unsigned)((n + 127) / 128), 31), 128, 0, st>>>((const uint4*)pt_src, n, (R*)vbar, ld,
-                                                                          out0);
+    k_adj_gather<R><<<dim3((unsigned)((j1 - j0 + 127) / 128), 31), 128, 0, st>>>(use_ptr, use_ent, j0, j1, (R*)vbar,
+                                                                                 ld, (const R*)tbar, nt);
     return cudaGetLastError();
   });
 }

@@ -624,6 +624,8 @@ lbm_status lbm_grid_bind(lbm_grid_t g, void* dev_ptr, size_t bytes, void* cuda_s
     if (!e) e = up(p.off_ex_node, p.ex_node.data(), 4 * p.ex_node.size());
     if (!e) e = up(p.off_ex_src, p.ex_src.data(), 4 * p.ex_src.size());
     if (!e) e = up(p.off_pt_src, p.pt_src.data(), 4 * p.pt_src.size());
+    if (!e) e = up(p.off_use_ptr, p.use_ptr.data(), 4 * p.use_ptr.size());
+    if (!e) e = up(p.off_use_ent, p.use_ent.data(), 4 * p.use_ent.size());
     if (!e) e = up(p.off_smp_node, p.smp_node.data(), 4 * p.smp_node.size());
     if (!e) e = up(p.off_smp_kind, p.smp_kind.data(), p.smp_kind.size());
     if (!e) e = up(p.off_cf_parent, p.cf_parent.data(), 4 * p.cf_parent.size());
@@ -1043,6 +1045,7 @@ lbm_status adjoint_supported(lbm_grid* g) {
 struct AdjLayout {
   std::vector<size_t> lam_off;   // per patch, in the packed lambda (and in the second buffer)
   std::vector<size_t> sbar_off;  // per patch (children), in the workspace
+  std::vector<size_t> tbar_off;  // per patch (children): the explode targets' adjoints [31][targets]
   std::vector<size_t> snap_patch_off;   // per patch, within an outer snapshot
   std::vector<size_t> inner_patch_off;  // per patch of level >= 1, within an inner snapshot
   // per patch and instant k: offset of the reconstruction values recorded when
@@ -1070,6 +1073,7 @@ AdjLayout adjoint_layout(const lbm_grid* g, int K) {
   };
   a.second_off = take(a.lam_bytes);
   for (auto& p : g->hg.P) a.sbar_off.push_back(take(31 * p.n_points() * rb));
+  for (auto& p : g->hg.P) a.tbar_off.push_back(take(31 * p.ex_node.size() * rb));
   a.snap_bytes = 0;
   for (auto& p : g->hg.P) {
     a.snap_patch_off.push_back(a.snap_bytes);
@@ -1292,17 +1296,20 @@ lbm_status adjoint_instant(lbm_grid* g, int k, uint8_t* lam[2], std::vector<int>
     const lbmk::PatchDev qv = view(g, q);
     uint8_t* sbar = ws + a.sbar_off[pi];
     const int64_t ns = (int64_t)p.smp_node.size(), ld = (int64_t)p.n_points();
-    const uint32_t* psrc = at<uint32_t>(g, p.off_pt_src);
     // the reconstruction values of this explode, recorded by the recompute
     const uint8_t* val = step + a.smp_rec_off[pi][k];
-    if (!e && ld) e = cudaMemsetAsync(sbar, 0, 31 * (size_t)ld * rb, sx);
+    uint8_t* tbar = ws + a.tbar_off[pi];
+    const int64_t nt = (int64_t)p.ex_node.size(), n1 = p.n_pt[0], n2 = p.n_pt[1];
+    const uint32_t* uptr = at<uint32_t>(g, p.off_use_ptr);
+    const uint32_t* uent = at<uint32_t>(g, p.off_use_ent);
     if (!e)
       e = lbmk::launch_adj_explode(storage, pv, lam_ptr(pi, lcur[pi]), at<uint32_t>(g, p.off_ex_node),
-                                   at<uint32_t>(g, p.off_ex_src), (int64_t)p.ex_one, (int64_t)p.ex_node.size(),
-                                   val, sbar, ld, p.beta, lbgk, sx);
-    if (!e)
-      e = lbmk::launch_adj_points(storage, psrc + 4 * (size_t)p.n_pt[0], p.n_pt[1], sbar, ld, ns + p.n_pt[0], sx);
-    if (!e) e = lbmk::launch_adj_points(storage, psrc, p.n_pt[0], sbar, ld, ns, sx);
+                                   at<uint32_t>(g, p.off_ex_src), (int64_t)p.ex_one, nt, val, tbar, ld, p.beta, lbgk,
+                                   sx);
+    // the point columns, last stage first, each from its consumers
+    if (!e) e = lbmk::launch_adj_gather(storage, uptr, uent, ns + n1, ns + n1 + n2, sbar, ld, tbar, nt, sx);
+    if (!e) e = lbmk::launch_adj_gather(storage, uptr, uent, ns, ns + n1, sbar, ld, tbar, nt, sx);
+    if (!e) e = lbmk::launch_adj_gather(storage, uptr, uent, 0, ns, sbar, ld, tbar, nt, sx);
     if (!e && !waited) {
       e = cudaStreamWaitEvent(sx, g->adj_sc, 0);
       if (!e) e = cudaStreamWaitEvent(sx, g->adj_cf, 0);

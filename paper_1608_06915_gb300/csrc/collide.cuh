@@ -238,9 +238,11 @@ __host__ __device__ constexpr int shear_class() {
 // exact-difference-method force f'_i += f^eq(rho, u + du) - f^eq(rho, u), and
 // the 0/0 guard gamma = 2 when <dh|dh> <= 1e-30 rho^2.  f holds deviation
 // populations f - W, the moments (rho~, rho, u) are those of f; f is replaced
-// by the post-collision deviations; returns gamma.  FM: compile-time mask of
-// the axes along which du may be nonzero (0: no force).  beta and du are the
-// same for every node of V (a pair of nodes shares its patch).
+// by the post-collision deviations; returns gamma.  With DF, f holds df itself
+// on entry (a state assembled as f^eq(rho, u) + df, whose df is known).  FM:
+// compile-time mask of the axes along which du may be nonzero (0: no force).
+// beta and du are the same for every node of V (a pair of nodes shares its
+// patch).
 //
 // Every per-direction quantity is a product of per-axis factors, so the loops
 // read small tables: q_i from (1 + q_xy)(1 + d_z) - 1, rho W_i from the four
@@ -248,7 +250,7 @@ __host__ __device__ constexpr int shear_class() {
 // (c_x, c_y) pair, the entropic weights 1/f^eq_i as 1/(g_x g_y) per column
 // times 1/(rho g_z) per layer.  The tables of f^eq are built twice (before
 // and after gamma) rather than held, which keeps few values live.
-template <typename V, int FM>
+template <typename V, int FM, bool DF = false>
 __device__ __forceinline__ V kbc_collide_v(V (&f)[27], V rho_t, V rho, V ux, V uy, V uz, V beta, V dux, V duy,
                                            V duz, bool du_x, bool du_y, bool du_z, bool lbgk) {
   AxisV<V> ex, ey, ez;
@@ -258,7 +260,7 @@ __device__ __forceinline__ V kbc_collide_v(V (&f)[27], V rho_t, V rho, V ux, V u
   // f^eq_i - W_i = W_i (rho~ + rho q_i), q_i = (1 + q_xy)(1 + d_z) - 1, from
   // the per-axis deviations; f becomes df = f - f^eq
   constexpr double WK[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
-  {
+  if constexpr (!DF) {
     V wr[4], wrt[4], qxy[3][3];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -407,14 +409,15 @@ struct CollideType<float> {
   using V = F1;
 };
 
-template <typename R, int FM>
+// DF: f holds df = f - f^eq(rho, u) on entry (kbc_collide_v).
+template <typename R, int FM, bool DF = false>
 __device__ __forceinline__ R kbc_collide_m(R (&f)[27], R rho_t, R rho, R ux, R uy, R uz, R beta, R dux, R duy,
                                            R duz, bool lbgk) {
   using V = typename CollideType<R>::V;
   V fv[27];
   unroll<27>([&](auto I) { fv[decltype(I)::value] = V(f[decltype(I)::value]); });
-  const V g = kbc_collide_v<V, FM>(fv, V(rho_t), V(rho), V(ux), V(uy), V(uz), V(beta), V(dux), V(duy), V(duz),
-                                   dux != R(0), duy != R(0), duz != R(0), lbgk);
+  const V g = kbc_collide_v<V, FM, DF>(fv, V(rho_t), V(rho), V(ux), V(uy), V(uz), V(beta), V(dux), V(duy),
+                                       V(duz), dux != R(0), duy != R(0), duz != R(0), lbgk);
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if constexpr (std::is_same<V, R>::value) f[i] = fv[i];

@@ -287,14 +287,14 @@ __device__ __forceinline__ R returning(const PatchDev& p, const S* __restrict__ 
   if (q < R(0.5)) {
     int b[3];
     bool ok = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    unroll<3>([&](auto A) {
+      constexpr int a = decltype(A)::value;
       b[a] = X[a] + c[a];
       if (b[a] < 0 || b[a] >= p.dim[a]) {
         if (p.span[a]) b[a] += b[a] < 0 ? p.dim[a] : -p.dim[a];
         else ok = false;
       }
-    }
+    });
     long long bi = 0;
     if (ok) {
       bi = node_index(p, b[0], b[1], b[2]);
@@ -317,19 +317,27 @@ __device__ __forceinline__ R returning(const PatchDev& p, const S* __restrict__ 
 // outlet (source clamped to the last node), periodic wrap on spanned axes.
 // A source that resolves to no node sets bit 0 of *status and falls back to
 // bounce-back (never produced by a validated layout).
-template <typename S, typename R>
+// TWO: in two passes, so that the loads of each pass are independent of each
+// other -- first every source node (or the bounce rule) and its class, then
+// the populations: two memory round trips for the node instead of up to one
+// per population, for the kernels whose few nodes leave the GPU waiting on
+// latency (the fix-up nodes); at the cost of registers, which throughput
+// kernels keep for occupancy.
+template <typename S, typename R, bool TWO = false>
 __device__ __forceinline__ void pull_generic(const PatchDev& p, const S* __restrict__ fin, int x, int y, int z,
                                              R (&f)[27], int* status) {
   const long long own = node_index(p, x, y, z);
   const int X[3] = {x, y, z};
   const int wk = p.wq_idx ? p.wq_idx[own] : -1;  // this node's row of wall fractions
-  unroll<27>([&](auto I) {
+  constexpr int kBounce = 0x100, kBad = 0x200;
+  // the source of population i (or the bounce rule) and its class
+  auto source = [&](auto I, long long& src) -> int {
     constexpr int i = decltype(I)::value;
     constexpr int c[3] = {CX(i), CY(i), CZ(i)};
     int s[3];
     bool bounce = false, bad = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    unroll<3>([&](auto A) {
+      constexpr int a = decltype(A)::value;
       s[a] = X[a] - c[a];
       if (s[a] < 0 || s[a] >= p.dim[a]) {
         if (p.span[a]) {
@@ -350,23 +358,34 @@ __device__ __forceinline__ void pull_generic(const PatchDev& p, const S* __restr
           bad = true;
         }
       }
-    }
-    long long src = own;
-    bool solid = false;
-    if (!bounce && !bad) {
-      src = node_index(p, s[0], s[1], s[2]);
-      const uint8_t t = p.type[src];
-      if (t == T_SOLID) bounce = solid = true;
-      else if (t == T_SKIP) bad = true;
-    }
-    if (bad) {
-      atomicOr(status, 1);
-      bounce = true;
-    }
+    });
+    src = own;
+    if (bad) return kBad;
+    if (bounce) return kBounce;
+    src = node_index(p, s[0], s[1], s[2]);
+    return p.type[src];
+  };
+  // population i from its source class
+  auto take = [&](auto I, int t, long long src) {
+    constexpr int i = decltype(I)::value;
+    const bool solid = t == T_SOLID, bad = t == kBad || t == T_SKIP;
+    if (bad) atomicOr(status, 1);
     if (solid && wk >= 0) f[i] = returning<i, S, R>(p, fin, own, X, R(p.wq[27 * wk + 26 - i]), false, R(0));
-    else if (bounce) f[i] = Stor<S>::ld(fin + (long long)(26 - i) * p.plane + own);
+    else if (solid || bad || t == kBounce) f[i] = Stor<S>::ld(fin + (long long)(26 - i) * p.plane + own);
     else f[i] = Stor<S>::ld(fin + (long long)i * p.plane + src);
-  });
+  };
+  if constexpr (TWO) {
+    long long src[27];
+    int cls[27];
+    unroll<27>([&](auto I) { cls[decltype(I)::value] = source(I, src[decltype(I)::value]); });
+    unroll<27>([&](auto I) { take(I, cls[decltype(I)::value], src[decltype(I)::value]); });
+  } else {
+    unroll<27>([&](auto I) {
+      long long src;
+      const int t = source(I, src);
+      take(I, t, src);
+    });
+  }
 }
 
 }  // namespace lbmk

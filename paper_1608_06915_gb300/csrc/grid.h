@@ -70,6 +70,12 @@ struct HostPatch {
   uint32_t ex_one = 0;              // targets [0, ex_one) read one point, the rest interpolate four
   std::vector<uint32_t> pt_src;     // 4 point ids per intermediate point (stage 1, then stage 2)
   uint32_t n_pt[2] = {0, 0};        // intermediate points per stage
+  // the transpose of ex_src and pt_src, for the adjoint: for each point
+  // column j, use_ent[use_ptr[j] .. use_ptr[j + 1]) lists the consumers that
+  // read it, each a target or a point id (bit 31 set: point) with its weight
+  // (bit 30 set: weight 1, a one-point target; else bits 28-29 the source slot
+  // of the four-point rule), in target order, then point order
+  std::vector<uint32_t> use_ptr, use_ent;
   std::vector<uint32_t> smp_node;   // per sample: node index in parent or child
   std::vector<uint8_t> smp_kind;    // per sample: S_PARENT / S_CHILD
   std::vector<uint32_t> cf_parent;  // coalesce: parent twin node
@@ -86,7 +92,7 @@ struct HostPatch {
   // device placement (byte offsets into the bound buffer)
   size_t off_f[2]{}, off_g[2]{}, off_type = 0;
   size_t off_tiles_pure[2]{}, off_tiles_mixed[2]{}, off_tiles_all[2]{}, off_fix_nodes[2]{};
-  size_t off_ex_node = 0, off_ex_src = 0, off_pt_src = 0;
+  size_t off_ex_node = 0, off_ex_src = 0, off_pt_src = 0, off_use_ptr = 0, off_use_ent = 0;
   size_t off_smp_node = 0, off_smp_kind = 0, off_smp_val = 0, off_cf_parent = 0, off_cf_child = 0;
   size_t off_drag_node = 0, off_drag_mask = 0, off_wq = 0, off_wq_idx = 0;
   int cur = 0;  // which population buffer holds the current state

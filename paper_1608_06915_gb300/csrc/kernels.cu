@@ -211,9 +211,12 @@ cudaError_t launch_points(int storage, int ncomp, const uint32_t* pt_src, int64_
 }
 
 // Child twins and reconstruction nodes: the last interpolation pass (or the
-// point itself), f = f^eq(rho~, u~) + neq~, then collide.  Targets
-// [0, n_one) read one point, the others interpolate four; a thread block
-// takes targets of one kind only.
+// point itself), f = f^eq(rho~, u~) + neq~, then collide.  The collision
+// starts from df = neq~ and the moments (rho~, u~) directly: f^eq(rho~, u~) +
+// neq~ has these moments (the product-form equilibrium carries the node's mass
+// and momentum exactly, and neq~ interpolates states without any), so its
+// df is neq~ up to rounding.  Targets [0, n_one) read one point, the others
+// interpolate four; a thread block takes targets of one kind only.
 template <int K, typename S, typename R, int FM>
 __device__ __forceinline__ void explode_node(const PatchDev& pc, S* __restrict__ fout_c,
                                              const uint32_t* __restrict__ ex_node, const uint4* __restrict__ ex_src,
@@ -241,18 +244,12 @@ __device__ __forceinline__ void explode_node(const PatchDev& pc, S* __restrict__
       f[i] = ip(4 + i);
     });
   }
-  R fe[27];
-  feq_dev(m[0], R(1) + m[0], m[1], m[2], m[3], fe);
-  unroll<27>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    f[i] += fe[i];
-  });
-  kbc_collide<R, FM>(f, beta_c, dux, duy, duz, lbgk != 0);
+  kbc_collide_m<R, FM, true>(f, m[0], R(1) + m[0], m[1], m[2], m[3], beta_c, dux, duy, duz, lbgk != 0);
   store_node<S, R>(pc, fout_c, __ldg(ex_node + k), f);
 }
 
 template <typename S, typename R, int FM>
-__global__ void __launch_bounds__(128, 5) k_explode(PatchDev pc, S* __restrict__ fout_c,
+__global__ void __launch_bounds__(128, 6) k_explode(PatchDev pc, S* __restrict__ fout_c,
                                                  const uint32_t* __restrict__ ex_node,
                                                  const uint4* __restrict__ ex_src, long long n_one, long long n,
                                                  unsigned blocks_one, const R* __restrict__ val, long long ld,

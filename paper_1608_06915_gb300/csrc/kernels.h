@@ -72,12 +72,17 @@ cudaError_t launch_adj_coalesce(int storage, const PatchDev& child, const void* 
                                 const uint32_t* cf_child, int64_t n, double r, double beta_p, int lbgk, int* status,
                                 cudaStream_t st);
 // vbar [31][ld]: adjoint of the point-space values (accumulated with atomics)
+// the explode adjoint writes, per target k, the adjoint of its 31
+// interpolated values to tbar[c][k] (c < 31, n targets)
 cudaError_t launch_adj_explode(int storage, const PatchDev& child, const void* lam_new_c, const uint32_t* ex_node,
-                               const uint32_t* ex_src, int64_t n_one, int64_t n, const void* val, void* vbar,
+                               const uint32_t* ex_src, int64_t n_one, int64_t n, const void* val, void* tbar,
                                int64_t ld, double beta_c, int lbgk, cudaStream_t st);
-// transpose of launch_points: vbar[c][src[4q + k]] += w_k vbar[c][out0 + q]
-cudaError_t launch_adj_points(int storage, const uint32_t* pt_src, int64_t n, void* vbar, int64_t ld, int64_t out0,
-                              cudaStream_t st);
+// transpose of the interpolation in gather form: vbar[c][j] for columns j in
+// [j0, j1) = sum over the consumers of column j (use_ptr, use_ent) of their
+// weight times tbar[c][target] or vbar[c][point]; the consumers of a stage
+// must be done first (stage 2, then stage 1, then the samples)
+cudaError_t launch_adj_gather(int storage, const uint32_t* use_ptr, const uint32_t* use_ent, int64_t j0, int64_t j1,
+                              void* vbar, int64_t ld, const void* tbar, int64_t nt, cudaStream_t st);
 cudaError_t launch_adj_samples(int storage, const PatchDev& parent, const void* fin_p, void* lam_p,
                                const PatchDev& child, const void* fin_c, void* lam_c, const uint32_t* smp_node,
                                const uint8_t* smp_kind, int64_t ns, const void* sbar, int64_t ld, double rescale_p,

@@ -792,6 +792,27 @@ std::string build_layout(HostGrid& g) {
         for (int k = 0; k < 4; ++k) c.ex_src.push_back(one && k > 0 ? 0u : final_id(tsrc[4 * e + k]));
       }
     }
+    // consumers of each point column (the transpose of the two tables), by
+    // counting sort: targets first, then points, each in index order
+    {
+      const size_t np = c.n_points(), nt = c.ex_node.size(), nq = (size_t)c.n_pt[0] + c.n_pt[1];
+      c.use_ptr.assign(np + 1, 0);
+      for (size_t k = 0; k < nt; ++k)
+        for (int j = 0; j < (k < c.ex_one ? 1 : 4); ++j) ++c.use_ptr[c.ex_src[4 * k + j] + 1];
+      for (size_t q = 0; q < nq; ++q)
+        for (int j = 0; j < 4; ++j) ++c.use_ptr[c.pt_src[4 * q + j] + 1];
+      for (size_t j = 0; j < np; ++j) c.use_ptr[j + 1] += c.use_ptr[j];
+      c.use_ent.assign(c.use_ptr[np], 0);
+      std::vector<uint32_t> fill(c.use_ptr.begin(), c.use_ptr.end() - 1);
+      for (size_t k = 0; k < nt; ++k) {
+        const bool one = k < c.ex_one;
+        for (int j = 0; j < (one ? 1 : 4); ++j)
+          c.use_ent[fill[c.ex_src[4 * k + j]]++] = (uint32_t)k | (one ? (1u << 30) : ((uint32_t)j << 28));
+      }
+      for (size_t q = 0; q < nq; ++q)
+        for (int j = 0; j < 4; ++j)
+          c.use_ent[fill[c.pt_src[4 * q + j]]++] = (uint32_t)(ns + q) | (1u << 31) | ((uint32_t)j << 28);
+    }
     // coalesce pairs: parent twins x_t,cf and the coinciding child node
     int64_t X[3];
     for (int64_t n = 0; n < par.plane; ++n) {
@@ -846,6 +867,8 @@ size_t plan_memory(HostGrid& g) {
     p.off_ex_node = take(4 * p.ex_node.size());
     p.off_ex_src = take(4 * p.ex_src.size());
     p.off_pt_src = take(4 * p.pt_src.size());
+    p.off_use_ptr = take(4 * p.use_ptr.size());
+    p.off_use_ent = take(4 * p.use_ent.size());
     p.off_smp_node = take(4 * p.smp_node.size());
     p.off_smp_kind = take(p.smp_kind.size());
     p.off_smp_val = take(ncomp * p.n_points() * g.real_bytes);

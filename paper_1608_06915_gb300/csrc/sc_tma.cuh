@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(128) k_sc_tiles(PatchDev p, const S* __restric
   if (!(ty == T_BULK || ty == T_BC || (ty == T_D1 && odd))) return;
   R f[27];
   if (ty == T_BULK) pull_bulk<S, R>(p, fin, x, y, z, f);
-  else pull_generic<S, R>(p, fin, x, y, z, f, status);
+  else pull_generic<S, R, true>(p, fin, x, y, z, f, status);
   kbc_collide<R, FM>(f, beta, dux, duy, duz, lbgk != 0);
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(128) k_sc_nodes(PatchDev p, const S* __restric
   const int x = (int)(own % p.nxp), y = (int)((own / p.nxp) % p.dim[1]);
   const int z = (int)(own / ((long long)p.nxp * p.dim[1]));
   R f[27];
-  pull_generic<S, R>(p, fin, x, y, z, f, status);
+  pull_generic<S, R, true>(p, fin, x, y, z, f, status);
   kbc_collide<R, FM>(f, beta, dux, duy, duz, lbgk != 0);
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
