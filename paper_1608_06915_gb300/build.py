@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
 SOURCES = ["layout.cpp", "kernels.cu", "sc_tma.cu", "sc_tma_fp32.cu", "sc_tma_fp64.cu", "sc_tma_fp16.cu", "sc_tma_bf16.cu", "thermal.cu", "thermal_tma.cu", "adjoint.cu", "api.cu"]
-HEADERS = ["grid.h", "device.cuh", "collide.cuh", "kernels.h", "sc_tma.cuh", "thermal.cuh"]
+HEADERS = ["grid.h", "device.cuh", "collide.cuh", "kernels.h", "sc_tma.cuh", "thermal.cuh", "warp.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

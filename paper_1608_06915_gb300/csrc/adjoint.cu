@@ -4,9 +4,12 @@
 // Every forward kernel maps the previous states (pulled) to the nodes it
 // writes; its adjoint takes the adjoint of those nodes (lambda_new), recomputes
 // the forward pre-collision state from the restored previous state, applies
-// the transposed Jacobian of the node map and scatters the result back along
-// the pull (a push: lambda_old[x - c_i][i] += ...).  Scatters that several
-// kernels share (sample nodes, coalesce sources) accumulate with atomic adds.
+// the transposed Jacobian of the node map and sends the result back along the
+// pull (a push to lambda_old[x - c_i][i]).  Each entry of lambda_old has one
+// puller, so it takes one store from the stream-collide adjoint and at most
+// one addition from a coupling adjoint, in stream order; the transposed
+// interpolation gathers over fixed consumer lists.  Results do not depend on
+// scheduling.
 //
 // Vector-Jacobian products used here (all per node, in registers):
 //   * KBC collision f' = f^eq + (1 - beta gamma) df + beta (gamma - 2) ds with
@@ -24,6 +27,7 @@
 #include "../../include/lbm.h"
 #include "device.cuh"
 #include "kernels.h"
+#include "warp.cuh"
 
 namespace lbmk {
 
@@ -410,40 +414,6 @@ __device__ __forceinline__ void pull_node(const PatchDev& p, const R* __restrict
 // lanes 27..31 hold zeros, and every sum over the populations is a butterfly
 // reduction across the warp.
 
-constexpr unsigned kFullMask = 0xffffffffu;
-
-// Sums over the warp of N values at once (the N butterflies interleaved).
-template <int N, typename R>
-__device__ __forceinline__ void wsum(R (&v)[N]) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int j = 0; j < N; ++j) v[j] += __shfl_xor_sync(kFullMask, v[j], o);
-  }
-}
-
-template <typename R>
-__device__ __forceinline__ R sel3(int c, const R (&a)[3]) {
-  return c < 0 ? a[0] : (c == 0 ? a[1] : a[2]);
-}
-
-// The lane's direction: idle lanes take the rest direction (finite
-// equilibrium values) and are masked out of every sum and store.
-struct Lane {
-  int i, c[3], na;  // direction, velocity, number of non-zero components
-  bool on;
-};
-
-__device__ __forceinline__ Lane lane_dir() {
-  Lane d;
-  const int l = threadIdx.x & 31;
-  d.on = l < 27;
-  d.i = d.on ? l : 13;
-  d.c[0] = d.i % 3 - 1, d.c[1] = (d.i / 3) % 3 - 1, d.c[2] = d.i / 9 - 1;
-  d.na = (d.c[0] != 0) + (d.c[1] != 0) + (d.c[2] != 0);
-  return d;
-}
-
 // Equilibrium quantities of one node, the lane's share: f^eq - W and f^eq of
 // its direction and the log-derivatives L_a(c_ia) of its axis factors.
 template <typename R>
@@ -647,9 +617,6 @@ __device__ __forceinline__ void push_one(const PatchDev& p, R* __restrict__ lam_
   else atomicAdd(lam_old + (long long)d.i * p.plane + node_index(p, s[0], s[1], s[2]), v);
 }
 
-__device__ __forceinline__ long long warp_id() {
-  return ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-}
 
 // coalesce: parent twin <- collide_parent(f^eq + r (f_child - f^eq)); one warp per twin
 template <typename R>
@@ -676,7 +643,7 @@ __global__ void __launch_bounds__(128) k_adj_coalesce(PatchDev pc, const R* __re
 
 // explode: child node <- collide_child(f^eq(rho~, u~) + neq~), (rho~, u~, neq~)
 // one point of the reconstruction point space or the four-point interpolation
-// of four; scatters the adjoint of the 31 values into vbar [31][ld].  One
+// of four; writes the adjoint of the 31 values to tbar [31][targets].  One
 // thread per node: the explode set is large enough (about ten thousand nodes)
 // that a warp per node would be bound by instruction issue.
 template <typename R>

@@ -365,11 +365,13 @@ __device__ __forceinline__ void pull_generic(const PatchDev& p, const S* __restr
     src = node_index(p, s[0], s[1], s[2]);
     return p.type[src];
   };
-  // population i from its source class
+  // population i from its source class; an unresolved source is reported
+  // once, after the loads (an atomic between them would order them)
+  bool any_bad = false;
   auto take = [&](auto I, int t, long long src) {
     constexpr int i = decltype(I)::value;
     const bool solid = t == T_SOLID, bad = t == kBad || t == T_SKIP;
-    if (bad) atomicOr(status, 1);
+    any_bad |= bad;
     if (solid && wk >= 0) f[i] = returning<i, S, R>(p, fin, own, X, R(p.wq[27 * wk + 26 - i]), false, R(0));
     else if (solid || bad || t == kBounce) f[i] = Stor<S>::ld(fin + (long long)(26 - i) * p.plane + own);
     else f[i] = Stor<S>::ld(fin + (long long)i * p.plane + src);
@@ -386,6 +388,7 @@ __device__ __forceinline__ void pull_generic(const PatchDev& p, const S* __restr
       take(I, t, src);
     });
   }
+  if (any_bad) atomicOr(status, 1);
 }
 
 }  // namespace lbmk

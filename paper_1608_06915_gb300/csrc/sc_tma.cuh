@@ -47,6 +47,7 @@
 #include "collide.cuh"
 #include "device.cuh"
 #include "kernels.h"
+#include "warp.cuh"
 
 namespace lbmk {
 
@@ -235,6 +236,7 @@ __device__ __forceinline__ constexpr int row_base(int i) {
 // their tile lists; each tile carries its patch's tensor maps, geometry,
 // relaxation and force.
 constexpr int kTmaBatch = 8;  // patches per launch
+constexpr long long kWarpNodes = 152 * 4 * 128;  // fix-up lists up to this size go one warp per node
 
 template <typename S, typename R>
 struct TmaPatch {
@@ -680,6 +682,26 @@ __global__ void __launch_bounds__(128) k_sc_nodes(PatchDev p, const S* __restric
   });
 }
 
+// Fix-up nodes, one warp per node (warp.cuh): for the few thousand fix-up
+// nodes around a solid body, where the few warps of a thread-per-node launch
+// would wait on the instruction fetch of its long unrolled code.
+template <typename S, typename R>
+__global__ void __launch_bounds__(128) k_sc_nodes_w(PatchDev p, const S* __restrict__ fin, S* __restrict__ fout,
+                                                    const uint32_t* __restrict__ nodes, long long n, R beta, R dux,
+                                                    R duy, R duz, int lbgk, int* status) {
+  const long long k = warp_id();
+  if (k >= n) return;  // whole warp
+  const Lane d = lane_dir();
+  const long long own = nodes[k];
+  const int x = (int)(own % p.nxp), y = (int)((own / p.nxp) % p.dim[1]);
+  const int z = (int)(own / ((long long)p.nxp * p.dim[1]));
+  bool bad = false;
+  const R f = d.on ? wpull_generic<S, R>(p, fin, x, y, z, d, bad) : R(0);
+  if (__any_sync(kFullMask, bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1);
+  const R fo = wkbc_collide<R>(f, d, beta, dux, duy, duz, lbgk != 0);
+  if (d.on) Stor<S>::st(fout + (long long)d.i * p.plane + own, fo);
+}
+
 template <typename S, typename R, int FM, int V>
 cudaError_t launch_tma_v(const TmaBatch<S, R>& b, cudaStream_t st) {
   constexpr int DI = TmaVariants<S>::DI[V], MINB = TmaVariants<S>::MINB[V];
@@ -788,6 +810,12 @@ cudaError_t sc_nodes_typed(const PatchDev& p, const void* fin, void* fout, const
   const unsigned grid = (unsigned)((n + 127) / 128);
   const S* in = (const S*)fin;
   S* out = (S*)fout;
+  // up to this many nodes a thread per node leaves the SMs nearly empty
+  // (fewer than four blocks of 128 per SM): one warp per node instead
+  if (n <= kWarpNodes) {
+    k_sc_nodes_w<S, R><<<(unsigned)((n + 3) / 4), 128, 0, st>>>(p, in, out, nodes, n, b, dx, dy, dz, lbgk, status);
+    return cudaGetLastError();
+  }
   switch (F.mask()) {
     case 0:
       k_sc_nodes<S, R, 0><<<grid, 128, 0, st>>>(p, in, out, nodes, n, b, dx, dy, dz, lbgk, status);

@@ -210,7 +210,7 @@ __device__ __forceinline__ void pull_generic_th(const PatchDev& p, const R* __re
   const int X[3] = {x, y, z};
   const int wk = p.wq_idx ? p.wq_idx[own] : -1;  // this node's row of wall fractions
   R rho_own_t = 0;
-  bool have_rho = false;
+  bool have_rho = false, any_bad = false;  // an unresolved source is reported once, after the loads
   unroll<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr int c[3] = {CX(i), CY(i), CZ(i)};
@@ -252,7 +252,7 @@ __device__ __forceinline__ void pull_generic_th(const PatchDev& p, const R* __re
       else if (t == T_SKIP) bad = true;
     }
     if (bad) {
-      atomicOr(status, 1);
+      any_bad = true;
       bounce = true;
     }
     if (bounce) {
@@ -282,6 +282,7 @@ __device__ __forceinline__ void pull_generic_th(const PatchDev& p, const R* __re
       g[i] = gin[(long long)i * p.plane + src];
     }
   });
+  if (any_bad) atomicOr(status, 1);
 }
 
 template <typename R>
