@@ -165,6 +165,29 @@ def test_sphere_storage_error(storage, bound):
     assert er < bound and eu < bound
 
 
+@pytest.mark.parametrize("nsolid", [40, 6000])
+def test_fixup_nodes_both_kernels_fp64(nsolid):
+    """Fix-up nodes next to scattered solid nodes in a periodic box with a
+    body force: a few hundred of them run one warp per node, tens of
+    thousands (above the warp path's limit of 77,824 in all, counted over the
+    layout's fix-up list) run a thread per node; populations against the
+    oracle after every step."""
+    rng = np.random.default_rng(7 if nsolid < 100 else 8)
+    n = (96, 96, 48) if nsolid > 100 else (32, 16, 16)
+    mask = np.zeros((n[2], n[1], n[0]), dtype=np.uint8)
+    idx = rng.choice(mask.size, size=nsolid, replace=False)
+    mask.reshape(-1)[idx] = 1
+    case = dict(name="porous", n=n, periodic=(1, 1, 1), walls=(0,) * 6, inflow_axis=-1, u_in=(0, 0, 0), boxes=[],
+                solid=dict(level=0, lo=(0, 0, 0), mask=mask), nu0=0.02, accel0=(1e-5, 0, 0), mirror_lbgk=False,
+                thermal=None)
+    g, o = twin(case, "fp64", lambda x, y, z, p, info: I.uniform_fields(x, (0.03, 0.01, 0.0)))
+    for s in range(2):
+        g.step(1)
+        o.step(1)
+        d = pop_diff(g, o)
+        assert d < 1e-12, (s, d)
+
+
 def test_drag_is_the_momentum_the_fluid_loses_on_gpu():
     """Periodic box with a solid ball, one level, FP64: the drag of the state a
     step starts from is the fluid momentum that step loses (diagnostics)."""
