@@ -249,7 +249,7 @@ __device__ __forceinline__ void explode_node(const PatchDev& pc, S* __restrict__
 }
 
 template <typename S, typename R, int FM>
-__global__ void __launch_bounds__(128, 6) k_explode(PatchDev pc, S* __restrict__ fout_c,
+__global__ void __launch_bounds__(128, 7) k_explode(PatchDev pc, S* __restrict__ fout_c,
                                                  const uint32_t* __restrict__ ex_node,
                                                  const uint4* __restrict__ ex_src, long long n_one, long long n,
                                                  unsigned blocks_one, const R* __restrict__ val, long long ld,
