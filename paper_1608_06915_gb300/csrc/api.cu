@@ -1098,7 +1098,8 @@ AdjLayout adjoint_layout(const lbm_grid* g, int K) {
     a.smp_rec_off.push_back(offs);
   }
   a.step_bytes = (rec + 255) / 256 * 256;
-  a.snap_off = take(a.step_bytes * (size_t)K);
+  // K records, then the outer snapshot that the last step writes for a next one
+  a.snap_off = take(a.step_bytes * (size_t)K + a.snap_bytes);
   a.slot_off = take(2 * sizeof(unsigned long long));  // the record's base word, then the copy-completion count
   a.partial_off = take(sizeof(double) * (kDiagBlocks * g->hg.P.size() + 1));
   a.total = w;
@@ -1142,13 +1143,8 @@ lbm_status recording_step(lbm_grid* g, const AdjLayout& a, unsigned long long* s
     segs.n = 0;
     segs.done = nullptr;
   };
-  // outer snapshot: every patch at the step's start
-  for (size_t pi = 0; pi < g->hg.P.size(); ++pi) {
-    const HostPatch& p = g->hg.P[pi];
-    add(a.snap_patch_off[pi], g->base + p.off_f[p.cur], 27 * (size_t)p.plane * g->hg.pop_bytes);
-  }
-  flush(false);
-  if (e) return cuda_check(g, e, "adjoint snapshot");
+  // (the outer snapshot of this step, every patch at the step's start, was
+  // taken with the previous step's last copy, or before the first step)
   for (int k = 1; k <= KI; ++k) {
     if (lbm_status st = run_instant(g, k)) return st;
     // the reconstruction values of the children that exploded at k
@@ -1166,9 +1162,34 @@ lbm_status recording_step(lbm_grid* g, const AdjLayout& a, unsigned long long* s
     if (k < KI) flush(false);
     if (e) return cuda_check(g, e, "adjoint snapshot");
   }
-  if (segs.n == 0) return cuda_check(g, lbmk::launch_word(slot, a.step_bytes, 1, g->stream), "adjoint snapshot slot");
+  // the outer snapshot of the next step (the state after this one), in the
+  // same launch as the last reconstruction values; it advances the base word
+  for (size_t pi = 0; pi < g->hg.P.size(); ++pi) {
+    const HostPatch& p = g->hg.P[pi];
+    add(a.step_bytes + a.snap_patch_off[pi], g->base + p.off_f[p.cur], 27 * (size_t)p.plane * g->hg.pop_bytes);
+  }
   flush(true);
   return cuda_check(g, e, "adjoint snapshot");
+}
+
+// The outer snapshot of the segment's first step, at the record's base word.
+cudaError_t first_snapshot(lbm_grid* g, const AdjLayout& a, unsigned long long* slot) {
+  lbmk::CopySegs segs{};
+  segs.rel = slot;
+  cudaError_t e = cudaSuccess;
+  for (size_t pi = 0; pi < g->hg.P.size() && !e; ++pi) {
+    if (segs.n == lbmk::kCopySegs) {
+      e = lbmk::launch_copy(segs, g->stream);
+      segs.n = 0;
+    }
+    const HostPatch& p = g->hg.P[pi];
+    segs.dst[segs.n] = reinterpret_cast<void*>(a.snap_patch_off[pi]);
+    segs.src[segs.n] = g->base + p.off_f[p.cur];
+    segs.bytes[segs.n] = 27 * (size_t)p.plane * g->hg.pop_bytes;
+    ++segs.n;
+  }
+  if (!e) e = lbmk::launch_copy(segs, g->stream);
+  return e;
 }
 
 // Copies the state of every patch to/from a packed buffer (restore: the current
@@ -1452,6 +1473,7 @@ lbm_status lbm_adjoint_step(lbm_grid_t g, const void* ckpt, int32_t K, void* lam
   // the recording step replays as one CUDA graph per buffer parity
   auto* slot = reinterpret_cast<unsigned long long*>(ws + a.slot_off);
   e = lbmk::launch_word(slot, (unsigned long long)(uintptr_t)(ws + a.snap_off), 0, g->stream);
+  if (!e) e = first_snapshot(g, a, slot);
   if (e) return cuda_check(g, e, "adjoint record");
   for (int s = 0; s < K; ++s) {
     if (!g->graphs || g->timing || !g->rec_warm) {

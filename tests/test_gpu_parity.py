@@ -529,7 +529,9 @@ def test_tma_variants_give_identical_results(storage):
             gb.step(5)
             torch.cuda.synchronize()
             for p in range(len(ga.patches)):
-                assert torch.equal(ga.get_populations(p), gb.get_populations(p)), (case["name"], v, p)
+                # the nodes of the patch (hole and solid nodes hold no state)
+                m = torch.from_numpy(ga.mask(p) == 1).cuda()
+                assert torch.equal(ga.get_populations(p)[:, m], gb.get_populations(p)[:, m]), (case["name"], v, p)
         with pytest.raises(Exception):
             gb.set_variant(nv)
 
