@@ -497,20 +497,10 @@ std::string build_layout(HostGrid& g) {
           int active[2] = {0, 0};
           bool inlet = false, outlet = false;
           std::vector<uint32_t> odd_nodes[2];  // updated nodes the row rule does not give
-          // the tile's 32-node warp segments with a node the pass must write (an
-          // updated node the row rule gives, or the fixed inlet node): the other
-          // segments hold only nodes that are not updated in the substep (holes,
-          // solid, interface) or fix-up nodes rewritten afterwards, so their warps
-          // skip the collision and the store
-          uint32_t wmask[2] = {0, 0};
           for (int64_t x = tx * 128; x < std::min<int64_t>(p.dim[0], tx * 128 + 128); ++x) {
             const int64_t m = (z * p.dim[1] + y) * p.nxp + x;
             const uint8_t t = p.type[m];
-            const uint32_t wbit = 1u << ((x - tx * 128) / 32);
-            if (t == T_INLET && d.inflow_axis == 0 && x == 0 && p.org[0] == 0) {
-              inlet = true;
-              wmask[0] |= wbit, wmask[1] |= wbit;
-            }
+            if (t == T_INLET && d.inflow_axis == 0 && x == 0 && p.org[0] == 0) inlet = true;
             bool act[2];
             act[0] = t == T_BULK || t == T_BC;
             act[1] = act[0] || t == T_D1;
@@ -526,11 +516,9 @@ std::string build_layout(HostGrid& g) {
                 else regular = o == 0;
               }
             }
-            for (int k = 0; k < 2; ++k) {
-              if (!act[k]) continue;
-              if (regular) wmask[k] |= wbit;
-              else odd_nodes[k].push_back((uint32_t)m);
-            }
+            if (!regular)
+              for (int k = 0; k < 2; ++k)
+                if (act[k]) odd_nodes[k].push_back((uint32_t)m);
           }
           const uint32_t id = (uint32_t)((z * p.dim[1] + y) * p.ntx + tx);
           // the TMA path fetches the periodic wrap of x-spanning rows as 16-byte
@@ -546,7 +534,7 @@ std::string build_layout(HostGrid& g) {
             if (wrap_ok && rule_ok && 2 * nodd <= active[k]) {
               const uint64_t fl = (inlet ? 1ull : 0ull) | (outlet ? 2ull : 0ull);
               R.pure[k].push_back((uint64_t)tx | ((uint64_t)y << 16) | ((uint64_t)z << 32) | ((uint64_t)bm << 48) |
-                                  (fl << 57) | ((uint64_t)wmask[k] << 59));
+                                  (fl << 57));
               R.fix[k].insert(R.fix[k].end(), odd_nodes[k].begin(), odd_nodes[k].end());
               R.ntma[k] += active[k] - nodd;
             } else {

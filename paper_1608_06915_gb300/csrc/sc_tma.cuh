@@ -195,11 +195,9 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 
 __device__ __forceinline__ int wrap_axis(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// tile list entries: x-tile | y << 16 | z << 32 | bounce mask << 48 | flags << 57 |
-// warp mask << 59 (flag 1: the row's first node is a fixed inlet node; flag 2:
-// its last node is the zero-gradient outlet; warp mask bit w: the w-th 32-node
-// segment holds a node the pass must write -- the others hold only nodes not
-// updated in the substep or fix-up nodes, and their warps skip the work)
+// tile list entries: x-tile | y << 16 | z << 32 | bounce mask << 48 | flags << 57
+// (flag 1: the row's first node is a fixed inlet node; flag 2: its last node
+// is the zero-gradient outlet)
 __device__ __forceinline__ void tile_xyz(unsigned long long t, int& tx, int& y, int& z) {
   tx = (int)(t & 0xffffu);
   y = (int)((t >> 16) & 0xffffu);
@@ -207,7 +205,6 @@ __device__ __forceinline__ void tile_xyz(unsigned long long t, int& tx, int& y, 
 }
 __device__ __forceinline__ int tile_bounce(unsigned long long t) { return (int)((t >> 48) & 0x1ffu); }
 __device__ __forceinline__ int tile_flags(unsigned long long t) { return (int)((t >> 57) & 3u); }
-__device__ __forceinline__ int tile_warps(unsigned long long t) { return (int)((t >> 59) & 15u); }
 
 // Shared-memory row of population i in a load stage (elements): group i / 3,
 // row i % 3 of the three-row box.
@@ -314,7 +311,7 @@ __global__ void __launch_bounds__(160, MINB) k_sc_tma(const __grid_constant__ Tm
       const int fl = tile_flags(te);
       const bool first = p.span[0] && tx == 0;
       const bool last = p.span[0] && (tx + 1) * C::BX >= p.dim[0];
-      tile_at[s] = make_int4(tx, ty, tz, bm | (fl << 9) | (ei << 11) | (tile_warps(te) << 14));
+      tile_at[s] = make_int4(tx, ty, tz, bm | (fl << 9) | (ei << 11));
       const uint32_t txw = 16u * (uint32_t)(9 - __popc(bm));  // wrap boxes of the rows not bounced
       mbar_expect_tx(&full[s], C::TX + (first ? txw : 0u) + (last ? txw : 0u));
       unsigned char* stage = smem + s * C::STAGE;
@@ -354,13 +351,7 @@ __global__ void __launch_bounds__(160, MINB) k_sc_tma(const __grid_constant__ Tm
     }
     const int4 tc = tile_at[s];
     const int tx = tc.x, y = tc.y, z = tc.z, bm = tc.w & 0x1ff, fl = (tc.w >> 9) & 3;
-    if (!((tc.w >> (14 + warp)) & 1)) {
-      // nothing this warp must write in this tile: release the stage
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
-      continue;
-    }
-    const TmaPatch<S, R>& E = b.e[(tc.w >> 11) & 7];
+    const TmaPatch<S, R>& E = b.e[tc.w >> 11];
     const PatchDev& p = E.p;
     const int x = tx * C::BX + tid;
     const S* st = reinterpret_cast<const S*>(smem + s * C::STAGE);
@@ -485,7 +476,7 @@ __device__ __forceinline__ void issue_tile(const TmaBatch<S, float>& b, int t, u
   const int fl = tile_flags(te);
   const bool first = p.span[0] && tx == 0;
   const bool last = p.span[0] && (tx + 1) * C::BX >= p.dim[0];
-  *tile_at = make_int4(tx, ty, tz, bm | (fl << 9) | (ei << 11));  // (the pair kernel computes every segment)
+  *tile_at = make_int4(tx, ty, tz, bm | (fl << 9) | (ei << 11));
   const uint32_t txw = 16u * (uint32_t)(9 - __popc(bm));  // wrap boxes of the rows not bounced
   mbar_expect_tx(full, C::TX + (first ? txw : 0u) + (last ? txw : 0u));
   unsigned char* side = stage + 9 * C::GROUP;
