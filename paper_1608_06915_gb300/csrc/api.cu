@@ -115,7 +115,16 @@ struct lbm_grid {
   cudaEvent_t fwd_fork = nullptr, fwd_join[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t fwd_pre = nullptr;  // the instant's pre-states are ready (before its TMA pass)
   std::vector<cudaEvent_t> patch_done;  // thermal model: a patch's stream-collide has been issued
+  // the adjoint's recording step: its snapshot copies run on rec_side beside
+  // the instants; rec_ev[k] marks instant k issued, rec_cp[k] copy k done
+  cudaStream_t rec_side = nullptr;
+  std::vector<cudaEvent_t> rec_ev, rec_cp;
   ~lbm_grid() {
+    if (rec_side) cudaStreamDestroy(rec_side);
+    for (auto& x : rec_ev)
+      if (x) cudaEventDestroy(x);
+    for (auto& x : rec_cp)
+      if (x) cudaEventDestroy(x);
     for (auto& x : fwd_side)
       if (x) cudaStreamDestroy(x);
     if (fwd_fork) cudaEventDestroy(fwd_fork);
@@ -1098,8 +1107,9 @@ AdjLayout adjoint_layout(const lbm_grid* g, int K) {
     a.smp_rec_off.push_back(offs);
   }
   a.step_bytes = (rec + 255) / 256 * 256;
-  // K records, then the outer snapshot that the last step writes for a next one
-  a.snap_off = take(a.step_bytes * (size_t)K + a.snap_bytes);
+  // a spare record, where the first step's copy 0 puts the values of a
+  // previous step that does not exist, then the K records
+  a.snap_off = take(a.step_bytes * (size_t)(K + 1)) + a.step_bytes;
   a.slot_off = take(2 * sizeof(unsigned long long));  // the record's base word, then the copy-completion count
   a.partial_off = take(sizeof(double) * (kDiagBlocks * g->hg.P.size() + 1));
   a.total = w;
@@ -1117,17 +1127,41 @@ uint8_t* pre_state(const lbm_grid* g, const AdjLayout& a, uint8_t* step, int pi,
 }
 
 // One coarse step of the recompute, recording its snapshots through the
-// device word at `slot` (the current step's record; advanced at the end), so
-// that one captured graph serves every step of the segment.
+// device word at `slot`, so that one captured graph serves every step of the
+// segment.  The copies run on their own stream beside the instants (on the
+// bound stream under per-launch timing).  Copy 0, beside instant 1, takes the
+// previous step's last reconstruction values (instant 2^(L-1)) into the
+// previous record, then this step's outer snapshot (every patch at the step's
+// start) into the next one, and advances the word to it.  Copy k, after
+// instant k < 2^(L-1), takes the reconstruction values of instant k and inner
+// snapshot k (the levels >= 1 after instant k), beside instant k + 1.
+// Ordering: instant 1 writes neither a step-start state nor a reconstruction
+// value (no patch explodes at an odd instant), and instant k + 1 writes
+// neither the states after instant k nor the values copy k reads (a patch's
+// state buffer is rewritten at its second step after k, its values at its
+// next explode, both at k + 2 or later); so instant m waits for copy m - 2
+// only, and the step ends after its last copy.
 lbm_status recording_step(lbm_grid* g, const AdjLayout& a, unsigned long long* slot) {
   const int L = g->hg.nlev, KI = 1 << (L - 1);
+  const bool side = !g->timing;
+  cudaError_t e = cudaSuccess;
+  if (side) {
+    if (!g->rec_side) e = cudaStreamCreateWithFlags(&g->rec_side, cudaStreamNonBlocking);
+    for (auto* v : {&g->rec_ev, &g->rec_cp})
+      while (!e && v->size() < (size_t)KI + 1) {
+        cudaEvent_t x = nullptr;
+        e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+        if (!e) v->push_back(x);
+      }
+    if (e) return cuda_check(g, e, "adjoint record stream");
+  }
+  cudaStream_t cs = side ? g->rec_side : g->stream;
   lbmk::CopySegs segs{};
   segs.rel = slot;
   unsigned* done = reinterpret_cast<unsigned*>(slot + 1);  // completion count beside the word
-  cudaError_t e = cudaSuccess;
   auto add = [&](size_t off, const void* src, size_t n) {
     if (segs.n == lbmk::kCopySegs) {
-      if (!e) e = lbmk::launch_copy(segs, g->stream);
+      if (!e) e = lbmk::launch_copy(segs, cs);
       segs.n = 0;
     }
     segs.dst[segs.n] = reinterpret_cast<void*>(off);
@@ -1135,57 +1169,58 @@ lbm_status recording_step(lbm_grid* g, const AdjLayout& a, unsigned long long* s
     segs.bytes[segs.n] = n;
     ++segs.n;
   };
-  auto flush = [&](bool last) {
-    // the step's last copy advances the record's base word when it is done
-    segs.done = last ? done : nullptr;
-    segs.advance = last ? a.step_bytes : 0;
-    if (!e) e = lbmk::launch_copy(segs, g->stream);
-    segs.n = 0;
-    segs.done = nullptr;
-  };
-  // (the outer snapshot of this step, every patch at the step's start, was
-  // taken with the previous step's last copy, or before the first step)
-  for (int k = 1; k <= KI; ++k) {
-    if (lbm_status st = run_instant(g, k)) return st;
-    // the reconstruction values of the children that exploded at k
+  // copy k, issued once instant k (k = 0: the previous step) has been issued
+  auto copy = [&](int k, bool advance) {
+    if (side && !e) e = cudaEventRecord(g->rec_ev[k], g->stream);
+    if (side && !e) e = cudaStreamWaitEvent(cs, g->rec_ev[k], 0);
+    const int kv = k ? k : KI;  // the instant whose reconstruction values copy k takes
     for (size_t pi = 0; pi < g->hg.P.size(); ++pi)
-      if (a.smp_rec_off[pi][k] != (size_t)-1)
-        add(a.smp_rec_off[pi][k], g->base + g->hg.P[pi].off_smp_val, 31 * g->hg.P[pi].n_points() * g->hg.real_bytes);
-    // inner snapshot k: the levels >= 1 after instant k
-    if (k < KI)
-      for (size_t pi = 0; pi < g->hg.P.size(); ++pi) {
-        const HostPatch& p = g->hg.P[pi];
-        if (p.level == 0) continue;
+      if (a.smp_rec_off[pi][kv] != (size_t)-1)
+        add(a.smp_rec_off[pi][kv], g->base + g->hg.P[pi].off_smp_val,
+            31 * g->hg.P[pi].n_points() * g->hg.real_bytes);
+    for (size_t pi = 0; pi < g->hg.P.size(); ++pi) {
+      const HostPatch& p = g->hg.P[pi];
+      if (k == 0)
+        add(a.step_bytes + a.snap_patch_off[pi], g->base + p.off_f[p.cur], 27 * (size_t)p.plane * g->hg.pop_bytes);
+      else if (p.level > 0)
         add(a.snap_bytes + (size_t)(k - 1) * a.inner_bytes + a.inner_patch_off[pi], g->base + p.off_f[p.cur],
             27 * (size_t)p.plane * g->hg.pop_bytes);
-      }
-    if (k < KI) flush(false);
-    if (e) return cuda_check(g, e, "adjoint snapshot");
+    }
+    // the advancing copy's last block moves the word on when it is done
+    segs.done = advance ? done : nullptr;
+    segs.advance = advance ? a.step_bytes : 0;
+    if (!e) e = lbmk::launch_copy(segs, cs);
+    segs.n = 0;
+    segs.done = nullptr;
+    if (side && !e) e = cudaEventRecord(g->rec_cp[k], cs);
+  };
+  copy(0, true);
+  for (int k = 1; k <= KI && !e; ++k) {
+    if (side && k >= 2) e = cudaStreamWaitEvent(g->stream, g->rec_cp[k - 2], 0);
+    if (e) break;
+    if (lbm_status st = run_instant(g, k)) return st;
+    if (k < KI) copy(k, false);
   }
-  // the outer snapshot of the next step (the state after this one), in the
-  // same launch as the last reconstruction values; it advances the base word
-  for (size_t pi = 0; pi < g->hg.P.size(); ++pi) {
-    const HostPatch& p = g->hg.P[pi];
-    add(a.step_bytes + a.snap_patch_off[pi], g->base + p.off_f[p.cur], 27 * (size_t)p.plane * g->hg.pop_bytes);
-  }
-  flush(true);
+  if (side && !e) e = cudaStreamWaitEvent(g->stream, g->rec_cp[KI - 1], 0);
   return cuda_check(g, e, "adjoint snapshot");
 }
 
-// The outer snapshot of the segment's first step, at the record's base word.
-cudaError_t first_snapshot(lbm_grid* g, const AdjLayout& a, unsigned long long* slot) {
+// The reconstruction values of the segment's last step at its last instant,
+// which no next step's copy 0 takes.
+cudaError_t last_values(lbm_grid* g, const AdjLayout& a, unsigned long long* slot) {
+  const int KI = 1 << (g->hg.nlev - 1);
   lbmk::CopySegs segs{};
   segs.rel = slot;
   cudaError_t e = cudaSuccess;
   for (size_t pi = 0; pi < g->hg.P.size() && !e; ++pi) {
+    if (a.smp_rec_off[pi][KI] == (size_t)-1) continue;
     if (segs.n == lbmk::kCopySegs) {
       e = lbmk::launch_copy(segs, g->stream);
       segs.n = 0;
     }
-    const HostPatch& p = g->hg.P[pi];
-    segs.dst[segs.n] = reinterpret_cast<void*>(a.snap_patch_off[pi]);
-    segs.src[segs.n] = g->base + p.off_f[p.cur];
-    segs.bytes[segs.n] = 27 * (size_t)p.plane * g->hg.pop_bytes;
+    segs.dst[segs.n] = reinterpret_cast<void*>(a.smp_rec_off[pi][KI]);
+    segs.src[segs.n] = g->base + g->hg.P[pi].off_smp_val;
+    segs.bytes[segs.n] = 31 * g->hg.P[pi].n_points() * g->hg.real_bytes;
     ++segs.n;
   }
   if (!e) e = lbmk::launch_copy(segs, g->stream);
@@ -1472,8 +1507,7 @@ lbm_status lbm_adjoint_step(lbm_grid_t g, const void* ckpt, int32_t K, void* lam
   // snapshots); the record's address is a device word the steps advance, so
   // the recording step replays as one CUDA graph per buffer parity
   auto* slot = reinterpret_cast<unsigned long long*>(ws + a.slot_off);
-  e = lbmk::launch_word(slot, (unsigned long long)(uintptr_t)(ws + a.snap_off), 0, g->stream);
-  if (!e) e = first_snapshot(g, a, slot);
+  e = lbmk::launch_word(slot, (unsigned long long)(uintptr_t)(ws + a.snap_off - a.step_bytes), 0, g->stream);
   if (e) return cuda_check(g, e, "adjoint record");
   for (int s = 0; s < K; ++s) {
     if (!g->graphs || g->timing || !g->rec_warm) {
@@ -1499,6 +1533,7 @@ lbm_status lbm_adjoint_step(lbm_grid_t g, const void* ckpt, int32_t K, void* lam
     for (auto& p : g->hg.P)
       if ((KI >> (L - 1 - p.level)) & 1) p.cur ^= 1;
   }
+  if (cudaError_t e2 = last_values(g, a, slot)) return cuda_check(g, e2, "adjoint record");
   if (!g->graphs || g->timing || !g->adj_swept) {
     // the first walk runs directly, so that capture finds every kernel loaded
     if (lbm_status st = adjoint_walk(g, K, lam, lcur, a, ws)) return st;
