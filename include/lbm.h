@@ -209,9 +209,11 @@ lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps);
 /* Autotuner of the instant schedule.  Isothermal model: a variant is a TMA
  * kernel (load stages in shared memory x CTAs per SM the register allocation
  * aims for; for FP32 arithmetic also the node-pair kernels on packed FP32x2
- * instructions) and a schedule of the reconstruction samples (after the TMA
- * pass, or beside it on the coupling streams): variant v = kernel + n_kernels *
- * schedule, 8 variants (4 for FP64 storage), all with identical results.
+ * instructions; last, the tile shape: 64-node tiles instead of 128, for rows
+ * narrower than a 128-node tile) and a schedule of the reconstruction samples
+ * (after the TMA pass, or beside it on the coupling streams): variant v =
+ * kernel + n_kernels * schedule, 10 variants (6 for FP64 storage), all with
+ * identical results.
  * Thermal model: 2 variants of its TMA pass (f and g stored from registers
  * straight to memory, or through a shared-memory stage by TMA), identical
  * results.  This times `trials` coarse steps of each variant

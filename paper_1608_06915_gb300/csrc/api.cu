@@ -116,11 +116,15 @@ struct lbm_grid {
   cudaEvent_t fwd_pre = nullptr;  // the instant's pre-states are ready (before its TMA pass)
   std::vector<cudaEvent_t> patch_done;  // thermal model: a patch's stream-collide has been issued
   // the adjoint's recording step: its snapshot copies run on rec_side beside
-  // the instants; rec_ev[k] marks instant k issued, rec_cp[k] copy k done
-  cudaStream_t rec_side = nullptr;
+  // the instants; rec_ev[k] marks instant k issued, rec_cp[k] copy k done;
+  // level 0's outer snapshot runs on rec_side0 (rec_l0: done)
+  cudaStream_t rec_side = nullptr, rec_side0 = nullptr;
+  cudaEvent_t rec_l0 = nullptr;
   std::vector<cudaEvent_t> rec_ev, rec_cp;
   ~lbm_grid() {
     if (rec_side) cudaStreamDestroy(rec_side);
+    if (rec_side0) cudaStreamDestroy(rec_side0);
+    if (rec_l0) cudaEventDestroy(rec_l0);
     for (auto& x : rec_ev)
       if (x) cudaEventDestroy(x);
     for (auto& x : rec_cp)
@@ -313,7 +317,9 @@ lbm_status run_instant(lbm_grid* g, int k) {
   if (!hg.thermal) {
     // TMA tile pass of every patch stepped at this instant: one persistent
     // launch per 8 patches, whatever their levels and sizes
+    // (the 64-node tile variant takes the half-tile lists and their load descriptors)
     std::vector<lbmk::TmaLaunchPatch> batch;
+    const bool half = lbmk::sc_tma_tile_nodes(storage, g->variant) == 64;
     double nodes = 0;
     for (int lev = 0; lev < L; ++lev) {
       const int stride = 1 << (L - 1 - lev);
@@ -321,9 +327,11 @@ lbm_status run_instant(lbm_grid* g, int k) {
       const int odd = (lev > 0 && (k / stride) % 2) ? 1 : 0;
       for (auto& p : hg.P) {
         if (p.level != lev || p.tiles_pure[odd].empty()) continue;
-        batch.push_back({p.tmap[p.cur], p.tmapo[1 - p.cur], p.tmapw[p.cur], view(g, p), g->base + p.off_f[p.cur],
-                         at<unsigned long long>(g, p.off_tiles_pure[odd]), (int64_t)p.tiles_pure[odd].size(),
-                         p.beta, level_force(g, lev)});
+        batch.push_back({half ? p.tmap64[p.cur] : p.tmap[p.cur], p.tmapo[1 - p.cur], p.tmapw[p.cur], view(g, p),
+                         g->base + p.off_f[p.cur],
+                         at<unsigned long long>(g, half ? p.off_tiles_half[odd] : p.off_tiles_pure[odd]),
+                         (int64_t)(half ? p.tiles_half[odd].size() : p.tiles_pure[odd].size()), p.beta,
+                         level_force(g, lev)});
         nodes += p.n_tma[odd];
       }
     }
@@ -645,6 +653,8 @@ lbm_status lbm_grid_bind(lbm_grid_t g, void* dev_ptr, size_t bytes, void* cuda_s
     if (!e) e = up(p.off_wq_idx, p.wq_idx.data(), 4 * p.wq_idx.size());
     for (int k = 0; k < 2; ++k)
       if (!e) e = up(p.off_tiles_pure[k], p.tiles_pure[k].data(), 8 * p.tiles_pure[k].size());
+    for (int k = 0; k < 2; ++k)
+      if (!e) e = up(p.off_tiles_half[k], p.tiles_half[k].data(), 8 * p.tiles_half[k].size());
     for (int k = 0; k < 2; ++k) {
       if (!e) e = up(p.off_tiles_mixed[k], p.tiles_mixed[k].data(), 4 * p.tiles_mixed[k].size());
       if (!e) e = up(p.off_fix_nodes[k], p.fix_nodes[k].data(), 4 * p.fix_nodes[k].size());
@@ -657,6 +667,7 @@ lbm_status lbm_grid_bind(lbm_grid_t g, void* dev_ptr, size_t bytes, void* cuda_s
       e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmap[k], g->base + p.off_f[k], view(g, p), 0);
       if (!e) e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmapo[k], g->base + p.off_f[k], view(g, p), 1);
       if (!e) e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmapw[k], g->base + p.off_f[k], view(g, p), 2);
+      if (!e) e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmap64[k], g->base + p.off_f[k], view(g, p), 3);
       if (g->hg.thermal) {
         if (!e) e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmapg[k], g->base + p.off_g[k], view(g, p), 0);
         if (!e) e = lbmk::make_tensor_map(g->hg.desc.storage, p.tmapgo[k], g->base + p.off_g[k], view(g, p), 1);
@@ -1140,13 +1151,19 @@ uint8_t* pre_state(const lbm_grid* g, const AdjLayout& a, uint8_t* step, int pi,
 // neither the states after instant k nor the values copy k reads (a patch's
 // state buffer is rewritten at its second step after k, its values at its
 // next explode, both at k + 2 or later); so instant m waits for copy m - 2
-// only, and the step ends after its last copy.
+// only, and the step ends after its last copy.  Level 0 steps once per
+// coarse step, so its step-start state stays unwritten through the step: with
+// refined levels, its part of copy 0 runs on a second stream once copy 0 has
+// advanced the word, beside the instants, and only the step's end waits for it.
 lbm_status recording_step(lbm_grid* g, const AdjLayout& a, unsigned long long* slot) {
   const int L = g->hg.nlev, KI = 1 << (L - 1);
   const bool side = !g->timing;
   cudaError_t e = cudaSuccess;
+  const bool split = L > 1;  // level 0's outer snapshot apart from copy 0
   if (side) {
     if (!g->rec_side) e = cudaStreamCreateWithFlags(&g->rec_side, cudaStreamNonBlocking);
+    if (!e && !g->rec_side0) e = cudaStreamCreateWithFlags(&g->rec_side0, cudaStreamNonBlocking);
+    if (!e && !g->rec_l0) e = cudaEventCreateWithFlags(&g->rec_l0, cudaEventDisableTiming);
     for (auto* v : {&g->rec_ev, &g->rec_cp})
       while (!e && v->size() < (size_t)KI + 1) {
         cudaEvent_t x = nullptr;
@@ -1180,7 +1197,7 @@ lbm_status recording_step(lbm_grid* g, const AdjLayout& a, unsigned long long* s
             31 * g->hg.P[pi].n_points() * g->hg.real_bytes);
     for (size_t pi = 0; pi < g->hg.P.size(); ++pi) {
       const HostPatch& p = g->hg.P[pi];
-      if (k == 0)
+      if (k == 0 && !(split && p.level == 0))
         add(a.step_bytes + a.snap_patch_off[pi], g->base + p.off_f[p.cur], 27 * (size_t)p.plane * g->hg.pop_bytes);
       else if (p.level > 0)
         add(a.snap_bytes + (size_t)(k - 1) * a.inner_bytes + a.inner_patch_off[pi], g->base + p.off_f[p.cur],
@@ -1195,6 +1212,27 @@ lbm_status recording_step(lbm_grid* g, const AdjLayout& a, unsigned long long* s
     if (side && !e) e = cudaEventRecord(g->rec_cp[k], cs);
   };
   copy(0, true);
+  if (split) {
+    // level 0's outer snapshot, into the record the word now holds
+    cudaStream_t c0 = side ? g->rec_side0 : g->stream;
+    lbmk::CopySegs s0{};
+    s0.rel = slot;
+    if (side && !e) e = cudaStreamWaitEvent(c0, g->rec_cp[0], 0);
+    for (size_t pi = 0; pi < g->hg.P.size() && !e; ++pi) {
+      const HostPatch& p = g->hg.P[pi];
+      if (p.level != 0) continue;
+      if (s0.n == lbmk::kCopySegs) {
+        e = lbmk::launch_copy(s0, c0);
+        s0.n = 0;
+      }
+      s0.dst[s0.n] = reinterpret_cast<void*>(a.snap_patch_off[pi]);
+      s0.src[s0.n] = g->base + p.off_f[p.cur];
+      s0.bytes[s0.n] = 27 * (size_t)p.plane * g->hg.pop_bytes;
+      ++s0.n;
+    }
+    if (!e) e = lbmk::launch_copy(s0, c0);
+    if (side && !e) e = cudaEventRecord(g->rec_l0, c0);
+  }
   for (int k = 1; k <= KI && !e; ++k) {
     if (side && k >= 2) e = cudaStreamWaitEvent(g->stream, g->rec_cp[k - 2], 0);
     if (e) break;
@@ -1202,6 +1240,7 @@ lbm_status recording_step(lbm_grid* g, const AdjLayout& a, unsigned long long* s
     if (k < KI) copy(k, false);
   }
   if (side && !e) e = cudaStreamWaitEvent(g->stream, g->rec_cp[KI - 1], 0);
+  if (side && split && !e) e = cudaStreamWaitEvent(g->stream, g->rec_l0, 0);
   return cuda_check(g, e, "adjoint snapshot");
 }
 

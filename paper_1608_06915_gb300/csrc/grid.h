@@ -50,6 +50,9 @@ struct HostPatch {
   int64_t ntx = 0;
   // TMA path ([0] even, [1] odd substeps): x-tile | y<<16 | z<<32 | bounce mask<<48 | flags<<57
   std::vector<uint64_t> tiles_pure[2];
+  // the same tiles as halves of 64 nodes (x-tile in units of 64; a half that
+  // starts beyond the row is left out), for the 64-node tile variant
+  std::vector<uint64_t> tiles_half[2];
   std::vector<uint32_t> tiles_mixed[2];  // other tiles with nodes to update: [0] even, [1] odd steps
   std::vector<uint32_t> tiles_all[2];    // every tile with nodes to update (thermal model, node by node)
   std::vector<uint32_t> fix_nodes[2];    // nodes of TMA tiles recomputed node by node after the tile pass
@@ -57,6 +60,7 @@ struct HostPatch {
   alignas(64) unsigned char tmap[2][128];   // TMA load descriptors of the two population buffers
   alignas(64) unsigned char tmapo[2][128];  // TMA store descriptors
   alignas(64) unsigned char tmapw[2][128];  // TMA 16-byte wrap descriptors
+  alignas(64) unsigned char tmap64[2][128];  // TMA load descriptors of 64-node tiles
   alignas(64) unsigned char tmapg[2][128];   // the same three for the thermal g buffers
   alignas(64) unsigned char tmapgo[2][128];
   alignas(64) unsigned char tmapgw[2][128];
@@ -91,7 +95,7 @@ struct HostPatch {
 
   // device placement (byte offsets into the bound buffer)
   size_t off_f[2]{}, off_g[2]{}, off_type = 0;
-  size_t off_tiles_pure[2]{}, off_tiles_mixed[2]{}, off_tiles_all[2]{}, off_fix_nodes[2]{};
+  size_t off_tiles_pure[2]{}, off_tiles_half[2]{}, off_tiles_mixed[2]{}, off_tiles_all[2]{}, off_fix_nodes[2]{};
   size_t off_ex_node = 0, off_ex_src = 0, off_pt_src = 0, off_use_ptr = 0, off_use_ent = 0;
   size_t off_smp_node = 0, off_smp_kind = 0, off_smp_val = 0, off_cf_parent = 0, off_cf_child = 0;
   size_t off_drag_node = 0, off_drag_mask = 0, off_wq = 0, off_wq_idx = 0;

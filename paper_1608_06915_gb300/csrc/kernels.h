@@ -97,7 +97,8 @@ cudaError_t launch_adj_grad_u0(int storage, const PatchDev& p, const void* fin, 
 // bytes, of the source buffer with the load box, of the destination buffer with
 // the store box, and of the source buffer with the wrap box; tiles:
 // x-tile | y << 16 | z << 32) and mixed tiles node by node (tile id
-// = (z * ny + y) * ntx + tx); a tile is 128 nodes along x.
+// = (z * ny + y) * ntx + tx); a tile is 128 nodes along x, or 64 for the
+// 64-node tile variant (its load descriptor and tile list then hold halves).
 // One patch of a batched TMA tile pass.
 struct TmaLaunchPatch {
   const void* tmap_in;    // load descriptor of the current buffer
@@ -117,13 +118,16 @@ struct TmaLaunchPatch {
 cudaError_t launch_sc_tma(int storage, const TmaLaunchPatch* ps, int n, int variant, int lbgk, int wait_sleeps,
                           int* status, cudaStream_t st);
 int sc_tma_variants(int storage);
+// nodes per tile of a variant: 128, or 64 (tmap_in of kind 3, the half-tile list)
+int sc_tma_tile_nodes(int storage, int variant);
 // node-by-node recomputation of listed nodes (after the TMA tile pass)
 cudaError_t launch_sc_nodes(int storage, const PatchDev& p, const void* fin, void* fout, const uint32_t* nodes,
                             int64_t n, double beta, const Force& F, int lbgk, int* status, cudaStream_t st);
 cudaError_t launch_sc_tiles(int storage, const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,
                             int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk, int* status,
                             cudaStream_t st);
-// kind 0: load box (tile row + halos), 1: store box (tile row), 2: 16-byte wrap box
+// kind 0: load box (128-node tile row + halos), 1: store box (one warp's 32 nodes),
+// 2: 16-byte wrap box, 3: load box of a 64-node tile row + halos
 cudaError_t make_tensor_map(int storage, void* out128, const void* base, const PatchDev& p, int kind);
 
 cudaError_t launch_coalesce(int storage, const PatchDev& child, const void* fin_child, const PatchDev& parent,

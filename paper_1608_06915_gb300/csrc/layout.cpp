@@ -471,6 +471,7 @@ std::string build_layout(HostGrid& g) {
     p.ntx = (p.dim[0] + 127) / 128;
     for (int k = 0; k < 2; ++k) {
       p.tiles_pure[k].clear();
+      p.tiles_half[k].clear();
       p.tiles_mixed[k].clear();
       p.tiles_all[k].clear();
       p.fix_nodes[k].clear();
@@ -549,6 +550,11 @@ std::string build_layout(HostGrid& g) {
       for (int k = 0; k < 2; ++k) {
         p.n_tma[k] += R.ntma[k];
         p.tiles_pure[k].insert(p.tiles_pure[k].end(), R.pure[k].begin(), R.pure[k].end());
+        for (uint64_t t : R.pure[k]) {
+          const uint64_t tx = t & 0xffffu, rest = t & ~(uint64_t)0xffffu;
+          p.tiles_half[k].push_back(rest | (2 * tx));
+          if ((int64_t)(2 * tx + 1) * 64 < p.dim[0]) p.tiles_half[k].push_back(rest | (2 * tx + 1));
+        }
         p.tiles_mixed[k].insert(p.tiles_mixed[k].end(), R.mixed[k].begin(), R.mixed[k].end());
         p.tiles_all[k].insert(p.tiles_all[k].end(), R.all[k].begin(), R.all[k].end());
         p.fix_nodes[k].insert(p.fix_nodes[k].end(), R.fix[k].begin(), R.fix[k].end());
@@ -858,6 +864,8 @@ size_t plan_memory(HostGrid& g) {
     p.off_type = take((size_t)p.plane);
     p.off_tiles_pure[0] = take(8 * p.tiles_pure[0].size());
     p.off_tiles_pure[1] = take(8 * p.tiles_pure[1].size());
+    p.off_tiles_half[0] = take(8 * p.tiles_half[0].size());
+    p.off_tiles_half[1] = take(8 * p.tiles_half[1].size());
     p.off_tiles_all[0] = take(4 * p.tiles_all[0].size());
     p.off_tiles_all[1] = take(4 * p.tiles_all[1].size());
     p.off_tiles_mixed[0] = take(4 * p.tiles_mixed[0].size());

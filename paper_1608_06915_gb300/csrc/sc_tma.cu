@@ -20,8 +20,12 @@ cudaError_t launch_sc_tma(int storage, const TmaLaunchPatch* ps, int n, int vari
 }
 
 // scalar kernels 0, 1 for every storage; packed-pair kernels 2, 3 for FP32
-// arithmetic (FP32 and 16-bit storage)
-int sc_tma_variants(int storage) { return storage == LBM_FP64 ? 2 : 4; }
+// arithmetic (FP32 and 16-bit storage); last, the scalar kernel on 64-node tiles
+int sc_tma_variants(int storage) { return storage == LBM_FP64 ? 3 : 5; }
+
+int sc_tma_tile_nodes(int storage, int variant) {
+  return variant == sc_tma_variants(storage) - 1 ? 64 : 128;
+}
 
 cudaError_t launch_sc_tiles(int storage, const PatchDev& p, const void* fin, void* fout, const uint32_t* tiles,
                             int64_t ntiles, int ntx, double beta, const Force& F, int odd, int lbgk, int* status,
@@ -58,8 +62,9 @@ cudaError_t launch_sc_nodes(int storage, const PatchDev& p, const void* fin, voi
 
 // Tensor map of one population buffer, 4-D [27][nz][ny][nx] with the row
 // pitch nxp.  Boxes: loads (W, 1, 1, 3) -- one row of three consecutive
-// populations; stores (32, 1, 1, 27) -- one warp's segment of all populations;
-// wrap (16 bytes, 1, 1, 1).  The x extent is the patch's node count, not the
+// populations, W of a 128-node tile (kind 0) or of a 64-node tile (kind 3);
+// stores (32, 1, 1, 27) -- one warp's segment of all populations; wrap (16
+// bytes, 1, 1, 1).  The x extent is the patch's node count, not the
 // padded pitch: the padding columns of a ragged row then lie outside the
 // tensor, so loads fill them without reading memory and stores skip them.
 cudaError_t make_tensor_map(int storage, void* out, const void* base, const PatchDev& p, int kind) {
@@ -98,6 +103,7 @@ cudaError_t make_tensor_map(int storage, void* out, const void* base, const Patc
   cuuint32_t np = 3;
   if (kind == 1) w = TmaCfg<float>::OSEG, np = 27;  // store box: one warp's 32-node segment
   if (kind == 2) w = 16 / es, np = 1;               // wrap box: 16 bytes
+  if (kind == 3) w -= TmaCfg<float>::BX - 64;        // load box of a 64-node tile
   const cuuint32_t box[4] = {(cuuint32_t)w, 1, 1, np};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = encode(reinterpret_cast<CUtensorMap*>(out), dt, 4, const_cast<void*>(base), dims, strides, box, estr,

@@ -51,18 +51,25 @@
 
 namespace lbmk {
 
-// Kernel variants the autotuner picks from: load stages DI and the CTAs per SM
-// the register allocation aims for (MINB).  Results do not depend on the variant.
+// Kernel variants the autotuner picks from: load stages DI, the CTAs per SM
+// the register allocation aims for (MINB) and the tile shape, BX nodes along
+// x.  Rows narrower than 128 nodes leave consumer warps of a 128-node tile
+// idle; 64-node tiles (two consumer warps, from the halves of the 128-node
+// tile list) keep them busy at more CTAs per SM.  Results do not depend on the
+// variant.
 template <typename S>
 struct TmaVariants {
-  static constexpr int N = 2;
-  static constexpr int DI[N] = {sizeof(S) == 8 ? 2 : 3, sizeof(S) == 8 ? 1 : 2};
-  static constexpr int MINB[N] = {1, sizeof(S) == 8 ? 3 : 4};
+  static constexpr int N = 3;
+  static constexpr int DI[N] = {sizeof(S) == 8 ? 2 : 3, sizeof(S) == 8 ? 1 : 2, 2};
+  static constexpr int MINB[N] = {1, sizeof(S) == 8 ? 3 : 4, sizeof(S) == 8 ? 4 : 6};
+  static constexpr int BX[N] = {128, 128, 64};
 };
 
-template <typename S, int DI_ = TmaVariants<S>::DI[0]>
+template <typename S, int DI_ = TmaVariants<S>::DI[0], int BX_ = 128>
 struct TmaCfg {
-  static constexpr int BX = 128;                                        // nodes per tile
+  static_assert(BX_ == 64 || BX_ == 128, "tile shapes");
+  static constexpr int BX = BX_;                                        // nodes per tile
+  static constexpr int NCW = BX / 32;                                   // consumer warps
   static constexpr int H = 16 / (int)sizeof(S);                         // halo, elements
   static constexpr int W = BX + 2 * H;                                  // load box width, elements
   static constexpr int GROUP = (3 * W * (int)sizeof(S) + 127) / 128 * 128;  // bytes per three-row box
@@ -70,13 +77,13 @@ struct TmaCfg {
   static constexpr int OSEGB = (27 * OSEG * (int)sizeof(S) + 127) / 128 * 128;  // bytes per [27][32] segment
   static constexpr int SIDE = 128;                                      // one 16-byte wrap box, padded
   static constexpr int STAGE = 9 * GROUP + 18 * SIDE;                   // rows + 2 x 9 wrap boxes
-  static constexpr int OSTAGE = 4 * OSEGB;                              // [warp][population][32 nodes]
+  static constexpr int OSTAGE = NCW * OSEGB;                            // [warp][population][32 nodes]
   static constexpr uint32_t TX = 27u * W * (uint32_t)sizeof(S);        // bytes of the 27 row loads
   static constexpr uint32_t TXW = 9u * 16u;                             // bytes of 9 wrap boxes
   static constexpr int DI = DI_;                                        // load stages
   static constexpr int DO = 1;                                          // store stages
   static constexpr int SMEM = DI * STAGE + DO * OSTAGE + 128;           // + slack for 128-byte alignment
-  static constexpr int THREADS = 160;                                   // 4 consumer warps + 1 producer
+  static constexpr int THREADS = BX + 32;                               // consumer warps + 1 producer
 };
 
 template <typename S>
@@ -208,9 +215,10 @@ __device__ __forceinline__ int tile_flags(unsigned long long t) { return (int)((
 
 // Shared-memory row of population i in a load stage (elements): group i / 3,
 // row i % 3 of the three-row box.
-template <typename S>
+template <typename S, int BX = 128>
 __device__ __forceinline__ constexpr int row_base(int i) {
-  return (i / 3) * (TmaCfg<S>::GROUP / (int)sizeof(S)) + (i % 3) * TmaCfg<S>::W;
+  using C = TmaCfg<S, TmaVariants<S>::DI[0], BX>;
+  return (i / 3) * (C::GROUP / (int)sizeof(S)) + (i % 3) * C::W;
 }
 
 // Walls across y or z: when the source row j = (c_y + 1) + 3 (c_z + 1) of a
@@ -265,10 +273,11 @@ __device__ __forceinline__ int batch_entry(const TmaBatch<S, R>& b, int t) {
   return e;
 }
 
-// MINB: CTAs per SM the register allocation aims for (launch bounds).
-template <typename S, typename R, int FM, int DI, int MINB>
-__global__ void __launch_bounds__(160, MINB) k_sc_tma(const __grid_constant__ TmaBatch<S, R> b) {
-  using C = TmaCfg<S, DI>;
+// MINB: CTAs per SM the register allocation aims for (launch bounds); BX:
+// nodes per tile (BX / 32 consumer warps, then the producer warp).
+template <typename S, typename R, int FM, int DI, int MINB, int BX = 128>
+__global__ void __launch_bounds__(BX + 32, MINB) k_sc_tma(const __grid_constant__ TmaBatch<S, R> b) {
+  using C = TmaCfg<S, DI, BX>;
   const int ntiles = b.ntiles;
   int* status = b.status;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -281,13 +290,13 @@ __global__ void __launch_bounds__(160, MINB) k_sc_tma(const __grid_constant__ Tm
   if (tid == 0) {
     for (int s = 0; s < C::DI; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 4);
+      mbar_init(&empty[s], C::NCW);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  if (warp == 4) {
+  if (warp == C::NCW) {
     // ---------------- producer (one thread: TMA operands stay warp-uniform) ----------------
     if (lane != 0) return;
     for (int q = 0; q < b.n; ++q) {
@@ -337,7 +346,7 @@ __global__ void __launch_bounds__(160, MINB) k_sc_tma(const __grid_constant__ Tm
     return;
   }
 
-  // ---------------- consumers (warps 0-3) ----------------
+  // ---------------- consumers (warps 0 .. NCW - 1) ----------------
   for (int k = 0; k < nmine; ++k) {
     const int s = k % C::DI;
     const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(k / C::DI) & 1u, b.wait_sleeps);
@@ -359,14 +368,14 @@ __global__ void __launch_bounds__(160, MINB) k_sc_tma(const __grid_constant__ Tm
     if (bm == 0) {
       unroll<27>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        f[i] = SCvt<S>::to(st[row_base<S>(i) + C::H + tid - CX(i)]);
+        f[i] = SCvt<S>::to(st[row_base<S, BX>(i) + C::H + tid - CX(i)]);
       });
     } else {
       unroll<27>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const bool b = (bm >> (i / 3)) & 1;
-        f[i] = SCvt<S>::to(st[b ? row_base<S>(3 * (i / 3) + 2 - i % 3) + C::H + tid
-                                : row_base<S>(i) + C::H + tid - CX(i)]);
+        f[i] = SCvt<S>::to(st[b ? row_base<S, BX>(3 * (i / 3) + 2 - i % 3) + C::H + tid
+                                : row_base<S, BX>(i) + C::H + tid - CX(i)]);
       });
     }
     if (p.span[0] && (x == 0 || x == p.dim[0] - 1)) {
@@ -386,7 +395,7 @@ __global__ void __launch_bounds__(160, MINB) k_sc_tma(const __grid_constant__ Tm
         // zero-gradient outlet: c_x = -1 populations from the node itself along x
         unroll<27>([&](auto I) {
           constexpr int i = decltype(I)::value;
-          if (CX(i) == -1 && !((bm >> (i / 3)) & 1)) f[i] = SCvt<S>::to(st[row_base<S>(i) + C::H + tid]);
+          if (CX(i) == -1 && !((bm >> (i / 3)) & 1)) f[i] = SCvt<S>::to(st[row_base<S, BX>(i) + C::H + tid]);
         });
       }
       if ((fl & 1) && x == 0) {
@@ -704,10 +713,10 @@ __global__ void __launch_bounds__(128) k_sc_nodes_w(PatchDev p, const S* __restr
 
 template <typename S, typename R, int FM, int V>
 cudaError_t launch_tma_v(const TmaBatch<S, R>& b, cudaStream_t st) {
-  constexpr int DI = TmaVariants<S>::DI[V], MINB = TmaVariants<S>::MINB[V];
-  using C = TmaCfg<S, DI>;
+  constexpr int DI = TmaVariants<S>::DI[V], MINB = TmaVariants<S>::MINB[V], BX = TmaVariants<S>::BX[V];
+  using C = TmaCfg<S, DI, BX>;
   static int blocks_per_sm = -1, sms = 0;
-  auto kern = k_sc_tma<S, R, FM, DI, MINB>;
+  auto kern = k_sc_tma<S, R, FM, DI, MINB, BX>;
   if (blocks_per_sm < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e) return e;
@@ -752,12 +761,19 @@ cudaError_t launch_tma2_v(const TmaBatch<S, float>& b, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Variants: 0, 1 the scalar kernel on 128-node tiles; for FP32 arithmetic
+// 2, 3 the node-pair kernel; last (2 for FP64, 4 otherwise) the scalar kernel
+// on 64-node tiles, whose batch carries the half-tile lists and descriptors
+// (sc_tma_tile_nodes).
 template <typename S, typename R, int FM>
 cudaError_t launch_tma_fm(const TmaBatch<S, R>& b, int variant, cudaStream_t st) {
-  static_assert(TmaVariants<S>::N == 2, "variant dispatch");
+  static_assert(TmaVariants<S>::N == 3 && TmaVariants<S>::BX[2] == 64, "variant dispatch");
   if constexpr (std::is_same<R, float>::value) {
     if (variant == 2) return launch_tma2_v<S, FM, 0>(b, st);
     if (variant == 3) return launch_tma2_v<S, FM, 1>(b, st);
+    if (variant == 4) return launch_tma_v<S, R, FM, 2>(b, st);
+  } else {
+    if (variant == 2) return launch_tma_v<S, R, FM, 2>(b, st);
   }
   return variant == 1 ? launch_tma_v<S, R, FM, 1>(b, st) : launch_tma_v<S, R, FM, 0>(b, st);
 }

@@ -507,12 +507,13 @@ def test_thermal_tma_variants_agree(pr):
 @pytest.mark.parametrize("storage", ["fp32", "fp64", "fp16s"])
 def test_tma_variants_give_identical_results(storage):
     """The autotuner's variants differ in staging, occupancy, nodes per
-    thread (single nodes, or node pairs on the packed FP32x2 instructions)
-    and the schedule of the reconstruction samples only: same bits after
-    several coarse steps on a three-level channel with walls and force, and
-    on the four-level sphere, for every variant (four TMA kernels for FP32
-    arithmetic, two for FP64, times two schedules)."""
-    nv = 4 if storage == "fp64" else 8
+    thread (single nodes, or node pairs on the packed FP32x2 instructions),
+    tile shape (128- or 64-node tiles) and the schedule of the reconstruction
+    samples only: same bits after several coarse steps on a three-level
+    channel with walls and force, and on the four-level sphere, for every
+    variant (five TMA kernels for FP32 arithmetic, three for FP64, times two
+    schedules)."""
+    nv = 6 if storage == "fp64" else 10
     import torch
     for case, fields in [
         (dict(I.channel_small_case(), accel0=(1e-5, 0, 0)),
