@@ -296,10 +296,12 @@ def gamma_indicator(g, bpu, peak, block=8, reps=10):
                 bytes_per_node=bpu / 2, achieved_gbs=gbs, frac=gbs / peak)
 
 
-def adjoint_ratio(dev, storage="fp32", K=20):
+def adjoint_ratio(dev, storage="fp32", K=20, reps=3):
     """Time of the discrete adjoint of K coarse steps (lbm_adjoint_step: restore,
     recompute with snapshots, reverse) over the time of K forward steps, on the
-    64^3 box with the [24,40]^3 box refined 2x (divergence-free random field)."""
+    64^3 box with the [24,40]^3 box refined 2x (divergence-free random field):
+    `reps` alternating timings of each, medians."""
+    import statistics
     import torch
     from paper_1608_06915_gb300 import inputs as I
     from paper_1608_06915_gb300 import lbm as L
@@ -320,20 +322,26 @@ def adjoint_ratio(dev, storage="fp32", K=20):
     for _ in range(2):
         g.adjoint_seed(lam, ws)
         g.adjoint_step(ck, K, lam, ws)
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    torch.cuda.synchronize(dev)
-    e[0].record(g.stream)
-    g.step(K)
-    e[1].record(g.stream)
-    g.adjoint_seed(lam, ws)
-    e[2].record(g.stream)
-    g.adjoint_step(ck, K, lam, ws)
-    e[3].record(g.stream)
-    torch.cuda.synchronize(dev)
-    fwd, adj = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    fwds, adjs = [], []
+    for _ in range(reps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize(dev)
+        e[0].record(g.stream)
+        g.step(K)
+        e[1].record(g.stream)
+        g.adjoint_seed(lam, ws)
+        e[2].record(g.stream)
+        g.adjoint_step(ck, K, lam, ws)  # leaves the state at the segment start
+        e[3].record(g.stream)
+        torch.cuda.synchronize(dev)
+        fwds.append(e[0].elapsed_time(e[1]) / K)
+        adjs.append(e[2].elapsed_time(e[3]) / K)
+    fwd, adj = statistics.median(fwds), statistics.median(adjs)
     return dict(workload="64^3 periodic, [24,40]^3 refined 2x, %s, segments of %d coarse steps" % (storage, K),
-                forward_ms_per_step=fwd / K, adjoint_ms_per_step=adj / K, ratio=adj / fwd, autotune=tune,
-                note="adjoint time includes restoring the checkpoint and recomputing the segment")
+                forward_ms_per_step=fwd, adjoint_ms_per_step=adj, ratio=adj / fwd, autotune=tune,
+                forward_ms_per_step_each=fwds, adjoint_ms_per_step_each=adjs,
+                note="medians of %d alternating timings; adjoint time includes restoring the checkpoint and "
+                     "recomputing the segment" % reps)
 
 
 def measure_workload(name, storage, steps, warmup, dev, pr=0.7, peak=None, instrument=True):

@@ -218,13 +218,14 @@ lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps);
  * straight to memory, or through a shared-memory stage by TMA), identical
  * results.  This times `trials` coarse steps of each variant
  * the way lbm_step runs them (graph replays unless lbm_graphs is off), CUDA
- * events around them, and keeps the fastest.  The state advances by
- * 1 + n_variants * (2 + trials) coarse steps: one untimed step first, and
- * per variant two untimed steps that capture its step graphs before the
- * trials.  chosen (nullable)
- * gets the variant kept, ms_per_step[0 .. min(n, max_variants)) (nullable)
- * the measured time per coarse step of each, n_variants (nullable) their
- * number.
+ * events around them, then the two fastest again over 3 * trials steps each,
+ * and keeps the faster of those.  The state advances by
+ * 1 + n_variants * (2 + trials) + 2 * (2 + 3 * trials) coarse steps (one
+ * variant: 1 + 2 + trials): one untimed step first, and per timing two
+ * untimed steps that capture the variant's step graphs before the trials.
+ * chosen (nullable) gets the variant kept, ms_per_step[0 .. min(n,
+ * max_variants)) (nullable) the measured time per coarse step of each (the
+ * longer timing for the two fastest), n_variants (nullable) their number.
  * Synchronises the bound stream; drops captured step graphs.  Without a call
  * the grid uses variant 0.  The paper has no counterpart. */
 lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms_per_step, int32_t max_variants,

@@ -84,12 +84,13 @@ struct lbm_grid {
   };
   std::vector<AdjGraph> acache;
   bool adj_swept = false;
-  // CUDA graphs of the recording step of the adjoint's recompute, keyed by the
-  // buffer indices, the record's device word and the record's size
+  // CUDA graphs of n recording steps of the adjoint's recompute, keyed by the
+  // buffer indices, the record's device word, the record's size and n
   struct RecGraph {
     std::vector<uint8_t> cur;
     const unsigned long long* slot;
     size_t step_bytes;
+    int n;
     cudaGraphExec_t exec;
   };
   std::vector<RecGraph> rcache;
@@ -821,6 +822,7 @@ lbm_status lbm_step(lbm_grid_t g, int64_t n_coarse_steps) {
 }
 
 constexpr int kAutotuneWarm = 2;
+constexpr int kAutotuneLong = 3;  // the two fastest variants are timed again over this many times the trials
 
 lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms_per_step, int32_t max_variants,
                         int32_t* n_variants) {
@@ -838,7 +840,7 @@ lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms
   g->presample = false;
   lbm_status st = e ? LBM_OK : coarse_step_eager(g);
   g->stepped = true;
-  for (int v = 0; v < nv && !e && !st; ++v) {
+  auto trial = [&](int v, int n) {
     g->variant = v % nt;
     g->presample = v >= nt;
     g->drop_graphs();
@@ -846,19 +848,29 @@ lbm_status lbm_autotune(lbm_grid_t g, int32_t trials, int32_t* chosen, float* ms
     // of both buffer parities of level 0 (or run directly without graphs)
     st = lbm_step(g, kAutotuneWarm);
     if (!st) e = cudaEventRecord(e0, g->stream);
-    if (!e && !st) st = lbm_step(g, trials);
+    if (!e && !st) st = lbm_step(g, n);
     if (!e && !st) e = cudaEventRecord(e1, g->stream);
     if (!e && !st) e = cudaEventSynchronize(e1);
     if (!e && !st) e = cudaEventElapsedTime(&ms[v], e0, e1);
-    ms[v] /= (float)trials;
+    ms[v] /= (float)n;
+  };
+  for (int v = 0; v < nv && !e && !st; ++v) trial(v, trials);
+  // the two fastest again, over three times the steps: short trials of
+  // schedules that differ by a few percent do not separate them reliably
+  int best = 0, second = nv > 1 ? 1 : 0;
+  if (ms[second] < ms[best]) std::swap(best, second);
+  for (int v = 2; v < nv; ++v) {
+    if (ms[v] < ms[best]) second = best, best = v;
+    else if (ms[v] < ms[second]) second = v;
   }
+  if (nv > 1)
+    for (int v : {best, second})
+      if (!e && !st) trial(v, kAutotuneLong * trials);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (st) return st;
   if (e) return cuda_check(g, e, "lbm_autotune");
-  int best = 0;
-  for (int v = 1; v < nv; ++v)
-    if (ms[v] < ms[best]) best = v;
+  if (nv > 1 && ms[second] < ms[best]) best = second;
   g->variant = best % nt;
   g->presample = best >= nt;
   g->stepped = true;
@@ -1445,10 +1457,10 @@ lbm_status adjoint_walk(lbm_grid* g, int K, uint8_t* lam[2], std::vector<int>& l
 
 constexpr size_t kMaxAdjGraphs = 64;
 
-// Captures one recording step of the recompute; the host-side buffer indices
-// are put back afterwards (capture launches nothing).
+// Captures n recording steps of the recompute as one graph; the host-side
+// buffer indices are put back afterwards (capture launches nothing).
 lbm_status capture_recording(lbm_grid* g, const AdjLayout& a, unsigned long long* slot, const std::vector<uint8_t>& key,
-                             cudaGraphExec_t* out) {
+                             int n, cudaGraphExec_t* out) {
   if (!g->cap_stream) {
     if (cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking))
       return cuda_check(g, e, "capture stream");
@@ -1456,7 +1468,8 @@ lbm_status capture_recording(lbm_grid* g, const AdjLayout& a, unsigned long long
   cudaStream_t keep = g->stream;
   g->stream = g->cap_stream;
   cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed);
-  lbm_status st = e ? LBM_OK : recording_step(g, a, slot);
+  lbm_status st = LBM_OK;
+  for (int j = 0; j < n && !e && !st; ++j) st = recording_step(g, a, slot);
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = e ? cudaSuccess : cudaStreamEndCapture(g->cap_stream, &graph);
   g->stream = keep;
@@ -1544,33 +1557,39 @@ lbm_status lbm_adjoint_step(lbm_grid_t g, const void* ckpt, int32_t K, void* lam
   if (e) return cuda_check(g, e, "adjoint restore");
   // recompute the segment, recording each coarse step (outer and inner
   // snapshots); the record's address is a device word the steps advance, so
-  // the recording step replays as one CUDA graph per buffer parity
+  // the segment's recording steps replay as one CUDA graph
   auto* slot = reinterpret_cast<unsigned long long*>(ws + a.slot_off);
   e = lbmk::launch_word(slot, (unsigned long long)(uintptr_t)(ws + a.snap_off - a.step_bytes), 0, g->stream);
   if (e) return cuda_check(g, e, "adjoint record");
-  for (int s = 0; s < K; ++s) {
-    if (!g->graphs || g->timing || !g->rec_warm) {
-      // the first recording step runs directly, so that capture finds every kernel loaded
+  int s0 = 0;
+  if (!g->graphs || g->timing || !g->rec_warm) {
+    // the first recording step runs directly, so that capture finds every
+    // kernel loaded (every step, without graphs or under per-launch timing)
+    const int n = (!g->graphs || g->timing) ? K : 1;
+    for (; s0 < n; ++s0)
       if (lbm_status st = recording_step(g, a, slot)) return st;
-      g->rec_warm = true;
-      continue;
-    }
+    g->rec_warm = true;
+  }
+  if (s0 < K) {
+    // the segment's remaining steps replay as one graph
+    const int n = K - s0;
     const std::vector<uint8_t> key = cur_key(g);
     cudaGraphExec_t exec = nullptr;
     for (auto& x : g->rcache)
-      if (x.cur == key && x.slot == slot && x.step_bytes == a.step_bytes) exec = x.exec;
+      if (x.cur == key && x.slot == slot && x.step_bytes == a.step_bytes && x.n == n) exec = x.exec;
     if (!exec) {
       if (g->rcache.size() >= kMaxStepGraphs) {
         for (auto& x : g->rcache) cudaGraphExecDestroy(x.exec);
         g->rcache.clear();
       }
-      if (lbm_status st = capture_recording(g, a, slot, key, &exec)) return st;
-      g->rcache.push_back({key, slot, a.step_bytes, exec});
+      if (lbm_status st = capture_recording(g, a, slot, key, n, &exec)) return st;
+      g->rcache.push_back({key, slot, a.step_bytes, n, exec});
     }
     if (cudaError_t e2 = cudaGraphLaunch(exec, g->stream)) return cuda_check(g, e2, "cudaGraphLaunch");
     const int L = g->hg.nlev, KI = 1 << (L - 1);
-    for (auto& p : g->hg.P)
-      if ((KI >> (L - 1 - p.level)) & 1) p.cur ^= 1;
+    for (int j = 0; j < n; ++j)
+      for (auto& p : g->hg.P)
+        if ((KI >> (L - 1 - p.level)) & 1) p.cur ^= 1;
   }
   if (cudaError_t e2 = last_values(g, a, slot)) return cuda_check(g, e2, "adjoint record");
   if (!g->graphs || g->timing || !g->adj_swept) {

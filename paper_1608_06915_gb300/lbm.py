@@ -352,9 +352,10 @@ class Grid:
 
     def autotune(self, trials: int = 2):
         """Times each variant (TMA kernel x schedule of the reconstruction
-        samples) over `trials` coarse steps as step() runs them, and keeps the
-        fastest: dict(chosen, ms_per_step).  The state advances by
-        1 + variants * (2 + trials) coarse steps."""
+        samples) over `trials` coarse steps as step() runs them, then the two
+        fastest over 3 * trials steps, and keeps the faster of those:
+        dict(chosen, ms_per_step).  The state advances by
+        1 + variants * (2 + trials) + 2 * (2 + 3 * trials) coarse steps."""
         chosen, n = ctypes.c_int32(), ctypes.c_int32()
         ms = (ctypes.c_float * 16)()
         _check(lib().lbm_autotune(self.handle, int(trials), ctypes.byref(chosen), ms, 16, ctypes.byref(n)),

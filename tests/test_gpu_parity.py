@@ -538,14 +538,15 @@ def test_tma_variants_give_identical_results(storage):
 
 
 def test_autotune_reports_and_keeps_the_state_consistent():
-    """autotune advances the state by 1 + variants x (2 + trials) steps, exactly as steps would."""
+    """autotune advances the state by 1 + variants x (2 + trials) + 2 x (2 + 3 trials)
+    steps (the two fastest variants timed again), exactly as steps would."""
     import torch
     case = dict(I.channel_small_case(), accel0=(1e-5, 0, 0))
     fields = lambda x, y, z, p, info: I.channel_fields(case, info["level"], info["org"], info["dim"])
     ga, o = twin(case, "fp64", fields)
     r = ga.autotune(trials=1)
     assert r["chosen"] in range(len(r["ms_per_step"])) and all(t > 0 for t in r["ms_per_step"])
-    o.step(1 + (2 + 1) * len(r["ms_per_step"]))  # trials = 1
+    o.step(1 + (2 + 1) * len(r["ms_per_step"]) + 2 * (2 + 3 * 1))  # trials = 1
     assert pop_diff(ga, o) < 1e-12
 
 
